@@ -1,0 +1,185 @@
+/*
+ * gpfdp -- GB300 (sm_103a) fitness evaluation of populations of huge
+ * prefix-encoded genetic-programming trees, full and incremental.
+ *
+ * The method is W. B. Langdon, "A Trillion Genetic Programming
+ * Instructions per Second" (arXiv 2205.03251):
+ *   - trees are flattened to one byte per node in depth-first prefix order
+ *     and kept in fixed-size preallocated buffers (Sec. 3.1, Sec. 5);
+ *   - every opcode is interpreted on every test case in one pass over the
+ *     tree (Sec. 4.2);
+ *   - children are made by subtree crossover, by copying or in place by
+ *     shifting the mother's tail (Fig. 1, Fig. 2, Sec. 5), with donated
+ *     subtrees copied out before any buffer is overwritten (Sec. 5,
+ *     "fatherless" crossover);
+ *   - a child is evaluated bottom up from the crossover point, carrying the
+ *     mother's evaluation beside it, and evaluation stops at the first node
+ *     where both agree on every test case (failed disruption propagation,
+ *     Sec. 6.2, Fig. 3).
+ *
+ * Conventions for every entry point:
+ *   - Return GP_OK (0) or a negative GP_E* code; gp_last_error() then holds
+ *     a one-line message.  No entry point aborts the process.
+ *   - Host pointers (const T* args) are read during the call only; the
+ *     library never keeps a caller pointer.  All device memory is owned by
+ *     the gp_pop object and released by gp_pop_destroy().
+ *   - Work is queued on the stream given to gp_pop_create(); calls return
+ *     before the GPU finishes except those documented as synchronising.
+ *   - Device-side failures (capacity, budget, bounded waits) are recorded
+ *     in a device status word and reported by the next synchronising call.
+ *
+ * Opcodes (one byte per node):
+ *   GP_FP32_ARITH: 0 '+', 1 '-', 2 '*', 3 protected '/', 4 x,
+ *                  5..255 constant consts[op-5]; protected '/' gives 1.0
+ *                  when the divisor equals zero (+0 or -0), else the IEEE
+ *                  single-precision quotient.  Left operand = first child.
+ *   GP_BOOL_MUX6:  0 AND, 1 OR, 2 NAND, 3 NOR, 4..9 inputs a0 a1 d0 d1 d2 d3;
+ *                  all 64 cases of the 6-multiplexer in one 64-bit word,
+ *                  case i having a0 = bit 0 ... d3 = bit 5 of i (Sec. 4.2).
+ * Arithmetic is IEEE binary32 with no contraction into fused multiply-add
+ * and no flushing of subnormals.  Fitness is sum_c |root(c) - target(c)|
+ * accumulated in case order in binary32 (Boolean: number of wrong cases).
+ */
+#ifndef GPFDP_H
+#define GPFDP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    GP_OK = 0,
+    GP_EINVAL = -1,     /* bad argument, malformed tree, bad opcode */
+    GP_ENOMEM = -2,     /* device allocation failed or cache budget exceeded */
+    GP_ECAPACITY = -3,  /* a tree does not fit its buffer (max_nodes) */
+    GP_ECUDA = -4,      /* a CUDA runtime call failed */
+    GP_ETIMEOUT = -5,   /* a bounded device-side wait gave up */
+    GP_ESTATE = -6      /* call out of order (e.g. incremental without crossover) */
+};
+
+enum { GP_FP32_ARITH = 0, GP_BOOL_MUX6 = 1 };
+enum { GP_PACK_NONE = 0, GP_PACK_STATIC = 1, GP_PACK_MLP = 2 };
+
+typedef struct gp_pop gp_pop;
+
+/* Population configuration (all fields by value). */
+typedef struct {
+    uint32_t pop_size;          /* P individuals (one child per crossover, P children per generation) */
+    uint32_t n_cases;           /* C test cases (FP32 set); ignored (64) for GP_BOOL_MUX6 */
+    uint32_t max_nodes;         /* per-tree buffer capacity in nodes (Sec. 4.2: user-set maximum size) */
+    uint32_t funcset;           /* GP_FP32_ARITH or GP_BOOL_MUX6 */
+    uint32_t cache_threshold;   /* subtree size from which node values are cached, 2..1024 (default 1024) */
+    uint32_t tournament;        /* tournament size (default 7) */
+    uint32_t packing;           /* GP_PACK_* order of incremental work */
+    uint32_t cases_per_lane;    /* 0 = auto; else 1, 2 or 4 test cases per GPU lane */
+    uint64_t cache_budget_bytes;/* device bytes for cached value vectors (0 = 40 GiB) */
+    uint64_t seed;              /* master seed of every stochastic choice */
+} gp_config;
+
+/* Per-call statistics of the last evaluation (host copy). */
+typedef struct {
+    uint64_t equivalent_ops;    /* sum of tree sizes x cases: every opcode on every case (Sec. 1) */
+    uint64_t actual_ops;        /* opcodes actually interpreted x cases */
+    uint64_t interp_ops;        /* of which by the subtree interpreter kernel */
+    uint64_t crossover_bytes;   /* algorithmic bytes moved by the last crossover */
+    uint64_t cache_entries;     /* cached nodes (subtree >= threshold) after the call */
+    uint64_t path_levels;       /* sum over children of levels walked above the crossover point */
+    uint32_t stopped;           /* children whose walk stopped below the root (fitness inherited) */
+    uint32_t children;          /* children evaluated */
+    uint32_t launches;          /* kernels launched by the call */
+    uint32_t reserved;
+    float    ms[8];             /* per-phase device milliseconds when profiling is on, mean over
+                                   the calls since profiling was (re)enabled (last 128 kept):
+                                   structure, items, skeleton, fitness, crossover, walk, cache, pack */
+} gp_stats;
+
+/*
+ * Create a population from host data.  x and targets hold n_cases floats
+ * (ignored for GP_BOOL_MUX6); consts holds 251 floats; tree i is
+ * ops[offsets[i] .. offsets[i+1]) (offsets has pop_size+1 entries).  Each
+ * tree must be a complete prefix expression with valid opcodes and at most
+ * max_nodes nodes.  `stream` is a cudaStream_t (NULL = legacy default);
+ * the caller keeps it alive until gp_pop_destroy().  Synchronising.
+ */
+int gp_pop_create(const gp_config* cfg, const float* x, const float* targets, const float* consts,
+                  const uint8_t* ops, const uint64_t* offsets, void* stream, gp_pop** out);
+
+void gp_pop_destroy(gp_pop* pop);
+
+/*
+ * Replace the trees of an existing population with pop_size new ones from
+ * host memory (same layout and rules as gp_pop_create; pinned host memory
+ * makes the copy asynchronous).  Cached values become stale until the next
+ * gp_eval_full().  The host buffers must stay valid until the stream
+ * reaches this point (synchronise, or call gp_fitness).
+ */
+int gp_load_trees(gp_pop* pop, const uint8_t* ops, const uint64_t* offsets);
+
+/* Message for the last failed call on pop (or on creation when pop is NULL). */
+const char* gp_last_error(const gp_pop* pop);
+
+/*
+ * Full interpretation (Sec. 4.2): every tree on every test case.  Builds
+ * the tree structure pass, evaluates all subtrees below the cache
+ * threshold, then the cached nodes bottom up, writes the value vector of
+ * every node whose subtree has >= cache_threshold nodes (and of each root)
+ * to the cache, and the fitness of every tree.  Asynchronous.
+ */
+int gp_eval_full(gp_pop* pop);
+
+/*
+ * Breed the next generation (Sec. 5, Sec. 6.3): tournament selection of a
+ * mother and a father per child, crossover points uniform over all nodes,
+ * donated subtrees copied out first, then each child is materialised --
+ * by copying into a free buffer (Fig. 1) or, for the last child of a
+ * mother, in place by moving the mother's tail (Fig. 2).  All draws are a
+ * function of (seed, generation, child, k).  The parents' cached values
+ * are retained for gp_eval_incremental().  Asynchronous.
+ */
+int gp_crossover(gp_pop* pop, uint32_t generation);
+
+/*
+ * Incremental evaluation of the children of the last gp_crossover()
+ * (Sec. 6.2, Fig. 3): from the crossover point towards the root, carrying
+ * the mother's values beside the child's, stopping where both agree on all
+ * cases bit for bit.  Leaves the children's fitness and cache in place of
+ * the parents'.  `stats` may be NULL; when given the call synchronises.
+ */
+int gp_eval_incremental(gp_pop* pop, gp_stats* stats);
+
+/* Copy P fitness values to host (FP32; Boolean: error counts as float).
+ * Synchronising. */
+int gp_fitness(const gp_pop* pop, float* host_out, uint32_t n);
+
+/* Copy the P x n_cases root values (FP32) or P root words (Boolean, as
+ * uint64) to host.  `bytes` is the size of host_out.  Synchronising. */
+int gp_root_values(const gp_pop* pop, void* host_out, size_t bytes);
+
+/* Copy tree i (its size into *size) to host_out of capacity cap bytes.
+ * Synchronising. */
+int gp_get_tree(const gp_pop* pop, uint32_t i, uint8_t* host_out, uint64_t cap, uint64_t* size);
+
+/* Cached nodes of tree i: up to nmax entries of (position, subtree end,
+ * parent entry index or -1), sorted by position; *n = count.  Any output
+ * pointer may be NULL.  Synchronising. */
+int gp_cache_entries(const gp_pop* pop, uint32_t i, uint32_t* pos, uint32_t* end, int32_t* parent,
+                     uint32_t nmax, uint32_t* n);
+
+/* Value vector of cache entry j of tree i (n_cases floats, or one uint64
+ * for Boolean) to host.  Synchronising. */
+int gp_cache_value(const gp_pop* pop, uint32_t i, uint32_t j, void* host_out, size_t bytes);
+
+/* Statistics of the last gp_eval_full / gp_eval_incremental.  Synchronising. */
+int gp_get_stats(const gp_pop* pop, gp_stats* out);
+
+/* Turn per-phase CUDA-event timing on (1) or off (0); either resets the
+ * recorded phase times. */
+int gp_set_profiling(gp_pop* pop, int on);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GPFDP_H */

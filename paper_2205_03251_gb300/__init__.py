@@ -1,0 +1,272 @@
+"""GB300 (sm_103a) evaluation of populations of huge prefix-encoded GP trees.
+
+Thin ctypes binding over the C-ABI declared in ``include/gpfdp.h``; every
+step of the computation runs in the CUDA library ``libgpfdp.so`` built in
+this directory by ``build()``.  There is no CPU fallback: when the library
+is missing or no GPU is present the calls raise.
+
+The functions keep the C names (``gp_pop_create``, ``gp_eval_full``,
+``gp_crossover``, ``gp_eval_incremental``, ``gp_fitness`` ...); the
+``Population`` class wraps them for convenience.  PyTorch is used only for
+the CUDA stream handle (``torch.cuda.current_stream()``) when no stream is
+given.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from ._build import LIB_PATH, build  # noqa: F401
+
+GP_OK, GP_EINVAL, GP_ENOMEM, GP_ECAPACITY, GP_ECUDA, GP_ETIMEOUT, GP_ESTATE = 0, -1, -2, -3, -4, -5, -6
+GP_FP32_ARITH, GP_BOOL_MUX6 = 0, 1
+GP_PACK_NONE, GP_PACK_STATIC, GP_PACK_MLP = 0, 1, 2
+ERRNAMES = {GP_EINVAL: "GP_EINVAL", GP_ENOMEM: "GP_ENOMEM", GP_ECAPACITY: "GP_ECAPACITY",
+            GP_ECUDA: "GP_ECUDA", GP_ETIMEOUT: "GP_ETIMEOUT", GP_ESTATE: "GP_ESTATE"}
+
+
+class GpConfig(ctypes.Structure):
+    _fields_ = [("pop_size", ctypes.c_uint32), ("n_cases", ctypes.c_uint32),
+                ("max_nodes", ctypes.c_uint32), ("funcset", ctypes.c_uint32),
+                ("cache_threshold", ctypes.c_uint32), ("tournament", ctypes.c_uint32),
+                ("packing", ctypes.c_uint32), ("cases_per_lane", ctypes.c_uint32),
+                ("cache_budget_bytes", ctypes.c_uint64), ("seed", ctypes.c_uint64)]
+
+
+class GpStats(ctypes.Structure):
+    _fields_ = [("equivalent_ops", ctypes.c_uint64), ("actual_ops", ctypes.c_uint64),
+                ("interp_ops", ctypes.c_uint64), ("crossover_bytes", ctypes.c_uint64),
+                ("cache_entries", ctypes.c_uint64), ("path_levels", ctypes.c_uint64),
+                ("stopped", ctypes.c_uint32), ("children", ctypes.c_uint32),
+                ("launches", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("ms", ctypes.c_float * 8)]
+
+    def as_dict(self) -> dict:
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k != "ms"}
+        d["ms"] = list(self.ms)
+        return d
+
+
+PHASES = ("structure", "items", "skeleton", "fitness", "crossover", "walk", "cache", "pack")
+
+_lib = None
+
+
+class GpError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERRNAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+def load() -> ctypes.CDLL:
+    """Load libgpfdp.so (built by build()); raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"CUDA library {LIB_PATH} is not built; call paper_2205_03251_gb300.build() "
+                           "(needs nvcc for sm_103a)")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, u32, u64, i32 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int
+    sig = {
+        "gp_pop_create": (i32, [ctypes.POINTER(GpConfig), vp, vp, vp, vp, vp, vp, ctypes.POINTER(vp)]),
+        "gp_pop_destroy": (None, [vp]),
+        "gp_load_trees": (i32, [vp, vp, vp]),
+        "gp_last_error": (ctypes.c_char_p, [vp]),
+        "gp_eval_full": (i32, [vp]),
+        "gp_crossover": (i32, [vp, u32]),
+        "gp_eval_incremental": (i32, [vp, ctypes.POINTER(GpStats)]),
+        "gp_fitness": (i32, [vp, vp, u32]),
+        "gp_root_values": (i32, [vp, vp, ctypes.c_size_t]),
+        "gp_get_tree": (i32, [vp, u32, vp, u64, ctypes.POINTER(u64)]),
+        "gp_cache_entries": (i32, [vp, u32, vp, vp, vp, u32, ctypes.POINTER(u32)]),
+        "gp_cache_value": (i32, [vp, u32, u32, vp, ctypes.c_size_t]),
+        "gp_get_stats": (i32, [vp, ctypes.POINTER(GpStats)]),
+        "gp_set_profiling": (i32, [vp, i32]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(rc: int, handle=None):
+    if rc != GP_OK:
+        msg = load().gp_last_error(handle)
+        raise GpError(rc, msg.decode() if msg else "")
+
+
+def _ptr(a: np.ndarray):
+    assert a.flags["C_CONTIGUOUS"]
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def _default_stream() -> int:
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("no CUDA device: the GP evaluator runs only on the GPU")
+    return torch.cuda.current_stream().cuda_stream
+
+
+# ------------------------------------------------------------------ C names
+
+def gp_pop_create(cfg: GpConfig, x, targets, consts, ops, offsets, stream=None):
+    """Create a population; returns the opaque handle (int)."""
+    lib = load()
+    x = np.ascontiguousarray(x, np.float32)
+    targets = np.ascontiguousarray(targets, np.float32)
+    consts = np.ascontiguousarray(consts, np.float32)
+    ops = np.ascontiguousarray(ops, np.uint8)
+    offsets = np.ascontiguousarray(offsets, np.uint64)
+    if stream is None:
+        stream = _default_stream()
+    elif hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    h = ctypes.c_void_p()
+    _check(lib.gp_pop_create(ctypes.byref(cfg), _ptr(x), _ptr(targets), _ptr(consts), _ptr(ops),
+                             _ptr(offsets), ctypes.c_void_p(stream), ctypes.byref(h)))
+    return h.value
+
+
+def gp_pop_destroy(h):
+    load().gp_pop_destroy(h)
+
+
+def gp_load_trees(h, ops, offsets):
+    """Upload new trees (host arrays; pin them for an asynchronous copy)."""
+    ops = np.ascontiguousarray(ops, np.uint8)
+    offsets = np.ascontiguousarray(offsets, np.uint64)
+    _check(load().gp_load_trees(h, _ptr(ops), _ptr(offsets)), h)
+
+
+def gp_eval_full(h):
+    _check(load().gp_eval_full(h), h)
+
+
+def gp_crossover(h, generation: int):
+    _check(load().gp_crossover(h, generation), h)
+
+
+def gp_eval_incremental(h, want_stats: bool = True):
+    st = GpStats()
+    _check(load().gp_eval_incremental(h, ctypes.byref(st) if want_stats else None), h)
+    return st if want_stats else None
+
+
+def gp_fitness(h, n: int) -> np.ndarray:
+    out = np.empty(n, np.float32)
+    _check(load().gp_fitness(h, _ptr(out), n), h)
+    return out
+
+
+def gp_root_values(h, P: int, C: int, boolean: bool = False) -> np.ndarray:
+    out = np.empty(P, np.uint64) if boolean else np.empty((P, C), np.float32)
+    _check(load().gp_root_values(h, _ptr(out), out.nbytes), h)
+    return out
+
+
+def gp_get_tree(h, i: int) -> np.ndarray:
+    n = ctypes.c_uint64()
+    _check(load().gp_get_tree(h, i, None, 0, ctypes.byref(n)), h)
+    out = np.empty(max(1, n.value), np.uint8)
+    _check(load().gp_get_tree(h, i, _ptr(out), out.nbytes, ctypes.byref(n)), h)
+    return out[:n.value]
+
+
+def gp_cache_entries(h, i: int):
+    n = ctypes.c_uint32()
+    _check(load().gp_cache_entries(h, i, None, None, None, 0, ctypes.byref(n)), h)
+    m = n.value
+    pos = np.empty(max(1, m), np.uint32)
+    end = np.empty(max(1, m), np.uint32)
+    par = np.empty(max(1, m), np.int32)
+    _check(load().gp_cache_entries(h, i, _ptr(pos), _ptr(end), _ptr(par), m, ctypes.byref(n)), h)
+    return pos[:m], end[:m], par[:m]
+
+
+def gp_cache_value(h, i: int, j: int, C: int, boolean: bool = False) -> np.ndarray:
+    out = np.empty(1, np.uint64) if boolean else np.empty(C, np.float32)
+    _check(load().gp_cache_value(h, i, j, _ptr(out), out.nbytes), h)
+    return out
+
+
+def gp_get_stats(h) -> GpStats:
+    st = GpStats()
+    _check(load().gp_get_stats(h, ctypes.byref(st)), h)
+    return st
+
+
+def gp_set_profiling(h, on: bool):
+    _check(load().gp_set_profiling(h, 1 if on else 0), h)
+
+
+# ------------------------------------------------------------------ convenience
+
+class Population:
+    """A population resident on the GPU.  ``ops``/``off`` as produced by the
+    ``synth`` generators: tree i is ops[off[i]:off[i+1]]."""
+
+    def __init__(self, x, t, consts, ops, off, *, max_nodes: int, cache_threshold: int = 1024,
+                 boolean: bool = False, tournament: int = 7, packing: int = GP_PACK_STATIC,
+                 cases_per_lane: int = 0, cache_budget_bytes: int = 0, seed: int = 0, stream=None):
+        off = np.asarray(off, np.uint64)
+        self.P = len(off) - 1
+        self.boolean = boolean
+        self.C = 64 if boolean else len(x)
+        cfg = GpConfig(pop_size=self.P, n_cases=self.C, max_nodes=max_nodes,
+                       funcset=GP_BOOL_MUX6 if boolean else GP_FP32_ARITH,
+                       cache_threshold=cache_threshold, tournament=tournament, packing=packing,
+                       cases_per_lane=cases_per_lane, cache_budget_bytes=cache_budget_bytes,
+                       seed=seed & (2**64 - 1))
+        if boolean:
+            x = np.zeros(1, np.float32)
+            t = np.zeros(1, np.float32)
+        self.h = gp_pop_create(cfg, x, t, consts, ops, off, stream)
+
+    def close(self):
+        if getattr(self, "h", None):
+            gp_pop_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def load_trees(self, ops, off):
+        gp_load_trees(self.h, ops, off)
+
+    def eval_full(self):
+        gp_eval_full(self.h)
+
+    def crossover(self, generation: int):
+        gp_crossover(self.h, generation)
+
+    def eval_incremental(self, want_stats: bool = True):
+        return gp_eval_incremental(self.h, want_stats)
+
+    def fitness(self) -> np.ndarray:
+        return gp_fitness(self.h, self.P)
+
+    def root_values(self) -> np.ndarray:
+        return gp_root_values(self.h, self.P, self.C, self.boolean)
+
+    def tree(self, i: int) -> np.ndarray:
+        return gp_get_tree(self.h, i)
+
+    def cache_entries(self, i: int):
+        return gp_cache_entries(self.h, i)
+
+    def cache_value(self, i: int, j: int) -> np.ndarray:
+        return gp_cache_value(self.h, i, j, self.C, self.boolean)
+
+    def stats(self) -> dict:
+        return gp_get_stats(self.h).as_dict()
+
+    def set_profiling(self, on: bool):
+        gp_set_profiling(self.h, on)

@@ -1,0 +1,79 @@
+// Shared device definitions for the gpfdp library (sm_103a).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#define GP_B 1024            // structure block: positions per warp pass (32 per lane)
+#define GP_NCONST 251        // ephemeral constant table
+#define GP_WARPS 8           // warps per CTA in the persistent kernels
+#define FULL 0xFFFFFFFFu
+
+// status word bits (device side)
+enum : uint32_t {
+    ST_STACK = 1u << 0,      // interpreter stack deeper than the configured bound
+    ST_ENTRIES = 1u << 1,    // cache-entry capacity exceeded
+    ST_STRUCT = 1u << 2,     // structure pass inconsistent (malformed tree)
+    ST_CAPACITY = 1u << 3,   // child larger than its buffer
+    ST_SLOTS = 1u << 4,      // value-slot pool exhausted (cache budget)
+    ST_TIMEOUT = 1u << 5,    // a bounded wait gave up
+    ST_PATH = 1u << 6,       // incremental walk scratch exceeded
+};
+
+// queue counters
+enum { Q_ITEMS = 0, Q_SKEL = 1, Q_WALK = 2, Q_MISC = 3, Q_ALLOC = 4, Q_PATHV = 5, NQ = 16 };
+
+struct DevPop {
+    // sizes
+    uint32_t P, C, Cpad, K, ncb, T, cap, funcset;
+    uint32_t Ecap, Scap, maxdepth, W;      // entries, slots, interpreter stack bound, smem stack depth
+    uint32_t ovf_warps;                    // warps with an overflow stack region
+    // population
+    uint8_t* arena;      // nbuf * cap bytes
+    uint32_t* buf;       // [P] buffer holding individual i
+    uint32_t* size;      // [P]
+    float* x;            // [Cpad] (padded cases are 0)
+    float* t;            // [C]
+    float* consts;       // [251]
+    float* fit;          // [P]
+    // structure / cache (current population)
+    uint32_t* blk_off;   // [P+1]
+    uint32_t* e_cnt;     // [P]
+    uint32_t* e_off;     // [P+1]
+    uint32_t* e_pos;     // [Ecap]
+    uint32_t* e_end;     // [Ecap]
+    int32_t* e_par;      // [Ecap]
+    int32_t* e_c0;       // [Ecap] large left child entry or -1
+    int32_t* e_c1;       // [Ecap] large right child entry or -1
+    uint32_t* e_slot;    // [Ecap] value slot
+    int4* stk;           // [Ecap] structure stack scratch (entry, balance, pos, -)
+    // items (small subtrees hanging off the cached skeleton)
+    uint32_t* it_start;  // [Ecap]
+    uint32_t* it_len;    // [Ecap]
+    uint32_t* order;     // [Ecap] work order
+    // values
+    float* slots;        // [Scap][Cpad]
+    float* ovf;          // interpreter stack overflow, per warp
+    uint32_t* status;    // [1]
+    uint32_t* q;         // [NQ] queue counters
+    unsigned long long* acc_ops;   // [4] actual-op counters
+};
+
+__device__ __forceinline__ uint32_t warp_bcast(uint32_t v, int src) { return __shfl_sync(FULL, v, src); }
+__device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
+
+__device__ __forceinline__ void set_status(uint32_t* st, uint32_t bit) { atomicOr(st, bit); }
+
+// individual i's buffer
+__device__ __forceinline__ const uint8_t* tree_ptr(const DevPop& d, uint32_t i) {
+    return d.arena + (size_t)d.buf[i] * d.cap;
+}
+
+// upper_bound over an exclusive prefix array off[0..n] (off[0] = 0): largest i with off[i] <= u
+__device__ __forceinline__ uint32_t find_segment(const uint32_t* off, uint32_t n, uint32_t u) {
+    uint32_t lo = 0, hi = n;          // off[lo] <= u < off[hi]
+    while (hi - lo > 1) {
+        uint32_t mid = (lo + hi) >> 1;
+        if (off[mid] <= u) lo = mid; else hi = mid;
+    }
+    return lo;
+}

@@ -1,0 +1,555 @@
+// gpfdp: C-ABI of the GB300 GP population evaluator (see include/gpfdp.h).
+#include "gpfdp.h"
+
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "structure.cuh"
+#include "interp.cuh"
+#include "eval_full.cuh"
+#include "generation.cuh"
+
+namespace {
+
+thread_local std::string g_create_error;
+
+enum Phase { PH_STRUCT = 0, PH_ITEMS, PH_SKEL, PH_FIT, PH_XO, PH_WALK, PH_CACHE, PH_PACK, NPH };
+constexpr int NREC = 128;   // event pairs kept per phase: stats average the last NREC calls
+
+}  // namespace
+
+struct gp_pop {
+    gp_config cfg;
+    cudaStream_t stream;
+    DevPop d;
+    StructBufs sb;
+    GenBufs gb;
+    int dev, nsm;
+    int grid_items, grid_warps, grid_threads;
+    size_t smem_items;
+    std::string err;
+    gp_stats stats;
+    bool profiling;
+    cudaEvent_t ev[NPH][NREC][2];
+    uint32_t ev_count[NPH];
+    bool have_children;
+    std::vector<void*> allocs;
+    uint64_t total_nodes_last;
+    uint32_t launches;
+    uint8_t* stage;          // device staging for uploads
+    uint64_t* stage_off;
+    uint64_t stage_cap;
+    std::vector<uint64_t> host_off;   // pageable copies kept alive until the next upload
+    std::vector<uint32_t> host_buf;
+};
+
+namespace {
+
+int fail(gp_pop* p, int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (p) p->err = buf; else g_create_error = buf;
+    return code;
+}
+
+#define CK(call)                                                                     \
+    do {                                                                             \
+        cudaError_t e_ = (call);                                                     \
+        if (e_ != cudaSuccess)                                                       \
+            return fail(pop, GP_ECUDA, "%s: %s", #call, cudaGetErrorString(e_));     \
+    } while (0)
+
+template <typename T>
+int dalloc(gp_pop* pop, T** ptr, size_t count) {
+    size_t bytes = count * sizeof(T);
+    if (bytes == 0) bytes = 16;
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(pop, GP_ENOMEM, "cudaMalloc of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+    }
+    pop->allocs.push_back(p);
+    *ptr = static_cast<T*>(p);
+    return GP_OK;
+}
+
+#define DA(ptr, n)                                   \
+    do {                                             \
+        int r_ = dalloc(pop, &(ptr), (size_t)(n));   \
+        if (r_) return r_;                           \
+    } while (0)
+
+void phase_begin(gp_pop* pop, int ph) {
+    if (pop->profiling) cudaEventRecord(pop->ev[ph][pop->ev_count[ph] % NREC][0], pop->stream);
+}
+void phase_end(gp_pop* pop, int ph) {
+    if (pop->profiling) cudaEventRecord(pop->ev[ph][pop->ev_count[ph]++ % NREC][1], pop->stream);
+}
+
+int check_status(gp_pop* pop) {
+    uint32_t st = 0;
+    cudaError_t e = cudaMemcpyAsync(&st, pop->d.status, sizeof st, cudaMemcpyDeviceToHost, pop->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(pop->stream);
+    if (e != cudaSuccess) return fail(pop, GP_ECUDA, "device error: %s", cudaGetErrorString(e));
+    if (!st) return GP_OK;
+    cudaMemsetAsync(pop->d.status, 0, sizeof(uint32_t), pop->stream);
+    if (st & ST_ENTRIES) return fail(pop, GP_ENOMEM, "cache entry capacity (%u) exceeded", pop->d.Ecap);
+    if (st & ST_SLOTS) return fail(pop, GP_ENOMEM, "cache value budget (%u slots) exceeded", pop->d.Scap);
+    if (st & ST_CAPACITY) return fail(pop, GP_ECAPACITY, "a child exceeded max_nodes");
+    if (st & ST_TIMEOUT) return fail(pop, GP_ETIMEOUT, "a bounded device wait gave up");
+    if (st & ST_STACK) return fail(pop, GP_EINVAL, "interpreter stack bound exceeded (malformed tree?)");
+    if (st & ST_PATH) return fail(pop, GP_ENOMEM, "incremental path scratch exceeded");
+    return fail(pop, GP_EINVAL, "structure pass inconsistent (status 0x%x)", st);
+}
+
+// Validate one tree on the host: a complete prefix expression of exactly n
+// nodes with opcodes of the function set.
+bool valid_tree(const uint8_t* ops, uint64_t n, uint32_t funcset) {
+    if (n == 0) return false;
+    int64_t need = 1;
+    for (uint64_t i = 0; i < n; ++i) {
+        if (need <= 0) return false;
+        uint8_t o = ops[i];
+        if (funcset == GP_BOOL_MUX6 && o > 9) return false;
+        need += (o < 4) ? 1 : -1;
+    }
+    return need == 0;
+}
+
+__global__ void k_scatter_trees(const uint8_t* __restrict__ src, const uint64_t* __restrict__ off, DevPop d) {
+    for (uint32_t i = blockIdx.x; i < d.P; i += gridDim.x) {
+        const uint8_t* s = src + off[i];
+        uint8_t* dst = d.arena + (size_t)d.buf[i] * d.cap;
+        const uint32_t n = (uint32_t)(off[i + 1] - off[i]);
+        for (uint32_t j = threadIdx.x; j < n; j += blockDim.x) dst[j] = s[j];
+        if (threadIdx.x == 0) d.size[i] = n;
+    }
+}
+
+template <int K>
+int setup_items_kernel(gp_pop* pop) {
+    size_t smem = (256 + (size_t)GP_WARPS * pop->d.W * 32 * K) * sizeof(float);
+    CK(cudaFuncSetAttribute(k_eval_items<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int nb = 0;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_eval_items<K>, GP_WARPS * 32, smem));
+    if (nb < 1) nb = 1;
+    pop->grid_items = nb * pop->nsm;
+    pop->smem_items = smem;
+    return GP_OK;
+}
+
+template <int K>
+void launch_items(gp_pop* pop) {
+    k_eval_items<K><<<pop->grid_items, GP_WARPS * 32, pop->smem_items, pop->stream>>>(pop->d, pop->sb.e_tree);
+}
+template <int K>
+void launch_skeleton(gp_pop* pop) {
+    k_eval_skeleton<K><<<pop->grid_warps, GP_WARPS * 32, 0, pop->stream>>>(pop->d);
+}
+
+void launch_by_k(gp_pop* pop, void (*f1)(gp_pop*), void (*f2)(gp_pop*), void (*f4)(gp_pop*)) {
+    if (pop->d.K == 1) f1(pop); else if (pop->d.K == 2) f2(pop); else f4(pop);
+}
+
+// Structure pass + full evaluation of the current population.
+int run_full(gp_pop* pop) {
+    DevPop& d = pop->d;
+    const int gthreads = pop->grid_threads;
+    CK(cudaMemsetAsync(d.q, 0, sizeof(uint32_t) * NQ, pop->stream));
+    CK(cudaMemsetAsync(d.acc_ops, 0, 4 * sizeof(unsigned long long), pop->stream));
+    pop->launches = 15;
+    phase_begin(pop, PH_STRUCT);
+    k_blk_offsets<<<1, 1024, 0, pop->stream>>>(d);
+    k_unit_flags<<<pop->nsm * 16, FLAG_WARPS * 32, 0, pop->stream>>>(d, pop->sb);
+    const int scan_grid = pop->nsm * 2;
+    k_scan_tiles<<<scan_grid, SCAN_TILE, 0, pop->stream>>>(d, pop->sb);
+    k_scan_top<<<1, SCAN_TILE, 0, pop->stream>>>(d, pop->sb);
+    k_scan_apply<<<scan_grid, SCAN_TILE, 0, pop->stream>>>(d, pop->sb);
+    k_tree_entry_offsets<<<(d.P + 256) / 256, 256, 0, pop->stream>>>(d, pop->sb);
+    k_emit_entries<<<pop->grid_warps, GP_WARPS * 32, 0, pop->stream>>>(d, pop->sb);
+    k_entry_ends<<<gthreads, 256, 0, pop->stream>>>(d, pop->sb);
+    k_entry_chunkmax<<<pop->grid_warps, GP_WARPS * 32, 0, pop->stream>>>(d, pop->sb);
+    k_entry_parents<<<gthreads, 256, 0, pop->stream>>>(d, pop->sb);
+    k_entry_links<<<gthreads, 256, 0, pop->stream>>>(d, pop->sb);
+    k_build_items<<<gthreads, 256, 0, pop->stream>>>(d, pop->sb.e_tree);
+    phase_end(pop, PH_STRUCT);
+    phase_begin(pop, PH_ITEMS);
+    launch_by_k(pop, launch_items<1>, launch_items<2>, launch_items<4>);
+    phase_end(pop, PH_ITEMS);
+    phase_begin(pop, PH_SKEL);
+    launch_by_k(pop, launch_skeleton<1>, launch_skeleton<2>, launch_skeleton<4>);
+    phase_end(pop, PH_SKEL);
+    phase_begin(pop, PH_FIT);
+    k_fitness<<<pop->grid_warps, GP_WARPS * 32, 0, pop->stream>>>(d);
+    phase_end(pop, PH_FIT);
+    CK(cudaGetLastError());
+    return GP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* gp_last_error(const gp_pop* pop) {
+    return pop ? pop->err.c_str() : g_create_error.c_str();
+}
+
+int gp_pop_create(const gp_config* cfg_in, const float* x, const float* targets, const float* consts,
+                  const uint8_t* ops, const uint64_t* offsets, void* stream, gp_pop** out) {
+    gp_pop* pop = nullptr;
+    if (!cfg_in || !out || !ops || !offsets || !consts) return fail(nullptr, GP_EINVAL, "null argument");
+    *out = nullptr;
+    gp_config cfg = *cfg_in;
+    if (cfg.pop_size == 0) return fail(nullptr, GP_EINVAL, "pop_size must be > 0");
+    if (cfg.funcset != GP_FP32_ARITH && cfg.funcset != GP_BOOL_MUX6) return fail(nullptr, GP_EINVAL, "bad funcset");
+    if (cfg.funcset == GP_BOOL_MUX6) return fail(nullptr, GP_EINVAL, "Boolean function set not built in this library");
+    if (cfg.n_cases == 0 || cfg.n_cases > (1u << 20)) return fail(nullptr, GP_EINVAL, "n_cases out of range");
+    if (!x || !targets) return fail(nullptr, GP_EINVAL, "null x/targets");
+    if (cfg.cache_threshold == 0) cfg.cache_threshold = 1024;
+    uint32_t T = cfg.cache_threshold;
+    if (T < 2 || T > GP_B || (T & (T - 1))) return fail(nullptr, GP_EINVAL, "cache_threshold must be a power of two in [2, 1024]");
+    if (cfg.max_nodes == 0 || cfg.max_nodes > (1u << 30)) return fail(nullptr, GP_EINVAL, "max_nodes out of range");
+    if (cfg.tournament == 0) cfg.tournament = 7;
+    if (cfg.cache_budget_bytes == 0) cfg.cache_budget_bytes = 40ull << 30;
+    uint32_t K = cfg.cases_per_lane;
+    if (K == 0) K = (cfg.n_cases <= 32) ? 1 : 2;
+    if (K != 1 && K != 2 && K != 4) return fail(nullptr, GP_EINVAL, "cases_per_lane must be 0, 1, 2 or 4");
+    const uint32_t P = cfg.pop_size;
+    for (uint32_t i = 0; i < P; ++i) {
+        if (offsets[i + 1] < offsets[i]) return fail(nullptr, GP_EINVAL, "offsets not increasing at %u", i);
+        uint64_t n = offsets[i + 1] - offsets[i];
+        if (n > cfg.max_nodes) return fail(nullptr, GP_ECAPACITY, "tree %u has %llu nodes > max_nodes", i, (unsigned long long)n);
+        if (!valid_tree(ops + offsets[i], n, cfg.funcset)) return fail(nullptr, GP_EINVAL, "tree %u is not a complete prefix expression of valid opcodes", i);
+    }
+
+    pop = new gp_pop();
+    pop->cfg = cfg;
+    pop->stream = static_cast<cudaStream_t>(stream);
+    pop->profiling = false;
+    pop->have_children = false;
+    pop->stage = nullptr;
+    pop->stage_off = nullptr;
+    pop->stage_cap = 0;
+    pop->launches = 0;
+    memset(&pop->stats, 0, sizeof pop->stats);
+    memset(pop->ev_count, 0, sizeof pop->ev_count);
+    int rc = GP_OK;
+    auto bail = [&](int code) { gp_pop_destroy(pop); return code; };
+    cudaError_t ce = cudaGetDevice(&pop->dev);
+    if (ce != cudaSuccess) { g_create_error = cudaGetErrorString(ce); delete pop; return GP_ECUDA; }
+    cudaDeviceGetAttribute(&pop->nsm, cudaDevAttrMultiProcessorCount, pop->dev);
+    for (int i = 0; i < NPH; ++i)
+        for (int j = 0; j < NREC; ++j) { cudaEventCreate(&pop->ev[i][j][0]); cudaEventCreate(&pop->ev[i][j][1]); }
+
+    DevPop& d = pop->d;
+    memset(&d, 0, sizeof d);
+    d.P = P;
+    d.C = cfg.n_cases;
+    d.K = K;
+    d.ncb = (d.C + 32 * K - 1) / (32 * K);
+    d.Cpad = d.ncb * 32 * K;
+    d.T = T;
+    d.cap = (uint32_t)(((uint64_t)cfg.max_nodes + GP_B - 1) / GP_B * GP_B);
+    d.funcset = cfg.funcset;
+    d.W = 16;                       // interpreter stack entries kept in shared memory
+    d.maxdepth = d.W + T + 2;       // subtrees below the threshold need at most T + 1 entries
+    const uint64_t total_cap = (uint64_t)P * d.cap;
+    uint64_t ecap = (uint64_t)P + total_cap / 128;
+    uint64_t scap = cfg.cache_budget_bytes / ((uint64_t)d.Cpad * sizeof(float));
+    if (scap > 2 * ecap) scap = 2 * ecap;
+    if (scap < 2ull * P) { g_create_error = "cache budget too small for one vector per tree"; delete pop; return GP_ENOMEM; }
+    if (ecap > scap) ecap = scap;
+    if (ecap > 0x7FFFFFFFull || scap > 0xFFFFFFFFull) { g_create_error = "cache too large for 32-bit indices"; delete pop; return GP_ENOMEM; }
+    d.Ecap = (uint32_t)ecap;
+    d.Scap = (uint32_t)scap;
+    const uint32_t nbuf = 2 * P;     // parents + children (copy targets)
+    d.ovf_warps = 0;
+
+    // grids
+    pop->grid_warps = pop->nsm * 8;
+    pop->grid_threads = pop->nsm * 8;
+
+#define DA2(ptr, n) do { int r_ = dalloc(pop, &(ptr), (size_t)(n)); if (r_) return bail(r_); } while (0)
+    DA2(d.arena, (size_t)nbuf * d.cap);
+    DA2(d.buf, P);
+    DA2(d.size, P);
+    DA2(d.x, d.Cpad);
+    DA2(d.t, d.C);
+    DA2(d.consts, 256);
+    DA2(d.fit, P);
+    DA2(d.blk_off, P + 1);
+    DA2(d.e_cnt, P);
+    DA2(d.e_off, P + 1);
+    DA2(d.e_pos, d.Ecap);
+    DA2(d.e_end, d.Ecap);
+    DA2(d.e_par, d.Ecap);
+    DA2(d.e_c0, d.Ecap);
+    DA2(d.e_c1, d.Ecap);
+    DA2(d.e_slot, d.Ecap);
+    DA2(d.it_start, d.Ecap);
+    DA2(d.it_len, d.Ecap);
+    DA2(d.order, d.Ecap);
+    DA2(d.slots, (size_t)d.Scap * d.Cpad);
+    DA2(d.status, 4);
+    DA2(d.q, NQ);
+    DA2(d.acc_ops, 4);
+    StructBufs& sb = pop->sb;
+    sb.Ucap = (uint32_t)(total_cap / GP_B + P);
+    DA2(sb.u_flags, (size_t)sb.Ucap * 32);
+    DA2(sb.u_cv0, (size_t)sb.Ucap * 32);
+    DA2(sb.u_cmax, (size_t)sb.Ucap * 32);
+    DA2(sb.u_total, sb.Ucap);
+    DA2(sb.u_max, sb.Ucap);
+    DA2(sb.u_cnt, sb.Ucap);
+    DA2(sb.u_epre, sb.Ucap + 1);
+    DA2(sb.u_bpre, sb.Ucap + 1);
+    DA2(sb.tile_c, sb.Ucap / SCAN_TILE + 2);
+    DA2(sb.tile_b, sb.Ucap / SCAN_TILE + 2);
+    DA2(sb.e_bal, d.Ecap);
+    DA2(sb.e_tree, d.Ecap);
+    DA2(sb.e_cmax, d.Ecap / 32 + 2);
+
+    // interpreter launch shape and its overflow stacks
+    {
+        int r = (K == 1) ? setup_items_kernel<1>(pop) : (K == 2) ? setup_items_kernel<2>(pop) : setup_items_kernel<4>(pop);
+        if (r) return bail(r);
+        d.ovf_warps = (uint32_t)pop->grid_items * GP_WARPS;
+        DA2(d.ovf, (size_t)d.ovf_warps * (d.maxdepth - d.W) * 32 * K);
+    }
+    rc = gen_alloc(pop->gb, d, [&](void** p, size_t bytes) {
+        void* q = nullptr;
+        if (cudaMalloc(&q, bytes ? bytes : 16) != cudaSuccess) { cudaGetLastError(); return false; }
+        pop->allocs.push_back(q);
+        *p = q;
+        return true;
+    });
+    if (rc) { fail(pop, GP_ENOMEM, "allocation of generation buffers failed"); g_create_error = pop->err; return bail(GP_ENOMEM); }
+
+    // inputs
+    std::vector<float> xp(d.Cpad, 0.0f);
+    memcpy(xp.data(), x, sizeof(float) * d.C);
+    std::vector<uint32_t> bufs(P);
+    for (uint32_t i = 0; i < P; ++i) bufs[i] = i;
+    uint8_t* stage = nullptr;
+    uint64_t* stage_off = nullptr;
+    const uint64_t total = offsets[P] - offsets[0];
+    std::vector<uint64_t> off0(P + 1);
+    for (uint32_t i = 0; i <= P; ++i) off0[i] = offsets[i] - offsets[0];
+#define CK2(call) do { cudaError_t e_ = (call); if (e_ != cudaSuccess) { fail(pop, GP_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); g_create_error = pop->err; cudaFree(stage); cudaFree(stage_off); return bail(GP_ECUDA); } } while (0)
+    CK2(cudaMalloc(&stage, total ? total : 16));
+    CK2(cudaMalloc(&stage_off, sizeof(uint64_t) * (P + 1)));
+    CK2(cudaMemcpyAsync(stage, ops + offsets[0], total, cudaMemcpyHostToDevice, pop->stream));
+    CK2(cudaMemcpyAsync(stage_off, off0.data(), sizeof(uint64_t) * (P + 1), cudaMemcpyHostToDevice, pop->stream));
+    CK2(cudaMemcpyAsync(d.x, xp.data(), sizeof(float) * d.Cpad, cudaMemcpyHostToDevice, pop->stream));
+    CK2(cudaMemcpyAsync(d.t, targets, sizeof(float) * d.C, cudaMemcpyHostToDevice, pop->stream));
+    CK2(cudaMemcpyAsync(d.consts, consts, sizeof(float) * GP_NCONST, cudaMemcpyHostToDevice, pop->stream));
+    CK2(cudaMemcpyAsync(d.buf, bufs.data(), sizeof(uint32_t) * P, cudaMemcpyHostToDevice, pop->stream));
+    CK2(cudaMemsetAsync(d.status, 0, 4 * sizeof(uint32_t), pop->stream));
+    CK2(cudaMemsetAsync(d.acc_ops, 0, 4 * sizeof(unsigned long long), pop->stream));
+    CK2(cudaMemsetAsync(d.fit, 0, sizeof(float) * P, pop->stream));
+    k_scatter_trees<<<(P < 4096 ? P : 4096), 256, 0, pop->stream>>>(stage, stage_off, d);
+    CK2(cudaGetLastError());
+    CK2(cudaStreamSynchronize(pop->stream));
+    cudaFree(stage);
+    cudaFree(stage_off);
+    pop->total_nodes_last = total;
+    *out = pop;
+    return GP_OK;
+}
+
+void gp_pop_destroy(gp_pop* pop) {
+    if (!pop) return;
+    if (pop->stream) cudaStreamSynchronize(pop->stream); else cudaDeviceSynchronize();
+    for (void* p : pop->allocs) cudaFree(p);
+    if (pop->stage) cudaFree(pop->stage);
+    if (pop->stage_off) cudaFree(pop->stage_off);
+    for (int i = 0; i < NPH; ++i)
+        for (int j = 0; j < NREC; ++j) { cudaEventDestroy(pop->ev[i][j][0]); cudaEventDestroy(pop->ev[i][j][1]); }
+    delete pop;
+}
+
+int gp_load_trees(gp_pop* pop, const uint8_t* ops, const uint64_t* offsets) {
+    if (!pop || !ops || !offsets) return GP_EINVAL;
+    const uint32_t P = pop->d.P;
+    for (uint32_t i = 0; i < P; ++i) {
+        if (offsets[i + 1] <= offsets[i]) return fail(pop, GP_EINVAL, "tree %u is empty or offsets decrease", i);
+        if (offsets[i + 1] - offsets[i] > pop->cfg.max_nodes) return fail(pop, GP_ECAPACITY, "tree %u exceeds max_nodes", i);
+    }
+    const uint64_t total = offsets[P] - offsets[0];
+    if (total > pop->stage_cap) {
+        if (pop->stage) { cudaStreamSynchronize(pop->stream); cudaFree(pop->stage); cudaFree(pop->stage_off); }
+        pop->stage = nullptr; pop->stage_off = nullptr; pop->stage_cap = 0;
+        CK(cudaMalloc(&pop->stage, total));
+        CK(cudaMalloc(&pop->stage_off, sizeof(uint64_t) * (P + 1)));
+        pop->stage_cap = total;
+        pop->host_off.resize(P + 1);
+        pop->host_buf.resize(P);
+        for (uint32_t i = 0; i < P; ++i) pop->host_buf[i] = i;
+    }
+    for (uint32_t i = 0; i <= P; ++i) pop->host_off[i] = offsets[i] - offsets[0];
+    CK(cudaMemcpyAsync(pop->stage, ops + offsets[0], total, cudaMemcpyHostToDevice, pop->stream));
+    CK(cudaMemcpyAsync(pop->stage_off, pop->host_off.data(), sizeof(uint64_t) * (P + 1), cudaMemcpyHostToDevice, pop->stream));
+    CK(cudaMemcpyAsync(pop->d.buf, pop->host_buf.data(), sizeof(uint32_t) * P, cudaMemcpyHostToDevice, pop->stream));
+    k_scatter_trees<<<(P < 4096 ? P : 4096), 256, 0, pop->stream>>>(pop->stage, pop->stage_off, pop->d);
+    CK(cudaGetLastError());
+    pop->have_children = false;
+    return GP_OK;
+}
+
+int gp_set_profiling(gp_pop* pop, int on) {
+    if (!pop) return GP_EINVAL;
+    pop->profiling = on != 0;
+    memset(pop->ev_count, 0, sizeof pop->ev_count);
+    return GP_OK;
+}
+
+int gp_eval_full(gp_pop* pop) {
+    if (!pop) return GP_EINVAL;
+    int rc = run_full(pop);
+    if (rc) return rc;
+    pop->have_children = false;
+    gen_mark_evaluated(pop->gb);
+    return GP_OK;
+}
+
+int gp_crossover(gp_pop* pop, uint32_t generation) {
+    if (!pop) return GP_EINVAL;
+    return gen_crossover(pop, generation);
+}
+
+int gp_eval_incremental(gp_pop* pop, gp_stats* stats) {
+    if (!pop) return GP_EINVAL;
+    int rc = gen_incremental(pop);
+    if (rc) return rc;
+    if (stats) return gp_get_stats(pop, stats);
+    return GP_OK;
+}
+
+int gp_fitness(const gp_pop* cpop, float* host_out, uint32_t n) {
+    gp_pop* pop = const_cast<gp_pop*>(cpop);
+    if (!pop || !host_out || n > pop->d.P) return GP_EINVAL;
+    int rc = check_status(pop);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(host_out, pop->d.fit, sizeof(float) * n, cudaMemcpyDeviceToHost, pop->stream));
+    CK(cudaStreamSynchronize(pop->stream));
+    return GP_OK;
+}
+
+int gp_root_values(const gp_pop* cpop, void* host_out, size_t bytes) {
+    gp_pop* pop = const_cast<gp_pop*>(cpop);
+    if (!pop || !host_out) return GP_EINVAL;
+    const DevPop& d = pop->d;
+    if (bytes < (size_t)d.P * d.C * sizeof(float)) return fail(pop, GP_EINVAL, "host buffer too small");
+    int rc = check_status(pop);
+    if (rc) return rc;
+    std::vector<uint32_t> eoff(d.P + 1), slot(1);
+    CK(cudaMemcpy(eoff.data(), d.e_off, sizeof(uint32_t) * (d.P + 1), cudaMemcpyDeviceToHost));
+    float* out = static_cast<float*>(host_out);
+    for (uint32_t i = 0; i < d.P; ++i) {
+        CK(cudaMemcpy(slot.data(), d.e_slot + eoff[i], sizeof(uint32_t), cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(out + (size_t)i * d.C, d.slots + (size_t)slot[0] * d.Cpad, sizeof(float) * d.C, cudaMemcpyDeviceToHost));
+    }
+    return GP_OK;
+}
+
+int gp_get_tree(const gp_pop* cpop, uint32_t i, uint8_t* host_out, uint64_t cap, uint64_t* size) {
+    gp_pop* pop = const_cast<gp_pop*>(cpop);
+    if (!pop || i >= pop->d.P || !size) return GP_EINVAL;
+    int rc = check_status(pop);
+    if (rc) return rc;
+    uint32_t n = 0, b = 0;
+    CK(cudaMemcpy(&n, pop->d.size + i, sizeof n, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(&b, pop->d.buf + i, sizeof b, cudaMemcpyDeviceToHost));
+    *size = n;
+    if (!host_out) return GP_OK;
+    if (cap < n) return fail(pop, GP_EINVAL, "host buffer too small for tree %u (%u nodes)", i, n);
+    CK(cudaMemcpy(host_out, pop->d.arena + (size_t)b * pop->d.cap, n, cudaMemcpyDeviceToHost));
+    return GP_OK;
+}
+
+int gp_cache_entries(const gp_pop* cpop, uint32_t i, uint32_t* pos, uint32_t* end, int32_t* parent,
+                     uint32_t nmax, uint32_t* n) {
+    gp_pop* pop = const_cast<gp_pop*>(cpop);
+    if (!pop || i >= pop->d.P || !n) return GP_EINVAL;
+    int rc = check_status(pop);
+    if (rc) return rc;
+    uint32_t eo[2];
+    CK(cudaMemcpy(eo, pop->d.e_off + i, sizeof eo, cudaMemcpyDeviceToHost));
+    uint32_t cnt = eo[1] - eo[0];
+    *n = cnt;
+    uint32_t m = cnt < nmax ? cnt : nmax;
+    if (m == 0) return GP_OK;
+    if (pos) CK(cudaMemcpy(pos, pop->d.e_pos + eo[0], sizeof(uint32_t) * m, cudaMemcpyDeviceToHost));
+    if (end) CK(cudaMemcpy(end, pop->d.e_end + eo[0], sizeof(uint32_t) * m, cudaMemcpyDeviceToHost));
+    if (parent) {
+        CK(cudaMemcpy(parent, pop->d.e_par + eo[0], sizeof(int32_t) * m, cudaMemcpyDeviceToHost));
+        for (uint32_t j = 0; j < m; ++j) if (parent[j] >= 0) parent[j] -= (int32_t)eo[0];
+    }
+    return GP_OK;
+}
+
+int gp_cache_value(const gp_pop* cpop, uint32_t i, uint32_t j, void* host_out, size_t bytes) {
+    gp_pop* pop = const_cast<gp_pop*>(cpop);
+    if (!pop || i >= pop->d.P || !host_out) return GP_EINVAL;
+    if (bytes < sizeof(float) * pop->d.C) return fail(pop, GP_EINVAL, "host buffer too small");
+    int rc = check_status(pop);
+    if (rc) return rc;
+    uint32_t eo[2];
+    CK(cudaMemcpy(eo, pop->d.e_off + i, sizeof eo, cudaMemcpyDeviceToHost));
+    if (j >= eo[1] - eo[0]) return fail(pop, GP_EINVAL, "entry %u out of range", j);
+    uint32_t slot = 0;
+    CK(cudaMemcpy(&slot, pop->d.e_slot + eo[0] + j, sizeof slot, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(host_out, pop->d.slots + (size_t)slot * pop->d.Cpad, sizeof(float) * pop->d.C, cudaMemcpyDeviceToHost));
+    return GP_OK;
+}
+
+int gp_get_stats(const gp_pop* cpop, gp_stats* out) {
+    gp_pop* pop = const_cast<gp_pop*>(cpop);
+    if (!pop || !out) return GP_EINVAL;
+    int rc = check_status(pop);
+    if (rc) return rc;
+    gp_stats s = pop->stats;
+    for (int i = 0; i < NPH && i < 8; ++i) {
+        s.ms[i] = 0.f;
+        uint32_t n = pop->ev_count[i] < (uint32_t)NREC ? pop->ev_count[i] : (uint32_t)NREC;
+        if (!pop->profiling || n == 0) continue;
+        double tot = 0.0;
+        uint32_t got = 0;
+        for (uint32_t j = 0; j < n; ++j) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, pop->ev[i][j][0], pop->ev[i][j][1]) == cudaSuccess) { tot += ms; ++got; }
+        }
+        s.ms[i] = got ? (float)(tot / got) : 0.f;     // mean over the recorded calls
+    }
+    uint32_t ne = 0;
+    unsigned long long acc[4];
+    CK(cudaMemcpy(&ne, pop->d.e_off + pop->d.P, sizeof ne, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(acc, pop->d.acc_ops, sizeof acc, cudaMemcpyDeviceToHost));
+    s.cache_entries = ne;
+    s.actual_ops = acc[0] * pop->d.C;
+    s.equivalent_ops = acc[1] * pop->d.C;
+    s.interp_ops = acc[2] * pop->d.C;
+    s.launches = pop->launches;
+    *out = s;
+    return GP_OK;
+}
+
+}  // extern "C"
+
+int gen_crossover(gp_pop* pop, uint32_t generation) {
+    (void)generation;
+    return fail(pop, GP_ESTATE, "crossover is not available in this build");
+}
+
+int gen_incremental(gp_pop* pop) {
+    return fail(pop, GP_ESTATE, "incremental evaluation is not available in this build");
+}

@@ -1,0 +1,460 @@
+// Structure pass: the nodes that head subtrees of at least T nodes (the
+// cached "skeleton"), with subtree ends, parents and large-child links.
+//
+// A prefix tree is read as a balance walk: b[0] = 0 and b[j+1] = b[j] + 1
+// for a leaf, - 1 for a binary function.  The subtree that starts at node i
+// is the contiguous run i .. end(i)-1 (Sec. 3.1: flattened trees keep each
+// subtree contiguous), where end(i) is the first j > i with b[j] = b[i]+1.
+// Hence node i heads a subtree of at least T nodes exactly when b never
+// rises above b[i] on (i, i+T).  Positions past the end count as leaves.
+//
+// All steps are data parallel:
+//   k_unit_flags    one warp per 1024-position block: flags, per-32-chunk
+//                   balances and maxima (window maxima of width T-1 from
+//                   segmented prefix/suffix maxima over T-aligned segments)
+//   k_scan_*        prefix sums of flag counts and block balances
+//   k_emit_entries  positions of flagged nodes, in order, with balances
+//   k_entry_ends    per entry: first later position where the balance
+//                   rises, via chunk and block maxima
+//   k_entry_parents per entry: nearest earlier entry whose subtree ends no
+//                   earlier (intervals are nested or disjoint)
+//   k_entry_links   left/right large-child links
+#pragma once
+#include "common.cuh"
+
+#define NEG_INF_I (-0x3FFFFFFF)
+
+struct StructBufs {
+    uint32_t* u_flags;   // [U*32]
+    int32_t* u_cv0;      // [U*32] balance before the chunk, relative to the block start
+    int32_t* u_cmax;     // [U*32] max after-balance in the chunk, relative to the block start
+    int32_t* u_total;    // [U]
+    int32_t* u_max;      // [U]
+    uint32_t* u_cnt;     // [U]
+    uint32_t* u_epre;    // [U+1] exclusive prefix of counts (global entry index)
+    int64_t* u_bpre;     // [U+1] exclusive prefix of block totals
+    uint32_t* tile_c;    // scan tiles
+    int64_t* tile_b;
+    int32_t* e_bal;      // [Ecap] balance before the entry's node (within its tree)
+    uint32_t* e_tree;    // [Ecap]
+    uint32_t* e_cmax;    // [Ecap/32+1] max end per 32-entry chunk
+    uint32_t Ucap;
+};
+
+// 32 leaf bits of positions p0..p0+31 (bit s = 1: leaf or past the end).
+// p0 is a multiple of 32 and the buffer capacity a multiple of GP_B, so the
+// 32-byte load stays inside the buffer whenever p0 < n.
+__device__ __forceinline__ uint32_t leaf_bits(const uint8_t* ops, uint32_t n, uint32_t p0) {
+    if (p0 >= n) return FULL;
+    const uint4* q = reinterpret_cast<const uint4*>(ops + p0);
+    uint4 a = __ldg(q), b = __ldg(q + 1);
+    uint32_t w[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+    uint32_t bits = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        uint32_t m = __vcmpgeu4(w[i], 0x04040404u) & 0x01010101u;   // opcode >= 4 is a leaf
+        bits |= ((m * 0x10204080u) >> 28) << (4 * i);
+    }
+    uint32_t left = n - p0;
+    if (left < 32) bits |= FULL << left;
+    return bits;
+}
+
+// balance after slot j (0..31) of a chunk whose before-balance is v0
+__device__ __forceinline__ int after_bal(uint32_t bits, int v0, int j) {
+    uint32_t m = (j >= 31) ? FULL : ((1u << (j + 1)) - 1u);
+    return v0 + 2 * __popc(bits & m) - (j + 1);
+}
+
+__device__ __forceinline__ int warp_incl_sum(int v) {
+    int lane = lane_id();
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int t = __shfl_up_sync(FULL, v, o);
+        if (lane >= o) v += t;
+    }
+    return v;
+}
+
+__device__ __forceinline__ int seg_prefix_max(int v, int L) {
+    int lane = lane_id();
+    for (int o = 1; o < L; o <<= 1) {
+        int t = __shfl_up_sync(FULL, v, o);
+        if ((lane & (L - 1)) >= o) v = max(v, t);
+    }
+    return v;
+}
+
+__device__ __forceinline__ int seg_suffix_max(int v, int L) {
+    int lane = lane_id();
+    for (int o = 1; o < L; o <<= 1) {
+        int t = __shfl_down_sync(FULL, v, o);
+        if ((lane & (L - 1)) + o < L) v = max(v, t);
+    }
+    return v;
+}
+
+// Block [base, base+GP_B) of a tree of n nodes; lane l owns positions
+// base+32l .. base+32l+31.  pm: 2*GP_B ints of per-warp shared scratch.
+#define FLAG_WARPS 4
+__global__ void __launch_bounds__(FLAG_WARPS * 32) k_unit_flags(DevPop d, StructBufs sb) {
+    __shared__ int pm_all[FLAG_WARPS][2 * GP_B];
+    int* pm = pm_all[threadIdx.x >> 5];
+    const int lane = lane_id();
+    const uint32_t nunits = d.blk_off[d.P];
+    const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+    const int Ts = (int)d.T;
+    for (uint32_t u = gw; u < nunits; u += nw) {
+        const uint32_t tree = find_segment(d.blk_off, d.P, u);
+        const uint32_t base = (u - d.blk_off[tree]) * GP_B;
+        const uint8_t* ops = tree_ptr(d, tree);
+        const uint32_t n = d.size[tree];
+        uint32_t b0 = leaf_bits(ops, n, base + 32 * lane);
+        uint32_t b1 = leaf_bits(ops, n, base + GP_B + 32 * lane);
+        int t0 = 2 * __popc(b0) - 32, t1 = 2 * __popc(b1) - 32;
+        int i0 = warp_incl_sum(t0), i1 = warp_incl_sum(t1);
+        int tot0 = __shfl_sync(FULL, i0, 31);
+        int v0 = i0 - t0;
+        int w0 = tot0 + i1 - t1;
+        int vk[32], vk1[32];
+        int cmax = NEG_INF_I;
+        {
+            int a = v0, c = w0;
+#pragma unroll
+            for (int s = 0; s < 32; ++s) {
+                vk[s] = a; vk1[s] = c;
+                a += ((b0 >> s) & 1) ? 1 : -1;
+                c += ((b1 >> s) & 1) ? 1 : -1;
+                cmax = max(cmax, a);
+            }
+        }
+        int smt[32];
+        if (Ts <= 32) {
+            int run0 = NEG_INF_I, run1 = NEG_INF_I;
+#pragma unroll
+            for (int s = 0; s < 32; ++s) {
+                if ((s & (Ts - 1)) == 0) { run0 = NEG_INF_I; run1 = NEG_INF_I; }
+                run0 = max(run0, vk[s]); run1 = max(run1, vk1[s]);
+                pm[32 * lane + s] = run0;
+                pm[GP_B + 32 * lane + s] = run1;
+            }
+            int run = NEG_INF_I;
+#pragma unroll
+            for (int s = 31; s >= 0; --s) {
+                run = max(run, vk[s]);
+                smt[s] = run;
+                if ((s & (Ts - 1)) == 0) run = NEG_INF_I;
+            }
+        } else {
+            const int L = Ts / 32;
+            int m0 = NEG_INF_I, m1 = NEG_INF_I;
+#pragma unroll
+            for (int s = 0; s < 32; ++s) { m0 = max(m0, vk[s]); m1 = max(m1, vk1[s]); }
+            int p0 = seg_prefix_max(m0, L), p1 = seg_prefix_max(m1, L);
+            int e0 = __shfl_up_sync(FULL, p0, 1), e1 = __shfl_up_sync(FULL, p1, 1);
+            if ((lane & (L - 1)) == 0) { e0 = NEG_INF_I; e1 = NEG_INF_I; }
+            int run0 = e0, run1 = e1;
+#pragma unroll
+            for (int s = 0; s < 32; ++s) {
+                run0 = max(run0, vk[s]); run1 = max(run1, vk1[s]);
+                pm[32 * lane + s] = run0;
+                pm[GP_B + 32 * lane + s] = run1;
+            }
+            int sfx = seg_suffix_max(m0, L);
+            int ex = __shfl_down_sync(FULL, sfx, 1);
+            if ((lane & (L - 1)) == L - 1) ex = NEG_INF_I;
+            int run = ex;
+#pragma unroll
+            for (int s = 31; s >= 0; --s) { run = max(run, vk[s]); smt[s] = run; }
+        }
+        __syncwarp();
+        int smt_next = __shfl_down_sync(FULL, smt[0], 1);
+        uint32_t flags = 0;
+#pragma unroll
+        for (int s = 0; s < 32; ++s) {
+            int j = 32 * lane + s;          // node i = base + j; window (i, i+T) = offsets [j+1, j+T-1]
+            int a = j + 1;
+            int pmv = pm[a + Ts - 2];
+            int wmax = ((a & (Ts - 1)) == 0) ? pmv : max(s < 31 ? smt[s + 1] : smt_next, pmv);
+            bool big = (wmax <= vk[s]) && ((uint32_t)(base + j) < n);
+            flags |= (uint32_t)big << s;
+        }
+        if (base == 0 && lane == 0 && n > 0) flags |= 1u;   // every root is cached
+        __syncwarp();
+        sb.u_flags[(size_t)u * 32 + lane] = flags;
+        sb.u_cv0[(size_t)u * 32 + lane] = v0;
+        sb.u_cmax[(size_t)u * 32 + lane] = cmax;
+        uint32_t c = __popc(flags);
+        int bm = cmax;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            c += __shfl_down_sync(FULL, c, o);
+            bm = max(bm, __shfl_down_sync(FULL, bm, o));
+        }
+        if (lane == 0) { sb.u_cnt[u] = c; sb.u_total[u] = tot0; sb.u_max[u] = bm; }
+    }
+}
+
+// ---- three-phase exclusive scan of (u_cnt, u_total) over all units ----
+#define SCAN_TILE 1024
+
+__device__ __forceinline__ void block_scan2(uint32_t& a, int64_t& b, uint32_t* wa, int64_t* wb) {
+    // inclusive block scan of (a, b), 1024 threads
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t ta = __shfl_up_sync(FULL, a, o);
+        int64_t tb = __shfl_up_sync(FULL, b, o);
+        if (lane >= o) { a += ta; b += tb; }
+    }
+    if (lane == 31) { wa[w] = a; wb[w] = b; }
+    __syncthreads();
+    if (w == 0) {
+        uint32_t xa = wa[lane];
+        int64_t xb = wb[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t ta = __shfl_up_sync(FULL, xa, o);
+            int64_t tb = __shfl_up_sync(FULL, xb, o);
+            if (lane >= o) { xa += ta; xb += tb; }
+        }
+        wa[lane] = xa; wb[lane] = xb;
+    }
+    __syncthreads();
+    if (w > 0) { a += wa[w - 1]; b += wb[w - 1]; }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(SCAN_TILE) k_scan_tiles(DevPop d, StructBufs sb) {
+    __shared__ uint32_t wa[32];
+    __shared__ int64_t wb[32];
+    const uint32_t nunits = d.blk_off[d.P];
+    const uint32_t ntiles = (nunits + SCAN_TILE - 1) / SCAN_TILE;
+    for (uint32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        uint32_t u = tile * SCAN_TILE + threadIdx.x;
+        uint32_t a = (u < nunits) ? sb.u_cnt[u] : 0;
+        int64_t b = (u < nunits) ? sb.u_total[u] : 0;
+        block_scan2(a, b, wa, wb);
+        if (threadIdx.x == SCAN_TILE - 1) { sb.tile_c[tile] = a; sb.tile_b[tile] = b; }
+    }
+}
+
+__global__ void __launch_bounds__(SCAN_TILE) k_scan_top(DevPop d, StructBufs sb) {
+    __shared__ uint32_t wa[32];
+    __shared__ int64_t wb[32];
+    __shared__ uint32_t ca;
+    __shared__ int64_t cb;
+    const uint32_t nunits = d.blk_off[d.P];
+    const uint32_t ntiles = (nunits + SCAN_TILE - 1) / SCAN_TILE;
+    if (threadIdx.x == 0) { ca = 0; cb = 0; }
+    __syncthreads();
+    for (uint32_t t0 = 0; t0 < ntiles; t0 += SCAN_TILE) {
+        uint32_t t = t0 + threadIdx.x;
+        uint32_t a = (t < ntiles) ? sb.tile_c[t] : 0;
+        int64_t b = (t < ntiles) ? sb.tile_b[t] : 0;
+        uint32_t a0 = a;
+        int64_t b0 = b;
+        block_scan2(a, b, wa, wb);
+        if (t < ntiles) { sb.tile_c[t] = a - a0 + ca; sb.tile_b[t] = b - b0 + cb; }   // exclusive
+        __syncthreads();
+        if (threadIdx.x == SCAN_TILE - 1) { ca += a; cb += b; }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        sb.u_epre[nunits] = ca;
+        sb.u_bpre[nunits] = cb;
+        if (ca > d.Ecap) set_status(d.status, ST_ENTRIES);
+    }
+}
+
+__global__ void __launch_bounds__(SCAN_TILE) k_scan_apply(DevPop d, StructBufs sb) {
+    __shared__ uint32_t wa[32];
+    __shared__ int64_t wb[32];
+    const uint32_t nunits = d.blk_off[d.P];
+    const uint32_t ntiles = (nunits + SCAN_TILE - 1) / SCAN_TILE;
+    for (uint32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        uint32_t u = tile * SCAN_TILE + threadIdx.x;
+        uint32_t a = (u < nunits) ? sb.u_cnt[u] : 0;
+        int64_t b = (u < nunits) ? sb.u_total[u] : 0;
+        uint32_t a0 = a;
+        int64_t b0 = b;
+        block_scan2(a, b, wa, wb);
+        if (u < nunits) {
+            sb.u_epre[u] = sb.tile_c[tile] + a - a0;
+            sb.u_bpre[u] = sb.tile_b[tile] + b - b0;
+        }
+    }
+}
+
+// e_off / e_cnt per tree from the unit prefix.
+__global__ void k_tree_entry_offsets(DevPop d, StructBufs sb) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i <= d.P; i += gridDim.x * blockDim.x) {
+        uint32_t v = sb.u_epre[d.blk_off[i]];
+        d.e_off[i] = v;
+        if (i < d.P) d.e_cnt[i] = sb.u_epre[d.blk_off[i + 1]] - v;
+    }
+}
+
+// Write each flagged node as an entry, in position order.
+__global__ void __launch_bounds__(GP_WARPS * 32) k_emit_entries(DevPop d, StructBufs sb) {
+    const int lane = lane_id();
+    const uint32_t nunits = d.blk_off[d.P];
+    if (sb.u_epre[nunits] > d.Ecap) return;
+    const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t u = gw; u < nunits; u += nw) {
+        if (sb.u_cnt[u] == 0) continue;
+        const uint32_t tree = find_segment(d.blk_off, d.P, u);
+        const uint32_t base = (u - d.blk_off[tree]) * GP_B;
+        const int64_t bbase = sb.u_bpre[u] - sb.u_bpre[d.blk_off[tree]];
+        uint32_t fl = sb.u_flags[(size_t)u * 32 + lane];
+        int v0 = sb.u_cv0[(size_t)u * 32 + lane];
+        uint32_t c = __popc(fl);
+        uint32_t incl = (uint32_t)warp_incl_sum((int)c);
+        uint32_t e = sb.u_epre[u] + incl - c;
+        if (fl) {
+            uint32_t bits = leaf_bits(tree_ptr(d, tree), d.size[tree], base + 32 * lane);
+            while (fl) {
+                int s = __ffs(fl) - 1;
+                fl &= fl - 1;
+                int bal = (int)bbase + v0 + 2 * __popc(bits & ((1u << s) - 1u)) - s;
+                d.e_pos[e] = base + 32 * lane + s;
+                sb.e_bal[e] = bal;
+                sb.e_tree[e] = tree;
+                d.e_c0[e] = -1;
+                d.e_c1[e] = -1;
+                d.e_slot[e] = e;
+                ++e;
+            }
+        }
+    }
+}
+
+// end(entry) = first position q >= pos with after-balance >= bal + 1, plus one.
+__global__ void k_entry_ends(DevPop d, StructBufs sb) {
+    const uint32_t ne = sb.u_epre[d.blk_off[d.P]];
+    if (ne > d.Ecap) return;
+    for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < ne; e += gridDim.x * blockDim.x) {
+        const uint32_t tree = sb.e_tree[e];
+        const uint32_t pos = d.e_pos[e];
+        const int target = sb.e_bal[e] + 1;
+        const uint8_t* ops = tree_ptr(d, tree);
+        const uint32_t n = d.size[tree];
+        const uint32_t u0 = d.blk_off[tree], nb = d.blk_off[tree + 1] - u0;
+        const int64_t bp0 = sb.u_bpre[u0];
+        uint32_t k = pos / GP_B, c = (pos % GP_B) / 32, s = pos % 32;
+        uint32_t endpos = 0xFFFFFFFFu;
+        // 1: rest of the node's own chunk
+        {
+            int bb = (int)(sb.u_bpre[u0 + k] - bp0);
+            int v0 = bb + sb.u_cv0[(size_t)(u0 + k) * 32 + c];
+            uint32_t bits = leaf_bits(ops, n, k * GP_B + c * 32);
+            for (uint32_t j = s; j < 32; ++j)
+                if (after_bal(bits, v0, (int)j) >= target) { endpos = k * GP_B + c * 32 + j + 1; break; }
+        }
+        // 2/3: later chunks of this block, then later blocks
+        uint32_t fk = 0xFFFFFFFFu, fc = 0;
+        if (endpos == 0xFFFFFFFFu) {
+            int bb = (int)(sb.u_bpre[u0 + k] - bp0);
+            for (uint32_t c2 = c + 1; c2 < 32; ++c2)
+                if (bb + sb.u_cmax[(size_t)(u0 + k) * 32 + c2] >= target) { fk = k; fc = c2; break; }
+            if (fk == 0xFFFFFFFFu) {
+                for (uint32_t k2 = k + 1; k2 < nb; ++k2) {
+                    int bb2 = (int)(sb.u_bpre[u0 + k2] - bp0);
+                    if (bb2 + sb.u_max[u0 + k2] >= target) {
+                        for (uint32_t c2 = 0; c2 < 32; ++c2)
+                            if (bb2 + sb.u_cmax[(size_t)(u0 + k2) * 32 + c2] >= target) { fk = k2; fc = c2; break; }
+                        break;
+                    }
+                }
+            }
+            if (fk != 0xFFFFFFFFu) {
+                int bb2 = (int)(sb.u_bpre[u0 + fk] - bp0);
+                int v0 = bb2 + sb.u_cv0[(size_t)(u0 + fk) * 32 + fc];
+                uint32_t bits = leaf_bits(ops, n, fk * GP_B + fc * 32);
+                for (uint32_t j = 0; j < 32; ++j)
+                    if (after_bal(bits, v0, (int)j) >= target) { endpos = fk * GP_B + fc * 32 + j + 1; break; }
+            }
+        }
+        // a well-formed tree closes exactly at its last node
+        if (endpos == 0xFFFFFFFFu || endpos > n || (pos == 0 && endpos != n)) { set_status(d.status, ST_STRUCT); endpos = n; }
+        d.e_end[e] = endpos;
+    }
+}
+
+__global__ void k_entry_chunkmax(DevPop d, StructBufs sb) {
+    const uint32_t ne = sb.u_epre[d.blk_off[d.P]];
+    if (ne > d.Ecap) return;
+    const uint32_t nch = (ne + 31) / 32;
+    const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t ch = gw; ch < nch; ch += nw) {
+        uint32_t e = ch * 32 + lane_id();
+        uint32_t v = (e < ne) ? d.e_end[e] : 0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_down_sync(FULL, v, o));
+        if (lane_id() == 0) sb.e_cmax[ch] = v;
+    }
+}
+
+// parent(e) = nearest earlier entry of the same tree whose subtree ends at
+// or after end(e): earlier entries either contain e (ancestors, end >=
+// end(e)) or end before pos(e) < end(e).
+__global__ void k_entry_parents(DevPop d, StructBufs sb) {
+    const uint32_t ne = sb.u_epre[d.blk_off[d.P]];
+    if (ne > d.Ecap) return;
+    for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < ne; e += gridDim.x * blockDim.x) {
+        const uint32_t tree = sb.e_tree[e];
+        const uint32_t e0 = d.e_off[tree];
+        int32_t par = -1;
+        if (e > e0) {
+            const uint32_t ee = d.e_end[e];
+            int64_t p = (int64_t)e - 1;
+            // within e's 32-entry chunk
+            int64_t cstart = (int64_t)(e & ~31u);
+            for (; p >= (int64_t)e0 && p >= cstart; --p)
+                if (d.e_end[p] >= ee) { par = (int32_t)p; break; }
+            // earlier chunks, skipping those whose maximum end is too small
+            if (par < 0) {
+                for (int64_t ch = cstart / 32 - 1; ch >= (int64_t)(e0 / 32) && par < 0; --ch) {
+                    if (sb.e_cmax[ch] < ee) continue;
+                    for (int64_t q = ch * 32 + 31; q >= ch * 32 && q >= (int64_t)e0; --q)
+                        if (d.e_end[q] >= ee) { par = (int32_t)q; break; }
+                }
+            }
+            if (par < 0) set_status(d.status, ST_STRUCT);
+        }
+        d.e_par[e] = par;
+    }
+}
+
+__global__ void k_entry_links(DevPop d, StructBufs sb) {
+    const uint32_t ne = sb.u_epre[d.blk_off[d.P]];
+    if (ne > d.Ecap) return;
+    for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < ne; e += gridDim.x * blockDim.x) {
+        int32_t p = d.e_par[e];
+        if (p < 0) continue;
+        if (d.e_pos[e] == d.e_pos[p] + 1) d.e_c0[p] = (int32_t)e;
+        else d.e_c1[p] = (int32_t)e;
+    }
+}
+
+// blk_off[i] = sum_{j<i} ceil(size_j / GP_B); one CTA of 1024 threads.
+__global__ void __launch_bounds__(1024) k_blk_offsets(DevPop d) {
+    __shared__ uint32_t wa[32];
+    __shared__ int64_t wb[32];
+    __shared__ uint32_t carry;
+    if (threadIdx.x == 0) { carry = 0; d.blk_off[0] = 0; }
+    __syncthreads();
+    for (uint32_t base = 0; base < d.P; base += blockDim.x) {
+        uint32_t i = base + threadIdx.x;
+        uint32_t a = (i < d.P) ? (d.size[i] + GP_B - 1) / GP_B : 0;
+        int64_t b = 0;
+        block_scan2(a, b, wa, wb);
+        if (i < d.P) d.blk_off[i + 1] = a + carry;
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) carry += a;
+        __syncthreads();
+    }
+}
