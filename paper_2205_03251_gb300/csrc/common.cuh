@@ -54,6 +54,7 @@ struct DevPop {
     float* slots;        // [Scap][Cpad]
     float* ovf;          // interpreter stack overflow, per warp
     uint32_t* status;    // [1]
+    uint32_t* e_total;   // [1] cache entries found by the structure pass
     uint32_t* q;         // [NQ] queue counters
     unsigned long long* acc_ops;   // [4] actual-op counters
 };

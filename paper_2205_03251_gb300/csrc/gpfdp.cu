@@ -6,6 +6,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "common.cuh"
@@ -46,6 +47,9 @@ struct gp_pop {
     uint64_t stage_cap;
     std::vector<uint64_t> host_off;   // pageable copies kept alive until the next upload
     std::vector<uint32_t> host_buf;
+    uint64_t slot_limit;              // value vectors the cache budget allows
+    std::vector<void*> cache_allocs;  // entry arrays and slots (regrown on demand)
+    uint32_t* e_total_h;              // pinned host copy of the entry count
 };
 
 namespace {
@@ -160,6 +164,35 @@ void launch_by_k(gp_pop* pop, void (*f1)(gp_pop*), void (*f2)(gp_pop*), void (*f
     if (pop->d.K == 1) f1(pop); else if (pop->d.K == 2) f2(pop); else f4(pop);
 }
 
+// (Re)allocate the cache-entry arrays for ecap entries and the value
+// slots for as many vectors (full evaluation gives entry e slot e).
+int grow_cache(gp_pop* pop, uint32_t ecap) {
+    DevPop& d = pop->d;
+    StructBufs& sb = pop->sb;
+    if ((uint64_t)ecap > pop->slot_limit)
+        return fail(pop, GP_ENOMEM, "cache needs %u value vectors, budget allows %llu", ecap,
+                    (unsigned long long)pop->slot_limit);
+    if (pop->stream) cudaStreamSynchronize(pop->stream); else cudaDeviceSynchronize();
+    for (void* p : pop->cache_allocs) cudaFree(p);
+    pop->cache_allocs.clear();
+    auto al = [&](auto** ptr, size_t count) -> bool {
+        void* p = nullptr;
+        size_t bytes = count * sizeof(**ptr);
+        if (cudaMalloc(&p, bytes ? bytes : 16) != cudaSuccess) { cudaGetLastError(); return false; }
+        pop->cache_allocs.push_back(p);
+        *ptr = static_cast<std::remove_reference_t<decltype(*ptr)>>(p);
+        return true;
+    };
+    bool ok = al(&d.e_pos, ecap) && al(&d.e_end, ecap) && al(&d.e_par, ecap) && al(&d.e_c0, ecap) &&
+              al(&d.e_c1, ecap) && al(&d.e_slot, ecap) && al(&d.it_start, ecap) && al(&d.it_len, ecap) &&
+              al(&d.order, ecap) && al(&sb.e_bal, ecap) && al(&sb.e_tree, ecap) && al(&sb.e_cmax, ecap / 32 + 2) &&
+              al(&d.slots, (size_t)ecap * d.Cpad);
+    if (!ok) return fail(pop, GP_ENOMEM, "allocation of a cache of %u entries failed", ecap);
+    d.Ecap = ecap;
+    d.Scap = ecap;
+    return GP_OK;
+}
+
 // Structure pass + full evaluation of the current population.
 int run_full(gp_pop* pop) {
     DevPop& d = pop->d;
@@ -174,6 +207,15 @@ int run_full(gp_pop* pop) {
     k_scan_tiles<<<scan_grid, SCAN_TILE, 0, pop->stream>>>(d, pop->sb);
     k_scan_top<<<1, SCAN_TILE, 0, pop->stream>>>(d, pop->sb);
     k_scan_apply<<<scan_grid, SCAN_TILE, 0, pop->stream>>>(d, pop->sb);
+    // entry count known: grow the cache arrays if this population needs more
+    CK(cudaMemcpyAsync(pop->e_total_h, d.e_total, sizeof(uint32_t), cudaMemcpyDeviceToHost, pop->stream));
+    CK(cudaStreamSynchronize(pop->stream));
+    if (*pop->e_total_h > d.Ecap) {
+        uint64_t want = (uint64_t)*pop->e_total_h + *pop->e_total_h / 4 + 64;
+        if (want > pop->slot_limit) want = pop->slot_limit;
+        int r = grow_cache(pop, (uint32_t)want);
+        if (r) return r;
+    }
     k_tree_entry_offsets<<<(d.P + 256) / 256, 256, 0, pop->stream>>>(d, pop->sb);
     k_emit_entries<<<pop->grid_warps, GP_WARPS * 32, 0, pop->stream>>>(d, pop->sb);
     k_entry_ends<<<gthreads, 256, 0, pop->stream>>>(d, pop->sb);
@@ -240,6 +282,7 @@ int gp_pop_create(const gp_config* cfg_in, const float* x, const float* targets,
     pop->stage_off = nullptr;
     pop->stage_cap = 0;
     pop->launches = 0;
+    pop->e_total_h = nullptr;
     memset(&pop->stats, 0, sizeof pop->stats);
     memset(pop->ev_count, 0, sizeof pop->ev_count);
     int rc = GP_OK;
@@ -263,14 +306,14 @@ int gp_pop_create(const gp_config* cfg_in, const float* x, const float* targets,
     d.W = 16;                       // interpreter stack entries kept in shared memory
     d.maxdepth = d.W + T + 2;       // subtrees below the threshold need at most T + 1 entries
     const uint64_t total_cap = (uint64_t)P * d.cap;
-    uint64_t ecap = (uint64_t)P + total_cap / 128;
-    uint64_t scap = cfg.cache_budget_bytes / ((uint64_t)d.Cpad * sizeof(float));
-    if (scap > 2 * ecap) scap = 2 * ecap;
-    if (scap < 2ull * P) { g_create_error = "cache budget too small for one vector per tree"; delete pop; return GP_ENOMEM; }
-    if (ecap > scap) ecap = scap;
-    if (ecap > 0x7FFFFFFFull || scap > 0xFFFFFFFFull) { g_create_error = "cache too large for 32-bit indices"; delete pop; return GP_ENOMEM; }
-    d.Ecap = (uint32_t)ecap;
-    d.Scap = (uint32_t)scap;
+    // initial cache-entry capacity; grown on demand by gp_eval_full
+    uint64_t ecap = (uint64_t)P + total_cap * 4 / T;
+    if (ecap > (uint64_t)P + total_cap) ecap = (uint64_t)P + total_cap;
+    if (ecap > (1ull << 26)) ecap = 1ull << 26;
+    pop->slot_limit = cfg.cache_budget_bytes / ((uint64_t)d.Cpad * sizeof(float));
+    if (pop->slot_limit > 0xFFFFFFF0ull) pop->slot_limit = 0xFFFFFFF0ull;
+    if (pop->slot_limit < 2ull * P) { g_create_error = "cache budget too small for one vector per tree"; delete pop; return GP_ENOMEM; }
+    if (ecap > pop->slot_limit) ecap = pop->slot_limit;
     const uint32_t nbuf = 2 * P;     // parents + children (copy targets)
     d.ovf_warps = 0;
 
@@ -289,17 +332,13 @@ int gp_pop_create(const gp_config* cfg_in, const float* x, const float* targets,
     DA2(d.blk_off, P + 1);
     DA2(d.e_cnt, P);
     DA2(d.e_off, P + 1);
-    DA2(d.e_pos, d.Ecap);
-    DA2(d.e_end, d.Ecap);
-    DA2(d.e_par, d.Ecap);
-    DA2(d.e_c0, d.Ecap);
-    DA2(d.e_c1, d.Ecap);
-    DA2(d.e_slot, d.Ecap);
-    DA2(d.it_start, d.Ecap);
-    DA2(d.it_len, d.Ecap);
-    DA2(d.order, d.Ecap);
-    DA2(d.slots, (size_t)d.Scap * d.Cpad);
+    {
+        int r = grow_cache(pop, (uint32_t)ecap);
+        if (r) { g_create_error = pop->err; return bail(r); }
+    }
     DA2(d.status, 4);
+    DA2(d.e_total, 4);
+    if (cudaMallocHost(&pop->e_total_h, sizeof(uint32_t)) != cudaSuccess) { g_create_error = "cudaMallocHost failed"; return bail(GP_ENOMEM); }
     DA2(d.q, NQ);
     DA2(d.acc_ops, 4);
     StructBufs& sb = pop->sb;
@@ -314,9 +353,6 @@ int gp_pop_create(const gp_config* cfg_in, const float* x, const float* targets,
     DA2(sb.u_bpre, sb.Ucap + 1);
     DA2(sb.tile_c, sb.Ucap / SCAN_TILE + 2);
     DA2(sb.tile_b, sb.Ucap / SCAN_TILE + 2);
-    DA2(sb.e_bal, d.Ecap);
-    DA2(sb.e_tree, d.Ecap);
-    DA2(sb.e_cmax, d.Ecap / 32 + 2);
 
     // interpreter launch shape and its overflow stacks
     {
@@ -370,6 +406,8 @@ void gp_pop_destroy(gp_pop* pop) {
     if (!pop) return;
     if (pop->stream) cudaStreamSynchronize(pop->stream); else cudaDeviceSynchronize();
     for (void* p : pop->allocs) cudaFree(p);
+    for (void* p : pop->cache_allocs) cudaFree(p);
+    if (pop->e_total_h) cudaFreeHost(pop->e_total_h);
     if (pop->stage) cudaFree(pop->stage);
     if (pop->stage_off) cudaFree(pop->stage_off);
     for (int i = 0; i < NPH; ++i)

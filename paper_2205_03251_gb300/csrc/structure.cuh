@@ -264,7 +264,7 @@ __global__ void __launch_bounds__(SCAN_TILE) k_scan_top(DevPop d, StructBufs sb)
     if (threadIdx.x == 0) {
         sb.u_epre[nunits] = ca;
         sb.u_bpre[nunits] = cb;
-        if (ca > d.Ecap) set_status(d.status, ST_ENTRIES);
+        *d.e_total = ca;
     }
 }
 
