@@ -47,8 +47,8 @@ struct DevPop {
     uint32_t* e_slot;    // [Ecap] value slot
     int4* stk;           // [Ecap] structure stack scratch (entry, balance, pos, -)
     // items (small subtrees hanging off the cached skeleton)
-    uint32_t* it_start;  // [Ecap]
-    uint32_t* it_len;    // [Ecap]
+    uint4* it_desc;      // [Ecap] (start, length, slot, buffer) of the entry's small-subtree item
+    uint4* sk_desc;      // [Ecap] (slot, operand slot, op | child flags, right child entry) for the skeleton pass
     uint32_t* order;     // [Ecap] work order
     // values
     float* slots;        // [Scap][Cpad]

@@ -129,19 +129,40 @@ bool valid_tree(const uint8_t* ops, uint64_t n, uint32_t funcset) {
     return need == 0;
 }
 
+// Copy tree i from the compact upload (any byte offset) into its aligned
+// buffer, 16 destination bytes per thread; the source is read as aligned
+// 16-byte chunks and shifted.  The upload buffer has 32 bytes of slack.
 __global__ void k_scatter_trees(const uint8_t* __restrict__ src, const uint64_t* __restrict__ off, DevPop d) {
     for (uint32_t i = blockIdx.x; i < d.P; i += gridDim.x) {
         const uint8_t* s = src + off[i];
         uint8_t* dst = d.arena + (size_t)d.buf[i] * d.cap;
         const uint32_t n = (uint32_t)(off[i + 1] - off[i]);
-        for (uint32_t j = threadIdx.x; j < n; j += blockDim.x) dst[j] = s[j];
         if (threadIdx.x == 0) d.size[i] = n;
+        const uintptr_t sa = reinterpret_cast<uintptr_t>(s);
+        const uint32_t m = (uint32_t)(sa & 15u);
+        const uint4* A = reinterpret_cast<const uint4*>(sa - m);
+        const uint32_t nq = (n + 15) / 16;
+        for (uint32_t q = threadIdx.x; q < nq; q += blockDim.x) {
+            const uint4 lo = A[q], hi = (m ? A[q + 1] : lo);
+            const uint32_t w[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
+            const uint32_t mw = m >> 2, sh = (m & 3u) * 8u;
+            uint32_t r[4];
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                uint32_t a = 0, b = 0;
+#pragma unroll
+                for (int c = 0; c < 4; ++c)
+                    if ((uint32_t)c == mw) { a = w[t + c]; b = w[t + c + 1]; }
+                r[t] = __funnelshift_r(a, b, sh);
+            }
+            reinterpret_cast<uint4*>(dst)[q] = make_uint4(r[0], r[1], r[2], r[3]);
+        }
     }
 }
 
 template <int K>
 int setup_items_kernel(gp_pop* pop) {
-    size_t smem = (256 + (size_t)GP_WARPS * pop->d.W * 32 * K) * sizeof(float);
+    size_t smem = SmemLayout<K>::total((int)pop->d.W, GP_WARPS);
     CK(cudaFuncSetAttribute(k_eval_items<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int nb = 0;
     CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_eval_items<K>, GP_WARPS * 32, smem));
@@ -153,7 +174,7 @@ int setup_items_kernel(gp_pop* pop) {
 
 template <int K>
 void launch_items(gp_pop* pop) {
-    k_eval_items<K><<<pop->grid_items, GP_WARPS * 32, pop->smem_items, pop->stream>>>(pop->d, pop->sb.e_tree);
+    k_eval_items<K><<<pop->grid_items, GP_WARPS * 32, pop->smem_items, pop->stream>>>(pop->d);
 }
 template <int K>
 void launch_skeleton(gp_pop* pop) {
@@ -184,7 +205,7 @@ int grow_cache(gp_pop* pop, uint32_t ecap) {
         return true;
     };
     bool ok = al(&d.e_pos, ecap) && al(&d.e_end, ecap) && al(&d.e_par, ecap) && al(&d.e_c0, ecap) &&
-              al(&d.e_c1, ecap) && al(&d.e_slot, ecap) && al(&d.it_start, ecap) && al(&d.it_len, ecap) &&
+              al(&d.e_c1, ecap) && al(&d.e_slot, ecap) && al(&d.it_desc, ecap) && al(&d.sk_desc, ecap) &&
               al(&d.order, ecap) && al(&sb.e_bal, ecap) && al(&sb.e_tree, ecap) && al(&sb.e_cmax, ecap / 32 + 2) &&
               al(&d.slots, (size_t)ecap * d.Cpad);
     if (!ok) return fail(pop, GP_ENOMEM, "allocation of a cache of %u entries failed", ecap);
@@ -381,7 +402,7 @@ int gp_pop_create(const gp_config* cfg_in, const float* x, const float* targets,
     std::vector<uint64_t> off0(P + 1);
     for (uint32_t i = 0; i <= P; ++i) off0[i] = offsets[i] - offsets[0];
 #define CK2(call) do { cudaError_t e_ = (call); if (e_ != cudaSuccess) { fail(pop, GP_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); g_create_error = pop->err; cudaFree(stage); cudaFree(stage_off); return bail(GP_ECUDA); } } while (0)
-    CK2(cudaMalloc(&stage, total ? total : 16));
+    CK2(cudaMalloc(&stage, total + 32));
     CK2(cudaMalloc(&stage_off, sizeof(uint64_t) * (P + 1)));
     CK2(cudaMemcpyAsync(stage, ops + offsets[0], total, cudaMemcpyHostToDevice, pop->stream));
     CK2(cudaMemcpyAsync(stage_off, off0.data(), sizeof(uint64_t) * (P + 1), cudaMemcpyHostToDevice, pop->stream));
@@ -426,7 +447,7 @@ int gp_load_trees(gp_pop* pop, const uint8_t* ops, const uint64_t* offsets) {
     if (total > pop->stage_cap) {
         if (pop->stage) { cudaStreamSynchronize(pop->stream); cudaFree(pop->stage); cudaFree(pop->stage_off); }
         pop->stage = nullptr; pop->stage_off = nullptr; pop->stage_cap = 0;
-        CK(cudaMalloc(&pop->stage, total));
+        CK(cudaMalloc(&pop->stage, total + 32));
         CK(cudaMalloc(&pop->stage_off, sizeof(uint64_t) * (P + 1)));
         pop->stage_cap = total;
         pop->host_off.resize(P + 1);

@@ -6,16 +6,21 @@
 // right to left, which visits every node after both of its children (the
 // reverse of prefix order is a postfix order of the mirrored tree, cf. the
 // RPN scan of Sec. 3.1), so a stack machine needs no recursion: a leaf
-// pushes, a function pops its right operand and combines it with the
-// running value (the left operand).  Each lane holds K test cases; the top
-// of the stack is in registers, the next W entries in shared memory and
-// deeper entries in a per-warp global overflow area.
+// pushes the running value and loads its own, a function pops its right
+// operand and combines it with the running value (its left operand).
+// Each lane holds K test cases; the running value is in registers, the
+// next W stack entries in shared memory, deeper ones in a per-warp global
+// overflow area.  The opcodes of the run are first staged into shared
+// memory with cp.async (one 16-byte copy per lane per 512 bytes), so the
+// interpreter reads one 32-bit word per four nodes without global latency.
 //
 // Arithmetic is binary32 with explicit round-to-nearest intrinsics (never
 // contracted into FMA); protected division returns 1 when the divisor
 // equals zero.
 #pragma once
 #include "common.cuh"
+
+#define STAGE_BYTES 2112     // >= 2*1024 - 1 nodes + 15 bytes of alignment, multiple of 16
 
 template <int K> struct VecT;
 template <> struct VecT<1> { typedef float type; };
@@ -35,46 +40,66 @@ __device__ __forceinline__ void vload(const float* p, float (&v)[K]) {
     else { float4 t = *reinterpret_cast<const float4*>(p); v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w; }
 }
 
+__device__ __forceinline__ float pdiv(float a, float b) {
+    return (b == 0.0f) ? 1.0f : __fdiv_rn(a, b);
+}
+
 __device__ __forceinline__ float apply_op(uint32_t op, float a, float b) {
     switch (op) {
     case 0: return __fadd_rn(a, b);
     case 1: return __fsub_rn(a, b);
     case 2: return __fmul_rn(a, b);
-    default: return (b == 0.0f) ? 1.0f : __fdiv_rn(a, b);
+    default: return pdiv(a, b);
     }
 }
 
 template <int K>
-struct WarpStack {
-    float* s;     // shared: W entries x 32 lanes x K
-    float* g;     // global overflow: (maxd - W) entries x 32 lanes x K
-    int W;
-    int maxd;
+__device__ __forceinline__ void apply_vec(uint32_t op, float (&a)[K], const float (&b)[K]) {
+    if (op < 2) {
+        if (op == 0) {
+#pragma unroll
+            for (int k = 0; k < K; ++k) a[k] = __fadd_rn(a[k], b[k]);
+        } else {
+#pragma unroll
+            for (int k = 0; k < K; ++k) a[k] = __fsub_rn(a[k], b[k]);
+        }
+    } else if (op == 2) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) a[k] = __fmul_rn(a[k], b[k]);
+    } else {
+#pragma unroll
+        for (int k = 0; k < K; ++k) a[k] = pdiv(a[k], b[k]);
+    }
+}
+
+// Per-warp interpreter context.
+template <int K>
+struct Ictx {
+    float* s;            // shared stack: W entries x 32 lanes x K (this lane's K at s + lane*K)
+    float* g;            // global overflow: (maxd - W) entries x 32 lanes x K
+    const float* kc;     // shared constant table indexed by opcode (kc[5..255])
+    int W, maxd;
+    float xv[K];         // this lane's test-case inputs
 };
 
 template <int K>
-struct InterpState {
+struct Istate {
     float acc[K];
-    int sp;
+    int sp;              // stack depth (entries)
     bool ok;
 };
 
+// One node, any stack depth (bounds checked).
 template <int K>
-__device__ __forceinline__ void interp_step(uint32_t op, InterpState<K>& st, const WarpStack<K>& ws,
-                                            const float (&xv)[K], const float* __restrict__ kc, int lane) {
+__device__ __forceinline__ void step_checked(uint32_t op, Istate<K>& st, const Ictx<K>& c, int lane) {
     if (op >= 4) {
-        if (st.sp < ws.W) vstore<K>(ws.s + ((size_t)st.sp * 32 + lane) * K, st.acc);
-        else if (st.sp < ws.maxd) vstore<K>(ws.g + ((size_t)(st.sp - ws.W) * 32 + lane) * K, st.acc);
+        if (st.sp < c.W) vstore<K>(c.s + ((size_t)st.sp * 32 + lane) * K, st.acc);
+        else if (st.sp < c.maxd) vstore<K>(c.g + ((size_t)(st.sp - c.W) * 32 + lane) * K, st.acc);
         else st.ok = false;
-        st.sp += (st.sp < ws.maxd) ? 1 : 0;
-        if (op == 4) {
+        if (st.sp < c.maxd) ++st.sp;
+        const float cv = c.kc[op];
 #pragma unroll
-            for (int k = 0; k < K; ++k) st.acc[k] = xv[k];
-        } else {
-            float c = kc[op - 5];
-#pragma unroll
-            for (int k = 0; k < K; ++k) st.acc[k] = c;
-        }
+        for (int k = 0; k < K; ++k) st.acc[k] = (op == 4) ? c.xv[k] : cv;
     } else {
         float r[K];
         if (st.sp <= 0) {
@@ -83,50 +108,86 @@ __device__ __forceinline__ void interp_step(uint32_t op, InterpState<K>& st, con
             for (int k = 0; k < K; ++k) r[k] = 0.f;
         } else {
             --st.sp;
-            if (st.sp < ws.W) vload<K>(ws.s + ((size_t)st.sp * 32 + lane) * K, r);
-            else vload<K>(ws.g + ((size_t)(st.sp - ws.W) * 32 + lane) * K, r);
+            if (st.sp < c.W) vload<K>(c.s + ((size_t)st.sp * 32 + lane) * K, r);
+            else vload<K>(c.g + ((size_t)(st.sp - c.W) * 32 + lane) * K, r);
         }
-#pragma unroll
-        for (int k = 0; k < K; ++k) st.acc[k] = apply_op(op, st.acc[k], r[k]);
+        apply_vec<K>(op, st.acc, r);
     }
 }
 
-__device__ __forceinline__ uint32_t byte_of(const uint4& w, int j) {
-    uint32_t word = (j < 4) ? w.x : (j < 8) ? w.y : (j < 12) ? w.z : w.w;
-    return (word >> (8 * (j & 3))) & 0xFFu;
-}
-
-// Evaluate ops[s..e) right to left; on return st.acc holds the value of
-// the subtree starting at s (the leftmost of the run).  The buffer must be
-// readable in whole aligned 16-byte chunks around [s, e).
+// One node when the whole stack access stays inside the shared window.
 template <int K>
-__device__ __forceinline__ void interp_run(const uint8_t* __restrict__ ops, uint32_t s, uint32_t e,
-                                           InterpState<K>& st, const WarpStack<K>& ws,
-                                           const float (&xv)[K], const float* __restrict__ kc) {
-    const int lane = lane_id();
-    if (e <= s) return;
-    uint32_t cb = (e - 1) & ~15u;
-    uint4 w = __ldg(reinterpret_cast<const uint4*>(ops + cb));
-    uint32_t p = e;
-    for (;;) {
-        const uint32_t lo = cb > s ? cb : s;
-        uint4 wn = w;
-        if (lo > s) wn = __ldg(reinterpret_cast<const uint4*>(ops + cb - 16));   // next chunk, early
-        if (lo == cb && p == cb + 16) {
+__device__ __forceinline__ void step_fast(uint32_t op, float (&acc)[K], float*& sptr, const Ictx<K>& c) {
+    if (op >= 4) {
+        vstore<K>(sptr, acc);
+        sptr += 32 * K;
+        const float cv = c.kc[op];
 #pragma unroll
-            for (int j = 15; j >= 0; --j) interp_step<K>(byte_of(w, j), st, ws, xv, kc, lane);
-        } else {
-#pragma unroll
-            for (int j = 15; j >= 0; --j) {
-                const uint32_t pos = cb + j;
-                if (pos >= lo && pos < p) interp_step<K>(byte_of(w, j), st, ws, xv, kc, lane);
-            }
-        }
-        if (lo <= s) break;
-        p = lo;
-        cb -= 16;
-        w = wn;
+        for (int k = 0; k < K; ++k) acc[k] = (op == 4) ? c.xv[k] : cv;
+    } else {
+        sptr -= 32 * K;
+        float r[K];
+        vload<K>(sptr, r);
+        apply_vec<K>(op, acc, r);
     }
+}
+
+// Evaluate the nodes [s, e) staged at `stage` (which holds bytes from
+// s & ~15 on) right to left; afterwards st.acc is the value of the subtree
+// starting at s.  Words of four nodes are run without per-node stack
+// checks when the depth leaves room for four pushes or pops.
+template <int K>
+__device__ __forceinline__ void interp_staged(const uint8_t* stage, uint32_t s, uint32_t e,
+                                              Istate<K>& st, const Ictx<K>& c) {
+    const int lane = lane_id();
+    const uint32_t a = s & ~15u;
+    uint32_t p = e;
+    // head: single nodes down to a multiple of 4
+    while (p > s && (p & 3u)) {
+        --p;
+        step_checked<K>(stage[p - a], st, c, lane);
+    }
+    const uint32_t* wp = reinterpret_cast<const uint32_t*>(stage);
+    while (p >= s + 4) {
+        const uint32_t w = wp[(p - 4 - a) >> 2];
+        if (st.sp >= 4 && st.sp + 4 <= c.W) {
+            float* sptr = c.s + ((size_t)st.sp * 32 + lane) * K;
+            step_fast<K>(w >> 24, st.acc, sptr, c);
+            step_fast<K>((w >> 16) & 0xFFu, st.acc, sptr, c);
+            step_fast<K>((w >> 8) & 0xFFu, st.acc, sptr, c);
+            step_fast<K>(w & 0xFFu, st.acc, sptr, c);
+            st.sp = (int)((sptr - c.s - lane * K) / (32 * K));
+        } else {
+            step_checked<K>(w >> 24, st, c, lane);
+            step_checked<K>((w >> 16) & 0xFFu, st, c, lane);
+            step_checked<K>((w >> 8) & 0xFFu, st, c, lane);
+            step_checked<K>(w & 0xFFu, st, c, lane);
+        }
+        p -= 4;
+    }
+    while (p > s) {
+        --p;
+        step_checked<K>(stage[p - a], st, c, lane);
+    }
+}
+
+// ---- staging with cp.async (16 bytes per lane per instruction) ----
+
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
+    uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(smem_dst));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// Issue the copy of bytes [s & ~15, roundup16(e)) of `tree` into `stage`.
+// The tree buffer's capacity is a multiple of 16, so the rounded range
+// stays inside it.  Requires e - (s & ~15) <= STAGE_BYTES.
+__device__ __forceinline__ void stage_issue(uint8_t* stage, const uint8_t* tree, uint32_t s, uint32_t e) {
+    const int lane = lane_id();
+    const uint32_t a = s & ~15u, b = (e + 15u) & ~15u;
+    for (uint32_t q = a + 16u * lane; q < b; q += 512u) cp_async16(stage + (q - a), tree + q);
 }
 
 template <int K>
@@ -151,4 +212,18 @@ __device__ __forceinline__ void store_slot(const DevPop& d, uint32_t slot, uint3
     float* p = d.slots + (size_t)slot * d.Cpad + cbk * 32 * K + lane;
 #pragma unroll
     for (int k = 0; k < K; ++k) p[k * 32] = v[k];
+}
+
+// Shared-memory layout of a CTA running the interpreter.
+template <int K>
+struct SmemLayout {
+    static constexpr size_t kc_bytes = 256 * sizeof(float);
+    __host__ __device__ static size_t stack_bytes(int W) { return (size_t)W * 32 * K * sizeof(float); }
+    __host__ __device__ static size_t warp_bytes(int W) { return stack_bytes(W) + 2 * STAGE_BYTES; }
+    __host__ __device__ static size_t total(int W, int warps) { return kc_bytes + warps * warp_bytes(W); }
+};
+
+// Fill the opcode-indexed constant table (kc[5 + i] = consts[i]).
+__device__ __forceinline__ void fill_kc(float* kc, const float* consts) {
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) kc[i] = (i >= 5) ? consts[i - 5] : 0.0f;
 }

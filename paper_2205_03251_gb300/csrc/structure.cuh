@@ -95,104 +95,99 @@ __device__ __forceinline__ int seg_suffix_max(int v, int L) {
 }
 
 // Block [base, base+GP_B) of a tree of n nodes; lane l owns positions
-// base+32l .. base+32l+31.  pm: 2*GP_B ints of per-warp shared scratch.
+// base+32l .. base+32l+31.  Window maxima use pm: per-warp shared prefix
+// maxima (within T-aligned segments) of blocks k and k+1; suffix maxima of
+// block k are kept as a running value in a reverse sweep.
 #define FLAG_WARPS 4
+// offset j in [0, 2*GP_B) -> padded transposed slot: lanes touching offsets
+// 32 apart (same slot s, consecutive lanes) hit consecutive banks
+#define PMX(j) ((((j) & 31) * 65) + ((j) >> 5))
 __global__ void __launch_bounds__(FLAG_WARPS * 32) k_unit_flags(DevPop d, StructBufs sb) {
-    __shared__ int pm_all[FLAG_WARPS][2 * GP_B];
+    __shared__ int pm_all[FLAG_WARPS][32 * 65];
     int* pm = pm_all[threadIdx.x >> 5];
     const int lane = lane_id();
     const uint32_t nunits = d.blk_off[d.P];
     const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
     const int Ts = (int)d.T;
+    const int L = Ts > 32 ? Ts / 32 : 1;          // lanes per T-segment
     for (uint32_t u = gw; u < nunits; u += nw) {
         const uint32_t tree = find_segment(d.blk_off, d.P, u);
         const uint32_t base = (u - d.blk_off[tree]) * GP_B;
         const uint8_t* ops = tree_ptr(d, tree);
         const uint32_t n = d.size[tree];
-        uint32_t b0 = leaf_bits(ops, n, base + 32 * lane);
-        uint32_t b1 = leaf_bits(ops, n, base + GP_B + 32 * lane);
-        int t0 = 2 * __popc(b0) - 32, t1 = 2 * __popc(b1) - 32;
-        int i0 = warp_incl_sum(t0), i1 = warp_incl_sum(t1);
-        int tot0 = __shfl_sync(FULL, i0, 31);
-        int v0 = i0 - t0;
-        int w0 = tot0 + i1 - t1;
-        int vk[32], vk1[32];
-        int cmax = NEG_INF_I;
+        const uint32_t b0 = leaf_bits(ops, n, base + 32 * lane);
+        const uint32_t b1 = leaf_bits(ops, n, base + GP_B + 32 * lane);
+        const int t0 = 2 * __popc(b0) - 32, t1 = 2 * __popc(b1) - 32;
+        const int i0 = warp_incl_sum(t0), i1 = warp_incl_sum(t1);
+        const int tot0 = __shfl_sync(FULL, i0, 31);
+        const int v0 = i0 - t0;               // block k: balance before the lane's first position
+        const int w0 = tot0 + i1 - t1;        // block k+1
+        // lane maxima of before-balances, and in-segment prefix maxima into pm
+        int m0 = NEG_INF_I, m1 = NEG_INF_I, cmax = NEG_INF_I;
         {
             int a = v0, c = w0;
-#pragma unroll
+#pragma unroll 4
             for (int s = 0; s < 32; ++s) {
-                vk[s] = a; vk1[s] = c;
+                m0 = max(m0, a); m1 = max(m1, c);
                 a += ((b0 >> s) & 1) ? 1 : -1;
                 c += ((b1 >> s) & 1) ? 1 : -1;
                 cmax = max(cmax, a);
             }
         }
-        int smt[32];
-        if (Ts <= 32) {
-            int run0 = NEG_INF_I, run1 = NEG_INF_I;
-#pragma unroll
+        int ex0 = NEG_INF_I, ex1 = NEG_INF_I, exs = NEG_INF_I;   // across-lane parts within the segment
+        if (Ts > 32) {
+            const int p0 = seg_prefix_max(m0, L), p1 = seg_prefix_max(m1, L);
+            ex0 = __shfl_up_sync(FULL, p0, 1);
+            ex1 = __shfl_up_sync(FULL, p1, 1);
+            if ((lane & (L - 1)) == 0) { ex0 = NEG_INF_I; ex1 = NEG_INF_I; }
+            const int sf = seg_suffix_max(m0, L);
+            exs = __shfl_down_sync(FULL, sf, 1);
+            if ((lane & (L - 1)) == L - 1) exs = NEG_INF_I;
+        }
+        {
+            int a = v0, c = w0, r0 = ex0, r1 = ex1;
+#pragma unroll 2
             for (int s = 0; s < 32; ++s) {
-                if ((s & (Ts - 1)) == 0) { run0 = NEG_INF_I; run1 = NEG_INF_I; }
-                run0 = max(run0, vk[s]); run1 = max(run1, vk1[s]);
-                pm[32 * lane + s] = run0;
-                pm[GP_B + 32 * lane + s] = run1;
+                if (Ts <= 32 && (s & (Ts - 1)) == 0) { r0 = NEG_INF_I; r1 = NEG_INF_I; }
+                r0 = max(r0, a); r1 = max(r1, c);
+                pm[PMX(32 * lane + s)] = r0;
+                pm[PMX(GP_B + 32 * lane + s)] = r1;
+                a += ((b0 >> s) & 1) ? 1 : -1;
+                c += ((b1 >> s) & 1) ? 1 : -1;
             }
-            int run = NEG_INF_I;
-#pragma unroll
-            for (int s = 31; s >= 0; --s) {
-                run = max(run, vk[s]);
-                smt[s] = run;
-                if ((s & (Ts - 1)) == 0) run = NEG_INF_I;
-            }
-        } else {
-            const int L = Ts / 32;
-            int m0 = NEG_INF_I, m1 = NEG_INF_I;
-#pragma unroll
-            for (int s = 0; s < 32; ++s) { m0 = max(m0, vk[s]); m1 = max(m1, vk1[s]); }
-            int p0 = seg_prefix_max(m0, L), p1 = seg_prefix_max(m1, L);
-            int e0 = __shfl_up_sync(FULL, p0, 1), e1 = __shfl_up_sync(FULL, p1, 1);
-            if ((lane & (L - 1)) == 0) { e0 = NEG_INF_I; e1 = NEG_INF_I; }
-            int run0 = e0, run1 = e1;
-#pragma unroll
-            for (int s = 0; s < 32; ++s) {
-                run0 = max(run0, vk[s]); run1 = max(run1, vk1[s]);
-                pm[32 * lane + s] = run0;
-                pm[GP_B + 32 * lane + s] = run1;
-            }
-            int sfx = seg_suffix_max(m0, L);
-            int ex = __shfl_down_sync(FULL, sfx, 1);
-            if ((lane & (L - 1)) == L - 1) ex = NEG_INF_I;
-            int run = ex;
-#pragma unroll
-            for (int s = 31; s >= 0; --s) { run = max(run, vk[s]); smt[s] = run; }
         }
         __syncwarp();
-        int smt_next = __shfl_down_sync(FULL, smt[0], 1);
+        // reverse sweep: sm = max of before-balances over [s+1, end of s's T-segment]
         uint32_t flags = 0;
-#pragma unroll
-        for (int s = 0; s < 32; ++s) {
-            int j = 32 * lane + s;          // node i = base + j; window (i, i+T) = offsets [j+1, j+T-1]
-            int a = j + 1;
-            int pmv = pm[a + Ts - 2];
-            int wmax = ((a & (Ts - 1)) == 0) ? pmv : max(s < 31 ? smt[s + 1] : smt_next, pmv);
-            bool big = (wmax <= vk[s]) && ((uint32_t)(base + j) < n);
-            flags |= (uint32_t)big << s;
+        {
+            int v = v0 + t0;                  // balance after the lane's last position
+            int sm = (Ts > 32) ? exs : NEG_INF_I;
+#pragma unroll 2
+            for (int s = 31; s >= 0; --s) {
+                v -= ((b0 >> s) & 1) ? 1 : -1;     // before-balance of slot s
+                const int j = 32 * lane + s;       // node i = base + j; window (i, i+T) = offsets [j+1, j+T-1]
+                const int a = j + 1;
+                const int pmv = pm[PMX(a + Ts - 2)];
+                const int wmax = ((a & (Ts - 1)) == 0) ? pmv : max(sm, pmv);
+                if (wmax <= v && (uint32_t)(base + j) < n) flags |= 1u << s;
+                sm = max(sm, v);
+                if (Ts <= 32 && (s & (Ts - 1)) == 0) sm = NEG_INF_I;
+            }
         }
         if (base == 0 && lane == 0 && n > 0) flags |= 1u;   // every root is cached
         __syncwarp();
         sb.u_flags[(size_t)u * 32 + lane] = flags;
         sb.u_cv0[(size_t)u * 32 + lane] = v0;
         sb.u_cmax[(size_t)u * 32 + lane] = cmax;
-        uint32_t c = __popc(flags);
+        uint32_t cnt = __popc(flags);
         int bm = cmax;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
-            c += __shfl_down_sync(FULL, c, o);
+            cnt += __shfl_down_sync(FULL, cnt, o);
             bm = max(bm, __shfl_down_sync(FULL, bm, o));
         }
-        if (lane == 0) { sb.u_cnt[u] = c; sb.u_total[u] = tot0; sb.u_max[u] = bm; }
+        if (lane == 0) { sb.u_cnt[u] = cnt; sb.u_total[u] = tot0; sb.u_max[u] = bm; }
     }
 }
 
@@ -331,6 +326,20 @@ __global__ void __launch_bounds__(GP_WARPS * 32) k_emit_entries(DevPop d, Struct
     }
 }
 
+// First chunk index c >= from (of 32) whose maximum reaches `need`, or 32;
+// eight independent loads per round.
+__device__ __forceinline__ uint32_t first_chunk_at_least(const int32_t* cm, uint32_t from, int need) {
+    for (uint32_t c0 = from; c0 < 32; c0 += 8) {
+        int v[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) v[j] = (c0 + j < 32) ? cm[c0 + j] : NEG_INF_I;
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+            if (v[j] >= need) return c0 + j;
+    }
+    return 32;
+}
+
 // end(entry) = first position q >= pos with after-balance >= bal + 1, plus one.
 __global__ void k_entry_ends(DevPop d, StructBufs sb) {
     const uint32_t ne = sb.u_epre[d.blk_off[d.P]];
@@ -357,16 +366,28 @@ __global__ void k_entry_ends(DevPop d, StructBufs sb) {
         uint32_t fk = 0xFFFFFFFFu, fc = 0;
         if (endpos == 0xFFFFFFFFu) {
             int bb = (int)(sb.u_bpre[u0 + k] - bp0);
-            for (uint32_t c2 = c + 1; c2 < 32; ++c2)
-                if (bb + sb.u_cmax[(size_t)(u0 + k) * 32 + c2] >= target) { fk = k; fc = c2; break; }
+            fc = first_chunk_at_least(sb.u_cmax + (size_t)(u0 + k) * 32, c + 1, target - bb);
+            if (fc < 32) fk = k;
             if (fk == 0xFFFFFFFFu) {
-                for (uint32_t k2 = k + 1; k2 < nb; ++k2) {
-                    int bb2 = (int)(sb.u_bpre[u0 + k2] - bp0);
-                    if (bb2 + sb.u_max[u0 + k2] >= target) {
-                        for (uint32_t c2 = 0; c2 < 32; ++c2)
-                            if (bb2 + sb.u_cmax[(size_t)(u0 + k2) * 32 + c2] >= target) { fk = k2; fc = c2; break; }
-                        break;
+                // later blocks, eight summaries per round of independent loads
+                uint32_t hitk = 0xFFFFFFFFu;
+                for (uint32_t k2 = k + 1; k2 < nb && hitk == 0xFFFFFFFFu; k2 += 8) {
+                    int64_t bpv[8];
+                    int mxv[8];
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        const uint32_t kk = k2 + j;
+                        bpv[j] = (kk < nb) ? sb.u_bpre[u0 + kk] : 0;
+                        mxv[j] = (kk < nb) ? sb.u_max[u0 + kk] : NEG_INF_I;
                     }
+#pragma unroll
+                    for (int j = 0; j < 8; ++j)
+                        if (hitk == 0xFFFFFFFFu && k2 + j < nb && (int)(bpv[j] - bp0) + mxv[j] >= target) hitk = k2 + j;
+                }
+                if (hitk != 0xFFFFFFFFu) {
+                    int bb2 = (int)(sb.u_bpre[u0 + hitk] - bp0);
+                    fc = first_chunk_at_least(sb.u_cmax + (size_t)(u0 + hitk) * 32, 0, target - bb2);
+                    if (fc < 32) fk = hitk;
                 }
             }
             if (fk != 0xFFFFFFFFu) {
