@@ -172,6 +172,12 @@ int gp_cache_entries(const gp_pop* pop, uint32_t i, uint32_t* pos, uint32_t* end
  * for Boolean) to host.  Synchronising. */
 int gp_cache_value(const gp_pop* pop, uint32_t i, uint32_t j, void* host_out, size_t bytes);
 
+/* Per child of the last gp_eval_incremental: the level at which the walk
+ * stopped (0 = at the crossover point; -1 = the root differed, fitness
+ * recomputed) and the number of levels evaluated above the crossover
+ * point.  Either pointer may be NULL; n <= pop_size.  Synchronising. */
+int gp_walk_info(const gp_pop* pop, int32_t* stop_level, uint32_t* levels, uint32_t n);
+
 /* Statistics of the last gp_eval_full / gp_eval_incremental.  Synchronising. */
 int gp_get_stats(const gp_pop* pop, gp_stats* out);
 

@@ -84,6 +84,7 @@ def load() -> ctypes.CDLL:
         "gp_cache_entries": (i32, [vp, u32, vp, vp, vp, u32, ctypes.POINTER(u32)]),
         "gp_cache_value": (i32, [vp, u32, u32, vp, ctypes.c_size_t]),
         "gp_get_stats": (i32, [vp, ctypes.POINTER(GpStats)]),
+        "gp_walk_info": (i32, [vp, vp, vp, u32]),
         "gp_set_profiling": (i32, [vp, i32]),
     }
     for name, (res, args) in sig.items():
@@ -200,6 +201,14 @@ def gp_get_stats(h) -> GpStats:
     return st
 
 
+def gp_walk_info(h, n: int):
+    """(stop level per child, levels walked per child) of the last incremental evaluation."""
+    stop = np.empty(n, np.int32)
+    lv = np.empty(n, np.uint32)
+    _check(load().gp_walk_info(h, _ptr(stop), _ptr(lv), n), h)
+    return stop, lv
+
+
 def gp_set_profiling(h, on: bool):
     _check(load().gp_set_profiling(h, 1 if on else 0), h)
 
@@ -267,6 +276,9 @@ class Population:
 
     def stats(self) -> dict:
         return gp_get_stats(self.h).as_dict()
+
+    def walk_info(self):
+        return gp_walk_info(self.h, self.P)
 
     def set_profiling(self, on: bool):
         gp_set_profiling(self.h, on)

@@ -45,7 +45,7 @@ struct DevPop {
     int32_t* e_c0;       // [Ecap] large left child entry or -1
     int32_t* e_c1;       // [Ecap] large right child entry or -1
     uint32_t* e_slot;    // [Ecap] value slot
-    int4* stk;           // [Ecap] structure stack scratch (entry, balance, pos, -)
+    uint32_t* e_tree;    // [Ecap] tree of the entry
     // items (small subtrees hanging off the cached skeleton)
     uint4* it_desc;      // [Ecap] (start, length, slot, buffer) of the entry's small-subtree item
     uint4* sk_desc;      // [Ecap] (slot, operand slot, op | child flags, right child entry) for the skeleton pass
@@ -54,6 +54,7 @@ struct DevPop {
     float* slots;        // [Scap][Cpad]
     float* ovf;          // interpreter stack overflow, per warp
     uint32_t* status;    // [1]
+    uint32_t* errinfo;   // [4] first failure: site, individual, position, detail
     uint32_t* e_total;   // [1] cache entries found by the structure pass
     uint32_t* q;         // [NQ] queue counters
     unsigned long long* acc_ops;   // [4] actual-op counters
@@ -63,6 +64,13 @@ __device__ __forceinline__ uint32_t warp_bcast(uint32_t v, int src) { return __s
 __device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
 
 __device__ __forceinline__ void set_status(uint32_t* st, uint32_t bit) { atomicOr(st, bit); }
+
+// Record the first failure site (kept until the host reads and clears it).
+__device__ __forceinline__ void set_error(const DevPop& d, uint32_t bit, uint32_t site, uint32_t who,
+                                          uint32_t pos, uint32_t detail) {
+    atomicOr(d.status, bit);
+    if (atomicCAS(d.errinfo, 0u, site) == 0u) { d.errinfo[1] = who; d.errinfo[2] = pos; d.errinfo[3] = detail; }
+}
 
 // individual i's buffer
 __device__ __forceinline__ const uint8_t* tree_ptr(const DevPop& d, uint32_t i) {

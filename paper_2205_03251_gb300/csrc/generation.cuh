@@ -1,21 +1,885 @@
-// Generation loop: selection, crossover and incremental evaluation.
+// One generation: selection, crossover (copy or in place), and the
+// incremental evaluation of the children with failed disruption
+// propagation (Sec. 5, Sec. 6.2, Sec. 6.3, Fig. 1-3).
 #pragma once
-#include "common.cuh"
+#include "interp.cuh"
+#include "structure.cuh"
 
-struct gp_pop;
+#define HALO_MAX 64            // largest |size change| moved in place (halo bytes per block)
+#define SHIFT_BS 4096          // bytes of tail per block of the in-place move
+#define PV_PER_CHILD 256       // walk records (new path values) reserved per child on average
+#define WALK_MAXLVL 520        // small-ancestor levels held in shared memory (T <= 1024)
+
+enum : uint32_t { F_LAST = 1u, F_CLONE = 2u, F_INPLACE = 4u };
+enum { M_NCOPY = 0, M_NINPLACE, M_NSHIFT, M_PV, M_FRAG, M_STASH, NMISC = 8 };
+enum { G_INTERP = 0, G_LEVELS, G_STOPPED, G_XOBYTES, G_PATHOPS, G_CHILDREN, G_EQUIV, NGSTAT = 8 };
+
+// Read-only view of the parents' cache during a generation.
+struct CacheView {
+    const uint32_t* e_off;
+    const uint32_t* e_pos;
+    const uint32_t* e_end;
+    const int32_t* e_par;
+    const int32_t* e_c0;
+    const int32_t* e_c1;
+    const uint32_t* e_slot;
+    const float* slots;
+};
 
 struct GenBufs {
+    uint32_t *pbuf, *psize;          // parents (swapped with DevPop buf/size each generation)
+    float* pfit;
+    uint32_t *mother, *father, *cpos, *rsz, *dpos, *ssz, *flags;
+    int32_t* lastidx;                // [P] highest child index of each mother, -1 if none
+    uint32_t* free_buf;              // [P] buffers holding no individual
+    uint32_t* free_next;             // [P]
+    uint32_t* hasip;                 // [P] parent keeps its buffer (in-place child)
+    uint32_t* misc;                  // [NMISC]
+    uint64_t* frag_off;              // [P+1] donated subtrees (16-aligned)
+    uint8_t* frag;
+    uint64_t frag_cap;
+    uint64_t* stash_off;             // [P+1] removed subtrees below the threshold (16-aligned)
+    uint8_t* stash;
+    uint64_t stash_cap;
+    uint32_t* shift_off;             // [P+1] in-place move blocks per child (prefix)
+    uint8_t* halo;                   // [blocks * HALO_MAX]
+    uint32_t shift_cap;
+    int32_t* stop;                   // [P] FDP stop level, -1 if the root differs
+    uint32_t* plen;                  // [P] levels evaluated above the crossover point
+    uint4* pv_rec;                   // [pvcap] (child, k, pos, slot)
+    uint32_t* pv_cnt;                // [P]
+    uint32_t* pv_off;                // [P+1]
+    uint2* pv_sorted;                // [pvcap] (pos, slot), per child in walk order
+    uint32_t pvcap;
+    uint32_t* order;                 // [P] walk order
+    unsigned long long* gstat;       // [NGSTAT]
+    uint32_t max_nodes, tsize;
+    uint64_t seed;
+    uint32_t gen;
     bool evaluated;
 };
 
-template <typename Alloc>
-int gen_alloc(GenBufs& g, const DevPop& d, Alloc alloc) {
-    (void)d; (void)alloc;
-    g.evaluated = false;
-    return 0;
+// ------------------------------------------------------------------ helpers
+
+__device__ __forceinline__ uint64_t sm64(uint64_t seed, uint64_t ctr) {
+    // SplitMix64 (Steele, Lea and Flood 2014): element ctr of the stream started at seed
+    uint64_t z = seed + (ctr + 1) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+__device__ __forceinline__ uint64_t draw(uint64_t seed, uint32_t gen, uint32_t child, uint32_t k) {
+    return sm64(seed, ((uint64_t)gen << 40) | ((uint64_t)child << 8) | (uint64_t)(k & 0xFFu));
+}
+__device__ __forceinline__ uint64_t below(uint64_t r, uint64_t n) { return ((r >> 32) * n) >> 32; }
+
+// Index of the entry at position x in [lo, hi) (sorted by position), or -1.
+__device__ __forceinline__ int32_t find_exact(const uint32_t* e_pos, uint32_t lo, uint32_t hi, uint32_t x) {
+    while (lo < hi) {
+        uint32_t mid = (lo + hi) >> 1;
+        uint32_t v = e_pos[mid];
+        if (v == x) return (int32_t)mid;
+        if (v < x) lo = mid + 1; else hi = mid;
+    }
+    return -1;
+}
+// Last entry with position < x in [lo, hi), or -1.
+__device__ __forceinline__ int32_t find_last_lt(const uint32_t* e_pos, uint32_t lo, uint32_t hi, uint32_t x) {
+    uint32_t a = lo, b = hi;            // first index with pos >= x
+    while (a < b) {
+        uint32_t mid = (a + b) >> 1;
+        if (e_pos[mid] < x) a = mid + 1; else b = mid;
+    }
+    return (a > lo) ? (int32_t)(a - 1) : -1;
 }
 
-inline void gen_mark_evaluated(GenBufs& g) { g.evaluated = true; }
+// Size of the subtree at x of a parent tree: a cached entry gives it
+// directly; otherwise it is below the threshold and a forward balance scan
+// of fewer than T bytes finds its end.
+__device__ uint32_t subtree_size_at(const DevPop& d, const CacheView& par, uint32_t t, const uint8_t* ops,
+                                    uint32_t n, uint32_t x) {
+    int32_t e = find_exact(par.e_pos, par.e_off[t], par.e_off[t + 1], x);
+    if (e >= 0) return par.e_end[e] - x;
+    int need = 1;
+    uint32_t q = x;
+    while (q < n) {
+        need += (ops[q] < 4) ? 1 : -1;
+        ++q;
+        if (need == 0) return q - x;
+    }
+    return n - x;     // unreachable for well-formed trees
+}
 
-int gen_crossover(gp_pop* pop, uint32_t generation);
-int gen_incremental(gp_pop* pop);
+__device__ __forceinline__ uint32_t tournament(const float* fit, uint32_t P, uint32_t T, uint64_t seed,
+                                               uint32_t gen, uint32_t child, uint32_t kbase) {
+    uint32_t best = 0;
+    float bf = 0.f;
+    for (uint32_t j = 0; j < T; ++j) {
+        uint32_t idx = (uint32_t)below(draw(seed, gen, child, kbase + j), P);
+        float f = fit[idx];
+        if (isnan(f)) f = __int_as_float(0x7F800000);
+        if (j == 0 || f < bf) { best = idx; bf = f; }
+    }
+    return best;
+}
+
+// 16 bytes starting at any address (two aligned loads and a funnel shift);
+// may read up to 31 bytes past p.
+__device__ __forceinline__ uint4 load16u(const uint8_t* p) {
+    const uintptr_t a = reinterpret_cast<uintptr_t>(p);
+    const uint32_t m = (uint32_t)(a & 15u);
+    const uint4* A = reinterpret_cast<const uint4*>(a - m);
+    const uint4 lo = A[0];
+    if (!m) return lo;
+    const uint4 hi = A[1];
+    const uint32_t w[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
+    const uint32_t mw = m >> 2, sh = (m & 3u) * 8u;
+    uint32_t r[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+        uint32_t x = 0, y = 0;
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+            if ((uint32_t)c == mw) { x = w[t + c]; y = w[t + c + 1]; }
+        r[t] = __funnelshift_r(x, y, sh);
+    }
+    return make_uint4(r[0], r[1], r[2], r[3]);
+}
+
+// ------------------------------------------------------------------ A5 plan
+
+// Child i: mother and father by tournament (draws 0..T-1 and T..2T-1), then
+// up to 8 attempts of crossover points uniform over the nodes of each
+// parent (draws 2T+2a, 2T+2a+1) whose child fits max_nodes; otherwise the
+// child is a copy of its mother.
+__global__ void k_plan(DevPop d, GenBufs g, CacheView par) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < d.P; i += gridDim.x * blockDim.x) {
+        const uint32_t T = g.tsize;
+        const uint32_t m = tournament(g.pfit, d.P, T, g.seed, g.gen, i, 0);
+        const uint32_t f = tournament(g.pfit, d.P, T, g.seed, g.gen, i, T);
+        const uint32_t sm = g.psize[m], sf = g.psize[f];
+        const uint8_t* om = d.arena + (size_t)g.pbuf[m] * d.cap;
+        const uint8_t* of = d.arena + (size_t)g.pbuf[f] * d.cap;
+        uint32_t fl = F_CLONE, cc = 0, rr = sm, dd = 0, ss = sm, ff = m;
+        for (uint32_t a = 0; a < 8; ++a) {
+            const uint32_t c1 = (uint32_t)below(draw(g.seed, g.gen, i, 2 * T + 2 * a), sm);
+            const uint32_t d1 = (uint32_t)below(draw(g.seed, g.gen, i, 2 * T + 2 * a + 1), sf);
+            const uint32_t r1 = subtree_size_at(d, par, m, om, sm, c1);
+            const uint32_t s1 = subtree_size_at(d, par, f, of, sf, d1);
+            if ((uint64_t)sm - r1 + s1 <= g.max_nodes) { fl = 0; cc = c1; rr = r1; dd = d1; ss = s1; ff = f; break; }
+        }
+        g.mother[i] = m; g.father[i] = ff; g.cpos[i] = cc; g.rsz[i] = rr; g.dpos[i] = dd; g.ssz[i] = ss;
+        g.flags[i] = fl;
+        atomicMax(&g.lastidx[m], (int32_t)i);
+    }
+}
+
+// Block-wide exclusive scan of v (1024 threads); returns the exclusive
+// prefix and adds the block total to *carry (shared).
+__device__ __forceinline__ uint64_t block_excl_scan(uint64_t v, uint64_t* ws, uint64_t* carry) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint64_t s = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) { uint64_t t = __shfl_up_sync(FULL, s, o); if (lane >= o) s += t; }
+    if (lane == 31) ws[w] = s;
+    __syncthreads();
+    if (w == 0) {
+        uint64_t x = ws[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) { uint64_t t = __shfl_up_sync(FULL, x, o); if (lane >= o) x += t; }
+        ws[lane] = x;
+    }
+    __syncthreads();
+    const uint64_t incl = s + (w > 0 ? ws[w - 1] : 0);
+    const uint64_t res = *carry + incl - v;
+    __syncthreads();
+    if (threadIdx.x == blockDim.x - 1) *carry += incl;
+    __syncthreads();
+    return res;
+}
+
+// Buffer assignment and offsets (one CTA of 1024 threads).  The last child
+// of a mother is built in place in her buffer when its size change is at
+// most HALO_MAX (Fig. 2), every other child is copied into a free buffer
+// (Fig. 1).  Buffers of parents without an in-place child are freed.
+__global__ void __launch_bounds__(1024) k_assign(DevPop d, GenBufs g) {
+    __shared__ uint64_t ws[32];
+    __shared__ uint64_t carry[5];
+    if (threadIdx.x < 5) carry[threadIdx.x] = 0;
+    for (uint32_t j = threadIdx.x; j < d.P; j += blockDim.x) g.hasip[j] = 0;
+    __syncthreads();
+    const uint32_t P = d.P;
+    for (uint32_t base = 0; base < P; base += blockDim.x) {
+        const uint32_t i = base + threadIdx.x;
+        uint32_t copy = 0, nblk = 0;
+        uint64_t fragb = 0, stashb = 0, xob = 0;
+        if (i < P) {
+            const uint32_t m = g.mother[i];
+            uint32_t fl = g.flags[i];
+            const bool last = g.lastidx[m] == (int32_t)i;
+            const bool clone = fl & F_CLONE;
+            const uint32_t r = g.rsz[i], s = g.ssz[i], c = g.cpos[i];
+            const uint32_t sm = g.psize[m];
+            const int64_t delta = (int64_t)s - (int64_t)r;
+            const bool inplace = last && (clone || (delta >= -HALO_MAX && delta <= HALO_MAX));
+            if (last) fl |= F_LAST;
+            if (inplace) { fl |= F_INPLACE; g.hasip[m] = 1; }
+            g.flags[i] = fl;
+            copy = inplace ? 0 : 1;
+            d.size[i] = (uint32_t)((int64_t)sm + delta);
+            if (!clone) {
+                fragb = (s + 15u) & ~15u;
+                if (r < d.T) stashb = (r + 15u) & ~15u;
+                const uint64_t tail = (uint64_t)sm - c - r;
+                if (inplace && delta != 0 && tail > 0) nblk = (uint32_t)((tail + SHIFT_BS - 1) / SHIFT_BS);
+                xob = 2ull * s + (r < d.T ? 2ull * r : 0) +
+                      (inplace ? (delta != 0 ? 2ull * tail : 0) + s : 2ull * ((uint64_t)sm - r + s));
+            } else if (!inplace) {
+                xob = 2ull * sm;
+            }
+        }
+        const uint64_t rank = block_excl_scan(copy, ws, &carry[0]);
+        const uint64_t fo = block_excl_scan(fragb, ws, &carry[1]);
+        const uint64_t so = block_excl_scan(stashb, ws, &carry[2]);
+        const uint64_t bo = block_excl_scan(nblk, ws, &carry[3]);
+        const uint64_t xo = block_excl_scan(xob, ws, &carry[4]);
+        (void)xo;
+        if (i < P) {
+            const uint32_t m = g.mother[i];
+            d.buf[i] = copy ? g.free_buf[rank] : g.pbuf[m];
+            g.frag_off[i] = fo;
+            g.stash_off[i] = so;
+            g.shift_off[i] = (uint32_t)bo;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        g.frag_off[P] = carry[1];
+        g.stash_off[P] = carry[2];
+        g.shift_off[P] = (uint32_t)carry[3];
+        g.misc[M_NCOPY] = (uint32_t)carry[0];
+        g.misc[M_NSHIFT] = (uint32_t)carry[3];
+        g.gstat[G_XOBYTES] = carry[4];
+        if (carry[1] > g.frag_cap || carry[2] > g.stash_cap || carry[3] > g.shift_cap) set_status(d.status, ST_CAPACITY);
+    }
+    __syncthreads();
+    // next free list: unused free buffers, then buffers of parents with no in-place child
+    const uint32_t ncopy = (uint32_t)carry[0];
+    __shared__ uint64_t carry2;
+    if (threadIdx.x == 0) carry2 = 0;
+    __syncthreads();
+    for (uint32_t k = threadIdx.x; k < P - ncopy; k += blockDim.x) g.free_next[k] = g.free_buf[ncopy + k];
+    for (uint32_t base = 0; base < P; base += blockDim.x) {
+        const uint32_t j = base + threadIdx.x;
+        const uint32_t fr = (j < P && !g.hasip[j]) ? 1u : 0u;
+        const uint64_t pos = block_excl_scan(fr, ws, &carry2);
+        if (fr && (P - ncopy) + pos < P) g.free_next[(P - ncopy) + pos] = g.pbuf[j];
+    }
+    __syncthreads();
+    for (uint32_t k = threadIdx.x; k < P; k += blockDim.x) g.free_buf[k] = g.free_next[k];
+}
+
+// ------------------------------------------------------------------ A6 gather
+
+// Donated subtrees (all children) and removed subtrees below the threshold
+// copied out before any buffer is written (Sec. 5: fatherless crossover).
+__global__ void k_gather(DevPop d, GenBufs g) {
+    if (g.frag_off[d.P] > g.frag_cap || g.stash_off[d.P] > g.stash_cap) return;
+    for (uint32_t i = blockIdx.x; i < d.P; i += gridDim.x) {
+        if (g.flags[i] & F_CLONE) continue;
+        const uint8_t* of = d.arena + (size_t)g.pbuf[g.father[i]] * d.cap + g.dpos[i];
+        uint8_t* dst = g.frag + g.frag_off[i];
+        const uint32_t s = g.ssz[i];
+        for (uint32_t q = threadIdx.x; q < (s + 15) / 16; q += blockDim.x)
+            reinterpret_cast<uint4*>(dst)[q] = load16u(of + 16 * q);
+        const uint32_t r = g.rsz[i];
+        if (r < d.T) {
+            const uint8_t* om = d.arena + (size_t)g.pbuf[g.mother[i]] * d.cap + g.cpos[i];
+            uint8_t* st = g.stash + g.stash_off[i];
+            for (uint32_t q = threadIdx.x; q < (r + 15) / 16; q += blockDim.x)
+                reinterpret_cast<uint4*>(st)[q] = load16u(om + 16 * q);
+        }
+    }
+}
+
+// ------------------------------------------------------------------ A8 materialise
+
+// Children built in a free buffer: mother head, donated subtree, mother
+// tail (Fig. 1), 16 destination bytes per thread.
+__global__ void k_copy_children(DevPop d, GenBufs g) {
+    if (g.frag_off[d.P] > g.frag_cap) return;
+    for (uint32_t i = blockIdx.x; i < d.P; i += gridDim.x) {
+        const uint32_t fl = g.flags[i];
+        if (fl & F_INPLACE) continue;
+        const uint32_t m = g.mother[i];
+        const uint8_t* om = d.arena + (size_t)g.pbuf[m] * d.cap;
+        uint8_t* dst = d.arena + (size_t)d.buf[i] * d.cap;
+        const uint32_t nk = d.size[i];
+        if (fl & F_CLONE) {
+            for (uint32_t q = threadIdx.x; q < (nk + 15) / 16; q += blockDim.x)
+                reinterpret_cast<uint4*>(dst)[q] = reinterpret_cast<const uint4*>(om)[q];
+            continue;
+        }
+        const uint32_t c = g.cpos[i], r = g.rsz[i], s = g.ssz[i];
+        const uint8_t* fr = g.frag + g.frag_off[i];
+        for (uint32_t q = threadIdx.x; q < (nk + 15) / 16; q += blockDim.x) {
+            const uint32_t o = 16 * q;
+            uint4 v;
+            if (o + 16 <= c) v = reinterpret_cast<const uint4*>(om)[q];
+            else if (o >= c + s) v = load16u(om + (o - s + r));
+            else if (o >= c && o + 16 <= c + s) v = load16u(fr + (o - c));
+            else {
+                uint8_t b[16];
+#pragma unroll
+                for (int t = 0; t < 16; ++t) {
+                    const uint32_t x = o + t;
+                    b[t] = (x < c) ? om[x] : (x < c + s) ? fr[x - c] : (x < nk ? om[x - s + r] : 0);
+                }
+                v = *reinterpret_cast<uint4*>(b);
+            }
+            reinterpret_cast<uint4*>(dst)[q] = v;
+        }
+    }
+}
+
+// In-place children (Fig. 2): the tail [c+r, n) of the mother moves by
+// delta = s - r within her buffer.  Blocks of SHIFT_BS source bytes move
+// concurrently; the |delta| bytes of a block that its neighbour overwrites
+// are saved first (k_save_halo) and read from there.
+__device__ __forceinline__ void shift_block_geom(const DevPop& d, const GenBufs& g, uint32_t b, uint32_t& i,
+                                                 uint32_t& j, uint32_t& nblk, uint32_t& src0, uint32_t& len,
+                                                 int32_t& delta) {
+    i = find_segment(g.shift_off, d.P, b);
+    j = b - g.shift_off[i];
+    nblk = g.shift_off[i + 1] - g.shift_off[i];
+    const uint32_t m = g.mother[i];
+    const uint32_t tail = g.psize[m] - g.cpos[i] - g.rsz[i];
+    src0 = g.cpos[i] + g.rsz[i] + j * SHIFT_BS;
+    len = min((uint32_t)SHIFT_BS, tail - j * SHIFT_BS);
+    delta = (int32_t)g.ssz[i] - (int32_t)g.rsz[i];
+}
+
+__global__ void k_save_halo(DevPop d, GenBufs g) {
+    const uint32_t nb = g.shift_off[d.P];
+    if (nb > g.shift_cap) return;
+    for (uint32_t b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += gridDim.x * blockDim.x) {
+        uint32_t i, j, nblk, src0, len;
+        int32_t delta;
+        shift_block_geom(d, g, b, i, j, nblk, src0, len, delta);
+        const uint8_t* buf = d.arena + (size_t)d.buf[i] * d.cap;
+        uint8_t* h = g.halo + (size_t)b * HALO_MAX;
+        const uint32_t ad = (uint32_t)(delta > 0 ? delta : -delta);
+        const uint32_t k = min(ad, len);
+        if (delta > 0 && j > 0) for (uint32_t t = 0; t < k; ++t) h[t] = buf[src0 + t];
+        if (delta < 0 && j + 1 < nblk) for (uint32_t t = 0; t < k; ++t) h[t] = buf[src0 + len - k + t];
+    }
+}
+
+__global__ void __launch_bounds__(256) k_shift(DevPop d, GenBufs g) {
+    __shared__ uint8_t sb[SHIFT_BS];
+    const uint32_t nb = g.shift_off[d.P];
+    if (nb > g.shift_cap) return;
+    for (uint32_t b = blockIdx.x; b < nb; b += gridDim.x) {
+        uint32_t i, j, nblk, src0, len;
+        int32_t delta;
+        shift_block_geom(d, g, b, i, j, nblk, src0, len, delta);
+        uint8_t* buf = d.arena + (size_t)d.buf[i] * d.cap;
+        const uint8_t* h = g.halo + (size_t)b * HALO_MAX;
+        const uint32_t ad = (uint32_t)(delta > 0 ? delta : -delta);
+        const uint32_t k = min(ad, len);
+        for (uint32_t t = threadIdx.x; t < len; t += blockDim.x) {
+            uint8_t v;
+            if (delta > 0 && j > 0 && t < k) v = h[t];
+            else if (delta < 0 && j + 1 < nblk && t >= len - k) v = h[t - (len - k)];
+            else v = buf[src0 + t];
+            sb[t] = v;
+        }
+        __syncthreads();
+        for (uint32_t t = threadIdx.x; t < len; t += blockDim.x) buf[(int64_t)src0 + delta + t] = sb[t];
+        __syncthreads();
+    }
+}
+
+// Donated subtree written into the in-place children (after the move).
+__global__ void k_write_frags(DevPop d, GenBufs g) {
+    if (g.frag_off[d.P] > g.frag_cap) return;
+    for (uint32_t i = blockIdx.x; i < d.P; i += gridDim.x) {
+        const uint32_t fl = g.flags[i];
+        if (!(fl & F_INPLACE) || (fl & F_CLONE)) continue;
+        uint8_t* dst = d.arena + (size_t)d.buf[i] * d.cap + g.cpos[i];
+        const uint8_t* fr = g.frag + g.frag_off[i];
+        const uint32_t s = g.ssz[i];
+        for (uint32_t t = threadIdx.x; t < s; t += blockDim.x) dst[t] = fr[t];
+    }
+}
+
+// ------------------------------------------------------------------ A7 incremental walk
+
+template <int K>
+struct WalkSmem {
+    // per warp: interpreter stack, two staging buffers, small-ancestor list, level ends
+    __host__ __device__ static size_t stack_bytes(int W) { return (size_t)W * 32 * K * sizeof(float); }
+    __host__ __device__ static size_t warp_bytes(int W) {
+        return stack_bytes(W) + 2 * STAGE_BYTES + 3 * WALK_MAXLVL * sizeof(uint32_t) + 64 * sizeof(float) * K;
+    }
+    __host__ __device__ static size_t total(int W, int warps) { return 256 * sizeof(float) + warps * warp_bytes(W); }
+};
+
+template <int K>
+__device__ __forceinline__ void load_vec(const float* slots, uint32_t Cpad, uint32_t slot, float (&v)[K]) {
+    const int lane = lane_id();
+    const float* p = slots + (size_t)slot * Cpad + lane;
+#pragma unroll
+    for (int k = 0; k < K; ++k) v[k] = __ldcg(p + k * 32);
+}
+
+template <int K>
+__device__ __forceinline__ bool same_bits(const float (&a)[K], const float (&b)[K], uint32_t C) {
+    const int lane = lane_id();
+    bool ok = true;
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+        if ((uint32_t)(k * 32 + lane) < C && __float_as_uint(a[k]) != __float_as_uint(b[k])) ok = false;
+    return __all_sync(FULL, ok);
+}
+
+// left/right combination keeping the operand order of the node
+template <int K>
+__device__ __forceinline__ void combine(uint32_t op, bool path_left, float (&v)[K], const float (&sib)[K]) {
+    if (path_left) apply_vec<K>(op, v, sib);
+    else {
+        float t[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) t[k] = sib[k];
+        apply_vec<K>(op, t, v);
+#pragma unroll
+        for (int k = 0; k < K; ++k) v[k] = t[k];
+    }
+}
+
+// Evaluate bytes [s, e) of `src` (a small run: e - (s & ~15) <= STAGE_BYTES).
+template <int K>
+__device__ __forceinline__ void eval_run(const uint8_t* src, uint32_t s, uint32_t e, uint8_t* stage,
+                                         const Ictx<K>& c, float (&out)[K], uint32_t* status) {
+    __syncwarp();
+    stage_issue(stage, src, s, e);
+    cp_async_commit();
+    cp_async_wait<0>();
+    __syncwarp();
+    Istate<K> st;
+#pragma unroll
+    for (int k = 0; k < K; ++k) st.acc[k] = 0.f;
+    st.sp = 0;
+    st.ok = true;
+    interp_staged<K>(stage, s, e, st, c);
+    if (!st.ok && lane_id() == 0) set_status(status, ST_STACK);
+#pragma unroll
+    for (int k = 0; k < K; ++k) out[k] = st.acc[k];
+}
+
+// Bottom-up incremental evaluation of one child per warp (Sec. 6.2, Fig. 3).
+// Level 0 compares the donated subtree's value with the removed subtree's;
+// each higher level combines the running values with the sibling's value
+// (cached when its subtree is large, else interpreted) and compares the
+// child's with the mother's.  The walk stops at the first level where the
+// two agree on every case, bit for bit.  Ancestors below the threshold lie
+// within T positions before the crossover point and are found by a
+// backward balance scan; larger ones come from the mother's cache links.
+// New values of nodes that are cached in the child are recorded in the
+// child's cache; above the stop only child-cached nodes that the mother
+// does not cache need computing.
+template <int K>
+__global__ void __launch_bounds__(GP_WARPS * 32) k_walk(DevPop d, GenBufs g, CacheView par) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float* kc = reinterpret_cast<float*>(smem_raw);
+    const int lane = lane_id(), warp = threadIdx.x >> 5;
+    fill_kc(kc, d.consts);
+    __syncthreads();
+    unsigned char* wb = smem_raw + 256 * sizeof(float) + (size_t)warp * WalkSmem<K>::warp_bytes((int)d.W);
+    Ictx<K> ic;
+    ic.s = reinterpret_cast<float*>(wb);
+    ic.W = (int)d.W;
+    ic.maxd = (int)d.maxdepth;
+    ic.kc = kc;
+    ic.g = d.ovf + (size_t)(blockIdx.x * GP_WARPS + warp) * (d.maxdepth - d.W) * 32 * K;
+    uint8_t* stA = wb + WalkSmem<K>::stack_bytes((int)d.W);
+    uint8_t* stB = stA + STAGE_BYTES;
+    uint32_t* anc = reinterpret_cast<uint32_t*>(stB + STAGE_BYTES);     // small ancestor positions
+    int32_t* ancg = reinterpret_cast<int32_t*>(anc + WALK_MAXLVL);       // their balance offsets G
+    uint32_t* lvl = reinterpret_cast<uint32_t*>(ancg + WALK_MAXLVL);     // lvl[v] = child end of level v
+    float* red = reinterpret_cast<float*>(lvl + WALK_MAXLVL);            // fitness reduction scratch
+    load_cases<K>(d, 0, ic.xv);
+    const uint32_t T = d.T;
+    const uint32_t Cn = d.C;
+    unsigned long long st_interp = 0, st_levels = 0, st_stopped = 0, st_pathops = 0;
+
+    for (;;) {
+        uint32_t qi = 0;
+        if (lane == 0) qi = atomicAdd(&d.q[Q_WALK], 1u);
+        qi = __shfl_sync(FULL, qi, 0);
+        if (qi >= d.P) break;
+        const uint32_t i = g.order[qi];
+        const uint32_t fl = g.flags[i];
+        const uint32_t m = g.mother[i];
+        if (fl & F_CLONE) {
+            if (lane == 0) { d.fit[i] = g.pfit[m]; g.stop[i] = 0; g.plen[i] = 0; g.pv_cnt[i] = 0; }
+            ++st_stopped;
+            continue;
+        }
+        const uint32_t f = g.father[i], c = g.cpos[i], r = g.rsz[i], dd = g.dpos[i], s = g.ssz[i];
+        const int32_t delta = (int32_t)s - (int32_t)r;
+        const uint32_t nk = d.size[i];
+        const uint8_t* ok_ = d.arena + (size_t)d.buf[i] * d.cap;     // child bytes
+        const uint32_t me0 = par.e_off[m], me1 = par.e_off[m + 1];
+        const uint32_t fe0 = par.e_off[f], fe1 = par.e_off[f + 1];
+        uint32_t npv = 0;
+
+        // ---- level 0: donated subtree vs removed subtree
+        float nv[K], ov[K];
+        if (s >= T || dd == 0) {
+            const int32_t ef = find_exact(par.e_pos, fe0, fe1, dd);
+            if (ef < 0) { if (lane == 0) set_error(d, ST_STRUCT, 3, i, dd, s); continue; }
+            load_vec<K>(par.slots, d.Cpad, par.e_slot[ef], nv);
+        } else {
+            eval_run<K>(ok_, c, c + s, stA, ic, nv, d.status);
+            st_interp += s;
+        }
+        int32_t em = -1;
+        if (r >= T || c == 0) {
+            em = find_exact(par.e_pos, me0, me1, c);
+            if (em < 0) { if (lane == 0) set_error(d, ST_STRUCT, 4, i, c, r); continue; }
+            load_vec<K>(par.slots, d.Cpad, par.e_slot[em], ov);
+        } else {
+            eval_run<K>(g.stash + g.stash_off[i], 0, r, stA, ic, ov, d.status);
+            st_interp += r;
+        }
+        bool stopped = same_bits<K>(nv, ov, Cn);
+        int32_t stop_level = stopped ? 0 : -1;
+        uint32_t levels = 0;
+        if (c == 0 && s < T && dd != 0) {
+            // the donated subtree becomes the child's root (always cached) but the
+            // father does not cache it: keep the value computed at level 0
+            uint32_t slot = 0;
+            if (lane == 0) slot = atomicAdd(&g.misc[M_PV], 1u);
+            slot = __shfl_sync(FULL, slot, 0);
+            if (slot >= g.pvcap) { if (lane == 0) set_status(d.status, ST_PATH); continue; }
+            float* dst = d.slots + (size_t)slot * d.Cpad + lane;
+#pragma unroll
+            for (int kk = 0; kk < K; ++kk) dst[kk * 32] = nv[kk];
+            if (lane == 0) g.pv_rec[slot] = make_uint4(i, npv, 0u, slot);
+            ++npv;
+        }
+
+        // ---- ancestors: deepest cached ancestor A, then the small ones below it
+        int32_t A = -1;
+        uint32_t nsmall = 0;
+        if (em >= 0) A = par.e_par[em];
+        else {
+            int32_t e = find_last_lt(par.e_pos, me0, me1, c);
+            uint32_t guard = 0;
+            while (e >= 0 && par.e_end[e] <= c && guard++ < (1u << 24)) e = par.e_par[e];
+            A = e;
+            if (A < 0) { if (lane == 0) set_error(d, ST_STRUCT, 5, i, c, 0); continue; }
+            // backward scan of (max(pos(A)+1, c-T+1) .. c-1]: G(j) = sum_{k=j}^{c-1} (arity_k - 1);
+            // j is an ancestor of c iff G(j) >= G(m) for every m in (j, c], G(c) = 0
+            const uint32_t pA = par.e_pos[A];
+            const uint32_t lo = max(pA + 1, (c + 1 > T) ? c + 1 - T : 0u);
+            if (lo < c) {
+                __syncwarp();
+                stage_issue(stB, ok_, lo, c);
+                cp_async_commit();
+                cp_async_wait<0>();
+                __syncwarp();
+                const uint32_t a16 = lo & ~15u;
+                // lane l: positions c-1-32l-t, t = 0..31 (nearest first)
+                int sum = 0, mx = -0x40000000;
+                for (int t = 0; t < 32; ++t) {
+                    const int64_t j = (int64_t)c - 1 - 32 * lane - t;
+                    if (j >= (int64_t)lo) { sum += (stB[j - a16] < 4) ? 1 : -1; mx = max(mx, sum); }
+                }
+                // G offset from the lanes nearer to c, and the maximum G seen before this lane
+                int incl = sum;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    int ts = __shfl_up_sync(FULL, incl, o);
+                    if (lane >= o) incl += ts;
+                }
+                const int base = incl - sum;
+                int pm = (mx > -0x40000000) ? base + mx : -0x40000000;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    int tm = __shfl_up_sync(FULL, pm, o);
+                    if (lane >= o) pm = max(pm, tm);
+                }
+                int prevmax = __shfl_up_sync(FULL, pm, 1);
+                if (lane == 0) prevmax = 0;            // G(c) = 0
+                prevmax = max(prevmax, 0);
+                uint32_t fmask = 0;
+                int run = prevmax, gsum = base;
+                for (int t = 0; t < 32; ++t) {
+                    const int64_t j = (int64_t)c - 1 - 32 * lane - t;
+                    if (j >= (int64_t)lo) {
+                        gsum += (stB[j - a16] < 4) ? 1 : -1;
+                        if (gsum >= run) { fmask |= 1u << t; run = gsum; }
+                    }
+                }
+                // compact in nearest-first order
+                const uint32_t cnt = __popc(fmask);
+                uint32_t off = cnt;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    uint32_t tt = __shfl_up_sync(FULL, off, o);
+                    if (lane >= o) off += tt;
+                }
+                off -= cnt;
+                const uint32_t tot = __shfl_sync(FULL, off + cnt, 31);
+                if (tot > WALK_MAXLVL - 2) { if (lane == 0) set_status(d.status, ST_PATH); continue; }
+                gsum = base;
+                uint32_t k = off;
+                for (int t = 0; t < 32; ++t) {
+                    const int64_t j = (int64_t)c - 1 - 32 * lane - t;
+                    if (j >= (int64_t)lo) {
+                        gsum += (stB[j - a16] < 4) ? 1 : -1;
+                        if (fmask & (1u << t)) { anc[k] = (uint32_t)j; ancg[k] = gsum; ++k; }
+                    }
+                }
+                nsmall = tot;
+                __syncwarp();
+            }
+        }
+        // ---- child ends of the small ancestors: forward scan after the donated subtree
+        // balance relative to b[c] is 1 at c+s; lvl[v] = first position where it reaches v
+        uint32_t maxv = 1;
+        if (nsmall) maxv = (uint32_t)ancg[nsmall - 1] + 1;
+        if (maxv >= WALK_MAXLVL) { if (lane == 0) set_status(d.status, ST_PATH); continue; }
+        if (nsmall) {
+            const uint32_t f0 = c + s;
+            const uint32_t f1 = f0 + T;
+            // sentinel 0 for levels the scan does not reach: their sibling ranges then fail the
+            // size check below instead of reading a stale end
+            for (uint32_t v = lane; v <= maxv; v += 32) lvl[v] = 0;
+            __syncwarp();
+            const uint32_t lim = min(f1, (nk + 15u) & ~15u);
+            if (f0 < lim) { stage_issue(stB, ok_, f0, lim); }
+            cp_async_commit();
+            cp_async_wait<0>();
+            __syncwarp();
+            const uint32_t a16 = f0 & ~15u;
+            if (lane == 0) lvl[1] = f0;
+            int sum = 0, mx = 0;
+            // lane l: positions f0 + 32l + t
+            for (int t = 0; t < 32; ++t) {
+                const uint32_t q = f0 + 32 * lane + t;
+                const int w = (q < nk && stB[q - a16] < 4) ? -1 : 1;
+                sum += w;
+                mx = max(mx, sum);
+            }
+            int incl = sum;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) { int ts = __shfl_up_sync(FULL, incl, o); if (lane >= o) incl += ts; }
+            const int base = 1 + incl - sum;          // balance before the lane's first position
+            int lmax = base + mx;                      // max after-balance in the lane (or base)
+            lmax = max(lmax, base);
+            int pm = lmax;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) { int tm = __shfl_up_sync(FULL, pm, o); if (lane >= o) pm = max(pm, tm); }
+            int prev = __shfl_up_sync(FULL, pm, 1);
+            if (lane == 0) prev = 1;
+            prev = max(prev, base);
+            int bal = base;
+            for (int t = 0; t < 32; ++t) {
+                const uint32_t q = f0 + 32 * lane + t;
+                bal += (q < nk && stB[q - a16] < 4) ? -1 : 1;
+                if (bal > prev) { if ((uint32_t)bal < WALK_MAXLVL) lvl[bal] = q + 1; prev = bal; }
+            }
+            __syncwarp();
+        }
+        // highest small ancestor that the child caches (needs a value even above the stop)
+        int32_t hneed = -1;
+        for (uint32_t k = 0; k < nsmall; ++k) {
+            const uint32_t p = anc[k];
+            const uint32_t pe = lvl[ancg[k] + 1];
+            if (pe - p >= T) hneed = (int32_t)k;
+        }
+
+        // ---- walk up
+        uint32_t q = c, qend = c + s;
+        int32_t qe = em;                 // entry of q in the mother cache, -1 if small
+        uint32_t k = 0;
+        int32_t pe_ = (nsmall > 0) ? -1 : A;
+        bool done = false;
+        uint32_t level = 0;
+        uint32_t guard = 0;
+        while (!done && guard++ < (1u << 24)) {
+            uint32_t p, pend;
+            int32_t pent;
+            if (k < nsmall) {
+                p = anc[k];
+                pend = lvl[ancg[k] + 1];
+                pent = -1;
+            } else {
+                pent = (k == nsmall) ? A : pe_;
+                if (pent < 0) break;                                 // above the root
+                p = par.e_pos[pent];
+                pend = (uint32_t)((int64_t)par.e_end[pent] + delta);
+            }
+            ++level;
+            const bool child_cached = (p == 0) || (pend - p >= T);
+            if (stopped) {
+                // values agree from here up; only small ancestors cached in the child need them
+                if (pent >= 0 || (int32_t)k > hneed) break;
+            }
+            const uint32_t op = ok_[p];
+            const bool left = (q == p + 1);
+            const uint32_t ss = left ? qend : p + 1;
+            const uint32_t se = left ? pend : q;
+            if (se <= ss || se > nk) { if (lane == 0) set_error(d, ST_STRUCT, 6, i, p, (se << 0)); break; }
+            float sv[K];
+            if (se - ss >= T) {
+                const int32_t sib = left ? par.e_c1[pent] : par.e_c0[pent];
+                if (pent < 0 || sib < 0) { if (lane == 0) set_error(d, ST_STRUCT, 7, i, p, se - ss); done = true; break; }
+                load_vec<K>(par.slots, d.Cpad, par.e_slot[sib], sv);
+            } else {
+                eval_run<K>(ok_, ss, se, stA, ic, sv, d.status);
+                st_interp += se - ss;
+            }
+            combine<K>(op, left, ov, sv);            // mother's value at p (exact recomputation)
+            if (!stopped) {
+                combine<K>(op, left, nv, sv);
+                if (pent >= 0) load_vec<K>(par.slots, d.Cpad, par.e_slot[pent], ov);
+                ++levels;
+                ++st_pathops;
+                if (same_bits<K>(nv, ov, Cn)) { stopped = true; stop_level = (int32_t)level; }
+            }
+            // record the child's value here when the child caches this node and the mother's
+            // cache cannot supply it (disrupted, or not cached in the mother)
+            if (child_cached && (!same_bits<K>(nv, ov, Cn) || pent < 0)) {
+                uint32_t slot = 0;
+                if (lane == 0) slot = atomicAdd(&g.misc[M_PV], 1u);
+                slot = __shfl_sync(FULL, slot, 0);
+                if (slot >= g.pvcap) { if (lane == 0) set_status(d.status, ST_PATH); done = true; break; }
+                float* dst = d.slots + (size_t)slot * d.Cpad + lane;
+                const float (&val)[K] = stopped ? ov : nv;
+#pragma unroll
+                for (int kk = 0; kk < K; ++kk) dst[kk * 32] = val[kk];
+                if (lane == 0) g.pv_rec[slot] = make_uint4(i, npv, p, slot);
+                ++npv;
+            }
+            q = p;
+            qend = pend;
+            qe = pent;
+            if (k >= nsmall) pe_ = par.e_par[pent];
+            ++k;
+            if (p == 0) break;
+        }
+        (void)qe;
+        // ---- fitness
+        if (lane == 0) { g.stop[i] = stop_level; g.plen[i] = levels; g.pv_cnt[i] = npv; }
+        if (stopped) {
+            if (lane == 0) d.fit[i] = g.pfit[m];
+            ++st_stopped;
+        } else {
+#pragma unroll
+            for (int kk = 0; kk < K; ++kk) red[kk * 32 + lane] = nv[kk];
+            __syncwarp();
+            if (lane == 0) {
+                float fsum = 0.0f;
+                for (uint32_t cc = 0; cc < Cn; ++cc) fsum = __fadd_rn(fsum, fabsf(__fsub_rn(red[cc], d.t[cc])));
+                d.fit[i] = fsum;
+            }
+            __syncwarp();
+        }
+        st_levels += levels;
+    }
+    if (lane == 0) {
+        atomicAdd(&g.gstat[G_INTERP], st_interp);
+        atomicAdd(&g.gstat[G_LEVELS], st_levels);
+        atomicAdd(&g.gstat[G_STOPPED], st_stopped);
+        atomicAdd(&g.gstat[G_PATHOPS], st_pathops);
+    }
+}
+
+// ------------------------------------------------------------------ A9 child cache
+
+// Walk records grouped per child in walk order (positions decreasing).
+__global__ void __launch_bounds__(1024) k_pv_offsets(DevPop d, GenBufs g) {
+    __shared__ uint64_t ws[32];
+    __shared__ uint64_t carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (uint32_t base = 0; base < d.P; base += blockDim.x) {
+        const uint32_t i = base + threadIdx.x;
+        const uint64_t v = (i < d.P) ? g.pv_cnt[i] : 0;
+        const uint64_t o = block_excl_scan(v, ws, &carry);
+        if (i < d.P) g.pv_off[i] = (uint32_t)o;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) g.pv_off[d.P] = (uint32_t)carry;
+}
+
+__global__ void k_pv_scatter(DevPop d, GenBufs g) {
+    const uint32_t n = min(g.misc[M_PV], g.pvcap);
+    for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+        const uint4 rec = g.pv_rec[r];
+        g.pv_sorted[g.pv_off[rec.x] + rec.y] = make_uint2(rec.z, rec.w);
+    }
+}
+
+// Value of every cached node of every child: from the walk's record when
+// the walk computed it, else from the parent whose subtree holds the same
+// bytes -- the mother for nodes outside the exchanged subtree (positions
+// after it shifted by the size change), the father inside it.
+__global__ void k_fill_child_cache(DevPop d, GenBufs g, CacheView par) {
+    const uint32_t ne = d.e_off[d.P];
+    if (ne > d.Ecap) return;
+    for (uint32_t x = blockIdx.x * blockDim.x + threadIdx.x; x < ne; x += gridDim.x * blockDim.x) {
+        const uint32_t i = d.e_tree[x];
+        const uint32_t pos = d.e_pos[x], end = d.e_end[x];
+        const uint32_t fl = g.flags[i];
+        const uint32_t m = g.mother[i];
+        const uint32_t c = g.cpos[i], r = g.rsz[i], s = g.ssz[i];
+        int32_t src = -1;
+        const bool anc = !(fl & F_CLONE) && ((pos < c && end > c) || (pos == c && s < d.T));
+        if (anc) {
+            // ancestor of the crossover point (or the donated root become the child's root):
+            // the walk's value when it made one
+            uint32_t lo = g.pv_off[i], hi = g.pv_off[i + 1];
+            int32_t hit = -1;
+            while (lo < hi) {                         // positions decrease along the record list
+                const uint32_t mid = (lo + hi) >> 1;
+                const uint32_t pp = g.pv_sorted[mid].x;
+                if (pp == pos) { hit = (int32_t)mid; break; }
+                if (pp > pos) lo = mid + 1; else hi = mid;
+            }
+            if (hit >= 0) { d.e_slot[x] = g.pv_sorted[hit].y; continue; }
+            if (pos < c) src = find_exact(par.e_pos, par.e_off[m], par.e_off[m + 1], pos);
+            else {
+                const uint32_t f = g.father[i];            // whole donated tree become the root
+                src = find_exact(par.e_pos, par.e_off[f], par.e_off[f + 1], g.dpos[i]);
+            }
+        } else if (fl & F_CLONE) src = find_exact(par.e_pos, par.e_off[m], par.e_off[m + 1], pos);
+        else if (pos >= c + s) src = find_exact(par.e_pos, par.e_off[m], par.e_off[m + 1], pos - s + r);
+        else if (pos >= c) {
+            const uint32_t f = g.father[i];
+            src = find_exact(par.e_pos, par.e_off[f], par.e_off[f + 1], pos - c + g.dpos[i]);
+        } else src = find_exact(par.e_pos, par.e_off[m], par.e_off[m + 1], pos);
+        const uint32_t slot = g.pvcap + x;
+        d.e_slot[x] = slot;
+        if (src < 0) { set_error(d, ST_STRUCT, 8 + (anc ? 1 : 0), i, pos, end); continue; }
+        const float4* sp = reinterpret_cast<const float4*>(par.slots + (size_t)par.e_slot[src] * d.Cpad);
+        float4* dp = reinterpret_cast<float4*>(d.slots + (size_t)slot * d.Cpad);
+        for (uint32_t k = 0; k < d.Cpad / 4; ++k) dp[k] = __ldcg(sp + k);
+    }
+}
+
+// equivalent-op count of the children (every opcode on every case)
+__global__ void k_child_sizes(DevPop d, GenBufs g) {
+    unsigned long long s = 0;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < d.P; i += gridDim.x * blockDim.x) s += d.size[i];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(FULL, s, o);
+    if ((threadIdx.x & 31) == 0 && s) atomicAdd(&g.gstat[G_EQUIV], s);
+}
+
+__global__ void k_order_identity(DevPop d, GenBufs g) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < d.P; i += gridDim.x * blockDim.x) g.order[i] = i;
+}

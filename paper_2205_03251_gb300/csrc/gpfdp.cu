@@ -7,6 +7,7 @@
 #include <cstring>
 #include <string>
 #include <type_traits>
+#include <utility>
 #include <vector>
 
 #include "common.cuh"
@@ -23,6 +24,22 @@ enum Phase { PH_STRUCT = 0, PH_ITEMS, PH_SKEL, PH_FIT, PH_XO, PH_WALK, PH_CACHE,
 constexpr int NREC = 128;   // event pairs kept per phase: stats average the last NREC calls
 
 }  // namespace
+
+// One cache (entries sorted by position per tree, plus value slots).  Two
+// exist: during a generation the parents' set is read while the children's
+// set is built.
+struct CacheSet {
+    uint32_t *e_cnt = nullptr, *e_off = nullptr, *e_pos = nullptr, *e_end = nullptr, *e_slot = nullptr;
+    uint32_t *order = nullptr, *e_tree = nullptr, *e_cmax = nullptr;
+    int32_t *e_par = nullptr, *e_c0 = nullptr, *e_c1 = nullptr, *e_bal = nullptr;
+    uint4 *it_desc = nullptr, *sk_desc = nullptr;
+    float* slots = nullptr;
+    uint32_t Ecap = 0, Scap = 0;
+    std::vector<void*> allocs;
+};
+
+int gen_crossover(gp_pop* pop, uint32_t generation);
+int gen_incremental(gp_pop* pop);
 
 struct gp_pop {
     gp_config cfg;
@@ -47,9 +64,14 @@ struct gp_pop {
     uint64_t stage_cap;
     std::vector<uint64_t> host_off;   // pageable copies kept alive until the next upload
     std::vector<uint32_t> host_buf;
+    std::vector<uint32_t> host_free;
     uint64_t slot_limit;              // value vectors the cache budget allows
-    std::vector<void*> cache_allocs;  // entry arrays and slots (regrown on demand)
+    CacheSet sets[2];
+    int cur;                          // set of the current population
     uint32_t* e_total_h;              // pinned host copy of the entry count
+    int grid_walk;
+    size_t smem_walk;
+    int last_kind;                    // 0 full evaluation, 1 generation
 };
 
 namespace {
@@ -105,14 +127,19 @@ int check_status(gp_pop* pop) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(pop->stream);
     if (e != cudaSuccess) return fail(pop, GP_ECUDA, "device error: %s", cudaGetErrorString(e));
     if (!st) return GP_OK;
+    uint32_t ei[4] = {0, 0, 0, 0};
+    cudaMemcpy(ei, pop->d.errinfo, sizeof ei, cudaMemcpyDeviceToHost);
     cudaMemsetAsync(pop->d.status, 0, sizeof(uint32_t), pop->stream);
+    cudaMemsetAsync(pop->d.errinfo, 0, sizeof ei, pop->stream);
+    char where[128] = "";
+    if (ei[0]) snprintf(where, sizeof where, " [site %u, individual %u, position %u, detail %u]", ei[0], ei[1], ei[2], ei[3]);
     if (st & ST_ENTRIES) return fail(pop, GP_ENOMEM, "cache entry capacity (%u) exceeded", pop->d.Ecap);
     if (st & ST_SLOTS) return fail(pop, GP_ENOMEM, "cache value budget (%u slots) exceeded", pop->d.Scap);
     if (st & ST_CAPACITY) return fail(pop, GP_ECAPACITY, "a child exceeded max_nodes");
     if (st & ST_TIMEOUT) return fail(pop, GP_ETIMEOUT, "a bounded device wait gave up");
     if (st & ST_STACK) return fail(pop, GP_EINVAL, "interpreter stack bound exceeded (malformed tree?)");
     if (st & ST_PATH) return fail(pop, GP_ENOMEM, "incremental path scratch exceeded");
-    return fail(pop, GP_EINVAL, "structure pass inconsistent (status 0x%x)", st);
+    return fail(pop, GP_EINVAL, "tree structure inconsistent (status 0x%x)%s", st, where);
 }
 
 // Validate one tree on the host: a complete prefix expression of exactly n
@@ -173,6 +200,20 @@ int setup_items_kernel(gp_pop* pop) {
 }
 
 template <int K>
+int setup_walk_kernel(gp_pop* pop) {
+    size_t smem = WalkSmem<K>::total((int)pop->d.W, GP_WARPS);
+    CK(cudaFuncSetAttribute(k_walk<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int nb = 0;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_walk<K>, GP_WARPS * 32, smem));
+    if (nb < 1) nb = 1;
+    // the walk shares the interpreter's per-warp overflow stacks
+    pop->grid_walk = nb * pop->nsm;
+    if (pop->grid_walk > pop->grid_items) pop->grid_walk = pop->grid_items;
+    pop->smem_walk = smem;
+    return GP_OK;
+}
+
+template <int K>
 void launch_items(gp_pop* pop) {
     k_eval_items<K><<<pop->grid_items, GP_WARPS * 32, pop->smem_items, pop->stream>>>(pop->d);
 }
@@ -185,43 +226,62 @@ void launch_by_k(gp_pop* pop, void (*f1)(gp_pop*), void (*f2)(gp_pop*), void (*f
     if (pop->d.K == 1) f1(pop); else if (pop->d.K == 2) f2(pop); else f4(pop);
 }
 
-// (Re)allocate the cache-entry arrays for ecap entries and the value
-// slots for as many vectors (full evaluation gives entry e slot e).
-int grow_cache(gp_pop* pop, uint32_t ecap) {
+// Point the kernels' view (DevPop, StructBufs) at the current cache set.
+void bind_set(gp_pop* pop) {
     DevPop& d = pop->d;
-    StructBufs& sb = pop->sb;
-    if ((uint64_t)ecap > pop->slot_limit)
-        return fail(pop, GP_ENOMEM, "cache needs %u value vectors, budget allows %llu", ecap,
-                    (unsigned long long)pop->slot_limit);
+    CacheSet& c = pop->sets[pop->cur];
+    d.e_cnt = c.e_cnt; d.e_off = c.e_off; d.e_pos = c.e_pos; d.e_end = c.e_end; d.e_par = c.e_par;
+    d.e_c0 = c.e_c0; d.e_c1 = c.e_c1; d.e_slot = c.e_slot; d.e_tree = c.e_tree; d.it_desc = c.it_desc;
+    d.sk_desc = c.sk_desc; d.order = c.order; d.slots = c.slots; d.Ecap = c.Ecap; d.Scap = c.Scap;
+    pop->sb.e_bal = c.e_bal; pop->sb.e_tree = c.e_tree; pop->sb.e_cmax = c.e_cmax;
+}
+
+CacheView view_of(const CacheSet& c) {
+    CacheView v;
+    v.e_off = c.e_off; v.e_pos = c.e_pos; v.e_end = c.e_end; v.e_par = c.e_par;
+    v.e_c0 = c.e_c0; v.e_c1 = c.e_c1; v.e_slot = c.e_slot; v.slots = c.slots;
+    return v;
+}
+
+// (Re)allocate cache set `which` for ecap entries.  Slots: the walk's
+// records first (pvcap), then one per entry.
+int grow_set(gp_pop* pop, int which, uint32_t ecap) {
+    CacheSet& c = pop->sets[which];
+    const DevPop& d = pop->d;
+    const uint64_t scap = (uint64_t)pop->gb.pvcap + ecap;
+    if (scap > pop->slot_limit)
+        return fail(pop, GP_ENOMEM, "cache needs %llu value vectors, budget allows %llu",
+                    (unsigned long long)scap, (unsigned long long)pop->slot_limit);
     if (pop->stream) cudaStreamSynchronize(pop->stream); else cudaDeviceSynchronize();
-    for (void* p : pop->cache_allocs) cudaFree(p);
-    pop->cache_allocs.clear();
+    for (void* p : c.allocs) cudaFree(p);
+    c.allocs.clear();
     auto al = [&](auto** ptr, size_t count) -> bool {
         void* p = nullptr;
         size_t bytes = count * sizeof(**ptr);
         if (cudaMalloc(&p, bytes ? bytes : 16) != cudaSuccess) { cudaGetLastError(); return false; }
-        pop->cache_allocs.push_back(p);
+        c.allocs.push_back(p);
         *ptr = static_cast<std::remove_reference_t<decltype(*ptr)>>(p);
         return true;
     };
-    bool ok = al(&d.e_pos, ecap) && al(&d.e_end, ecap) && al(&d.e_par, ecap) && al(&d.e_c0, ecap) &&
-              al(&d.e_c1, ecap) && al(&d.e_slot, ecap) && al(&d.it_desc, ecap) && al(&d.sk_desc, ecap) &&
-              al(&d.order, ecap) && al(&sb.e_bal, ecap) && al(&sb.e_tree, ecap) && al(&sb.e_cmax, ecap / 32 + 2) &&
-              al(&d.slots, (size_t)ecap * d.Cpad);
+    bool ok = al(&c.e_cnt, d.P + 1) && al(&c.e_off, d.P + 1) && al(&c.e_pos, ecap) && al(&c.e_end, ecap) &&
+              al(&c.e_par, ecap) && al(&c.e_c0, ecap) && al(&c.e_c1, ecap) && al(&c.e_slot, ecap) &&
+              al(&c.it_desc, ecap) && al(&c.sk_desc, ecap) && al(&c.order, ecap) && al(&c.e_bal, ecap) &&
+              al(&c.e_tree, ecap) && al(&c.e_cmax, ecap / 32 + 2) && al(&c.slots, (size_t)scap * d.Cpad);
     if (!ok) return fail(pop, GP_ENOMEM, "allocation of a cache of %u entries failed", ecap);
-    d.Ecap = ecap;
-    d.Scap = ecap;
+    cudaMemset(c.e_off, 0, sizeof(uint32_t) * (d.P + 1));
+    c.Ecap = ecap;
+    c.Scap = (uint32_t)scap;
+    if (which == pop->cur) bind_set(pop);
     return GP_OK;
 }
 
-// Structure pass + full evaluation of the current population.
-int run_full(gp_pop* pop) {
+int grow_cache(gp_pop* pop, uint32_t ecap) { return grow_set(pop, pop->cur, ecap); }
+
+// Structure pass of the current population into the current cache set:
+// cached nodes with ends, parents and links (grows the set if needed).
+int run_structure(gp_pop* pop) {
     DevPop& d = pop->d;
     const int gthreads = pop->grid_threads;
-    CK(cudaMemsetAsync(d.q, 0, sizeof(uint32_t) * NQ, pop->stream));
-    CK(cudaMemsetAsync(d.acc_ops, 0, 4 * sizeof(unsigned long long), pop->stream));
-    pop->launches = 15;
-    phase_begin(pop, PH_STRUCT);
     k_blk_offsets<<<1, 1024, 0, pop->stream>>>(d);
     k_unit_flags<<<pop->nsm * 16, FLAG_WARPS * 32, 0, pop->stream>>>(d, pop->sb);
     const int scan_grid = pop->nsm * 2;
@@ -233,7 +293,7 @@ int run_full(gp_pop* pop) {
     CK(cudaStreamSynchronize(pop->stream));
     if (*pop->e_total_h > d.Ecap) {
         uint64_t want = (uint64_t)*pop->e_total_h + *pop->e_total_h / 4 + 64;
-        if (want > pop->slot_limit) want = pop->slot_limit;
+        if (want + pop->gb.pvcap > pop->slot_limit) want = pop->slot_limit - pop->gb.pvcap;
         int r = grow_cache(pop, (uint32_t)want);
         if (r) return r;
     }
@@ -243,6 +303,22 @@ int run_full(gp_pop* pop) {
     k_entry_chunkmax<<<pop->grid_warps, GP_WARPS * 32, 0, pop->stream>>>(d, pop->sb);
     k_entry_parents<<<gthreads, 256, 0, pop->stream>>>(d, pop->sb);
     k_entry_links<<<gthreads, 256, 0, pop->stream>>>(d, pop->sb);
+    return GP_OK;
+}
+
+// Structure pass + full evaluation of the current population.
+int run_full(gp_pop* pop) {
+    DevPop& d = pop->d;
+    const int gthreads = pop->grid_threads;
+    CK(cudaMemsetAsync(d.q, 0, sizeof(uint32_t) * NQ, pop->stream));
+    CK(cudaMemsetAsync(d.acc_ops, 0, 4 * sizeof(unsigned long long), pop->stream));
+    pop->launches = 15;
+    pop->last_kind = 0;
+    phase_begin(pop, PH_STRUCT);
+    {
+        int r = run_structure(pop);
+        if (r) return r;
+    }
     k_build_items<<<gthreads, 256, 0, pop->stream>>>(d, pop->sb.e_tree);
     phase_end(pop, PH_STRUCT);
     phase_begin(pop, PH_ITEMS);
@@ -304,6 +380,7 @@ int gp_pop_create(const gp_config* cfg_in, const float* x, const float* targets,
     pop->stage_cap = 0;
     pop->launches = 0;
     pop->e_total_h = nullptr;
+    pop->last_kind = 0;
     memset(&pop->stats, 0, sizeof pop->stats);
     memset(pop->ev_count, 0, sizeof pop->ev_count);
     int rc = GP_OK;
@@ -343,7 +420,7 @@ int gp_pop_create(const gp_config* cfg_in, const float* x, const float* targets,
     pop->grid_threads = pop->nsm * 8;
 
 #define DA2(ptr, n) do { int r_ = dalloc(pop, &(ptr), (size_t)(n)); if (r_) return bail(r_); } while (0)
-    DA2(d.arena, (size_t)nbuf * d.cap);
+    DA2(d.arena, (size_t)nbuf * d.cap + 4096);     // slack: scans and 16-byte copies may read past the last buffer
     DA2(d.buf, P);
     DA2(d.size, P);
     DA2(d.x, d.Cpad);
@@ -351,13 +428,15 @@ int gp_pop_create(const gp_config* cfg_in, const float* x, const float* targets,
     DA2(d.consts, 256);
     DA2(d.fit, P);
     DA2(d.blk_off, P + 1);
-    DA2(d.e_cnt, P);
-    DA2(d.e_off, P + 1);
-    {
-        int r = grow_cache(pop, (uint32_t)ecap);
+    pop->gb.pvcap = P * PV_PER_CHILD;
+    pop->cur = 0;
+    for (int w = 1; w >= 0; --w) {
+        int r = grow_set(pop, w, (uint32_t)ecap);
         if (r) { g_create_error = pop->err; return bail(r); }
     }
     DA2(d.status, 4);
+    DA2(d.errinfo, 4);
+    cudaMemset(d.errinfo, 0, 4 * sizeof(uint32_t));
     DA2(d.e_total, 4);
     if (cudaMallocHost(&pop->e_total_h, sizeof(uint32_t)) != cudaSuccess) { g_create_error = "cudaMallocHost failed"; return bail(GP_ENOMEM); }
     DA2(d.q, NQ);
@@ -382,14 +461,38 @@ int gp_pop_create(const gp_config* cfg_in, const float* x, const float* targets,
         d.ovf_warps = (uint32_t)pop->grid_items * GP_WARPS;
         DA2(d.ovf, (size_t)d.ovf_warps * (d.maxdepth - d.W) * 32 * K);
     }
-    rc = gen_alloc(pop->gb, d, [&](void** p, size_t bytes) {
-        void* q = nullptr;
-        if (cudaMalloc(&q, bytes ? bytes : 16) != cudaSuccess) { cudaGetLastError(); return false; }
-        pop->allocs.push_back(q);
-        *p = q;
-        return true;
-    });
-    if (rc) { fail(pop, GP_ENOMEM, "allocation of generation buffers failed"); g_create_error = pop->err; return bail(GP_ENOMEM); }
+    // generation buffers
+    {
+        GenBufs& g = pop->gb;
+        g.max_nodes = cfg.max_nodes;
+        g.tsize = cfg.tournament;
+        g.seed = cfg.seed;
+        g.gen = 0;
+        g.evaluated = false;
+        g.frag_cap = (uint64_t)P * d.cap;
+        g.stash_cap = (uint64_t)P * (T + 16);
+        g.shift_cap = (uint32_t)((uint64_t)P * d.cap / SHIFT_BS + P);
+        DA2(g.pbuf, P); DA2(g.psize, P); DA2(g.pfit, P);
+        DA2(g.mother, P); DA2(g.father, P); DA2(g.cpos, P); DA2(g.rsz, P); DA2(g.dpos, P); DA2(g.ssz, P);
+        DA2(g.flags, P); DA2(g.lastidx, P); DA2(g.free_buf, P); DA2(g.free_next, P); DA2(g.hasip, P);
+        DA2(g.misc, NMISC);
+        DA2(g.frag_off, P + 1); DA2(g.frag, g.frag_cap + 64);
+        DA2(g.stash_off, P + 1); DA2(g.stash, g.stash_cap + 64);
+        DA2(g.shift_off, P + 1); DA2(g.halo, (size_t)g.shift_cap * HALO_MAX);
+        DA2(g.stop, P); DA2(g.plen, P);
+        DA2(g.pv_rec, g.pvcap); DA2(g.pv_cnt, P); DA2(g.pv_off, P + 1); DA2(g.pv_sorted, g.pvcap);
+        DA2(g.order, P); DA2(g.gstat, NGSTAT);
+        std::vector<uint32_t> fb(P);
+        for (uint32_t i = 0; i < P; ++i) fb[i] = P + i;          // buffers P..2P-1 start free
+        if (cudaMemcpy(g.free_buf, fb.data(), sizeof(uint32_t) * P, cudaMemcpyHostToDevice) != cudaSuccess)
+            return bail(GP_ECUDA);
+        cudaMemset(g.gstat, 0, sizeof(unsigned long long) * NGSTAT);
+    }
+    // incremental walk launch shape
+    {
+        int r = (K == 1) ? setup_walk_kernel<1>(pop) : (K == 2) ? setup_walk_kernel<2>(pop) : setup_walk_kernel<4>(pop);
+        if (r) return bail(r);
+    }
 
     // inputs
     std::vector<float> xp(d.Cpad, 0.0f);
@@ -427,7 +530,7 @@ void gp_pop_destroy(gp_pop* pop) {
     if (!pop) return;
     if (pop->stream) cudaStreamSynchronize(pop->stream); else cudaDeviceSynchronize();
     for (void* p : pop->allocs) cudaFree(p);
-    for (void* p : pop->cache_allocs) cudaFree(p);
+    for (int w = 0; w < 2; ++w) for (void* p : pop->sets[w].allocs) cudaFree(p);
     if (pop->e_total_h) cudaFreeHost(pop->e_total_h);
     if (pop->stage) cudaFree(pop->stage);
     if (pop->stage_off) cudaFree(pop->stage_off);
@@ -460,7 +563,13 @@ int gp_load_trees(gp_pop* pop, const uint8_t* ops, const uint64_t* offsets) {
     CK(cudaMemcpyAsync(pop->d.buf, pop->host_buf.data(), sizeof(uint32_t) * P, cudaMemcpyHostToDevice, pop->stream));
     k_scatter_trees<<<(P < 4096 ? P : 4096), 256, 0, pop->stream>>>(pop->stage, pop->stage_off, pop->d);
     CK(cudaGetLastError());
+    if (pop->host_free.size() != P) {
+        pop->host_free.resize(P);
+        for (uint32_t i = 0; i < P; ++i) pop->host_free[i] = P + i;
+    }
+    CK(cudaMemcpyAsync(pop->gb.free_buf, pop->host_free.data(), sizeof(uint32_t) * P, cudaMemcpyHostToDevice, pop->stream));
     pop->have_children = false;
+    pop->gb.evaluated = false;
     return GP_OK;
 }
 
@@ -476,7 +585,7 @@ int gp_eval_full(gp_pop* pop) {
     int rc = run_full(pop);
     if (rc) return rc;
     pop->have_children = false;
-    gen_mark_evaluated(pop->gb);
+    pop->gb.evaluated = true;
     return GP_OK;
 }
 
@@ -571,6 +680,17 @@ int gp_cache_value(const gp_pop* cpop, uint32_t i, uint32_t j, void* host_out, s
     return GP_OK;
 }
 
+int gp_walk_info(const gp_pop* cpop, int32_t* stop_level, uint32_t* levels, uint32_t n) {
+    gp_pop* pop = const_cast<gp_pop*>(cpop);
+    if (!pop || n > pop->d.P) return GP_EINVAL;
+    if (pop->last_kind != 1) return fail(pop, GP_ESTATE, "no incremental evaluation has run");
+    int rc = check_status(pop);
+    if (rc) return rc;
+    if (stop_level) CK(cudaMemcpy(stop_level, pop->gb.stop, sizeof(int32_t) * n, cudaMemcpyDeviceToHost));
+    if (levels) CK(cudaMemcpy(levels, pop->gb.plen, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost));
+    return GP_OK;
+}
+
 int gp_get_stats(const gp_pop* cpop, gp_stats* out) {
     gp_pop* pop = const_cast<gp_pop*>(cpop);
     if (!pop || !out) return GP_EINVAL;
@@ -590,25 +710,116 @@ int gp_get_stats(const gp_pop* cpop, gp_stats* out) {
         s.ms[i] = got ? (float)(tot / got) : 0.f;     // mean over the recorded calls
     }
     uint32_t ne = 0;
-    unsigned long long acc[4];
     CK(cudaMemcpy(&ne, pop->d.e_off + pop->d.P, sizeof ne, cudaMemcpyDeviceToHost));
-    CK(cudaMemcpy(acc, pop->d.acc_ops, sizeof acc, cudaMemcpyDeviceToHost));
     s.cache_entries = ne;
-    s.actual_ops = acc[0] * pop->d.C;
-    s.equivalent_ops = acc[1] * pop->d.C;
-    s.interp_ops = acc[2] * pop->d.C;
     s.launches = pop->launches;
+    if (pop->last_kind == 0) {
+        unsigned long long acc[4];
+        CK(cudaMemcpy(acc, pop->d.acc_ops, sizeof acc, cudaMemcpyDeviceToHost));
+        s.actual_ops = acc[0] * pop->d.C;
+        s.equivalent_ops = acc[1] * pop->d.C;
+        s.interp_ops = acc[2] * pop->d.C;
+        s.children = 0;
+    } else {
+        unsigned long long gs[NGSTAT];
+        CK(cudaMemcpy(gs, pop->gb.gstat, sizeof gs, cudaMemcpyDeviceToHost));
+        s.equivalent_ops = gs[G_EQUIV] * pop->d.C;
+        s.interp_ops = gs[G_INTERP] * pop->d.C;
+        s.actual_ops = (gs[G_INTERP] + gs[G_PATHOPS]) * pop->d.C;
+        s.crossover_bytes = gs[G_XOBYTES];
+        s.path_levels = gs[G_LEVELS];
+        s.stopped = (uint32_t)gs[G_STOPPED];
+        s.children = pop->d.P;
+    }
     *out = s;
     return GP_OK;
 }
 
 }  // extern "C"
 
-int gen_crossover(gp_pop* pop, uint32_t generation) {
-    (void)generation;
-    return fail(pop, GP_ESTATE, "crossover is not available in this build");
+namespace {
+
+void swap_generation(gp_pop* pop) {
+    DevPop& d = pop->d;
+    GenBufs& g = pop->gb;
+    std::swap(d.buf, g.pbuf);
+    std::swap(d.size, g.psize);
+    std::swap(d.fit, g.pfit);
 }
 
+template <int K>
+void launch_walk(gp_pop* pop, const CacheView& par) {
+    k_walk<K><<<pop->grid_walk, GP_WARPS * 32, pop->smem_walk, pop->stream>>>(pop->d, pop->gb, par);
+}
+
+}  // namespace
+
+// Selection, crossover plan, fragment gather and materialisation of the
+// children (copy, or in place for the last child of a mother).  The
+// parents' trees stay addressable through the retained buffer indices until
+// their buffers are overwritten; their cache set is kept for the walk.
+int gen_crossover(gp_pop* pop, uint32_t generation) {
+    DevPop& d = pop->d;
+    GenBufs& g = pop->gb;
+    if (!g.evaluated) return fail(pop, GP_ESTATE, "gp_crossover needs an evaluated population (gp_eval_full or gp_eval_incremental first)");
+    if (pop->have_children) return fail(pop, GP_ESTATE, "children of the last crossover are not evaluated yet");
+    g.gen = generation;
+    swap_generation(pop);
+    const CacheView par = view_of(pop->sets[pop->cur]);
+    pop->cur ^= 1;
+    bind_set(pop);
+    const int gt = pop->grid_threads;
+    phase_begin(pop, PH_XO);
+    CK(cudaMemsetAsync(g.lastidx, 0xFF, sizeof(int32_t) * d.P, pop->stream));
+    CK(cudaMemsetAsync(g.misc, 0, sizeof(uint32_t) * NMISC, pop->stream));
+    CK(cudaMemsetAsync(g.gstat, 0, sizeof(unsigned long long) * NGSTAT, pop->stream));
+    k_plan<<<(d.P + 255) / 256, 256, 0, pop->stream>>>(d, g, par);
+    k_assign<<<1, 1024, 0, pop->stream>>>(d, g);
+    k_gather<<<pop->nsm * 4, 256, 0, pop->stream>>>(d, g);
+    k_copy_children<<<pop->nsm * 4, 256, 0, pop->stream>>>(d, g);
+    k_save_halo<<<gt, 256, 0, pop->stream>>>(d, g);
+    k_shift<<<pop->nsm * 8, 256, 0, pop->stream>>>(d, g);
+    k_write_frags<<<pop->nsm * 4, 256, 0, pop->stream>>>(d, g);
+    phase_end(pop, PH_XO);
+    CK(cudaGetLastError());
+    pop->have_children = true;
+    g.evaluated = false;
+    pop->launches = 7;
+    return GP_OK;
+}
+
+// Children's cache structure, the incremental walk, then the children's
+// cache values.
 int gen_incremental(gp_pop* pop) {
-    return fail(pop, GP_ESTATE, "incremental evaluation is not available in this build");
+    DevPop& d = pop->d;
+    GenBufs& g = pop->gb;
+    if (!pop->have_children) return fail(pop, GP_ESTATE, "gp_eval_incremental needs the children of a gp_crossover");
+    if (d.ncb != 1) return fail(pop, GP_EINVAL, "incremental evaluation supports up to %u test cases (32 x cases_per_lane)", 32 * d.K);
+    const CacheView par = view_of(pop->sets[pop->cur ^ 1]);
+    const int gt = pop->grid_threads;
+    CK(cudaMemsetAsync(d.q, 0, sizeof(uint32_t) * NQ, pop->stream));
+    phase_begin(pop, PH_STRUCT);
+    {
+        int r = run_structure(pop);
+        if (r) return r;
+    }
+    phase_end(pop, PH_STRUCT);
+    phase_begin(pop, PH_PACK);
+    k_order_identity<<<(d.P + 255) / 256, 256, 0, pop->stream>>>(d, g);
+    phase_end(pop, PH_PACK);
+    phase_begin(pop, PH_WALK);
+    if (d.K == 1) launch_walk<1>(pop, par); else if (d.K == 2) launch_walk<2>(pop, par); else launch_walk<4>(pop, par);
+    phase_end(pop, PH_WALK);
+    phase_begin(pop, PH_CACHE);
+    k_pv_offsets<<<1, 1024, 0, pop->stream>>>(d, g);
+    k_pv_scatter<<<gt, 256, 0, pop->stream>>>(d, g);
+    k_fill_child_cache<<<gt, 256, 0, pop->stream>>>(d, g, par);
+    k_child_sizes<<<(d.P + 255) / 256, 256, 0, pop->stream>>>(d, g);
+    phase_end(pop, PH_CACHE);
+    CK(cudaGetLastError());
+    pop->launches += 11 + 6;
+    pop->have_children = false;
+    g.evaluated = true;
+    pop->last_kind = 1;
+    return GP_OK;
 }

@@ -36,7 +36,7 @@ struct StructBufs {
     uint32_t* tile_c;    // scan tiles
     int64_t* tile_b;
     int32_t* e_bal;      // [Ecap] balance before the entry's node (within its tree)
-    uint32_t* e_tree;    // [Ecap]
+    uint32_t* e_tree;    // [Ecap] (same array as DevPop::e_tree)
     uint32_t* e_cmax;    // [Ecap/32+1] max end per 32-entry chunk
     uint32_t Ucap;
 };
@@ -399,7 +399,7 @@ __global__ void k_entry_ends(DevPop d, StructBufs sb) {
             }
         }
         // a well-formed tree closes exactly at its last node
-        if (endpos == 0xFFFFFFFFu || endpos > n || (pos == 0 && endpos != n)) { set_status(d.status, ST_STRUCT); endpos = n; }
+        if (endpos == 0xFFFFFFFFu || endpos > n || (pos == 0 && endpos != n)) { set_error(d, ST_STRUCT, 1, tree, pos, endpos); endpos = n; }
         d.e_end[e] = endpos;
     }
 }
@@ -444,7 +444,7 @@ __global__ void k_entry_parents(DevPop d, StructBufs sb) {
                         if (d.e_end[q] >= ee) { par = (int32_t)q; break; }
                 }
             }
-            if (par < 0) set_status(d.status, ST_STRUCT);
+            if (par < 0) set_error(d, ST_STRUCT, 2, tree, d.e_pos[e], e - e0);
         }
         d.e_par[e] = par;
     }

@@ -1,0 +1,169 @@
+"""Parity of the CUDA generation loop with the CPU oracle: the children
+(trees, bit for bit), their fitness (incremental evaluation must equal full
+evaluation of the spliced child), the failed-disruption-propagation stop
+levels, and the children's cache (positions and values)."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gp():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need cuda:0"
+    import paper_2205_03251_gb300 as gp
+    gp.build()
+    gp.load()
+    return gp
+
+
+def _expected_entries(tree, T):
+    import oracle
+    ends = oracle.tree_ends(tree).astype(np.int64)
+    size = ends - np.arange(len(tree))
+    pos = np.nonzero(size >= T)[0]
+    if len(pos) == 0 or pos[0] != 0:
+        pos = np.concatenate([[0], pos])
+    return pos, ends[pos]
+
+
+def run_generations(gp, w, *, T, gens, max_nodes, seed=1234, cache_check=8, stop_check=True,
+                    cases_per_lane=0):
+    import oracle
+    ops, off = w["ops"], w["off"]
+    k, x, t = w["consts"], w["x"], w["t"]
+    P = len(off) - 1
+    pop = gp.Population(x, t, k, ops, off, max_nodes=max_nodes, cache_threshold=T, seed=seed,
+                        cases_per_lane=cases_per_lane)
+    pop.eval_full()
+    fit = pop.fitness()
+    _, ofit = oracle.eval_pop_f32(ops, off, k, x, t)
+    assert np.array_equal(oracle.canon_nan(fit), oracle.canon_nan(ofit))
+    cur_ops, cur_off = ops, off
+    rng = np.random.default_rng(seed)
+    history = []
+    for g in range(gens):
+        pl = oracle.plan(cur_ops, cur_off, fit, T=7, seed=seed, gen=g, max_nodes=max_nodes)
+        kops, koff = oracle.breed(cur_ops, cur_off, pl)
+        pop.crossover(g)
+        # children, byte for byte (before and after their evaluation)
+        for i in range(P):
+            want = kops[int(koff[i]):int(koff[i + 1])]
+            got = pop.tree(i)
+            assert np.array_equal(got, want), f"gen {g}: child {i} differs after crossover"
+        st = pop.eval_incremental()
+        for i in range(P):
+            want = kops[int(koff[i]):int(koff[i + 1])]
+            got = pop.tree(i)
+            assert np.array_equal(got, want), f"gen {g}: child {i} differs"
+        # incremental fitness == full evaluation of the spliced child
+        _, kfit = oracle.eval_pop_f32(kops, koff, k, x, t)
+        gfit = pop.fitness()
+        bad = np.nonzero(oracle.canon_nan(gfit) != oracle.canon_nan(kfit))[0]
+        assert len(bad) == 0, f"gen {g}: fitness differs for children {bad[:10]}"
+        # stop levels of the failed-disruption-propagation walk
+        stop, lv = pop.walk_info()
+        if stop_check:
+            for i in range(P):
+                m = int(pl["mother"][i])
+                mom = cur_ops[int(cur_off[m]):int(cur_off[m + 1])]
+                kid = kops[int(koff[i]):int(koff[i + 1])]
+                ostop, depth = oracle.fdp_walk(mom, kid, int(pl["c"][i]), k, x)
+                assert stop[i] == ostop, f"gen {g}: child {i} stops at {stop[i]}, oracle {ostop}"
+        # children's cache: positions and sampled values
+        for i in rng.choice(P, size=min(P, cache_check), replace=False):
+            kid = kops[int(koff[i]):int(koff[i + 1])]
+            pos, end, par = pop.cache_entries(int(i))
+            epos, eend = _expected_entries(kid, T)
+            assert np.array_equal(pos, epos) and np.array_equal(end, eend), f"gen {g}: child {i} cache structure"
+            for j in np.unique(np.linspace(0, len(pos) - 1, min(len(pos), 5)).astype(int)):
+                want = oracle.eval_node_f32(kid, int(pos[j]), k, x)
+                assert np.array_equal(oracle.canon_nan(pop.cache_value(int(i), int(j))), oracle.canon_nan(want)), \
+                    f"gen {g}: child {i} cached value at {pos[j]}"
+        assert st.equivalent_ops == int(np.diff(koff).sum()) * len(x)
+        history.append((st.as_dict(), stop.copy()))
+        fit = gfit
+        cur_ops, cur_off = kops, koff
+    pop.close()
+    return history
+
+
+@pytest.mark.parametrize("T", [1024, 64, 8])
+def test_generations_rhh(gp, T):
+    import synth
+    w = synth.workload(0, n_trees=120)
+    run_generations(gp, w, T=T, gens=4, max_nodes=20000)
+
+
+def test_generations_small_cases_and_lanes(gp):
+    import synth
+    for C, K in ((1, 0), (32, 1), (33, 2), (100, 4)):
+        w = synth.workload(0, n_trees=60, n_cases=C)
+        run_generations(gp, w, T=32, gens=2, max_nodes=20000, cases_per_lane=K)
+
+
+def test_generations_tight_size_limit_makes_copies(gp):
+    import synth
+    w = synth.workload(0, n_trees=80)
+    maxn = int(np.diff(w["off"]).max())
+    hist = run_generations(gp, w, T=16, gens=3, max_nodes=maxn)
+    assert all(h[0]["children"] == 80 for h in hist)
+
+
+def test_generations_grafted_trees(gp):
+    import synth
+    ops, off = synth.population("big", synth.MASTER_SEED + 1, 24, target=60_000)
+    x, t = synth.cases(synth.MASTER_SEED + 1, 48)
+    w = {"ops": ops, "off": off, "x": x, "t": t, "consts": synth.consts(synth.MASTER_SEED + 1)}
+    hist = run_generations(gp, w, T=1024, gens=3, max_nodes=1 << 18, stop_check=True)
+    # failed disruption propagation stops most walks below the root
+    stopped = sum(int((h[1] >= 0).sum()) for h in hist)
+    assert stopped > 0
+
+
+def test_generations_tiny_trees(gp):
+    # single leaves, three-node trees and the threshold 2 (every function cached)
+    import synth
+    sizes = np.array([1, 1, 3, 3, 5, 7, 9, 15, 31, 63] * 4, np.uint64)
+    ops, off = synth.population("remy", 91, len(sizes), sizes=sizes)
+    x, t = synth.cases(91, 48)
+    w = {"ops": ops, "off": off, "x": x, "t": t, "consts": synth.consts(91)}
+    for T in (2, 4, 1024):
+        run_generations(gp, w, T=T, gens=3, max_nodes=4096)
+
+
+def test_full_size_generation_sampled(gp):
+    """500 trees of ~1e6 nodes: two generations; sampled children against
+    the oracle (tree bytes, fitness); statistics of the walk."""
+    import oracle
+    import synth
+    w = synth.workload(1)
+    ops, off, k, x, t = w["ops"], w["off"], w["consts"], w["x"], w["t"]
+    maxn = 1 << 21
+    pop = gp.Population(x, t, k, ops, off, max_nodes=maxn, cache_threshold=1024, seed=77)
+    pop.eval_full()
+    fit = pop.fitness()
+    cur_ops, cur_off = ops, off
+    for g in range(2):
+        pl = oracle.plan(cur_ops, cur_off, fit, T=7, seed=77, gen=g, max_nodes=maxn)
+        pop.crossover(g)
+        st = pop.eval_incremental()
+        gfit = pop.fitness()
+        stop, lv = pop.walk_info()
+        for i in (0, 123, 499):
+            m, f = int(pl["mother"][i]), int(pl["father"][i])
+            mom = cur_ops[int(cur_off[m]):int(cur_off[m + 1])]
+            dad = cur_ops[int(cur_off[f]):int(cur_off[f + 1])]
+            kid = oracle.splice(mom, int(pl["c"][i]), int(pl["r"][i]), dad, int(pl["d"][i]), int(pl["s"][i]))
+            assert np.array_equal(pop.tree(i), kid)
+            want = oracle.fitness_f32(oracle.eval_node_f32(kid, 0, k, x), t)
+            assert oracle.canon_nan(np.array([gfit[i]]))[0] == oracle.canon_nan(np.array([want]))[0]
+        assert st.equivalent_ops > 0 and st.actual_ops < st.equivalent_ops
+        # next generation's parents, as the oracle sees them: only the plan's inputs are needed
+        sizes = np.array([len(pop.tree(i)) for i in range(len(off) - 1)])
+        cur_ops = np.concatenate([pop.tree(i) for i in range(len(off) - 1)])
+        cur_off = np.zeros(len(sizes) + 1, np.uint64)
+        cur_off[1:] = np.cumsum(sizes)
+        fit = gfit
+    pop.close()
