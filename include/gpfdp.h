@@ -90,7 +90,10 @@ typedef struct {
     uint32_t stopped;           /* children whose walk stopped below the root (fitness inherited) */
     uint32_t children;          /* children evaluated */
     uint32_t launches;          /* kernels launched by the call */
-    uint32_t reserved;
+    uint32_t cum_calls;         /* evaluations since profiling was (re)enabled */
+    uint64_t cum_equivalent_ops;/* sums of the three counters above over those calls */
+    uint64_t cum_actual_ops;
+    uint64_t cum_crossover_bytes;
     float    ms[8];             /* per-phase device milliseconds when profiling is on, mean over
                                    the calls since profiling was (re)enabled (last 128 kept):
                                    structure, items, skeleton, fitness, crossover, walk, cache, pack */

@@ -40,8 +40,9 @@ class GpStats(ctypes.Structure):
                 ("interp_ops", ctypes.c_uint64), ("crossover_bytes", ctypes.c_uint64),
                 ("cache_entries", ctypes.c_uint64), ("path_levels", ctypes.c_uint64),
                 ("stopped", ctypes.c_uint32), ("children", ctypes.c_uint32),
-                ("launches", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
-                ("ms", ctypes.c_float * 8)]
+                ("launches", ctypes.c_uint32), ("cum_calls", ctypes.c_uint32),
+                ("cum_equivalent_ops", ctypes.c_uint64), ("cum_actual_ops", ctypes.c_uint64),
+                ("cum_crossover_bytes", ctypes.c_uint64), ("ms", ctypes.c_float * 8)]
 
     def as_dict(self) -> dict:
         d = {k: getattr(self, k) for k, _ in self._fields_ if k != "ms"}

@@ -69,6 +69,8 @@ struct gp_pop {
     CacheSet sets[2];
     int cur;                          // set of the current population
     uint32_t* e_total_h;              // pinned host copy of the entry count
+    unsigned long long* cum;          // device: equivalent, actual, crossover bytes, calls
+    uint32_t cum_calls;
     int grid_walk;
     size_t smem_walk;
     int last_kind;                    // 0 full evaluation, 1 generation
@@ -226,6 +228,20 @@ void launch_by_k(gp_pop* pop, void (*f1)(gp_pop*), void (*f2)(gp_pop*), void (*f
     if (pop->d.K == 1) f1(pop); else if (pop->d.K == 2) f2(pop); else f4(pop);
 }
 
+// Add the last evaluation's counters to the running totals (device side, no sync).
+__global__ void k_accumulate(unsigned long long* cum, const unsigned long long* acc, const unsigned long long* gst,
+                             uint32_t C, int kind) {
+    if (threadIdx.x != 0) return;
+    if (kind == 0) {
+        cum[0] += acc[1] * C;
+        cum[1] += acc[0] * C;
+    } else {
+        cum[0] += gst[G_EQUIV] * C;
+        cum[1] += (gst[G_INTERP] + gst[G_PATHOPS]) * C;
+        cum[2] += gst[G_XOBYTES];
+    }
+}
+
 // Point the kernels' view (DevPop, StructBufs) at the current cache set.
 void bind_set(gp_pop* pop) {
     DevPop& d = pop->d;
@@ -312,7 +328,7 @@ int run_full(gp_pop* pop) {
     const int gthreads = pop->grid_threads;
     CK(cudaMemsetAsync(d.q, 0, sizeof(uint32_t) * NQ, pop->stream));
     CK(cudaMemsetAsync(d.acc_ops, 0, 4 * sizeof(unsigned long long), pop->stream));
-    pop->launches = 15;
+    pop->launches = 16;
     pop->last_kind = 0;
     phase_begin(pop, PH_STRUCT);
     {
@@ -330,6 +346,8 @@ int run_full(gp_pop* pop) {
     phase_begin(pop, PH_FIT);
     k_fitness<<<pop->grid_warps, GP_WARPS * 32, 0, pop->stream>>>(d);
     phase_end(pop, PH_FIT);
+    k_accumulate<<<1, 32, 0, pop->stream>>>(pop->cum, d.acc_ops, pop->gb.gstat, d.C, 0);
+    ++pop->cum_calls;
     CK(cudaGetLastError());
     return GP_OK;
 }
@@ -435,6 +453,9 @@ int gp_pop_create(const gp_config* cfg_in, const float* x, const float* targets,
         if (r) { g_create_error = pop->err; return bail(r); }
     }
     DA2(d.status, 4);
+    DA2(pop->cum, 4);
+    cudaMemset(pop->cum, 0, 4 * sizeof(unsigned long long));
+    pop->cum_calls = 0;
     DA2(d.errinfo, 4);
     cudaMemset(d.errinfo, 0, 4 * sizeof(uint32_t));
     DA2(d.e_total, 4);
@@ -577,6 +598,8 @@ int gp_set_profiling(gp_pop* pop, int on) {
     if (!pop) return GP_EINVAL;
     pop->profiling = on != 0;
     memset(pop->ev_count, 0, sizeof pop->ev_count);
+    CK(cudaMemsetAsync(pop->cum, 0, 4 * sizeof(unsigned long long), pop->stream));
+    pop->cum_calls = 0;
     return GP_OK;
 }
 
@@ -713,6 +736,14 @@ int gp_get_stats(const gp_pop* cpop, gp_stats* out) {
     CK(cudaMemcpy(&ne, pop->d.e_off + pop->d.P, sizeof ne, cudaMemcpyDeviceToHost));
     s.cache_entries = ne;
     s.launches = pop->launches;
+    {
+        unsigned long long cm[4];
+        CK(cudaMemcpy(cm, pop->cum, sizeof cm, cudaMemcpyDeviceToHost));
+        s.cum_equivalent_ops = cm[0];
+        s.cum_actual_ops = cm[1];
+        s.cum_crossover_bytes = cm[2];
+        s.cum_calls = pop->cum_calls;
+    }
     if (pop->last_kind == 0) {
         unsigned long long acc[4];
         CK(cudaMemcpy(acc, pop->d.acc_ops, sizeof acc, cudaMemcpyDeviceToHost));
@@ -816,8 +847,10 @@ int gen_incremental(gp_pop* pop) {
     k_fill_child_cache<<<gt, 256, 0, pop->stream>>>(d, g, par);
     k_child_sizes<<<(d.P + 255) / 256, 256, 0, pop->stream>>>(d, g);
     phase_end(pop, PH_CACHE);
+    k_accumulate<<<1, 32, 0, pop->stream>>>(pop->cum, d.acc_ops, g.gstat, d.C, 1);
+    ++pop->cum_calls;
     CK(cudaGetLastError());
-    pop->launches += 11 + 6;
+    pop->launches += 11 + 7;
     pop->have_children = false;
     g.evaluated = true;
     pop->last_kind = 1;
