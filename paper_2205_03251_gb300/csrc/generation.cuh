@@ -46,10 +46,17 @@ struct GenBufs {
     uint32_t shift_cap;
     int32_t* stop;                   // [P] FDP stop level, -1 if the root differs
     uint32_t* plen;                  // [P] levels evaluated above the crossover point
-    uint4* pv_rec;                   // [pvcap] (child, k, pos, slot)
+    uint4* pv_rec;                   // [pvcap] (child, k, pos, slot | insert<<31)
+    float* pv_val;                   // [pvcap][Cpad] the walk's new values
+    int32_t* walkA;                  // [P] deepest cached ancestor (mother entry) of the crossover point
+    uint32_t* nins;                  // [P] child-cached nodes the mother does not cache (inserted entries)
+    uint4* mb;                       // [P] merge bounds: first mother entry >= c, >= c+r, father >= d, >= d+s
+    uint32_t* mcnt;                  // [P+1] children's entry counts, then offsets
+    uint32_t* src;                   // [Ecap] value source of each child entry (bit 31: walk record)
     uint32_t* pv_cnt;                // [P]
     uint32_t* pv_off;                // [P+1]
-    uint2* pv_sorted;                // [pvcap] (pos, slot), per child in walk order
+    uint4* pv_sorted;                // [pvcap] (pos, slot | insert<<31, child end, 0), per child in walk order
+    uint32_t* pv_end;                // [pvcap] child end of the recorded node
     uint32_t pvcap;
     uint32_t* order;                 // [P] walk order
     unsigned long long* gstat;       // [NGSTAT]
@@ -521,8 +528,9 @@ __global__ void __launch_bounds__(GP_WARPS * 32) k_walk(DevPop d, GenBufs g, Cac
         const uint32_t i = g.order[qi];
         const uint32_t fl = g.flags[i];
         const uint32_t m = g.mother[i];
+        if (lane == 0) { g.walkA[i] = -1; g.nins[i] = 0; g.pv_cnt[i] = 0; }
         if (fl & F_CLONE) {
-            if (lane == 0) { d.fit[i] = g.pfit[m]; g.stop[i] = 0; g.plen[i] = 0; g.pv_cnt[i] = 0; }
+            if (lane == 0) { d.fit[i] = g.pfit[m]; g.stop[i] = 0; g.plen[i] = 0; }
             ++st_stopped;
             continue;
         }
@@ -532,7 +540,7 @@ __global__ void __launch_bounds__(GP_WARPS * 32) k_walk(DevPop d, GenBufs g, Cac
         const uint8_t* ok_ = d.arena + (size_t)d.buf[i] * d.cap;     // child bytes
         const uint32_t me0 = par.e_off[m], me1 = par.e_off[m + 1];
         const uint32_t fe0 = par.e_off[f], fe1 = par.e_off[f + 1];
-        uint32_t npv = 0;
+        uint32_t npv = 0, nins_i = 0;
 
         // ---- level 0: donated subtree vs removed subtree
         float nv[K], ov[K];
@@ -563,11 +571,12 @@ __global__ void __launch_bounds__(GP_WARPS * 32) k_walk(DevPop d, GenBufs g, Cac
             if (lane == 0) slot = atomicAdd(&g.misc[M_PV], 1u);
             slot = __shfl_sync(FULL, slot, 0);
             if (slot >= g.pvcap) { if (lane == 0) set_status(d.status, ST_PATH); continue; }
-            float* dst = d.slots + (size_t)slot * d.Cpad + lane;
+            float* dst = g.pv_val + (size_t)slot * d.Cpad + lane;
 #pragma unroll
             for (int kk = 0; kk < K; ++kk) dst[kk * 32] = nv[kk];
-            if (lane == 0) g.pv_rec[slot] = make_uint4(i, npv, 0u, slot);
+            if (lane == 0) { g.pv_rec[slot] = make_uint4(i, npv, 0u, slot | 0x80000000u); g.pv_end[slot] = s; }
             ++npv;
+            ++nins_i;
         }
 
         // ---- ancestors: deepest cached ancestor A, then the small ones below it
@@ -758,12 +767,16 @@ __global__ void __launch_bounds__(GP_WARPS * 32) k_walk(DevPop d, GenBufs g, Cac
                 if (lane == 0) slot = atomicAdd(&g.misc[M_PV], 1u);
                 slot = __shfl_sync(FULL, slot, 0);
                 if (slot >= g.pvcap) { if (lane == 0) set_status(d.status, ST_PATH); done = true; break; }
-                float* dst = d.slots + (size_t)slot * d.Cpad + lane;
+                float* dst = g.pv_val + (size_t)slot * d.Cpad + lane;
                 const float (&val)[K] = stopped ? ov : nv;
 #pragma unroll
                 for (int kk = 0; kk < K; ++kk) dst[kk * 32] = val[kk];
-                if (lane == 0) g.pv_rec[slot] = make_uint4(i, npv, p, slot);
+                if (lane == 0) {
+                    g.pv_rec[slot] = make_uint4(i, npv, p, slot | (pent < 0 ? 0x80000000u : 0u));
+                    g.pv_end[slot] = pend;
+                }
                 ++npv;
+                if (pent < 0) ++nins_i;
             }
             q = p;
             qend = pend;
@@ -774,7 +787,7 @@ __global__ void __launch_bounds__(GP_WARPS * 32) k_walk(DevPop d, GenBufs g, Cac
         }
         (void)qe;
         // ---- fitness
-        if (lane == 0) { g.stop[i] = stop_level; g.plen[i] = levels; g.pv_cnt[i] = npv; }
+        if (lane == 0) { g.stop[i] = stop_level; g.plen[i] = levels; g.pv_cnt[i] = npv; g.nins[i] = nins_i; g.walkA[i] = A; }
         if (stopped) {
             if (lane == 0) d.fit[i] = g.pfit[m];
             ++st_stopped;
@@ -821,54 +834,244 @@ __global__ void k_pv_scatter(DevPop d, GenBufs g) {
     const uint32_t n = min(g.misc[M_PV], g.pvcap);
     for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
         const uint4 rec = g.pv_rec[r];
-        g.pv_sorted[g.pv_off[rec.x] + rec.y] = make_uint2(rec.z, rec.w);
+        g.pv_sorted[g.pv_off[rec.x] + rec.y] = make_uint4(rec.z, rec.w, g.pv_end[r], 0u);
     }
 }
 
-// Value of every cached node of every child: from the walk's record when
-// the walk computed it, else from the parent whose subtree holds the same
-// bytes -- the mother for nodes outside the exchanged subtree (positions
-// after it shifted by the size change), the father inside it.
-__global__ void k_fill_child_cache(DevPop d, GenBufs g, CacheView par) {
+// ---- children's cache by merging the parents' entries (no structure pass)
+//
+// A child's cached nodes, in position order, are: the mother's cached nodes
+// before the crossover point (ancestors of it re-sized by the size change,
+// dropped when they fall below the threshold, plus ancestors that rise
+// above it, which the walk recorded), the father's cached nodes inside the
+// donated subtree (moved to the crossover point), then the mother's cached
+// nodes after the removed subtree (moved by the size change).
+
+__device__ __forceinline__ uint32_t lower_bound_pos(const uint32_t* e_pos, uint32_t lo, uint32_t hi, uint32_t x) {
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (e_pos[mid] < x) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+// deepest cached ancestor of c in the mother (entry index) or -1
+__device__ __forceinline__ int32_t mother_anchor(const CacheView& par, uint32_t me0, uint32_t me1, uint32_t c,
+                                                 uint32_t r, uint32_t T) {
+    if (c == 0) return -1;
+    int32_t e;
+    if (r >= T) {
+        e = find_exact(par.e_pos, me0, me1, c);
+        return e >= 0 ? par.e_par[e] : -1;
+    }
+    e = find_last_lt(par.e_pos, me0, me1, c);
+    uint32_t guard = 0;
+    while (e >= 0 && par.e_end[e] <= c && guard++ < (1u << 24)) e = par.e_par[e];
+    return e;
+}
+
+__device__ __forceinline__ bool drops(const CacheView& par, int32_t e, int32_t delta, uint32_t T) {
+    const uint32_t pos = par.e_pos[e];
+    return pos > 0 && (int64_t)par.e_end[e] + delta - (int64_t)pos < (int64_t)T;
+}
+
+__global__ void k_merge_count(DevPop d, GenBufs g, CacheView par) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < d.P; i += gridDim.x * blockDim.x) {
+        const uint32_t m = g.mother[i];
+        const uint32_t me0 = par.e_off[m], me1 = par.e_off[m + 1];
+        if (g.flags[i] & F_CLONE) { g.mcnt[i] = me1 - me0; continue; }
+        const uint32_t f = g.father[i], c = g.cpos[i], r = g.rsz[i], dd = g.dpos[i], s = g.ssz[i];
+        const int32_t delta = (int32_t)s - (int32_t)r;
+        const uint32_t fe0 = par.e_off[f], fe1 = par.e_off[f + 1];
+        const uint32_t jc = lower_bound_pos(par.e_pos, me0, me1, c);
+        const uint32_t jcr = lower_bound_pos(par.e_pos, me0, me1, c + r);
+        uint32_t jd = lower_bound_pos(par.e_pos, fe0, fe1, dd);
+        const uint32_t jds = lower_bound_pos(par.e_pos, fe0, fe1, dd + s);
+        // a father's root is cached whatever its size; inside the child it is
+        // cached only when it becomes the child's root or is itself large
+        if (dd == 0 && c != 0 && s < d.T && jd < jds) ++jd;
+        uint32_t ndrop = 0;
+        if (delta < 0) {
+            int32_t e = mother_anchor(par, me0, me1, c, r, d.T);
+            uint32_t guard = 0;
+            while (e >= 0 && drops(par, e, delta, d.T) && guard++ < (1u << 24)) { ++ndrop; e = par.e_par[e]; }
+        }
+        g.mb[i] = make_uint4(jc, jcr, jd, jds);
+        g.mcnt[i] = (jc - me0) - ndrop + g.nins[i] + (jds - jd) + (me1 - jcr);
+    }
+}
+
+// Exclusive scan of the counts into the children's entry offsets.
+__global__ void __launch_bounds__(1024) k_merge_offsets(DevPop d, GenBufs g) {
+    __shared__ uint64_t ws[32];
+    __shared__ uint64_t carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (uint32_t base = 0; base < d.P; base += blockDim.x) {
+        const uint32_t i = base + threadIdx.x;
+        const uint64_t v = (i < d.P) ? g.mcnt[i] : 0;
+        const uint64_t o = block_excl_scan(v, ws, &carry);
+        if (i < d.P) { d.e_off[i] = (uint32_t)o; d.e_cnt[i] = (uint32_t)v; }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        d.e_off[d.P] = (uint32_t)carry;
+        *d.e_total = (uint32_t)carry;
+    }
+}
+
+__device__ __forceinline__ void put_entry(const DevPop& d, GenBufs& g, uint32_t x, uint32_t pos, uint32_t end,
+                                          uint32_t tree, uint32_t src) {
+    d.e_pos[x] = pos;
+    d.e_end[x] = end;
+    d.e_tree[x] = tree;
+    d.e_c0[x] = -1;
+    d.e_c1[x] = -1;
+    d.e_par[x] = -1;
+    d.e_slot[x] = x;
+    g.src[x] = src;
+}
+
+// walk record of child i at position pos (records are sorted by decreasing position), or -1
+__device__ __forceinline__ int32_t find_record(const GenBufs& g, uint32_t i, uint32_t pos) {
+    uint32_t lo = g.pv_off[i], hi = g.pv_off[i + 1];
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        const uint32_t pp = g.pv_sorted[mid].x;
+        if (pp == pos) return (int32_t)mid;
+        if (pp > pos) lo = mid + 1; else hi = mid;
+    }
+    return -1;
+}
+
+// One warp per child writes its entries (position, end, value source).
+__global__ void k_merge_write(DevPop d, GenBufs g, CacheView par) {
+    const int lane = lane_id();
+    const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+    if (d.e_off[d.P] > d.Ecap) return;
+    const uint32_t T = d.T;
+    for (uint32_t i = gw; i < d.P; i += nw) {
+        const uint32_t o = d.e_off[i];
+        const uint32_t m = g.mother[i];
+        const uint32_t me0 = par.e_off[m], me1 = par.e_off[m + 1];
+        if (g.flags[i] & F_CLONE) {
+            for (uint32_t k = lane; k < me1 - me0; k += 32) {
+                const uint32_t e = me0 + k;
+                put_entry(d, g, o + k, par.e_pos[e], par.e_end[e], i, par.e_slot[e]);
+            }
+            continue;
+        }
+        const uint32_t f = g.father[i], c = g.cpos[i], dd = g.dpos[i], s = g.ssz[i];
+        const int32_t delta = (int32_t)s - (int32_t)g.rsz[i];
+        const uint4 mb = g.mb[i];
+        const uint32_t jc = mb.x, jcr = mb.y, jd = mb.z, jds = mb.w;
+        const uint32_t r0 = g.pv_off[i], r1 = g.pv_off[i + 1];
+        // part 1: mother entries before c, merged with inserted ancestors (pos < c)
+        uint32_t kept = 0;
+        for (uint32_t base = me0; base < jc; base += 32) {
+            const uint32_t e = base + lane;
+            const bool valid = e < jc;
+            uint32_t pos = 0, end = 0;
+            bool keep = false, anc = false;
+            if (valid) {
+                pos = par.e_pos[e];
+                end = par.e_end[e];
+                anc = end > c;
+                keep = !(anc && drops(par, (int32_t)e, delta, T));
+            }
+            const uint32_t bal = __ballot_sync(FULL, keep);
+            if (keep) {
+                uint32_t insb = 0;
+                for (uint32_t q = r0; q < r1; ++q) {
+                    const uint4 rec = g.pv_sorted[q];
+                    if ((rec.y & 0x80000000u) && rec.x < pos) ++insb;
+                }
+                const uint32_t x = o + kept + __popc(bal & ((1u << lane) - 1u)) + insb;
+                uint32_t src = par.e_slot[e];
+                if (anc) {
+                    const int32_t h = find_record(g, i, pos);
+                    if (h >= 0) src = g.pv_sorted[h].y | 0x80000000u;
+                }
+                put_entry(d, g, x, pos, anc ? (uint32_t)((int64_t)end + delta) : end, i, src);
+            }
+            kept += __popc(bal);
+        }
+        // inserted ancestors (and the root made of a small donated subtree)
+        const int32_t anchor = (delta < 0) ? mother_anchor(par, me0, me1, c, g.rsz[i], T) : -1;
+        uint32_t nbefore = kept, rootins = 0;
+        for (uint32_t q0 = r0; q0 < r1; q0 += 32) {
+            const uint32_t q = q0 + lane;
+            bool ins = false;
+            uint4 rec = make_uint4(0, 0, 0, 0);
+            if (q < r1) { rec = g.pv_sorted[q]; ins = (rec.y & 0x80000000u) != 0; }
+            const uint32_t ib = __ballot_sync(FULL, ins && rec.x < c);
+            const uint32_t rb = __ballot_sync(FULL, ins && rec.x == c);
+            if (ins) {
+                uint32_t x;
+                if (rec.x < c) {
+                    // kept mother entries before rec.x, plus inserts before rec.x
+                    uint32_t mlt = lower_bound_pos(par.e_pos, me0, jc, rec.x) - me0;
+                    int32_t e = anchor;
+                    uint32_t guard = 0;
+                    while (e >= 0 && drops(par, e, delta, T) && guard++ < (1u << 24)) {
+                        if (par.e_pos[e] < rec.x) --mlt;
+                        e = par.e_par[e];
+                    }
+                    uint32_t ilt = 0;
+                    for (uint32_t q2 = r0; q2 < r1; ++q2) {
+                        const uint4 r2 = g.pv_sorted[q2];
+                        if ((r2.y & 0x80000000u) && r2.x < rec.x) ++ilt;
+                    }
+                    x = o + mlt + ilt;
+                } else {
+                    x = 0xFFFFFFFFu;     // placed below, after all entries before c
+                }
+                if (x != 0xFFFFFFFFu) put_entry(d, g, x, rec.x, rec.z, i, (rec.y & 0x7FFFFFFFu) | 0x80000000u);
+            }
+            nbefore += __popc(ib);
+            rootins += __popc(rb);
+            if (rb & (1u << lane)) {
+                // position c itself: filled after the count of earlier inserts is known
+            }
+        }
+        if (rootins) {
+            for (uint32_t q = r0; q < r1; ++q) {
+                const uint4 rec = g.pv_sorted[q];
+                if ((rec.y & 0x80000000u) && rec.x == c && lane == 0)
+                    put_entry(d, g, o + nbefore, rec.x, rec.z, i, (rec.y & 0x7FFFFFFFu) | 0x80000000u);
+            }
+        }
+        const uint32_t o2 = o + nbefore + rootins;
+        // part 2: father entries in the donated subtree
+        for (uint32_t k = lane; k < jds - jd; k += 32) {
+            const uint32_t e = jd + k;
+            put_entry(d, g, o2 + k, par.e_pos[e] - dd + c, par.e_end[e] - dd + c, i, par.e_slot[e]);
+        }
+        (void)f;
+        // part 3: mother entries after the removed subtree
+        const uint32_t o3 = o2 + (jds - jd);
+        for (uint32_t k = lane; k < me1 - jcr; k += 32) {
+            const uint32_t e = jcr + k;
+            put_entry(d, g, o3 + k, (uint32_t)((int64_t)par.e_pos[e] + delta), (uint32_t)((int64_t)par.e_end[e] + delta),
+                      i, par.e_slot[e]);
+        }
+    }
+}
+
+// Value vectors of the children's entries: one warp per entry, lanes over cases.
+__global__ void k_copy_values(DevPop d, GenBufs g, CacheView par) {
     const uint32_t ne = d.e_off[d.P];
     if (ne > d.Ecap) return;
-    for (uint32_t x = blockIdx.x * blockDim.x + threadIdx.x; x < ne; x += gridDim.x * blockDim.x) {
-        const uint32_t i = d.e_tree[x];
-        const uint32_t pos = d.e_pos[x], end = d.e_end[x];
-        const uint32_t fl = g.flags[i];
-        const uint32_t m = g.mother[i];
-        const uint32_t c = g.cpos[i], r = g.rsz[i], s = g.ssz[i];
-        int32_t src = -1;
-        const bool anc = !(fl & F_CLONE) && ((pos < c && end > c) || (pos == c && s < d.T));
-        if (anc) {
-            // ancestor of the crossover point (or the donated root become the child's root):
-            // the walk's value when it made one
-            uint32_t lo = g.pv_off[i], hi = g.pv_off[i + 1];
-            int32_t hit = -1;
-            while (lo < hi) {                         // positions decrease along the record list
-                const uint32_t mid = (lo + hi) >> 1;
-                const uint32_t pp = g.pv_sorted[mid].x;
-                if (pp == pos) { hit = (int32_t)mid; break; }
-                if (pp > pos) lo = mid + 1; else hi = mid;
-            }
-            if (hit >= 0) { d.e_slot[x] = g.pv_sorted[hit].y; continue; }
-            if (pos < c) src = find_exact(par.e_pos, par.e_off[m], par.e_off[m + 1], pos);
-            else {
-                const uint32_t f = g.father[i];            // whole donated tree become the root
-                src = find_exact(par.e_pos, par.e_off[f], par.e_off[f + 1], g.dpos[i]);
-            }
-        } else if (fl & F_CLONE) src = find_exact(par.e_pos, par.e_off[m], par.e_off[m + 1], pos);
-        else if (pos >= c + s) src = find_exact(par.e_pos, par.e_off[m], par.e_off[m + 1], pos - s + r);
-        else if (pos >= c) {
-            const uint32_t f = g.father[i];
-            src = find_exact(par.e_pos, par.e_off[f], par.e_off[f + 1], pos - c + g.dpos[i]);
-        } else src = find_exact(par.e_pos, par.e_off[m], par.e_off[m + 1], pos);
-        const uint32_t slot = g.pvcap + x;
-        d.e_slot[x] = slot;
-        if (src < 0) { set_error(d, ST_STRUCT, 8 + (anc ? 1 : 0), i, pos, end); continue; }
-        const float4* sp = reinterpret_cast<const float4*>(par.slots + (size_t)par.e_slot[src] * d.Cpad);
-        float4* dp = reinterpret_cast<float4*>(d.slots + (size_t)slot * d.Cpad);
-        for (uint32_t k = 0; k < d.Cpad / 4; ++k) dp[k] = __ldcg(sp + k);
+    const int lane = lane_id();
+    const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t x = gw; x < ne; x += nw) {
+        const uint32_t sr = g.src[x];
+        const float* sp = (sr & 0x80000000u) ? g.pv_val + (size_t)(sr & 0x7FFFFFFFu) * d.Cpad
+                                             : par.slots + (size_t)sr * d.Cpad;
+        float* dp = d.slots + (size_t)x * d.Cpad;
+        for (uint32_t k = lane; k < d.Cpad; k += 32) dp[k] = __ldcg(sp + k);
     }
 }
 

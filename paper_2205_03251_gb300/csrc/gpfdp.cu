@@ -30,7 +30,7 @@ constexpr int NREC = 128;   // event pairs kept per phase: stats average the las
 // set is built.
 struct CacheSet {
     uint32_t *e_cnt = nullptr, *e_off = nullptr, *e_pos = nullptr, *e_end = nullptr, *e_slot = nullptr;
-    uint32_t *order = nullptr, *e_tree = nullptr, *e_cmax = nullptr;
+    uint32_t *order = nullptr, *e_tree = nullptr, *e_cmax = nullptr, *msrc = nullptr;
     int32_t *e_par = nullptr, *e_c0 = nullptr, *e_c1 = nullptr, *e_bal = nullptr;
     uint4 *it_desc = nullptr, *sk_desc = nullptr;
     float* slots = nullptr;
@@ -250,6 +250,7 @@ void bind_set(gp_pop* pop) {
     d.e_c0 = c.e_c0; d.e_c1 = c.e_c1; d.e_slot = c.e_slot; d.e_tree = c.e_tree; d.it_desc = c.it_desc;
     d.sk_desc = c.sk_desc; d.order = c.order; d.slots = c.slots; d.Ecap = c.Ecap; d.Scap = c.Scap;
     pop->sb.e_bal = c.e_bal; pop->sb.e_tree = c.e_tree; pop->sb.e_cmax = c.e_cmax;
+    pop->gb.src = c.msrc;
 }
 
 CacheView view_of(const CacheSet& c) {
@@ -259,12 +260,11 @@ CacheView view_of(const CacheSet& c) {
     return v;
 }
 
-// (Re)allocate cache set `which` for ecap entries.  Slots: the walk's
-// records first (pvcap), then one per entry.
+// (Re)allocate cache set `which` for ecap entries (one value slot each).
 int grow_set(gp_pop* pop, int which, uint32_t ecap) {
     CacheSet& c = pop->sets[which];
     const DevPop& d = pop->d;
-    const uint64_t scap = (uint64_t)pop->gb.pvcap + ecap;
+    const uint64_t scap = ecap;
     if (scap > pop->slot_limit)
         return fail(pop, GP_ENOMEM, "cache needs %llu value vectors, budget allows %llu",
                     (unsigned long long)scap, (unsigned long long)pop->slot_limit);
@@ -282,7 +282,8 @@ int grow_set(gp_pop* pop, int which, uint32_t ecap) {
     bool ok = al(&c.e_cnt, d.P + 1) && al(&c.e_off, d.P + 1) && al(&c.e_pos, ecap) && al(&c.e_end, ecap) &&
               al(&c.e_par, ecap) && al(&c.e_c0, ecap) && al(&c.e_c1, ecap) && al(&c.e_slot, ecap) &&
               al(&c.it_desc, ecap) && al(&c.sk_desc, ecap) && al(&c.order, ecap) && al(&c.e_bal, ecap) &&
-              al(&c.e_tree, ecap) && al(&c.e_cmax, ecap / 32 + 2) && al(&c.slots, (size_t)scap * d.Cpad);
+              al(&c.e_tree, ecap) && al(&c.e_cmax, ecap / 32 + 2) && al(&c.msrc, ecap) &&
+              al(&c.slots, (size_t)scap * d.Cpad);
     if (!ok) return fail(pop, GP_ENOMEM, "allocation of a cache of %u entries failed", ecap);
     cudaMemset(c.e_off, 0, sizeof(uint32_t) * (d.P + 1));
     c.Ecap = ecap;
@@ -309,7 +310,7 @@ int run_structure(gp_pop* pop) {
     CK(cudaStreamSynchronize(pop->stream));
     if (*pop->e_total_h > d.Ecap) {
         uint64_t want = (uint64_t)*pop->e_total_h + *pop->e_total_h / 4 + 64;
-        if (want + pop->gb.pvcap > pop->slot_limit) want = pop->slot_limit - pop->gb.pvcap;
+        if (want > pop->slot_limit) want = pop->slot_limit;
         int r = grow_cache(pop, (uint32_t)want);
         if (r) return r;
     }
@@ -502,6 +503,8 @@ int gp_pop_create(const gp_config* cfg_in, const float* x, const float* targets,
         DA2(g.shift_off, P + 1); DA2(g.halo, (size_t)g.shift_cap * HALO_MAX);
         DA2(g.stop, P); DA2(g.plen, P);
         DA2(g.pv_rec, g.pvcap); DA2(g.pv_cnt, P); DA2(g.pv_off, P + 1); DA2(g.pv_sorted, g.pvcap);
+        DA2(g.pv_end, g.pvcap); DA2(g.pv_val, (size_t)g.pvcap * d.Cpad);
+        DA2(g.walkA, P); DA2(g.nins, P); DA2(g.mb, P); DA2(g.mcnt, P + 1);
         DA2(g.order, P); DA2(g.gstat, NGSTAT);
         std::vector<uint32_t> fb(P);
         for (uint32_t i = 0; i < P; ++i) fb[i] = P + i;          // buffers P..2P-1 start free
@@ -829,12 +832,6 @@ int gen_incremental(gp_pop* pop) {
     const CacheView par = view_of(pop->sets[pop->cur ^ 1]);
     const int gt = pop->grid_threads;
     CK(cudaMemsetAsync(d.q, 0, sizeof(uint32_t) * NQ, pop->stream));
-    phase_begin(pop, PH_STRUCT);
-    {
-        int r = run_structure(pop);
-        if (r) return r;
-    }
-    phase_end(pop, PH_STRUCT);
     phase_begin(pop, PH_PACK);
     k_order_identity<<<(d.P + 255) / 256, 256, 0, pop->stream>>>(d, g);
     phase_end(pop, PH_PACK);
@@ -844,13 +841,28 @@ int gen_incremental(gp_pop* pop) {
     phase_begin(pop, PH_CACHE);
     k_pv_offsets<<<1, 1024, 0, pop->stream>>>(d, g);
     k_pv_scatter<<<gt, 256, 0, pop->stream>>>(d, g);
-    k_fill_child_cache<<<gt, 256, 0, pop->stream>>>(d, g, par);
+    k_merge_count<<<(d.P + 255) / 256, 256, 0, pop->stream>>>(d, g, par);
+    k_merge_offsets<<<1, 1024, 0, pop->stream>>>(d, g);
+    CK(cudaMemcpyAsync(pop->e_total_h, d.e_total, sizeof(uint32_t), cudaMemcpyDeviceToHost, pop->stream));
+    CK(cudaStreamSynchronize(pop->stream));
+    if (*pop->e_total_h > d.Ecap) {
+        uint64_t want = (uint64_t)*pop->e_total_h + *pop->e_total_h / 4 + 64;
+        if (want > pop->slot_limit) want = pop->slot_limit;
+        int r = grow_cache(pop, (uint32_t)want);
+        if (r) return r;
+        k_merge_offsets<<<1, 1024, 0, pop->stream>>>(d, g);
+    }
+    k_merge_write<<<pop->grid_warps, GP_WARPS * 32, 0, pop->stream>>>(d, g, par);
+    k_copy_values<<<pop->nsm * 16, 256, 0, pop->stream>>>(d, g, par);
+    k_entry_chunkmax<<<pop->grid_warps, GP_WARPS * 32, 0, pop->stream>>>(d, pop->sb);
+    k_entry_parents<<<gt, 256, 0, pop->stream>>>(d, pop->sb);
+    k_entry_links<<<gt, 256, 0, pop->stream>>>(d, pop->sb);
     k_child_sizes<<<(d.P + 255) / 256, 256, 0, pop->stream>>>(d, g);
     phase_end(pop, PH_CACHE);
     k_accumulate<<<1, 32, 0, pop->stream>>>(pop->cum, d.acc_ops, g.gstat, d.C, 1);
     ++pop->cum_calls;
     CK(cudaGetLastError());
-    pop->launches += 11 + 7;
+    pop->launches += 12;
     pop->have_children = false;
     g.evaluated = true;
     pop->last_kind = 1;

@@ -405,7 +405,7 @@ __global__ void k_entry_ends(DevPop d, StructBufs sb) {
 }
 
 __global__ void k_entry_chunkmax(DevPop d, StructBufs sb) {
-    const uint32_t ne = sb.u_epre[d.blk_off[d.P]];
+    const uint32_t ne = d.e_off[d.P];
     if (ne > d.Ecap) return;
     const uint32_t nch = (ne + 31) / 32;
     const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -423,7 +423,7 @@ __global__ void k_entry_chunkmax(DevPop d, StructBufs sb) {
 // or after end(e): earlier entries either contain e (ancestors, end >=
 // end(e)) or end before pos(e) < end(e).
 __global__ void k_entry_parents(DevPop d, StructBufs sb) {
-    const uint32_t ne = sb.u_epre[d.blk_off[d.P]];
+    const uint32_t ne = d.e_off[d.P];
     if (ne > d.Ecap) return;
     for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < ne; e += gridDim.x * blockDim.x) {
         const uint32_t tree = sb.e_tree[e];
@@ -451,7 +451,7 @@ __global__ void k_entry_parents(DevPop d, StructBufs sb) {
 }
 
 __global__ void k_entry_links(DevPop d, StructBufs sb) {
-    const uint32_t ne = sb.u_epre[d.blk_off[d.P]];
+    const uint32_t ne = d.e_off[d.P];
     if (ne > d.Ecap) return;
     for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < ne; e += gridDim.x * blockDim.x) {
         int32_t p = d.e_par[e];

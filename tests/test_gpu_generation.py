@@ -25,10 +25,18 @@ def _expected_entries(tree, T):
     pos = np.nonzero(size >= T)[0]
     if len(pos) == 0 or pos[0] != 0:
         pos = np.concatenate([[0], pos])
-    return pos, ends[pos]
+    end = ends[pos]
+    par = np.full(len(pos), -1, np.int64)
+    stack = []
+    for j, (p, e) in enumerate(zip(pos, end)):
+        while stack and end[stack[-1]] <= p:
+            stack.pop()
+        par[j] = stack[-1] if stack else -1
+        stack.append(j)
+    return pos, end, par
 
 
-def run_generations(gp, w, *, T, gens, max_nodes, seed=1234, cache_check=8, stop_check=True,
+def run_generations(gp, w, *, T, gens, max_nodes, seed=1234, cache_check=16, stop_check=True,
                     cases_per_lane=0):
     import oracle
     ops, off = w["ops"], w["off"]
@@ -75,8 +83,12 @@ def run_generations(gp, w, *, T, gens, max_nodes, seed=1234, cache_check=8, stop
         for i in rng.choice(P, size=min(P, cache_check), replace=False):
             kid = kops[int(koff[i]):int(koff[i + 1])]
             pos, end, par = pop.cache_entries(int(i))
-            epos, eend = _expected_entries(kid, T)
-            assert np.array_equal(pos, epos) and np.array_equal(end, eend), f"gen {g}: child {i} cache structure"
+            epos, eend, epar = _expected_entries(kid, T)
+            assert np.array_equal(pos, epos) and np.array_equal(end, eend), (
+                f"gen {g}: child {i} cache structure: got pos {pos[:12]} end {end[:12]}, "
+                f"want pos {epos[:12]} end {eend[:12]}; plan c={pl['c'][i]} r={pl['r'][i]} d={pl['d'][i]} "
+                f"s={pl['s'][i]} mother={pl['mother'][i]} father={pl['father'][i]} size={len(kid)} stop={stop[i]}")
+            assert np.array_equal(par, epar), f"gen {g}: child {i} cache parents"
             for j in np.unique(np.linspace(0, len(pos) - 1, min(len(pos), 5)).astype(int)):
                 want = oracle.eval_node_f32(kid, int(pos[j]), k, x)
                 assert np.array_equal(oracle.canon_nan(pop.cache_value(int(i), int(j))), oracle.canon_nan(want)), \
