@@ -188,6 +188,34 @@ int gp_get_stats(const gp_pop* pop, gp_stats* out);
  * recorded phase times. */
 int gp_set_profiling(gp_pop* pop, int on);
 
+/*
+ * Full evaluation of a batch of small trees without any device allocation
+ * (the paper has no counterpart; this is a service for callers that cannot
+ * call cudaMalloc -- e.g. code running while another component captures the
+ * stream into a CUDA graph, or an embedding whose memory is fixed at start).
+ * All pointers but status_out are device pointers owned by the caller:
+ *   d_ops      16-byte aligned opcodes; tree i is d_ops[d_off[i] .. d_off[i+1]);
+ *              ops_bytes (a multiple of 16) must cover every tree rounded up to 16
+ *   d_off      n_trees + 1 uint64 offsets; each tree 1..1023 nodes
+ *   d_x, d_t   n_cases inputs and targets (1 <= n_cases <= 4096); d_consts 251 floats
+ *   d_values   out: n_trees x n_cases root values (row per tree)
+ *   d_fitness  out: n_trees fitness values (sum of |value - target| in case order)
+ * Same arithmetic as gp_eval_full.  Scratch (the interpreter's deep-stack
+ * overflow for 64 warps, a work counter, a status word) lives in one
+ * file-scope device array of about 8.5 MB that every GPU loading the library
+ * holds until exit.  The first call on a device looks up that array's device
+ * address (cudaGetSymbolAddress) with the device current; make that first
+ * call before any stream capture.  Every call shares the array: calls whose
+ * GPU work overlaps (other streams, or not yet finished) race and must be
+ * serialised.  Each call clears its counter and status word first, then
+ * waits for its stream to finish.  Returns GP_EINVAL for bad arguments or a
+ * malformed tree, GP_ECAPACITY when a tree is empty, larger than 1023 nodes
+ * or outside ops_bytes; *status_out (host, may be NULL) gets the raw flags.
+ */
+int gp_eval_small_noalloc(const uint8_t* d_ops, size_t ops_bytes, const uint64_t* d_off, uint32_t n_trees,
+                          const float* d_x, const float* d_t, const float* d_consts, uint32_t n_cases,
+                          float* d_values, float* d_fitness, void* stream, uint32_t* status_out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -86,6 +86,8 @@ def load() -> ctypes.CDLL:
         "gp_cache_value": (i32, [vp, u32, u32, vp, ctypes.c_size_t]),
         "gp_get_stats": (i32, [vp, ctypes.POINTER(GpStats)]),
         "gp_walk_info": (i32, [vp, vp, vp, u32]),
+        "gp_eval_small_noalloc": (i32, [vp, ctypes.c_size_t, vp, u32, vp, vp, vp, u32, vp, vp, vp,
+                                        ctypes.POINTER(u32)]),
         "gp_set_profiling": (i32, [vp, i32]),
     }
     for name, (res, args) in sig.items():
@@ -208,6 +210,28 @@ def gp_walk_info(h, n: int):
     lv = np.empty(n, np.uint32)
     _check(load().gp_walk_info(h, _ptr(stop), _ptr(lv), n), h)
     return stop, lv
+
+
+def gp_eval_small_noalloc(ops, off, x, t, consts, values, fitness, stream=None) -> int:
+    """Evaluate small trees with no device allocation (see include/gpfdp.h).
+    Every array argument is a CUDA tensor owned by the caller: ops (uint8,
+    length a multiple of 16), off (int64, n_trees+1), x, t (float32, C),
+    consts (float32, 251), values (float32, n_trees x C), fitness (float32,
+    n_trees).  Returns the raw status flags; raises GpError on failure."""
+    if stream is None:
+        stream = _default_stream()
+    elif hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    st = ctypes.c_uint32(0)
+    rc = load().gp_eval_small_noalloc(ctypes.c_void_p(ops.data_ptr()), ops.numel(),
+                                      ctypes.c_void_p(off.data_ptr()), off.numel() - 1,
+                                      ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(t.data_ptr()),
+                                      ctypes.c_void_p(consts.data_ptr()), x.numel(),
+                                      ctypes.c_void_p(values.data_ptr()), ctypes.c_void_p(fitness.data_ptr()),
+                                      ctypes.c_void_p(stream), ctypes.byref(st))
+    if rc != GP_OK:
+        raise GpError(rc, f"gp_eval_small_noalloc failed (status flags 0x{st.value:x})")
+    return st.value
 
 
 def gp_set_profiling(h, on: bool):

@@ -31,12 +31,13 @@ def sources() -> list[str]:
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile csrc/gpfdp.cu into libgpfdp.so next to this file."""
+    """Compile csrc/*.cu into libgpfdp.so next to this file."""
     newest = max(os.path.getmtime(p) for p in sources())
     if not force and os.path.exists(LIB_PATH) and os.path.getmtime(LIB_PATH) >= newest:
         return LIB_PATH
     tmp = LIB_PATH + f".{os.getpid()}.tmp"
-    cmd = [_nvcc(), *NVCC_FLAGS, "-I", INCLUDE, "-o", tmp, os.path.join(CSRC, "gpfdp.cu")]
+    units = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
+    cmd = [_nvcc(), *NVCC_FLAGS, "-I", INCLUDE, "-o", tmp, *units]
     if verbose:
         print(" ".join(cmd))
     subprocess.check_call(cmd)
