@@ -77,6 +77,8 @@ typedef struct {
     uint32_t cases_per_lane;    /* 0 = auto; else 1, 2 or 4 test cases per GPU lane */
     uint64_t cache_budget_bytes;/* device bytes for cached value vectors (0 = 40 GiB) */
     uint64_t seed;              /* master seed of every stochastic choice */
+    uint32_t walk_warps;        /* 0 = as many as fit; else at most this many warps run the walk */
+    uint32_t mlp_lr_micro;      /* Adam learning rate of the packing MLP in 1e-6 units (0 = 1000) */
 } gp_config;
 
 /* Per-call statistics of the last evaluation (host copy). */
@@ -180,6 +182,29 @@ int gp_cache_value(const gp_pop* pop, uint32_t i, uint32_t j, void* host_out, si
  * recomputed) and the number of levels evaluated above the crossover
  * point.  Either pointer may be NULL; n <= pop_size.  Synchronising. */
 int gp_walk_info(const gp_pop* pop, int32_t* stop_level, uint32_t* levels, uint32_t n);
+
+/*
+ * Work packing of the last gp_eval_incremental (Sec. 3 and Sec. 4.1 of
+ * the paper: run the longest tasks first; one slow evaluation holds up the
+ * population).  Per child: the packing MLP's prediction of
+ * log2(1 + levels walked) made before the walk, the measured value, the
+ * static packing key log2(1 + mother size), and the walk queue (order[k] =
+ * child walked k-th); *loss = mean squared error of the training step that
+ * followed the walk.  Any pointer may be NULL; n <= pop_size.
+ * Synchronising.
+ */
+int gp_pack_info(const gp_pop* pop, float* predicted, float* measured, float* size_key, uint32_t* order,
+                 uint32_t n, float* loss);
+
+/*
+ * Loss and gradient of the packing MLP (16 -> 64 -> 64 -> 1, ReLU) on the
+ * GPU for given host weights w (5,313 floats: W1[64][16], b1[64],
+ * W2[64][64], b2[64], w3[64], b3), features x (n x 16) and targets y (n):
+ * loss = mean (f(x) - y)^2, grad = d loss / d w.  Uses the same kernels as
+ * the online training; allocates and frees its own device buffers.
+ * Synchronising.
+ */
+int gp_mlp_eval_grad(const float* w, const float* x, const float* y, uint32_t n, float* loss, float* grad);
 
 /* Statistics of the last gp_eval_full / gp_eval_incremental.  Synchronising. */
 int gp_get_stats(const gp_pop* pop, gp_stats* out);

@@ -32,7 +32,8 @@ class GpConfig(ctypes.Structure):
                 ("max_nodes", ctypes.c_uint32), ("funcset", ctypes.c_uint32),
                 ("cache_threshold", ctypes.c_uint32), ("tournament", ctypes.c_uint32),
                 ("packing", ctypes.c_uint32), ("cases_per_lane", ctypes.c_uint32),
-                ("cache_budget_bytes", ctypes.c_uint64), ("seed", ctypes.c_uint64)]
+                ("cache_budget_bytes", ctypes.c_uint64), ("seed", ctypes.c_uint64),
+                ("walk_warps", ctypes.c_uint32), ("mlp_lr_micro", ctypes.c_uint32)]
 
 
 class GpStats(ctypes.Structure):
@@ -86,6 +87,8 @@ def load() -> ctypes.CDLL:
         "gp_cache_value": (i32, [vp, u32, u32, vp, ctypes.c_size_t]),
         "gp_get_stats": (i32, [vp, ctypes.POINTER(GpStats)]),
         "gp_walk_info": (i32, [vp, vp, vp, u32]),
+        "gp_pack_info": (i32, [vp, vp, vp, vp, vp, u32, vp]),
+        "gp_mlp_eval_grad": (i32, [vp, vp, vp, u32, vp, vp]),
         "gp_eval_small_noalloc": (i32, [vp, ctypes.c_size_t, vp, u32, vp, vp, vp, u32, vp, vp, vp,
                                         ctypes.POINTER(u32)]),
         "gp_set_profiling": (i32, [vp, i32]),
@@ -234,6 +237,33 @@ def gp_eval_small_noalloc(ops, off, x, t, consts, values, fitness, stream=None) 
     return st.value
 
 
+def gp_pack_info(h, n: int):
+    """(predicted, measured, size key, queue order, training loss) of the last
+    incremental evaluation."""
+    pred = np.empty(n, np.float32)
+    meas = np.empty(n, np.float32)
+    key = np.empty(n, np.float32)
+    order = np.empty(n, np.uint32)
+    loss = np.zeros(1, np.float32)
+    _check(load().gp_pack_info(h, _ptr(pred), _ptr(meas), _ptr(key), _ptr(order), n, _ptr(loss)), h)
+    return pred, meas, key, order, float(loss[0])
+
+
+MLP_NP = 64 * 16 + 64 + 64 * 64 + 64 + 64 + 1
+
+
+def gp_mlp_eval_grad(w, x, y):
+    """(loss, gradient) of the packing MLP computed by the GPU kernels."""
+    w = np.ascontiguousarray(w, np.float32)
+    x = np.ascontiguousarray(x, np.float32)
+    y = np.ascontiguousarray(y, np.float32)
+    assert w.size == MLP_NP and x.shape[1] == 16 and x.shape[0] == y.size
+    loss = np.zeros(1, np.float32)
+    grad = np.empty(MLP_NP, np.float32)
+    _check(load().gp_mlp_eval_grad(_ptr(w), _ptr(x), _ptr(y), y.size, _ptr(loss), _ptr(grad)))
+    return float(loss[0]), grad
+
+
 def gp_set_profiling(h, on: bool):
     _check(load().gp_set_profiling(h, 1 if on else 0), h)
 
@@ -246,7 +276,8 @@ class Population:
 
     def __init__(self, x, t, consts, ops, off, *, max_nodes: int, cache_threshold: int = 1024,
                  boolean: bool = False, tournament: int = 7, packing: int = GP_PACK_STATIC,
-                 cases_per_lane: int = 0, cache_budget_bytes: int = 0, seed: int = 0, stream=None):
+                 cases_per_lane: int = 0, cache_budget_bytes: int = 0, seed: int = 0, stream=None,
+                 walk_warps: int = 0, mlp_lr_micro: int = 0):
         off = np.asarray(off, np.uint64)
         self.P = len(off) - 1
         self.boolean = boolean
@@ -255,7 +286,7 @@ class Population:
                        funcset=GP_BOOL_MUX6 if boolean else GP_FP32_ARITH,
                        cache_threshold=cache_threshold, tournament=tournament, packing=packing,
                        cases_per_lane=cases_per_lane, cache_budget_bytes=cache_budget_bytes,
-                       seed=seed & (2**64 - 1))
+                       seed=seed & (2**64 - 1), walk_warps=walk_warps, mlp_lr_micro=mlp_lr_micro)
         if boolean:
             x = np.zeros(1, np.float32)
             t = np.zeros(1, np.float32)
@@ -304,6 +335,9 @@ class Population:
 
     def walk_info(self):
         return gp_walk_info(self.h, self.P)
+
+    def pack_info(self):
+        return gp_pack_info(self.h, self.P)
 
     def set_profiling(self, on: bool):
         gp_set_profiling(self.h, on)

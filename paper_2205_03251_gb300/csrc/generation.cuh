@@ -4,6 +4,7 @@
 #pragma once
 #include "interp.cuh"
 #include "structure.cuh"
+#include "mlp.cuh"
 
 #define HALO_MAX 64            // largest |size change| moved in place (halo bytes per block)
 #define SHIFT_BS 4096          // bytes of tail per block of the in-place move
@@ -1081,6 +1082,60 @@ __global__ void k_child_sizes(DevPop d, GenBufs g) {
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < d.P; i += gridDim.x * blockDim.x) s += d.size[i];
     for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(FULL, s, o);
     if ((threadIdx.x & 31) == 0 && s) atomicAdd(&g.gstat[G_EQUIV], s);
+}
+
+// Features of each child known before its walk (16 per child, scaled to
+// about [0, 1]): parent and exchanged-subtree sizes, size change, relative
+// crossover points, whether the exchanged subtrees are cached, the parents'
+// fitness, cache sizes and the spread of their root value vectors, a clone
+// flag and a constant.
+__global__ void k_mlp_features(DevPop d, GenBufs g, CacheView par, MlpBufs b) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < d.P; i += gridDim.x * blockDim.x) {
+        const uint32_t m = g.mother[i], f = g.father[i], c = g.cpos[i], r = g.rsz[i], dd = g.dpos[i], s = g.ssz[i];
+        const float sm = (float)g.psize[m], sf = (float)g.psize[f];
+        float* x = b.feat + (size_t)i * MLP_IN;
+        const float dl = (float)s - (float)r;
+        x[0] = log2f(1.f + sm) / 21.f;
+        x[1] = log2f(1.f + sf) / 21.f;
+        x[2] = log2f(1.f + (float)r) / 21.f;
+        x[3] = log2f(1.f + (float)s) / 21.f;
+        x[4] = copysignf(log2f(1.f + fabsf(dl)), dl) / 21.f;
+        x[5] = (float)c / sm;
+        x[6] = (float)dd / sf;
+        x[7] = (r >= d.T) ? 1.f : 0.f;
+        x[8] = (s >= d.T) ? 1.f : 0.f;
+        const float fm = g.pfit[m], ff = g.pfit[f];
+        x[9] = isfinite(fm) ? fminf(log2f(1.f + fabsf(fm)) / 8.f, 4.f) : 4.f;
+        x[10] = isfinite(ff) ? fminf(log2f(1.f + fabsf(ff)) / 8.f, 4.f) : 4.f;
+        x[11] = log2f(1.f + (float)(par.e_off[m + 1] - par.e_off[m])) / 16.f;
+        float spread[2];
+        for (int q = 0; q < 2; ++q) {
+            const uint32_t t = q ? f : m;
+            const float* v = par.slots + (size_t)par.e_slot[par.e_off[t]] * d.Cpad;
+            float lo = INFINITY, hi = -INFINITY;
+            for (uint32_t cc = 0; cc < d.C; ++cc) {
+                const float a = v[cc];
+                if (isfinite(a)) { lo = fminf(lo, a); hi = fmaxf(hi, a); }
+            }
+            spread[q] = (hi >= lo) ? fminf(log2f(1.f + (hi - lo)) / 8.f, 4.f) : 4.f;
+        }
+        x[12] = spread[0];
+        x[13] = spread[1];
+        x[14] = (g.flags[i] & F_CLONE) ? 1.f : 0.f;
+        x[15] = 1.f;
+    }
+}
+
+// static packing key: the mother's size (largest first)
+__global__ void k_static_key(DevPop d, GenBufs g, MlpBufs b) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < d.P; i += gridDim.x * blockDim.x)
+        b.target[i] = (float)g.psize[g.mother[i]];
+}
+
+// training targets: log2(1 + levels the walk evaluated)
+__global__ void k_mlp_targets(DevPop d, GenBufs g, MlpBufs b) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < d.P; i += gridDim.x * blockDim.x)
+        b.target[i] = log2f(1.f + (float)g.plen[i]);
 }
 
 __global__ void k_order_identity(DevPop d, GenBufs g) {

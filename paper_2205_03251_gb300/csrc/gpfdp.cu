@@ -72,7 +72,10 @@ struct gp_pop {
     unsigned long long* cum;          // device: equivalent, actual, crossover bytes, calls
     uint32_t cum_calls;
     int grid_walk;
+    int grid_walk_max;
     size_t smem_walk;
+    MlpBufs mlp;
+    float mlp_lr;
     int last_kind;                    // 0 full evaluation, 1 generation
 };
 
@@ -516,6 +519,23 @@ int gp_pop_create(const gp_config* cfg_in, const float* x, const float* targets,
     {
         int r = (K == 1) ? setup_walk_kernel<1>(pop) : (K == 2) ? setup_walk_kernel<2>(pop) : setup_walk_kernel<4>(pop);
         if (r) return bail(r);
+        pop->grid_walk_max = pop->grid_walk;
+        if (cfg.walk_warps) {
+            int g = (int)((cfg.walk_warps + GP_WARPS - 1) / GP_WARPS);
+            if (g < pop->grid_walk) pop->grid_walk = g;
+        }
+    }
+    // packing MLP
+    {
+        MlpBufs& b = pop->mlp;
+        b.cap = P;
+        DA2(b.w, MLP_NP); DA2(b.m, MLP_NP); DA2(b.v, MLP_NP); DA2(b.wb, MLP_NP); DA2(b.grad, MLP_NP);
+        DA2(b.feat, (size_t)P * MLP_IN); DA2(b.pred, P); DA2(b.pred_pack, P); DA2(b.target, P); DA2(b.h1, (size_t)P * MLP_H);
+        DA2(b.h2, (size_t)P * MLP_H); DA2(b.dy, P); DA2(b.dh2, (size_t)P * MLP_H); DA2(b.dh1, (size_t)P * MLP_H);
+        DA2(b.loss, 1); DA2(b.step, 1);
+        pop->mlp_lr = (cfg.mlp_lr_micro ? cfg.mlp_lr_micro : 1000u) * 1e-6f;
+        k_mlp_init<<<(MLP_NP + 255) / 256, 256, 0, pop->stream>>>(b, cfg.seed ^ 0x3131A5A5ull);
+        cudaMemsetAsync(b.loss, 0, sizeof(float), pop->stream);
     }
 
     // inputs
@@ -717,6 +737,60 @@ int gp_walk_info(const gp_pop* cpop, int32_t* stop_level, uint32_t* levels, uint
     return GP_OK;
 }
 
+int gp_pack_info(const gp_pop* cpop, float* predicted, float* measured, float* size_key, uint32_t* order,
+                 uint32_t n, float* loss) {
+    gp_pop* pop = const_cast<gp_pop*>(cpop);
+    if (!pop || n > pop->d.P) return GP_EINVAL;
+    if (pop->last_kind != 1) return fail(pop, GP_ESTATE, "no incremental evaluation has run");
+    int rc = check_status(pop);
+    if (rc) return rc;
+    if (predicted) CK(cudaMemcpy(predicted, pop->mlp.pred_pack, sizeof(float) * n, cudaMemcpyDeviceToHost));
+    if (measured) CK(cudaMemcpy(measured, pop->mlp.target, sizeof(float) * n, cudaMemcpyDeviceToHost));
+    if (size_key) {
+        std::vector<float> f((size_t)n * MLP_IN);
+        CK(cudaMemcpy(f.data(), pop->mlp.feat, sizeof(float) * f.size(), cudaMemcpyDeviceToHost));
+        for (uint32_t i = 0; i < n; ++i) size_key[i] = f[(size_t)i * MLP_IN] * 21.f;
+    }
+    if (order) CK(cudaMemcpy(order, pop->gb.order, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost));
+    if (loss) CK(cudaMemcpy(loss, pop->mlp.loss, sizeof(float), cudaMemcpyDeviceToHost));
+    return GP_OK;
+}
+
+int gp_mlp_eval_grad(const float* w, const float* x, const float* y, uint32_t n, float* loss, float* grad) {
+    if (!w || !x || !y || !loss || !grad || n == 0) return GP_EINVAL;
+    MlpBufs b{};
+    std::vector<void*> mem;
+    auto al = [&](auto** ptr, size_t count) -> bool {
+        void* p = nullptr;
+        if (cudaMalloc(&p, count * sizeof(**ptr) + 16) != cudaSuccess) { cudaGetLastError(); return false; }
+        mem.push_back(p);
+        *ptr = static_cast<std::remove_reference_t<decltype(*ptr)>>(p);
+        return true;
+    };
+    int rc = GP_OK;
+    if (!(al(&b.w, MLP_NP) && al(&b.grad, MLP_NP) && al(&b.feat, (size_t)n * MLP_IN) && al(&b.pred, n) &&
+          al(&b.target, n) && al(&b.h1, (size_t)n * MLP_H) && al(&b.h2, (size_t)n * MLP_H) && al(&b.dy, n) &&
+          al(&b.dh2, (size_t)n * MLP_H) && al(&b.dh1, (size_t)n * MLP_H) && al(&b.loss, 1))) rc = GP_ENOMEM;
+    if (rc == GP_OK) {
+        cudaMemcpy(b.w, w, sizeof(float) * MLP_NP, cudaMemcpyHostToDevice);
+        cudaMemcpy(b.feat, x, sizeof(float) * n * MLP_IN, cudaMemcpyHostToDevice);
+        cudaMemcpy(b.target, y, sizeof(float) * n, cudaMemcpyHostToDevice);
+        const int pb = (int)((n + 255) / 256);
+        k_mlp_forward_train<<<pb, 256>>>(b, n);
+        k_mlp_backward_act<<<pb, 256>>>(b, n);
+        k_mlp_loss<<<1, 256>>>(b, n);
+        k_mlp_backward_params<<<(MLP_NP + 255) / 256, 256>>>(b, n);
+        if (cudaDeviceSynchronize() != cudaSuccess) rc = GP_ECUDA;
+        else {
+            cudaMemcpy(loss, b.loss, sizeof(float), cudaMemcpyDeviceToHost);
+            cudaMemcpy(grad, b.grad, sizeof(float) * MLP_NP, cudaMemcpyDeviceToHost);
+        }
+    }
+    for (void* p : mem) cudaFree(p);
+    if (rc) g_create_error = "gp_mlp_eval_grad failed";
+    return rc;
+}
+
 int gp_get_stats(const gp_pop* cpop, gp_stats* out) {
     gp_pop* pop = const_cast<gp_pop*>(cpop);
     if (!pop || !out) return GP_EINVAL;
@@ -833,11 +907,29 @@ int gen_incremental(gp_pop* pop) {
     const int gt = pop->grid_threads;
     CK(cudaMemsetAsync(d.q, 0, sizeof(uint32_t) * NQ, pop->stream));
     phase_begin(pop, PH_PACK);
-    k_order_identity<<<(d.P + 255) / 256, 256, 0, pop->stream>>>(d, g);
+    const int pb = (d.P + 255) / 256;
+    k_mlp_features<<<pb, 256, 0, pop->stream>>>(d, g, par, pop->mlp);
+    k_mlp_infer<<<pb, 256, 0, pop->stream>>>(pop->mlp, d.P, pop->mlp.pred_pack);
+    if (pop->cfg.packing == GP_PACK_MLP && d.P <= SORT_MAX) {
+        k_sort_desc<<<1, 1024, 0, pop->stream>>>(pop->mlp.pred_pack, d.P, g.order);
+    } else if (pop->cfg.packing == GP_PACK_STATIC && d.P <= SORT_MAX) {
+        k_static_key<<<pb, 256, 0, pop->stream>>>(d, g, pop->mlp);
+        k_sort_desc<<<1, 1024, 0, pop->stream>>>(pop->mlp.target, d.P, g.order);
+    } else {
+        k_order_identity<<<pb, 256, 0, pop->stream>>>(d, g);
+    }
     phase_end(pop, PH_PACK);
     phase_begin(pop, PH_WALK);
     if (d.K == 1) launch_walk<1>(pop, par); else if (d.K == 2) launch_walk<2>(pop, par); else launch_walk<4>(pop, par);
     phase_end(pop, PH_WALK);
+    // online training of the packing MLP on the levels the walks took
+    k_mlp_targets<<<pb, 256, 0, pop->stream>>>(d, g, pop->mlp);
+    k_mlp_forward_train<<<pb, 256, 0, pop->stream>>>(pop->mlp, d.P);
+    k_mlp_backward_act<<<pb, 256, 0, pop->stream>>>(pop->mlp, d.P);
+    k_mlp_loss<<<1, 256, 0, pop->stream>>>(pop->mlp, d.P);
+    k_mlp_backward_params<<<(MLP_NP + 255) / 256, 256, 0, pop->stream>>>(pop->mlp, d.P);
+    k_mlp_adam<<<(MLP_NP + 255) / 256, 256, 0, pop->stream>>>(pop->mlp, pop->mlp_lr);
+    k_mlp_bump<<<1, 32, 0, pop->stream>>>(pop->mlp);
     phase_begin(pop, PH_CACHE);
     k_pv_offsets<<<1, 1024, 0, pop->stream>>>(d, g);
     k_pv_scatter<<<gt, 256, 0, pop->stream>>>(d, g);
@@ -862,7 +954,7 @@ int gen_incremental(gp_pop* pop) {
     k_accumulate<<<1, 32, 0, pop->stream>>>(pop->cum, d.acc_ops, g.gstat, d.C, 1);
     ++pop->cum_calls;
     CK(cudaGetLastError());
-    pop->launches += 12;
+    pop->launches += 12 + 10;
     pop->have_children = false;
     g.evaluated = true;
     pop->last_kind = 1;

@@ -1,0 +1,225 @@
+// Learned work packing: a 16 -> 64 -> 64 -> 1 MLP (ReLU) predicts how many
+// levels each child's incremental walk will evaluate, from features known
+// before the walk; the walk's queue is ordered longest first (Sec. 3: long
+// tasks first; Sec. 4.1: one slow evaluation can hold up the population).
+// Trained online on the levels the walks actually took: forward, backward
+// and an Adam update in plain FP32 kernels; inference uses a BF16 copy of
+// the weights with FP32 accumulation.  The order never changes a result --
+// every child's walk is independent.
+#pragma once
+#include <cuda_bf16.h>
+#include "common.cuh"
+
+#define MLP_IN 16
+#define MLP_H 64
+// parameter layout (floats)
+#define MLP_W1 0                               // [64][16]
+#define MLP_B1 (MLP_W1 + MLP_H * MLP_IN)       // [64]
+#define MLP_W2 (MLP_B1 + MLP_H)                // [64][64]
+#define MLP_B2 (MLP_W2 + MLP_H * MLP_H)        // [64]
+#define MLP_W3 (MLP_B2 + MLP_H)                // [64]
+#define MLP_B3 (MLP_W3 + MLP_H)                // [1]
+#define MLP_NP (MLP_B3 + 1)                    // 5313
+
+struct MlpBufs {
+    float* w;          // [MLP_NP] FP32 master weights
+    float* m;          // Adam first moment
+    float* v;          // Adam second moment
+    __nv_bfloat16* wb; // BF16 inference copy
+    float* grad;       // [MLP_NP]
+    float* feat;       // [N][16]
+    float* pred;       // [N] training forward output
+    float* pred_pack;  // [N] BF16 inference output used for packing
+    float* target;     // [N]
+    float* h1;         // [N][64] post-ReLU
+    float* h2;         // [N][64]
+    float* dy;         // [N]
+    float* dh2;        // [N][64]
+    float* dh1;        // [N][64]
+    float* loss;       // [1]
+    uint32_t* step;    // [1] Adam step counter
+    uint32_t cap;
+};
+
+// ---- forward (FP32 master weights), keeping activations for the backward pass
+__global__ void k_mlp_forward_train(MlpBufs b, uint32_t n) {
+    for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
+        const float* x = b.feat + (size_t)s * MLP_IN;
+        float h1[MLP_H];
+        for (int j = 0; j < MLP_H; ++j) {
+            float a = b.w[MLP_B1 + j];
+            for (int f = 0; f < MLP_IN; ++f) a = fmaf(b.w[MLP_W1 + j * MLP_IN + f], x[f], a);
+            h1[j] = a > 0.f ? a : 0.f;
+            b.h1[(size_t)s * MLP_H + j] = h1[j];
+        }
+        float y = b.w[MLP_B3];
+        for (int j = 0; j < MLP_H; ++j) {
+            float a = b.w[MLP_B2 + j];
+            for (int k = 0; k < MLP_H; ++k) a = fmaf(b.w[MLP_W2 + j * MLP_H + k], h1[k], a);
+            const float h = a > 0.f ? a : 0.f;
+            b.h2[(size_t)s * MLP_H + j] = h;
+            y = fmaf(b.w[MLP_W3 + j], h, y);
+        }
+        b.pred[s] = y;
+        // loss = mean (y - t)^2 -> dL/dy = 2 (y - t) / n
+        b.dy[s] = 2.f * (y - b.target[s]) / (float)n;
+    }
+}
+
+// dh2 = dy * w3 * [h2 > 0]; dh1 = (W2^T dh2) * [h1 > 0]
+__global__ void k_mlp_backward_act(MlpBufs b, uint32_t n) {
+    for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
+        float dh2[MLP_H];
+        for (int j = 0; j < MLP_H; ++j) {
+            dh2[j] = (b.h2[(size_t)s * MLP_H + j] > 0.f) ? b.dy[s] * b.w[MLP_W3 + j] : 0.f;
+            b.dh2[(size_t)s * MLP_H + j] = dh2[j];
+        }
+        for (int k = 0; k < MLP_H; ++k) {
+            float a = 0.f;
+            if (b.h1[(size_t)s * MLP_H + k] > 0.f)
+                for (int j = 0; j < MLP_H; ++j) a = fmaf(b.w[MLP_W2 + j * MLP_H + k], dh2[j], a);
+            b.dh1[(size_t)s * MLP_H + k] = a;
+        }
+    }
+}
+
+// One thread per parameter: the gradient summed over the batch, in sample order.
+__global__ void k_mlp_backward_params(MlpBufs b, uint32_t n) {
+    for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < MLP_NP; p += gridDim.x * blockDim.x) {
+        float g = 0.f;
+        if (p < MLP_B1) {
+            const uint32_t j = p / MLP_IN, f = p % MLP_IN;
+            for (uint32_t s = 0; s < n; ++s) g = fmaf(b.dh1[(size_t)s * MLP_H + j], b.feat[(size_t)s * MLP_IN + f], g);
+        } else if (p < MLP_W2) {
+            const uint32_t j = p - MLP_B1;
+            for (uint32_t s = 0; s < n; ++s) g += b.dh1[(size_t)s * MLP_H + j];
+        } else if (p < MLP_B2) {
+            const uint32_t j = (p - MLP_W2) / MLP_H, k = (p - MLP_W2) % MLP_H;
+            for (uint32_t s = 0; s < n; ++s) g = fmaf(b.dh2[(size_t)s * MLP_H + j], b.h1[(size_t)s * MLP_H + k], g);
+        } else if (p < MLP_W3) {
+            const uint32_t j = p - MLP_B2;
+            for (uint32_t s = 0; s < n; ++s) g += b.dh2[(size_t)s * MLP_H + j];
+        } else if (p < MLP_B3) {
+            const uint32_t j = p - MLP_W3;
+            for (uint32_t s = 0; s < n; ++s) g = fmaf(b.dy[s], b.h2[(size_t)s * MLP_H + j], g);
+        } else {
+            for (uint32_t s = 0; s < n; ++s) g += b.dy[s];
+        }
+        b.grad[p] = g;
+    }
+}
+
+__global__ void k_mlp_loss(MlpBufs b, uint32_t n) {
+    if (blockIdx.x != 0) return;
+    __shared__ float red[256];
+    float a = 0.f;
+    for (uint32_t s = threadIdx.x; s < n; s += blockDim.x) {
+        const float e = b.pred[s] - b.target[s];
+        a += e * e;
+    }
+    red[threadIdx.x] = a;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *b.loss = red[0] / (float)(n ? n : 1);
+}
+
+// Adam (Kingma and Ba 2015), then refresh the BF16 inference copy.
+__global__ void k_mlp_adam(MlpBufs b, float lr) {
+    const uint32_t t = *b.step + 1;
+    const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+    const float c1 = 1.f - powf(b1, (float)t), c2 = 1.f - powf(b2, (float)t);
+    for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < MLP_NP; p += gridDim.x * blockDim.x) {
+        const float g = b.grad[p];
+        const float m = b1 * b.m[p] + (1.f - b1) * g;
+        const float v = b2 * b.v[p] + (1.f - b2) * g * g;
+        b.m[p] = m;
+        b.v[p] = v;
+        const float w = b.w[p] - lr * (m / c1) / (sqrtf(v / c2) + eps);
+        b.w[p] = w;
+        b.wb[p] = __float2bfloat16_rn(w);
+    }
+}
+
+__global__ void k_mlp_bump(MlpBufs b) { if (threadIdx.x == 0 && blockIdx.x == 0) *b.step += 1; }
+
+// Inference with the BF16 weights staged in shared memory.
+__global__ void __launch_bounds__(256) k_mlp_infer(MlpBufs b, uint32_t n, float* __restrict__ out) {
+    __shared__ float w[MLP_NP];
+    for (uint32_t p = threadIdx.x; p < MLP_NP; p += blockDim.x) w[p] = __bfloat162float(b.wb[p]);
+    __syncthreads();
+    for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
+        const float* x = b.feat + (size_t)s * MLP_IN;
+        float xv[MLP_IN];
+        for (int f = 0; f < MLP_IN; ++f) xv[f] = x[f];
+        float h1[MLP_H];
+        for (int j = 0; j < MLP_H; ++j) {
+            float a = w[MLP_B1 + j];
+            for (int f = 0; f < MLP_IN; ++f) a = fmaf(w[MLP_W1 + j * MLP_IN + f], xv[f], a);
+            h1[j] = a > 0.f ? a : 0.f;
+        }
+        float y = w[MLP_B3];
+        for (int j = 0; j < MLP_H; ++j) {
+            float a = w[MLP_B2 + j];
+            for (int k = 0; k < MLP_H; ++k) a = fmaf(w[MLP_W2 + j * MLP_H + k], h1[k], a);
+            y = fmaf(w[MLP_W3 + j], a > 0.f ? a : 0.f, y);
+        }
+        out[s] = y;
+    }
+}
+
+// Deterministic initialisation (He-uniform from a counter hash).
+__global__ void k_mlp_init(MlpBufs b, uint64_t seed) {
+    for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < MLP_NP; p += gridDim.x * blockDim.x) {
+        uint64_t z = seed + (p + 1) * 0x9E3779B97F4A7C15ull;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z ^= z >> 31;
+        const float u = (float)(z >> 40) * (1.0f / 16777216.0f) * 2.f - 1.f;
+        float w = 0.f;
+        if (p < MLP_B1) w = u * sqrtf(6.f / MLP_IN);
+        else if (p >= MLP_W2 && p < MLP_B2) w = u * sqrtf(6.f / MLP_H);
+        else if (p >= MLP_W3 && p < MLP_B3) w = u * sqrtf(6.f / MLP_H);
+        b.w[p] = w;
+        b.m[p] = 0.f;
+        b.v[p] = 0.f;
+        b.wb[p] = __float2bfloat16_rn(w);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) *b.step = 0;
+}
+
+// Sort n (<= 4096) keys descending with their indices: one CTA, bitonic in
+// shared memory.  Ties keep the lower index first (stable order).
+#define SORT_MAX 4096
+__global__ void __launch_bounds__(1024) k_sort_desc(const float* __restrict__ key, uint32_t n, uint32_t* __restrict__ order) {
+    __shared__ float ks[SORT_MAX];
+    __shared__ uint32_t is[SORT_MAX];
+    uint32_t m = 1;
+    while (m < n) m <<= 1;
+    for (uint32_t i = threadIdx.x; i < m; i += blockDim.x) {
+        float kv = (i < n) ? key[i] : -INFINITY;
+        if (isnan(kv)) kv = -INFINITY;
+        ks[i] = kv;
+        is[i] = i;
+    }
+    __syncthreads();
+    for (uint32_t size = 2; size <= m; size <<= 1) {
+        for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
+            for (uint32_t i = threadIdx.x; i < m; i += blockDim.x) {
+                const uint32_t j = i ^ stride;
+                if (j > i) {
+                    const bool desc = (i & size) == 0;
+                    const float a = ks[i], c = ks[j];
+                    const uint32_t ia = is[i], ic = is[j];
+                    // "a before c" in descending order with index tie-break
+                    const bool a_first = (a > c) || (a == c && ia < ic);
+                    if (desc ? !a_first : a_first) { ks[i] = c; ks[j] = a; is[i] = ic; is[j] = ia; }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) order[i] = is[i];
+}
