@@ -196,7 +196,7 @@ def gp_cache_entries(h, i: int):
 
 
 def gp_cache_value(h, i: int, j: int, C: int, boolean: bool = False) -> np.ndarray:
-    out = np.empty(1, np.uint64) if boolean else np.empty(C, np.float32)
+    out = np.empty(1, np.uint64) if boolean else np.empty(C, np.float32)   # Boolean: the 64-case word
     _check(load().gp_cache_value(h, i, j, _ptr(out), out.nbytes), h)
     return out
 

@@ -30,12 +30,13 @@ __global__ void k_build_items(DevPop d, const uint32_t* __restrict__ e_tree) {
 // Persistent warps over (item, case block) units.  The next unit's index
 // and descriptor are fetched, and its opcodes staged, while the current
 // one is interpreted (two staging buffers per warp).
-template <int K>
+template <int K, bool B>
 __global__ void __launch_bounds__(GP_WARPS * 32) k_eval_items(DevPop d) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float* kc = reinterpret_cast<float*>(smem_raw);
     const int lane = lane_id(), warp = threadIdx.x >> 5;
     fill_kc(kc, d.consts);
+    fill_kb(kc + 256);
     __syncthreads();
     unsigned char* wbase = smem_raw + SmemLayout<K>::kc_bytes + (size_t)warp * SmemLayout<K>::warp_bytes((int)d.W);
     Ictx<K> c;
@@ -43,6 +44,7 @@ __global__ void __launch_bounds__(GP_WARPS * 32) k_eval_items(DevPop d) {
     c.W = (int)d.W;
     c.maxd = (int)d.maxdepth;
     c.kc = kc;
+    c.kb = kc + 256;
     uint8_t* const stage0 = wbase + SmemLayout<K>::stack_bytes((int)d.W);   // two buffers of STAGE_BYTES
     const uint32_t gwarp = blockIdx.x * GP_WARPS + warp;
     c.g = d.ovf + (size_t)gwarp * (d.maxdepth - d.W) * 32 * K;
@@ -80,7 +82,7 @@ __global__ void __launch_bounds__(GP_WARPS * 32) k_eval_items(DevPop d) {
             for (int k = 0; k < K; ++k) st.acc[k] = 0.f;
             st.sp = 0;
             st.ok = true;
-            interp_staged<K>(stage0 + cur * STAGE_BYTES, desc.x, desc.x + desc.y, st, c);
+            interp_staged<K, B>(stage0 + cur * STAGE_BYTES, desc.x, desc.x + desc.y, st, c);
             if (!st.ok && lane == 0) set_status(d.status, ST_STACK);
             store_slot<K>(d, desc.z, cbk, st.acc);
             if (cbk == 0) ops_done += desc.y;
@@ -101,7 +103,7 @@ __global__ void __launch_bounds__(GP_WARPS * 32) k_eval_items(DevPop d) {
 // value -- then combined in order; a right child inside the same group is
 // taken from the group's own results.
 #define SKB 16
-template <int K>
+template <int K, bool B>
 __global__ void __launch_bounds__(GP_WARPS * 32) k_eval_skeleton(DevPop d) {
     const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
@@ -156,11 +158,11 @@ __global__ void __launch_bounds__(GP_WARPS * 32) k_eval_skeleton(DevPop d) {
                             if (has0) {                       // left = entry e+1 = prev
 #pragma unroll
                                 for (int k = 0; k < K; ++k) val[k] = prev[k];
-                                apply_vec<K>(op, val, o);
+                                apply_vec<K, B>(op, val, o);
                             } else {                          // right = entry e+1 = prev
 #pragma unroll
                                 for (int k = 0; k < K; ++k) val[k] = o[k];
-                                apply_vec<K>(op, val, prev);
+                                apply_vec<K, B>(op, val, prev);
                             }
                             store_slot<K>(d, slots[j], cbk, val);
                             if (cbk == 0) ++cnt;
@@ -178,7 +180,11 @@ __global__ void __launch_bounds__(GP_WARPS * 32) k_eval_skeleton(DevPop d) {
 }
 
 // Fitness of every tree from its root's cached vector: sum over cases in
-// case order of |value - target| in binary32.
+// case order of |value - target| in binary32; Boolean: wrong cases out of 64.
+__device__ __forceinline__ float bool_errors(const float* v) {
+    return (float)(__popc(__float_as_uint(v[0]) ^ mux_target_half(0)) + __popc(__float_as_uint(v[1]) ^ mux_target_half(1)));
+}
+
 __global__ void k_fitness(DevPop d) {
     const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
@@ -187,7 +193,12 @@ __global__ void k_fitness(DevPop d) {
         if (lane_id() == 0) {
             const float* v = d.slots + (size_t)d.e_slot[d.e_off[tree]] * d.Cpad;
             float f = 0.0f;
-            for (uint32_t c = 0; c < d.C; ++c) f = __fadd_rn(f, fabsf(__fsub_rn(__ldcg(v + c), d.t[c])));
+            if (d.funcset == 1u) {
+                const float w[2] = {__ldcg(v), __ldcg(v + 1)};
+                f = bool_errors(w);
+            } else {
+                for (uint32_t c = 0; c < d.C; ++c) f = __fadd_rn(f, fabsf(__fsub_rn(__ldcg(v + c), d.t[c])));
+            }
             d.fit[tree] = f;
             atomicAdd(&d.acc_ops[1], (unsigned long long)d.size[tree]);
         }

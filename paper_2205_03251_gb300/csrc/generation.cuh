@@ -430,7 +430,7 @@ struct WalkSmem {
     __host__ __device__ static size_t warp_bytes(int W) {
         return stack_bytes(W) + 2 * STAGE_BYTES + 3 * WALK_MAXLVL * sizeof(uint32_t) + 64 * sizeof(float) * K;
     }
-    __host__ __device__ static size_t total(int W, int warps) { return 256 * sizeof(float) + warps * warp_bytes(W); }
+    __host__ __device__ static size_t total(int W, int warps) { return (256 + 6 * 32) * sizeof(float) + warps * warp_bytes(W); }
 };
 
 template <int K>
@@ -452,21 +452,21 @@ __device__ __forceinline__ bool same_bits(const float (&a)[K], const float (&b)[
 }
 
 // left/right combination keeping the operand order of the node
-template <int K>
+template <int K, bool B>
 __device__ __forceinline__ void combine(uint32_t op, bool path_left, float (&v)[K], const float (&sib)[K]) {
-    if (path_left) apply_vec<K>(op, v, sib);
+    if (path_left) apply_vec<K, B>(op, v, sib);
     else {
         float t[K];
 #pragma unroll
         for (int k = 0; k < K; ++k) t[k] = sib[k];
-        apply_vec<K>(op, t, v);
+        apply_vec<K, B>(op, t, v);
 #pragma unroll
         for (int k = 0; k < K; ++k) v[k] = t[k];
     }
 }
 
 // Evaluate bytes [s, e) of `src` (a small run: e - (s & ~15) <= STAGE_BYTES).
-template <int K>
+template <int K, bool B>
 __device__ __forceinline__ void eval_run(const uint8_t* src, uint32_t s, uint32_t e, uint8_t* stage,
                                          const Ictx<K>& c, float (&out)[K], uint32_t* status) {
     __syncwarp();
@@ -479,7 +479,7 @@ __device__ __forceinline__ void eval_run(const uint8_t* src, uint32_t s, uint32_
     for (int k = 0; k < K; ++k) st.acc[k] = 0.f;
     st.sp = 0;
     st.ok = true;
-    interp_staged<K>(stage, s, e, st, c);
+    interp_staged<K, B>(stage, s, e, st, c);
     if (!st.ok && lane_id() == 0) set_status(status, ST_STACK);
 #pragma unroll
     for (int k = 0; k < K; ++k) out[k] = st.acc[k];
@@ -496,19 +496,21 @@ __device__ __forceinline__ void eval_run(const uint8_t* src, uint32_t s, uint32_
 // New values of nodes that are cached in the child are recorded in the
 // child's cache; above the stop only child-cached nodes that the mother
 // does not cache need computing.
-template <int K>
+template <int K, bool B>
 __global__ void __launch_bounds__(GP_WARPS * 32) k_walk(DevPop d, GenBufs g, CacheView par) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float* kc = reinterpret_cast<float*>(smem_raw);
     const int lane = lane_id(), warp = threadIdx.x >> 5;
     fill_kc(kc, d.consts);
+    fill_kb(kc + 256);
     __syncthreads();
-    unsigned char* wb = smem_raw + 256 * sizeof(float) + (size_t)warp * WalkSmem<K>::warp_bytes((int)d.W);
+    unsigned char* wb = smem_raw + (256 + 6 * 32) * sizeof(float) + (size_t)warp * WalkSmem<K>::warp_bytes((int)d.W);
     Ictx<K> ic;
     ic.s = reinterpret_cast<float*>(wb);
     ic.W = (int)d.W;
     ic.maxd = (int)d.maxdepth;
     ic.kc = kc;
+    ic.kb = kc + 256;
     ic.g = d.ovf + (size_t)(blockIdx.x * GP_WARPS + warp) * (d.maxdepth - d.W) * 32 * K;
     uint8_t* stA = wb + WalkSmem<K>::stack_bytes((int)d.W);
     uint8_t* stB = stA + STAGE_BYTES;
@@ -550,7 +552,7 @@ __global__ void __launch_bounds__(GP_WARPS * 32) k_walk(DevPop d, GenBufs g, Cac
             if (ef < 0) { if (lane == 0) set_error(d, ST_STRUCT, 3, i, dd, s); continue; }
             load_vec<K>(par.slots, d.Cpad, par.e_slot[ef], nv);
         } else {
-            eval_run<K>(ok_, c, c + s, stA, ic, nv, d.status);
+            eval_run<K, B>(ok_, c, c + s, stA, ic, nv, d.status);
             st_interp += s;
         }
         int32_t em = -1;
@@ -559,7 +561,7 @@ __global__ void __launch_bounds__(GP_WARPS * 32) k_walk(DevPop d, GenBufs g, Cac
             if (em < 0) { if (lane == 0) set_error(d, ST_STRUCT, 4, i, c, r); continue; }
             load_vec<K>(par.slots, d.Cpad, par.e_slot[em], ov);
         } else {
-            eval_run<K>(g.stash + g.stash_off[i], 0, r, stA, ic, ov, d.status);
+            eval_run<K, B>(g.stash + g.stash_off[i], 0, r, stA, ic, ov, d.status);
             st_interp += r;
         }
         bool stopped = same_bits<K>(nv, ov, Cn);
@@ -750,12 +752,12 @@ __global__ void __launch_bounds__(GP_WARPS * 32) k_walk(DevPop d, GenBufs g, Cac
                 if (pent < 0 || sib < 0) { if (lane == 0) set_error(d, ST_STRUCT, 7, i, p, se - ss); done = true; break; }
                 load_vec<K>(par.slots, d.Cpad, par.e_slot[sib], sv);
             } else {
-                eval_run<K>(ok_, ss, se, stA, ic, sv, d.status);
+                eval_run<K, B>(ok_, ss, se, stA, ic, sv, d.status);
                 st_interp += se - ss;
             }
-            combine<K>(op, left, ov, sv);            // mother's value at p (exact recomputation)
+            combine<K, B>(op, left, ov, sv);            // mother's value at p (exact recomputation)
             if (!stopped) {
-                combine<K>(op, left, nv, sv);
+                combine<K, B>(op, left, nv, sv);
                 if (pent >= 0) load_vec<K>(par.slots, d.Cpad, par.e_slot[pent], ov);
                 ++levels;
                 ++st_pathops;
@@ -798,7 +800,12 @@ __global__ void __launch_bounds__(GP_WARPS * 32) k_walk(DevPop d, GenBufs g, Cac
             __syncwarp();
             if (lane == 0) {
                 float fsum = 0.0f;
-                for (uint32_t cc = 0; cc < Cn; ++cc) fsum = __fadd_rn(fsum, fabsf(__fsub_rn(red[cc], d.t[cc])));
+                if (B) {
+                    fsum = (float)(__popc(__float_as_uint(red[0]) ^ mux_target_half(0)) +
+                                   __popc(__float_as_uint(red[1]) ^ mux_target_half(1)));
+                } else {
+                    for (uint32_t cc = 0; cc < Cn; ++cc) fsum = __fadd_rn(fsum, fabsf(__fsub_rn(red[cc], d.t[cc])));
+                }
                 d.fit[i] = fsum;
             }
             __syncwarp();

@@ -76,6 +76,7 @@ struct gp_pop {
     size_t smem_walk;
     MlpBufs mlp;
     float mlp_lr;
+    uint32_t cases_stat;              // test cases per value vector (64 for the Boolean word)
     int last_kind;                    // 0 full evaluation, 1 generation
 };
 
@@ -192,24 +193,24 @@ __global__ void k_scatter_trees(const uint8_t* __restrict__ src, const uint64_t*
     }
 }
 
-template <int K>
+template <int K, bool B = false>
 int setup_items_kernel(gp_pop* pop) {
     size_t smem = SmemLayout<K>::total((int)pop->d.W, GP_WARPS);
-    CK(cudaFuncSetAttribute(k_eval_items<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    CK(cudaFuncSetAttribute(k_eval_items<K, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int nb = 0;
-    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_eval_items<K>, GP_WARPS * 32, smem));
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_eval_items<K, B>, GP_WARPS * 32, smem));
     if (nb < 1) nb = 1;
     pop->grid_items = nb * pop->nsm;
     pop->smem_items = smem;
     return GP_OK;
 }
 
-template <int K>
+template <int K, bool B = false>
 int setup_walk_kernel(gp_pop* pop) {
     size_t smem = WalkSmem<K>::total((int)pop->d.W, GP_WARPS);
-    CK(cudaFuncSetAttribute(k_walk<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    CK(cudaFuncSetAttribute(k_walk<K, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int nb = 0;
-    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_walk<K>, GP_WARPS * 32, smem));
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_walk<K, B>, GP_WARPS * 32, smem));
     if (nb < 1) nb = 1;
     // the walk shares the interpreter's per-warp overflow stacks
     pop->grid_walk = nb * pop->nsm;
@@ -218,17 +219,19 @@ int setup_walk_kernel(gp_pop* pop) {
     return GP_OK;
 }
 
-template <int K>
+template <int K, bool B = false>
 void launch_items(gp_pop* pop) {
-    k_eval_items<K><<<pop->grid_items, GP_WARPS * 32, pop->smem_items, pop->stream>>>(pop->d);
+    k_eval_items<K, B><<<pop->grid_items, GP_WARPS * 32, pop->smem_items, pop->stream>>>(pop->d);
 }
-template <int K>
+template <int K, bool B = false>
 void launch_skeleton(gp_pop* pop) {
-    k_eval_skeleton<K><<<pop->grid_warps, GP_WARPS * 32, 0, pop->stream>>>(pop->d);
+    k_eval_skeleton<K, B><<<pop->grid_warps, GP_WARPS * 32, 0, pop->stream>>>(pop->d);
 }
 
-void launch_by_k(gp_pop* pop, void (*f1)(gp_pop*), void (*f2)(gp_pop*), void (*f4)(gp_pop*)) {
-    if (pop->d.K == 1) f1(pop); else if (pop->d.K == 2) f2(pop); else f4(pop);
+// dispatch on cases per lane; the Boolean set always runs with K = 1
+void launch_by_k(gp_pop* pop, void (*f1)(gp_pop*), void (*f2)(gp_pop*), void (*f4)(gp_pop*), void (*fb)(gp_pop*)) {
+    if (pop->d.funcset == GP_BOOL_MUX6) fb(pop);
+    else if (pop->d.K == 1) f1(pop); else if (pop->d.K == 2) f2(pop); else f4(pop);
 }
 
 // Add the last evaluation's counters to the running totals (device side, no sync).
@@ -342,15 +345,15 @@ int run_full(gp_pop* pop) {
     k_build_items<<<gthreads, 256, 0, pop->stream>>>(d, pop->sb.e_tree);
     phase_end(pop, PH_STRUCT);
     phase_begin(pop, PH_ITEMS);
-    launch_by_k(pop, launch_items<1>, launch_items<2>, launch_items<4>);
+    launch_by_k(pop, launch_items<1>, launch_items<2>, launch_items<4>, launch_items<1, true>);
     phase_end(pop, PH_ITEMS);
     phase_begin(pop, PH_SKEL);
-    launch_by_k(pop, launch_skeleton<1>, launch_skeleton<2>, launch_skeleton<4>);
+    launch_by_k(pop, launch_skeleton<1>, launch_skeleton<2>, launch_skeleton<4>, launch_skeleton<1, true>);
     phase_end(pop, PH_SKEL);
     phase_begin(pop, PH_FIT);
     k_fitness<<<pop->grid_warps, GP_WARPS * 32, 0, pop->stream>>>(d);
     phase_end(pop, PH_FIT);
-    k_accumulate<<<1, 32, 0, pop->stream>>>(pop->cum, d.acc_ops, pop->gb.gstat, d.C, 0);
+    k_accumulate<<<1, 32, 0, pop->stream>>>(pop->cum, d.acc_ops, pop->gb.gstat, pop->cases_stat, 0);
     ++pop->cum_calls;
     CK(cudaGetLastError());
     return GP_OK;
@@ -372,9 +375,10 @@ int gp_pop_create(const gp_config* cfg_in, const float* x, const float* targets,
     gp_config cfg = *cfg_in;
     if (cfg.pop_size == 0) return fail(nullptr, GP_EINVAL, "pop_size must be > 0");
     if (cfg.funcset != GP_FP32_ARITH && cfg.funcset != GP_BOOL_MUX6) return fail(nullptr, GP_EINVAL, "bad funcset");
-    if (cfg.funcset == GP_BOOL_MUX6) return fail(nullptr, GP_EINVAL, "Boolean function set not built in this library");
+    const bool boolean = cfg.funcset == GP_BOOL_MUX6;
+    if (boolean) { cfg.n_cases = 2; cfg.cases_per_lane = 1; }   // 64 cases: two 32-bit words
     if (cfg.n_cases == 0 || cfg.n_cases > (1u << 20)) return fail(nullptr, GP_EINVAL, "n_cases out of range");
-    if (!x || !targets) return fail(nullptr, GP_EINVAL, "null x/targets");
+    if (!boolean && (!x || !targets)) return fail(nullptr, GP_EINVAL, "null x/targets");
     if (cfg.cache_threshold == 0) cfg.cache_threshold = 1024;
     uint32_t T = cfg.cache_threshold;
     if (T < 2 || T > GP_B || (T & (T - 1))) return fail(nullptr, GP_EINVAL, "cache_threshold must be a power of two in [2, 1024]");
@@ -403,6 +407,7 @@ int gp_pop_create(const gp_config* cfg_in, const float* x, const float* targets,
     pop->launches = 0;
     pop->e_total_h = nullptr;
     pop->last_kind = 0;
+    pop->cases_stat = boolean ? 64u : cfg.n_cases;
     memset(&pop->stats, 0, sizeof pop->stats);
     memset(pop->ev_count, 0, sizeof pop->ev_count);
     int rc = GP_OK;
@@ -481,7 +486,8 @@ int gp_pop_create(const gp_config* cfg_in, const float* x, const float* targets,
 
     // interpreter launch shape and its overflow stacks
     {
-        int r = (K == 1) ? setup_items_kernel<1>(pop) : (K == 2) ? setup_items_kernel<2>(pop) : setup_items_kernel<4>(pop);
+        int r = (cfg.funcset == GP_BOOL_MUX6) ? setup_items_kernel<1, true>(pop)
+                : (K == 1) ? setup_items_kernel<1>(pop) : (K == 2) ? setup_items_kernel<2>(pop) : setup_items_kernel<4>(pop);
         if (r) return bail(r);
         d.ovf_warps = (uint32_t)pop->grid_items * GP_WARPS;
         DA2(d.ovf, (size_t)d.ovf_warps * (d.maxdepth - d.W) * 32 * K);
@@ -517,7 +523,8 @@ int gp_pop_create(const gp_config* cfg_in, const float* x, const float* targets,
     }
     // incremental walk launch shape
     {
-        int r = (K == 1) ? setup_walk_kernel<1>(pop) : (K == 2) ? setup_walk_kernel<2>(pop) : setup_walk_kernel<4>(pop);
+        int r = (cfg.funcset == GP_BOOL_MUX6) ? setup_walk_kernel<1, true>(pop)
+                : (K == 1) ? setup_walk_kernel<1>(pop) : (K == 2) ? setup_walk_kernel<2>(pop) : setup_walk_kernel<4>(pop);
         if (r) return bail(r);
         pop->grid_walk_max = pop->grid_walk;
         if (cfg.walk_warps) {
@@ -539,8 +546,8 @@ int gp_pop_create(const gp_config* cfg_in, const float* x, const float* targets,
     }
 
     // inputs
-    std::vector<float> xp(d.Cpad, 0.0f);
-    memcpy(xp.data(), x, sizeof(float) * d.C);
+    std::vector<float> xp(d.Cpad, 0.0f), tp(d.C, 0.0f);
+    if (!boolean) { memcpy(xp.data(), x, sizeof(float) * d.C); memcpy(tp.data(), targets, sizeof(float) * d.C); }
     std::vector<uint32_t> bufs(P);
     for (uint32_t i = 0; i < P; ++i) bufs[i] = i;
     uint8_t* stage = nullptr;
@@ -554,7 +561,7 @@ int gp_pop_create(const gp_config* cfg_in, const float* x, const float* targets,
     CK2(cudaMemcpyAsync(stage, ops + offsets[0], total, cudaMemcpyHostToDevice, pop->stream));
     CK2(cudaMemcpyAsync(stage_off, off0.data(), sizeof(uint64_t) * (P + 1), cudaMemcpyHostToDevice, pop->stream));
     CK2(cudaMemcpyAsync(d.x, xp.data(), sizeof(float) * d.Cpad, cudaMemcpyHostToDevice, pop->stream));
-    CK2(cudaMemcpyAsync(d.t, targets, sizeof(float) * d.C, cudaMemcpyHostToDevice, pop->stream));
+    CK2(cudaMemcpyAsync(d.t, tp.data(), sizeof(float) * d.C, cudaMemcpyHostToDevice, pop->stream));
     CK2(cudaMemcpyAsync(d.consts, consts, sizeof(float) * GP_NCONST, cudaMemcpyHostToDevice, pop->stream));
     CK2(cudaMemcpyAsync(d.buf, bufs.data(), sizeof(uint32_t) * P, cudaMemcpyHostToDevice, pop->stream));
     CK2(cudaMemsetAsync(d.status, 0, 4 * sizeof(uint32_t), pop->stream));
@@ -662,15 +669,23 @@ int gp_root_values(const gp_pop* cpop, void* host_out, size_t bytes) {
     gp_pop* pop = const_cast<gp_pop*>(cpop);
     if (!pop || !host_out) return GP_EINVAL;
     const DevPop& d = pop->d;
-    if (bytes < (size_t)d.P * d.C * sizeof(float)) return fail(pop, GP_EINVAL, "host buffer too small");
+    const bool boolean = d.funcset == GP_BOOL_MUX6;
+    const size_t need = boolean ? (size_t)d.P * sizeof(uint64_t) : (size_t)d.P * d.C * sizeof(float);
+    if (bytes < need) return fail(pop, GP_EINVAL, "host buffer too small");
     int rc = check_status(pop);
     if (rc) return rc;
     std::vector<uint32_t> eoff(d.P + 1), slot(1);
     CK(cudaMemcpy(eoff.data(), d.e_off, sizeof(uint32_t) * (d.P + 1), cudaMemcpyDeviceToHost));
-    float* out = static_cast<float*>(host_out);
     for (uint32_t i = 0; i < d.P; ++i) {
         CK(cudaMemcpy(slot.data(), d.e_slot + eoff[i], sizeof(uint32_t), cudaMemcpyDeviceToHost));
-        CK(cudaMemcpy(out + (size_t)i * d.C, d.slots + (size_t)slot[0] * d.Cpad, sizeof(float) * d.C, cudaMemcpyDeviceToHost));
+        if (boolean) {
+            uint32_t w[2];
+            CK(cudaMemcpy(w, d.slots + (size_t)slot[0] * d.Cpad, sizeof w, cudaMemcpyDeviceToHost));
+            static_cast<uint64_t*>(host_out)[i] = (uint64_t)w[0] | ((uint64_t)w[1] << 32);
+        } else {
+            CK(cudaMemcpy(static_cast<float*>(host_out) + (size_t)i * d.C, d.slots + (size_t)slot[0] * d.Cpad,
+                          sizeof(float) * d.C, cudaMemcpyDeviceToHost));
+        }
     }
     return GP_OK;
 }
@@ -722,6 +737,7 @@ int gp_cache_value(const gp_pop* cpop, uint32_t i, uint32_t j, void* host_out, s
     if (j >= eo[1] - eo[0]) return fail(pop, GP_EINVAL, "entry %u out of range", j);
     uint32_t slot = 0;
     CK(cudaMemcpy(&slot, pop->d.e_slot + eo[0] + j, sizeof slot, cudaMemcpyDeviceToHost));
+    // Boolean: the two 32-bit halves of the 64-case word (low half first)
     CK(cudaMemcpy(host_out, pop->d.slots + (size_t)slot * pop->d.Cpad, sizeof(float) * pop->d.C, cudaMemcpyDeviceToHost));
     return GP_OK;
 }
@@ -824,16 +840,16 @@ int gp_get_stats(const gp_pop* cpop, gp_stats* out) {
     if (pop->last_kind == 0) {
         unsigned long long acc[4];
         CK(cudaMemcpy(acc, pop->d.acc_ops, sizeof acc, cudaMemcpyDeviceToHost));
-        s.actual_ops = acc[0] * pop->d.C;
-        s.equivalent_ops = acc[1] * pop->d.C;
-        s.interp_ops = acc[2] * pop->d.C;
+        s.actual_ops = acc[0] * pop->cases_stat;
+        s.equivalent_ops = acc[1] * pop->cases_stat;
+        s.interp_ops = acc[2] * pop->cases_stat;
         s.children = 0;
     } else {
         unsigned long long gs[NGSTAT];
         CK(cudaMemcpy(gs, pop->gb.gstat, sizeof gs, cudaMemcpyDeviceToHost));
-        s.equivalent_ops = gs[G_EQUIV] * pop->d.C;
-        s.interp_ops = gs[G_INTERP] * pop->d.C;
-        s.actual_ops = (gs[G_INTERP] + gs[G_PATHOPS]) * pop->d.C;
+        s.equivalent_ops = gs[G_EQUIV] * pop->cases_stat;
+        s.interp_ops = gs[G_INTERP] * pop->cases_stat;
+        s.actual_ops = (gs[G_INTERP] + gs[G_PATHOPS]) * pop->cases_stat;
         s.crossover_bytes = gs[G_XOBYTES];
         s.path_levels = gs[G_LEVELS];
         s.stopped = (uint32_t)gs[G_STOPPED];
@@ -855,9 +871,9 @@ void swap_generation(gp_pop* pop) {
     std::swap(d.fit, g.pfit);
 }
 
-template <int K>
+template <int K, bool B = false>
 void launch_walk(gp_pop* pop, const CacheView& par) {
-    k_walk<K><<<pop->grid_walk, GP_WARPS * 32, pop->smem_walk, pop->stream>>>(pop->d, pop->gb, par);
+    k_walk<K, B><<<pop->grid_walk, GP_WARPS * 32, pop->smem_walk, pop->stream>>>(pop->d, pop->gb, par);
 }
 
 }  // namespace
@@ -920,7 +936,8 @@ int gen_incremental(gp_pop* pop) {
     }
     phase_end(pop, PH_PACK);
     phase_begin(pop, PH_WALK);
-    if (d.K == 1) launch_walk<1>(pop, par); else if (d.K == 2) launch_walk<2>(pop, par); else launch_walk<4>(pop, par);
+    if (d.funcset == GP_BOOL_MUX6) launch_walk<1, true>(pop, par);
+    else if (d.K == 1) launch_walk<1>(pop, par); else if (d.K == 2) launch_walk<2>(pop, par); else launch_walk<4>(pop, par);
     phase_end(pop, PH_WALK);
     // online training of the packing MLP on the levels the walks took
     k_mlp_targets<<<pb, 256, 0, pop->stream>>>(d, g, pop->mlp);
@@ -951,7 +968,7 @@ int gen_incremental(gp_pop* pop) {
     k_entry_links<<<gt, 256, 0, pop->stream>>>(d, pop->sb);
     k_child_sizes<<<(d.P + 255) / 256, 256, 0, pop->stream>>>(d, g);
     phase_end(pop, PH_CACHE);
-    k_accumulate<<<1, 32, 0, pop->stream>>>(pop->cum, d.acc_ops, g.gstat, d.C, 1);
+    k_accumulate<<<1, 32, 0, pop->stream>>>(pop->cum, d.acc_ops, g.gstat, pop->cases_stat, 1);
     ++pop->cum_calls;
     CK(cudaGetLastError());
     pop->launches += 12 + 10;

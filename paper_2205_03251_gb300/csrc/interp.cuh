@@ -53,8 +53,20 @@ __device__ __forceinline__ float apply_op(uint32_t op, float a, float b) {
     }
 }
 
-template <int K>
+// Boolean 6-multiplexer set: 0 AND, 1 OR, 2 NAND, 3 NOR on 32-case halves
+// of the 64-case word (the value bits travel in float registers).
+__device__ __forceinline__ uint32_t bool_op(uint32_t op, uint32_t x, uint32_t y) {
+    uint32_t r = (op & 1u) ? (x | y) : (x & y);
+    return (op & 2u) ? ~r : r;
+}
+
+template <int K, bool B = false>
 __device__ __forceinline__ void apply_vec(uint32_t op, float (&a)[K], const float (&b)[K]) {
+    if constexpr (B) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) a[k] = __uint_as_float(bool_op(op, __float_as_uint(a[k]), __float_as_uint(b[k])));
+        return;
+    }
     if (op < 2) {
         if (op == 0) {
 #pragma unroll
@@ -78,9 +90,22 @@ struct Ictx {
     float* s;            // shared stack: W entries x 32 lanes x K (this lane's K at s + lane*K)
     float* g;            // global overflow: (maxd - W) entries x 32 lanes x K
     const float* kc;     // shared constant table indexed by opcode (kc[5..255])
+    const float* kb;     // Boolean: shared input words, kb[(op-4)*32 + lane] for op 4..9
     int W, maxd;
     float xv[K];         // this lane's test-case inputs
 };
+
+template <int K, bool B>
+__device__ __forceinline__ void leaf_value(uint32_t op, float (&acc)[K], const Ictx<K>& c, int lane) {
+    if constexpr (B) {
+        const uint32_t j = (op - 4u) < 6u ? op - 4u : 0u;
+        acc[0] = c.kb[j * 32 + lane];
+    } else {
+        const float cv = c.kc[op];
+#pragma unroll
+        for (int k = 0; k < K; ++k) acc[k] = (op == 4) ? c.xv[k] : cv;
+    }
+}
 
 template <int K>
 struct Istate {
@@ -90,16 +115,14 @@ struct Istate {
 };
 
 // One node, any stack depth (bounds checked).
-template <int K>
+template <int K, bool B = false>
 __device__ __forceinline__ void step_checked(uint32_t op, Istate<K>& st, const Ictx<K>& c, int lane) {
     if (op >= 4) {
         if (st.sp < c.W) vstore<K>(c.s + ((size_t)st.sp * 32 + lane) * K, st.acc);
         else if (st.sp < c.maxd) vstore<K>(c.g + ((size_t)(st.sp - c.W) * 32 + lane) * K, st.acc);
         else st.ok = false;
         if (st.sp < c.maxd) ++st.sp;
-        const float cv = c.kc[op];
-#pragma unroll
-        for (int k = 0; k < K; ++k) st.acc[k] = (op == 4) ? c.xv[k] : cv;
+        leaf_value<K, B>(op, st.acc, c, lane);
     } else {
         float r[K];
         if (st.sp <= 0) {
@@ -111,24 +134,22 @@ __device__ __forceinline__ void step_checked(uint32_t op, Istate<K>& st, const I
             if (st.sp < c.W) vload<K>(c.s + ((size_t)st.sp * 32 + lane) * K, r);
             else vload<K>(c.g + ((size_t)(st.sp - c.W) * 32 + lane) * K, r);
         }
-        apply_vec<K>(op, st.acc, r);
+        apply_vec<K, B>(op, st.acc, r);
     }
 }
 
 // One node when the whole stack access stays inside the shared window.
-template <int K>
-__device__ __forceinline__ void step_fast(uint32_t op, float (&acc)[K], float*& sptr, const Ictx<K>& c) {
+template <int K, bool B = false>
+__device__ __forceinline__ void step_fast(uint32_t op, float (&acc)[K], float*& sptr, const Ictx<K>& c, int lane) {
     if (op >= 4) {
         vstore<K>(sptr, acc);
         sptr += 32 * K;
-        const float cv = c.kc[op];
-#pragma unroll
-        for (int k = 0; k < K; ++k) acc[k] = (op == 4) ? c.xv[k] : cv;
+        leaf_value<K, B>(op, acc, c, lane);
     } else {
         sptr -= 32 * K;
         float r[K];
         vload<K>(sptr, r);
-        apply_vec<K>(op, acc, r);
+        apply_vec<K, B>(op, acc, r);
     }
 }
 
@@ -136,7 +157,7 @@ __device__ __forceinline__ void step_fast(uint32_t op, float (&acc)[K], float*& 
 // s & ~15 on) right to left; afterwards st.acc is the value of the subtree
 // starting at s.  Words of four nodes are run without per-node stack
 // checks when the depth leaves room for four pushes or pops.
-template <int K>
+template <int K, bool B = false>
 __device__ __forceinline__ void interp_staged(const uint8_t* stage, uint32_t s, uint32_t e,
                                               Istate<K>& st, const Ictx<K>& c) {
     const int lane = lane_id();
@@ -145,29 +166,29 @@ __device__ __forceinline__ void interp_staged(const uint8_t* stage, uint32_t s, 
     // head: single nodes down to a multiple of 4
     while (p > s && (p & 3u)) {
         --p;
-        step_checked<K>(stage[p - a], st, c, lane);
+        step_checked<K, B>(stage[p - a], st, c, lane);
     }
     const uint32_t* wp = reinterpret_cast<const uint32_t*>(stage);
     while (p >= s + 4) {
         const uint32_t w = wp[(p - 4 - a) >> 2];
         if (st.sp >= 4 && st.sp + 4 <= c.W) {
             float* sptr = c.s + ((size_t)st.sp * 32 + lane) * K;
-            step_fast<K>(w >> 24, st.acc, sptr, c);
-            step_fast<K>((w >> 16) & 0xFFu, st.acc, sptr, c);
-            step_fast<K>((w >> 8) & 0xFFu, st.acc, sptr, c);
-            step_fast<K>(w & 0xFFu, st.acc, sptr, c);
+            step_fast<K, B>(w >> 24, st.acc, sptr, c, lane);
+            step_fast<K, B>((w >> 16) & 0xFFu, st.acc, sptr, c, lane);
+            step_fast<K, B>((w >> 8) & 0xFFu, st.acc, sptr, c, lane);
+            step_fast<K, B>(w & 0xFFu, st.acc, sptr, c, lane);
             st.sp = (int)((sptr - c.s - lane * K) / (32 * K));
         } else {
-            step_checked<K>(w >> 24, st, c, lane);
-            step_checked<K>((w >> 16) & 0xFFu, st, c, lane);
-            step_checked<K>((w >> 8) & 0xFFu, st, c, lane);
-            step_checked<K>(w & 0xFFu, st, c, lane);
+            step_checked<K, B>(w >> 24, st, c, lane);
+            step_checked<K, B>((w >> 16) & 0xFFu, st, c, lane);
+            step_checked<K, B>((w >> 8) & 0xFFu, st, c, lane);
+            step_checked<K, B>(w & 0xFFu, st, c, lane);
         }
         p -= 4;
     }
     while (p > s) {
         --p;
-        step_checked<K>(stage[p - a], st, c, lane);
+        step_checked<K, B>(stage[p - a], st, c, lane);
     }
 }
 
@@ -217,11 +238,36 @@ __device__ __forceinline__ void store_slot(const DevPop& d, uint32_t slot, uint3
 // Shared-memory layout of a CTA running the interpreter.
 template <int K>
 struct SmemLayout {
-    static constexpr size_t kc_bytes = 256 * sizeof(float);
+    static constexpr size_t kc_bytes = (256 + 6 * 32) * sizeof(float);   // constants, then Boolean inputs
     __host__ __device__ static size_t stack_bytes(int W) { return (size_t)W * 32 * K * sizeof(float); }
     __host__ __device__ static size_t warp_bytes(int W) { return stack_bytes(W) + 2 * STAGE_BYTES; }
     __host__ __device__ static size_t total(int W, int warps) { return kc_bytes + warps * warp_bytes(W); }
 };
+
+// Boolean 6-multiplexer: 64 cases in one word, case i has a0 = bit 0, a1 =
+// bit 1, d0..d3 = bits 2..5 of i; input j's word has bit i set iff bit j of
+// i is set.  Lane 0 holds cases 0..31, lane 1 cases 32..63 (32-bit halves).
+__device__ __forceinline__ uint32_t mux_input_half(uint32_t j, uint32_t half) {
+    uint32_t w = 0;
+    for (uint32_t b = 0; b < 32; ++b) w |= (((b + 32u * half) >> j) & 1u) << b;
+    return w;
+}
+__device__ __forceinline__ uint32_t mux_target_half(uint32_t half) {
+    uint32_t w = 0;
+    for (uint32_t b = 0; b < 32; ++b) {
+        const uint32_t i = b + 32u * half;
+        const uint32_t addr = (i & 1u) + 2u * ((i >> 1) & 1u);
+        w |= ((i >> (2u + addr)) & 1u) << b;
+    }
+    return w;
+}
+// kb[j*32 + lane] = input word j's half for lanes 0 and 1, zero elsewhere
+__device__ __forceinline__ void fill_kb(float* kb) {
+    for (int i = threadIdx.x; i < 6 * 32; i += blockDim.x) {
+        const uint32_t j = i / 32, l = i % 32;
+        kb[i] = __uint_as_float(l < 2 ? mux_input_half(j, l) : 0u);
+    }
+}
 
 // Fill the opcode-indexed constant table (kc[5 + i] = consts[i]).
 __device__ __forceinline__ void fill_kc(float* kc, const float* consts) {
