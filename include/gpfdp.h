@@ -209,6 +209,70 @@ int gp_mlp_eval_grad(const float* w, const float* x, const float* y, uint32_t n,
 /* Statistics of the last gp_eval_full / gp_eval_incremental.  Synchronising. */
 int gp_get_stats(const gp_pop* pop, gp_stats* out);
 
+/*
+ * Graph mode (on = 1): size both cache sets for reserve_entries cached
+ * nodes (exactly that many when nonzero; 0 = at least twice the current
+ * count plus 64 per tree) and stop the host-side regrowing, so that
+ * gp_crossover, gp_eval_incremental (with stats NULL) and gp_eval_full
+ * issue no synchronising call and can be captured into a CUDA graph on the
+ * population's stream (gp_graph_capture).  A cache that outgrows the
+ * reservation stops every later kernel and is reported as GP_ENOMEM by the
+ * next synchronising call; the population must then be reloaded.  If the
+ * current population's cache set was resized it must be evaluated again
+ * (gp_eval_full) before the next gp_crossover.  on = 0 restores regrowing
+ * and drops a captured graph.  Synchronising.
+ */
+int gp_set_graph_mode(gp_pop* pop, int on, uint64_t reserve_entries);
+
+/*
+ * Capture n_generations (even, >= 2) generations -- gp_crossover then
+ * gp_eval_incremental each -- into one CUDA graph on the population's
+ * stream.  Nothing runs during the capture.  Each gp_graph_launch replays
+ * them: the r-th replay (r = 0, 1, ...) breeds generations
+ * first_generation + r * n_generations + k, k = 0 .. n_generations - 1, so
+ * replays give the same populations, bit for bit, as the eager calls with
+ * those generation numbers.  Needs graph mode and an evaluated population;
+ * a later cache regrow or gp_set_graph_mode(pop, 0, 0) drops the graph.
+ * gp_graph_launch is asynchronous; errors raised by the replayed kernels
+ * (e.g. GP_ENOMEM when the reservation is exceeded, after which the
+ * population must be reloaded) surface at the next synchronising call.
+ */
+int gp_graph_capture(gp_pop* pop, uint32_t first_generation, uint32_t n_generations);
+int gp_graph_launch(gp_pop* pop);
+
+/* One autotuner candidate and what it measured. */
+typedef struct {
+    uint32_t cases_per_lane;    /* K: test cases per lane, i.e. 32 x K cases per warp task */
+    uint32_t cache_threshold;   /* T: subtree size from which values are cached (the subtree split) */
+    int32_t  status;            /* GP_OK, or the error that ruled the candidate out */
+    uint32_t identical;         /* 1 when its fitness equals the first valid candidate's, bit for bit */
+    float    ms_full;           /* one gp_eval_full, device milliseconds */
+    float    ms_generation;     /* one generation (crossover + incremental), mean over a graph replay */
+} gp_tune_result;
+
+/*
+ * Autotune the work splits for a population: for every pair of
+ * ks[0..n_k) x ts[0..n_t) (cases_per_lane x cache_threshold) build the
+ * population described by base and the host data (same rules as
+ * gp_pop_create), time one gp_eval_full and, when generations > 0 (even),
+ * one replay of a captured graph of that many generations (after one
+ * warm-up replay), and check that its fitness matches the first candidate's
+ * bit for bit.  results[a * n_t + b] receives candidate (ks[a], ts[b]);
+ * *best = base with the fastest valid candidate's two fields (fastest per
+ * generation when generations > 0, else fastest full evaluation).  One
+ * candidate's population exists at a time.  Synchronising.  Returns
+ * GP_ENOMEM when no candidate could run.  The paper has no counterpart:
+ * its CPU interpreter has one fixed layout.
+ */
+int gp_autotune(const gp_config* base, const float* x, const float* targets, const float* consts,
+                const uint8_t* ops, const uint64_t* offsets, const uint32_t* ks, uint32_t n_k,
+                const uint32_t* ts, uint32_t n_t, uint32_t generations, void* stream,
+                gp_tune_result* results, gp_config* best);
+
+/* The autotuner's choice rule on its own: index of the fastest candidate
+ * with status GP_OK and identical = 1 (ties: the earlier), or -1. */
+int gp_autotune_pick(const gp_tune_result* results, uint32_t n, uint32_t generations);
+
 /* Turn per-phase CUDA-event timing on (1) or off (0); either resets the
  * recorded phase times. */
 int gp_set_profiling(gp_pop* pop, int on);

@@ -51,6 +51,15 @@ class GpStats(ctypes.Structure):
         return d
 
 
+class GpTuneResult(ctypes.Structure):
+    _fields_ = [("cases_per_lane", ctypes.c_uint32), ("cache_threshold", ctypes.c_uint32),
+                ("status", ctypes.c_int32), ("identical", ctypes.c_uint32),
+                ("ms_full", ctypes.c_float), ("ms_generation", ctypes.c_float)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 PHASES = ("structure", "items", "skeleton", "fitness", "crossover", "walk", "cache", "pack")
 
 _lib = None
@@ -92,6 +101,12 @@ def load() -> ctypes.CDLL:
         "gp_eval_small_noalloc": (i32, [vp, ctypes.c_size_t, vp, u32, vp, vp, vp, u32, vp, vp, vp,
                                         ctypes.POINTER(u32)]),
         "gp_set_profiling": (i32, [vp, i32]),
+        "gp_set_graph_mode": (i32, [vp, i32, u64]),
+        "gp_graph_capture": (i32, [vp, u32, u32]),
+        "gp_graph_launch": (i32, [vp]),
+        "gp_autotune": (i32, [ctypes.POINTER(GpConfig), vp, vp, vp, vp, vp, vp, u32, vp, u32, u32, vp,
+                              ctypes.POINTER(GpTuneResult), ctypes.POINTER(GpConfig)]),
+        "gp_autotune_pick": (i32, [ctypes.POINTER(GpTuneResult), u32, u32]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -264,6 +279,68 @@ def gp_mlp_eval_grad(w, x, y):
     return float(loss[0]), grad
 
 
+def gp_set_graph_mode(h, on: bool, reserve_entries: int = 0):
+    _check(load().gp_set_graph_mode(h, 1 if on else 0, reserve_entries), h)
+
+
+def gp_graph_capture(h, first_generation: int, n_generations: int):
+    _check(load().gp_graph_capture(h, first_generation, n_generations), h)
+
+
+def gp_graph_launch(h):
+    _check(load().gp_graph_launch(h), h)
+
+
+def gp_autotune(cfg: GpConfig, x, targets, consts, ops, offsets, ks, ts, generations: int, stream=None):
+    """Time every (cases_per_lane, cache_threshold) pair of ks x ts on this
+    population; returns (best GpConfig, list of GpTuneResult dicts)."""
+    lib = load()
+    x = np.ascontiguousarray(x, np.float32)
+    targets = np.ascontiguousarray(targets, np.float32)
+    consts = np.ascontiguousarray(consts, np.float32)
+    ops = np.ascontiguousarray(ops, np.uint8)
+    offsets = np.ascontiguousarray(offsets, np.uint64)
+    ks = np.ascontiguousarray(ks, np.uint32)
+    ts = np.ascontiguousarray(ts, np.uint32)
+    if stream is None:
+        stream = _default_stream()
+    elif hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    res = (GpTuneResult * (len(ks) * len(ts)))()
+    best = GpConfig()
+    _check(lib.gp_autotune(ctypes.byref(cfg), _ptr(x), _ptr(targets), _ptr(consts), _ptr(ops), _ptr(offsets),
+                           _ptr(ks), len(ks), _ptr(ts), len(ts), generations, ctypes.c_void_p(stream),
+                           res, ctypes.byref(best)))
+    return best, [r.as_dict() for r in res]
+
+
+def gp_autotune_pick(results: list[dict], generations: int) -> int:
+    """The autotuner's choice rule applied to a list of result dicts."""
+    arr = (GpTuneResult * max(1, len(results)))()
+    for j, r in enumerate(results):
+        for k, _ in GpTuneResult._fields_:
+            setattr(arr[j], k, r.get(k, 0))
+    return load().gp_autotune_pick(arr, len(results), generations)
+
+
+def autotune(x, t, consts, ops, off, *, max_nodes: int, ks=(1, 2, 4), ts=(64, 256, 1024),
+             generations: int = 2, boolean: bool = False, tournament: int = 7, packing: int = GP_PACK_STATIC,
+             cache_budget_bytes: int = 0, seed: int = 0, stream=None):
+    """Autotune the case and subtree splits for a population; returns
+    (keyword arguments for Population with the chosen split, result table)."""
+    off = np.asarray(off, np.uint64)
+    C = 64 if boolean else len(x)
+    if boolean:
+        x = np.zeros(1, np.float32)
+        t = np.zeros(1, np.float32)
+    cfg = GpConfig(pop_size=len(off) - 1, n_cases=C, max_nodes=max_nodes,
+                   funcset=GP_BOOL_MUX6 if boolean else GP_FP32_ARITH, cache_threshold=1024,
+                   tournament=tournament, packing=packing, cases_per_lane=0,
+                   cache_budget_bytes=cache_budget_bytes, seed=seed & (2**64 - 1))
+    best, table = gp_autotune(cfg, x, t, consts, ops, off, ks, ts, generations, stream)
+    return {"cases_per_lane": best.cases_per_lane, "cache_threshold": best.cache_threshold}, table
+
+
 def gp_set_profiling(h, on: bool):
     _check(load().gp_set_profiling(h, 1 if on else 0), h)
 
@@ -341,3 +418,12 @@ class Population:
 
     def set_profiling(self, on: bool):
         gp_set_profiling(self.h, on)
+
+    def set_graph_mode(self, on: bool, reserve_entries: int = 0):
+        gp_set_graph_mode(self.h, on, reserve_entries)
+
+    def graph_capture(self, first_generation: int, n_generations: int):
+        gp_graph_capture(self.h, first_generation, n_generations)
+
+    def graph_launch(self):
+        gp_graph_launch(self.h)

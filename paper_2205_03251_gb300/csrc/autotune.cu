@@ -1,0 +1,118 @@
+// Project-written autotuner for the two splits of the evaluation work:
+// cases_per_lane (how many test cases each lane carries, i.e. the case
+// tile of one warp: 32 x K cases) and cache_threshold (the subtree size
+// from which node values are cached, i.e. where trees are cut into the
+// warp-sized subtree tasks of the interpreter and the levels of the
+// incremental walk).  Each candidate is measured on the caller's own
+// population: a full evaluation, then a captured graph of generations, both
+// timed with CUDA events on the population's stream.  Results never depend
+// on the split -- every case is computed by the same binary32 operations in
+// the same order -- and the tuner checks that too: each candidate's fitness
+// vector is compared bit for bit with the first one's.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+#include <vector>
+#include "../../include/gpfdp.h"
+
+namespace {
+
+// time the work queued by fn on `stream`, in milliseconds (synchronising)
+template <typename F>
+int timed_ms(cudaStream_t stream, float* ms, F&& fn) {
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
+        if (a) cudaEventDestroy(a);
+        cudaGetLastError();
+        return GP_ECUDA;
+    }
+    cudaEventRecord(a, stream);
+    int rc = fn();
+    cudaEventRecord(b, stream);
+    cudaError_t e = cudaEventSynchronize(b);
+    if (rc == GP_OK && e != cudaSuccess) rc = GP_ECUDA;
+    if (rc == GP_OK) cudaEventElapsedTime(ms, a, b);
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    return rc;
+}
+
+int run_candidate(const gp_config* cfg, const float* x, const float* targets, const float* consts,
+                  const uint8_t* ops, const uint64_t* offsets, uint32_t generations, cudaStream_t stream,
+                  gp_tune_result* res, std::vector<float>& fit) {
+    gp_pop* pop = nullptr;
+    int rc = gp_pop_create(cfg, x, targets, consts, ops, offsets, stream, &pop);
+    if (rc) return rc;
+    // first evaluation: loads the kernels and sizes the cache (may regrow)
+    rc = gp_eval_full(pop);
+    if (!rc) rc = gp_fitness(pop, fit.data(), cfg->pop_size);
+    // graph mode with the cache pre-sized from that evaluation
+    if (!rc && generations) rc = gp_set_graph_mode(pop, 1, 0);
+    float ms = 0.f;
+    if (!rc) rc = timed_ms(stream, &ms, [&] { return gp_eval_full(pop); });
+    res->ms_full = ms;
+    if (!rc && generations) {
+        rc = gp_graph_capture(pop, 0, generations);
+        // one replay to warm up, then the timed one: generations G .. 2G-1
+        if (!rc) rc = gp_graph_launch(pop);
+        if (!rc) rc = gp_fitness(pop, fit.data(), cfg->pop_size);
+        if (!rc) rc = timed_ms(stream, &ms, [&] { return gp_graph_launch(pop); });
+        if (!rc) rc = gp_fitness(pop, fit.data(), cfg->pop_size);
+        res->ms_generation = rc ? 0.f : ms / (float)generations;
+    }
+    gp_pop_destroy(pop);
+    return rc;
+}
+
+}  // namespace
+
+extern "C" {
+
+int gp_autotune_pick(const gp_tune_result* results, uint32_t n, uint32_t generations) {
+    if (!results) return -1;
+    int best = -1;
+    for (uint32_t j = 0; j < n; ++j) {
+        const gp_tune_result& r = results[j];
+        if (r.status != GP_OK || !r.identical) continue;
+        const float key = generations ? r.ms_generation : r.ms_full;
+        const float bk = best < 0 ? 0.f : (generations ? results[best].ms_generation : results[best].ms_full);
+        if (best < 0 || key < bk) best = (int)j;   // ties keep the earlier candidate
+    }
+    return best;
+}
+
+int gp_autotune(const gp_config* base, const float* x, const float* targets, const float* consts,
+                const uint8_t* ops, const uint64_t* offsets, const uint32_t* ks, uint32_t n_k,
+                const uint32_t* ts, uint32_t n_t, uint32_t generations, void* stream,
+                gp_tune_result* results, gp_config* best) {
+    if (!base || !consts || !ops || !offsets || !ks || !ts || !results || !best || n_k == 0 || n_t == 0)
+        return GP_EINVAL;
+    if (generations & 1u) return GP_EINVAL;
+    const uint32_t n = n_k * n_t;
+    std::vector<float> ref(base->pop_size), fit(base->pop_size);
+    bool have_ref = false;
+    for (uint32_t a = 0; a < n_k; ++a) {
+        for (uint32_t b = 0; b < n_t; ++b) {
+            gp_tune_result& r = results[a * n_t + b];
+            memset(&r, 0, sizeof r);
+            r.cases_per_lane = ks[a];
+            r.cache_threshold = ts[b];
+            gp_config cfg = *base;
+            cfg.cases_per_lane = ks[a];
+            cfg.cache_threshold = ts[b];
+            r.status = run_candidate(&cfg, x, targets, consts, ops, offsets, generations,
+                                     static_cast<cudaStream_t>(stream), &r, fit);
+            if (r.status != GP_OK) continue;
+            if (!have_ref) { ref = fit; have_ref = true; }
+            r.identical = memcmp(ref.data(), fit.data(), sizeof(float) * base->pop_size) == 0 ? 1u : 0u;
+        }
+    }
+    const int j = gp_autotune_pick(results, n, generations);
+    if (j < 0) return GP_ENOMEM;
+    *best = *base;
+    best->cases_per_lane = results[j].cases_per_lane;
+    best->cache_threshold = results[j].cache_threshold;
+    return GP_OK;
+}
+
+}  // extern "C"

@@ -27,6 +27,7 @@ struct DevPop {
     uint32_t P, C, Cpad, K, ncb, T, cap, funcset;
     uint32_t Ecap, Scap, maxdepth, W;      // entries, slots, interpreter stack bound, smem stack depth
     uint32_t ovf_warps;                    // warps with an overflow stack region
+    uint32_t strict_cap;                   // 1: a cache larger than Ecap is an error (no host regrow)
     // population
     uint8_t* arena;      // nbuf * cap bytes
     uint32_t* buf;       // [P] buffer holding individual i
@@ -62,6 +63,13 @@ struct DevPop {
 
 __device__ __forceinline__ uint32_t warp_bcast(uint32_t v, int src) { return __shfl_sync(FULL, v, src); }
 __device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
+
+// In graph mode the cache arrays are never regrown: a kernel that finds the
+// entry count above Ecap raises ST_ENTRIES, and every later kernel of the
+// (captured) sequence that indexes a cache or a plan returns at once.
+__device__ __forceinline__ bool halted(const DevPop& d) {
+    return d.strict_cap && (*reinterpret_cast<const volatile uint32_t*>(d.status) & ST_ENTRIES);
+}
 
 __device__ __forceinline__ void set_status(uint32_t* st, uint32_t bit) { atomicOr(st, bit); }
 

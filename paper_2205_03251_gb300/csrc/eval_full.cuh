@@ -9,6 +9,7 @@
 // children -- the whole subtree when both children are small, else the
 // small child (its value is parked in e's slot until the skeleton pass).
 __global__ void k_build_items(DevPop d, const uint32_t* __restrict__ e_tree) {
+    if (halted(d)) return;
     const uint32_t ne = d.e_off[d.P];
     if (ne > d.Ecap) return;
     for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < ne; e += gridDim.x * blockDim.x) {
@@ -32,6 +33,7 @@ __global__ void k_build_items(DevPop d, const uint32_t* __restrict__ e_tree) {
 // one is interpreted (two staging buffers per warp).
 template <int K, bool B>
 __global__ void __launch_bounds__(GP_WARPS * 32) k_eval_items(DevPop d) {
+    if (halted(d)) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float* kc = reinterpret_cast<float*>(smem_raw);
     const int lane = lane_id(), warp = threadIdx.x >> 5;
@@ -105,6 +107,7 @@ __global__ void __launch_bounds__(GP_WARPS * 32) k_eval_items(DevPop d) {
 #define SKB 16
 template <int K, bool B>
 __global__ void __launch_bounds__(GP_WARPS * 32) k_eval_skeleton(DevPop d) {
+    if (halted(d)) return;
     const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
     const int lane = lane_id();
@@ -186,6 +189,7 @@ __device__ __forceinline__ float bool_errors(const float* v) {
 }
 
 __global__ void k_fitness(DevPop d) {
+    if (halted(d)) return;
     const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
     if (d.e_off[d.P] > d.Ecap) return;

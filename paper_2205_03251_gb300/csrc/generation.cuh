@@ -62,8 +62,10 @@ struct GenBufs {
     uint32_t* order;                 // [P] walk order
     unsigned long long* gstat;       // [NGSTAT]
     uint32_t max_nodes, tsize;
+    float* wscr;                     // [walk warps][2][Cpad] running values when a vector spans several case blocks
     uint64_t seed;
     uint32_t gen;
+    const uint32_t* gen_add;         // device word added to gen (generations replayed by a captured graph)
     bool evaluated;
 };
 
@@ -161,17 +163,19 @@ __device__ __forceinline__ uint4 load16u(const uint8_t* p) {
 // parent (draws 2T+2a, 2T+2a+1) whose child fits max_nodes; otherwise the
 // child is a copy of its mother.
 __global__ void k_plan(DevPop d, GenBufs g, CacheView par) {
+    if (halted(d)) return;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < d.P; i += gridDim.x * blockDim.x) {
         const uint32_t T = g.tsize;
-        const uint32_t m = tournament(g.pfit, d.P, T, g.seed, g.gen, i, 0);
-        const uint32_t f = tournament(g.pfit, d.P, T, g.seed, g.gen, i, T);
+        const uint32_t gen = g.gen + *g.gen_add;
+        const uint32_t m = tournament(g.pfit, d.P, T, g.seed, gen, i, 0);
+        const uint32_t f = tournament(g.pfit, d.P, T, g.seed, gen, i, T);
         const uint32_t sm = g.psize[m], sf = g.psize[f];
         const uint8_t* om = d.arena + (size_t)g.pbuf[m] * d.cap;
         const uint8_t* of = d.arena + (size_t)g.pbuf[f] * d.cap;
         uint32_t fl = F_CLONE, cc = 0, rr = sm, dd = 0, ss = sm, ff = m;
         for (uint32_t a = 0; a < 8; ++a) {
-            const uint32_t c1 = (uint32_t)below(draw(g.seed, g.gen, i, 2 * T + 2 * a), sm);
-            const uint32_t d1 = (uint32_t)below(draw(g.seed, g.gen, i, 2 * T + 2 * a + 1), sf);
+            const uint32_t c1 = (uint32_t)below(draw(g.seed, gen, i, 2 * T + 2 * a), sm);
+            const uint32_t d1 = (uint32_t)below(draw(g.seed, gen, i, 2 * T + 2 * a + 1), sf);
             const uint32_t r1 = subtree_size_at(d, par, m, om, sm, c1);
             const uint32_t s1 = subtree_size_at(d, par, f, of, sf, d1);
             if ((uint64_t)sm - r1 + s1 <= g.max_nodes) { fl = 0; cc = c1; rr = r1; dd = d1; ss = s1; ff = f; break; }
@@ -211,6 +215,7 @@ __device__ __forceinline__ uint64_t block_excl_scan(uint64_t v, uint64_t* ws, ui
 // most HALO_MAX (Fig. 2), every other child is copied into a free buffer
 // (Fig. 1).  Buffers of parents without an in-place child are freed.
 __global__ void __launch_bounds__(1024) k_assign(DevPop d, GenBufs g) {
+    if (halted(d)) return;
     __shared__ uint64_t ws[32];
     __shared__ uint64_t carry[5];
     if (threadIdx.x < 5) carry[threadIdx.x] = 0;
@@ -292,6 +297,7 @@ __global__ void __launch_bounds__(1024) k_assign(DevPop d, GenBufs g) {
 // Donated subtrees (all children) and removed subtrees below the threshold
 // copied out before any buffer is written (Sec. 5: fatherless crossover).
 __global__ void k_gather(DevPop d, GenBufs g) {
+    if (halted(d)) return;
     if (g.frag_off[d.P] > g.frag_cap || g.stash_off[d.P] > g.stash_cap) return;
     for (uint32_t i = blockIdx.x; i < d.P; i += gridDim.x) {
         if (g.flags[i] & F_CLONE) continue;
@@ -315,6 +321,7 @@ __global__ void k_gather(DevPop d, GenBufs g) {
 // Children built in a free buffer: mother head, donated subtree, mother
 // tail (Fig. 1), 16 destination bytes per thread.
 __global__ void k_copy_children(DevPop d, GenBufs g) {
+    if (halted(d)) return;
     if (g.frag_off[d.P] > g.frag_cap) return;
     for (uint32_t i = blockIdx.x; i < d.P; i += gridDim.x) {
         const uint32_t fl = g.flags[i];
@@ -368,6 +375,7 @@ __device__ __forceinline__ void shift_block_geom(const DevPop& d, const GenBufs&
 }
 
 __global__ void k_save_halo(DevPop d, GenBufs g) {
+    if (halted(d)) return;
     const uint32_t nb = g.shift_off[d.P];
     if (nb > g.shift_cap) return;
     for (uint32_t b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += gridDim.x * blockDim.x) {
@@ -384,6 +392,7 @@ __global__ void k_save_halo(DevPop d, GenBufs g) {
 }
 
 __global__ void __launch_bounds__(256) k_shift(DevPop d, GenBufs g) {
+    if (halted(d)) return;
     __shared__ uint8_t sb[SHIFT_BS];
     const uint32_t nb = g.shift_off[d.P];
     if (nb > g.shift_cap) return;
@@ -410,6 +419,7 @@ __global__ void __launch_bounds__(256) k_shift(DevPop d, GenBufs g) {
 
 // Donated subtree written into the in-place children (after the move).
 __global__ void k_write_frags(DevPop d, GenBufs g) {
+    if (halted(d)) return;
     if (g.frag_off[d.P] > g.frag_cap) return;
     for (uint32_t i = blockIdx.x; i < d.P; i += gridDim.x) {
         const uint32_t fl = g.flags[i];
@@ -434,9 +444,10 @@ struct WalkSmem {
 };
 
 template <int K>
-__device__ __forceinline__ void load_vec(const float* slots, uint32_t Cpad, uint32_t slot, float (&v)[K]) {
+__device__ __forceinline__ void load_vec(const float* slots, uint32_t Cpad, uint32_t slot, float (&v)[K],
+                                         uint32_t cb = 0) {
     const int lane = lane_id();
-    const float* p = slots + (size_t)slot * Cpad + lane;
+    const float* p = slots + (size_t)slot * Cpad + cb * 32 * K + lane;
 #pragma unroll
     for (int k = 0; k < K; ++k) v[k] = __ldcg(p + k * 32);
 }
@@ -449,6 +460,20 @@ __device__ __forceinline__ bool same_bits(const float (&a)[K], const float (&b)[
     for (int k = 0; k < K; ++k)
         if ((uint32_t)(k * 32 + lane) < C && __float_as_uint(a[k]) != __float_as_uint(b[k])) ok = false;
     return __all_sync(FULL, ok);
+}
+
+// case block cb of a running value vector kept in the warp's scratch row
+template <int K>
+__device__ __forceinline__ void store_blk(float* row, uint32_t cb, const float (&v)[K]) {
+    float* p = row + cb * 32 * K + lane_id();
+#pragma unroll
+    for (int k = 0; k < K; ++k) p[k * 32] = v[k];
+}
+template <int K>
+__device__ __forceinline__ void load_blk(const float* row, uint32_t cb, float (&v)[K]) {
+    const float* p = row + cb * 32 * K + lane_id();
+#pragma unroll
+    for (int k = 0; k < K; ++k) v[k] = p[k * 32];
 }
 
 // left/right combination keeping the operand order of the node
@@ -498,6 +523,7 @@ __device__ __forceinline__ void eval_run(const uint8_t* src, uint32_t s, uint32_
 // does not cache need computing.
 template <int K, bool B>
 __global__ void __launch_bounds__(GP_WARPS * 32) k_walk(DevPop d, GenBufs g, CacheView par) {
+    if (halted(d)) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float* kc = reinterpret_cast<float*>(smem_raw);
     const int lane = lane_id(), warp = threadIdx.x >> 5;
@@ -521,6 +547,15 @@ __global__ void __launch_bounds__(GP_WARPS * 32) k_walk(DevPop d, GenBufs g, Cac
     load_cases<K>(d, 0, ic.xv);
     const uint32_t T = d.T;
     const uint32_t Cn = d.C;
+    // value vectors longer than one case block (32 K cases): the warp walks
+    // each level block by block and parks the running values in a scratch row
+    const uint32_t ncb = d.ncb;
+    float* wsn = nullptr;
+    float* wso = nullptr;
+    if (ncb > 1) {
+        wsn = g.wscr + (size_t)(blockIdx.x * GP_WARPS + warp) * 2 * d.Cpad;
+        wso = wsn + d.Cpad;
+    }
     unsigned long long st_interp = 0, st_levels = 0, st_stopped = 0, st_pathops = 0;
 
     for (;;) {
@@ -547,37 +582,44 @@ __global__ void __launch_bounds__(GP_WARPS * 32) k_walk(DevPop d, GenBufs g, Cac
 
         // ---- level 0: donated subtree vs removed subtree
         float nv[K], ov[K];
+        int32_t ef = -1, em = -1;
         if (s >= T || dd == 0) {
-            const int32_t ef = find_exact(par.e_pos, fe0, fe1, dd);
+            ef = find_exact(par.e_pos, fe0, fe1, dd);
             if (ef < 0) { if (lane == 0) set_error(d, ST_STRUCT, 3, i, dd, s); continue; }
-            load_vec<K>(par.slots, d.Cpad, par.e_slot[ef], nv);
-        } else {
-            eval_run<K, B>(ok_, c, c + s, stA, ic, nv, d.status);
-            st_interp += s;
         }
-        int32_t em = -1;
         if (r >= T || c == 0) {
             em = find_exact(par.e_pos, me0, me1, c);
             if (em < 0) { if (lane == 0) set_error(d, ST_STRUCT, 4, i, c, r); continue; }
-            load_vec<K>(par.slots, d.Cpad, par.e_slot[em], ov);
-        } else {
-            eval_run<K, B>(g.stash + g.stash_off[i], 0, r, stA, ic, ov, d.status);
-            st_interp += r;
         }
-        bool stopped = same_bits<K>(nv, ov, Cn);
+        // the donated subtree becomes the child's root (always cached) but the
+        // father does not cache it: keep the value computed at level 0
+        const bool root_rec = (c == 0 && s < T && dd != 0);
+        uint32_t rslot = 0;
+        if (root_rec) {
+            if (lane == 0) rslot = atomicAdd(&g.misc[M_PV], 1u);
+            rslot = __shfl_sync(FULL, rslot, 0);
+            if (rslot >= g.pvcap) { if (lane == 0) set_status(d.status, ST_PATH); continue; }
+        }
+        bool eq0 = true;
+        for (uint32_t cb = 0; cb < ncb; ++cb) {
+            if (ncb > 1) load_cases<K>(d, cb, ic.xv);
+            if (ef >= 0) load_vec<K>(par.slots, d.Cpad, par.e_slot[ef], nv, cb);
+            else { eval_run<K, B>(ok_, c, c + s, stA, ic, nv, d.status); st_interp += s; }
+            if (em >= 0) load_vec<K>(par.slots, d.Cpad, par.e_slot[em], ov, cb);
+            else { eval_run<K, B>(g.stash + g.stash_off[i], 0, r, stA, ic, ov, d.status); st_interp += r; }
+            eq0 = same_bits<K>(nv, ov, Cn - cb * 32 * K) && eq0;
+            if (root_rec) {
+                float* dst = g.pv_val + (size_t)rslot * d.Cpad + cb * 32 * K + lane;
+#pragma unroll
+                for (int kk = 0; kk < K; ++kk) dst[kk * 32] = nv[kk];
+            }
+            if (ncb > 1) { store_blk<K>(wsn, cb, nv); store_blk<K>(wso, cb, ov); }
+        }
+        bool stopped = eq0;
         int32_t stop_level = stopped ? 0 : -1;
         uint32_t levels = 0;
-        if (c == 0 && s < T && dd != 0) {
-            // the donated subtree becomes the child's root (always cached) but the
-            // father does not cache it: keep the value computed at level 0
-            uint32_t slot = 0;
-            if (lane == 0) slot = atomicAdd(&g.misc[M_PV], 1u);
-            slot = __shfl_sync(FULL, slot, 0);
-            if (slot >= g.pvcap) { if (lane == 0) set_status(d.status, ST_PATH); continue; }
-            float* dst = g.pv_val + (size_t)slot * d.Cpad + lane;
-#pragma unroll
-            for (int kk = 0; kk < K; ++kk) dst[kk * 32] = nv[kk];
-            if (lane == 0) { g.pv_rec[slot] = make_uint4(i, npv, 0u, slot | 0x80000000u); g.pv_end[slot] = s; }
+        if (root_rec) {
+            if (lane == 0) { g.pv_rec[rslot] = make_uint4(i, npv, 0u, rslot | 0x80000000u); g.pv_end[rslot] = s; }
             ++npv;
             ++nins_i;
         }
@@ -746,34 +788,47 @@ __global__ void __launch_bounds__(GP_WARPS * 32) k_walk(DevPop d, GenBufs g, Cac
             const uint32_t ss = left ? qend : p + 1;
             const uint32_t se = left ? pend : q;
             if (se <= ss || se > nk) { if (lane == 0) set_error(d, ST_STRUCT, 6, i, p, (se << 0)); break; }
-            float sv[K];
+            int32_t sib = -1;
             if (se - ss >= T) {
-                const int32_t sib = left ? par.e_c1[pent] : par.e_c0[pent];
-                if (pent < 0 || sib < 0) { if (lane == 0) set_error(d, ST_STRUCT, 7, i, p, se - ss); done = true; break; }
-                load_vec<K>(par.slots, d.Cpad, par.e_slot[sib], sv);
-            } else {
-                eval_run<K, B>(ok_, ss, se, stA, ic, sv, d.status);
-                st_interp += se - ss;
+                sib = (pent < 0) ? -1 : (left ? par.e_c1[pent] : par.e_c0[pent]);
+                if (sib < 0) { if (lane == 0) set_error(d, ST_STRUCT, 7, i, p, se - ss); done = true; break; }
             }
-            combine<K, B>(op, left, ov, sv);            // mother's value at p (exact recomputation)
+            bool lvl_eq = true;
+            for (uint32_t cb = 0; cb < ncb; ++cb) {
+                if (ncb > 1) { load_cases<K>(d, cb, ic.xv); load_blk<K>(wsn, cb, nv); load_blk<K>(wso, cb, ov); }
+                float sv[K];
+                if (sib >= 0) load_vec<K>(par.slots, d.Cpad, par.e_slot[sib], sv, cb);
+                else { eval_run<K, B>(ok_, ss, se, stA, ic, sv, d.status); st_interp += se - ss; }
+                combine<K, B>(op, left, ov, sv);            // mother's value at p (exact recomputation)
+                if (!stopped) {
+                    combine<K, B>(op, left, nv, sv);
+                    if (pent >= 0) load_vec<K>(par.slots, d.Cpad, par.e_slot[pent], ov, cb);
+                    lvl_eq = same_bits<K>(nv, ov, Cn - cb * 32 * K) && lvl_eq;
+                }
+                if (ncb > 1) { store_blk<K>(wsn, cb, nv); store_blk<K>(wso, cb, ov); }
+            }
             if (!stopped) {
-                combine<K, B>(op, left, nv, sv);
-                if (pent >= 0) load_vec<K>(par.slots, d.Cpad, par.e_slot[pent], ov);
                 ++levels;
                 ++st_pathops;
-                if (same_bits<K>(nv, ov, Cn)) { stopped = true; stop_level = (int32_t)level; }
+                if (lvl_eq) { stopped = true; stop_level = (int32_t)level; }
             }
             // record the child's value here when the child caches this node and the mother's
-            // cache cannot supply it (disrupted, or not cached in the mother)
-            if (child_cached && (!same_bits<K>(nv, ov, Cn) || pent < 0)) {
+            // cache cannot supply it (disrupted, or not cached in the mother); above the
+            // stop only small ancestors (pent < 0) get here
+            if (child_cached && (!lvl_eq || pent < 0)) {
                 uint32_t slot = 0;
                 if (lane == 0) slot = atomicAdd(&g.misc[M_PV], 1u);
                 slot = __shfl_sync(FULL, slot, 0);
                 if (slot >= g.pvcap) { if (lane == 0) set_status(d.status, ST_PATH); done = true; break; }
                 float* dst = g.pv_val + (size_t)slot * d.Cpad + lane;
-                const float (&val)[K] = stopped ? ov : nv;
+                if (ncb == 1) {
+                    const float (&val)[K] = stopped ? ov : nv;
 #pragma unroll
-                for (int kk = 0; kk < K; ++kk) dst[kk * 32] = val[kk];
+                    for (int kk = 0; kk < K; ++kk) dst[kk * 32] = val[kk];
+                } else {
+                    const float* row = stopped ? wso : wsn;
+                    for (uint32_t e = 0; e < ncb * K; ++e) dst[e * 32] = row[e * 32 + lane];
+                }
                 if (lane == 0) {
                     g.pv_rec[slot] = make_uint4(i, npv, p, slot | (pent < 0 ? 0x80000000u : 0u));
                     g.pv_end[slot] = pend;
@@ -795,16 +850,22 @@ __global__ void __launch_bounds__(GP_WARPS * 32) k_walk(DevPop d, GenBufs g, Cac
             if (lane == 0) d.fit[i] = g.pfit[m];
             ++st_stopped;
         } else {
+            // case cc of the child's root vector sits at vec[cc] in either layout
+            const float* vec = red;
+            if (ncb == 1) {
 #pragma unroll
-            for (int kk = 0; kk < K; ++kk) red[kk * 32 + lane] = nv[kk];
+                for (int kk = 0; kk < K; ++kk) red[kk * 32 + lane] = nv[kk];
+            } else {
+                vec = wsn;
+            }
             __syncwarp();
             if (lane == 0) {
                 float fsum = 0.0f;
                 if (B) {
-                    fsum = (float)(__popc(__float_as_uint(red[0]) ^ mux_target_half(0)) +
-                                   __popc(__float_as_uint(red[1]) ^ mux_target_half(1)));
+                    fsum = (float)(__popc(__float_as_uint(vec[0]) ^ mux_target_half(0)) +
+                                   __popc(__float_as_uint(vec[1]) ^ mux_target_half(1)));
                 } else {
-                    for (uint32_t cc = 0; cc < Cn; ++cc) fsum = __fadd_rn(fsum, fabsf(__fsub_rn(red[cc], d.t[cc])));
+                    for (uint32_t cc = 0; cc < Cn; ++cc) fsum = __fadd_rn(fsum, fabsf(__fsub_rn(vec[cc], d.t[cc])));
                 }
                 d.fit[i] = fsum;
             }
@@ -824,6 +885,7 @@ __global__ void __launch_bounds__(GP_WARPS * 32) k_walk(DevPop d, GenBufs g, Cac
 
 // Walk records grouped per child in walk order (positions decreasing).
 __global__ void __launch_bounds__(1024) k_pv_offsets(DevPop d, GenBufs g) {
+    if (halted(d)) return;
     __shared__ uint64_t ws[32];
     __shared__ uint64_t carry;
     if (threadIdx.x == 0) carry = 0;
@@ -839,6 +901,7 @@ __global__ void __launch_bounds__(1024) k_pv_offsets(DevPop d, GenBufs g) {
 }
 
 __global__ void k_pv_scatter(DevPop d, GenBufs g) {
+    if (halted(d)) return;
     const uint32_t n = min(g.misc[M_PV], g.pvcap);
     for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
         const uint4 rec = g.pv_rec[r];
@@ -884,6 +947,7 @@ __device__ __forceinline__ bool drops(const CacheView& par, int32_t e, int32_t d
 }
 
 __global__ void k_merge_count(DevPop d, GenBufs g, CacheView par) {
+    if (halted(d)) return;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < d.P; i += gridDim.x * blockDim.x) {
         const uint32_t m = g.mother[i];
         const uint32_t me0 = par.e_off[m], me1 = par.e_off[m + 1];
@@ -911,6 +975,7 @@ __global__ void k_merge_count(DevPop d, GenBufs g, CacheView par) {
 
 // Exclusive scan of the counts into the children's entry offsets.
 __global__ void __launch_bounds__(1024) k_merge_offsets(DevPop d, GenBufs g) {
+    if (halted(d)) return;
     __shared__ uint64_t ws[32];
     __shared__ uint64_t carry;
     if (threadIdx.x == 0) carry = 0;
@@ -925,6 +990,7 @@ __global__ void __launch_bounds__(1024) k_merge_offsets(DevPop d, GenBufs g) {
     if (threadIdx.x == 0) {
         d.e_off[d.P] = (uint32_t)carry;
         *d.e_total = (uint32_t)carry;
+        if (d.strict_cap && carry > d.Ecap) set_status(d.status, ST_ENTRIES);
     }
 }
 
@@ -954,6 +1020,7 @@ __device__ __forceinline__ int32_t find_record(const GenBufs& g, uint32_t i, uin
 
 // One warp per child writes its entries (position, end, value source).
 __global__ void k_merge_write(DevPop d, GenBufs g, CacheView par) {
+    if (halted(d)) return;
     const int lane = lane_id();
     const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
@@ -1069,6 +1136,7 @@ __global__ void k_merge_write(DevPop d, GenBufs g, CacheView par) {
 
 // Value vectors of the children's entries: one warp per entry, lanes over cases.
 __global__ void k_copy_values(DevPop d, GenBufs g, CacheView par) {
+    if (halted(d)) return;
     const uint32_t ne = d.e_off[d.P];
     if (ne > d.Ecap) return;
     const int lane = lane_id();
@@ -1085,6 +1153,7 @@ __global__ void k_copy_values(DevPop d, GenBufs g, CacheView par) {
 
 // equivalent-op count of the children (every opcode on every case)
 __global__ void k_child_sizes(DevPop d, GenBufs g) {
+    if (halted(d)) return;
     unsigned long long s = 0;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < d.P; i += gridDim.x * blockDim.x) s += d.size[i];
     for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(FULL, s, o);
@@ -1097,6 +1166,7 @@ __global__ void k_child_sizes(DevPop d, GenBufs g) {
 // fitness, cache sizes and the spread of their root value vectors, a clone
 // flag and a constant.
 __global__ void k_mlp_features(DevPop d, GenBufs g, CacheView par, MlpBufs b) {
+    if (halted(d)) return;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < d.P; i += gridDim.x * blockDim.x) {
         const uint32_t m = g.mother[i], f = g.father[i], c = g.cpos[i], r = g.rsz[i], dd = g.dpos[i], s = g.ssz[i];
         const float sm = (float)g.psize[m], sf = (float)g.psize[f];
@@ -1135,16 +1205,19 @@ __global__ void k_mlp_features(DevPop d, GenBufs g, CacheView par, MlpBufs b) {
 
 // static packing key: the mother's size (largest first)
 __global__ void k_static_key(DevPop d, GenBufs g, MlpBufs b) {
+    if (halted(d)) return;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < d.P; i += gridDim.x * blockDim.x)
         b.target[i] = (float)g.psize[g.mother[i]];
 }
 
 // training targets: log2(1 + levels the walk evaluated)
 __global__ void k_mlp_targets(DevPop d, GenBufs g, MlpBufs b) {
+    if (halted(d)) return;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < d.P; i += gridDim.x * blockDim.x)
         b.target[i] = log2f(1.f + (float)g.plen[i]);
 }
 
 __global__ void k_order_identity(DevPop d, GenBufs g) {
+    if (halted(d)) return;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < d.P; i += gridDim.x * blockDim.x) g.order[i] = i;
 }

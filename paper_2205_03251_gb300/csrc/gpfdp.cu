@@ -78,6 +78,11 @@ struct gp_pop {
     float mlp_lr;
     uint32_t cases_stat;              // test cases per value vector (64 for the Boolean word)
     int last_kind;                    // 0 full evaluation, 1 generation
+    uint32_t* gwords;                 // device: [0] = 0, [1] = generations replayed by the captured graph
+    cudaGraphExec_t gexec;            // captured generation loop (graph mode)
+    uint32_t graph_n;                 // generations per replay
+    uint32_t graph_launches;          // kernel launches per replay
+    cudaStream_t cap_stream;          // private capture stream when the population runs on the legacy stream
 };
 
 namespace {
@@ -234,6 +239,11 @@ void launch_by_k(gp_pop* pop, void (*f1)(gp_pop*), void (*f2)(gp_pop*), void (*f
     else if (pop->d.K == 1) f1(pop); else if (pop->d.K == 2) f2(pop); else f4(pop);
 }
 
+// Advance the generation offset of a captured generation loop (last node of the graph).
+__global__ void k_graph_advance(uint32_t* ctr, uint32_t n) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) *ctr += n;
+}
+
 // Add the last evaluation's counters to the running totals (device side, no sync).
 __global__ void k_accumulate(unsigned long long* cum, const unsigned long long* acc, const unsigned long long* gst,
                              uint32_t C, int kind) {
@@ -275,6 +285,7 @@ int grow_set(gp_pop* pop, int which, uint32_t ecap) {
         return fail(pop, GP_ENOMEM, "cache needs %llu value vectors, budget allows %llu",
                     (unsigned long long)scap, (unsigned long long)pop->slot_limit);
     if (pop->stream) cudaStreamSynchronize(pop->stream); else cudaDeviceSynchronize();
+    if (pop->gexec) { cudaGraphExecDestroy(pop->gexec); pop->gexec = nullptr; pop->graph_n = 0; }
     for (void* p : c.allocs) cudaFree(p);
     c.allocs.clear();
     auto al = [&](auto** ptr, size_t count) -> bool {
@@ -312,13 +323,16 @@ int run_structure(gp_pop* pop) {
     k_scan_top<<<1, SCAN_TILE, 0, pop->stream>>>(d, pop->sb);
     k_scan_apply<<<scan_grid, SCAN_TILE, 0, pop->stream>>>(d, pop->sb);
     // entry count known: grow the cache arrays if this population needs more
-    CK(cudaMemcpyAsync(pop->e_total_h, d.e_total, sizeof(uint32_t), cudaMemcpyDeviceToHost, pop->stream));
-    CK(cudaStreamSynchronize(pop->stream));
-    if (*pop->e_total_h > d.Ecap) {
-        uint64_t want = (uint64_t)*pop->e_total_h + *pop->e_total_h / 4 + 64;
-        if (want > pop->slot_limit) want = pop->slot_limit;
-        int r = grow_cache(pop, (uint32_t)want);
-        if (r) return r;
+    // (in graph mode the arrays are pre-sized and an overflow is reported instead)
+    if (!d.strict_cap) {
+        CK(cudaMemcpyAsync(pop->e_total_h, d.e_total, sizeof(uint32_t), cudaMemcpyDeviceToHost, pop->stream));
+        CK(cudaStreamSynchronize(pop->stream));
+        if (*pop->e_total_h > d.Ecap) {
+            uint64_t want = (uint64_t)*pop->e_total_h + *pop->e_total_h / 4 + 64;
+            if (want > pop->slot_limit) want = pop->slot_limit;
+            int r = grow_cache(pop, (uint32_t)want);
+            if (r) return r;
+        }
     }
     k_tree_entry_offsets<<<(d.P + 256) / 256, 256, 0, pop->stream>>>(d, pop->sb);
     k_emit_entries<<<pop->grid_warps, GP_WARPS * 32, 0, pop->stream>>>(d, pop->sb);
@@ -410,7 +424,9 @@ int gp_pop_create(const gp_config* cfg_in, const float* x, const float* targets,
     pop->cases_stat = boolean ? 64u : cfg.n_cases;
     memset(&pop->stats, 0, sizeof pop->stats);
     memset(pop->ev_count, 0, sizeof pop->ev_count);
-    int rc = GP_OK;
+    pop->gexec = nullptr;
+    pop->graph_n = 0;
+    pop->cap_stream = nullptr;
     auto bail = [&](int code) { gp_pop_destroy(pop); return code; };
     cudaError_t ce = cudaGetDevice(&pop->dev);
     if (ce != cudaSuccess) { g_create_error = cudaGetErrorString(ce); delete pop; return GP_ECUDA; }
@@ -500,6 +516,9 @@ int gp_pop_create(const gp_config* cfg_in, const float* x, const float* targets,
         g.seed = cfg.seed;
         g.gen = 0;
         g.evaluated = false;
+        DA2(pop->gwords, 2);
+        cudaMemset(pop->gwords, 0, 2 * sizeof(uint32_t));
+        g.gen_add = pop->gwords;
         g.frag_cap = (uint64_t)P * d.cap;
         g.stash_cap = (uint64_t)P * (T + 16);
         g.shift_cap = (uint32_t)((uint64_t)P * d.cap / SHIFT_BS + P);
@@ -527,6 +546,8 @@ int gp_pop_create(const gp_config* cfg_in, const float* x, const float* targets,
                 : (K == 1) ? setup_walk_kernel<1>(pop) : (K == 2) ? setup_walk_kernel<2>(pop) : setup_walk_kernel<4>(pop);
         if (r) return bail(r);
         pop->grid_walk_max = pop->grid_walk;
+        // running-value rows of the walk when a vector spans several case blocks
+        DA2(pop->gb.wscr, d.ncb > 1 ? (size_t)pop->grid_walk * GP_WARPS * 2 * d.Cpad : 4);
         if (cfg.walk_warps) {
             int g = (int)((cfg.walk_warps + GP_WARPS - 1) / GP_WARPS);
             if (g < pop->grid_walk) pop->grid_walk = g;
@@ -580,6 +601,8 @@ int gp_pop_create(const gp_config* cfg_in, const float* x, const float* targets,
 void gp_pop_destroy(gp_pop* pop) {
     if (!pop) return;
     if (pop->stream) cudaStreamSynchronize(pop->stream); else cudaDeviceSynchronize();
+    if (pop->gexec) cudaGraphExecDestroy(pop->gexec);
+    if (pop->cap_stream) cudaStreamDestroy(pop->cap_stream);
     for (void* p : pop->allocs) cudaFree(p);
     for (int w = 0; w < 2; ++w) for (void* p : pop->sets[w].allocs) cudaFree(p);
     if (pop->e_total_h) cudaFreeHost(pop->e_total_h);
@@ -621,6 +644,112 @@ int gp_load_trees(gp_pop* pop, const uint8_t* ops, const uint64_t* offsets) {
     CK(cudaMemcpyAsync(pop->gb.free_buf, pop->host_free.data(), sizeof(uint32_t) * P, cudaMemcpyHostToDevice, pop->stream));
     pop->have_children = false;
     pop->gb.evaluated = false;
+    return GP_OK;
+}
+
+int gp_set_graph_mode(gp_pop* pop, int on, uint64_t reserve_entries) {
+    if (!pop) return GP_EINVAL;
+    if (!on) {
+        if (pop->gexec) { cudaStreamSynchronize(pop->stream); cudaGraphExecDestroy(pop->gexec); pop->gexec = nullptr; pop->graph_n = 0; }
+        pop->d.strict_cap = 0;
+        return GP_OK;
+    }
+    int rc = check_status(pop);
+    if (rc) return rc;
+    uint32_t cur_total = 0;
+    CK(cudaMemcpy(&cur_total, pop->d.e_off + pop->d.P, sizeof cur_total, cudaMemcpyDeviceToHost));
+    uint64_t want = reserve_entries ? reserve_entries : 2ull * cur_total + 64ull * pop->d.P;
+    if (want > pop->slot_limit) want = pop->slot_limit;
+    // an explicit reservation sets both sets to exactly that size; the
+    // default only grows them
+    for (int k = 0; k < 2; ++k) {
+        const int w = k == 0 ? (pop->cur ^ 1) : pop->cur;
+        if (pop->sets[w].Ecap < want || (reserve_entries && pop->sets[w].Ecap != want)) {
+            int r = grow_set(pop, w, (uint32_t)want);
+            if (r) return r;
+            // the current set held the population's values: gp_eval_full must rebuild them
+            if (w == pop->cur) pop->gb.evaluated = false;
+        }
+    }
+    pop->d.strict_cap = 1;
+    return GP_OK;
+}
+
+int gp_graph_capture(gp_pop* pop, uint32_t first_generation, uint32_t n_generations) {
+    if (!pop) return GP_EINVAL;
+    if (!pop->d.strict_cap) return fail(pop, GP_ESTATE, "gp_graph_capture needs graph mode (gp_set_graph_mode)");
+    if (n_generations < 2 || (n_generations & 1u))
+        return fail(pop, GP_EINVAL, "n_generations must be even and at least 2 (got %u)", n_generations);
+    GenBufs& g = pop->gb;
+    if (!g.evaluated || pop->have_children)
+        return fail(pop, GP_ESTATE, "gp_graph_capture needs an evaluated population with no pending children");
+    int rc = check_status(pop);
+    if (rc) return rc;
+    if (pop->gexec) { cudaGraphExecDestroy(pop->gexec); pop->gexec = nullptr; pop->graph_n = 0; }
+    CK(cudaMemsetAsync(pop->gwords + 1, 0, sizeof(uint32_t), pop->stream));
+    CK(cudaStreamSynchronize(pop->stream));
+    // capturing runs the host side of every generation without executing it:
+    // keep the host state and put it back afterwards (with an even count the
+    // double-buffer roles end where they began)
+    // the legacy default stream cannot be captured: capture on a private
+    // stream (the graph is then launched on the population's own stream)
+    cudaStream_t own = pop->stream;
+    if (!own) {
+        if (!pop->cap_stream) CK(cudaStreamCreateWithFlags(&pop->cap_stream, cudaStreamNonBlocking));
+        pop->stream = pop->cap_stream;
+    }
+    cudaError_t be = cudaStreamBeginCapture(pop->stream, cudaStreamCaptureModeThreadLocal);
+    if (be != cudaSuccess) {
+        pop->stream = own;
+        cudaGetLastError();
+        return fail(pop, GP_ECUDA, "cudaStreamBeginCapture failed: %s", cudaGetErrorString(be));
+    }
+    const DevPop d0 = pop->d;
+    const GenBufs g0 = g;
+    const int cur0 = pop->cur;
+    const bool prof0 = pop->profiling;
+    const uint32_t calls0 = pop->cum_calls;
+    const int kind0 = pop->last_kind;
+    pop->profiling = false;
+    g.gen_add = pop->gwords + 1;
+    uint32_t launches = 0;
+    cudaGraph_t graph = nullptr;
+    int r = GP_OK;
+    for (uint32_t k = 0; k < n_generations && r == GP_OK; ++k) {
+        r = gen_crossover(pop, first_generation + k);
+        if (r == GP_OK) r = gen_incremental(pop);
+        launches += pop->launches;
+    }
+    if (r == GP_OK) k_graph_advance<<<1, 32, 0, pop->stream>>>(pop->gwords + 1, n_generations);
+    cudaError_t ce = cudaStreamEndCapture(pop->stream, &graph);
+    pop->stream = own;
+    pop->d = d0;
+    g = g0;
+    pop->cur = cur0;
+    bind_set(pop);
+    pop->profiling = prof0;
+    pop->cum_calls = calls0;
+    pop->last_kind = kind0;
+    pop->have_children = false;
+    if (r != GP_OK) { if (graph) cudaGraphDestroy(graph); cudaGetLastError(); return r; }
+    if (ce != cudaSuccess) { cudaGetLastError(); return fail(pop, GP_ECUDA, "stream capture failed: %s", cudaGetErrorString(ce)); }
+    ce = cudaGraphInstantiate(&pop->gexec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ce != cudaSuccess) { pop->gexec = nullptr; cudaGetLastError(); return fail(pop, GP_ECUDA, "graph instantiation failed: %s", cudaGetErrorString(ce)); }
+    pop->graph_n = n_generations;
+    pop->graph_launches = launches + 1;
+    return GP_OK;
+}
+
+int gp_graph_launch(gp_pop* pop) {
+    if (!pop) return GP_EINVAL;
+    if (!pop->gexec) return fail(pop, GP_ESTATE, "no captured graph (gp_graph_capture)");
+    if (!pop->gb.evaluated || pop->have_children)
+        return fail(pop, GP_ESTATE, "gp_graph_launch needs an evaluated population with no pending children");
+    CK(cudaGraphLaunch(pop->gexec, pop->stream));
+    pop->cum_calls += pop->graph_n;
+    pop->launches = pop->graph_launches;
+    pop->last_kind = 1;
     return GP_OK;
 }
 
@@ -918,7 +1047,6 @@ int gen_incremental(gp_pop* pop) {
     DevPop& d = pop->d;
     GenBufs& g = pop->gb;
     if (!pop->have_children) return fail(pop, GP_ESTATE, "gp_eval_incremental needs the children of a gp_crossover");
-    if (d.ncb != 1) return fail(pop, GP_EINVAL, "incremental evaluation supports up to %u test cases (32 x cases_per_lane)", 32 * d.K);
     const CacheView par = view_of(pop->sets[pop->cur ^ 1]);
     const int gt = pop->grid_threads;
     CK(cudaMemsetAsync(d.q, 0, sizeof(uint32_t) * NQ, pop->stream));
@@ -952,14 +1080,16 @@ int gen_incremental(gp_pop* pop) {
     k_pv_scatter<<<gt, 256, 0, pop->stream>>>(d, g);
     k_merge_count<<<(d.P + 255) / 256, 256, 0, pop->stream>>>(d, g, par);
     k_merge_offsets<<<1, 1024, 0, pop->stream>>>(d, g);
-    CK(cudaMemcpyAsync(pop->e_total_h, d.e_total, sizeof(uint32_t), cudaMemcpyDeviceToHost, pop->stream));
-    CK(cudaStreamSynchronize(pop->stream));
-    if (*pop->e_total_h > d.Ecap) {
-        uint64_t want = (uint64_t)*pop->e_total_h + *pop->e_total_h / 4 + 64;
-        if (want > pop->slot_limit) want = pop->slot_limit;
-        int r = grow_cache(pop, (uint32_t)want);
-        if (r) return r;
-        k_merge_offsets<<<1, 1024, 0, pop->stream>>>(d, g);
+    if (!d.strict_cap) {
+        CK(cudaMemcpyAsync(pop->e_total_h, d.e_total, sizeof(uint32_t), cudaMemcpyDeviceToHost, pop->stream));
+        CK(cudaStreamSynchronize(pop->stream));
+        if (*pop->e_total_h > d.Ecap) {
+            uint64_t want = (uint64_t)*pop->e_total_h + *pop->e_total_h / 4 + 64;
+            if (want > pop->slot_limit) want = pop->slot_limit;
+            int r = grow_cache(pop, (uint32_t)want);
+            if (r) return r;
+            k_merge_offsets<<<1, 1024, 0, pop->stream>>>(d, g);
+        }
     }
     k_merge_write<<<pop->grid_warps, GP_WARPS * 32, 0, pop->stream>>>(d, g, par);
     k_copy_values<<<pop->nsm * 16, 256, 0, pop->stream>>>(d, g, par);

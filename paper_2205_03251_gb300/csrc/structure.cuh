@@ -260,6 +260,7 @@ __global__ void __launch_bounds__(SCAN_TILE) k_scan_top(DevPop d, StructBufs sb)
         sb.u_epre[nunits] = ca;
         sb.u_bpre[nunits] = cb;
         *d.e_total = ca;
+        if (d.strict_cap && ca > d.Ecap) set_status(d.status, ST_ENTRIES);
     }
 }
 

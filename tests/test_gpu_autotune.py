@@ -1,0 +1,34 @@
+"""The autotuner on the uneven log-uniform population: every split it tries
+runs, gives the same fitness bit for bit (the split never changes a
+result), and the one it picks is the fastest it measured."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("boolean", [False, True])
+def test_autotune_uneven_population(boolean):
+    import torch
+    import synth
+    import paper_2205_03251_gb300 as gp
+    assert torch.cuda.is_available()
+    gp.build()
+    gp.load()
+    w = synth.workload(3, n_trees=256, target=30_000, boolean=boolean)
+    ks = (1,) if boolean else (1, 2, 4)
+    ts = (32, 256, 1024)
+    best, table = gp.autotune(w["x"], w["t"], w["consts"], w["ops"], w["off"], max_nodes=60_000,
+                              ks=ks, ts=ts, generations=2, boolean=boolean, seed=9)
+    assert len(table) == len(ks) * len(ts)
+    assert all(r["status"] == 0 for r in table), table
+    assert all(r["identical"] == 1 for r in table), table
+    assert all(r["ms_full"] > 0 and r["ms_generation"] > 0 for r in table)
+    j = int(np.argmin([r["ms_generation"] for r in table]))
+    assert (best["cases_per_lane"], best["cache_threshold"]) == (table[j]["cases_per_lane"],
+                                                                 table[j]["cache_threshold"])
+    # the chosen split runs the same evolution as any other
+    pop = gp.Population(None if boolean else w["x"], None if boolean else w["t"], w["consts"], w["ops"],
+                        w["off"], max_nodes=60_000, boolean=boolean, seed=9, **best)
+    pop.eval_full()
+    pop.close()

@@ -115,6 +115,22 @@ def test_generations_small_cases_and_lanes(gp):
         run_generations(gp, w, T=32, gens=2, max_nodes=20000, cases_per_lane=K)
 
 
+def test_generations_several_case_blocks(gp):
+    """Value vectors longer than one warp's case block (32 x cases_per_lane):
+    the walk goes block by block and stops only where every block agrees."""
+    import synth
+    for C, K in ((1024, 4), (100, 1), (200, 2), (1024, 1)):
+        w = synth.workload(0, n_trees=48, n_cases=C)
+        run_generations(gp, w, T=32, gens=2, max_nodes=20000, cases_per_lane=K, cache_check=8)
+
+
+def test_generations_uneven_population_1024_cases(gp):
+    """The uneven log-uniform population with 1,024 test cases."""
+    import synth
+    w = synth.workload(3, n_trees=64, target=20_000, n_cases=1024)
+    run_generations(gp, w, T=256, gens=2, max_nodes=40_000, cache_check=6)
+
+
 def test_generations_tight_size_limit_makes_copies(gp):
     import synth
     w = synth.workload(0, n_trees=80)
