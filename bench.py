@@ -37,6 +37,7 @@ if ROOT not in sys.path:
 import numpy as np  # noqa: E402
 
 METRIC = "equivalent GPop/s (opcodes x test cases / s)"
+PACKING = {"none": 0, "static": 1, "mlp": 2}
 N_SM_DEFAULT = 152
 FP32_LANES_PER_SM = 128
 
@@ -44,18 +45,30 @@ FP32_LANES_PER_SM = 128
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=60)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default 100 generations, 50 for uneven, 20 full evaluations)")
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="generation", choices=["generation", "full"])
-    ap.add_argument("--trees", type=int, default=500)
+    ap.add_argument("--workload", default="generation", choices=["generation", "full", "uneven"])
+    ap.add_argument("--trees", type=int, default=None, help="default 500 (uneven: 4,096)")
     ap.add_argument("--target", type=int, default=1_000_000)
     ap.add_argument("--cases", type=int, default=48)
+    ap.add_argument("--boolean", action="store_true", help="uneven workload on the 6-multiplexer")
     ap.add_argument("--threshold", type=int, default=1024)
-    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--packing", default="mlp", choices=list(PACKING))
+    ap.add_argument("--graph", dest="graph", action="store_true", default=True)
+    ap.add_argument("--no-graph", dest="graph", action="store_false")
+    ap.add_argument("--autotune", dest="autotune", action="store_true", default=True)
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false")
+    ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu", action="store_true")
-    return ap.parse_args()
+    a = ap.parse_args()
+    if a.steps is None:
+        a.steps = {"generation": 100, "uneven": 50, "full": 20}[a.workload]
+    if a.trees is None:
+        a.trees = 4096 if a.workload == "uneven" else 500
+    return a
 
 
 def measured_peaks():
@@ -118,6 +131,15 @@ class ClockSampler:
 
 def make_workload(args, rank: int):
     import synth
+    if args.workload == "uneven":
+        # each rank its own population of the same recipe (weak scaling)
+        w = synth.workload(3, n_trees=args.trees, n_cases=args.cases, target=args.target, boolean=args.boolean)
+        if rank:
+            sizes = synth.log_uniform_sizes(w["seed"] + rank, args.trees, 1e1, float(args.target))
+            w["ops"], w["off"] = synth.population("remy", w["seed"] + rank, args.trees, boolean=args.boolean,
+                                                  sizes=sizes)
+        w["max_nodes"] = 2 * args.target + 4096
+        return w
     seed_shift = rank
     ops, off = synth.population("big", synth.MASTER_SEED + 1 + seed_shift, args.trees, target=args.target)
     x, t = synth.cases(synth.MASTER_SEED + 1, args.cases)
@@ -127,64 +149,161 @@ def make_workload(args, rank: int):
 
 def workload_config(args, w):
     what = ("one generation: selection, crossover, incremental evaluation with failed disruption "
-            "propagation" if args.workload == "generation" else "full evaluation")
-    return {"workload": f"{args.trees} grafted ramped-half-and-half trees of ~{args.target:.0e} nodes, "
-                        f"{args.cases} cases, {what}",
-            "trees": args.trees, "nodes": int(w["off"][-1]), "cases": args.cases,
-            "cache_threshold": args.threshold,
+            "propagation" if args.workload != "full" else "full evaluation")
+    if args.workload == "uneven":
+        cases = "64 Boolean 6-multiplexer cases (one 64-bit word)" if args.boolean else f"{args.cases} cases"
+        desc = (f"{args.trees} Remy trees with sizes log-uniform in [1e1, {args.target:.0e}] nodes, "
+                f"{cases}, {what}")
+    else:
+        desc = f"{args.trees} grafted ramped-half-and-half trees of ~{args.target:.0e} nodes, {args.cases} cases, {what}"
+    return {"workload": desc, "trees": args.trees, "nodes": int(w["off"][-1]),
+            "cases": 64 if w.get("boolean") else args.cases, "cache_threshold": args.threshold,
             "l2": "opcode arena %.2f GB > 129 MB L2; no flush" % (int(w["off"][-1]) / 1e9)}
 
 
 def cpu_baseline(w, seconds: float):
-    """Time the CPU oracle (single thread, as it stands) on the first trees
-    of the workload until about `seconds` of work."""
+    """Time the CPU oracle as it stands on a bounded sample of the workload:
+    first on one thread, then with one thread per host core pulling whole
+    trees from a shared queue (the paper's threading of independent
+    evaluations).  The oracle's C calls release the GIL."""
     import oracle
     oracle.build()
     ops, off = w["ops"], w["off"]
-    done_nodes, n, t0 = 0, 0, time.perf_counter()
-    while n < len(off) - 1:
-        sub_off = off[n:n + 2] - off[n]
-        oracle.eval_pop_f32(ops[int(off[n]):int(off[n + 1])], sub_off, w["consts"], w["x"], w["t"])
-        done_nodes += int(off[n + 1] - off[n])
-        n += 1
-        if time.perf_counter() - t0 > seconds:
+    boolean = bool(w.get("boolean"))
+    C = 64 if boolean else len(w["x"])
+    P = len(off) - 1
+
+    def one(n):
+        sub = off[n:n + 2] - off[n]
+        tree = ops[int(off[n]):int(off[n + 1])]
+        if boolean:
+            oracle.eval_pop_bool(tree, sub)
+        else:
+            oracle.eval_pop_f32(tree, sub, w["consts"], w["x"], w["t"])
+        return int(off[n + 1] - off[n])
+
+    def run(threads: int, budget: float):
+        lock = threading.Lock()
+        nxt = [0]
+        done = [0, 0]
+        t0 = time.perf_counter()
+
+        def worker():
+            while True:
+                with lock:
+                    if nxt[0] >= P or time.perf_counter() - t0 > budget:
+                        return
+                    n = nxt[0]
+                    nxt[0] += 1
+                k = one(n)
+                with lock:
+                    done[0] += k
+                    done[1] += 1
+        ts = [threading.Thread(target=worker) for _ in range(threads)]
+        for t in ts:
+            t.start()
+        for t in ts:
+            t.join()
+        dt = time.perf_counter() - t0
+        return done[0] * C / dt / 1e9, done[1], done[0], dt
+
+    one_v, one_n, one_nodes, one_dt = run(1, seconds / 3)
+    cores = os.cpu_count() or 1
+    all_v, all_n, all_nodes, all_dt = run(cores, 2 * seconds / 3)
+    kind = "recursive Boolean oracle" if boolean else "recursive FP32 oracle"
+    return {"value": all_v, "unit": "GPop/s", "cores": cores, "kind": "oracle",
+            "sample": f"{all_n} trees ({all_nodes} nodes) x {C} cases in {all_dt:.1f} s, {kind}, one thread per "
+                      f"core taking whole trees from a shared queue",
+            "single_thread": {"value": one_v, "cores": 1,
+                              "sample": f"{one_n} trees ({one_nodes} nodes) x {C} cases in {one_dt:.1f} s"}}
+
+
+def reference_units(w, lo: int = 1024, hi: int = 65536, want: int = 4096):
+    """Disjoint subtrees (each a complete tree of lo..hi nodes) cut from the
+    workload's trees in order: the reference arm's units of work."""
+    import oracle
+    ops, off = w["ops"], w["off"]
+    units = []
+    for n in range(len(off) - 1):
+        tree = ops[int(off[n]):int(off[n + 1])]
+        if len(tree) <= hi:
+            units.append(tree)
+        else:
+            ends = oracle.tree_ends(tree)
+            i = 0
+            while i < len(tree) and len(units) < want:
+                sz = int(ends[i]) - i
+                if lo <= sz <= hi:
+                    units.append(tree[i:int(ends[i])])
+                    i = int(ends[i])
+                else:
+                    i += 1
+        if len(units) >= want:
             break
-    dt = time.perf_counter() - t0
-    C = len(w["x"])
-    return {"value": done_nodes * C / dt / 1e9, "unit": "GPop/s", "cores": 1, "kind": "oracle",
-            "sample": f"first {n} trees ({done_nodes} nodes) x {C} cases, recursive FP32 oracle, {dt:.1f} s"}
+    return units
 
 
 def run_reference(args):
-    """--impl reference: the CPU oracle, timed per step on a bounded sample."""
+    """--impl reference: the CPU oracle as it stands, one thread per host
+    core, each step a bounded sample of the same workload: one subtree of
+    the workload's trees per thread."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     w = make_workload(args, 0)
     import oracle
     oracle.build()
-    ops, off, C = w["ops"], w["off"], len(w["x"])
-    per_step = 1          # trees per step, ~0.5 s of CPU work each
-    def step(i):
-        j = (i * per_step) % (len(off) - 1 - per_step)
-        sub = off[j:j + per_step + 1] - off[j]
-        oracle.eval_pop_f32(ops[int(off[j]):int(off[j + per_step])], sub, w["consts"], w["x"], w["t"])
-        return int(off[j + per_step] - off[j])
-    for i in range(args.warmup):
-        step(i)
+    boolean = bool(w.get("boolean"))
+    C = 64 if boolean else len(w["x"])
+    units = reference_units(w)
+    cores = os.cpu_count() or 1
+    pos = [0]
+
+    def one(tree):
+        sub = np.array([0, len(tree)], np.uint64)
+        if boolean:
+            oracle.eval_pop_bool(tree, sub)
+        else:
+            oracle.eval_pop_f32(tree, sub, w["consts"], w["x"], w["t"])
+
+    def step():
+        batch = [units[(pos[0] + j) % len(units)] for j in range(cores)]
+        pos[0] += cores
+        ts = [threading.Thread(target=one, args=(u,)) for u in batch]
+        for t in ts:
+            t.start()
+        for t in ts:
+            t.join()
+        return sum(len(u) for u in batch)
+
+    for _ in range(args.warmup):
+        step()
     nodes, t0 = 0, time.perf_counter()
-    for i in range(args.steps):
-        nodes += step(args.warmup + i)
+    for _ in range(args.steps):
+        nodes += step()
     dt = time.perf_counter() - t0
     val = nodes * C / dt / 1e9
+    kind = "recursive Boolean oracle" if boolean else "recursive FP32 oracle"
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "GPop/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64" if boolean else "f32",
             "data": "synthetic", "config": workload_config(args, w),
-            "cpu_baseline": {"value": val, "unit": "GPop/s", "cores": 1, "kind": "oracle",
-                             "sample": f"{per_step} trees per step of the same workload, recursive FP32 oracle"},
+            "cpu_baseline": {"value": val, "unit": "GPop/s", "cores": cores, "kind": "oracle",
+                             "sample": f"per step {cores} subtrees of 1,024-65,536 nodes cut from the workload's "
+                                       f"trees, one per thread, {kind}"},
             "e2e": {"value": val, "unit": "GPop/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def graph_chunk(k: int) -> int:
+    """Generations per captured graph for k timed steps: the largest even
+    divisor of k up to 100 (0 when k is odd: the loop then runs eagerly)."""
+    if k % 2:
+        return 0
+    for g in range(min(k, 100), 1, -1):
+        if g % 2 == 0 and k % g == 0:
+            return g
+    return 0
 
 
 def main():
@@ -207,9 +326,23 @@ def main():
     gp.load()
     w = make_workload(args, rank)
     stream = torch.cuda.current_stream()
-    maxn = 1 << 21
-    pop = gp.Population(w["x"], w["t"], w["consts"], w["ops"], w["off"], max_nodes=maxn,
-                        cache_threshold=args.threshold, seed=0x5EED + rank, stream=stream)
+    boolean = bool(w.get("boolean"))
+    maxn = w.get("max_nodes", 1 << 21)
+    pop_kw = {"cache_threshold": args.threshold, "packing": PACKING[args.packing]}
+    tune = None
+    if args.workload == "uneven" and args.autotune:
+        ks = (1,) if boolean else (1, 2, 4)
+        best, table = gp.autotune(w["x"], w["t"], w["consts"], w["ops"], w["off"], max_nodes=maxn, ks=ks,
+                                  ts=(256, 1024), generations=2, boolean=boolean, seed=0x5EED + rank,
+                                  packing=pop_kw["packing"], stream=stream)
+        pop_kw.update(best)
+        tune = {"chosen": best, "candidates": [{k: r[k] for k in ("cases_per_lane", "cache_threshold",
+                                                                   "ms_full", "ms_generation", "identical")}
+                                               for r in table]}
+    pop = gp.Population(None if boolean else w["x"], None if boolean else w["t"], w["consts"], w["ops"], w["off"],
+                        max_nodes=maxn, boolean=boolean, seed=0x5EED + rank, stream=stream, **pop_kw)
+    generational = args.workload != "full"
+    chunk = graph_chunk(args.steps) if (generational and args.graph) else 0
 
     def timed(step, n):
         pop.set_profiling(True)
@@ -227,7 +360,10 @@ def main():
     # full evaluation (also the starting point of the generation loop)
     for _ in range(2):
         pop.eval_full()
-    full_ms, full_st = timed(pop.eval_full, 3 if args.workload == "generation" else 0) if args.workload == "generation" else (None, None)
+    full_ms, full_st = timed(pop.eval_full, 3) if generational else (None, None)
+    if chunk:
+        pop.set_graph_mode(True)         # pre-sized caches, no host syncs in the loop
+        pop.eval_full()
 
     gen = [0]
 
@@ -236,15 +372,25 @@ def main():
         pop.eval_incremental(want_stats=False)
         gen[0] += 1
 
-    step = gen_step if args.workload == "generation" else pop.eval_full
+    step = gen_step if generational else pop.eval_full
     for _ in range(args.warmup):
         step()
+    n_calls, launches_per_call = args.steps, None
+    if chunk:
+        # capture `chunk` generations with phase events (the graph is uploaded at capture;
+        # the eager warm-up steps above ran every kernel of the loop)
+        pop.set_profiling(True)
+        pop.graph_capture(gen[0], chunk)
+        step = pop.graph_launch
+        n_calls = args.steps // chunk
     torch.cuda.synchronize()
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)
-    ms, st = timed(step, args.steps)
+    ms, st = timed(step, n_calls)
     clk = clocks.stop()
+    if chunk:
+        gen[0] += args.steps
     if dist:
         t = torch.tensor([ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -266,9 +412,16 @@ def main():
 
     line = {"metric": METRIC, "value": value, "unit": "GPop/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64" if boolean else "f32", "data": "synthetic",
             "config": workload_config(args, w), "actual_gpops": actual, "phase_ms": phases}
-    if args.workload == "generation":
+    line["config"]["execution"] = (f"CUDA graph of {chunk} generations, {n_calls} replay(s) timed "
+                                   f"after {args.warmup} eager warm-up generations" if chunk else "eager calls")
+    line["config"]["packing"] = args.packing
+    if tune:
+        line["config"]["cases_per_lane"] = pop_kw["cases_per_lane"]
+        line["config"]["cache_threshold"] = pop_kw["cache_threshold"]
+        line["autotune"] = tune
+    if generational:
         xo_ms = phases["crossover"]
         xo_bytes = st["cum_crossover_bytes"] / max(1, st["cum_calls"])
         xo_gbs = xo_bytes / (xo_ms * 1e-3) / 1e9 if xo_ms > 0 else None
@@ -277,12 +430,14 @@ def main():
         line["full_eval_gpops"] = (full_st["cum_equivalent_ops"] / (full_ms * 1e-3) / 1e9) if full_ms else None
         line["stopped_fraction"] = st["stopped"] / max(1, st["children"])
         line["path_levels_per_child"] = st["path_levels"] / max(1, st["children"])
-        # the generation is dominated by the children's structure pass and the walk;
-        # report the crossover kernels against HBM (their bytes are exact)
+        # the crossover kernels are the HBM-bound part of a generation (their bytes are exact)
         line["roofline"] = {"bound": "hbm", "achieved": xo_gbs, "peak": hbm, "unit": "GB/s",
                             "frac": (xo_gbs / hbm) if (xo_gbs and hbm) else None, "traffic": None,
                             "kernel": "crossover phase (gather, copy, in-place move, fragment write)",
-                            "peak_note": "MEASURED_PEAKS.json hbm_gbs (copy, read+write)"}
+                            "peak_note": "MEASURED_PEAKS.json hbm_gbs (copy, read+write), of measured",
+                            "timing": "CUDA events around the phase inside the timed region"
+                                      + (" (event-record nodes of the graph, mean over the last replay)"
+                                         if chunk else "")}
     else:
         t_items = phases["items"]
         achieved = st["interp_ops"] / (t_items * 1e-3) / 1e12 if t_items > 0 else None
@@ -290,15 +445,15 @@ def main():
                             "frac": (achieved / alu_peak) if achieved else None, "traffic": None,
                             "kernel": "k_eval_items (subtree interpreter)",
                             "peak_note": f"{nsm} SMs x 128 FP32 lanes x {sm_max:.0f} MHz; one node x case = one lane op"}
-    line["gpu_launches"] = st["launches"] * args.steps
+    line["gpu_launches"] = st["launches"] * n_calls
     line["clocks"] = clk
 
     # end to end through the public API
     pop.set_profiling(False)
-    if args.workload == "generation":
+    P = len(w["off"]) - 1
+    if generational:
         # a generation has no host inputs (the population stays resident); the host reads back the
         # fitness of every child and the best child's tree each step
-        P = args.trees
         t0 = time.perf_counter()
         d2h = 0
         for _ in range(args.e2e_steps):
@@ -308,11 +463,11 @@ def main():
             tr = pop.tree(best)
             d2h += 4 * P + len(tr)
         e2e_s = time.perf_counter() - t0
-        st2 = pop.stats()
-        eq_last = st2["equivalent_ops"]
-        e2e = {"value": eq_last * args.e2e_steps / e2e_s / 1e9, "unit": "GPop/s", "h2d_bytes_per_step": 0,
+        eq = pop.stats()["cum_equivalent_ops"]          # summed on the device over the e2e steps
+        e2e = {"value": eq / e2e_s / 1e9, "unit": "GPop/s", "h2d_bytes_per_step": 0,
                "d2h_bytes_per_step": d2h // args.e2e_steps,
-               "note": "generation steps through gp_crossover + gp_eval_incremental + gp_fitness + gp_get_tree"}
+               "note": "eager generation steps through gp_crossover + gp_eval_incremental + gp_fitness + "
+                       "gp_get_tree"}
     else:
         pinned = torch.empty(len(w["ops"]), dtype=torch.uint8, pin_memory=True)
         pinned.numpy()[:] = w["ops"]
@@ -329,7 +484,7 @@ def main():
         e2e_s = time.perf_counter() - t0
         eq = pop.stats()["equivalent_ops"]
         e2e = {"value": eq * args.e2e_steps / e2e_s / 1e9, "unit": "GPop/s",
-               "h2d_bytes_per_step": int(w["off"][-1]) + 8 * (args.trees + 1), "d2h_bytes_per_step": 4 * args.trees}
+               "h2d_bytes_per_step": int(w["off"][-1]) + 8 * (P + 1), "d2h_bytes_per_step": 4 * P}
     if dist:
         t = torch.tensor([e2e["value"]], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MIN)

@@ -79,6 +79,9 @@ typedef struct {
     uint64_t seed;              /* master seed of every stochastic choice */
     uint32_t walk_warps;        /* 0 = as many as fit; else at most this many warps run the walk */
     uint32_t mlp_lr_micro;      /* Adam learning rate of the packing MLP in 1e-6 units (0 = 1000) */
+    uint32_t walk_team;         /* warps per child in the incremental walk: 1, 2, 4, 8, or 0 = auto
+                                   (the largest team with which every child runs at once, else 1) */
+    uint32_t reserved;          /* must be 0 */
 } gp_config;
 
 /* Per-call statistics of the last evaluation (host copy). */

@@ -33,7 +33,8 @@ class GpConfig(ctypes.Structure):
                 ("cache_threshold", ctypes.c_uint32), ("tournament", ctypes.c_uint32),
                 ("packing", ctypes.c_uint32), ("cases_per_lane", ctypes.c_uint32),
                 ("cache_budget_bytes", ctypes.c_uint64), ("seed", ctypes.c_uint64),
-                ("walk_warps", ctypes.c_uint32), ("mlp_lr_micro", ctypes.c_uint32)]
+                ("walk_warps", ctypes.c_uint32), ("mlp_lr_micro", ctypes.c_uint32),
+                ("walk_team", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
 
 
 class GpStats(ctypes.Structure):
@@ -354,7 +355,7 @@ class Population:
     def __init__(self, x, t, consts, ops, off, *, max_nodes: int, cache_threshold: int = 1024,
                  boolean: bool = False, tournament: int = 7, packing: int = GP_PACK_STATIC,
                  cases_per_lane: int = 0, cache_budget_bytes: int = 0, seed: int = 0, stream=None,
-                 walk_warps: int = 0, mlp_lr_micro: int = 0):
+                 walk_warps: int = 0, mlp_lr_micro: int = 0, walk_team: int = 0):
         off = np.asarray(off, np.uint64)
         self.P = len(off) - 1
         self.boolean = boolean
@@ -363,7 +364,8 @@ class Population:
                        funcset=GP_BOOL_MUX6 if boolean else GP_FP32_ARITH,
                        cache_threshold=cache_threshold, tournament=tournament, packing=packing,
                        cases_per_lane=cases_per_lane, cache_budget_bytes=cache_budget_bytes,
-                       seed=seed & (2**64 - 1), walk_warps=walk_warps, mlp_lr_micro=mlp_lr_micro)
+                       seed=seed & (2**64 - 1), walk_warps=walk_warps, mlp_lr_micro=mlp_lr_micro,
+                       walk_team=walk_team)
         if boolean:
             x = np.zeros(1, np.float32)
             t = np.zeros(1, np.float32)

@@ -8,6 +8,7 @@
 
 #define HALO_MAX 64            // largest |size change| moved in place (halo bytes per block)
 #define SHIFT_BS 4096          // bytes of tail per block of the in-place move
+#define COPY_CH 32768          // bytes of a copied child per work unit
 #define PV_PER_CHILD 256       // walk records (new path values) reserved per child on average
 #define WALK_MAXLVL 520        // small-ancestor levels held in shared memory (T <= 1024)
 
@@ -43,6 +44,7 @@ struct GenBufs {
     uint8_t* stash;
     uint64_t stash_cap;
     uint32_t* shift_off;             // [P+1] in-place move blocks per child (prefix)
+    uint32_t* copy_off;              // [P+1] COPY_CH-byte chunks of the copied children (prefix)
     uint8_t* halo;                   // [blocks * HALO_MAX]
     uint32_t shift_cap;
     int32_t* stop;                   // [P] FDP stop level, -1 if the root differs
@@ -62,7 +64,6 @@ struct GenBufs {
     uint32_t* order;                 // [P] walk order
     unsigned long long* gstat;       // [NGSTAT]
     uint32_t max_nodes, tsize;
-    float* wscr;                     // [walk warps][2][Cpad] running values when a vector spans several case blocks
     uint64_t seed;
     uint32_t gen;
     const uint32_t* gen_add;         // device word added to gen (generations replayed by a captured graph)
@@ -217,14 +218,14 @@ __device__ __forceinline__ uint64_t block_excl_scan(uint64_t v, uint64_t* ws, ui
 __global__ void __launch_bounds__(1024) k_assign(DevPop d, GenBufs g) {
     if (halted(d)) return;
     __shared__ uint64_t ws[32];
-    __shared__ uint64_t carry[5];
-    if (threadIdx.x < 5) carry[threadIdx.x] = 0;
+    __shared__ uint64_t carry[6];
+    if (threadIdx.x < 6) carry[threadIdx.x] = 0;
     for (uint32_t j = threadIdx.x; j < d.P; j += blockDim.x) g.hasip[j] = 0;
     __syncthreads();
     const uint32_t P = d.P;
     for (uint32_t base = 0; base < P; base += blockDim.x) {
         const uint32_t i = base + threadIdx.x;
-        uint32_t copy = 0, nblk = 0;
+        uint32_t copy = 0, nblk = 0, nch = 0;
         uint64_t fragb = 0, stashb = 0, xob = 0;
         if (i < P) {
             const uint32_t m = g.mother[i];
@@ -240,6 +241,7 @@ __global__ void __launch_bounds__(1024) k_assign(DevPop d, GenBufs g) {
             g.flags[i] = fl;
             copy = inplace ? 0 : 1;
             d.size[i] = (uint32_t)((int64_t)sm + delta);
+            if (copy) nch = (uint32_t)(((int64_t)sm + delta + COPY_CH - 1) / COPY_CH);
             if (!clone) {
                 fragb = (s + 15u) & ~15u;
                 if (r < d.T) stashb = (r + 15u) & ~15u;
@@ -256,6 +258,7 @@ __global__ void __launch_bounds__(1024) k_assign(DevPop d, GenBufs g) {
         const uint64_t so = block_excl_scan(stashb, ws, &carry[2]);
         const uint64_t bo = block_excl_scan(nblk, ws, &carry[3]);
         const uint64_t xo = block_excl_scan(xob, ws, &carry[4]);
+        const uint64_t co = block_excl_scan(nch, ws, &carry[5]);
         (void)xo;
         if (i < P) {
             const uint32_t m = g.mother[i];
@@ -263,6 +266,7 @@ __global__ void __launch_bounds__(1024) k_assign(DevPop d, GenBufs g) {
             g.frag_off[i] = fo;
             g.stash_off[i] = so;
             g.shift_off[i] = (uint32_t)bo;
+            g.copy_off[i] = (uint32_t)co;
         }
     }
     __syncthreads();
@@ -270,6 +274,7 @@ __global__ void __launch_bounds__(1024) k_assign(DevPop d, GenBufs g) {
         g.frag_off[P] = carry[1];
         g.stash_off[P] = carry[2];
         g.shift_off[P] = (uint32_t)carry[3];
+        g.copy_off[P] = (uint32_t)carry[5];
         g.misc[M_NCOPY] = (uint32_t)carry[0];
         g.misc[M_NSHIFT] = (uint32_t)carry[3];
         g.gstat[G_XOBYTES] = carry[4];
@@ -319,40 +324,51 @@ __global__ void k_gather(DevPop d, GenBufs g) {
 // ------------------------------------------------------------------ A8 materialise
 
 // Children built in a free buffer: mother head, donated subtree, mother
-// tail (Fig. 1), 16 destination bytes per thread.
-__global__ void k_copy_children(DevPop d, GenBufs g) {
+// tail (Fig. 1).  The copies are cut into COPY_CH-byte chunks spread over
+// the whole grid; each thread moves 16 destination bytes at a time, four
+// loads in flight before the stores.
+__device__ __forceinline__ uint4 child_quad(const uint8_t* __restrict__ om, const uint8_t* __restrict__ fr,
+                                            uint32_t o, uint32_t c, uint32_t r, uint32_t s, uint32_t nk) {
+    if (o + 16 <= c) return *reinterpret_cast<const uint4*>(om + o);
+    if (o >= c + s) return load16u(om + (o - s + r));
+    if (o >= c && o + 16 <= c + s) return load16u(fr + (o - c));
+    uint8_t b[16];
+#pragma unroll
+    for (int t = 0; t < 16; ++t) {
+        const uint32_t x = o + t;
+        b[t] = (x < c) ? om[x] : (x < c + s) ? fr[x - c] : (x < nk ? om[x - s + r] : 0);
+    }
+    return *reinterpret_cast<uint4*>(b);
+}
+
+__global__ void __launch_bounds__(256) k_copy_children(DevPop d, GenBufs g) {
     if (halted(d)) return;
     if (g.frag_off[d.P] > g.frag_cap) return;
-    for (uint32_t i = blockIdx.x; i < d.P; i += gridDim.x) {
+    const uint32_t nu = g.copy_off[d.P];
+    constexpr uint32_t QCH = COPY_CH / 16;
+    for (uint32_t u = blockIdx.x; u < nu; u += gridDim.x) {
+        const uint32_t i = find_segment(g.copy_off, d.P, u);
+        const uint32_t j = u - g.copy_off[i];
         const uint32_t fl = g.flags[i];
-        if (fl & F_INPLACE) continue;
-        const uint32_t m = g.mother[i];
-        const uint8_t* om = d.arena + (size_t)g.pbuf[m] * d.cap;
-        uint8_t* dst = d.arena + (size_t)d.buf[i] * d.cap;
+        const uint8_t* om = d.arena + (size_t)g.pbuf[g.mother[i]] * d.cap;
+        uint4* dst = reinterpret_cast<uint4*>(d.arena + (size_t)d.buf[i] * d.cap);
         const uint32_t nk = d.size[i];
-        if (fl & F_CLONE) {
-            for (uint32_t q = threadIdx.x; q < (nk + 15) / 16; q += blockDim.x)
-                reinterpret_cast<uint4*>(dst)[q] = reinterpret_cast<const uint4*>(om)[q];
-            continue;
-        }
-        const uint32_t c = g.cpos[i], r = g.rsz[i], s = g.ssz[i];
-        const uint8_t* fr = g.frag + g.frag_off[i];
-        for (uint32_t q = threadIdx.x; q < (nk + 15) / 16; q += blockDim.x) {
-            const uint32_t o = 16 * q;
-            uint4 v;
-            if (o + 16 <= c) v = reinterpret_cast<const uint4*>(om)[q];
-            else if (o >= c + s) v = load16u(om + (o - s + r));
-            else if (o >= c && o + 16 <= c + s) v = load16u(fr + (o - c));
-            else {
-                uint8_t b[16];
+        const uint32_t q0 = j * QCH, q1 = min((nk + 15) / 16, q0 + QCH);
+        const bool clone = (fl & F_CLONE) != 0;
+        const uint32_t c = clone ? nk : g.cpos[i], r = clone ? 0 : g.rsz[i], s = clone ? 0 : g.ssz[i];
+        const uint8_t* fr = g.frag + (clone ? 0 : g.frag_off[i]);
+        for (uint32_t q = q0 + threadIdx.x; q < q1; q += 4 * 256) {
+            uint4 v[4];
 #pragma unroll
-                for (int t = 0; t < 16; ++t) {
-                    const uint32_t x = o + t;
-                    b[t] = (x < c) ? om[x] : (x < c + s) ? fr[x - c] : (x < nk ? om[x - s + r] : 0);
-                }
-                v = *reinterpret_cast<uint4*>(b);
+            for (int t = 0; t < 4; ++t) {
+                const uint32_t qq = q + t * 256;
+                if (qq < q1) v[t] = clone ? reinterpret_cast<const uint4*>(om)[qq] : child_quad(om, fr, 16 * qq, c, r, s, nk);
             }
-            reinterpret_cast<uint4*>(dst)[q] = v;
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                const uint32_t qq = q + t * 256;
+                if (qq < q1) dst[qq] = v[t];
+            }
         }
     }
 }
@@ -393,7 +409,8 @@ __global__ void k_save_halo(DevPop d, GenBufs g) {
 
 __global__ void __launch_bounds__(256) k_shift(DevPop d, GenBufs g) {
     if (halted(d)) return;
-    __shared__ uint8_t sb[SHIFT_BS];
+    // the block's source bytes from its 16-byte-aligned start, plus slack for the shifted reads
+    __shared__ __align__(16) uint8_t sb[SHIFT_BS + 48];
     const uint32_t nb = g.shift_off[d.P];
     if (nb > g.shift_cap) return;
     for (uint32_t b = blockIdx.x; b < nb; b += gridDim.x) {
@@ -404,44 +421,77 @@ __global__ void __launch_bounds__(256) k_shift(DevPop d, GenBufs g) {
         const uint8_t* h = g.halo + (size_t)b * HALO_MAX;
         const uint32_t ad = (uint32_t)(delta > 0 ? delta : -delta);
         const uint32_t k = min(ad, len);
-        for (uint32_t t = threadIdx.x; t < len; t += blockDim.x) {
-            uint8_t v;
-            if (delta > 0 && j > 0 && t < k) v = h[t];
-            else if (delta < 0 && j + 1 < nblk && t >= len - k) v = h[t - (len - k)];
-            else v = buf[src0 + t];
-            sb[t] = v;
-        }
+        const uint32_t a0 = src0 & ~15u, m0 = src0 & 15u;
+        // stage the source quads (bytes a neighbour may be writing are replaced from the halo below)
+        const uint32_t nq = (m0 + len + 15u) / 16u;
+        for (uint32_t q = threadIdx.x; q < nq; q += blockDim.x)
+            reinterpret_cast<uint4*>(sb)[q] = reinterpret_cast<const uint4*>(buf + a0)[q];
         __syncthreads();
-        for (uint32_t t = threadIdx.x; t < len; t += blockDim.x) buf[(int64_t)src0 + delta + t] = sb[t];
+        if (delta > 0 && j > 0) { for (uint32_t t = threadIdx.x; t < k; t += blockDim.x) sb[m0 + t] = h[t]; }
+        if (delta < 0 && j + 1 < nblk) { for (uint32_t t = threadIdx.x; t < k; t += blockDim.x) sb[m0 + len - k + t] = h[t]; }
+        __syncthreads();
+        // destination [dst0, dst0 + len): whole aligned quads in the middle, single bytes at the ends
+        const uint32_t dst0 = (uint32_t)((int64_t)src0 + delta);
+        const uint32_t dq0 = (dst0 + 15u) / 16u, dq1 = (dst0 + len) / 16u;
+        const uint32_t head_end = min(16u * dq0, dst0 + len);
+        const uint32_t tail_begin = max(16u * dq1, head_end);
+        for (uint32_t x = dst0 + threadIdx.x; x < head_end; x += blockDim.x) buf[x] = sb[m0 + (x - dst0)];
+        for (uint32_t x = tail_begin + threadIdx.x; x < dst0 + len; x += blockDim.x) buf[x] = sb[m0 + (x - dst0)];
+        if (dq1 > dq0) {
+            // sb byte of destination byte 16 dq: m0 + 16 dq - dst0 (same misalignment for every quad)
+            const uint32_t u0 = m0 + 16u * dq0 - dst0;
+            const uint32_t mu = u0 & 15u, mw = mu >> 2, sh = (mu & 3u) * 8u;
+            uint4* dst = reinterpret_cast<uint4*>(buf);
+            for (uint32_t q = dq0 + threadIdx.x; q < dq1; q += blockDim.x) {
+                const uint32_t u = (u0 >> 4) + (q - dq0);
+                const uint4 lo = reinterpret_cast<const uint4*>(sb)[u];
+                uint4 v = lo;
+                if (mu) {
+                    const uint4 hi = reinterpret_cast<const uint4*>(sb)[u + 1];
+                    const uint32_t w[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
+                    uint32_t r[4];
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) {
+                        uint32_t xx = 0, yy = 0;
+#pragma unroll
+                        for (int c = 0; c < 4; ++c)
+                            if ((uint32_t)c == mw) { xx = w[t + c]; yy = w[t + c + 1]; }
+                        r[t] = __funnelshift_r(xx, yy, sh);
+                    }
+                    v = make_uint4(r[0], r[1], r[2], r[3]);
+                }
+                dst[q] = v;
+            }
+        }
         __syncthreads();
     }
 }
 
-// Donated subtree written into the in-place children (after the move).
+// Donated subtree written into the in-place children (after the move):
+// whole aligned quads of the destination from the (shifted) fragment, single
+// bytes at the two ends.
 __global__ void k_write_frags(DevPop d, GenBufs g) {
     if (halted(d)) return;
     if (g.frag_off[d.P] > g.frag_cap) return;
     for (uint32_t i = blockIdx.x; i < d.P; i += gridDim.x) {
         const uint32_t fl = g.flags[i];
         if (!(fl & F_INPLACE) || (fl & F_CLONE)) continue;
-        uint8_t* dst = d.arena + (size_t)d.buf[i] * d.cap + g.cpos[i];
+        uint8_t* buf = d.arena + (size_t)d.buf[i] * d.cap;
         const uint8_t* fr = g.frag + g.frag_off[i];
-        const uint32_t s = g.ssz[i];
-        for (uint32_t t = threadIdx.x; t < s; t += blockDim.x) dst[t] = fr[t];
+        const uint32_t c = g.cpos[i], s = g.ssz[i];
+        const uint32_t dq0 = (c + 15u) / 16u, dq1 = (c + s) / 16u;
+        const uint32_t head_end = min(16u * dq0, c + s);
+        const uint32_t tail_begin = max(16u * dq1, head_end);
+        for (uint32_t x = c + threadIdx.x; x < head_end; x += blockDim.x) buf[x] = fr[x - c];
+        for (uint32_t x = tail_begin + threadIdx.x; x < c + s; x += blockDim.x) buf[x] = fr[x - c];
+        if (dq1 > dq0) {
+            for (uint32_t q = dq0 + threadIdx.x; q < dq1; q += blockDim.x)
+                reinterpret_cast<uint4*>(buf)[q] = load16u(fr + (16u * q - c));
+        }
     }
 }
 
 // ------------------------------------------------------------------ A7 incremental walk
-
-template <int K>
-struct WalkSmem {
-    // per warp: interpreter stack, two staging buffers, small-ancestor list, level ends
-    __host__ __device__ static size_t stack_bytes(int W) { return (size_t)W * 32 * K * sizeof(float); }
-    __host__ __device__ static size_t warp_bytes(int W) {
-        return stack_bytes(W) + 2 * STAGE_BYTES + 3 * WALK_MAXLVL * sizeof(uint32_t) + 64 * sizeof(float) * K;
-    }
-    __host__ __device__ static size_t total(int W, int warps) { return (256 + 6 * 32) * sizeof(float) + warps * warp_bytes(W); }
-};
 
 template <int K>
 __device__ __forceinline__ void load_vec(const float* slots, uint32_t Cpad, uint32_t slot, float (&v)[K],
@@ -453,28 +503,59 @@ __device__ __forceinline__ void load_vec(const float* slots, uint32_t Cpad, uint
 }
 
 template <int K>
-__device__ __forceinline__ bool same_bits(const float (&a)[K], const float (&b)[K], uint32_t C) {
-    const int lane = lane_id();
-    bool ok = true;
-#pragma unroll
-    for (int k = 0; k < K; ++k)
-        if ((uint32_t)(k * 32 + lane) < C && __float_as_uint(a[k]) != __float_as_uint(b[k])) ok = false;
-    return __all_sync(FULL, ok);
-}
-
-// case block cb of a running value vector kept in the warp's scratch row
-template <int K>
 __device__ __forceinline__ void store_blk(float* row, uint32_t cb, const float (&v)[K]) {
     float* p = row + cb * 32 * K + lane_id();
 #pragma unroll
     for (int k = 0; k < K; ++k) p[k * 32] = v[k];
 }
+
 template <int K>
 __device__ __forceinline__ void load_blk(const float* row, uint32_t cb, float (&v)[K]) {
     const float* p = row + cb * 32 * K + lane_id();
 #pragma unroll
     for (int k = 0; k < K; ++k) v[k] = p[k * 32];
 }
+
+
+// Shared-memory layout of one walk team (a CTA of nw warps working on one
+// child): constant tables, the small-ancestor lists, the level descriptors
+// of a batch, the running value vectors of the child and of the mother,
+// the siblings' vectors of a batch, a few broadcast words, then per warp an
+// interpreter stack and two staging buffers.
+struct LevelDesc {
+    uint32_t p, pend, ss, se;   // ancestor, its end in the child, sibling range [ss, se)
+    int32_t pent, sib;          // mother cache entry of p (-1: small) and of the sibling (-1: interpret)
+    uint32_t flags;             // op | left << 8 | child-cached << 9 | bad range << 10 | missing sibling << 11
+    int32_t k;                  // ancestor index along the path
+    uint32_t pslot, sslot;      // value slots of pent and sib in the mother's cache
+    uint32_t pad0, pad1;
+};
+#define LD_LEFT (1u << 8)
+#define LD_CACHED (1u << 9)
+#define LD_BAD (1u << 10)
+#define LD_NOSIB (1u << 11)
+
+template <int K>
+struct TeamLayout {
+    uint32_t kc, anc, ancg, lvl, desc, nv, ov, sv, mv, sc, warp0, warp_bytes, total;
+    __host__ __device__ TeamLayout(int W, uint32_t Cpad, uint32_t nw) {
+        uint32_t o = 0;
+        kc = o;   o += (256 + 6 * 32) * 4;
+        anc = o;  o += WALK_MAXLVL * 4;
+        ancg = o; o += WALK_MAXLVL * 4;
+        lvl = o;  o += WALK_MAXLVL * 4;
+        desc = o; o += 8 * sizeof(LevelDesc);
+        nv = o;   o += Cpad * 4;
+        ov = o;   o += Cpad * 4;
+        sv = o;   o += 8 * Cpad * 4;
+        mv = o;   o += 8 * Cpad * 4;
+        sc = o;   o += 16 * 4;
+        o = (o + 15u) & ~15u;
+        warp0 = o;
+        warp_bytes = (uint32_t)W * 32 * K * 4 + 2 * STAGE_BYTES;
+        total = o + nw * warp_bytes;
+    }
+};
 
 // left/right combination keeping the operand order of the node
 template <int K, bool B>
@@ -510,70 +591,223 @@ __device__ __forceinline__ void eval_run(const uint8_t* src, uint32_t s, uint32_
     for (int k = 0; k < K; ++k) out[k] = st.acc[k];
 }
 
-// Bottom-up incremental evaluation of one child per warp (Sec. 6.2, Fig. 3).
-// Level 0 compares the donated subtree's value with the removed subtree's;
-// each higher level combines the running values with the sibling's value
-// (cached when its subtree is large, else interpreted) and compares the
-// child's with the mother's.  The walk stops at the first level where the
-// two agree on every case, bit for bit.  Ancestors below the threshold lie
-// within T positions before the crossover point and are found by a
-// backward balance scan; larger ones come from the mother's cache links.
-// New values of nodes that are cached in the child are recorded in the
+// Ancestors of the crossover point c in the child, for one warp: the
+// deepest ancestor A that the mother caches, the small ancestors below it
+// (positions anc[], balance offsets ancg[], nearest first) from a backward
+// balance scan over at most T bytes before c, and the child ends of those
+// levels (lvl[v] = end of the ancestor whose subtree closes at balance v)
+// from a forward scan after the donated subtree.  Returns false on an
+// inconsistency (recorded in the status word).
+template <int K>
+__device__ bool walk_ancestors(const DevPop& d, const CacheView& par, uint32_t i, const uint8_t* ok_, uint32_t c,
+                               uint32_t s, uint32_t nk, int32_t em, uint32_t me0, uint32_t me1, uint8_t* stB,
+                               uint32_t* anc, int32_t* ancg, uint32_t* lvl, int32_t& A_out, uint32_t& nsmall_out,
+                               int32_t& hneed_out) {
+    const int lane = lane_id();
+    const uint32_t T = d.T;
+    int32_t A = -1;
+    uint32_t nsmall = 0;
+    if (em >= 0) A = par.e_par[em];
+    else {
+        int32_t e = find_last_lt(par.e_pos, me0, me1, c);
+        uint32_t guard = 0;
+        while (e >= 0 && par.e_end[e] <= c && guard++ < (1u << 24)) e = par.e_par[e];
+        A = e;
+        if (A < 0) { if (lane == 0) set_error(d, ST_STRUCT, 5, i, c, 0); return false; }
+        // backward scan of (max(pos(A)+1, c-T+1) .. c-1]: G(j) = sum_{k=j}^{c-1} (arity_k - 1);
+        // j is an ancestor of c iff G(j) >= G(m) for every m in (j, c], G(c) = 0
+        const uint32_t pA = par.e_pos[A];
+        const uint32_t lo = max(pA + 1, (c + 1 > T) ? c + 1 - T : 0u);
+        if (lo < c) {
+            __syncwarp();
+            stage_issue(stB, ok_, lo, c);
+            cp_async_commit();
+            cp_async_wait<0>();
+            __syncwarp();
+            const uint32_t a16 = lo & ~15u;
+            // lane l: positions c-1-32l-t, t = 0..31 (nearest first)
+            int sum = 0, mx = -0x40000000;
+            for (int t = 0; t < 32; ++t) {
+                const int64_t j = (int64_t)c - 1 - 32 * lane - t;
+                if (j >= (int64_t)lo) { sum += (stB[j - a16] < 4) ? 1 : -1; mx = max(mx, sum); }
+            }
+            // G offset from the lanes nearer to c, and the maximum G seen before this lane
+            int incl = sum;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                int ts = __shfl_up_sync(FULL, incl, o);
+                if (lane >= o) incl += ts;
+            }
+            const int base = incl - sum;
+            int pm = (mx > -0x40000000) ? base + mx : -0x40000000;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                int tm = __shfl_up_sync(FULL, pm, o);
+                if (lane >= o) pm = max(pm, tm);
+            }
+            int prevmax = __shfl_up_sync(FULL, pm, 1);
+            if (lane == 0) prevmax = 0;            // G(c) = 0
+            prevmax = max(prevmax, 0);
+            uint32_t fmask = 0;
+            int run = prevmax, gsum = base;
+            for (int t = 0; t < 32; ++t) {
+                const int64_t j = (int64_t)c - 1 - 32 * lane - t;
+                if (j >= (int64_t)lo) {
+                    gsum += (stB[j - a16] < 4) ? 1 : -1;
+                    if (gsum >= run) { fmask |= 1u << t; run = gsum; }
+                }
+            }
+            // compact in nearest-first order
+            const uint32_t cnt = __popc(fmask);
+            uint32_t off = cnt;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                uint32_t tt = __shfl_up_sync(FULL, off, o);
+                if (lane >= o) off += tt;
+            }
+            off -= cnt;
+            const uint32_t tot = __shfl_sync(FULL, off + cnt, 31);
+            if (tot > WALK_MAXLVL - 2) { if (lane == 0) set_status(d.status, ST_PATH); return false; }
+            gsum = base;
+            uint32_t k = off;
+            for (int t = 0; t < 32; ++t) {
+                const int64_t j = (int64_t)c - 1 - 32 * lane - t;
+                if (j >= (int64_t)lo) {
+                    gsum += (stB[j - a16] < 4) ? 1 : -1;
+                    if (fmask & (1u << t)) { anc[k] = (uint32_t)j; ancg[k] = gsum; ++k; }
+                }
+            }
+            nsmall = tot;
+            __syncwarp();
+        }
+    }
+    // ---- child ends of the small ancestors: forward scan after the donated subtree
+    // balance relative to b[c] is 1 at c+s; lvl[v] = first position where it reaches v
+    uint32_t maxv = 1;
+    if (nsmall) maxv = (uint32_t)ancg[nsmall - 1] + 1;
+    if (maxv >= WALK_MAXLVL) { if (lane == 0) set_status(d.status, ST_PATH); return false; }
+    int32_t hneed = -1;
+    if (nsmall) {
+        const uint32_t f0 = c + s;
+        const uint32_t f1 = f0 + T;
+        // sentinel 0 for levels the scan does not reach: their sibling ranges then fail the
+        // size check of the walk instead of reading a stale end
+        for (uint32_t v = lane; v <= maxv; v += 32) lvl[v] = 0;
+        __syncwarp();
+        const uint32_t lim = min(f1, (nk + 15u) & ~15u);
+        if (f0 < lim) { stage_issue(stB, ok_, f0, lim); }
+        cp_async_commit();
+        cp_async_wait<0>();
+        __syncwarp();
+        const uint32_t a16 = f0 & ~15u;
+        if (lane == 0) lvl[1] = f0;
+        int sum = 0, mx = 0;
+        // lane l: positions f0 + 32l + t
+        for (int t = 0; t < 32; ++t) {
+            const uint32_t q = f0 + 32 * lane + t;
+            const int w = (q < nk && stB[q - a16] < 4) ? -1 : 1;
+            sum += w;
+            mx = max(mx, sum);
+        }
+        int incl = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) { int ts = __shfl_up_sync(FULL, incl, o); if (lane >= o) incl += ts; }
+        const int base = 1 + incl - sum;          // balance before the lane's first position
+        int lmax = base + mx;                      // max after-balance in the lane (or base)
+        lmax = max(lmax, base);
+        int pm = lmax;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) { int tm = __shfl_up_sync(FULL, pm, o); if (lane >= o) pm = max(pm, tm); }
+        int prev = __shfl_up_sync(FULL, pm, 1);
+        if (lane == 0) prev = 1;
+        prev = max(prev, base);
+        int bal = base;
+        for (int t = 0; t < 32; ++t) {
+            const uint32_t q = f0 + 32 * lane + t;
+            bal += (q < nk && stB[q - a16] < 4) ? -1 : 1;
+            if (bal > prev) { if ((uint32_t)bal < WALK_MAXLVL) lvl[bal] = q + 1; prev = bal; }
+        }
+        __syncwarp();
+        // highest small ancestor that the child caches (needs a value even above the stop)
+        for (uint32_t k = lane; k < nsmall; k += 32) {
+            const uint32_t p = anc[k];
+            const uint32_t pe = lvl[ancg[k] + 1];
+            if (pe - p >= T) hneed = max(hneed, (int32_t)k);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) hneed = max(hneed, __shfl_xor_sync(FULL, hneed, o));
+    }
+    A_out = A;
+    nsmall_out = nsmall;
+    hneed_out = hneed;
+    return true;
+}
+
+// Bottom-up incremental evaluation of one child per team of nw warps
+// (Sec. 6.2, Fig. 3).  Level 0 compares the donated subtree's value with
+// the removed subtree's; each higher level combines the running values with
+// the sibling's value (cached when its subtree is large, else interpreted)
+// and compares the child's with the mother's.  The walk stops at the first
+// level where the two agree on every case, bit for bit.  Ancestors below
+// the threshold lie within T positions before the crossover point and are
+// found by a backward balance scan; larger ones come from the mother's cache
+// links.  The siblings' values do not depend on the path, so a team
+// evaluates the siblings of several levels at once (one warp each, or one
+// warp per case block), then combines them level by level and stops where
+// the method stops; siblings computed past the stop are discarded.  New
+// values of nodes that are cached in the child are recorded for the
 // child's cache; above the stop only child-cached nodes that the mother
 // does not cache need computing.
 template <int K, bool B>
-__global__ void __launch_bounds__(GP_WARPS * 32) k_walk(DevPop d, GenBufs g, CacheView par) {
+__global__ void __launch_bounds__(256) k_walk(DevPop d, GenBufs g, CacheView par, uint32_t nw) {
     if (halted(d)) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float* kc = reinterpret_cast<float*>(smem_raw);
-    const int lane = lane_id(), warp = threadIdx.x >> 5;
+    const uint32_t Cpad = d.Cpad, Cn = d.C, ncb = d.ncb, T = d.T;
+    const TeamLayout<K> L((int)d.W, Cpad, nw);
+    float* kc = reinterpret_cast<float*>(smem_raw + L.kc);
+    uint32_t* anc = reinterpret_cast<uint32_t*>(smem_raw + L.anc);
+    int32_t* ancg = reinterpret_cast<int32_t*>(smem_raw + L.ancg);
+    uint32_t* lvl = reinterpret_cast<uint32_t*>(smem_raw + L.lvl);
+    LevelDesc* desc = reinterpret_cast<LevelDesc*>(smem_raw + L.desc);
+    float* nvs = reinterpret_cast<float*>(smem_raw + L.nv);
+    float* ovs = reinterpret_cast<float*>(smem_raw + L.ov);
+    float* svs = reinterpret_cast<float*>(smem_raw + L.sv);
+    float* mvs = reinterpret_cast<float*>(smem_raw + L.mv);
+    volatile uint32_t* sc = reinterpret_cast<volatile uint32_t*>(smem_raw + L.sc);
+    const int lane = lane_id();
+    const uint32_t warp = threadIdx.x >> 5, tid = threadIdx.x, nthr = nw * 32;
     fill_kc(kc, d.consts);
     fill_kb(kc + 256);
     __syncthreads();
-    unsigned char* wb = smem_raw + (256 + 6 * 32) * sizeof(float) + (size_t)warp * WalkSmem<K>::warp_bytes((int)d.W);
+    unsigned char* wb = smem_raw + L.warp0 + warp * L.warp_bytes;
     Ictx<K> ic;
     ic.s = reinterpret_cast<float*>(wb);
     ic.W = (int)d.W;
     ic.maxd = (int)d.maxdepth;
     ic.kc = kc;
     ic.kb = kc + 256;
-    ic.g = d.ovf + (size_t)(blockIdx.x * GP_WARPS + warp) * (d.maxdepth - d.W) * 32 * K;
-    uint8_t* stA = wb + WalkSmem<K>::stack_bytes((int)d.W);
+    ic.g = d.ovf + (size_t)(blockIdx.x * nw + warp) * (d.maxdepth - d.W) * 32 * K;
+    uint8_t* stA = wb + (size_t)d.W * 32 * K * 4;
     uint8_t* stB = stA + STAGE_BYTES;
-    uint32_t* anc = reinterpret_cast<uint32_t*>(stB + STAGE_BYTES);     // small ancestor positions
-    int32_t* ancg = reinterpret_cast<int32_t*>(anc + WALK_MAXLVL);       // their balance offsets G
-    uint32_t* lvl = reinterpret_cast<uint32_t*>(ancg + WALK_MAXLVL);     // lvl[v] = child end of level v
-    float* red = reinterpret_cast<float*>(lvl + WALK_MAXLVL);            // fitness reduction scratch
-    load_cases<K>(d, 0, ic.xv);
-    const uint32_t T = d.T;
-    const uint32_t Cn = d.C;
-    // value vectors longer than one case block (32 K cases): the warp walks
-    // each level block by block and parks the running values in a scratch row
-    const uint32_t ncb = d.ncb;
-    float* wsn = nullptr;
-    float* wso = nullptr;
-    if (ncb > 1) {
-        wsn = g.wscr + (size_t)(blockIdx.x * GP_WARPS + warp) * 2 * d.Cpad;
-        wso = wsn + d.Cpad;
-    }
+    // levels per batch: one per warp, or fewer when a level spans several case blocks
+    const uint32_t nlb = max(1u, min(8u, nw / ncb));
     unsigned long long st_interp = 0, st_levels = 0, st_stopped = 0, st_pathops = 0;
 
     for (;;) {
-        uint32_t qi = 0;
-        if (lane == 0) qi = atomicAdd(&d.q[Q_WALK], 1u);
-        qi = __shfl_sync(FULL, qi, 0);
+        if (tid == 0) sc[0] = atomicAdd(&d.q[Q_WALK], 1u);
+        __syncthreads();
+        const uint32_t qi = sc[0];
+        __syncthreads();
         if (qi >= d.P) break;
         const uint32_t i = g.order[qi];
         const uint32_t fl = g.flags[i];
         const uint32_t m = g.mother[i];
-        if (lane == 0) { g.walkA[i] = -1; g.nins[i] = 0; g.pv_cnt[i] = 0; }
+        if (tid == 0) { g.walkA[i] = -1; g.nins[i] = 0; g.pv_cnt[i] = 0; }
         if (fl & F_CLONE) {
-            if (lane == 0) { d.fit[i] = g.pfit[m]; g.stop[i] = 0; g.plen[i] = 0; }
-            ++st_stopped;
+            if (tid == 0) { d.fit[i] = g.pfit[m]; g.stop[i] = 0; g.plen[i] = 0; ++st_stopped; }
             continue;
         }
         const uint32_t f = g.father[i], c = g.cpos[i], r = g.rsz[i], dd = g.dpos[i], s = g.ssz[i];
-        const int32_t delta = (int32_t)s - (int32_t)r;
         const uint32_t nk = d.size[i];
         const uint8_t* ok_ = d.arena + (size_t)d.buf[i] * d.cap;     // child bytes
         const uint32_t me0 = par.e_off[m], me1 = par.e_off[m + 1];
@@ -581,300 +815,224 @@ __global__ void __launch_bounds__(GP_WARPS * 32) k_walk(DevPop d, GenBufs g, Cac
         uint32_t npv = 0, nins_i = 0;
 
         // ---- level 0: donated subtree vs removed subtree
-        float nv[K], ov[K];
         int32_t ef = -1, em = -1;
         if (s >= T || dd == 0) {
             ef = find_exact(par.e_pos, fe0, fe1, dd);
-            if (ef < 0) { if (lane == 0) set_error(d, ST_STRUCT, 3, i, dd, s); continue; }
+            if (ef < 0) { if (tid == 0) set_error(d, ST_STRUCT, 3, i, dd, s); continue; }
         }
         if (r >= T || c == 0) {
             em = find_exact(par.e_pos, me0, me1, c);
-            if (em < 0) { if (lane == 0) set_error(d, ST_STRUCT, 4, i, c, r); continue; }
+            if (em < 0) { if (tid == 0) set_error(d, ST_STRUCT, 4, i, c, r); continue; }
         }
         // the donated subtree becomes the child's root (always cached) but the
         // father does not cache it: keep the value computed at level 0
         const bool root_rec = (c == 0 && s < T && dd != 0);
         uint32_t rslot = 0;
         if (root_rec) {
-            if (lane == 0) rslot = atomicAdd(&g.misc[M_PV], 1u);
-            rslot = __shfl_sync(FULL, rslot, 0);
-            if (rslot >= g.pvcap) { if (lane == 0) set_status(d.status, ST_PATH); continue; }
+            if (tid == 0) sc[1] = atomicAdd(&g.misc[M_PV], 1u);
+            __syncthreads();
+            rslot = sc[1];
+            __syncthreads();
+            if (rslot >= g.pvcap) { if (tid == 0) set_status(d.status, ST_PATH); continue; }
         }
-        bool eq0 = true;
-        for (uint32_t cb = 0; cb < ncb; ++cb) {
-            if (ncb > 1) load_cases<K>(d, cb, ic.xv);
-            if (ef >= 0) load_vec<K>(par.slots, d.Cpad, par.e_slot[ef], nv, cb);
-            else { eval_run<K, B>(ok_, c, c + s, stA, ic, nv, d.status); st_interp += s; }
-            if (em >= 0) load_vec<K>(par.slots, d.Cpad, par.e_slot[em], ov, cb);
-            else { eval_run<K, B>(g.stash + g.stash_off[i], 0, r, stA, ic, ov, d.status); st_interp += r; }
-            eq0 = same_bits<K>(nv, ov, Cn - cb * 32 * K) && eq0;
-            if (root_rec) {
-                float* dst = g.pv_val + (size_t)rslot * d.Cpad + cb * 32 * K + lane;
-#pragma unroll
-                for (int kk = 0; kk < K; ++kk) dst[kk * 32] = nv[kk];
+        for (uint32_t it = warp; it < 2 * ncb; it += nw) {
+            const uint32_t which = it & 1u, cb = it >> 1;
+            load_cases<K>(d, cb, ic.xv);
+            float v[K];
+            if (which == 0) {
+                if (ef >= 0) load_vec<K>(par.slots, Cpad, par.e_slot[ef], v, cb);
+                else { eval_run<K, B>(ok_, c, c + s, stA, ic, v, d.status); st_interp += s; }
+            } else {
+                if (em >= 0) load_vec<K>(par.slots, Cpad, par.e_slot[em], v, cb);
+                else { eval_run<K, B>(g.stash + g.stash_off[i], 0, r, stA, ic, v, d.status); st_interp += r; }
             }
-            if (ncb > 1) { store_blk<K>(wsn, cb, nv); store_blk<K>(wso, cb, ov); }
+            store_blk<K>(which == 0 ? nvs : ovs, cb, v);
         }
-        bool stopped = eq0;
+        __syncthreads();
+        bool okc = true;
+        for (uint32_t j = tid; j < Cn; j += nthr)
+            if (__float_as_uint(nvs[j]) != __float_as_uint(ovs[j])) okc = false;
+        bool stopped = __syncthreads_and(okc) != 0;
         int32_t stop_level = stopped ? 0 : -1;
         uint32_t levels = 0;
         if (root_rec) {
-            if (lane == 0) { g.pv_rec[rslot] = make_uint4(i, npv, 0u, rslot | 0x80000000u); g.pv_end[rslot] = s; }
+            float* dst = g.pv_val + (size_t)rslot * Cpad;
+            for (uint32_t j = tid; j < Cpad; j += nthr) dst[j] = nvs[j];
+            if (tid == 0) { g.pv_rec[rslot] = make_uint4(i, npv, 0u, rslot | 0x80000000u); g.pv_end[rslot] = s; }
             ++npv;
             ++nins_i;
         }
 
-        // ---- ancestors: deepest cached ancestor A, then the small ones below it
-        int32_t A = -1;
-        uint32_t nsmall = 0;
-        if (em >= 0) A = par.e_par[em];
-        else {
-            int32_t e = find_last_lt(par.e_pos, me0, me1, c);
-            uint32_t guard = 0;
-            while (e >= 0 && par.e_end[e] <= c && guard++ < (1u << 24)) e = par.e_par[e];
-            A = e;
-            if (A < 0) { if (lane == 0) set_error(d, ST_STRUCT, 5, i, c, 0); continue; }
-            // backward scan of (max(pos(A)+1, c-T+1) .. c-1]: G(j) = sum_{k=j}^{c-1} (arity_k - 1);
-            // j is an ancestor of c iff G(j) >= G(m) for every m in (j, c], G(c) = 0
-            const uint32_t pA = par.e_pos[A];
-            const uint32_t lo = max(pA + 1, (c + 1 > T) ? c + 1 - T : 0u);
-            if (lo < c) {
-                __syncwarp();
-                stage_issue(stB, ok_, lo, c);
-                cp_async_commit();
-                cp_async_wait<0>();
-                __syncwarp();
-                const uint32_t a16 = lo & ~15u;
-                // lane l: positions c-1-32l-t, t = 0..31 (nearest first)
-                int sum = 0, mx = -0x40000000;
-                for (int t = 0; t < 32; ++t) {
-                    const int64_t j = (int64_t)c - 1 - 32 * lane - t;
-                    if (j >= (int64_t)lo) { sum += (stB[j - a16] < 4) ? 1 : -1; mx = max(mx, sum); }
-                }
-                // G offset from the lanes nearer to c, and the maximum G seen before this lane
-                int incl = sum;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    int ts = __shfl_up_sync(FULL, incl, o);
-                    if (lane >= o) incl += ts;
-                }
-                const int base = incl - sum;
-                int pm = (mx > -0x40000000) ? base + mx : -0x40000000;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    int tm = __shfl_up_sync(FULL, pm, o);
-                    if (lane >= o) pm = max(pm, tm);
-                }
-                int prevmax = __shfl_up_sync(FULL, pm, 1);
-                if (lane == 0) prevmax = 0;            // G(c) = 0
-                prevmax = max(prevmax, 0);
-                uint32_t fmask = 0;
-                int run = prevmax, gsum = base;
-                for (int t = 0; t < 32; ++t) {
-                    const int64_t j = (int64_t)c - 1 - 32 * lane - t;
-                    if (j >= (int64_t)lo) {
-                        gsum += (stB[j - a16] < 4) ? 1 : -1;
-                        if (gsum >= run) { fmask |= 1u << t; run = gsum; }
-                    }
-                }
-                // compact in nearest-first order
-                const uint32_t cnt = __popc(fmask);
-                uint32_t off = cnt;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    uint32_t tt = __shfl_up_sync(FULL, off, o);
-                    if (lane >= o) off += tt;
-                }
-                off -= cnt;
-                const uint32_t tot = __shfl_sync(FULL, off + cnt, 31);
-                if (tot > WALK_MAXLVL - 2) { if (lane == 0) set_status(d.status, ST_PATH); continue; }
-                gsum = base;
-                uint32_t k = off;
-                for (int t = 0; t < 32; ++t) {
-                    const int64_t j = (int64_t)c - 1 - 32 * lane - t;
-                    if (j >= (int64_t)lo) {
-                        gsum += (stB[j - a16] < 4) ? 1 : -1;
-                        if (fmask & (1u << t)) { anc[k] = (uint32_t)j; ancg[k] = gsum; ++k; }
-                    }
-                }
-                nsmall = tot;
-                __syncwarp();
-            }
+        // ---- ancestors (warp 0), broadcast through shared memory
+        if (warp == 0) {
+            int32_t A = -1, hneed = -1;
+            uint32_t nsmall = 0;
+            const bool ok = walk_ancestors<K>(d, par, i, ok_, c, s, nk, em, me0, me1, stB, anc, ancg, lvl, A,
+                                              nsmall, hneed);
+            if (lane == 0) { sc[2] = nsmall; sc[3] = (uint32_t)A; sc[4] = ok ? 0u : 1u; sc[5] = (uint32_t)hneed; }
         }
-        // ---- child ends of the small ancestors: forward scan after the donated subtree
-        // balance relative to b[c] is 1 at c+s; lvl[v] = first position where it reaches v
-        uint32_t maxv = 1;
-        if (nsmall) maxv = (uint32_t)ancg[nsmall - 1] + 1;
-        if (maxv >= WALK_MAXLVL) { if (lane == 0) set_status(d.status, ST_PATH); continue; }
-        if (nsmall) {
-            const uint32_t f0 = c + s;
-            const uint32_t f1 = f0 + T;
-            // sentinel 0 for levels the scan does not reach: their sibling ranges then fail the
-            // size check below instead of reading a stale end
-            for (uint32_t v = lane; v <= maxv; v += 32) lvl[v] = 0;
-            __syncwarp();
-            const uint32_t lim = min(f1, (nk + 15u) & ~15u);
-            if (f0 < lim) { stage_issue(stB, ok_, f0, lim); }
-            cp_async_commit();
-            cp_async_wait<0>();
-            __syncwarp();
-            const uint32_t a16 = f0 & ~15u;
-            if (lane == 0) lvl[1] = f0;
-            int sum = 0, mx = 0;
-            // lane l: positions f0 + 32l + t
-            for (int t = 0; t < 32; ++t) {
-                const uint32_t q = f0 + 32 * lane + t;
-                const int w = (q < nk && stB[q - a16] < 4) ? -1 : 1;
-                sum += w;
-                mx = max(mx, sum);
-            }
-            int incl = sum;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) { int ts = __shfl_up_sync(FULL, incl, o); if (lane >= o) incl += ts; }
-            const int base = 1 + incl - sum;          // balance before the lane's first position
-            int lmax = base + mx;                      // max after-balance in the lane (or base)
-            lmax = max(lmax, base);
-            int pm = lmax;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) { int tm = __shfl_up_sync(FULL, pm, o); if (lane >= o) pm = max(pm, tm); }
-            int prev = __shfl_up_sync(FULL, pm, 1);
-            if (lane == 0) prev = 1;
-            prev = max(prev, base);
-            int bal = base;
-            for (int t = 0; t < 32; ++t) {
-                const uint32_t q = f0 + 32 * lane + t;
-                bal += (q < nk && stB[q - a16] < 4) ? -1 : 1;
-                if (bal > prev) { if ((uint32_t)bal < WALK_MAXLVL) lvl[bal] = q + 1; prev = bal; }
-            }
-            __syncwarp();
-        }
-        // highest small ancestor that the child caches (needs a value even above the stop)
-        int32_t hneed = -1;
-        for (uint32_t k = 0; k < nsmall; ++k) {
-            const uint32_t p = anc[k];
-            const uint32_t pe = lvl[ancg[k] + 1];
-            if (pe - p >= T) hneed = (int32_t)k;
-        }
+        __syncthreads();
+        const uint32_t nsmall = sc[2];
+        const int32_t A = (int32_t)sc[3];
+        const int32_t hneed = (int32_t)sc[5];
+        if (sc[4]) continue;
 
-        // ---- walk up
-        uint32_t q = c, qend = c + s;
-        int32_t qe = em;                 // entry of q in the mother cache, -1 if small
-        uint32_t k = 0;
-        int32_t pe_ = (nsmall > 0) ? -1 : A;
+        // ---- walk up, a batch of levels at a time
+        uint32_t bq = c, bqend = c + s, bk = 0;          // path state of the descriptor builder (thread 0)
+        int32_t bpe = (nsmall > 0) ? -1 : A;
+        bool btop = false;
         bool done = false;
         uint32_t level = 0;
         uint32_t guard = 0;
         while (!done && guard++ < (1u << 24)) {
-            uint32_t p, pend;
-            int32_t pent;
-            if (k < nsmall) {
-                p = anc[k];
-                pend = lvl[ancg[k] + 1];
-                pent = -1;
-            } else {
-                pent = (k == nsmall) ? A : pe_;
-                if (pent < 0) break;                                 // above the root
-                p = par.e_pos[pent];
-                pend = (uint32_t)((int64_t)par.e_end[pent] + delta);
+            if (tid == 0) {
+                uint32_t nl = 0;
+                while (nl < nlb && !btop) {
+                    uint32_t p, pend;
+                    int32_t pent;
+                    if (bk < nsmall) {
+                        p = anc[bk];
+                        pend = lvl[ancg[bk] + 1];
+                        pent = -1;
+                    } else {
+                        pent = (bk == nsmall) ? A : bpe;
+                        if (pent < 0) { btop = true; break; }                  // above the root
+                        p = par.e_pos[pent];
+                        pend = (uint32_t)((int64_t)par.e_end[pent] + ((int64_t)s - (int64_t)r));
+                    }
+                    // above the stop only small ancestors that the child caches need values
+                    if (stopped && (pent >= 0 || (int32_t)bk > hneed)) { btop = true; break; }
+                    const bool left = (bq == p + 1);
+                    const uint32_t ss = left ? bqend : p + 1;
+                    const uint32_t se = left ? pend : bq;
+                    uint32_t flg = ok_[p] | (left ? LD_LEFT : 0u) | ((p == 0 || pend - p >= T) ? LD_CACHED : 0u);
+                    int32_t sib = -1;
+                    if (se <= ss || se > nk) flg |= LD_BAD;
+                    else if (se - ss >= T) {
+                        sib = (pent < 0) ? -1 : (left ? par.e_c1[pent] : par.e_c0[pent]);
+                        if (sib < 0) flg |= LD_NOSIB;
+                    }
+                    LevelDesc& D = desc[nl++];
+                    D.p = p; D.pend = pend; D.ss = ss; D.se = se; D.pent = pent; D.sib = sib; D.flags = flg;
+                    D.k = (int32_t)bk;
+                    D.pslot = (pent >= 0) ? par.e_slot[pent] : 0u;
+                    D.sslot = (sib >= 0) ? par.e_slot[sib] : 0u;
+                    if (flg & (LD_BAD | LD_NOSIB)) { btop = true; break; }
+                    bq = p;
+                    bqend = pend;
+                    if (bk >= nsmall) bpe = par.e_par[pent];
+                    ++bk;
+                    if (p == 0) { btop = true; break; }
+                }
+                sc[6] = nl;
+                sc[7] = btop ? 1u : 0u;
             }
-            ++level;
-            const bool child_cached = (p == 0) || (pend - p >= T);
-            if (stopped) {
-                // values agree from here up; only small ancestors cached in the child need them
-                if (pent >= 0 || (int32_t)k > hneed) break;
+            __syncthreads();
+            const uint32_t nl = sc[6];
+            const bool top = sc[7] != 0;
+            if (nl == 0) break;
+            // siblings of the batch's levels, one (level, case block) per warp at a time
+            for (uint32_t it = warp; it < nl * ncb; it += nw) {
+                const uint32_t l = it / ncb, cb = it - l * ncb;
+                const LevelDesc& D = desc[l];
+                if (D.flags & (LD_BAD | LD_NOSIB)) continue;
+                if (stopped && (D.pent >= 0 || D.k > hneed)) continue;       // never combined
+                float v[K];
+                // the mother's cached value at p, needed for the comparison below the stop
+                if (!stopped && D.pent >= 0) {
+                    load_vec<K>(par.slots, Cpad, D.pslot, v, cb);
+                    store_blk<K>(mvs + l * Cpad, cb, v);
+                }
+                if (D.sib >= 0) load_vec<K>(par.slots, Cpad, D.sslot, v, cb);
+                else {
+                    load_cases<K>(d, cb, ic.xv);
+                    eval_run<K, B>(ok_, D.ss, D.se, stA, ic, v, d.status);
+                    st_interp += D.se - D.ss;
+                }
+                store_blk<K>(svs + l * Cpad, cb, v);
             }
-            const uint32_t op = ok_[p];
-            const bool left = (q == p + 1);
-            const uint32_t ss = left ? qend : p + 1;
-            const uint32_t se = left ? pend : q;
-            if (se <= ss || se > nk) { if (lane == 0) set_error(d, ST_STRUCT, 6, i, p, (se << 0)); break; }
-            int32_t sib = -1;
-            if (se - ss >= T) {
-                sib = (pent < 0) ? -1 : (left ? par.e_c1[pent] : par.e_c0[pent]);
-                if (sib < 0) { if (lane == 0) set_error(d, ST_STRUCT, 7, i, p, se - ss); done = true; break; }
-            }
-            bool lvl_eq = true;
-            for (uint32_t cb = 0; cb < ncb; ++cb) {
-                if (ncb > 1) { load_cases<K>(d, cb, ic.xv); load_blk<K>(wsn, cb, nv); load_blk<K>(wso, cb, ov); }
-                float sv[K];
-                if (sib >= 0) load_vec<K>(par.slots, d.Cpad, par.e_slot[sib], sv, cb);
-                else { eval_run<K, B>(ok_, ss, se, stA, ic, sv, d.status); st_interp += se - ss; }
-                combine<K, B>(op, left, ov, sv);            // mother's value at p (exact recomputation)
+            __syncthreads();
+            for (uint32_t l = 0; l < nl; ++l) {
+                const LevelDesc D = desc[l];
+                if (stopped && (D.pent >= 0 || D.k > hneed)) { done = true; break; }
+                ++level;
+                if (D.flags & (LD_BAD | LD_NOSIB)) {
+                    if (tid == 0) set_error(d, ST_STRUCT, (D.flags & LD_BAD) ? 6 : 7, i, D.p, D.se - D.ss);
+                    done = true;
+                    break;
+                }
+                const uint32_t op = D.flags & 0xFFu;
+                const bool left = (D.flags & LD_LEFT) != 0;
+                const float* svl = svs + l * Cpad;
+                const float* pvv = (D.pent >= 0) ? mvs + l * Cpad : nullptr;
+                bool okl = true;
+                for (uint32_t j = tid; j < Cpad; j += nthr) {
+                    float o[1] = {ovs[j]};
+                    const float sv1[1] = {svl[j]};
+                    combine<1, B>(op, left, o, sv1);         // mother's value at p (exact recomputation)
+                    if (!stopped) {
+                        float n1[1] = {nvs[j]};
+                        combine<1, B>(op, left, n1, sv1);
+                        nvs[j] = n1[0];
+                        if (pvv) o[0] = pvv[j];
+                        if (j < Cn && __float_as_uint(n1[0]) != __float_as_uint(o[0])) okl = false;
+                    }
+                    ovs[j] = o[0];
+                }
+                const bool lvl_eq = __syncthreads_and(okl) != 0;
                 if (!stopped) {
-                    combine<K, B>(op, left, nv, sv);
-                    if (pent >= 0) load_vec<K>(par.slots, d.Cpad, par.e_slot[pent], ov, cb);
-                    lvl_eq = same_bits<K>(nv, ov, Cn - cb * 32 * K) && lvl_eq;
+                    ++levels;
+                    ++st_pathops;
+                    if (lvl_eq) { stopped = true; stop_level = (int32_t)level; }
                 }
-                if (ncb > 1) { store_blk<K>(wsn, cb, nv); store_blk<K>(wso, cb, ov); }
-            }
-            if (!stopped) {
-                ++levels;
-                ++st_pathops;
-                if (lvl_eq) { stopped = true; stop_level = (int32_t)level; }
-            }
-            // record the child's value here when the child caches this node and the mother's
-            // cache cannot supply it (disrupted, or not cached in the mother); above the
-            // stop only small ancestors (pent < 0) get here
-            if (child_cached && (!lvl_eq || pent < 0)) {
-                uint32_t slot = 0;
-                if (lane == 0) slot = atomicAdd(&g.misc[M_PV], 1u);
-                slot = __shfl_sync(FULL, slot, 0);
-                if (slot >= g.pvcap) { if (lane == 0) set_status(d.status, ST_PATH); done = true; break; }
-                float* dst = g.pv_val + (size_t)slot * d.Cpad + lane;
-                if (ncb == 1) {
-                    const float (&val)[K] = stopped ? ov : nv;
-#pragma unroll
-                    for (int kk = 0; kk < K; ++kk) dst[kk * 32] = val[kk];
-                } else {
-                    const float* row = stopped ? wso : wsn;
-                    for (uint32_t e = 0; e < ncb * K; ++e) dst[e * 32] = row[e * 32 + lane];
+                // record the child's value here when the child caches this node and the mother's
+                // cache cannot supply it (disrupted, or not cached in the mother); above the
+                // stop only small ancestors (pent < 0) get here
+                if ((D.flags & LD_CACHED) && (!lvl_eq || D.pent < 0)) {
+                    if (tid == 0) sc[1] = atomicAdd(&g.misc[M_PV], 1u);
+                    __syncthreads();
+                    const uint32_t slot = sc[1];
+                    if (slot >= g.pvcap) { if (tid == 0) set_status(d.status, ST_PATH); done = true; break; }
+                    const float* src = stopped ? ovs : nvs;
+                    float* dst = g.pv_val + (size_t)slot * Cpad;
+                    for (uint32_t j = tid; j < Cpad; j += nthr) dst[j] = src[j];
+                    if (tid == 0) {
+                        g.pv_rec[slot] = make_uint4(i, npv, D.p, slot | (D.pent < 0 ? 0x80000000u : 0u));
+                        g.pv_end[slot] = D.pend;
+                    }
+                    ++npv;
+                    if (D.pent < 0) ++nins_i;
                 }
-                if (lane == 0) {
-                    g.pv_rec[slot] = make_uint4(i, npv, p, slot | (pent < 0 ? 0x80000000u : 0u));
-                    g.pv_end[slot] = pend;
-                }
-                ++npv;
-                if (pent < 0) ++nins_i;
+                if (D.p == 0) { done = true; break; }
             }
-            q = p;
-            qend = pend;
-            qe = pent;
-            if (k >= nsmall) pe_ = par.e_par[pent];
-            ++k;
-            if (p == 0) break;
+            if (top) done = true;
+            __syncthreads();                 // the builder rewrites the descriptors next
         }
-        (void)qe;
         // ---- fitness
-        if (lane == 0) { g.stop[i] = stop_level; g.plen[i] = levels; g.pv_cnt[i] = npv; g.nins[i] = nins_i; g.walkA[i] = A; }
-        if (stopped) {
-            if (lane == 0) d.fit[i] = g.pfit[m];
-            ++st_stopped;
-        } else {
-            // case cc of the child's root vector sits at vec[cc] in either layout
-            const float* vec = red;
-            if (ncb == 1) {
-#pragma unroll
-                for (int kk = 0; kk < K; ++kk) red[kk * 32 + lane] = nv[kk];
+        if (tid == 0) {
+            g.stop[i] = stop_level;
+            g.plen[i] = levels;
+            g.pv_cnt[i] = npv;
+            g.nins[i] = nins_i;
+            g.walkA[i] = A;
+            if (stopped) {
+                d.fit[i] = g.pfit[m];
+                ++st_stopped;
             } else {
-                vec = wsn;
-            }
-            __syncwarp();
-            if (lane == 0) {
                 float fsum = 0.0f;
                 if (B) {
-                    fsum = (float)(__popc(__float_as_uint(vec[0]) ^ mux_target_half(0)) +
-                                   __popc(__float_as_uint(vec[1]) ^ mux_target_half(1)));
+                    fsum = (float)(__popc(__float_as_uint(nvs[0]) ^ mux_target_half(0)) +
+                                   __popc(__float_as_uint(nvs[1]) ^ mux_target_half(1)));
                 } else {
-                    for (uint32_t cc = 0; cc < Cn; ++cc) fsum = __fadd_rn(fsum, fabsf(__fsub_rn(vec[cc], d.t[cc])));
+                    for (uint32_t cc = 0; cc < Cn; ++cc) fsum = __fadd_rn(fsum, fabsf(__fsub_rn(nvs[cc], d.t[cc])));
                 }
                 d.fit[i] = fsum;
             }
-            __syncwarp();
+            st_levels += levels;
         }
-        st_levels += levels;
     }
-    if (lane == 0) {
-        atomicAdd(&g.gstat[G_INTERP], st_interp);
+    if (lane == 0) atomicAdd(&g.gstat[G_INTERP], st_interp);
+    if (tid == 0) {
         atomicAdd(&g.gstat[G_LEVELS], st_levels);
         atomicAdd(&g.gstat[G_STOPPED], st_stopped);
         atomicAdd(&g.gstat[G_PATHOPS], st_pathops);

@@ -55,6 +55,11 @@ struct gp_pop {
     bool profiling;
     cudaEvent_t ev[NPH][NREC][2];
     uint32_t ev_count[NPH];
+    // phase events recorded by a captured graph (external event-record nodes):
+    // the stats of a replay average the generations of the last replay
+    cudaEvent_t gev[NPH][NREC][2];
+    uint32_t gev_n[NPH];
+    bool gev_made, capturing, graph_prof, stats_graph;
     bool have_children;
     std::vector<void*> allocs;
     uint64_t total_nodes_last;
@@ -73,6 +78,7 @@ struct gp_pop {
     uint32_t cum_calls;
     int grid_walk;
     int grid_walk_max;
+    uint32_t walk_nw;                 // warps per child in the incremental walk
     size_t smem_walk;
     MlpBufs mlp;
     float mlp_lr;
@@ -126,10 +132,23 @@ int dalloc(gp_pop* pop, T** ptr, size_t count) {
     } while (0)
 
 void phase_begin(gp_pop* pop, int ph) {
-    if (pop->profiling) cudaEventRecord(pop->ev[ph][pop->ev_count[ph] % NREC][0], pop->stream);
+    if (!pop->profiling) return;
+    if (pop->capturing) {
+        if (pop->gev_n[ph] < (uint32_t)NREC)
+            cudaEventRecordWithFlags(pop->gev[ph][pop->gev_n[ph]][0], pop->stream, cudaEventRecordExternal);
+        return;
+    }
+    cudaEventRecord(pop->ev[ph][pop->ev_count[ph] % NREC][0], pop->stream);
 }
 void phase_end(gp_pop* pop, int ph) {
-    if (pop->profiling) cudaEventRecord(pop->ev[ph][pop->ev_count[ph]++ % NREC][1], pop->stream);
+    if (!pop->profiling) return;
+    if (pop->capturing) {
+        if (pop->gev_n[ph] < (uint32_t)NREC)
+            cudaEventRecordWithFlags(pop->gev[ph][pop->gev_n[ph]++][1], pop->stream, cudaEventRecordExternal);
+        return;
+    }
+    pop->stats_graph = false;
+    cudaEventRecord(pop->ev[ph][pop->ev_count[ph]++ % NREC][1], pop->stream);
 }
 
 int check_status(gp_pop* pop) {
@@ -210,16 +229,39 @@ int setup_items_kernel(gp_pop* pop) {
     return GP_OK;
 }
 
+// Team size of the incremental walk (warps per child) and its launch
+// shape.  Auto: the largest team (8, 4, 2) with which every child of the
+// population gets its own team at once, else one warp per child (more
+// children than teams: throughput first).
 template <int K, bool B = false>
-int setup_walk_kernel(gp_pop* pop) {
-    size_t smem = WalkSmem<K>::total((int)pop->d.W, GP_WARPS);
-    CK(cudaFuncSetAttribute(k_walk<K, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    int nb = 0;
-    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_walk<K, B>, GP_WARPS * 32, smem));
-    if (nb < 1) nb = 1;
-    // the walk shares the interpreter's per-warp overflow stacks
-    pop->grid_walk = nb * pop->nsm;
-    if (pop->grid_walk > pop->grid_items) pop->grid_walk = pop->grid_items;
+int setup_walk_kernel(gp_pop* pop, uint32_t team) {
+    const uint32_t ovf = pop->d.ovf_warps;      // the walk shares the interpreter's per-warp overflow stacks
+    CK(cudaFuncSetAttribute(k_walk<K, B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            (int)TeamLayout<K>((int)pop->d.W, pop->d.Cpad, 8).total));
+    auto shape = [&](uint32_t nw, int& grid, size_t& smem) -> int {
+        smem = TeamLayout<K>((int)pop->d.W, pop->d.Cpad, nw).total;
+        int nb = 0;
+        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_walk<K, B>, (int)nw * 32, smem));
+        if (nb < 1) nb = 1;
+        grid = nb * pop->nsm;
+        if ((uint32_t)grid * nw > ovf) grid = (int)(ovf / nw);
+        return GP_OK;
+    };
+    uint32_t nw = team;
+    int grid = 0;
+    size_t smem = 0;
+    if (!nw) {
+        nw = 1;
+        for (uint32_t cand : {8u, 4u, 2u}) {
+            int r = shape(cand, grid, smem);
+            if (r) return r;
+            if ((uint32_t)grid >= pop->d.P) { nw = cand; break; }
+        }
+    }
+    int r = shape(nw, grid, smem);
+    if (r) return r;
+    pop->walk_nw = nw;
+    pop->grid_walk = grid;
     pop->smem_walk = smem;
     return GP_OK;
 }
@@ -402,6 +444,9 @@ int gp_pop_create(const gp_config* cfg_in, const float* x, const float* targets,
     uint32_t K = cfg.cases_per_lane;
     if (K == 0) K = (cfg.n_cases <= 32) ? 1 : 2;
     if (K != 1 && K != 2 && K != 4) return fail(nullptr, GP_EINVAL, "cases_per_lane must be 0, 1, 2 or 4");
+    if (cfg.walk_team != 0 && cfg.walk_team != 1 && cfg.walk_team != 2 && cfg.walk_team != 4 && cfg.walk_team != 8)
+        return fail(nullptr, GP_EINVAL, "walk_team must be 0, 1, 2, 4 or 8");
+    if (cfg.reserved != 0) return fail(nullptr, GP_EINVAL, "reserved config field must be 0");
     const uint32_t P = cfg.pop_size;
     for (uint32_t i = 0; i < P; ++i) {
         if (offsets[i + 1] < offsets[i]) return fail(nullptr, GP_EINVAL, "offsets not increasing at %u", i);
@@ -427,6 +472,8 @@ int gp_pop_create(const gp_config* cfg_in, const float* x, const float* targets,
     pop->gexec = nullptr;
     pop->graph_n = 0;
     pop->cap_stream = nullptr;
+    pop->gev_made = pop->capturing = pop->graph_prof = pop->stats_graph = false;
+    memset(pop->gev_n, 0, sizeof pop->gev_n);
     auto bail = [&](int code) { gp_pop_destroy(pop); return code; };
     cudaError_t ce = cudaGetDevice(&pop->dev);
     if (ce != cudaSuccess) { g_create_error = cudaGetErrorString(ce); delete pop; return GP_ECUDA; }
@@ -529,6 +576,7 @@ int gp_pop_create(const gp_config* cfg_in, const float* x, const float* targets,
         DA2(g.frag_off, P + 1); DA2(g.frag, g.frag_cap + 64);
         DA2(g.stash_off, P + 1); DA2(g.stash, g.stash_cap + 64);
         DA2(g.shift_off, P + 1); DA2(g.halo, (size_t)g.shift_cap * HALO_MAX);
+        DA2(g.copy_off, P + 1);
         DA2(g.stop, P); DA2(g.plen, P);
         DA2(g.pv_rec, g.pvcap); DA2(g.pv_cnt, P); DA2(g.pv_off, P + 1); DA2(g.pv_sorted, g.pvcap);
         DA2(g.pv_end, g.pvcap); DA2(g.pv_val, (size_t)g.pvcap * d.Cpad);
@@ -542,14 +590,14 @@ int gp_pop_create(const gp_config* cfg_in, const float* x, const float* targets,
     }
     // incremental walk launch shape
     {
-        int r = (cfg.funcset == GP_BOOL_MUX6) ? setup_walk_kernel<1, true>(pop)
-                : (K == 1) ? setup_walk_kernel<1>(pop) : (K == 2) ? setup_walk_kernel<2>(pop) : setup_walk_kernel<4>(pop);
+        const uint32_t team = cfg.walk_team;
+        int r = (cfg.funcset == GP_BOOL_MUX6) ? setup_walk_kernel<1, true>(pop, team)
+                : (K == 1) ? setup_walk_kernel<1>(pop, team) : (K == 2) ? setup_walk_kernel<2>(pop, team)
+                : setup_walk_kernel<4>(pop, team);
         if (r) return bail(r);
         pop->grid_walk_max = pop->grid_walk;
-        // running-value rows of the walk when a vector spans several case blocks
-        DA2(pop->gb.wscr, d.ncb > 1 ? (size_t)pop->grid_walk * GP_WARPS * 2 * d.Cpad : 4);
         if (cfg.walk_warps) {
-            int g = (int)((cfg.walk_warps + GP_WARPS - 1) / GP_WARPS);
+            int g = (int)((cfg.walk_warps + pop->walk_nw - 1) / pop->walk_nw);
             if (g < pop->grid_walk) pop->grid_walk = g;
         }
     }
@@ -610,6 +658,9 @@ void gp_pop_destroy(gp_pop* pop) {
     if (pop->stage_off) cudaFree(pop->stage_off);
     for (int i = 0; i < NPH; ++i)
         for (int j = 0; j < NREC; ++j) { cudaEventDestroy(pop->ev[i][j][0]); cudaEventDestroy(pop->ev[i][j][1]); }
+    if (pop->gev_made)
+        for (int i = 0; i < NPH; ++i)
+            for (int j = 0; j < NREC; ++j) { cudaEventDestroy(pop->gev[i][j][0]); cudaEventDestroy(pop->gev[i][j][1]); }
     delete pop;
 }
 
@@ -691,6 +742,11 @@ int gp_graph_capture(gp_pop* pop, uint32_t first_generation, uint32_t n_generati
     // capturing runs the host side of every generation without executing it:
     // keep the host state and put it back afterwards (with an even count the
     // double-buffer roles end where they began)
+    if (pop->profiling && !pop->gev_made) {
+        for (int i = 0; i < NPH; ++i)
+            for (int j = 0; j < NREC; ++j) { CK(cudaEventCreate(&pop->gev[i][j][0])); CK(cudaEventCreate(&pop->gev[i][j][1])); }
+        pop->gev_made = true;
+    }
     // the legacy default stream cannot be captured: capture on a private
     // stream (the graph is then launched on the population's own stream)
     cudaStream_t own = pop->stream;
@@ -707,10 +763,10 @@ int gp_graph_capture(gp_pop* pop, uint32_t first_generation, uint32_t n_generati
     const DevPop d0 = pop->d;
     const GenBufs g0 = g;
     const int cur0 = pop->cur;
-    const bool prof0 = pop->profiling;
     const uint32_t calls0 = pop->cum_calls;
     const int kind0 = pop->last_kind;
-    pop->profiling = false;
+    pop->capturing = true;
+    memset(pop->gev_n, 0, sizeof pop->gev_n);
     g.gen_add = pop->gwords + 1;
     uint32_t launches = 0;
     cudaGraph_t graph = nullptr;
@@ -727,7 +783,8 @@ int gp_graph_capture(gp_pop* pop, uint32_t first_generation, uint32_t n_generati
     g = g0;
     pop->cur = cur0;
     bind_set(pop);
-    pop->profiling = prof0;
+    pop->capturing = false;
+    pop->graph_prof = pop->profiling;
     pop->cum_calls = calls0;
     pop->last_kind = kind0;
     pop->have_children = false;
@@ -736,6 +793,9 @@ int gp_graph_capture(gp_pop* pop, uint32_t first_generation, uint32_t n_generati
     ce = cudaGraphInstantiate(&pop->gexec, graph, 0);
     cudaGraphDestroy(graph);
     if (ce != cudaSuccess) { pop->gexec = nullptr; cudaGetLastError(); return fail(pop, GP_ECUDA, "graph instantiation failed: %s", cudaGetErrorString(ce)); }
+    // upload now, so that the first replay does not pay for it
+    ce = cudaGraphUpload(pop->gexec, own ? own : 0);
+    if (ce != cudaSuccess) { cudaGetLastError(); return fail(pop, GP_ECUDA, "graph upload failed: %s", cudaGetErrorString(ce)); }
     pop->graph_n = n_generations;
     pop->graph_launches = launches + 1;
     return GP_OK;
@@ -748,6 +808,7 @@ int gp_graph_launch(gp_pop* pop) {
         return fail(pop, GP_ESTATE, "gp_graph_launch needs an evaluated population with no pending children");
     CK(cudaGraphLaunch(pop->gexec, pop->stream));
     pop->cum_calls += pop->graph_n;
+    pop->stats_graph = pop->graph_prof && pop->profiling;
     pop->launches = pop->graph_launches;
     pop->last_kind = 1;
     return GP_OK;
@@ -920,9 +981,7 @@ int gp_mlp_eval_grad(const float* w, const float* x, const float* y, uint32_t n,
         cudaMemcpy(b.w, w, sizeof(float) * MLP_NP, cudaMemcpyHostToDevice);
         cudaMemcpy(b.feat, x, sizeof(float) * n * MLP_IN, cudaMemcpyHostToDevice);
         cudaMemcpy(b.target, y, sizeof(float) * n, cudaMemcpyHostToDevice);
-        const int pb = (int)((n + 255) / 256);
-        k_mlp_forward_train<<<pb, 256>>>(b, n);
-        k_mlp_backward_act<<<pb, 256>>>(b, n);
+        k_mlp_train_pass<<<(n + 7) / 8 < 1024 ? (n + 7) / 8 : 1024, 256>>>(b, n);
         k_mlp_loss<<<1, 256>>>(b, n);
         k_mlp_backward_params<<<(MLP_NP + 255) / 256, 256>>>(b, n);
         if (cudaDeviceSynchronize() != cudaSuccess) rc = GP_ECUDA;
@@ -944,13 +1003,17 @@ int gp_get_stats(const gp_pop* cpop, gp_stats* out) {
     gp_stats s = pop->stats;
     for (int i = 0; i < NPH && i < 8; ++i) {
         s.ms[i] = 0.f;
-        uint32_t n = pop->ev_count[i] < (uint32_t)NREC ? pop->ev_count[i] : (uint32_t)NREC;
+        const bool gr = pop->stats_graph;
+        uint32_t n = gr ? pop->gev_n[i] : (pop->ev_count[i] < (uint32_t)NREC ? pop->ev_count[i] : (uint32_t)NREC);
         if (!pop->profiling || n == 0) continue;
         double tot = 0.0;
         uint32_t got = 0;
         for (uint32_t j = 0; j < n; ++j) {
             float ms = 0.f;
-            if (cudaEventElapsedTime(&ms, pop->ev[i][j][0], pop->ev[i][j][1]) == cudaSuccess) { tot += ms; ++got; }
+            cudaEvent_t a = gr ? pop->gev[i][j][0] : pop->ev[i][j][0];
+            cudaEvent_t b = gr ? pop->gev[i][j][1] : pop->ev[i][j][1];
+            if (cudaEventElapsedTime(&ms, a, b) == cudaSuccess) { tot += ms; ++got; }
+            else cudaGetLastError();          // a pair never recorded: skip it, leave no sticky error
         }
         s.ms[i] = got ? (float)(tot / got) : 0.f;     // mean over the recorded calls
     }
@@ -1002,7 +1065,7 @@ void swap_generation(gp_pop* pop) {
 
 template <int K, bool B = false>
 void launch_walk(gp_pop* pop, const CacheView& par) {
-    k_walk<K, B><<<pop->grid_walk, GP_WARPS * 32, pop->smem_walk, pop->stream>>>(pop->d, pop->gb, par);
+    k_walk<K, B><<<pop->grid_walk, pop->walk_nw * 32, pop->smem_walk, pop->stream>>>(pop->d, pop->gb, par, pop->walk_nw);
 }
 
 }  // namespace
@@ -1029,7 +1092,7 @@ int gen_crossover(gp_pop* pop, uint32_t generation) {
     k_plan<<<(d.P + 255) / 256, 256, 0, pop->stream>>>(d, g, par);
     k_assign<<<1, 1024, 0, pop->stream>>>(d, g);
     k_gather<<<pop->nsm * 4, 256, 0, pop->stream>>>(d, g);
-    k_copy_children<<<pop->nsm * 4, 256, 0, pop->stream>>>(d, g);
+    k_copy_children<<<pop->nsm * 8, 256, 0, pop->stream>>>(d, g);
     k_save_halo<<<gt, 256, 0, pop->stream>>>(d, g);
     k_shift<<<pop->nsm * 8, 256, 0, pop->stream>>>(d, g);
     k_write_frags<<<pop->nsm * 4, 256, 0, pop->stream>>>(d, g);
@@ -1053,7 +1116,8 @@ int gen_incremental(gp_pop* pop) {
     phase_begin(pop, PH_PACK);
     const int pb = (d.P + 255) / 256;
     k_mlp_features<<<pb, 256, 0, pop->stream>>>(d, g, par, pop->mlp);
-    k_mlp_infer<<<pb, 256, 0, pop->stream>>>(pop->mlp, d.P, pop->mlp.pred_pack);
+    const int mb = (d.P + 7) / 8 < pop->nsm * 2 ? (d.P + 7) / 8 : pop->nsm * 2;   // 8 samples per CTA pass
+    k_mlp_infer<<<mb, 256, 0, pop->stream>>>(pop->mlp, d.P, pop->mlp.pred_pack);
     if (pop->cfg.packing == GP_PACK_MLP && d.P <= SORT_MAX) {
         k_sort_desc<<<1, 1024, 0, pop->stream>>>(pop->mlp.pred_pack, d.P, g.order);
     } else if (pop->cfg.packing == GP_PACK_STATIC && d.P <= SORT_MAX) {
@@ -1069,8 +1133,7 @@ int gen_incremental(gp_pop* pop) {
     phase_end(pop, PH_WALK);
     // online training of the packing MLP on the levels the walks took
     k_mlp_targets<<<pb, 256, 0, pop->stream>>>(d, g, pop->mlp);
-    k_mlp_forward_train<<<pb, 256, 0, pop->stream>>>(pop->mlp, d.P);
-    k_mlp_backward_act<<<pb, 256, 0, pop->stream>>>(pop->mlp, d.P);
+    k_mlp_train_pass<<<mb, 256, 0, pop->stream>>>(pop->mlp, d.P);
     k_mlp_loss<<<1, 256, 0, pop->stream>>>(pop->mlp, d.P);
     k_mlp_backward_params<<<(MLP_NP + 255) / 256, 256, 0, pop->stream>>>(pop->mlp, d.P);
     k_mlp_adam<<<(MLP_NP + 255) / 256, 256, 0, pop->stream>>>(pop->mlp, pop->mlp_lr);

@@ -41,45 +41,98 @@ struct MlpBufs {
     uint32_t cap;
 };
 
-// ---- forward (FP32 master weights), keeping activations for the backward pass
-__global__ void k_mlp_forward_train(MlpBufs b, uint32_t n) {
-    for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
-        const float* x = b.feat + (size_t)s * MLP_IN;
-        float h1[MLP_H];
-        for (int j = 0; j < MLP_H; ++j) {
-            float a = b.w[MLP_B1 + j];
-            for (int f = 0; f < MLP_IN; ++f) a = fmaf(b.w[MLP_W1 + j * MLP_IN + f], x[f], a);
-            h1[j] = a > 0.f ? a : 0.f;
-            b.h1[(size_t)s * MLP_H + j] = h1[j];
-        }
-        float y = b.w[MLP_B3];
-        for (int j = 0; j < MLP_H; ++j) {
-            float a = b.w[MLP_B2 + j];
-            for (int k = 0; k < MLP_H; ++k) a = fmaf(b.w[MLP_W2 + j * MLP_H + k], h1[k], a);
-            const float h = a > 0.f ? a : 0.f;
-            b.h2[(size_t)s * MLP_H + j] = h;
-            y = fmaf(b.w[MLP_W3 + j], h, y);
-        }
-        b.pred[s] = y;
-        // loss = mean (y - t)^2 -> dL/dy = 2 (y - t) / n
-        b.dy[s] = 2.f * (y - b.target[s]) / (float)n;
+// Weights staged in shared memory for warp-per-sample passes: W1 transposed
+// ([16][64], so that lane j reads unit j's weights without bank conflicts),
+// W2 both ways ([64][64] row-major for the backward pass, transposed for the
+// forward pass), biases and the output layer.
+struct MlpSmem {
+    float w1t[MLP_IN * MLP_H];
+    float b1[MLP_H];
+    float w2[MLP_H * MLP_H];
+    float w2t[MLP_H * MLP_H];
+    float b2[MLP_H];
+    float w3[MLP_H];
+    float b3;
+};
+
+template <bool BF16>
+__device__ void mlp_stage(MlpSmem& m, const MlpBufs& b) {
+    for (uint32_t p = threadIdx.x; p < MLP_NP; p += blockDim.x) {
+        const float w = BF16 ? __bfloat162float(b.wb[p]) : b.w[p];
+        if (p < MLP_B1) m.w1t[(p % MLP_IN) * MLP_H + p / MLP_IN] = w;
+        else if (p < MLP_W2) m.b1[p - MLP_B1] = w;
+        else if (p < MLP_B2) {
+            const uint32_t q = p - MLP_W2;
+            m.w2[q] = w;
+            m.w2t[(q % MLP_H) * MLP_H + q / MLP_H] = w;
+        } else if (p < MLP_W3) m.b2[p - MLP_B2] = w;
+        else if (p < MLP_B3) m.w3[p - MLP_W3] = w;
+        else m.b3 = w;
     }
 }
 
-// dh2 = dy * w3 * [h2 > 0]; dh1 = (W2^T dh2) * [h1 > 0]
-__global__ void k_mlp_backward_act(MlpBufs b, uint32_t n) {
-    for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
-        float dh2[MLP_H];
+// One sample by one warp: lane l holds hidden units l and l + 32 of both
+// layers; returns the output (all lanes).
+__device__ __forceinline__ float mlp_forward_warp(const MlpSmem& m, const float* __restrict__ x, float& h1a,
+                                                  float& h1b, float& h2a, float& h2b) {
+    const int lane = lane_id();
+    const float xv = lane < MLP_IN ? x[lane] : 0.f;
+    float a0 = m.b1[lane], a1 = m.b1[lane + 32];
+#pragma unroll
+    for (int f = 0; f < MLP_IN; ++f) {
+        const float xf = __shfl_sync(FULL, xv, f);
+        a0 = fmaf(m.w1t[f * MLP_H + lane], xf, a0);
+        a1 = fmaf(m.w1t[f * MLP_H + lane + 32], xf, a1);
+    }
+    h1a = a0 > 0.f ? a0 : 0.f;
+    h1b = a1 > 0.f ? a1 : 0.f;
+    float c0 = m.b2[lane], c1 = m.b2[lane + 32];
+#pragma unroll 8
+    for (int k = 0; k < MLP_H; ++k) {
+        const float hk = __shfl_sync(FULL, k < 32 ? h1a : h1b, k & 31);
+        c0 = fmaf(m.w2t[k * MLP_H + lane], hk, c0);
+        c1 = fmaf(m.w2t[k * MLP_H + lane + 32], hk, c1);
+    }
+    h2a = c0 > 0.f ? c0 : 0.f;
+    h2b = c1 > 0.f ? c1 : 0.f;
+    float y = fmaf(m.w3[lane], h2a, m.w3[lane + 32] * h2b);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) y += __shfl_xor_sync(FULL, y, o);
+    return y + m.b3;
+}
+
+// Training pass over the batch (FP32 master weights): forward, keeping the
+// activations, then dL/dy for loss = mean (y - t)^2 and the activation
+// gradients dh2 = dy * w3 * [h2 > 0], dh1 = (W2^T dh2) * [h1 > 0].
+__global__ void __launch_bounds__(256) k_mlp_train_pass(MlpBufs b, uint32_t n) {
+    __shared__ MlpSmem m;
+    mlp_stage<false>(m, b);
+    __syncthreads();
+    const int lane = lane_id();
+    const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t s = gw; s < n; s += nwarps) {
+        float h1a, h1b, h2a, h2b;
+        const float y = mlp_forward_warp(m, b.feat + (size_t)s * MLP_IN, h1a, h1b, h2a, h2b);
+        float* H1 = b.h1 + (size_t)s * MLP_H;
+        float* H2 = b.h2 + (size_t)s * MLP_H;
+        H1[lane] = h1a; H1[lane + 32] = h1b;
+        H2[lane] = h2a; H2[lane + 32] = h2b;
+        const float dy = 2.f * (y - b.target[s]) / (float)n;
+        if (lane == 0) { b.pred[s] = y; b.dy[s] = dy; }
+        const float d2a = h2a > 0.f ? dy * m.w3[lane] : 0.f;
+        const float d2b = h2b > 0.f ? dy * m.w3[lane + 32] : 0.f;
+        float* D2 = b.dh2 + (size_t)s * MLP_H;
+        D2[lane] = d2a; D2[lane + 32] = d2b;
+        float e0 = 0.f, e1 = 0.f;
+#pragma unroll 8
         for (int j = 0; j < MLP_H; ++j) {
-            dh2[j] = (b.h2[(size_t)s * MLP_H + j] > 0.f) ? b.dy[s] * b.w[MLP_W3 + j] : 0.f;
-            b.dh2[(size_t)s * MLP_H + j] = dh2[j];
+            const float dj = __shfl_sync(FULL, j < 32 ? d2a : d2b, j & 31);
+            e0 = fmaf(m.w2[j * MLP_H + lane], dj, e0);
+            e1 = fmaf(m.w2[j * MLP_H + lane + 32], dj, e1);
         }
-        for (int k = 0; k < MLP_H; ++k) {
-            float a = 0.f;
-            if (b.h1[(size_t)s * MLP_H + k] > 0.f)
-                for (int j = 0; j < MLP_H; ++j) a = fmaf(b.w[MLP_W2 + j * MLP_H + k], dh2[j], a);
-            b.dh1[(size_t)s * MLP_H + k] = a;
-        }
+        float* D1 = b.dh1 + (size_t)s * MLP_H;
+        D1[lane] = h1a > 0.f ? e0 : 0.f;
+        D1[lane + 32] = h1b > 0.f ? e1 : 0.f;
     }
 }
 
@@ -145,28 +198,17 @@ __global__ void k_mlp_adam(MlpBufs b, float lr) {
 
 __global__ void k_mlp_bump(MlpBufs b) { if (threadIdx.x == 0 && blockIdx.x == 0) *b.step += 1; }
 
-// Inference with the BF16 weights staged in shared memory.
+// Inference with the BF16 copy of the weights (staged in shared memory as
+// FP32), one sample per warp.
 __global__ void __launch_bounds__(256) k_mlp_infer(MlpBufs b, uint32_t n, float* __restrict__ out) {
-    __shared__ float w[MLP_NP];
-    for (uint32_t p = threadIdx.x; p < MLP_NP; p += blockDim.x) w[p] = __bfloat162float(b.wb[p]);
+    __shared__ MlpSmem m;
+    mlp_stage<true>(m, b);
     __syncthreads();
-    for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
-        const float* x = b.feat + (size_t)s * MLP_IN;
-        float xv[MLP_IN];
-        for (int f = 0; f < MLP_IN; ++f) xv[f] = x[f];
-        float h1[MLP_H];
-        for (int j = 0; j < MLP_H; ++j) {
-            float a = w[MLP_B1 + j];
-            for (int f = 0; f < MLP_IN; ++f) a = fmaf(w[MLP_W1 + j * MLP_IN + f], xv[f], a);
-            h1[j] = a > 0.f ? a : 0.f;
-        }
-        float y = w[MLP_B3];
-        for (int j = 0; j < MLP_H; ++j) {
-            float a = w[MLP_B2 + j];
-            for (int k = 0; k < MLP_H; ++k) a = fmaf(w[MLP_W2 + j * MLP_H + k], h1[k], a);
-            y = fmaf(w[MLP_W3 + j], a > 0.f ? a : 0.f, y);
-        }
-        out[s] = y;
+    const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t s = gw; s < n; s += nwarps) {
+        float h1a, h1b, h2a, h2b;
+        const float y = mlp_forward_warp(m, b.feat + (size_t)s * MLP_IN, h1a, h1b, h2a, h2b);
+        if (lane_id() == 0) out[s] = y;
     }
 }
 

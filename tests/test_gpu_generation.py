@@ -37,13 +37,13 @@ def _expected_entries(tree, T):
 
 
 def run_generations(gp, w, *, T, gens, max_nodes, seed=1234, cache_check=16, stop_check=True,
-                    cases_per_lane=0):
+                    cases_per_lane=0, walk_team=0):
     import oracle
     ops, off = w["ops"], w["off"]
     k, x, t = w["consts"], w["x"], w["t"]
     P = len(off) - 1
     pop = gp.Population(x, t, k, ops, off, max_nodes=max_nodes, cache_threshold=T, seed=seed,
-                        cases_per_lane=cases_per_lane)
+                        cases_per_lane=cases_per_lane, walk_team=walk_team)
     pop.eval_full()
     fit = pop.fitness()
     _, ofit = oracle.eval_pop_f32(ops, off, k, x, t)
@@ -129,6 +129,24 @@ def test_generations_uneven_population_1024_cases(gp):
     import synth
     w = synth.workload(3, n_trees=64, target=20_000, n_cases=1024)
     run_generations(gp, w, T=256, gens=2, max_nodes=40_000, cache_check=6)
+
+
+@pytest.mark.parametrize("team", [1, 2, 4, 8])
+def test_generations_walk_team_sizes(gp, team):
+    """Every team size of the incremental walk (warps per child) gives the
+    oracle's children, fitness and stop levels; with one and several case
+    blocks per vector."""
+    import synth
+    for C, K in ((48, 2), (200, 1)):
+        w = synth.workload(0, n_trees=40, n_cases=C)
+        run_generations(gp, w, T=16, gens=2, max_nodes=20000, cases_per_lane=K, walk_team=team, cache_check=6)
+
+
+def test_walk_team_is_validated(gp):
+    import synth
+    w = synth.workload(0, n_trees=4)
+    with pytest.raises(gp.GpError):
+        gp.Population(w["x"], w["t"], w["consts"], w["ops"], w["off"], max_nodes=4096, walk_team=3)
 
 
 def test_generations_tight_size_limit_makes_copies(gp):
