@@ -6,6 +6,7 @@
 #define GP_B 1024            // structure block: positions per warp pass (32 per lane)
 #define GP_NCONST 251        // ephemeral constant table
 #define GP_WARPS 8           // warps per CTA in the persistent kernels
+#define FREE_TILE 4096       // slots per CTA in the free-slot scan
 #define FULL 0xFFFFFFFFu
 
 // status word bits (device side)
@@ -51,8 +52,11 @@ struct DevPop {
     uint4* it_desc;      // [Ecap] (start, length, slot, buffer) of the entry's small-subtree item
     uint4* sk_desc;      // [Ecap] (slot, operand slot, op | child flags, right child entry) for the skeleton pass
     uint32_t* order;     // [Ecap] work order
-    // values
+    // values: one pool of slots shared by the parents' and the children's caches
     float* slots;        // [Scap][Cpad]
+    uint32_t* live;      // [Scap] generation stamp of the last cache that referenced the slot
+    uint32_t* freeslot;  // [Scap] free slots in slot order (first ones used for new values)
+    uint32_t* ftile;     // [Scap / FREE_TILE + 1] free slots per tile, then their exclusive prefix
     float* ovf;          // interpreter stack overflow, per warp
     uint32_t* status;    // [1]
     uint32_t* errinfo;   // [4] first failure: site, individual, position, detail

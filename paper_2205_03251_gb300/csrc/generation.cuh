@@ -67,6 +67,7 @@ struct GenBufs {
     uint64_t seed;
     uint32_t gen;
     const uint32_t* gen_add;         // device word added to gen (generations replayed by a captured graph)
+    uint32_t* stamp;                 // [1] generation stamp of the slot pool's live marks
     bool evaluated;
 };
 
@@ -1149,9 +1150,14 @@ __global__ void __launch_bounds__(1024) k_merge_offsets(DevPop d, GenBufs g) {
         d.e_off[d.P] = (uint32_t)carry;
         *d.e_total = (uint32_t)carry;
         if (d.strict_cap && carry > d.Ecap) set_status(d.status, ST_ENTRIES);
+        *g.stamp += 1;               // a new generation of live marks in the slot pool
     }
 }
 
+// A child's cache entry.  src is the mother's (or father's) value slot, which
+// the child shares, or (bit 31 set) a walk record whose new value gets a
+// free slot of the pool later (k_copy_values).
+#define SLOT_NEW 0xFFFFFFFFu
 __device__ __forceinline__ void put_entry(const DevPop& d, GenBufs& g, uint32_t x, uint32_t pos, uint32_t end,
                                           uint32_t tree, uint32_t src) {
     d.e_pos[x] = pos;
@@ -1160,7 +1166,7 @@ __device__ __forceinline__ void put_entry(const DevPop& d, GenBufs& g, uint32_t 
     d.e_c0[x] = -1;
     d.e_c1[x] = -1;
     d.e_par[x] = -1;
-    d.e_slot[x] = x;
+    d.e_slot[x] = (src & 0x80000000u) ? SLOT_NEW : src;
     g.src[x] = src;
 }
 
@@ -1292,7 +1298,99 @@ __global__ void k_merge_write(DevPop d, GenBufs g, CacheView par) {
     }
 }
 
-// Value vectors of the children's entries: one warp per entry, lanes over cases.
+// ---- slot pool: the children's entries share the parents' value slots;
+// slots that no child entry references are free again, and the walk's new
+// values go to the first free ones (in slot order).
+
+// Mark the slots the children's cache references with this generation's stamp.
+__global__ void k_mark_live(DevPop d, GenBufs g) {
+    if (halted(d)) return;
+    const uint32_t ne = d.e_off[d.P];
+    if (ne > d.Ecap) return;
+    const uint32_t stamp = *g.stamp;
+    for (uint32_t x = blockIdx.x * blockDim.x + threadIdx.x; x < ne; x += gridDim.x * blockDim.x) {
+        const uint32_t sl = d.e_slot[x];
+        if (sl != SLOT_NEW && sl < d.Scap) d.live[sl] = stamp;
+    }
+}
+
+__device__ __forceinline__ uint32_t block_reduce_add(uint32_t v, uint32_t* ws) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+    __syncthreads();
+    if (lane == 0) ws[w] = v;
+    __syncthreads();
+    uint32_t t = 0;
+    for (uint32_t k = 0; k < (blockDim.x >> 5); ++k) t += ws[k];
+    return t;
+}
+
+// Free slots per tile of FREE_TILE slots (1024 threads, four slots each).
+__global__ void __launch_bounds__(1024) k_free_count(DevPop d, GenBufs g) {
+    if (halted(d)) return;
+    __shared__ uint32_t ws[32];
+    const uint32_t stamp = *g.stamp;
+    const uint32_t nt = (d.Scap + FREE_TILE - 1) / FREE_TILE;
+    for (uint32_t t = blockIdx.x; t < nt; t += gridDim.x) {
+        const uint32_t s0 = t * FREE_TILE + 4 * threadIdx.x;
+        uint32_t c = 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) c += (s0 + k < d.Scap && d.live[s0 + k] != stamp) ? 1u : 0u;
+        c = block_reduce_add(c, ws);
+        if (threadIdx.x == 0) d.ftile[t] = c;
+    }
+}
+
+// Exclusive prefix of the per-tile counts (one CTA); too few free slots for
+// the walk's new values is a budget error.
+__global__ void __launch_bounds__(1024) k_free_top(DevPop d, GenBufs g) {
+    if (halted(d)) return;
+    __shared__ uint64_t ws[32];
+    __shared__ uint64_t carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    const uint32_t nt = (d.Scap + FREE_TILE - 1) / FREE_TILE;
+    for (uint32_t base = 0; base < nt; base += blockDim.x) {
+        const uint32_t t = base + threadIdx.x;
+        const uint64_t v = (t < nt) ? d.ftile[t] : 0;
+        const uint64_t o = block_excl_scan(v, ws, &carry);
+        if (t < nt) d.ftile[t] = (uint32_t)o;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        d.ftile[nt] = (uint32_t)min(carry, (uint64_t)0xFFFFFFFFu);     // free slots in all
+        if (carry < min(g.misc[M_PV], g.pvcap)) set_status(d.status, ST_SLOTS);
+    }
+}
+
+// freeslot[r] = the r-th free slot, for the ranks the new values need.
+__global__ void __launch_bounds__(1024) k_free_emit(DevPop d, GenBufs g) {
+    if (halted(d)) return;
+    __shared__ uint64_t ws[32];
+    __shared__ uint64_t carry;
+    const uint32_t stamp = *g.stamp;
+    const uint32_t need = min(g.misc[M_PV], g.pvcap);
+    const uint32_t nt = (d.Scap + FREE_TILE - 1) / FREE_TILE;
+    for (uint32_t t = blockIdx.x; t < nt; t += gridDim.x) {
+        const uint32_t base = d.ftile[t];
+        if (base >= need) continue;                       // uniform per CTA
+        if (threadIdx.x == 0) carry = base;
+        __syncthreads();
+        const uint32_t s0 = t * FREE_TILE + 4 * threadIdx.x;
+        uint32_t fr[4], c = 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) { fr[k] = (s0 + k < d.Scap && d.live[s0 + k] != stamp) ? 1u : 0u; c += fr[k]; }
+        uint32_t r = (uint32_t)block_excl_scan(c, ws, &carry);
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            if (fr[k]) { if (r < need) d.freeslot[r] = s0 + k; ++r; }
+        __syncthreads();
+    }
+}
+
+// New values of the children's cache (walk records): each takes the free
+// slot of its record's rank; one warp per 32 entries, lanes over cases.
 __global__ void k_copy_values(DevPop d, GenBufs g, CacheView par) {
     if (halted(d)) return;
     const uint32_t ne = d.e_off[d.P];
@@ -1300,13 +1398,26 @@ __global__ void k_copy_values(DevPop d, GenBufs g, CacheView par) {
     const int lane = lane_id();
     const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
-    for (uint32_t x = gw; x < ne; x += nw) {
-        const uint32_t sr = g.src[x];
-        const float* sp = (sr & 0x80000000u) ? g.pv_val + (size_t)(sr & 0x7FFFFFFFu) * d.Cpad
-                                             : par.slots + (size_t)sr * d.Cpad;
-        float* dp = d.slots + (size_t)x * d.Cpad;
-        for (uint32_t k = lane; k < d.Cpad; k += 32) dp[k] = __ldcg(sp + k);
+    const uint32_t nt = (d.Scap + FREE_TILE - 1) / FREE_TILE;
+    const uint32_t need = min(min(g.misc[M_PV], g.pvcap), d.ftile[nt]);
+    for (uint32_t x0 = 32 * gw; x0 < ne; x0 += 32 * nw) {
+        const uint32_t x = x0 + lane;
+        const bool isnew = x < ne && d.e_slot[x] == SLOT_NEW;
+        uint32_t nb = __ballot_sync(FULL, isnew);
+        while (nb) {
+            const int l = __ffs(nb) - 1;
+            nb &= nb - 1;
+            const uint32_t xx = x0 + l;
+            const uint32_t r = g.src[xx] & 0x7FFFFFFFu;
+            if (r >= need) { if (lane == 0) set_status(d.status, ST_SLOTS); continue; }
+            const uint32_t sl = d.freeslot[r];
+            const float* sp = g.pv_val + (size_t)r * d.Cpad;
+            float* dp = d.slots + (size_t)sl * d.Cpad;
+            for (uint32_t k = lane; k < d.Cpad; k += 32) dp[k] = __ldcg(sp + k);
+            if (lane == 0) d.e_slot[xx] = sl;
+        }
     }
+    (void)par;
 }
 
 // equivalent-op count of the children (every opcode on every case)

@@ -33,8 +33,7 @@ struct CacheSet {
     uint32_t *order = nullptr, *e_tree = nullptr, *e_cmax = nullptr, *msrc = nullptr;
     int32_t *e_par = nullptr, *e_c0 = nullptr, *e_c1 = nullptr, *e_bal = nullptr;
     uint4 *it_desc = nullptr, *sk_desc = nullptr;
-    float* slots = nullptr;
-    uint32_t Ecap = 0, Scap = 0;
+    uint32_t Ecap = 0;
     std::vector<void*> allocs;
 };
 
@@ -71,6 +70,11 @@ struct gp_pop {
     std::vector<uint32_t> host_buf;
     std::vector<uint32_t> host_free;
     uint64_t slot_limit;              // value vectors the cache budget allows
+    float* pool;                      // value slots shared by both cache sets
+    uint32_t* live;                   // [pool_cap] live stamps
+    uint32_t* freeslot;               // [pool_cap]
+    uint32_t* ftile;                  // [pool_cap / FREE_TILE + 1]
+    uint64_t pool_cap;
     CacheSet sets[2];
     int cur;                          // set of the current population
     uint32_t* e_total_h;              // pinned host copy of the entry count
@@ -306,26 +310,63 @@ void bind_set(gp_pop* pop) {
     CacheSet& c = pop->sets[pop->cur];
     d.e_cnt = c.e_cnt; d.e_off = c.e_off; d.e_pos = c.e_pos; d.e_end = c.e_end; d.e_par = c.e_par;
     d.e_c0 = c.e_c0; d.e_c1 = c.e_c1; d.e_slot = c.e_slot; d.e_tree = c.e_tree; d.it_desc = c.it_desc;
-    d.sk_desc = c.sk_desc; d.order = c.order; d.slots = c.slots; d.Ecap = c.Ecap; d.Scap = c.Scap;
+    d.sk_desc = c.sk_desc; d.order = c.order; d.Ecap = c.Ecap;
+    d.slots = pop->pool; d.live = pop->live; d.freeslot = pop->freeslot; d.ftile = pop->ftile;
+    d.Scap = (uint32_t)pop->pool_cap;
     pop->sb.e_bal = c.e_bal; pop->sb.e_tree = c.e_tree; pop->sb.e_cmax = c.e_cmax;
     pop->gb.src = c.msrc;
 }
 
-CacheView view_of(const CacheSet& c) {
+CacheView view_of(const gp_pop* pop, const CacheSet& c) {
     CacheView v;
     v.e_off = c.e_off; v.e_pos = c.e_pos; v.e_end = c.e_end; v.e_par = c.e_par;
-    v.e_c0 = c.e_c0; v.e_c1 = c.e_c1; v.e_slot = c.e_slot; v.slots = c.slots;
+    v.e_c0 = c.e_c0; v.e_c1 = c.e_c1; v.e_slot = c.e_slot; v.slots = pop->pool;
     return v;
 }
 
-// (Re)allocate cache set `which` for ecap entries (one value slot each).
+// Grow the shared slot pool to at least `want` slots, keeping the values
+// and live marks it holds (the parents' values may still be in use).
+int ensure_pool(gp_pop* pop, uint64_t want) {
+    if (want <= pop->pool_cap) return GP_OK;
+    if (want > pop->slot_limit)
+        return fail(pop, GP_ENOMEM, "cache needs %llu value vectors, budget allows %llu",
+                    (unsigned long long)want, (unsigned long long)pop->slot_limit);
+    if (pop->stream) cudaStreamSynchronize(pop->stream); else cudaDeviceSynchronize();
+    if (pop->gexec) { cudaGraphExecDestroy(pop->gexec); pop->gexec = nullptr; pop->graph_n = 0; }
+    const size_t Cpad = pop->d.Cpad;
+    float* np = nullptr;
+    uint32_t *nl = nullptr, *nf = nullptr, *nt = nullptr;
+    const size_t ntile = want / FREE_TILE + 2;
+    if (cudaMalloc(&np, want * Cpad * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&nl, want * sizeof(uint32_t)) != cudaSuccess ||
+        cudaMalloc(&nf, want * sizeof(uint32_t)) != cudaSuccess ||
+        cudaMalloc(&nt, ntile * sizeof(uint32_t)) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(np); cudaFree(nl); cudaFree(nf); cudaFree(nt);
+        return fail(pop, GP_ENOMEM, "allocation of a value pool of %llu slots failed", (unsigned long long)want);
+    }
+    cudaMemset(nl, 0, want * sizeof(uint32_t));
+    if (pop->pool) {
+        cudaMemcpy(np, pop->pool, pop->pool_cap * Cpad * sizeof(float), cudaMemcpyDeviceToDevice);
+        cudaMemcpy(nl, pop->live, pop->pool_cap * sizeof(uint32_t), cudaMemcpyDeviceToDevice);
+        cudaFree(pop->pool); cudaFree(pop->live); cudaFree(pop->freeslot); cudaFree(pop->ftile);
+    }
+    pop->pool = np; pop->live = nl; pop->freeslot = nf; pop->ftile = nt;
+    pop->pool_cap = want;
+    DevPop& d = pop->d;
+    d.slots = np; d.live = nl; d.freeslot = nf; d.ftile = nt; d.Scap = (uint32_t)want;
+    return GP_OK;
+}
+
+// (Re)allocate the index arrays of cache set `which` for ecap entries, and
+// make the shared pool hold ecap values plus the walk's new ones.
 int grow_set(gp_pop* pop, int which, uint32_t ecap) {
     CacheSet& c = pop->sets[which];
     const DevPop& d = pop->d;
-    const uint64_t scap = ecap;
-    if (scap > pop->slot_limit)
-        return fail(pop, GP_ENOMEM, "cache needs %llu value vectors, budget allows %llu",
-                    (unsigned long long)scap, (unsigned long long)pop->slot_limit);
+    {
+        int r = ensure_pool(pop, (uint64_t)ecap + pop->gb.pvcap);
+        if (r) return r;
+    }
     if (pop->stream) cudaStreamSynchronize(pop->stream); else cudaDeviceSynchronize();
     if (pop->gexec) { cudaGraphExecDestroy(pop->gexec); pop->gexec = nullptr; pop->graph_n = 0; }
     for (void* p : c.allocs) cudaFree(p);
@@ -341,12 +382,10 @@ int grow_set(gp_pop* pop, int which, uint32_t ecap) {
     bool ok = al(&c.e_cnt, d.P + 1) && al(&c.e_off, d.P + 1) && al(&c.e_pos, ecap) && al(&c.e_end, ecap) &&
               al(&c.e_par, ecap) && al(&c.e_c0, ecap) && al(&c.e_c1, ecap) && al(&c.e_slot, ecap) &&
               al(&c.it_desc, ecap) && al(&c.sk_desc, ecap) && al(&c.order, ecap) && al(&c.e_bal, ecap) &&
-              al(&c.e_tree, ecap) && al(&c.e_cmax, ecap / 32 + 2) && al(&c.msrc, ecap) &&
-              al(&c.slots, (size_t)scap * d.Cpad);
+              al(&c.e_tree, ecap) && al(&c.e_cmax, ecap / 32 + 2) && al(&c.msrc, ecap);
     if (!ok) return fail(pop, GP_ENOMEM, "allocation of a cache of %u entries failed", ecap);
     cudaMemset(c.e_off, 0, sizeof(uint32_t) * (d.P + 1));
     c.Ecap = ecap;
-    c.Scap = (uint32_t)scap;
     if (which == pop->cur) bind_set(pop);
     return GP_OK;
 }
@@ -500,8 +539,9 @@ int gp_pop_create(const gp_config* cfg_in, const float* x, const float* targets,
     if (ecap > (1ull << 26)) ecap = 1ull << 26;
     pop->slot_limit = cfg.cache_budget_bytes / ((uint64_t)d.Cpad * sizeof(float));
     if (pop->slot_limit > 0xFFFFFFF0ull) pop->slot_limit = 0xFFFFFFF0ull;
-    if (pop->slot_limit < 2ull * P) { g_create_error = "cache budget too small for one vector per tree"; delete pop; return GP_ENOMEM; }
-    if (ecap > pop->slot_limit) ecap = pop->slot_limit;
+    const uint64_t pv_slots = (uint64_t)P * PV_PER_CHILD;
+    if (pop->slot_limit < 2ull * P + pv_slots) { g_create_error = "cache budget too small for one vector per tree"; delete pop; return GP_ENOMEM; }
+    if (ecap + pv_slots > pop->slot_limit) ecap = pop->slot_limit - pv_slots;
     const uint32_t nbuf = 2 * P;     // parents + children (copy targets)
     d.ovf_warps = 0;
 
@@ -563,9 +603,10 @@ int gp_pop_create(const gp_config* cfg_in, const float* x, const float* targets,
         g.seed = cfg.seed;
         g.gen = 0;
         g.evaluated = false;
-        DA2(pop->gwords, 2);
-        cudaMemset(pop->gwords, 0, 2 * sizeof(uint32_t));
+        DA2(pop->gwords, 4);
+        cudaMemset(pop->gwords, 0, 4 * sizeof(uint32_t));
         g.gen_add = pop->gwords;
+        g.stamp = pop->gwords + 2;
         g.frag_cap = (uint64_t)P * d.cap;
         g.stash_cap = (uint64_t)P * (T + 16);
         g.shift_cap = (uint32_t)((uint64_t)P * d.cap / SHIFT_BS + P);
@@ -651,6 +692,7 @@ void gp_pop_destroy(gp_pop* pop) {
     if (pop->stream) cudaStreamSynchronize(pop->stream); else cudaDeviceSynchronize();
     if (pop->gexec) cudaGraphExecDestroy(pop->gexec);
     if (pop->cap_stream) cudaStreamDestroy(pop->cap_stream);
+    cudaFree(pop->pool); cudaFree(pop->live); cudaFree(pop->freeslot); cudaFree(pop->ftile);
     for (void* p : pop->allocs) cudaFree(p);
     for (int w = 0; w < 2; ++w) for (void* p : pop->sets[w].allocs) cudaFree(p);
     if (pop->e_total_h) cudaFreeHost(pop->e_total_h);
@@ -1081,7 +1123,7 @@ int gen_crossover(gp_pop* pop, uint32_t generation) {
     if (pop->have_children) return fail(pop, GP_ESTATE, "children of the last crossover are not evaluated yet");
     g.gen = generation;
     swap_generation(pop);
-    const CacheView par = view_of(pop->sets[pop->cur]);
+    const CacheView par = view_of(pop, pop->sets[pop->cur]);
     pop->cur ^= 1;
     bind_set(pop);
     const int gt = pop->grid_threads;
@@ -1110,7 +1152,7 @@ int gen_incremental(gp_pop* pop) {
     DevPop& d = pop->d;
     GenBufs& g = pop->gb;
     if (!pop->have_children) return fail(pop, GP_ESTATE, "gp_eval_incremental needs the children of a gp_crossover");
-    const CacheView par = view_of(pop->sets[pop->cur ^ 1]);
+    const CacheView par = view_of(pop, pop->sets[pop->cur ^ 1]);
     const int gt = pop->grid_threads;
     CK(cudaMemsetAsync(d.q, 0, sizeof(uint32_t) * NQ, pop->stream));
     phase_begin(pop, PH_PACK);
@@ -1155,6 +1197,10 @@ int gen_incremental(gp_pop* pop) {
         }
     }
     k_merge_write<<<pop->grid_warps, GP_WARPS * 32, 0, pop->stream>>>(d, g, par);
+    k_mark_live<<<gt, 256, 0, pop->stream>>>(d, g);
+    k_free_count<<<pop->nsm * 2, 1024, 0, pop->stream>>>(d, g);
+    k_free_top<<<1, 1024, 0, pop->stream>>>(d, g);
+    k_free_emit<<<pop->nsm * 2, 1024, 0, pop->stream>>>(d, g);
     k_copy_values<<<pop->nsm * 16, 256, 0, pop->stream>>>(d, g, par);
     k_entry_chunkmax<<<pop->grid_warps, GP_WARPS * 32, 0, pop->stream>>>(d, pop->sb);
     k_entry_parents<<<gt, 256, 0, pop->stream>>>(d, pop->sb);
@@ -1164,7 +1210,7 @@ int gen_incremental(gp_pop* pop) {
     k_accumulate<<<1, 32, 0, pop->stream>>>(pop->cum, d.acc_ops, g.gstat, pop->cases_stat, 1);
     ++pop->cum_calls;
     CK(cudaGetLastError());
-    pop->launches += 12 + 10;
+    pop->launches += 12 + 14;
     pop->have_children = false;
     g.evaluated = true;
     pop->last_kind = 1;
