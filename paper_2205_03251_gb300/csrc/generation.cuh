@@ -105,36 +105,6 @@ __device__ __forceinline__ int32_t find_last_lt(const uint32_t* e_pos, uint32_t 
     return (a > lo) ? (int32_t)(a - 1) : -1;
 }
 
-// Size of the subtree at x of a parent tree: a cached entry gives it
-// directly; otherwise it is below the threshold and a forward balance scan
-// of fewer than T bytes finds its end.
-__device__ uint32_t subtree_size_at(const DevPop& d, const CacheView& par, uint32_t t, const uint8_t* ops,
-                                    uint32_t n, uint32_t x) {
-    int32_t e = find_exact(par.e_pos, par.e_off[t], par.e_off[t + 1], x);
-    if (e >= 0) return par.e_end[e] - x;
-    int need = 1;
-    uint32_t q = x;
-    while (q < n) {
-        need += (ops[q] < 4) ? 1 : -1;
-        ++q;
-        if (need == 0) return q - x;
-    }
-    return n - x;     // unreachable for well-formed trees
-}
-
-__device__ __forceinline__ uint32_t tournament(const float* fit, uint32_t P, uint32_t T, uint64_t seed,
-                                               uint32_t gen, uint32_t child, uint32_t kbase) {
-    uint32_t best = 0;
-    float bf = 0.f;
-    for (uint32_t j = 0; j < T; ++j) {
-        uint32_t idx = (uint32_t)below(draw(seed, gen, child, kbase + j), P);
-        float f = fit[idx];
-        if (isnan(f)) f = __int_as_float(0x7F800000);
-        if (j == 0 || f < bf) { best = idx; bf = f; }
-    }
-    return best;
-}
-
 // 16 bytes starting at any address (two aligned loads and a funnel shift);
 // may read up to 31 bytes past p.
 __device__ __forceinline__ uint4 load16u(const uint8_t* p) {
@@ -158,6 +128,77 @@ __device__ __forceinline__ uint4 load16u(const uint8_t* p) {
     return make_uint4(r[0], r[1], r[2], r[3]);
 }
 
+// Size of the subtree at x of a parent tree: a cached entry gives it
+// directly; otherwise it is below the threshold and a forward balance scan
+// of fewer than T bytes finds its end, here by a whole warp: 512 bytes per
+// step, each lane summing (arity - 1) over 16 of them; the first lane whose
+// running balance reaches zero finds the end.  All lanes return the size.
+__device__ uint32_t warp_subtree_size_at(const CacheView& par, uint32_t t, const uint8_t* ops, uint32_t n,
+                                         uint32_t x) {
+    const int lane = lane_id();
+    const int32_t e = find_exact(par.e_pos, par.e_off[t], par.e_off[t + 1], x);
+    if (e >= 0) return par.e_end[e] - x;
+    int bal = 1;                                      // nodes still needed at the window start
+    for (uint32_t w0 = x; w0 < n; w0 += 512) {
+        const uint32_t p0 = w0 + 16u * lane;
+        uint32_t wd[4] = {0, 0, 0, 0};
+        if (p0 < n) {
+            const uint4 v = load16u(ops + p0);
+            wd[0] = v.x; wd[1] = v.y; wd[2] = v.z; wd[3] = v.w;
+        }
+        int tot = 0, mn = 1 << 30;
+#pragma unroll
+        for (int b = 0; b < 16; ++b) {
+            if (p0 + b < n) {
+                const uint32_t op = (wd[b >> 2] >> (8 * (b & 3))) & 0xFFu;
+                tot += (op < 4) ? 1 : -1;
+                mn = min(mn, tot);
+            }
+        }
+        int incl = tot;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(FULL, incl, o);
+            if (lane >= o) incl += v;
+        }
+        const int start = bal + incl - tot;
+        const uint32_t hit = __ballot_sync(FULL, mn != (1 << 30) && start + mn <= 0);
+        if (hit) {
+            const int src = __ffs(hit) - 1;
+            uint32_t end = 0;
+            if (lane == src) {
+                int sv = start;
+#pragma unroll
+                for (int b = 0; b < 16; ++b) {
+                    if (end == 0 && p0 + b < n) {
+                        const uint32_t op = (wd[b >> 2] >> (8 * (b & 3))) & 0xFFu;
+                        sv += (op < 4) ? 1 : -1;
+                        if (sv == 0) end = p0 + b + 1;
+                    }
+                }
+            }
+            end = __shfl_sync(FULL, end, src);
+            return end - x;
+        }
+        bal += __shfl_sync(FULL, incl, 31);
+    }
+    return n - x;     // unreachable for well-formed trees
+}
+
+__device__ __forceinline__ uint32_t tournament(const float* fit, uint32_t P, uint32_t T, uint64_t seed,
+                                               uint32_t gen, uint32_t child, uint32_t kbase) {
+    uint32_t best = 0;
+    float bf = 0.f;
+    for (uint32_t j = 0; j < T; ++j) {
+        uint32_t idx = (uint32_t)below(draw(seed, gen, child, kbase + j), P);
+        float f = fit[idx];
+        if (isnan(f)) f = __int_as_float(0x7F800000);
+        if (j == 0 || f < bf) { best = idx; bf = f; }
+    }
+    return best;
+}
+
+
 // ------------------------------------------------------------------ A5 plan
 
 // Child i: mother and father by tournament (draws 0..T-1 and T..2T-1), then
@@ -166,7 +207,8 @@ __device__ __forceinline__ uint4 load16u(const uint8_t* p) {
 // child is a copy of its mother.
 __global__ void k_plan(DevPop d, GenBufs g, CacheView par) {
     if (halted(d)) return;
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < d.P; i += gridDim.x * blockDim.x) {
+    const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nwp = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t i = gw; i < d.P; i += nwp) {       // one warp per child
         const uint32_t T = g.tsize;
         const uint32_t gen = g.gen + *g.gen_add;
         const uint32_t m = tournament(g.pfit, d.P, T, g.seed, gen, i, 0);
@@ -178,13 +220,15 @@ __global__ void k_plan(DevPop d, GenBufs g, CacheView par) {
         for (uint32_t a = 0; a < 8; ++a) {
             const uint32_t c1 = (uint32_t)below(draw(g.seed, gen, i, 2 * T + 2 * a), sm);
             const uint32_t d1 = (uint32_t)below(draw(g.seed, gen, i, 2 * T + 2 * a + 1), sf);
-            const uint32_t r1 = subtree_size_at(d, par, m, om, sm, c1);
-            const uint32_t s1 = subtree_size_at(d, par, f, of, sf, d1);
+            const uint32_t r1 = warp_subtree_size_at(par, m, om, sm, c1);
+            const uint32_t s1 = warp_subtree_size_at(par, f, of, sf, d1);
             if ((uint64_t)sm - r1 + s1 <= g.max_nodes) { fl = 0; cc = c1; rr = r1; dd = d1; ss = s1; ff = f; break; }
         }
-        g.mother[i] = m; g.father[i] = ff; g.cpos[i] = cc; g.rsz[i] = rr; g.dpos[i] = dd; g.ssz[i] = ss;
-        g.flags[i] = fl;
-        atomicMax(&g.lastidx[m], (int32_t)i);
+        if (lane_id() == 0) {
+            g.mother[i] = m; g.father[i] = ff; g.cpos[i] = cc; g.rsz[i] = rr; g.dpos[i] = dd; g.ssz[i] = ss;
+            g.flags[i] = fl;
+            atomicMax(&g.lastidx[m], (int32_t)i);
+        }
     }
 }
 
@@ -1182,51 +1226,80 @@ __device__ __forceinline__ int32_t find_record(const GenBufs& g, uint32_t i, uin
     return -1;
 }
 
-// One warp per child writes its entries (position, end, value source).
-__global__ void k_merge_write(DevPop d, GenBufs g, CacheView par) {
+// One CTA per child writes its entries (position, end, value source):
+// the mother's entries before c (dropping ancestors that fall below the
+// threshold, merged with the walk's inserted ancestors), the root made of a
+// small donated subtree, the father's entries of the donated subtree, and
+// the mother's entries after the removed subtree, shifted by delta.
+#define MERGE_MAXINS 1024
+__global__ void __launch_bounds__(256) k_merge_write(DevPop d, GenBufs g, CacheView par) {
     if (halted(d)) return;
-    const int lane = lane_id();
-    const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
     if (d.e_off[d.P] > d.Ecap) return;
+    __shared__ uint32_t s_ins[MERGE_MAXINS];   // positions of inserted ancestors before c, decreasing
+    __shared__ uint64_t ws[32];
+    __shared__ uint64_t cins, ckept;
+    const uint32_t tid = threadIdx.x, nthr = blockDim.x;
+    const int lane = lane_id();
     const uint32_t T = d.T;
-    for (uint32_t i = gw; i < d.P; i += nw) {
+    for (uint32_t i = blockIdx.x; i < d.P; i += gridDim.x) {
         const uint32_t o = d.e_off[i];
         const uint32_t m = g.mother[i];
         const uint32_t me0 = par.e_off[m], me1 = par.e_off[m + 1];
         if (g.flags[i] & F_CLONE) {
-            for (uint32_t k = lane; k < me1 - me0; k += 32) {
+            for (uint32_t k = tid; k < me1 - me0; k += nthr) {
                 const uint32_t e = me0 + k;
                 put_entry(d, g, o + k, par.e_pos[e], par.e_end[e], i, par.e_slot[e]);
             }
             continue;
         }
-        const uint32_t f = g.father[i], c = g.cpos[i], dd = g.dpos[i], s = g.ssz[i];
-        const int32_t delta = (int32_t)s - (int32_t)g.rsz[i];
+        const uint32_t c = g.cpos[i], dd = g.dpos[i];
+        const int32_t delta = (int32_t)g.ssz[i] - (int32_t)g.rsz[i];
         const uint4 mb = g.mb[i];
         const uint32_t jc = mb.x, jcr = mb.y, jd = mb.z, jds = mb.w;
         const uint32_t r0 = g.pv_off[i], r1 = g.pv_off[i + 1];
-        // part 1: mother entries before c, merged with inserted ancestors (pos < c)
-        uint32_t kept = 0;
-        for (uint32_t base = me0; base < jc; base += 32) {
-            const uint32_t e = base + lane;
-            const bool valid = e < jc;
+        if (tid == 0) { cins = 0; ckept = 0; }
+        __syncthreads();
+        // inserted ancestors before c, in record order (positions decreasing)
+        uint32_t rootins = 0;
+        for (uint32_t base = r0; base < r1; base += nthr) {
+            const uint32_t q = base + tid;
+            bool ins_lt = false;
+            if (q < r1) {
+                const uint4 rec = g.pv_sorted[q];
+                const bool ins = (rec.y & 0x80000000u) != 0;
+                ins_lt = ins && rec.x < c;
+                if (ins && rec.x == c) rootins = 1;
+            }
+            const uint64_t rk = block_excl_scan(ins_lt ? 1u : 0u, ws, &cins);
+            if (ins_lt && rk < MERGE_MAXINS) s_ins[rk] = g.pv_sorted[q].x;
+        }
+        rootins = __syncthreads_or(rootins) ? 1u : 0u;
+        const uint32_t nins_lt = (uint32_t)cins;
+        if (nins_lt > MERGE_MAXINS) {
+            if (tid == 0) set_status(d.status, ST_PATH);
+            __syncthreads();
+            continue;
+        }
+        // part 1: mother entries before c, one row of nthr entries at a time
+        for (uint32_t base = me0; base < jc; base += nthr) {
+            const uint32_t e = base + tid;
             uint32_t pos = 0, end = 0;
             bool keep = false, anc = false;
-            if (valid) {
+            if (e < jc) {
                 pos = par.e_pos[e];
                 end = par.e_end[e];
                 anc = end > c;
                 keep = !(anc && drops(par, (int32_t)e, delta, T));
             }
-            const uint32_t bal = __ballot_sync(FULL, keep);
+            const uint64_t kb = block_excl_scan(keep ? 1u : 0u, ws, &ckept);
             if (keep) {
-                uint32_t insb = 0;
-                for (uint32_t q = r0; q < r1; ++q) {
-                    const uint4 rec = g.pv_sorted[q];
-                    if ((rec.y & 0x80000000u) && rec.x < pos) ++insb;
+                // inserted ancestors before pos: s_ins is decreasing, so they are its tail
+                uint32_t lo = 0, hi = nins_lt;         // first index with s_ins < pos
+                while (lo < hi) {
+                    const uint32_t mid = (lo + hi) >> 1;
+                    if (s_ins[mid] >= pos) lo = mid + 1; else hi = mid;
                 }
-                const uint32_t x = o + kept + __popc(bal & ((1u << lane) - 1u)) + insb;
+                const uint32_t x = o + (uint32_t)kb + (nins_lt - lo);
                 uint32_t src = par.e_slot[e];
                 if (anc) {
                     const int32_t h = find_record(g, i, pos);
@@ -1234,67 +1307,49 @@ __global__ void k_merge_write(DevPop d, GenBufs g, CacheView par) {
                 }
                 put_entry(d, g, x, pos, anc ? (uint32_t)((int64_t)end + delta) : end, i, src);
             }
-            kept += __popc(bal);
         }
-        // inserted ancestors (and the root made of a small donated subtree)
-        const int32_t anchor = (delta < 0) ? mother_anchor(par, me0, me1, c, g.rsz[i], T) : -1;
-        uint32_t nbefore = kept, rootins = 0;
-        for (uint32_t q0 = r0; q0 < r1; q0 += 32) {
-            const uint32_t q = q0 + lane;
-            bool ins = false;
-            uint4 rec = make_uint4(0, 0, 0, 0);
-            if (q < r1) { rec = g.pv_sorted[q]; ins = (rec.y & 0x80000000u) != 0; }
-            const uint32_t ib = __ballot_sync(FULL, ins && rec.x < c);
-            const uint32_t rb = __ballot_sync(FULL, ins && rec.x == c);
-            if (ins) {
-                uint32_t x;
-                if (rec.x < c) {
-                    // kept mother entries before rec.x, plus inserts before rec.x
-                    uint32_t mlt = lower_bound_pos(par.e_pos, me0, jc, rec.x) - me0;
-                    int32_t e = anchor;
-                    uint32_t guard = 0;
-                    while (e >= 0 && drops(par, e, delta, T) && guard++ < (1u << 24)) {
-                        if (par.e_pos[e] < rec.x) --mlt;
-                        e = par.e_par[e];
-                    }
-                    uint32_t ilt = 0;
-                    for (uint32_t q2 = r0; q2 < r1; ++q2) {
-                        const uint4 r2 = g.pv_sorted[q2];
-                        if ((r2.y & 0x80000000u) && r2.x < rec.x) ++ilt;
-                    }
-                    x = o + mlt + ilt;
-                } else {
-                    x = 0xFFFFFFFFu;     // placed below, after all entries before c
+        const uint32_t kept = (uint32_t)ckept;
+        // inserted ancestors before c (few): kept mother entries and inserts before each
+        if (tid < 32) {
+            const int32_t anchor = (delta < 0) ? mother_anchor(par, me0, me1, c, g.rsz[i], T) : -1;
+            for (uint32_t k = lane; k < nins_lt; k += 32) {
+                const uint32_t px = s_ins[k];
+                uint32_t mlt = lower_bound_pos(par.e_pos, me0, jc, px) - me0;
+                int32_t e = anchor;
+                uint32_t guard = 0;
+                while (e >= 0 && drops(par, e, delta, T) && guard++ < (1u << 24)) {
+                    if (par.e_pos[e] < px) --mlt;
+                    e = par.e_par[e];
                 }
-                if (x != 0xFFFFFFFFu) put_entry(d, g, x, rec.x, rec.z, i, (rec.y & 0x7FFFFFFFu) | 0x80000000u);
+                const uint32_t ilt = nins_lt - 1 - k;          // s_ins is decreasing and distinct
+                const int32_t h = find_record(g, i, px);
+                if (h >= 0) {
+                    const uint4 rec = g.pv_sorted[h];
+                    put_entry(d, g, o + mlt + ilt, rec.x, rec.z, i, (rec.y & 0x7FFFFFFFu) | 0x80000000u);
+                }
             }
-            nbefore += __popc(ib);
-            rootins += __popc(rb);
-            if (rb & (1u << lane)) {
-                // position c itself: filled after the count of earlier inserts is known
+            if (rootins && lane == 0) {
+                const int32_t h = find_record(g, i, c);
+                if (h >= 0) {
+                    const uint4 rec = g.pv_sorted[h];
+                    put_entry(d, g, o + kept + nins_lt, rec.x, rec.z, i, (rec.y & 0x7FFFFFFFu) | 0x80000000u);
+                }
             }
         }
-        if (rootins) {
-            for (uint32_t q = r0; q < r1; ++q) {
-                const uint4 rec = g.pv_sorted[q];
-                if ((rec.y & 0x80000000u) && rec.x == c && lane == 0)
-                    put_entry(d, g, o + nbefore, rec.x, rec.z, i, (rec.y & 0x7FFFFFFFu) | 0x80000000u);
-            }
-        }
-        const uint32_t o2 = o + nbefore + rootins;
+        const uint32_t o2 = o + kept + nins_lt + rootins;
         // part 2: father entries in the donated subtree
-        for (uint32_t k = lane; k < jds - jd; k += 32) {
+        for (uint32_t k = tid; k < jds - jd; k += nthr) {
             const uint32_t e = jd + k;
             put_entry(d, g, o2 + k, par.e_pos[e] - dd + c, par.e_end[e] - dd + c, i, par.e_slot[e]);
         }
-        (void)f;
         // part 3: mother entries after the removed subtree
         const uint32_t o3 = o2 + (jds - jd);
-        for (uint32_t k = lane; k < me1 - jcr; k += 32) {
+        for (uint32_t k = tid; k < me1 - jcr; k += nthr) {
             const uint32_t e = jcr + k;
             put_entry(d, g, o3 + k, (uint32_t)((int64_t)par.e_pos[e] + delta), (uint32_t)((int64_t)par.e_end[e] + delta),
                       i, par.e_slot[e]);
         }
+        __syncthreads();              // shared lists are rewritten for the next child
     }
 }
 

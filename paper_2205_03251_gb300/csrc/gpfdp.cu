@@ -650,6 +650,7 @@ int gp_pop_create(const gp_config* cfg_in, const float* x, const float* targets,
         DA2(b.feat, (size_t)P * MLP_IN); DA2(b.pred, P); DA2(b.pred_pack, P); DA2(b.target, P); DA2(b.h1, (size_t)P * MLP_H);
         DA2(b.h2, (size_t)P * MLP_H); DA2(b.dy, P); DA2(b.dh2, (size_t)P * MLP_H); DA2(b.dh1, (size_t)P * MLP_H);
         DA2(b.loss, 1); DA2(b.step, 1);
+        DA2(b.part, (size_t)((P + MLP_CH - 1) / MLP_CH) * MLP_NP);
         pop->mlp_lr = (cfg.mlp_lr_micro ? cfg.mlp_lr_micro : 1000u) * 1e-6f;
         k_mlp_init<<<(MLP_NP + 255) / 256, 256, 0, pop->stream>>>(b, cfg.seed ^ 0x3131A5A5ull);
         cudaMemsetAsync(b.loss, 0, sizeof(float), pop->stream);
@@ -1018,14 +1019,16 @@ int gp_mlp_eval_grad(const float* w, const float* x, const float* y, uint32_t n,
     int rc = GP_OK;
     if (!(al(&b.w, MLP_NP) && al(&b.grad, MLP_NP) && al(&b.feat, (size_t)n * MLP_IN) && al(&b.pred, n) &&
           al(&b.target, n) && al(&b.h1, (size_t)n * MLP_H) && al(&b.h2, (size_t)n * MLP_H) && al(&b.dy, n) &&
-          al(&b.dh2, (size_t)n * MLP_H) && al(&b.dh1, (size_t)n * MLP_H) && al(&b.loss, 1))) rc = GP_ENOMEM;
+          al(&b.dh2, (size_t)n * MLP_H) && al(&b.dh1, (size_t)n * MLP_H) && al(&b.loss, 1) &&
+          al(&b.part, (size_t)((n + MLP_CH - 1) / MLP_CH) * MLP_NP))) rc = GP_ENOMEM;
     if (rc == GP_OK) {
         cudaMemcpy(b.w, w, sizeof(float) * MLP_NP, cudaMemcpyHostToDevice);
         cudaMemcpy(b.feat, x, sizeof(float) * n * MLP_IN, cudaMemcpyHostToDevice);
         cudaMemcpy(b.target, y, sizeof(float) * n, cudaMemcpyHostToDevice);
         k_mlp_train_pass<<<(n + 7) / 8 < 1024 ? (n + 7) / 8 : 1024, 256>>>(b, n);
         k_mlp_loss<<<1, 256>>>(b, n);
-        k_mlp_backward_params<<<(MLP_NP + 255) / 256, 256>>>(b, n);
+        k_mlp_grad_chunks<<<(n + MLP_CH - 1) / MLP_CH, 256>>>(b, n);
+        k_mlp_grad_reduce<<<(MLP_NP + 255) / 256, 256>>>(b, n);
         if (cudaDeviceSynchronize() != cudaSuccess) rc = GP_ECUDA;
         else {
             cudaMemcpy(loss, b.loss, sizeof(float), cudaMemcpyDeviceToHost);
@@ -1131,7 +1134,7 @@ int gen_crossover(gp_pop* pop, uint32_t generation) {
     CK(cudaMemsetAsync(g.lastidx, 0xFF, sizeof(int32_t) * d.P, pop->stream));
     CK(cudaMemsetAsync(g.misc, 0, sizeof(uint32_t) * NMISC, pop->stream));
     CK(cudaMemsetAsync(g.gstat, 0, sizeof(unsigned long long) * NGSTAT, pop->stream));
-    k_plan<<<(d.P + 255) / 256, 256, 0, pop->stream>>>(d, g, par);
+    k_plan<<<(d.P + 7) / 8, 256, 0, pop->stream>>>(d, g, par);
     k_assign<<<1, 1024, 0, pop->stream>>>(d, g);
     k_gather<<<pop->nsm * 4, 256, 0, pop->stream>>>(d, g);
     k_copy_children<<<pop->nsm * 8, 256, 0, pop->stream>>>(d, g);
@@ -1177,7 +1180,8 @@ int gen_incremental(gp_pop* pop) {
     k_mlp_targets<<<pb, 256, 0, pop->stream>>>(d, g, pop->mlp);
     k_mlp_train_pass<<<mb, 256, 0, pop->stream>>>(pop->mlp, d.P);
     k_mlp_loss<<<1, 256, 0, pop->stream>>>(pop->mlp, d.P);
-    k_mlp_backward_params<<<(MLP_NP + 255) / 256, 256, 0, pop->stream>>>(pop->mlp, d.P);
+    k_mlp_grad_chunks<<<(d.P + MLP_CH - 1) / MLP_CH, 256, 0, pop->stream>>>(pop->mlp, d.P);
+    k_mlp_grad_reduce<<<(MLP_NP + 255) / 256, 256, 0, pop->stream>>>(pop->mlp, d.P);
     k_mlp_adam<<<(MLP_NP + 255) / 256, 256, 0, pop->stream>>>(pop->mlp, pop->mlp_lr);
     k_mlp_bump<<<1, 32, 0, pop->stream>>>(pop->mlp);
     phase_begin(pop, PH_CACHE);
@@ -1196,7 +1200,7 @@ int gen_incremental(gp_pop* pop) {
             k_merge_offsets<<<1, 1024, 0, pop->stream>>>(d, g);
         }
     }
-    k_merge_write<<<pop->grid_warps, GP_WARPS * 32, 0, pop->stream>>>(d, g, par);
+    k_merge_write<<<d.P < (uint32_t)pop->nsm * 8 ? d.P : pop->nsm * 8, 256, 0, pop->stream>>>(d, g, par);
     k_mark_live<<<gt, 256, 0, pop->stream>>>(d, g);
     k_free_count<<<pop->nsm * 2, 1024, 0, pop->stream>>>(d, g);
     k_free_top<<<1, 1024, 0, pop->stream>>>(d, g);

@@ -20,6 +20,7 @@
 #define MLP_W3 (MLP_B2 + MLP_H)                // [64]
 #define MLP_B3 (MLP_W3 + MLP_H)                // [1]
 #define MLP_NP (MLP_B3 + 1)                    // 5313
+#define MLP_CH 32                              // samples per chunk of the gradient sums
 
 struct MlpBufs {
     float* w;          // [MLP_NP] FP32 master weights
@@ -37,6 +38,7 @@ struct MlpBufs {
     float* dh2;        // [N][64]
     float* dh1;        // [N][64]
     float* loss;       // [1]
+    float* part;       // [ceil(N / MLP_CH)][MLP_NP] per-chunk gradient sums
     uint32_t* step;    // [1] Adam step counter
     uint32_t cap;
 };
@@ -136,29 +138,66 @@ __global__ void __launch_bounds__(256) k_mlp_train_pass(MlpBufs b, uint32_t n) {
     }
 }
 
-// One thread per parameter: the gradient summed over the batch, in sample order.
-__global__ void k_mlp_backward_params(MlpBufs b, uint32_t n) {
-    for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < MLP_NP; p += gridDim.x * blockDim.x) {
-        float g = 0.f;
-        if (p < MLP_B1) {
-            const uint32_t j = p / MLP_IN, f = p % MLP_IN;
-            for (uint32_t s = 0; s < n; ++s) g = fmaf(b.dh1[(size_t)s * MLP_H + j], b.feat[(size_t)s * MLP_IN + f], g);
-        } else if (p < MLP_W2) {
-            const uint32_t j = p - MLP_B1;
-            for (uint32_t s = 0; s < n; ++s) g += b.dh1[(size_t)s * MLP_H + j];
-        } else if (p < MLP_B2) {
-            const uint32_t j = (p - MLP_W2) / MLP_H, k = (p - MLP_W2) % MLP_H;
-            for (uint32_t s = 0; s < n; ++s) g = fmaf(b.dh2[(size_t)s * MLP_H + j], b.h1[(size_t)s * MLP_H + k], g);
-        } else if (p < MLP_W3) {
-            const uint32_t j = p - MLP_B2;
-            for (uint32_t s = 0; s < n; ++s) g += b.dh2[(size_t)s * MLP_H + j];
-        } else if (p < MLP_B3) {
-            const uint32_t j = p - MLP_W3;
-            for (uint32_t s = 0; s < n; ++s) g = fmaf(b.dy[s], b.h2[(size_t)s * MLP_H + j], g);
-        } else {
-            for (uint32_t s = 0; s < n; ++s) g += b.dy[s];
+// Parameter gradients, in two steps: per chunk of MLP_CH samples (staged in
+// shared memory) every parameter's sum over the chunk in sample order, then
+// the chunks' sums added in chunk order.
+struct MlpChunk {
+    float feat[MLP_CH][MLP_IN];
+    float h1[MLP_CH][MLP_H];
+    float h2[MLP_CH][MLP_H];
+    float dh1[MLP_CH][MLP_H];
+    float dh2[MLP_CH][MLP_H];
+    float dy[MLP_CH];
+};
+
+__global__ void __launch_bounds__(256) k_mlp_grad_chunks(MlpBufs b, uint32_t n) {
+    __shared__ MlpChunk ch;
+    const uint32_t nch = (n + MLP_CH - 1) / MLP_CH;
+    for (uint32_t c = blockIdx.x; c < nch; c += gridDim.x) {
+        const uint32_t s0 = c * MLP_CH, ns = min((uint32_t)MLP_CH, n - s0);
+        __syncthreads();
+        for (uint32_t k = threadIdx.x; k < ns * MLP_IN; k += blockDim.x) ch.feat[k / MLP_IN][k % MLP_IN] = b.feat[(size_t)s0 * MLP_IN + k];
+        for (uint32_t k = threadIdx.x; k < ns * MLP_H; k += blockDim.x) {
+            const size_t g = (size_t)s0 * MLP_H + k;
+            ch.h1[k / MLP_H][k % MLP_H] = b.h1[g];
+            ch.h2[k / MLP_H][k % MLP_H] = b.h2[g];
+            ch.dh1[k / MLP_H][k % MLP_H] = b.dh1[g];
+            ch.dh2[k / MLP_H][k % MLP_H] = b.dh2[g];
         }
-        b.grad[p] = g;
+        for (uint32_t k = threadIdx.x; k < ns; k += blockDim.x) ch.dy[k] = b.dy[s0 + k];
+        __syncthreads();
+        float* out = b.part + (size_t)c * MLP_NP;
+        for (uint32_t p = threadIdx.x; p < MLP_NP; p += blockDim.x) {
+            float gsum = 0.f;
+            if (p < MLP_B1) {
+                const uint32_t j = p / MLP_IN, f = p % MLP_IN;
+                for (uint32_t t = 0; t < ns; ++t) gsum = fmaf(ch.dh1[t][j], ch.feat[t][f], gsum);
+            } else if (p < MLP_W2) {
+                const uint32_t j = p - MLP_B1;
+                for (uint32_t t = 0; t < ns; ++t) gsum += ch.dh1[t][j];
+            } else if (p < MLP_B2) {
+                const uint32_t j = (p - MLP_W2) / MLP_H, k = (p - MLP_W2) % MLP_H;
+                for (uint32_t t = 0; t < ns; ++t) gsum = fmaf(ch.dh2[t][j], ch.h1[t][k], gsum);
+            } else if (p < MLP_W3) {
+                const uint32_t j = p - MLP_B2;
+                for (uint32_t t = 0; t < ns; ++t) gsum += ch.dh2[t][j];
+            } else if (p < MLP_B3) {
+                const uint32_t j = p - MLP_W3;
+                for (uint32_t t = 0; t < ns; ++t) gsum = fmaf(ch.dy[t], ch.h2[t][j], gsum);
+            } else {
+                for (uint32_t t = 0; t < ns; ++t) gsum += ch.dy[t];
+            }
+            out[p] = gsum;
+        }
+    }
+}
+
+__global__ void k_mlp_grad_reduce(MlpBufs b, uint32_t n) {
+    const uint32_t nch = (n + MLP_CH - 1) / MLP_CH;
+    for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < MLP_NP; p += gridDim.x * blockDim.x) {
+        float gsum = 0.f;
+        for (uint32_t c = 0; c < nch; ++c) gsum += b.part[(size_t)c * MLP_NP + p];
+        b.grad[p] = gsum;
     }
 }
 
