@@ -580,21 +580,28 @@ struct LevelDesc {
 #define LD_BAD (1u << 10)
 #define LD_NOSIB (1u << 11)
 
+#define WALK_RING 16           // most levels a walk team keeps in flight (descriptors and sibling values)
+#define WALK_SPIN (1u << 22)   // bound on the polls of one wait inside a walk team
+
+// levels in flight: fewer when value vectors are long
+__host__ __device__ inline uint32_t walk_ring(uint32_t Cpad) { return Cpad <= 128 ? 16u : Cpad <= 256 ? 8u : 4u; }
+
 template <int K>
 struct TeamLayout {
     uint32_t kc, anc, ancg, lvl, desc, nv, ov, sv, mv, sc, warp0, warp_bytes, total;
     __host__ __device__ TeamLayout(int W, uint32_t Cpad, uint32_t nw) {
+        const uint32_t ring = walk_ring(Cpad);
         uint32_t o = 0;
         kc = o;   o += (256 + 6 * 32) * 4;
         anc = o;  o += WALK_MAXLVL * 4;
         ancg = o; o += WALK_MAXLVL * 4;
         lvl = o;  o += WALK_MAXLVL * 4;
-        desc = o; o += 8 * sizeof(LevelDesc);
+        desc = o; o += WALK_RING * sizeof(LevelDesc);
         nv = o;   o += Cpad * 4;
         ov = o;   o += Cpad * 4;
-        sv = o;   o += 8 * Cpad * 4;
-        mv = o;   o += 8 * Cpad * 4;
-        sc = o;   o += 16 * 4;
+        sv = o;   o += ring * Cpad * 4;
+        mv = o;   o += ring * Cpad * 4;
+        sc = o;   o += (16 + 2 * WALK_RING) * 4;
         o = (o + 15u) & ~15u;
         warp0 = o;
         warp_bytes = (uint32_t)W * 32 * K * 4 + 2 * STAGE_BYTES;
@@ -834,8 +841,11 @@ __global__ void __launch_bounds__(256) k_walk(DevPop d, GenBufs g, CacheView par
     ic.g = d.ovf + (size_t)(blockIdx.x * nw + warp) * (d.maxdepth - d.W) * 32 * K;
     uint8_t* stA = wb + (size_t)d.W * 32 * K * 4;
     uint8_t* stB = stA + STAGE_BYTES;
-    // levels per batch: one per warp, or fewer when a level spans several case blocks
-    const uint32_t nlb = max(1u, min(8u, nw / ncb));
+    volatile uint32_t* dtag = sc + 16;                 // [WALK_RING] level + 1 whose descriptor is in the slot
+    volatile uint32_t* vcnt = sc + 16 + WALK_RING;     // [WALK_RING] case blocks of the slot's sibling done
+    const uint32_t nev = nw - 1;                       // sibling evaluators (warps 1..nw-1)
+    const uint32_t ring = walk_ring(Cpad);
+    const uint32_t ahead = ring;                       // levels built ahead of the combination
     unsigned long long st_interp = 0, st_levels = 0, st_stopped = 0, st_pathops = 0;
 
     for (;;) {
@@ -899,7 +909,6 @@ __global__ void __launch_bounds__(256) k_walk(DevPop d, GenBufs g, CacheView par
             if (__float_as_uint(nvs[j]) != __float_as_uint(ovs[j])) okc = false;
         bool stopped = __syncthreads_and(okc) != 0;
         int32_t stop_level = stopped ? 0 : -1;
-        uint32_t levels = 0;
         if (root_rec) {
             float* dst = g.pv_val + (size_t)rslot * Cpad;
             for (uint32_t j = tid; j < Cpad; j += nthr) dst[j] = nvs[j];
@@ -922,137 +931,217 @@ __global__ void __launch_bounds__(256) k_walk(DevPop d, GenBufs g, CacheView par
         const int32_t hneed = (int32_t)sc[5];
         if (sc[4]) continue;
 
-        // ---- walk up, a batch of levels at a time
-        uint32_t bq = c, bqend = c + s, bk = 0;          // path state of the descriptor builder (thread 0)
-        int32_t bpe = (nsmall > 0) ? -1 : A;
-        bool btop = false;
-        bool done = false;
-        uint32_t level = 0;
-        uint32_t guard = 0;
-        while (!done && guard++ < (1u << 24)) {
-            if (tid == 0) {
-                uint32_t nl = 0;
-                while (nl < nlb && !btop) {
-                    uint32_t p, pend;
-                    int32_t pent;
-                    if (bk < nsmall) {
-                        p = anc[bk];
-                        pend = lvl[ancg[bk] + 1];
-                        pent = -1;
-                    } else {
-                        pent = (bk == nsmall) ? A : bpe;
-                        if (pent < 0) { btop = true; break; }                  // above the root
-                        p = par.e_pos[pent];
-                        pend = (uint32_t)((int64_t)par.e_end[pent] + ((int64_t)s - (int64_t)r));
+        // ---- walk up.  Warp 0 builds level descriptors ahead (a ring of
+        // WALK_RING levels) and combines the levels in order as their sibling
+        // values arrive; warps 1.. evaluate siblings ahead of it, level after
+        // level, each without waiting for the others.  The combination stops
+        // where the method stops; siblings computed past it are discarded.
+        if (tid < WALK_RING) { dtag[tid] = 0u; vcnt[tid] = 0u; }
+        if (tid == 0) sc[8] = 0u;                          // done flag
+        __syncthreads();
+        bool stopped_w = stopped;
+        int32_t stop_level_w = stop_level;
+        uint32_t levels_w = 0;
+        if (warp == 0) {
+            uint32_t bq = c, bqend = c + s, bk = 0;        // builder state (lane 0)
+            int32_t bpe = (nsmall > 0) ? -1 : A;
+            bool btop = false;
+            uint32_t nb = 0, ncm = 0, level = 0;           // levels built, levels combined
+            uint32_t rbase = 0, rleft = 0;                 // this child's reserved record slots
+            bool fail = false;
+            uint32_t guard = 0;
+            while (guard++ < (1u << 24)) {
+                // build ahead while the ring has room
+                if (lane == 0) {
+                    while (!btop && nb < ncm + ahead) {
+                        uint32_t p, pend;
+                        int32_t pent;
+                        if (bk < nsmall) {
+                            p = anc[bk];
+                            pend = lvl[ancg[bk] + 1];
+                            pent = -1;
+                        } else {
+                            pent = (bk == nsmall) ? A : bpe;
+                            if (pent < 0) { btop = true; break; }                  // above the root
+                            p = par.e_pos[pent];
+                            pend = (uint32_t)((int64_t)par.e_end[pent] + ((int64_t)s - (int64_t)r));
+                        }
+                        // above the stop only small ancestors that the child caches need values
+                        if (stopped_w && (pent >= 0 || (int32_t)bk > hneed)) { btop = true; break; }
+                        const bool left = (bq == p + 1);
+                        const uint32_t ss = left ? bqend : p + 1;
+                        const uint32_t se = left ? pend : bq;
+                        uint32_t flg = ok_[p] | (left ? LD_LEFT : 0u) | ((p == 0 || pend - p >= T) ? LD_CACHED : 0u);
+                        int32_t sib = -1;
+                        if (se <= ss || se > nk) flg |= LD_BAD;
+                        else if (se - ss >= T) {
+                            sib = (pent < 0) ? -1 : (left ? par.e_c1[pent] : par.e_c0[pent]);
+                            if (sib < 0) flg |= LD_NOSIB;
+                        }
+                        LevelDesc& D = desc[nb % ring];
+                        D.p = p; D.pend = pend; D.ss = ss; D.se = se; D.pent = pent; D.sib = sib; D.flags = flg;
+                        D.k = (int32_t)bk;
+                        D.pslot = (pent >= 0) ? par.e_slot[pent] : 0u;
+                        D.sslot = (sib >= 0) ? par.e_slot[sib] : 0u;
+                        __threadfence_block();
+                        dtag[nb % ring] = nb + 1;
+                        ++nb;
+                        if (flg & (LD_BAD | LD_NOSIB)) { btop = true; break; }
+                        bq = p;
+                        bqend = pend;
+                        if (bk >= nsmall) bpe = par.e_par[pent];
+                        ++bk;
+                        if (p == 0) { btop = true; break; }
                     }
-                    // above the stop only small ancestors that the child caches need values
-                    if (stopped && (pent >= 0 || (int32_t)bk > hneed)) { btop = true; break; }
-                    const bool left = (bq == p + 1);
-                    const uint32_t ss = left ? bqend : p + 1;
-                    const uint32_t se = left ? pend : bq;
-                    uint32_t flg = ok_[p] | (left ? LD_LEFT : 0u) | ((p == 0 || pend - p >= T) ? LD_CACHED : 0u);
-                    int32_t sib = -1;
-                    if (se <= ss || se > nk) flg |= LD_BAD;
-                    else if (se - ss >= T) {
-                        sib = (pent < 0) ? -1 : (left ? par.e_c1[pent] : par.e_c0[pent]);
-                        if (sib < 0) flg |= LD_NOSIB;
+                }
+                __syncwarp();
+                nb = __shfl_sync(FULL, nb, 0);
+                btop = __shfl_sync(FULL, btop ? 1u : 0u, 0) != 0;
+                if (ncm == nb) {
+                    if (btop) break;                                           // nothing left to combine
+                    continue;
+                }
+                const uint32_t slot = ncm % ring;
+                LevelDesc D = desc[slot];
+                if (stopped_w && (D.pent >= 0 || D.k > hneed)) break;
+                // the level's sibling values: from the evaluators, or computed here in a team of one
+                if (nev == 0) {
+                    if (!(D.flags & (LD_BAD | LD_NOSIB))) {
+                        for (uint32_t cb = 0; cb < ncb; ++cb) {
+                            float v[K];
+                            if (!stopped_w && D.pent >= 0) {
+                                load_vec<K>(par.slots, Cpad, D.pslot, v, cb);
+                                store_blk<K>(mvs + slot * Cpad, cb, v);
+                            }
+                            if (D.sib >= 0) load_vec<K>(par.slots, Cpad, D.sslot, v, cb);
+                            else {
+                                load_cases<K>(d, cb, ic.xv);
+                                eval_run<K, B>(ok_, D.ss, D.se, stA, ic, v, d.status);
+                                st_interp += D.se - D.ss;
+                            }
+                            store_blk<K>(svs + slot * Cpad, cb, v);
+                        }
                     }
-                    LevelDesc& D = desc[nl++];
-                    D.p = p; D.pend = pend; D.ss = ss; D.se = se; D.pent = pent; D.sib = sib; D.flags = flg;
-                    D.k = (int32_t)bk;
-                    D.pslot = (pent >= 0) ? par.e_slot[pent] : 0u;
-                    D.sslot = (sib >= 0) ? par.e_slot[sib] : 0u;
-                    if (flg & (LD_BAD | LD_NOSIB)) { btop = true; break; }
-                    bq = p;
-                    bqend = pend;
-                    if (bk >= nsmall) bpe = par.e_par[pent];
-                    ++bk;
-                    if (p == 0) { btop = true; break; }
+                } else {
+                    uint32_t spins = 0, ready = 0;
+                    while ((ready = __shfl_sync(FULL, lane == 0 ? vcnt[slot] : 0u, 0)) < ncb && ++spins < WALK_SPIN)
+                        __nanosleep(64);
+                    if (ready < ncb) { if (lane == 0) set_status(d.status, ST_TIMEOUT); fail = true; break; }
+                    __threadfence_block();
                 }
-                sc[6] = nl;
-                sc[7] = btop ? 1u : 0u;
-            }
-            __syncthreads();
-            const uint32_t nl = sc[6];
-            const bool top = sc[7] != 0;
-            if (nl == 0) break;
-            // siblings of the batch's levels, one (level, case block) per warp at a time
-            for (uint32_t it = warp; it < nl * ncb; it += nw) {
-                const uint32_t l = it / ncb, cb = it - l * ncb;
-                const LevelDesc& D = desc[l];
-                if (D.flags & (LD_BAD | LD_NOSIB)) continue;
-                if (stopped && (D.pent >= 0 || D.k > hneed)) continue;       // never combined
-                float v[K];
-                // the mother's cached value at p, needed for the comparison below the stop
-                if (!stopped && D.pent >= 0) {
-                    load_vec<K>(par.slots, Cpad, D.pslot, v, cb);
-                    store_blk<K>(mvs + l * Cpad, cb, v);
-                }
-                if (D.sib >= 0) load_vec<K>(par.slots, Cpad, D.sslot, v, cb);
-                else {
-                    load_cases<K>(d, cb, ic.xv);
-                    eval_run<K, B>(ok_, D.ss, D.se, stA, ic, v, d.status);
-                    st_interp += D.se - D.ss;
-                }
-                store_blk<K>(svs + l * Cpad, cb, v);
-            }
-            __syncthreads();
-            for (uint32_t l = 0; l < nl; ++l) {
-                const LevelDesc D = desc[l];
-                if (stopped && (D.pent >= 0 || D.k > hneed)) { done = true; break; }
+                __syncwarp();
                 ++level;
                 if (D.flags & (LD_BAD | LD_NOSIB)) {
-                    if (tid == 0) set_error(d, ST_STRUCT, (D.flags & LD_BAD) ? 6 : 7, i, D.p, D.se - D.ss);
-                    done = true;
+                    if (lane == 0) set_error(d, ST_STRUCT, (D.flags & LD_BAD) ? 6 : 7, i, D.p, D.se - D.ss);
+                    fail = true;
                     break;
                 }
                 const uint32_t op = D.flags & 0xFFu;
                 const bool left = (D.flags & LD_LEFT) != 0;
-                const float* svl = svs + l * Cpad;
-                const float* pvv = (D.pent >= 0) ? mvs + l * Cpad : nullptr;
+                const float* svl = svs + slot * Cpad;
+                const float* pvv = mvs + slot * Cpad;
                 bool okl = true;
-                for (uint32_t j = tid; j < Cpad; j += nthr) {
+                for (uint32_t j = lane; j < Cpad; j += 32) {
                     float o[1] = {ovs[j]};
                     const float sv1[1] = {svl[j]};
                     combine<1, B>(op, left, o, sv1);         // mother's value at p (exact recomputation)
-                    if (!stopped) {
+                    if (!stopped_w) {
                         float n1[1] = {nvs[j]};
                         combine<1, B>(op, left, n1, sv1);
                         nvs[j] = n1[0];
-                        if (pvv) o[0] = pvv[j];
+                        if (D.pent >= 0) o[0] = pvv[j];
                         if (j < Cn && __float_as_uint(n1[0]) != __float_as_uint(o[0])) okl = false;
                     }
                     ovs[j] = o[0];
                 }
-                const bool lvl_eq = __syncthreads_and(okl) != 0;
-                if (!stopped) {
-                    ++levels;
+                const bool lvl_eq = __all_sync(FULL, okl);
+                __syncwarp();
+                if (!stopped_w) {
+                    ++levels_w;
                     ++st_pathops;
-                    if (lvl_eq) { stopped = true; stop_level = (int32_t)level; }
+                    if (lvl_eq) { stopped_w = true; stop_level_w = (int32_t)level; }
                 }
                 // record the child's value here when the child caches this node and the mother's
                 // cache cannot supply it (disrupted, or not cached in the mother); above the
                 // stop only small ancestors (pent < 0) get here
                 if ((D.flags & LD_CACHED) && (!lvl_eq || D.pent < 0)) {
-                    if (tid == 0) sc[1] = atomicAdd(&g.misc[M_PV], 1u);
-                    __syncthreads();
-                    const uint32_t slot = sc[1];
-                    if (slot >= g.pvcap) { if (tid == 0) set_status(d.status, ST_PATH); done = true; break; }
-                    const float* src = stopped ? ovs : nvs;
-                    float* dst = g.pv_val + (size_t)slot * Cpad;
-                    for (uint32_t j = tid; j < Cpad; j += nthr) dst[j] = src[j];
-                    if (tid == 0) {
-                        g.pv_rec[slot] = make_uint4(i, npv, D.p, slot | (D.pent < 0 ? 0x80000000u : 0u));
-                        g.pv_end[slot] = D.pend;
+                    if (rleft == 0) {
+                        uint32_t b0 = 0;
+                        if (lane == 0) b0 = atomicAdd(&g.misc[M_PV], 8u);
+                        rbase = __shfl_sync(FULL, b0, 0);
+                        rleft = 8;
+                    }
+                    const uint32_t rs = rbase++;
+                    --rleft;
+                    if (rs >= g.pvcap) { if (lane == 0) set_status(d.status, ST_PATH); fail = true; break; }
+                    const float* src = stopped_w ? ovs : nvs;
+                    float* dst = g.pv_val + (size_t)rs * Cpad;
+                    for (uint32_t j = lane; j < Cpad; j += 32) dst[j] = src[j];
+                    if (lane == 0) {
+                        g.pv_rec[rs] = make_uint4(i, npv, D.p, rs | (D.pent < 0 ? 0x80000000u : 0u));
+                        g.pv_end[rs] = D.pend;
                     }
                     ++npv;
                     if (D.pent < 0) ++nins_i;
                 }
-                if (D.p == 0) { done = true; break; }
+                // release the slot to the builder
+                if (lane == 0) vcnt[slot] = 0u;
+                __syncwarp();
+                ++ncm;
+                if (D.p == 0) break;
             }
-            if (top) done = true;
-            __syncthreads();                 // the builder rewrites the descriptors next
+            // reserved record slots left unused are marked as holes
+            for (uint32_t k = lane; k < rleft; k += 32)
+                if (rbase + k < g.pvcap) g.pv_rec[rbase + k] = make_uint4(0xFFFFFFFFu, 0u, 0u, 0u);
+            (void)fail;
+            __threadfence_block();
+            if (lane == 0) sc[8] = 1u;                      // evaluators stop
+        } else {
+            // evaluators: (level, case block) items it = warp - 1, warp - 1 + nev, ...
+            for (uint32_t it = warp - 1;; it += nev) {
+                const uint32_t k = it / ncb, cb = it - k * ncb;
+                const uint32_t slot = k % ring;
+                uint32_t spins = 0, st = 0;
+                for (;;) {
+                    st = __shfl_sync(FULL, lane == 0 ? (sc[8] ? 0xFFFFFFFFu : dtag[slot]) : 0u, 0);
+                    if (st == 0xFFFFFFFFu || st == k + 1) break;
+                    if (++spins >= WALK_SPIN) break;
+                    __nanosleep(64);
+                }
+                if (st != k + 1) {
+                    if (st != 0xFFFFFFFFu && lane == 0) set_status(d.status, ST_TIMEOUT);
+                    break;
+                }
+                __threadfence_block();
+                const LevelDesc D = desc[slot];
+                if (!(D.flags & (LD_BAD | LD_NOSIB))) {
+                    float v[K];
+                    if (D.pent >= 0) {
+                        load_vec<K>(par.slots, Cpad, D.pslot, v, cb);
+                        store_blk<K>(mvs + slot * Cpad, cb, v);
+                    }
+                    if (D.sib >= 0) load_vec<K>(par.slots, Cpad, D.sslot, v, cb);
+                    else {
+                        load_cases<K>(d, cb, ic.xv);
+                        eval_run<K, B>(ok_, D.ss, D.se, stA, ic, v, d.status);
+                        st_interp += D.se - D.ss;
+                    }
+                    store_blk<K>(svs + slot * Cpad, cb, v);
+                }
+                __threadfence_block();
+                __syncwarp();
+                if (lane == 0) atomicAdd(const_cast<uint32_t*>(&vcnt[slot]), 1u);
+            }
         }
+        __syncthreads();
+        // the combiner's results, from warp 0 to the team
+        if (tid == 0) { sc[9] = stopped_w ? 1u : 0u; sc[10] = (uint32_t)stop_level_w; sc[11] = levels_w; sc[12] = npv; sc[13] = nins_i; }
+        __syncthreads();
+        stopped = sc[9] != 0;
+        stop_level = (int32_t)sc[10];
+        const uint32_t levels = sc[11];
+        npv = sc[12];
+        nins_i = sc[13];
         // ---- fitness
         if (tid == 0) {
             g.stop[i] = stop_level;
@@ -1075,6 +1164,7 @@ __global__ void __launch_bounds__(256) k_walk(DevPop d, GenBufs g, CacheView par
             }
             st_levels += levels;
         }
+        __syncthreads();                     // nvs and the shared words are reused by the next child
     }
     if (lane == 0) atomicAdd(&g.gstat[G_INTERP], st_interp);
     if (tid == 0) {
@@ -1108,6 +1198,7 @@ __global__ void k_pv_scatter(DevPop d, GenBufs g) {
     const uint32_t n = min(g.misc[M_PV], g.pvcap);
     for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
         const uint4 rec = g.pv_rec[r];
+        if (rec.x >= d.P) continue;                     // a reserved slot left unused
         g.pv_sorted[g.pv_off[rec.x] + rec.y] = make_uint4(rec.z, rec.w, g.pv_end[r], 0u);
     }
 }
