@@ -155,8 +155,14 @@ __device__ __forceinline__ void step_fast(uint32_t op, float (&acc)[K], float*& 
 
 // Evaluate the nodes [s, e) staged at `stage` (which holds bytes from
 // s & ~15 on) right to left; afterwards st.acc is the value of the subtree
-// starting at s.  Words of four nodes are run without per-node stack
-// checks when the depth leaves room for four pushes or pops.
+// starting at s.  Words of four nodes run without per-node checks while the
+// shared window has room for four pushes.  A complete subtree never pops
+// below the bottom of its own stack, so the fast path does not test for
+// that per node: a word that ends below the bottom (a malformed run) marks
+// the run failed and leaves the fast path, so at most four entries below the
+// warp's stack are touched -- every shared-memory layout keeps that much
+// room below each stack -- and so does a run that does not end with exactly
+// one entry (the initial running value) on the stack.
 template <int K, bool B = false>
 __device__ __forceinline__ void interp_staged(const uint8_t* stage, uint32_t s, uint32_t e,
                                               Istate<K>& st, const Ictx<K>& c) {
@@ -169,27 +175,37 @@ __device__ __forceinline__ void interp_staged(const uint8_t* stage, uint32_t s, 
         step_checked<K, B>(stage[p - a], st, c, lane);
     }
     const uint32_t* wp = reinterpret_cast<const uint32_t*>(stage);
+    float* const sbase = c.s + lane * K;
+    const int wfast = c.W - 4;
+    bool under = false;
     while (p >= s + 4) {
-        const uint32_t w = wp[(p - 4 - a) >> 2];
-        if (st.sp >= 4 && st.sp + 4 <= c.W) {
-            float* sptr = c.s + ((size_t)st.sp * 32 + lane) * K;
-            step_fast<K, B>(w >> 24, st.acc, sptr, c, lane);
-            step_fast<K, B>((w >> 16) & 0xFFu, st.acc, sptr, c, lane);
-            step_fast<K, B>((w >> 8) & 0xFFu, st.acc, sptr, c, lane);
-            step_fast<K, B>(w & 0xFFu, st.acc, sptr, c, lane);
-            st.sp = (int)((sptr - c.s - lane * K) / (32 * K));
+        if (st.sp >= 0 && st.sp <= wfast) {
+            float* sptr = sbase + (ptrdiff_t)st.sp * 32 * K;
+            float* const sfast = sbase + (ptrdiff_t)wfast * 32 * K;
+            do {
+                const uint32_t w = wp[(p - 4 - a) >> 2];
+                step_fast<K, B>(w >> 24, st.acc, sptr, c, lane);
+                step_fast<K, B>((w >> 16) & 0xFFu, st.acc, sptr, c, lane);
+                step_fast<K, B>((w >> 8) & 0xFFu, st.acc, sptr, c, lane);
+                step_fast<K, B>(w & 0xFFu, st.acc, sptr, c, lane);
+                under |= (sptr < sbase);
+                p -= 4;
+            } while (p >= s + 4 && sptr <= sfast && sptr >= sbase);
+            st.sp = (int)((sptr - sbase) / (32 * K));
         } else {
+            const uint32_t w = wp[(p - 4 - a) >> 2];
             step_checked<K, B>(w >> 24, st, c, lane);
             step_checked<K, B>((w >> 16) & 0xFFu, st, c, lane);
             step_checked<K, B>((w >> 8) & 0xFFu, st, c, lane);
             step_checked<K, B>(w & 0xFFu, st, c, lane);
+            p -= 4;
         }
-        p -= 4;
     }
     while (p > s) {
         --p;
         step_checked<K, B>(stage[p - a], st, c, lane);
     }
+    if (under || st.sp != 1) st.ok = false;
 }
 
 // ---- staging with cp.async (16 bytes per lane per instruction) ----
@@ -238,7 +254,9 @@ __device__ __forceinline__ void store_slot(const DevPop& d, uint32_t slot, uint3
 // Shared-memory layout of a CTA running the interpreter.
 template <int K>
 struct SmemLayout {
-    static constexpr size_t kc_bytes = (256 + 6 * 32) * sizeof(float);   // constants, then Boolean inputs
+    // constants, then Boolean inputs, padded to four stack entries (at K = 4)
+    // so that a malformed run's underflow stays inside the CTA's memory
+    static constexpr size_t kc_bytes = (256 + 6 * 32) * sizeof(float) + 4 * 32 * 4 * sizeof(float);
     __host__ __device__ static size_t stack_bytes(int W) { return (size_t)W * 32 * K * sizeof(float); }
     __host__ __device__ static size_t warp_bytes(int W) { return stack_bytes(W) + 2 * STAGE_BYTES; }
     __host__ __device__ static size_t total(int W, int warps) { return kc_bytes + warps * warp_bytes(W); }

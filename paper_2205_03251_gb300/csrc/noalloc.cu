@@ -58,9 +58,18 @@ struct NaArgs {
 };
 
 __global__ void __launch_bounds__(NA_WARPS * 32) k_eval_small_noalloc(NaArgs a) {
-    __shared__ __align__(16) float kc[256];
-    __shared__ __align__(16) float sstack[NA_WARPS][NA_W * 32 * NA_K];
-    __shared__ __align__(16) uint8_t stage[NA_WARPS][STAGE_BYTES];
+    // one block of shared memory: four stack entries of room below the first
+    // stack (the interpreter's fast path may touch them on a malformed tree)
+    struct NaSmem {
+        float pad[4 * 32 * NA_K];
+        float kc[256];
+        float sstack[NA_WARPS][NA_W * 32 * NA_K];
+        uint8_t stage[NA_WARPS][STAGE_BYTES];
+    };
+    __shared__ __align__(16) NaSmem sm;
+    float* const kc = sm.kc;
+    float (*const sstack)[NA_W * 32 * NA_K] = sm.sstack;
+    uint8_t (*const stage)[STAGE_BYTES] = sm.stage;
     const int lane = lane_id(), warp = threadIdx.x >> 5;
     fill_kc(kc, a.consts);
     __syncthreads();
