@@ -811,7 +811,7 @@ __device__ bool walk_ancestors(const DevPop& d, const CacheView& par, uint32_t i
 // child's cache; above the stop only child-cached nodes that the mother
 // does not cache need computing.
 template <int K, bool B>
-__global__ void __launch_bounds__(256) k_walk(DevPop d, GenBufs g, CacheView par, uint32_t nw) {
+__global__ void __launch_bounds__(256, 2) k_walk(DevPop d, GenBufs g, CacheView par, uint32_t nw) {
     if (halted(d)) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const uint32_t Cpad = d.Cpad, Cn = d.C, ncb = d.ncb, T = d.T;

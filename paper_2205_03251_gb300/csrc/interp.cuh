@@ -114,11 +114,41 @@ struct Istate {
     bool ok;
 };
 
-// One node, any stack depth (bounds checked).
+// Shared-memory accesses by 32-bit shared-window address (no generic
+// 64-bit pointer arithmetic on the interpreter's hot path).  They are
+// volatile, so they keep their order among themselves: a push is never
+// moved past the pop of the same entry.
+template <int K>
+__device__ __forceinline__ void sts_vec(uint32_t a, const float (&v)[K]) {
+    if constexpr (K == 1) asm volatile("st.shared.f32 [%0], %1;" ::"r"(a), "f"(v[0]));
+    else if constexpr (K == 2) asm volatile("st.shared.v2.f32 [%0], {%1, %2};" ::"r"(a), "f"(v[0]), "f"(v[1]));
+    else asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(a), "f"(v[0]), "f"(v[1]), "f"(v[2]), "f"(v[3]));
+}
+template <int K>
+__device__ __forceinline__ void lds_vec(uint32_t a, float (&v)[K]) {
+    if constexpr (K == 1) asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v[0]) : "r"(a));
+    else if constexpr (K == 2) asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v[0]), "=f"(v[1]) : "r"(a));
+    else asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]) : "r"(a));
+}
+__device__ __forceinline__ float lds_f32(uint32_t a) {
+    float v;
+    asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(a));
+    return v;
+}
+__device__ __forceinline__ uint32_t lds_u32(uint32_t a) {
+    uint32_t v;
+    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(a));
+    return v;
+}
+
+// One node, any stack depth (bounds checked).  The shared window is
+// accessed through the same volatile helpers as the fast path (so the two
+// keep their order), the overflow area through ordinary global accesses.
 template <int K, bool B = false>
 __device__ __forceinline__ void step_checked(uint32_t op, Istate<K>& st, const Ictx<K>& c, int lane) {
+    const uint32_t sw = (uint32_t)__cvta_generic_to_shared(c.s) + (uint32_t)lane * K * 4;
     if (op >= 4) {
-        if (st.sp < c.W) vstore<K>(c.s + ((size_t)st.sp * 32 + lane) * K, st.acc);
+        if (st.sp < c.W) sts_vec<K>(sw + (uint32_t)st.sp * 32 * K * 4, st.acc);
         else if (st.sp < c.maxd) vstore<K>(c.g + ((size_t)(st.sp - c.W) * 32 + lane) * K, st.acc);
         else st.ok = false;
         if (st.sp < c.maxd) ++st.sp;
@@ -131,24 +161,34 @@ __device__ __forceinline__ void step_checked(uint32_t op, Istate<K>& st, const I
             for (int k = 0; k < K; ++k) r[k] = 0.f;
         } else {
             --st.sp;
-            if (st.sp < c.W) vload<K>(c.s + ((size_t)st.sp * 32 + lane) * K, r);
+            if (st.sp < c.W) lds_vec<K>(sw + (uint32_t)st.sp * 32 * K * 4, r);
             else vload<K>(c.g + ((size_t)(st.sp - c.W) * 32 + lane) * K, r);
         }
         apply_vec<K, B>(op, st.acc, r);
     }
 }
 
-// One node when the whole stack access stays inside the shared window.
+// One node when the whole stack access stays inside the shared window;
+// sa is this lane's next free stack entry, kca the constant table and kba
+// this lane's Boolean input words (shared-window addresses).
 template <int K, bool B = false>
-__device__ __forceinline__ void step_fast(uint32_t op, float (&acc)[K], float*& sptr, const Ictx<K>& c, int lane) {
+__device__ __forceinline__ void step_fast(uint32_t op, float (&acc)[K], uint32_t& sa, uint32_t kca, uint32_t kba,
+                                          const Ictx<K>& c) {
     if (op >= 4) {
-        vstore<K>(sptr, acc);
-        sptr += 32 * K;
-        leaf_value<K, B>(op, acc, c, lane);
+        sts_vec<K>(sa, acc);
+        sa += 32 * K * 4;
+        if constexpr (B) {
+            const uint32_t j = (op - 4u) < 6u ? op - 4u : 0u;
+            acc[0] = lds_f32(kba + j * 32 * 4);
+        } else {
+            const float cv = lds_f32(kca + op * 4);
+#pragma unroll
+            for (int k = 0; k < K; ++k) acc[k] = (op == 4) ? c.xv[k] : cv;
+        }
     } else {
-        sptr -= 32 * K;
+        sa -= 32 * K * 4;
         float r[K];
-        vload<K>(sptr, r);
+        lds_vec<K>(sa, r);
         apply_vec<K, B>(op, acc, r);
     }
 }
@@ -175,23 +215,26 @@ __device__ __forceinline__ void interp_staged(const uint8_t* stage, uint32_t s, 
         step_checked<K, B>(stage[p - a], st, c, lane);
     }
     const uint32_t* wp = reinterpret_cast<const uint32_t*>(stage);
-    float* const sbase = c.s + lane * K;
+    const uint32_t wa = (uint32_t)__cvta_generic_to_shared(stage) - a;      // shared address of byte 0
+    const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(c.s) + lane * K * 4;
+    const uint32_t kca = (uint32_t)__cvta_generic_to_shared(c.kc);
+    const uint32_t kba = B ? (uint32_t)__cvta_generic_to_shared(c.kb) + lane * 4 : 0u;
     const int wfast = c.W - 4;
+    const uint32_t sfast = sbase + (uint32_t)wfast * 32 * K * 4;
     bool under = false;
     while (p >= s + 4) {
         if (st.sp >= 0 && st.sp <= wfast) {
-            float* sptr = sbase + (ptrdiff_t)st.sp * 32 * K;
-            float* const sfast = sbase + (ptrdiff_t)wfast * 32 * K;
+            uint32_t sa = sbase + (uint32_t)st.sp * 32 * K * 4;
             do {
-                const uint32_t w = wp[(p - 4 - a) >> 2];
-                step_fast<K, B>(w >> 24, st.acc, sptr, c, lane);
-                step_fast<K, B>((w >> 16) & 0xFFu, st.acc, sptr, c, lane);
-                step_fast<K, B>((w >> 8) & 0xFFu, st.acc, sptr, c, lane);
-                step_fast<K, B>(w & 0xFFu, st.acc, sptr, c, lane);
-                under |= (sptr < sbase);
+                const uint32_t w = lds_u32(wa + p - 4);
+                step_fast<K, B>(w >> 24, st.acc, sa, kca, kba, c);
+                step_fast<K, B>((w >> 16) & 0xFFu, st.acc, sa, kca, kba, c);
+                step_fast<K, B>((w >> 8) & 0xFFu, st.acc, sa, kca, kba, c);
+                step_fast<K, B>(w & 0xFFu, st.acc, sa, kca, kba, c);
+                under |= ((int32_t)(sa - sbase) < 0);
                 p -= 4;
-            } while (p >= s + 4 && sptr <= sfast && sptr >= sbase);
-            st.sp = (int)((sptr - sbase) / (32 * K));
+            } while (p >= s + 4 && (int32_t)(sa - sfast) <= 0 && (int32_t)(sa - sbase) >= 0);
+            st.sp = (int32_t)(sa - sbase) / (32 * K * 4);
         } else {
             const uint32_t w = wp[(p - 4 - a) >> 2];
             step_checked<K, B>(w >> 24, st, c, lane);
