@@ -60,6 +60,7 @@ def parse():
     ap.add_argument("--no-graph", dest="graph", action="store_false")
     ap.add_argument("--autotune", dest="autotune", action="store_true", default=True)
     ap.add_argument("--no-autotune", dest="autotune", action="store_false")
+    ap.add_argument("--cache-budget-gb", type=int, default=40, help="device memory for cached value vectors")
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu", action="store_true")
@@ -69,6 +70,18 @@ def parse():
     if a.trees is None:
         a.trees = 4096 if a.workload == "uneven" else 500
     return a
+
+
+def profile_figure(name: str, key: str):
+    """A figure recorded in a committed ncu summary under profiles/ (a line
+    `key: value`), or None."""
+    try:
+        for line in open(os.path.join(ROOT, "profiles", name)):
+            if line.startswith(key + ":"):
+                return float(line.split(":", 1)[1])
+    except OSError:
+        pass
+    return None
 
 
 def measured_peaks():
@@ -328,15 +341,17 @@ def main():
     stream = torch.cuda.current_stream()
     boolean = bool(w.get("boolean"))
     maxn = w.get("max_nodes", 1 << 21)
-    pop_kw = {"cache_threshold": args.threshold, "packing": PACKING[args.packing]}
+    pop_kw = {"cache_threshold": args.threshold, "packing": PACKING[args.packing],
+              "cache_budget_bytes": args.cache_budget_gb << 30}
     tune = None
     if args.workload == "uneven" and args.autotune:
-        ks = (1,) if boolean else (1, 2, 4)
+        ks = (1,) if boolean else ((1, 2) if args.cases <= 64 else (2, 4))
         best, table = gp.autotune(w["x"], w["t"], w["consts"], w["ops"], w["off"], max_nodes=maxn, ks=ks,
-                                  ts=(256, 1024), generations=2, boolean=boolean, seed=0x5EED + rank,
-                                  packing=pop_kw["packing"], stream=stream)
+                                  ts=(256, 1024), teams=(1, 2, 4), generations=2, boolean=boolean,
+                                  seed=0x5EED + rank, packing=pop_kw["packing"], stream=stream,
+                                  cache_budget_bytes=args.cache_budget_gb << 30)
         pop_kw.update(best)
-        tune = {"chosen": best, "candidates": [{k: r[k] for k in ("cases_per_lane", "cache_threshold",
+        tune = {"chosen": best, "candidates": [{k: r[k] for k in ("cases_per_lane", "cache_threshold", "walk_team",
                                                                    "ms_full", "ms_generation", "identical")}
                                                for r in table]}
     pop = gp.Population(None if boolean else w["x"], None if boolean else w["t"], w["consts"], w["ops"], w["off"],
@@ -420,6 +435,7 @@ def main():
     if tune:
         line["config"]["cases_per_lane"] = pop_kw["cases_per_lane"]
         line["config"]["cache_threshold"] = pop_kw["cache_threshold"]
+        line["config"]["walk_team"] = pop_kw["walk_team"]
         line["autotune"] = tune
     if generational:
         xo_ms = phases["crossover"]
@@ -430,19 +446,34 @@ def main():
         line["full_eval_gpops"] = (full_st["cum_equivalent_ops"] / (full_ms * 1e-3) / 1e9) if full_ms else None
         line["stopped_fraction"] = st["stopped"] / max(1, st["children"])
         line["path_levels_per_child"] = st["path_levels"] / max(1, st["children"])
-        # the crossover kernels are the HBM-bound part of a generation (their bytes are exact)
-        line["roofline"] = {"bound": "hbm", "achieved": xo_gbs, "peak": hbm, "unit": "GB/s",
-                            "frac": (xo_gbs / hbm) if (xo_gbs and hbm) else None, "traffic": None,
-                            "kernel": "crossover phase (gather, copy, in-place move, fragment write)",
-                            "peak_note": "MEASURED_PEAKS.json hbm_gbs (copy, read+write), of measured",
-                            "timing": "CUDA events around the phase inside the timed region"
-                                      + (" (event-record nodes of the graph, mean over the last replay)"
-                                         if chunk else "")}
+        timing = ("CUDA events around the phase inside the timed region"
+                  + (" (event-record nodes of the graph, mean over the last replay)" if chunk else ""))
+        # the dominant kernel of a generation is the walk: interpreted node-cases against the FP32 lane rate
+        walk_ms = phases["walk"]
+        walk_ops = st["cum_actual_ops"] / max(1, st["cum_calls"])
+        walk_t = walk_ops / (walk_ms * 1e-3) / 1e12 if walk_ms > 0 else None
+        per_child = profile_figure("k_walk_generation_200x1e6.md", "traffic_bytes_per_child")
+        line["roofline"] = {"bound": "alu", "achieved": walk_t, "peak": alu_peak, "unit": "TFLOP/s",
+                            "frac": (walk_t / alu_peak) if walk_t else None,
+                            "traffic": per_child * (len(w["off"]) - 1) if per_child else None,
+                            "kernel": "k_walk (incremental evaluation with FDP; critical-path bound)",
+                            "peak_note": f"{nsm} SMs x 128 FP32 lanes x {sm_max:.0f} MHz; one node x case = one lane op",
+                            "timing": timing}
+        # the HBM-bound part: the crossover kernels (their bytes are exact)
+        ratio = profile_figure("crossover_dram_traffic_100x1e6.md", "traffic_per_algorithmic_byte")
+        line["roofline_crossover"] = {"bound": "hbm", "achieved": xo_gbs, "peak": hbm, "unit": "GB/s",
+                                      "frac": (xo_gbs / hbm) if (xo_gbs and hbm) else None,
+                                      "traffic": ratio * xo_bytes if ratio else None,
+                                      "kernel": "crossover phase (gather, copy, in-place move, fragment write)",
+                                      "peak_note": "MEASURED_PEAKS.json hbm_gbs (copy, read+write), of measured",
+                                      "timing": timing}
     else:
         t_items = phases["items"]
         achieved = st["interp_ops"] / (t_items * 1e-3) / 1e12 if t_items > 0 else None
+        per_node = profile_figure("k_eval_items_full_eval_100x1e6.md", "traffic_bytes_per_node")
         line["roofline"] = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
-                            "frac": (achieved / alu_peak) if achieved else None, "traffic": None,
+                            "frac": (achieved / alu_peak) if achieved else None,
+                            "traffic": per_node * int(w["off"][-1]) if per_node else None,
                             "kernel": "k_eval_items (subtree interpreter)",
                             "peak_note": f"{nsm} SMs x 128 FP32 lanes x {sm_max:.0f} MHz; one node x case = one lane op"}
     line["gpu_launches"] = st["launches"] * n_calls

@@ -247,6 +247,7 @@ int gp_graph_launch(gp_pop* pop);
 typedef struct {
     uint32_t cases_per_lane;    /* K: test cases per lane, i.e. 32 x K cases per warp task */
     uint32_t cache_threshold;   /* T: subtree size from which values are cached (the subtree split) */
+    uint32_t walk_team;         /* warps per child in the incremental walk */
     int32_t  status;            /* GP_OK, or the error that ruled the candidate out */
     uint32_t identical;         /* 1 when its fitness equals the first valid candidate's, bit for bit */
     float    ms_full;           /* one gp_eval_full, device milliseconds */
@@ -254,23 +255,23 @@ typedef struct {
 } gp_tune_result;
 
 /*
- * Autotune the work splits for a population: for every pair of
- * ks[0..n_k) x ts[0..n_t) (cases_per_lane x cache_threshold) build the
- * population described by base and the host data (same rules as
- * gp_pop_create), time one gp_eval_full and, when generations > 0 (even),
- * one replay of a captured graph of that many generations (after one
- * warm-up replay), and check that its fitness matches the first candidate's
- * bit for bit.  results[a * n_t + b] receives candidate (ks[a], ts[b]);
- * *best = base with the fastest valid candidate's two fields (fastest per
- * generation when generations > 0, else fastest full evaluation).  One
- * candidate's population exists at a time.  Synchronising.  Returns
- * GP_ENOMEM when no candidate could run.  The paper has no counterpart:
- * its CPU interpreter has one fixed layout.
+ * Autotune the work splits for a population: for every triple of
+ * ks[0..n_k) x ts[0..n_t) x teams[0..n_team) (cases_per_lane x
+ * cache_threshold x walk_team) build the population described by base and
+ * the host data (same rules as gp_pop_create), time one gp_eval_full and,
+ * when generations > 0 (even), one replay of a captured graph of that many
+ * generations (after one warm-up replay), and check that its fitness matches
+ * the first candidate's bit for bit.  results[(a * n_t + b) * n_team + w]
+ * receives candidate (ks[a], ts[b], teams[w]); *best = base with the fastest
+ * valid candidate's three fields (fastest per generation when generations >
+ * 0, else fastest full evaluation).  One candidate's population exists at a
+ * time.  Synchronising.  Returns GP_ENOMEM when no candidate could run.
+ * The paper has no counterpart: its CPU interpreter has one fixed layout.
  */
 int gp_autotune(const gp_config* base, const float* x, const float* targets, const float* consts,
                 const uint8_t* ops, const uint64_t* offsets, const uint32_t* ks, uint32_t n_k,
-                const uint32_t* ts, uint32_t n_t, uint32_t generations, void* stream,
-                gp_tune_result* results, gp_config* best);
+                const uint32_t* ts, uint32_t n_t, const uint32_t* teams, uint32_t n_team,
+                uint32_t generations, void* stream, gp_tune_result* results, gp_config* best);
 
 /* The autotuner's choice rule on its own: index of the fastest candidate
  * with status GP_OK and identical = 1 (ties: the earlier), or -1. */

@@ -54,7 +54,7 @@ class GpStats(ctypes.Structure):
 
 class GpTuneResult(ctypes.Structure):
     _fields_ = [("cases_per_lane", ctypes.c_uint32), ("cache_threshold", ctypes.c_uint32),
-                ("status", ctypes.c_int32), ("identical", ctypes.c_uint32),
+                ("walk_team", ctypes.c_uint32), ("status", ctypes.c_int32), ("identical", ctypes.c_uint32),
                 ("ms_full", ctypes.c_float), ("ms_generation", ctypes.c_float)]
 
     def as_dict(self) -> dict:
@@ -105,7 +105,7 @@ def load() -> ctypes.CDLL:
         "gp_set_graph_mode": (i32, [vp, i32, u64]),
         "gp_graph_capture": (i32, [vp, u32, u32]),
         "gp_graph_launch": (i32, [vp]),
-        "gp_autotune": (i32, [ctypes.POINTER(GpConfig), vp, vp, vp, vp, vp, vp, u32, vp, u32, u32, vp,
+        "gp_autotune": (i32, [ctypes.POINTER(GpConfig), vp, vp, vp, vp, vp, vp, u32, vp, u32, vp, u32, u32, vp,
                               ctypes.POINTER(GpTuneResult), ctypes.POINTER(GpConfig)]),
         "gp_autotune_pick": (i32, [ctypes.POINTER(GpTuneResult), u32, u32]),
     }
@@ -292,9 +292,10 @@ def gp_graph_launch(h):
     _check(load().gp_graph_launch(h), h)
 
 
-def gp_autotune(cfg: GpConfig, x, targets, consts, ops, offsets, ks, ts, generations: int, stream=None):
-    """Time every (cases_per_lane, cache_threshold) pair of ks x ts on this
-    population; returns (best GpConfig, list of GpTuneResult dicts)."""
+def gp_autotune(cfg: GpConfig, x, targets, consts, ops, offsets, ks, ts, teams, generations: int, stream=None):
+    """Time every (cases_per_lane, cache_threshold, walk_team) triple of
+    ks x ts x teams on this population; returns (best GpConfig, list of
+    GpTuneResult dicts)."""
     lib = load()
     x = np.ascontiguousarray(x, np.float32)
     targets = np.ascontiguousarray(targets, np.float32)
@@ -303,15 +304,16 @@ def gp_autotune(cfg: GpConfig, x, targets, consts, ops, offsets, ks, ts, generat
     offsets = np.ascontiguousarray(offsets, np.uint64)
     ks = np.ascontiguousarray(ks, np.uint32)
     ts = np.ascontiguousarray(ts, np.uint32)
+    teams = np.ascontiguousarray(teams, np.uint32)
     if stream is None:
         stream = _default_stream()
     elif hasattr(stream, "cuda_stream"):
         stream = stream.cuda_stream
-    res = (GpTuneResult * (len(ks) * len(ts)))()
+    res = (GpTuneResult * (len(ks) * len(ts) * len(teams)))()
     best = GpConfig()
     _check(lib.gp_autotune(ctypes.byref(cfg), _ptr(x), _ptr(targets), _ptr(consts), _ptr(ops), _ptr(offsets),
-                           _ptr(ks), len(ks), _ptr(ts), len(ts), generations, ctypes.c_void_p(stream),
-                           res, ctypes.byref(best)))
+                           _ptr(ks), len(ks), _ptr(ts), len(ts), _ptr(teams), len(teams), generations,
+                           ctypes.c_void_p(stream), res, ctypes.byref(best)))
     return best, [r.as_dict() for r in res]
 
 
@@ -324,11 +326,12 @@ def gp_autotune_pick(results: list[dict], generations: int) -> int:
     return load().gp_autotune_pick(arr, len(results), generations)
 
 
-def autotune(x, t, consts, ops, off, *, max_nodes: int, ks=(1, 2, 4), ts=(64, 256, 1024),
+def autotune(x, t, consts, ops, off, *, max_nodes: int, ks=(1, 2, 4), ts=(64, 256, 1024), teams=(0,),
              generations: int = 2, boolean: bool = False, tournament: int = 7, packing: int = GP_PACK_STATIC,
              cache_budget_bytes: int = 0, seed: int = 0, stream=None):
-    """Autotune the case and subtree splits for a population; returns
-    (keyword arguments for Population with the chosen split, result table)."""
+    """Autotune the case, subtree and walk-team splits for a population;
+    returns (keyword arguments for Population with the chosen split, result
+    table).  A team of 0 means the automatic choice."""
     off = np.asarray(off, np.uint64)
     C = 64 if boolean else len(x)
     if boolean:
@@ -338,8 +341,9 @@ def autotune(x, t, consts, ops, off, *, max_nodes: int, ks=(1, 2, 4), ts=(64, 25
                    funcset=GP_BOOL_MUX6 if boolean else GP_FP32_ARITH, cache_threshold=1024,
                    tournament=tournament, packing=packing, cases_per_lane=0,
                    cache_budget_bytes=cache_budget_bytes, seed=seed & (2**64 - 1))
-    best, table = gp_autotune(cfg, x, t, consts, ops, off, ks, ts, generations, stream)
-    return {"cases_per_lane": best.cases_per_lane, "cache_threshold": best.cache_threshold}, table
+    best, table = gp_autotune(cfg, x, t, consts, ops, off, ks, ts, teams, generations, stream)
+    return ({"cases_per_lane": best.cases_per_lane, "cache_threshold": best.cache_threshold,
+             "walk_team": best.walk_team}, table)
 
 
 def gp_set_profiling(h, on: bool):

@@ -410,7 +410,10 @@ int run_structure(gp_pop* pop) {
         CK(cudaStreamSynchronize(pop->stream));
         if (*pop->e_total_h > d.Ecap) {
             uint64_t want = (uint64_t)*pop->e_total_h + *pop->e_total_h / 4 + 64;
-            if (want > pop->slot_limit) want = pop->slot_limit;
+            const uint64_t room = pop->slot_limit > pop->gb.pvcap ? pop->slot_limit - pop->gb.pvcap : 0;
+            if (want > room) want = room;
+            if (want < *pop->e_total_h)
+                return fail(pop, GP_ENOMEM, "cache of %u entries exceeds the cache budget", *pop->e_total_h);
             int r = grow_cache(pop, (uint32_t)want);
             if (r) return r;
         }
@@ -753,7 +756,11 @@ int gp_set_graph_mode(gp_pop* pop, int on, uint64_t reserve_entries) {
     uint32_t cur_total = 0;
     CK(cudaMemcpy(&cur_total, pop->d.e_off + pop->d.P, sizeof cur_total, cudaMemcpyDeviceToHost));
     uint64_t want = reserve_entries ? reserve_entries : 2ull * cur_total + 64ull * pop->d.P;
-    if (want > pop->slot_limit) want = pop->slot_limit;
+    // the pool holds the entries' values plus the walk's new ones
+    const uint64_t room = pop->slot_limit > pop->gb.pvcap ? pop->slot_limit - pop->gb.pvcap : 0;
+    if (want > room) want = room;
+    if (!reserve_entries && want < cur_total)
+        return fail(pop, GP_ENOMEM, "the cache budget cannot hold the current cache");
     // an explicit reservation sets both sets to exactly that size; the
     // default only grows them
     for (int k = 0; k < 2; ++k) {
@@ -1194,7 +1201,10 @@ int gen_incremental(gp_pop* pop) {
         CK(cudaStreamSynchronize(pop->stream));
         if (*pop->e_total_h > d.Ecap) {
             uint64_t want = (uint64_t)*pop->e_total_h + *pop->e_total_h / 4 + 64;
-            if (want > pop->slot_limit) want = pop->slot_limit;
+            const uint64_t room = pop->slot_limit > pop->gb.pvcap ? pop->slot_limit - pop->gb.pvcap : 0;
+            if (want > room) want = room;
+            if (want < *pop->e_total_h)
+                return fail(pop, GP_ENOMEM, "cache of %u entries exceeds the cache budget", *pop->e_total_h);
             int r = grow_cache(pop, (uint32_t)want);
             if (r) return r;
             k_merge_offsets<<<1, 1024, 0, pop->stream>>>(d, g);

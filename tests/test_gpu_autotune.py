@@ -18,15 +18,16 @@ def test_autotune_uneven_population(boolean):
     w = synth.workload(3, n_trees=256, target=30_000, boolean=boolean)
     ks = (1,) if boolean else (1, 2, 4)
     ts = (32, 256, 1024)
+    teams = (1, 4)
     best, table = gp.autotune(w["x"], w["t"], w["consts"], w["ops"], w["off"], max_nodes=60_000,
-                              ks=ks, ts=ts, generations=2, boolean=boolean, seed=9)
-    assert len(table) == len(ks) * len(ts)
+                              ks=ks, ts=ts, teams=teams, generations=2, boolean=boolean, seed=9)
+    assert len(table) == len(ks) * len(ts) * len(teams)
     assert all(r["status"] == 0 for r in table), table
     assert all(r["identical"] == 1 for r in table), table
     assert all(r["ms_full"] > 0 and r["ms_generation"] > 0 for r in table)
     j = int(np.argmin([r["ms_generation"] for r in table]))
-    assert (best["cases_per_lane"], best["cache_threshold"]) == (table[j]["cases_per_lane"],
-                                                                 table[j]["cache_threshold"])
+    assert (best["cases_per_lane"], best["cache_threshold"], best["walk_team"]) == (
+        table[j]["cases_per_lane"], table[j]["cache_threshold"], table[j]["walk_team"])
     # the chosen split runs the same evolution as any other
     pop = gp.Population(None if boolean else w["x"], None if boolean else w["t"], w["consts"], w["ops"],
                         w["off"], max_nodes=60_000, boolean=boolean, seed=9, **best)
