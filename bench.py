@@ -49,7 +49,9 @@ def parse():
                     help="timed steps (default 100 generations, 50 for uneven, 20 full evaluations)")
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="generation", choices=["generation", "full", "uneven"])
+    ap.add_argument("--workload", default="generation", choices=["generation", "full", "uneven", "packing"])
+    ap.add_argument("--walk-warps", type=int, default=128,
+                    help="packing workload: warps the walk may use (fewer teams than children)")
     ap.add_argument("--trees", type=int, default=None, help="default 500 (uneven: 4,096)")
     ap.add_argument("--target", type=int, default=1_000_000)
     ap.add_argument("--cases", type=int, default=48)
@@ -66,7 +68,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     a = ap.parse_args()
     if a.steps is None:
-        a.steps = {"generation": 100, "uneven": 50, "full": 20}[a.workload]
+        a.steps = {"generation": 100, "uneven": 50, "full": 20, "packing": 1000}[a.workload]
     if a.trees is None:
         a.trees = 4096 if a.workload == "uneven" else 500
     return a
@@ -319,10 +321,70 @@ def graph_chunk(k: int) -> int:
     return 0
 
 
+def run_packing(args):
+    """Learned against static packing: the same generations (same seed) with
+    the MLP order and with the mother-size order, the walk limited to
+    --walk-warps warps so that children queue for teams; fitness must come
+    out bit-identical."""
+    import torch
+    import paper_2205_03251_gb300 as gp
+    gp.build()
+    gp.load()
+    torch.cuda.set_device(0)
+    w = make_workload(args, 0)
+    stream = torch.cuda.current_stream()
+    chunk = graph_chunk(args.steps) or 2
+    steps = (args.steps // chunk) * chunk
+    arms = {}
+    for name in ("mlp", "static"):
+        pop = gp.Population(w["x"], w["t"], w["consts"], w["ops"], w["off"], max_nodes=1 << 21,
+                            cache_threshold=args.threshold, seed=0x5EED, stream=stream, packing=PACKING[name],
+                            walk_warps=args.walk_warps)
+        pop.eval_full()
+        pop.set_graph_mode(True)
+        pop.eval_full()
+        gen = 0
+        for _ in range(args.warmup):
+            pop.crossover(gen)
+            pop.eval_incremental(want_stats=False)
+            gen += 1
+        pop.set_profiling(True)
+        pop.graph_capture(gen, chunk)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps // chunk):
+            pop.graph_launch()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        st = pop.stats()
+        arms[name] = {"ms": ms, "equivalent": st["cum_equivalent_ops"], "fitness": pop.fitness().copy(),
+                      "walk_ms": dict(zip(gp.PHASES, st["ms"]))["walk"], "pack": pop.pack_info()}
+        pop.close()
+    m, s_ = arms["mlp"], arms["static"]
+    value = m["equivalent"] / (m["ms"] * 1e-3) / 1e9
+    pred, meas, key, order, loss = m["pack"]
+    line = {"metric": METRIC, "value": value, "unit": "GPop/s", "n_gpus": 1, "steps": steps,
+            "warmup": args.warmup, "ms_per_step": m["ms"] / steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": dict(workload_config(args, w), packing="mlp vs static", walk_warps=args.walk_warps,
+                           execution=f"CUDA graphs of {chunk} generations, {steps // chunk} replays per arm"),
+            "static_value": s_["equivalent"] / (s_["ms"] * 1e-3) / 1e9,
+            "mlp_over_static": s_["ms"] / m["ms"],
+            "walk_ms_last_replay": {"mlp": m["walk_ms"], "static": s_["walk_ms"]},
+            "fitness_identical": bool(m["fitness"].tobytes() == s_["fitness"].tobytes()),
+            "mlp_loss_last": float(loss)}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.workload == "packing":
+        run_packing(args)
         return
     import torch
     import paper_2205_03251_gb300 as gp

@@ -80,7 +80,7 @@ typedef struct {
     uint32_t walk_warps;        /* 0 = as many as fit; else at most this many warps run the walk */
     uint32_t mlp_lr_micro;      /* Adam learning rate of the packing MLP in 1e-6 units (0 = 1000) */
     uint32_t walk_team;         /* warps per child in the incremental walk: 1, 2, 4, 8, or 0 = auto
-                                   (the largest team with which every child runs at once, else 1) */
+                                   (8 when every child gets a team at once, else 4) */
     uint32_t reserved;          /* must be 0 */
 } gp_config;
 
@@ -182,8 +182,10 @@ int gp_cache_value(const gp_pop* pop, uint32_t i, uint32_t j, void* host_out, si
 
 /* Per child of the last gp_eval_incremental: the level at which the walk
  * stopped (0 = at the crossover point; -1 = the root differed, fitness
- * recomputed) and the number of levels evaluated above the crossover
- * point.  Either pointer may be NULL; n <= pop_size.  Synchronising. */
+ * recomputed; -2 = a child smaller than the cache threshold, evaluated in
+ * one pass instead of walked -- same fitness bits) and the number of levels
+ * evaluated above the crossover point.  Either pointer may be NULL; n <=
+ * pop_size.  Synchronising. */
 int gp_walk_info(const gp_pop* pop, int32_t* stop_level, uint32_t* levels, uint32_t n);
 
 /*
@@ -260,8 +262,8 @@ typedef struct {
  * cache_threshold x walk_team) build the population described by base and
  * the host data (same rules as gp_pop_create), time one gp_eval_full and,
  * when generations > 0 (even), one replay of a captured graph of that many
- * generations (after one warm-up replay), and check that its fitness matches
- * the first candidate's bit for bit.  results[(a * n_t + b) * n_team + w]
+ * generations (after four warm-up replays), and check that its fitness
+ * matches the first candidate's bit for bit.  results[(a * n_t + b) * n_team + w]
  * receives candidate (ks[a], ts[b], teams[w]); *best = base with the fastest
  * valid candidate's three fields (fastest per generation when generations >
  * 0, else fastest full evaluation).  One candidate's population exists at a

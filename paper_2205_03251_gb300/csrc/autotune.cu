@@ -54,8 +54,9 @@ int run_candidate(const gp_config* cfg, const float* x, const float* targets, co
     res->ms_full = ms;
     if (!rc && generations) {
         rc = gp_graph_capture(pop, 0, generations);
-        // one replay to warm up, then the timed one: generations G .. 2G-1
-        if (!rc) rc = gp_graph_launch(pop);
+        // four replays to warm up (a new population changes fastest in its
+        // first generations), then the timed one: generations 4G .. 5G-1
+        for (int w = 0; w < 4 && !rc; ++w) rc = gp_graph_launch(pop);
         if (!rc) rc = gp_fitness(pop, fit.data(), cfg->pop_size);
         if (!rc) rc = timed_ms(stream, &ms, [&] { return gp_graph_launch(pop); });
         if (!rc) rc = gp_fitness(pop, fit.data(), cfg->pop_size);

@@ -869,6 +869,61 @@ __global__ void __launch_bounds__(256, 2) k_walk(DevPop d, GenBufs g, CacheView 
         const uint32_t fe0 = par.e_off[f], fe1 = par.e_off[f + 1];
         uint32_t npv = 0, nins_i = 0;
 
+        // ---- a child smaller than the threshold caches only its root: one
+        // pass over the whole child costs less than a walk of its levels (same
+        // values, bit for bit); its root value is recorded when it differs from
+        // the mother's (or is a new root made of a small donated subtree)
+        if (nk < T) {
+            for (uint32_t cb = warp; cb < ncb; cb += nw) {
+                load_cases<K>(d, cb, ic.xv);
+                float v[K];
+                eval_run<K, B>(ok_, 0, nk, stA, ic, v, d.status);
+                st_interp += nk;
+                store_blk<K>(nvs, cb, v);
+                if (c != 0) {
+                    load_vec<K>(par.slots, Cpad, par.e_slot[me0], v, cb);
+                    store_blk<K>(ovs, cb, v);
+                }
+            }
+            __syncthreads();
+            bool same = (c != 0);
+            if (same)
+                for (uint32_t j = tid; j < Cn; j += nthr)
+                    if (__float_as_uint(nvs[j]) != __float_as_uint(ovs[j])) same = false;
+            same = __syncthreads_and(same) != 0;
+            const bool rec = (c != 0) ? !same : (dd != 0);
+            uint32_t slot = 0;
+            if (rec) {
+                if (tid == 0) sc[1] = atomicAdd(&g.misc[M_PV], 1u);
+                __syncthreads();
+                slot = sc[1];
+                __syncthreads();
+                if (slot >= g.pvcap) { if (tid == 0) set_status(d.status, ST_PATH); continue; }
+                float* dst = g.pv_val + (size_t)slot * Cpad;
+                for (uint32_t j = tid; j < Cpad; j += nthr) dst[j] = nvs[j];
+            }
+            if (tid == 0) {
+                if (rec) {
+                    g.pv_rec[slot] = make_uint4(i, 0u, 0u, slot | (c == 0 ? 0x80000000u : 0u));
+                    g.pv_end[slot] = nk;
+                }
+                g.pv_cnt[i] = rec ? 1u : 0u;
+                g.nins[i] = (rec && c == 0) ? 1u : 0u;
+                g.stop[i] = -2;                 // evaluated in one pass, no walk
+                g.plen[i] = 0;
+                if (B) {
+                    d.fit[i] = (float)(__popc(__float_as_uint(nvs[0]) ^ mux_target_half(0)) +
+                                       __popc(__float_as_uint(nvs[1]) ^ mux_target_half(1)));
+                } else {
+                    float fsum = 0.0f;
+                    for (uint32_t cc = 0; cc < Cn; ++cc) fsum = __fadd_rn(fsum, fabsf(__fsub_rn(nvs[cc], d.t[cc])));
+                    d.fit[i] = fsum;
+                }
+            }
+            __syncthreads();                 // nvs and the shared words are reused by the next child
+            continue;
+        }
+
         // ---- level 0: donated subtree vs removed subtree
         int32_t ef = -1, em = -1;
         if (s >= T || dd == 0) {

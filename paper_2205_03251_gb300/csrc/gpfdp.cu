@@ -234,9 +234,10 @@ int setup_items_kernel(gp_pop* pop) {
 }
 
 // Team size of the incremental walk (warps per child) and its launch
-// shape.  Auto: the largest team (8, 4, 2) with which every child of the
-// population gets its own team at once, else one warp per child (more
-// children than teams: throughput first).
+// shape.  Auto: a team of 8 when every child of the population gets its own
+// team at once, else 4 (one building and combining warp and three sibling
+// evaluators: enough resident warps per SM to hide the interpreter's
+// latency when children queue for teams).
 template <int K, bool B = false>
 int setup_walk_kernel(gp_pop* pop, uint32_t team) {
     const uint32_t ovf = pop->d.ovf_warps;      // the walk shares the interpreter's per-warp overflow stacks
@@ -255,12 +256,9 @@ int setup_walk_kernel(gp_pop* pop, uint32_t team) {
     int grid = 0;
     size_t smem = 0;
     if (!nw) {
-        nw = 1;
-        for (uint32_t cand : {8u, 4u, 2u}) {
-            int r = shape(cand, grid, smem);
-            if (r) return r;
-            if ((uint32_t)grid >= pop->d.P) { nw = cand; break; }
-        }
+        int r = shape(8, grid, smem);
+        if (r) return r;
+        nw = ((uint32_t)grid >= pop->d.P) ? 8u : 4u;
     }
     int r = shape(nw, grid, smem);
     if (r) return r;

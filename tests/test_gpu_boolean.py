@@ -93,8 +93,11 @@ def test_boolean_generations(gp, T):
         stop, _ = pop.walk_info()
         for i in range(100):
             m = int(pl["mother"][i])
-            ostop, _ = oracle.fdp_walk_bool(cur_ops[int(cur_off[m]):int(cur_off[m + 1])],
-                                            kops[int(koff[i]):int(koff[i + 1])], int(pl["c"][i]))
+            kid = kops[int(koff[i]):int(koff[i + 1])]
+            if stop[i] == -2:                 # one-pass evaluation below the threshold
+                assert len(kid) < T
+                continue
+            ostop, _ = oracle.fdp_walk_bool(cur_ops[int(cur_off[m]):int(cur_off[m + 1])], kid, int(pl["c"][i]))
             assert stop[i] == ostop
         fit = gfit
         cur_ops, cur_off = kops, koff

@@ -77,6 +77,10 @@ def run_generations(gp, w, *, T, gens, max_nodes, seed=1234, cache_check=16, sto
                 m = int(pl["mother"][i])
                 mom = cur_ops[int(cur_off[m]):int(cur_off[m + 1])]
                 kid = kops[int(koff[i]):int(koff[i + 1])]
+                if stop[i] == -2:
+                    # below the threshold the child is evaluated in one pass, not walked
+                    assert len(kid) < T
+                    continue
                 ostop, depth = oracle.fdp_walk(mom, kid, int(pl["c"][i]), k, x)
                 assert stop[i] == ostop, f"gen {g}: child {i} stops at {stop[i]}, oracle {ostop}"
         # children's cache: positions and sampled values
