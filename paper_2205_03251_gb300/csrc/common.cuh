@@ -7,6 +7,7 @@
 #define GP_NCONST 251        // ephemeral constant table
 #define GP_WARPS 8           // warps per CTA in the persistent kernels
 #define FREE_TILE 4096       // slots per CTA in the free-slot scan
+#define SLOT_NEW 0xFFFFFFFFu // cache entry whose value slot is assigned later in the generation
 #define FULL 0xFFFFFFFFu
 
 // status word bits (device side)

@@ -7,7 +7,7 @@
 #include "mlp.cuh"
 
 #define HALO_MAX 64            // largest |size change| moved in place (halo bytes per block)
-#define SHIFT_BS 4096          // bytes of tail per block of the in-place move
+#define SHIFT_BS 16384         // bytes of tail per block of the in-place move
 #define COPY_CH 32768          // bytes of a copied child per work unit
 #define PV_PER_CHILD 256       // walk records (new path values) reserved per child on average
 #define WALK_MAXLVL 520        // small-ancestor levels held in shared memory (T <= 1024)
@@ -68,6 +68,7 @@ struct GenBufs {
     uint32_t gen;
     const uint32_t* gen_add;         // device word added to gen (generations replayed by a captured graph)
     uint32_t* stamp;                 // [1] generation stamp of the slot pool's live marks
+    uint32_t* rec_entry;             // [pvcap] child cache entry that takes each walk record's value, or ~0
     bool evaluated;
 };
 
@@ -435,24 +436,27 @@ __device__ __forceinline__ void shift_block_geom(const DevPop& d, const GenBufs&
     delta = (int32_t)g.ssz[i] - (int32_t)g.rsz[i];
 }
 
+// One thread per possible halo byte (HALO_MAX per block).
 __global__ void k_save_halo(DevPop d, GenBufs g) {
     if (halted(d)) return;
     const uint32_t nb = g.shift_off[d.P];
     if (nb > g.shift_cap) return;
-    for (uint32_t b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += gridDim.x * blockDim.x) {
+    for (uint32_t u = blockIdx.x * blockDim.x + threadIdx.x; u < nb * HALO_MAX; u += gridDim.x * blockDim.x) {
+        const uint32_t b = u / HALO_MAX, t = u % HALO_MAX;
         uint32_t i, j, nblk, src0, len;
         int32_t delta;
         shift_block_geom(d, g, b, i, j, nblk, src0, len, delta);
-        const uint8_t* buf = d.arena + (size_t)d.buf[i] * d.cap;
-        uint8_t* h = g.halo + (size_t)b * HALO_MAX;
         const uint32_t ad = (uint32_t)(delta > 0 ? delta : -delta);
         const uint32_t k = min(ad, len);
-        if (delta > 0 && j > 0) for (uint32_t t = 0; t < k; ++t) h[t] = buf[src0 + t];
-        if (delta < 0 && j + 1 < nblk) for (uint32_t t = 0; t < k; ++t) h[t] = buf[src0 + len - k + t];
+        if (t >= k) continue;
+        const uint8_t* buf = d.arena + (size_t)d.buf[i] * d.cap;
+        uint8_t* h = g.halo + (size_t)b * HALO_MAX;
+        if (delta > 0 && j > 0) h[t] = buf[src0 + t];
+        if (delta < 0 && j + 1 < nblk) h[t] = buf[src0 + len - k + t];
     }
 }
 
-__global__ void __launch_bounds__(256) k_shift(DevPop d, GenBufs g) {
+__global__ void __launch_bounds__(512) k_shift(DevPop d, GenBufs g) {
     if (halted(d)) return;
     // the block's source bytes from its 16-byte-aligned start, plus slack for the shifted reads
     __shared__ __align__(16) uint8_t sb[SHIFT_BS + 48];
@@ -905,6 +909,7 @@ __global__ void __launch_bounds__(256, 2) k_walk(DevPop d, GenBufs g, CacheView 
             if (tid == 0) {
                 if (rec) {
                     g.pv_rec[slot] = make_uint4(i, 0u, 0u, slot | (c == 0 ? 0x80000000u : 0u));
+                    g.rec_entry[slot] = 0xFFFFFFFFu;
                     g.pv_end[slot] = nk;
                 }
                 g.pv_cnt[i] = rec ? 1u : 0u;
@@ -967,7 +972,11 @@ __global__ void __launch_bounds__(256, 2) k_walk(DevPop d, GenBufs g, CacheView 
         if (root_rec) {
             float* dst = g.pv_val + (size_t)rslot * Cpad;
             for (uint32_t j = tid; j < Cpad; j += nthr) dst[j] = nvs[j];
-            if (tid == 0) { g.pv_rec[rslot] = make_uint4(i, npv, 0u, rslot | 0x80000000u); g.pv_end[rslot] = s; }
+            if (tid == 0) {
+                g.pv_rec[rslot] = make_uint4(i, npv, 0u, rslot | 0x80000000u);
+                g.pv_end[rslot] = s;
+                g.rec_entry[rslot] = 0xFFFFFFFFu;
+            }
             ++npv;
             ++nins_i;
         }
@@ -1134,6 +1143,7 @@ __global__ void __launch_bounds__(256, 2) k_walk(DevPop d, GenBufs g, CacheView 
                     for (uint32_t j = lane; j < Cpad; j += 32) dst[j] = src[j];
                     if (lane == 0) {
                         g.pv_rec[rs] = make_uint4(i, npv, D.p, rs | (D.pent < 0 ? 0x80000000u : 0u));
+                        g.rec_entry[rs] = 0xFFFFFFFFu;
                         g.pv_end[rs] = D.pend;
                     }
                     ++npv;
@@ -1147,7 +1157,10 @@ __global__ void __launch_bounds__(256, 2) k_walk(DevPop d, GenBufs g, CacheView 
             }
             // reserved record slots left unused are marked as holes
             for (uint32_t k = lane; k < rleft; k += 32)
-                if (rbase + k < g.pvcap) g.pv_rec[rbase + k] = make_uint4(0xFFFFFFFFu, 0u, 0u, 0u);
+                if (rbase + k < g.pvcap) {
+                    g.pv_rec[rbase + k] = make_uint4(0xFFFFFFFFu, 0u, 0u, 0u);
+                    g.rec_entry[rbase + k] = 0xFFFFFFFFu;
+                }
             (void)fail;
             __threadfence_block();
             if (lane == 0) sc[8] = 1u;                      // evaluators stop
@@ -1347,7 +1360,6 @@ __global__ void __launch_bounds__(1024) k_merge_offsets(DevPop d, GenBufs g) {
 // A child's cache entry.  src is the mother's (or father's) value slot, which
 // the child shares, or (bit 31 set) a walk record whose new value gets a
 // free slot of the pool later (k_copy_values).
-#define SLOT_NEW 0xFFFFFFFFu
 __device__ __forceinline__ void put_entry(const DevPop& d, GenBufs& g, uint32_t x, uint32_t pos, uint32_t end,
                                           uint32_t tree, uint32_t src) {
     d.e_pos[x] = pos;
@@ -1358,6 +1370,7 @@ __device__ __forceinline__ void put_entry(const DevPop& d, GenBufs& g, uint32_t 
     d.e_par[x] = -1;
     d.e_slot[x] = (src & 0x80000000u) ? SLOT_NEW : src;
     g.src[x] = src;
+    if (src & 0x80000000u) g.rec_entry[src & 0x7FFFFFFFu] = x;
 }
 
 // walk record of child i at position pos (records are sorted by decreasing position), or -1
@@ -1590,8 +1603,9 @@ __global__ void __launch_bounds__(1024) k_free_emit(DevPop d, GenBufs g) {
     }
 }
 
-// New values of the children's cache (walk records): each takes the free
-// slot of its record's rank; one warp per 32 entries, lanes over cases.
+// New values of the children's cache (walk records): each record that
+// became an entry takes the free slot of its rank; one warp per record,
+// lanes over cases.
 __global__ void k_copy_values(DevPop d, GenBufs g, CacheView par) {
     if (halted(d)) return;
     const uint32_t ne = d.e_off[d.P];
@@ -1600,23 +1614,17 @@ __global__ void k_copy_values(DevPop d, GenBufs g, CacheView par) {
     const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
     const uint32_t nt = (d.Scap + FREE_TILE - 1) / FREE_TILE;
-    const uint32_t need = min(min(g.misc[M_PV], g.pvcap), d.ftile[nt]);
-    for (uint32_t x0 = 32 * gw; x0 < ne; x0 += 32 * nw) {
-        const uint32_t x = x0 + lane;
-        const bool isnew = x < ne && d.e_slot[x] == SLOT_NEW;
-        uint32_t nb = __ballot_sync(FULL, isnew);
-        while (nb) {
-            const int l = __ffs(nb) - 1;
-            nb &= nb - 1;
-            const uint32_t xx = x0 + l;
-            const uint32_t r = g.src[xx] & 0x7FFFFFFFu;
-            if (r >= need) { if (lane == 0) set_status(d.status, ST_SLOTS); continue; }
-            const uint32_t sl = d.freeslot[r];
-            const float* sp = g.pv_val + (size_t)r * d.Cpad;
-            float* dp = d.slots + (size_t)sl * d.Cpad;
-            for (uint32_t k = lane; k < d.Cpad; k += 32) dp[k] = __ldcg(sp + k);
-            if (lane == 0) d.e_slot[xx] = sl;
-        }
+    const uint32_t nrec = min(g.misc[M_PV], g.pvcap);
+    const uint32_t avail = min(nrec, d.ftile[nt]);
+    for (uint32_t r = gw; r < nrec; r += nw) {
+        const uint32_t x = g.rec_entry[r];
+        if (x >= ne) continue;                           // not an entry of the children's cache
+        if (r >= avail) { if (lane == 0) set_status(d.status, ST_SLOTS); continue; }
+        const uint32_t sl = d.freeslot[r];
+        const float* sp = g.pv_val + (size_t)r * d.Cpad;
+        float* dp = d.slots + (size_t)sl * d.Cpad;
+        for (uint32_t k = lane; k < d.Cpad; k += 32) dp[k] = __ldcg(sp + k);
+        if (lane == 0) d.e_slot[x] = sl;
     }
     (void)par;
 }

@@ -622,6 +622,7 @@ int gp_pop_create(const gp_config* cfg_in, const float* x, const float* targets,
         DA2(g.stop, P); DA2(g.plen, P);
         DA2(g.pv_rec, g.pvcap); DA2(g.pv_cnt, P); DA2(g.pv_off, P + 1); DA2(g.pv_sorted, g.pvcap);
         DA2(g.pv_end, g.pvcap); DA2(g.pv_val, (size_t)g.pvcap * d.Cpad);
+        DA2(g.rec_entry, g.pvcap);
         DA2(g.walkA, P); DA2(g.nins, P); DA2(g.mb, P); DA2(g.mcnt, P + 1);
         DA2(g.order, P); DA2(g.gstat, NGSTAT);
         std::vector<uint32_t> fb(P);
@@ -1134,7 +1135,6 @@ int gen_crossover(gp_pop* pop, uint32_t generation) {
     const CacheView par = view_of(pop, pop->sets[pop->cur]);
     pop->cur ^= 1;
     bind_set(pop);
-    const int gt = pop->grid_threads;
     phase_begin(pop, PH_XO);
     CK(cudaMemsetAsync(g.lastidx, 0xFF, sizeof(int32_t) * d.P, pop->stream));
     CK(cudaMemsetAsync(g.misc, 0, sizeof(uint32_t) * NMISC, pop->stream));
@@ -1143,8 +1143,8 @@ int gen_crossover(gp_pop* pop, uint32_t generation) {
     k_assign<<<1, 1024, 0, pop->stream>>>(d, g);
     k_gather<<<pop->nsm * 4, 256, 0, pop->stream>>>(d, g);
     k_copy_children<<<pop->nsm * 8, 256, 0, pop->stream>>>(d, g);
-    k_save_halo<<<gt, 256, 0, pop->stream>>>(d, g);
-    k_shift<<<pop->nsm * 8, 256, 0, pop->stream>>>(d, g);
+    k_save_halo<<<pop->nsm * 8, 256, 0, pop->stream>>>(d, g);
+    k_shift<<<pop->nsm * 4, 512, 0, pop->stream>>>(d, g);
     k_write_frags<<<pop->nsm * 4, 256, 0, pop->stream>>>(d, g);
     phase_end(pop, PH_XO);
     CK(cudaGetLastError());

@@ -455,6 +455,8 @@ __global__ void k_entry_links(DevPop d, StructBufs sb) {
     const uint32_t ne = d.e_off[d.P];
     if (ne > d.Ecap) return;
     for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < ne; e += gridDim.x * blockDim.x) {
+        // every entry must hold a value slot by now; never leave one unassigned
+        if (d.e_slot[e] == SLOT_NEW) { d.e_slot[e] = 0; set_error(d, ST_STRUCT, 8, d.e_tree[e], d.e_pos[e], 0); }
         int32_t p = d.e_par[e];
         if (p < 0) continue;
         if (d.e_pos[e] == d.e_pos[p] + 1) d.e_c0[p] = (int32_t)e;
