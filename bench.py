@@ -176,11 +176,13 @@ def workload_config(args, w):
             "l2": "opcode arena %.2f GB > 129 MB L2; no flush" % (int(w["off"][-1]) / 1e9)}
 
 
-def cpu_baseline(w, seconds: float):
+def cpu_baseline(w, seconds: float, gpu_fit=None):
     """Time the CPU oracle as it stands on a bounded sample of the workload:
     first on one thread, then with one thread per host core pulling whole
     trees from a shared queue (the paper's threading of independent
-    evaluations).  The oracle's C calls release the GIL."""
+    evaluations).  The oracle's C calls release the GIL.  With the GPU's
+    fitness of the initial trees, the single-thread sample is also evaluated
+    in FP64 and the largest relative difference reported."""
     import oracle
     oracle.build()
     ops, off = w["ops"], w["off"]
@@ -226,11 +228,18 @@ def cpu_baseline(w, seconds: float):
     cores = os.cpu_count() or 1
     all_v, all_n, all_nodes, all_dt = run(cores, 2 * seconds / 3)
     kind = "recursive Boolean oracle" if boolean else "recursive FP32 oracle"
-    return {"value": all_v, "unit": "GPop/s", "cores": cores, "kind": "oracle",
-            "sample": f"{all_n} trees ({all_nodes} nodes) x {C} cases in {all_dt:.1f} s, {kind}, one thread per "
-                      f"core taking whole trees from a shared queue",
-            "single_thread": {"value": one_v, "cores": 1,
-                              "sample": f"{one_n} trees ({one_nodes} nodes) x {C} cases in {one_dt:.1f} s"}}
+    out = {"value": all_v, "unit": "GPop/s", "cores": cores, "kind": "oracle",
+           "sample": f"{all_n} trees ({all_nodes} nodes) x {C} cases in {all_dt:.1f} s, {kind}, one thread per "
+                     f"core taking whole trees from a shared queue",
+           "single_thread": {"value": one_v, "cores": 1,
+                             "sample": f"{one_n} trees ({one_nodes} nodes) x {C} cases in {one_dt:.1f} s"}}
+    if gpu_fit is not None and one_n:
+        n = min(one_n, len(gpu_fit))
+        f64 = oracle.eval_pop_f64(ops[:int(off[n])], off[:n + 1], w["consts"], w["x"], w["t"])
+        rel, nonfinite = oracle.max_rel_diff(gpu_fit[:n], f64)
+        out["gpu_vs_fp64"] = {"trees": n, "max_rel_diff": rel, "nonfinite": nonfinite,
+                              "note": "GPU FP32 fitness of the initial trees against the FP64 oracle (reported, not gated)"}
+    return out
 
 
 def reference_units(w, lo: int = 1024, hi: int = 65536, want: int = 4096):
@@ -437,6 +446,7 @@ def main():
     # full evaluation (also the starting point of the generation loop)
     for _ in range(2):
         pop.eval_full()
+    fit0 = None if boolean else pop.fitness().copy()     # the initial trees' fitness, for the FP64 comparison
     full_ms, full_st = timed(pop.eval_full, 3) if generational else (None, None)
     if chunk:
         pop.set_graph_mode(True)         # pre-sized caches, no host syncs in the loop
@@ -586,7 +596,7 @@ def main():
     pop.close()
     if rank == 0:
         if not args.no_cpu and world == 1:
-            line["cpu_baseline"] = cpu_baseline(w, args.cpu_seconds)
+            line["cpu_baseline"] = cpu_baseline(w, args.cpu_seconds, fit0)
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

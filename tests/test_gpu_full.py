@@ -53,6 +53,10 @@ def _check_population(gp, w, T, K=0, check_cache=True, max_nodes=None):
     st = pop.stats()
     assert st["equivalent_ops"] == int(sizes.sum()) * len(w["x"])
     assert st["actual_ops"] == st["equivalent_ops"]
+    # the error bound of binary32 against binary64 arithmetic: reported, not gated
+    rel, nonfinite = oracle.max_rel_diff(fit, oracle.eval_pop_f64(ops, off, w["consts"], w["x"], w["t"]))
+    print(f"T={T} K={K}: max relative difference of the FP32 fitness from FP64: {rel:.3e} "
+          f"({nonfinite} non-finite)")
     if check_cache:
         for i in range(len(off) - 1):
             tree = ops[int(off[i]):int(off[i + 1])]

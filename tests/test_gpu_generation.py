@@ -217,3 +217,45 @@ def test_full_size_generation_sampled(gp):
         cur_off[1:] = np.cumsum(sizes)
         fit = gfit
     pop.close()
+
+
+def test_full_size_uneven_population_sampled(gp):
+    """The 4,096-tree population with log-uniform sizes in [1e1, 1e6]: full
+    evaluation of sampled trees (the largest included) and two generations
+    with sampled children against the oracle."""
+    import oracle
+    import synth
+    w = synth.workload(3)
+    ops, off, k, x, t = w["ops"], w["off"], w["consts"], w["x"], w["t"]
+    P = len(off) - 1
+    sizes = np.diff(off).astype(np.int64)
+    maxn = 2_004_096
+    pop = gp.Population(x, t, k, ops, off, max_nodes=maxn, cache_threshold=1024, seed=12)
+    pop.eval_full()
+    fit = pop.fitness()
+    rng = np.random.default_rng(3)
+    sample = list(rng.choice(P, 12, replace=False)) + [int(np.argmax(sizes)), int(np.argmin(sizes))]
+    for i in sample:
+        tree = ops[int(off[i]):int(off[i + 1])]
+        want = oracle.fitness_f32(oracle.eval_node_f32(tree, 0, k, x), t)
+        assert oracle.canon_nan(np.array([fit[i]]))[0] == oracle.canon_nan(np.array([want]))[0], i
+    cur_ops, cur_off = ops, off
+    for g in range(2):
+        pl = oracle.plan(cur_ops, cur_off, fit, T=7, seed=12, gen=g, max_nodes=maxn)
+        pop.crossover(g)
+        pop.eval_incremental()
+        gfit = pop.fitness()
+        for i in list(rng.choice(P, 10, replace=False)):
+            m, f = int(pl["mother"][i]), int(pl["father"][i])
+            mom = cur_ops[int(cur_off[m]):int(cur_off[m + 1])]
+            dad = cur_ops[int(cur_off[f]):int(cur_off[f + 1])]
+            kid = oracle.splice(mom, int(pl["c"][i]), int(pl["r"][i]), dad, int(pl["d"][i]), int(pl["s"][i]))
+            assert np.array_equal(pop.tree(i), kid)
+            want = oracle.fitness_f32(oracle.eval_node_f32(kid, 0, k, x), t)
+            assert oracle.canon_nan(np.array([gfit[i]]))[0] == oracle.canon_nan(np.array([want]))[0]
+        sz = np.array([len(pop.tree(i)) for i in range(P)])
+        cur_ops = np.concatenate([pop.tree(i) for i in range(P)])
+        cur_off = np.zeros(P + 1, np.uint64)
+        cur_off[1:] = np.cumsum(sz)
+        fit = gfit
+    pop.close()
