@@ -58,6 +58,10 @@ def parse():
     ap.add_argument("--boolean", action="store_true", help="uneven workload on the 6-multiplexer")
     ap.add_argument("--threshold", type=int, default=1024)
     ap.add_argument("--packing", default="mlp", choices=list(PACKING))
+    ap.add_argument("--lazy", dest="lazy", action="store_true", default=True,
+                    help="fitness-first order (default): build only the children selected as parents")
+    ap.add_argument("--eager", dest="lazy", action="store_false",
+                    help="build every child at crossover (in-place for a mother's last child)")
     ap.add_argument("--graph", dest="graph", action="store_true", default=True)
     ap.add_argument("--no-graph", dest="graph", action="store_false")
     ap.add_argument("--autotune", dest="autotune", action="store_true", default=True)
@@ -413,7 +417,7 @@ def main():
     boolean = bool(w.get("boolean"))
     maxn = w.get("max_nodes", 1 << 21)
     pop_kw = {"cache_threshold": args.threshold, "packing": PACKING[args.packing],
-              "cache_budget_bytes": args.cache_budget_gb << 30}
+              "cache_budget_bytes": args.cache_budget_gb << 30, "lazy": args.lazy}
     tune = None
     if args.workload == "uneven" and args.autotune:
         ks = (1,) if boolean else ((1, 2) if args.cases <= 64 else (2, 4))
@@ -504,13 +508,15 @@ def main():
     line["config"]["execution"] = (f"CUDA graph of {chunk} generations, {n_calls} replay(s) timed "
                                    f"after {args.warmup} eager warm-up generations" if chunk else "eager calls")
     line["config"]["packing"] = args.packing
+    line["config"]["children"] = ("fitness-first: only the children selected as parents are built"
+                                  if args.lazy else "every child built at crossover")
     if tune:
         line["config"]["cases_per_lane"] = pop_kw["cases_per_lane"]
         line["config"]["cache_threshold"] = pop_kw["cache_threshold"]
         line["config"]["walk_team"] = pop_kw["walk_team"]
         line["autotune"] = tune
     if generational:
-        xo_ms = phases["crossover"]
+        xo_ms = phases["crossover"] + phases.get("materialise", 0.0)
         xo_bytes = st["cum_crossover_bytes"] / max(1, st["cum_calls"])
         xo_gbs = xo_bytes / (xo_ms * 1e-3) / 1e9 if xo_ms > 0 else None
         line["crossover_gbs"] = xo_gbs

@@ -81,7 +81,11 @@ typedef struct {
     uint32_t mlp_lr_micro;      /* Adam learning rate of the packing MLP in 1e-6 units (0 = 1000) */
     uint32_t walk_team;         /* warps per child in the incremental walk: 1, 2, 4, 8, or 0 = auto
                                    (8 when every child gets a team at once, else 4) */
-    uint32_t reserved;          /* must be 0 */
+    uint32_t lazy_children;     /* 1 = fitness-first order (Sec. 6.3): the walk reads each child
+                                   through its parents, the next generation's plan is drawn
+                                   right after it, and only the children selected as parents
+                                   get a tree buffer and a cache (no in-place construction);
+                                   results are identical.  0 = build every child at crossover */
 } gp_config;
 
 /* Per-call statistics of the last evaluation (host copy). */
@@ -99,9 +103,10 @@ typedef struct {
     uint64_t cum_equivalent_ops;/* sums of the three counters above over those calls */
     uint64_t cum_actual_ops;
     uint64_t cum_crossover_bytes;
-    float    ms[8];             /* per-phase device milliseconds when profiling is on, mean over
+    float    ms[9];             /* per-phase device milliseconds when profiling is on, mean over
                                    the calls since profiling was (re)enabled (last 128 kept):
-                                   structure, items, skeleton, fitness, crossover, walk, cache, pack */
+                                   structure, items, skeleton, fitness, crossover, walk, cache, pack,
+                                   materialise (fitness-first order: next plan and the parents' copies) */
 } gp_stats;
 
 /*

@@ -34,7 +34,7 @@ class GpConfig(ctypes.Structure):
                 ("packing", ctypes.c_uint32), ("cases_per_lane", ctypes.c_uint32),
                 ("cache_budget_bytes", ctypes.c_uint64), ("seed", ctypes.c_uint64),
                 ("walk_warps", ctypes.c_uint32), ("mlp_lr_micro", ctypes.c_uint32),
-                ("walk_team", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+                ("walk_team", ctypes.c_uint32), ("lazy_children", ctypes.c_uint32)]
 
 
 class GpStats(ctypes.Structure):
@@ -44,7 +44,7 @@ class GpStats(ctypes.Structure):
                 ("stopped", ctypes.c_uint32), ("children", ctypes.c_uint32),
                 ("launches", ctypes.c_uint32), ("cum_calls", ctypes.c_uint32),
                 ("cum_equivalent_ops", ctypes.c_uint64), ("cum_actual_ops", ctypes.c_uint64),
-                ("cum_crossover_bytes", ctypes.c_uint64), ("ms", ctypes.c_float * 8)]
+                ("cum_crossover_bytes", ctypes.c_uint64), ("ms", ctypes.c_float * 9)]
 
     def as_dict(self) -> dict:
         d = {k: getattr(self, k) for k, _ in self._fields_ if k != "ms"}
@@ -61,7 +61,7 @@ class GpTuneResult(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
-PHASES = ("structure", "items", "skeleton", "fitness", "crossover", "walk", "cache", "pack")
+PHASES = ("structure", "items", "skeleton", "fitness", "crossover", "walk", "cache", "pack", "materialise")
 
 _lib = None
 
@@ -359,7 +359,7 @@ class Population:
     def __init__(self, x, t, consts, ops, off, *, max_nodes: int, cache_threshold: int = 1024,
                  boolean: bool = False, tournament: int = 7, packing: int = GP_PACK_STATIC,
                  cases_per_lane: int = 0, cache_budget_bytes: int = 0, seed: int = 0, stream=None,
-                 walk_warps: int = 0, mlp_lr_micro: int = 0, walk_team: int = 0):
+                 walk_warps: int = 0, mlp_lr_micro: int = 0, walk_team: int = 0, lazy: bool = False):
         off = np.asarray(off, np.uint64)
         self.P = len(off) - 1
         self.boolean = boolean
@@ -369,7 +369,7 @@ class Population:
                        cache_threshold=cache_threshold, tournament=tournament, packing=packing,
                        cases_per_lane=cases_per_lane, cache_budget_bytes=cache_budget_bytes,
                        seed=seed & (2**64 - 1), walk_warps=walk_warps, mlp_lr_micro=mlp_lr_micro,
-                       walk_team=walk_team)
+                       walk_team=walk_team, lazy_children=1 if lazy else 0)
         if boolean:
             x = np.zeros(1, np.float32)
             t = np.zeros(1, np.float32)

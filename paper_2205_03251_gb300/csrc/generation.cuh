@@ -69,6 +69,13 @@ struct GenBufs {
     const uint32_t* gen_add;         // device word added to gen (generations replayed by a captured graph)
     uint32_t* stamp;                 // [1] generation stamp of the slot pool's live marks
     uint32_t* rec_entry;             // [pvcap] child cache entry that takes each walk record's value, or ~0
+    // fitness-first materialisation: the next generation's plan is drawn right
+    // after the walk, and only the children it selects as parents get a tree
+    // buffer and a cache
+    uint32_t lazy;                   // 1: the walk reads children through their mother and father
+    uint32_t *nmother, *nfather, *ncpos, *nrsz, *ndpos, *nssz, *nflags;   // [P] next generation's plan
+    uint32_t* sel;                   // [P] 1 for a child that is a parent of the next generation
+    uint32_t* nfree;                 // [1] entries of the free-buffer stack (lazy mode: up to 2P)
     bool evaluated;
 };
 
@@ -233,6 +240,72 @@ __global__ void k_plan(DevPop d, GenBufs g, CacheView par) {
     }
 }
 
+// ------------------------------------------------------------------ fitness-first materialisation
+//
+// The paper observes that most children never become parents (Sec. 6.3) and
+// that only those needed later must be built.  In this mode the walk reads a
+// child through its mother's buffer and the father's donated subtree, the
+// next generation's plan is drawn right after the walk, and only the
+// children it selects get a tree buffer and a cache.  The draws are the same
+// as in the eager order, so every result is identical.
+
+#define BUF_NONE 0xFFFFFFFFu
+
+// Subtree size at x of child t of the current generation (not built yet):
+// from its plan and its parents' caches and bytes.
+__device__ uint32_t virtual_subtree_size(const DevPop& d, const GenBufs& g, const CacheView& par, uint32_t t,
+                                         uint32_t x) {
+    const uint32_t m = g.mother[t];
+    const uint8_t* mb = d.arena + (size_t)g.pbuf[m] * d.cap;
+    const uint32_t sm = g.psize[m];
+    if (g.flags[t] & F_CLONE) return warp_subtree_size_at(par, m, mb, sm, x);
+    const uint32_t c = g.cpos[t], r = g.rsz[t], s = g.ssz[t];
+    if (x >= c && x < c + s) {
+        const uint32_t f = g.father[t];
+        return warp_subtree_size_at(par, f, d.arena + (size_t)g.pbuf[f] * d.cap, g.psize[f], g.dpos[t] + (x - c));
+    }
+    if (x >= c + s) return warp_subtree_size_at(par, m, mb, sm, x - s + r);
+    const uint32_t ms = warp_subtree_size_at(par, m, mb, sm, x);
+    return (x + ms > c) ? ms + s - r : ms;          // an ancestor of c changes by the size change
+}
+
+// The next generation's plan from the current children's fitness, drawn
+// exactly as k_plan draws it (generation gen + 1), one warp per child.
+__global__ void k_plan_next(DevPop d, GenBufs g, CacheView par) {
+    if (halted(d)) return;
+    const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nwp = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t i = gw; i < d.P; i += nwp) {
+        const uint32_t T = g.tsize;
+        const uint32_t gen = g.gen + 1 + *g.gen_add;
+        const uint32_t m = tournament(d.fit, d.P, T, g.seed, gen, i, 0);
+        const uint32_t f = tournament(d.fit, d.P, T, g.seed, gen, i, T);
+        const uint32_t sm = d.size[m], sf = d.size[f];
+        uint32_t fl = F_CLONE, cc = 0, rr = sm, dd = 0, ss = sm, ff = m;
+        for (uint32_t a = 0; a < 8; ++a) {
+            const uint32_t c1 = (uint32_t)below(draw(g.seed, gen, i, 2 * T + 2 * a), sm);
+            const uint32_t d1 = (uint32_t)below(draw(g.seed, gen, i, 2 * T + 2 * a + 1), sf);
+            const uint32_t r1 = virtual_subtree_size(d, g, par, m, c1);
+            const uint32_t s1 = virtual_subtree_size(d, g, par, f, d1);
+            if ((uint64_t)sm - r1 + s1 <= g.max_nodes) { fl = 0; cc = c1; rr = r1; dd = d1; ss = s1; ff = f; break; }
+        }
+        if (lane_id() == 0) {
+            g.nmother[i] = m; g.nfather[i] = ff; g.ncpos[i] = cc; g.nrsz[i] = rr; g.ndpos[i] = dd; g.nssz[i] = ss;
+            g.nflags[i] = fl;
+            g.sel[m] = 1u;
+            g.sel[ff] = 1u;
+        }
+    }
+}
+
+// The plan drawn after the last walk becomes this generation's.
+__global__ void k_plan_take(DevPop d, GenBufs g) {
+    if (halted(d)) return;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < d.P; i += gridDim.x * blockDim.x) {
+        g.mother[i] = g.nmother[i]; g.father[i] = g.nfather[i]; g.cpos[i] = g.ncpos[i];
+        g.rsz[i] = g.nrsz[i]; g.dpos[i] = g.ndpos[i]; g.ssz[i] = g.nssz[i]; g.flags[i] = g.nflags[i];
+    }
+}
+
 // Block-wide exclusive scan of v (1024 threads); returns the exclusive
 // prefix and adds the block total to *carry (shared).
 __device__ __forceinline__ uint64_t block_excl_scan(uint64_t v, uint64_t* ws, uint64_t* carry) {
@@ -341,6 +414,115 @@ __global__ void __launch_bounds__(1024) k_assign(DevPop d, GenBufs g) {
     }
     __syncthreads();
     for (uint32_t k = threadIdx.x; k < P; k += blockDim.x) g.free_buf[k] = g.free_next[k];
+}
+
+// Fitness-first order, at crossover: child sizes, fragment and stash
+// offsets; no child is built yet (one CTA of 1024 threads).
+__global__ void __launch_bounds__(1024) k_assign_lazy(DevPop d, GenBufs g) {
+    if (halted(d)) return;
+    __shared__ uint64_t ws[32];
+    __shared__ uint64_t carry[3];
+    if (threadIdx.x < 3) carry[threadIdx.x] = 0;
+    __syncthreads();
+    const uint32_t P = d.P;
+    for (uint32_t base = 0; base < P; base += blockDim.x) {
+        const uint32_t i = base + threadIdx.x;
+        uint64_t fragb = 0, stashb = 0, xob = 0;
+        if (i < P) {
+            const uint32_t m = g.mother[i];
+            const bool clone = g.flags[i] & F_CLONE;
+            const uint32_t r = g.rsz[i], s = g.ssz[i];
+            d.size[i] = (uint32_t)((int64_t)g.psize[m] + (int64_t)s - (int64_t)r);
+            d.buf[i] = BUF_NONE;
+            if (!clone) {
+                fragb = (s + 15u) & ~15u;
+                if (r < d.T) stashb = (r + 15u) & ~15u;
+                xob = 2ull * s + (r < d.T ? 2ull * r : 0);
+            }
+        }
+        const uint64_t fo = block_excl_scan(fragb, ws, &carry[0]);
+        const uint64_t so = block_excl_scan(stashb, ws, &carry[1]);
+        const uint64_t xo = block_excl_scan(xob, ws, &carry[2]);
+        (void)xo;
+        if (i < P) {
+            g.frag_off[i] = fo;
+            g.stash_off[i] = so;
+            g.shift_off[i] = 0;
+            g.copy_off[i] = 0;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        g.frag_off[P] = carry[0];
+        g.stash_off[P] = carry[1];
+        g.shift_off[P] = 0;
+        g.copy_off[P] = 0;
+        g.gstat[G_XOBYTES] = carry[2];
+        if (carry[0] > g.frag_cap || carry[1] > g.stash_cap) set_status(d.status, ST_CAPACITY);
+    }
+}
+
+// Fitness-first order, after the walk: the children selected as parents
+// take buffers from the free stack and get copy chunks; the previous
+// parents' buffers return to the stack (they are read by the copies, and
+// by gp_get_tree of unselected children, until the next materialisation).
+__global__ void __launch_bounds__(1024) k_materialise_assign(DevPop d, GenBufs g) {
+    if (halted(d)) return;
+    __shared__ uint64_t ws[32];
+    __shared__ uint64_t carry[3];
+    __shared__ uint32_t nfree0;
+    if (threadIdx.x < 3) carry[threadIdx.x] = 0;
+    if (threadIdx.x == 0) nfree0 = *g.nfree;
+    __syncthreads();
+    const uint32_t P = d.P;
+    // count the selected children first: they take the top of the stack
+    for (uint32_t base = 0; base < P; base += blockDim.x) {
+        const uint32_t i = base + threadIdx.x;
+        const uint32_t selc = (i < P && g.sel[i]) ? 1u : 0u;
+        block_excl_scan(selc, ws, &carry[2]);
+    }
+    const uint32_t nsel = (uint32_t)carry[2];
+    if (nsel > nfree0) {
+        if (threadIdx.x == 0) set_status(d.status, ST_CAPACITY);
+        return;
+    }
+    const uint32_t take0 = nfree0 - nsel;
+    for (uint32_t base = 0; base < P; base += blockDim.x) {
+        const uint32_t i = base + threadIdx.x;
+        uint32_t selc = 0, nch = 0;
+        uint64_t xob = 0;
+        if (i < P && g.sel[i]) {
+            selc = 1;
+            const uint32_t nk = d.size[i];
+            nch = (nk + COPY_CH - 1) / COPY_CH;
+            xob = 2ull * nk;
+        }
+        const uint64_t rank = block_excl_scan(selc, ws, &carry[0]);
+        const uint64_t co = block_excl_scan(nch, ws, &carry[1]);
+        if (i < P) {
+            d.buf[i] = selc ? g.free_buf[take0 + rank] : BUF_NONE;
+            g.copy_off[i] = (uint32_t)co;
+            if (selc) atomicAdd(&g.gstat[G_XOBYTES], xob);
+        }
+    }
+    __syncthreads();
+    // previous parents' buffers back on the stack
+    __shared__ uint64_t cfree;
+    if (threadIdx.x == 0) cfree = 0;
+    __syncthreads();
+    for (uint32_t base = 0; base < P; base += blockDim.x) {
+        const uint32_t j = base + threadIdx.x;
+        const uint32_t b = (j < P) ? g.pbuf[j] : BUF_NONE;
+        const uint32_t has = (b != BUF_NONE) ? 1u : 0u;
+        const uint64_t pos = block_excl_scan(has, ws, &cfree);
+        if (has) g.free_buf[take0 + pos] = b;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        g.copy_off[P] = (uint32_t)carry[1];
+        g.misc[M_NCOPY] = nsel;
+        *g.nfree = take0 + (uint32_t)cfree;
+    }
 }
 
 // ------------------------------------------------------------------ A6 gather
@@ -655,7 +837,8 @@ __device__ __forceinline__ void eval_run(const uint8_t* src, uint32_t s, uint32_
 // from a forward scan after the donated subtree.  Returns false on an
 // inconsistency (recorded in the status word).
 template <int K>
-__device__ bool walk_ancestors(const DevPop& d, const CacheView& par, uint32_t i, const uint8_t* ok_, uint32_t c,
+__device__ bool walk_ancestors(const DevPop& d, const CacheView& par, uint32_t i, const uint8_t* ok_, int32_t tdl,
+                               uint32_t c,
                                uint32_t s, uint32_t nk, int32_t em, uint32_t me0, uint32_t me1, uint8_t* stB,
                                uint32_t* anc, int32_t* ancg, uint32_t* lvl, int32_t& A_out, uint32_t& nsmall_out,
                                int32_t& hneed_out) {
@@ -750,12 +933,13 @@ __device__ bool walk_ancestors(const DevPop& d, const CacheView& par, uint32_t i
         // size check of the walk instead of reading a stale end
         for (uint32_t v = lane; v <= maxv; v += 32) lvl[v] = 0;
         __syncwarp();
+        // child positions q >= c + s are bytes q - tdl of ok_
         const uint32_t lim = min(f1, (nk + 15u) & ~15u);
-        if (f0 < lim) { stage_issue(stB, ok_, f0, lim); }
+        if (f0 < lim) { stage_issue(stB, ok_, f0 - tdl, lim - tdl); }
         cp_async_commit();
         cp_async_wait<0>();
         __syncwarp();
-        const uint32_t a16 = f0 & ~15u;
+        const uint32_t a16 = ((f0 - tdl) & ~15u) + tdl;
         if (lane == 0) lvl[1] = f0;
         int sum = 0, mx = 0;
         // lane l: positions f0 + 32l + t
@@ -868,7 +1052,11 @@ __global__ void __launch_bounds__(256, 2) k_walk(DevPop d, GenBufs g, CacheView 
         }
         const uint32_t f = g.father[i], c = g.cpos[i], r = g.rsz[i], dd = g.dpos[i], s = g.ssz[i];
         const uint32_t nk = d.size[i];
-        const uint8_t* ok_ = d.arena + (size_t)d.buf[i] * d.cap;     // child bytes
+        // child bytes: its own buffer, or (fitness-first mode, the child not built
+        // yet) its mother's, where a position x >= c + s of the child is byte x - tdl
+        const bool virt = g.lazy != 0;
+        const uint8_t* ok_ = virt ? d.arena + (size_t)g.pbuf[m] * d.cap : d.arena + (size_t)d.buf[i] * d.cap;
+        const int32_t tdl = virt ? (int32_t)s - (int32_t)r : 0;
         const uint32_t me0 = par.e_off[m], me1 = par.e_off[m + 1];
         const uint32_t fe0 = par.e_off[f], fe1 = par.e_off[f + 1];
         uint32_t npv = 0, nins_i = 0;
@@ -881,7 +1069,25 @@ __global__ void __launch_bounds__(256, 2) k_walk(DevPop d, GenBufs g, CacheView 
             for (uint32_t cb = warp; cb < ncb; cb += nw) {
                 load_cases<K>(d, cb, ic.xv);
                 float v[K];
-                eval_run<K, B>(ok_, 0, nk, stA, ic, v, d.status);
+                if (virt) {
+                    // the whole child from its three pieces: mother head, donated subtree, mother tail
+                    const uint8_t* fb = d.arena + (size_t)g.pbuf[f] * d.cap;
+                    __syncwarp();
+                    for (uint32_t x = lane; x < nk; x += 32)
+                        stA[x] = x < c ? ok_[x] : (x < c + s ? fb[dd + (x - c)] : ok_[x - tdl]);
+                    __syncwarp();
+                    Istate<K> ist;
+#pragma unroll
+                    for (int kk = 0; kk < K; ++kk) ist.acc[kk] = 0.f;
+                    ist.sp = 0;
+                    ist.ok = true;
+                    interp_staged<K, B>(stA, 0, nk, ist, ic);
+                    if (!ist.ok && lane == 0) set_status(d.status, ST_STACK);
+#pragma unroll
+                    for (int kk = 0; kk < K; ++kk) v[kk] = ist.acc[kk];
+                } else {
+                    eval_run<K, B>(ok_, 0, nk, stA, ic, v, d.status);
+                }
                 st_interp += nk;
                 store_blk<K>(nvs, cb, v);
                 if (c != 0) {
@@ -956,7 +1162,11 @@ __global__ void __launch_bounds__(256, 2) k_walk(DevPop d, GenBufs g, CacheView 
             float v[K];
             if (which == 0) {
                 if (ef >= 0) load_vec<K>(par.slots, Cpad, par.e_slot[ef], v, cb);
-                else { eval_run<K, B>(ok_, c, c + s, stA, ic, v, d.status); st_interp += s; }
+                else {
+                    if (virt) eval_run<K, B>(d.arena + (size_t)g.pbuf[f] * d.cap, dd, dd + s, stA, ic, v, d.status);
+                    else eval_run<K, B>(ok_, c, c + s, stA, ic, v, d.status);
+                    st_interp += s;
+                }
             } else {
                 if (em >= 0) load_vec<K>(par.slots, Cpad, par.e_slot[em], v, cb);
                 else { eval_run<K, B>(g.stash + g.stash_off[i], 0, r, stA, ic, v, d.status); st_interp += r; }
@@ -985,7 +1195,7 @@ __global__ void __launch_bounds__(256, 2) k_walk(DevPop d, GenBufs g, CacheView 
         if (warp == 0) {
             int32_t A = -1, hneed = -1;
             uint32_t nsmall = 0;
-            const bool ok = walk_ancestors<K>(d, par, i, ok_, c, s, nk, em, me0, me1, stB, anc, ancg, lvl, A,
+            const bool ok = walk_ancestors<K>(d, par, i, ok_, tdl, c, s, nk, em, me0, me1, stB, anc, ancg, lvl, A,
                                               nsmall, hneed);
             if (lane == 0) { sc[2] = nsmall; sc[3] = (uint32_t)A; sc[4] = ok ? 0u : 1u; sc[5] = (uint32_t)hneed; }
         }
@@ -1080,7 +1290,8 @@ __global__ void __launch_bounds__(256, 2) k_walk(DevPop d, GenBufs g, CacheView 
                             if (D.sib >= 0) load_vec<K>(par.slots, Cpad, D.sslot, v, cb);
                             else {
                                 load_cases<K>(d, cb, ic.xv);
-                                eval_run<K, B>(ok_, D.ss, D.se, stA, ic, v, d.status);
+                                const uint32_t sh = (D.flags & LD_LEFT) ? (uint32_t)tdl : 0u;
+                                eval_run<K, B>(ok_, D.ss - sh, D.se - sh, stA, ic, v, d.status);
                                 st_interp += D.se - D.ss;
                             }
                             store_blk<K>(svs + slot * Cpad, cb, v);
@@ -1191,7 +1402,8 @@ __global__ void __launch_bounds__(256, 2) k_walk(DevPop d, GenBufs g, CacheView 
                     if (D.sib >= 0) load_vec<K>(par.slots, Cpad, D.sslot, v, cb);
                     else {
                         load_cases<K>(d, cb, ic.xv);
-                        eval_run<K, B>(ok_, D.ss, D.se, stA, ic, v, d.status);
+                        const uint32_t sh = (D.flags & LD_LEFT) ? (uint32_t)tdl : 0u;
+                        eval_run<K, B>(ok_, D.ss - sh, D.se - sh, stA, ic, v, d.status);
                         st_interp += D.se - D.ss;
                     }
                     store_blk<K>(svs + slot * Cpad, cb, v);
@@ -1313,6 +1525,7 @@ __global__ void k_merge_count(DevPop d, GenBufs g, CacheView par) {
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < d.P; i += gridDim.x * blockDim.x) {
         const uint32_t m = g.mother[i];
         const uint32_t me0 = par.e_off[m], me1 = par.e_off[m + 1];
+        if (g.lazy && !g.sel[i]) { g.mcnt[i] = 0; continue; }     // never a parent: no cache
         if (g.flags[i] & F_CLONE) { g.mcnt[i] = me1 - me0; continue; }
         const uint32_t f = g.father[i], c = g.cpos[i], r = g.rsz[i], dd = g.dpos[i], s = g.ssz[i];
         const int32_t delta = (int32_t)s - (int32_t)r;
@@ -1401,6 +1614,7 @@ __global__ void __launch_bounds__(256) k_merge_write(DevPop d, GenBufs g, CacheV
     const int lane = lane_id();
     const uint32_t T = d.T;
     for (uint32_t i = blockIdx.x; i < d.P; i += gridDim.x) {
+        if (g.lazy && !g.sel[i]) continue;                      // uniform per CTA
         const uint32_t o = d.e_off[i];
         const uint32_t m = g.mother[i];
         const uint32_t me0 = par.e_off[m], me1 = par.e_off[m + 1];

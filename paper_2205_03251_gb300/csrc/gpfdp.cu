@@ -20,7 +20,7 @@ namespace {
 
 thread_local std::string g_create_error;
 
-enum Phase { PH_STRUCT = 0, PH_ITEMS, PH_SKEL, PH_FIT, PH_XO, PH_WALK, PH_CACHE, PH_PACK, NPH };
+enum Phase { PH_STRUCT = 0, PH_ITEMS, PH_SKEL, PH_FIT, PH_XO, PH_WALK, PH_CACHE, PH_PACK, PH_MAT, NPH };
 constexpr int NREC = 128;   // event pairs kept per phase: stats average the last NREC calls
 
 }  // namespace
@@ -93,6 +93,11 @@ struct gp_pop {
     uint32_t graph_n;                 // generations per replay
     uint32_t graph_launches;          // kernel launches per replay
     cudaStream_t cap_stream;          // private capture stream when the population runs on the legacy stream
+    // fitness-first materialisation
+    bool have_next_plan;              // the last walk drew the next generation's plan
+    uint32_t planned_gen;             // ... for this generation number
+    bool lazy_pending;                // some individuals exist only through their parents
+    uint32_t host_nfree;              // pageable source of the free-stack count upload
 };
 
 namespace {
@@ -486,7 +491,7 @@ int gp_pop_create(const gp_config* cfg_in, const float* x, const float* targets,
     if (K != 1 && K != 2 && K != 4) return fail(nullptr, GP_EINVAL, "cases_per_lane must be 0, 1, 2 or 4");
     if (cfg.walk_team != 0 && cfg.walk_team != 1 && cfg.walk_team != 2 && cfg.walk_team != 4 && cfg.walk_team != 8)
         return fail(nullptr, GP_EINVAL, "walk_team must be 0, 1, 2, 4 or 8");
-    if (cfg.reserved != 0) return fail(nullptr, GP_EINVAL, "reserved config field must be 0");
+    if (cfg.lazy_children > 1) return fail(nullptr, GP_EINVAL, "lazy_children must be 0 or 1");
     const uint32_t P = cfg.pop_size;
     for (uint32_t i = 0; i < P; ++i) {
         if (offsets[i + 1] < offsets[i]) return fail(nullptr, GP_EINVAL, "offsets not increasing at %u", i);
@@ -613,7 +618,7 @@ int gp_pop_create(const gp_config* cfg_in, const float* x, const float* targets,
         g.shift_cap = (uint32_t)((uint64_t)P * d.cap / SHIFT_BS + P);
         DA2(g.pbuf, P); DA2(g.psize, P); DA2(g.pfit, P);
         DA2(g.mother, P); DA2(g.father, P); DA2(g.cpos, P); DA2(g.rsz, P); DA2(g.dpos, P); DA2(g.ssz, P);
-        DA2(g.flags, P); DA2(g.lastidx, P); DA2(g.free_buf, P); DA2(g.free_next, P); DA2(g.hasip, P);
+        DA2(g.flags, P); DA2(g.lastidx, P); DA2(g.free_buf, 2 * P); DA2(g.free_next, P); DA2(g.hasip, P);
         DA2(g.misc, NMISC);
         DA2(g.frag_off, P + 1); DA2(g.frag, g.frag_cap + 64);
         DA2(g.stash_off, P + 1); DA2(g.stash, g.stash_cap + 64);
@@ -623,11 +628,16 @@ int gp_pop_create(const gp_config* cfg_in, const float* x, const float* targets,
         DA2(g.pv_rec, g.pvcap); DA2(g.pv_cnt, P); DA2(g.pv_off, P + 1); DA2(g.pv_sorted, g.pvcap);
         DA2(g.pv_end, g.pvcap); DA2(g.pv_val, (size_t)g.pvcap * d.Cpad);
         DA2(g.rec_entry, g.pvcap);
+        g.lazy = cfg.lazy_children;
+        DA2(g.nmother, P); DA2(g.nfather, P); DA2(g.ncpos, P); DA2(g.nrsz, P); DA2(g.ndpos, P); DA2(g.nssz, P);
+        DA2(g.nflags, P); DA2(g.sel, P); DA2(g.nfree, 1);
         DA2(g.walkA, P); DA2(g.nins, P); DA2(g.mb, P); DA2(g.mcnt, P + 1);
         DA2(g.order, P); DA2(g.gstat, NGSTAT);
         std::vector<uint32_t> fb(P);
         for (uint32_t i = 0; i < P; ++i) fb[i] = P + i;          // buffers P..2P-1 start free
-        if (cudaMemcpy(g.free_buf, fb.data(), sizeof(uint32_t) * P, cudaMemcpyHostToDevice) != cudaSuccess)
+        const uint32_t nfree_init = P;
+        if (cudaMemcpy(g.nfree, &nfree_init, sizeof nfree_init, cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(g.free_buf, fb.data(), sizeof(uint32_t) * P, cudaMemcpyHostToDevice) != cudaSuccess)
             return bail(GP_ECUDA);
         cudaMemset(g.gstat, 0, sizeof(unsigned long long) * NGSTAT);
     }
@@ -738,6 +748,10 @@ int gp_load_trees(gp_pop* pop, const uint8_t* ops, const uint64_t* offsets) {
         for (uint32_t i = 0; i < P; ++i) pop->host_free[i] = P + i;
     }
     CK(cudaMemcpyAsync(pop->gb.free_buf, pop->host_free.data(), sizeof(uint32_t) * P, cudaMemcpyHostToDevice, pop->stream));
+    pop->host_nfree = P;
+    CK(cudaMemcpyAsync(pop->gb.nfree, &pop->host_nfree, sizeof(uint32_t), cudaMemcpyHostToDevice, pop->stream));
+    pop->have_next_plan = false;
+    pop->lazy_pending = false;
     pop->have_children = false;
     pop->gb.evaluated = false;
     return GP_OK;
@@ -783,6 +797,8 @@ int gp_graph_capture(gp_pop* pop, uint32_t first_generation, uint32_t n_generati
     GenBufs& g = pop->gb;
     if (!g.evaluated || pop->have_children)
         return fail(pop, GP_ESTATE, "gp_graph_capture needs an evaluated population with no pending children");
+    if (g.lazy && (!pop->have_next_plan || pop->planned_gen != first_generation))
+        return fail(pop, GP_ESTATE, "fitness-first mode: capture after a generation, starting at the planned one");
     int rc = check_status(pop);
     if (rc) return rc;
     if (pop->gexec) { cudaGraphExecDestroy(pop->gexec); pop->gexec = nullptr; pop->graph_n = 0; }
@@ -814,6 +830,8 @@ int gp_graph_capture(gp_pop* pop, uint32_t first_generation, uint32_t n_generati
     const int cur0 = pop->cur;
     const uint32_t calls0 = pop->cum_calls;
     const int kind0 = pop->last_kind;
+    const bool plan0 = pop->have_next_plan, pend0 = pop->lazy_pending;
+    const uint32_t pgen0 = pop->planned_gen;
     pop->capturing = true;
     memset(pop->gev_n, 0, sizeof pop->gev_n);
     g.gen_add = pop->gwords + 1;
@@ -835,6 +853,9 @@ int gp_graph_capture(gp_pop* pop, uint32_t first_generation, uint32_t n_generati
     pop->capturing = false;
     pop->graph_prof = pop->profiling;
     pop->cum_calls = calls0;
+    pop->have_next_plan = plan0;
+    pop->lazy_pending = pend0;
+    pop->planned_gen = pgen0;
     pop->last_kind = kind0;
     pop->have_children = false;
     if (r != GP_OK) { if (graph) cudaGraphDestroy(graph); cudaGetLastError(); return r; }
@@ -857,6 +878,10 @@ int gp_graph_launch(gp_pop* pop) {
         return fail(pop, GP_ESTATE, "gp_graph_launch needs an evaluated population with no pending children");
     CK(cudaGraphLaunch(pop->gexec, pop->stream));
     pop->cum_calls += pop->graph_n;
+    if (pop->gb.lazy) {
+        pop->planned_gen += pop->graph_n;
+        pop->lazy_pending = true;
+    }
     pop->stats_graph = pop->graph_prof && pop->profiling;
     pop->launches = pop->graph_launches;
     pop->last_kind = 1;
@@ -874,10 +899,13 @@ int gp_set_profiling(gp_pop* pop, int on) {
 
 int gp_eval_full(gp_pop* pop) {
     if (!pop) return GP_EINVAL;
+    if (pop->lazy_pending)
+        return fail(pop, GP_ESTATE, "fitness-first mode keeps only the parents' trees; gp_load_trees before gp_eval_full");
     int rc = run_full(pop);
     if (rc) return rc;
     pop->have_children = false;
     pop->gb.evaluated = true;
+    pop->have_next_plan = false;
     return GP_OK;
 }
 
@@ -916,6 +944,12 @@ int gp_root_values(const gp_pop* cpop, void* host_out, size_t bytes) {
     std::vector<uint32_t> eoff(d.P + 1), slot(1);
     CK(cudaMemcpy(eoff.data(), d.e_off, sizeof(uint32_t) * (d.P + 1), cudaMemcpyDeviceToHost));
     for (uint32_t i = 0; i < d.P; ++i) {
+        if (eoff[i + 1] == eoff[i]) {
+            // fitness-first mode: a child that is not a parent keeps no cache
+            if (boolean) static_cast<uint64_t*>(host_out)[i] = 0;
+            else for (uint32_t k = 0; k < d.C; ++k) static_cast<float*>(host_out)[(size_t)i * d.C + k] = NAN;
+            continue;
+        }
         CK(cudaMemcpy(slot.data(), d.e_slot + eoff[i], sizeof(uint32_t), cudaMemcpyDeviceToHost));
         if (boolean) {
             uint32_t w[2];
@@ -940,7 +974,33 @@ int gp_get_tree(const gp_pop* cpop, uint32_t i, uint8_t* host_out, uint64_t cap,
     *size = n;
     if (!host_out) return GP_OK;
     if (cap < n) return fail(pop, GP_EINVAL, "host buffer too small for tree %u (%u nodes)", i, n);
-    CK(cudaMemcpy(host_out, pop->d.arena + (size_t)b * pop->d.cap, n, cudaMemcpyDeviceToHost));
+    if (b != BUF_NONE) {
+        CK(cudaMemcpy(host_out, pop->d.arena + (size_t)b * pop->d.cap, n, cudaMemcpyDeviceToHost));
+        return GP_OK;
+    }
+    // a child of the fitness-first order that is not built: mother's head,
+    // the donated subtree (from the father), mother's tail
+    const GenBufs& g = pop->gb;
+    uint32_t m = 0, f = 0, c = 0, r = 0, dd = 0, sv = 0, fl = 0, bm = 0, bf = 0;
+    CK(cudaMemcpy(&m, g.mother + i, 4, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(&f, g.father + i, 4, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(&c, g.cpos + i, 4, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(&r, g.rsz + i, 4, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(&dd, g.dpos + i, 4, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(&sv, g.ssz + i, 4, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(&fl, g.flags + i, 4, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(&bm, g.pbuf + m, 4, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(&bf, g.pbuf + f, 4, cudaMemcpyDeviceToHost));
+    if (bm == BUF_NONE || bf == BUF_NONE) return fail(pop, GP_ESTATE, "tree %u is no longer available", i);
+    const uint8_t* mb = pop->d.arena + (size_t)bm * pop->d.cap;
+    if (fl & F_CLONE) {
+        CK(cudaMemcpy(host_out, mb, n, cudaMemcpyDeviceToHost));
+        return GP_OK;
+    }
+    const uint8_t* fbp = pop->d.arena + (size_t)bf * pop->d.cap;
+    if (c) CK(cudaMemcpy(host_out, mb, c, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(host_out + c, fbp + dd, sv, cudaMemcpyDeviceToHost));
+    if (n > c + sv) CK(cudaMemcpy(host_out + c + sv, mb + c + r, n - c - sv, cudaMemcpyDeviceToHost));
     return GP_OK;
 }
 
@@ -1052,7 +1112,7 @@ int gp_get_stats(const gp_pop* cpop, gp_stats* out) {
     int rc = check_status(pop);
     if (rc) return rc;
     gp_stats s = pop->stats;
-    for (int i = 0; i < NPH && i < 8; ++i) {
+    for (int i = 0; i < NPH && i < 9; ++i) {
         s.ms[i] = 0.f;
         const bool gr = pop->stats_graph;
         uint32_t n = gr ? pop->gev_n[i] : (pop->ev_count[i] < (uint32_t)NREC ? pop->ev_count[i] : (uint32_t)NREC);
@@ -1130,6 +1190,9 @@ int gen_crossover(gp_pop* pop, uint32_t generation) {
     GenBufs& g = pop->gb;
     if (!g.evaluated) return fail(pop, GP_ESTATE, "gp_crossover needs an evaluated population (gp_eval_full or gp_eval_incremental first)");
     if (pop->have_children) return fail(pop, GP_ESTATE, "children of the last crossover are not evaluated yet");
+    if (g.lazy && pop->have_next_plan && generation != pop->planned_gen)
+        return fail(pop, GP_ESTATE, "fitness-first mode drew generation %u's plan; gp_crossover(%u) must follow",
+                    pop->planned_gen, generation);
     g.gen = generation;
     swap_generation(pop);
     const CacheView par = view_of(pop, pop->sets[pop->cur]);
@@ -1139,6 +1202,21 @@ int gen_crossover(gp_pop* pop, uint32_t generation) {
     CK(cudaMemsetAsync(g.lastidx, 0xFF, sizeof(int32_t) * d.P, pop->stream));
     CK(cudaMemsetAsync(g.misc, 0, sizeof(uint32_t) * NMISC, pop->stream));
     CK(cudaMemsetAsync(g.gstat, 0, sizeof(unsigned long long) * NGSTAT, pop->stream));
+    if (g.lazy) {
+        // fitness-first: the plan (drawn after the last walk, or now for freshly
+        // evaluated parents), fragments and stash; the children are built later
+        if (pop->have_next_plan) k_plan_take<<<(d.P + 255) / 256, 256, 0, pop->stream>>>(d, g);
+        else k_plan<<<(d.P + 7) / 8, 256, 0, pop->stream>>>(d, g, par);
+        k_assign_lazy<<<1, 1024, 0, pop->stream>>>(d, g);
+        k_gather<<<pop->nsm * 4, 256, 0, pop->stream>>>(d, g);
+        phase_end(pop, PH_XO);
+        CK(cudaGetLastError());
+        pop->have_children = true;
+        pop->lazy_pending = true;
+        g.evaluated = false;
+        pop->launches = 3;
+        return GP_OK;
+    }
     k_plan<<<(d.P + 7) / 8, 256, 0, pop->stream>>>(d, g, par);
     k_assign<<<1, 1024, 0, pop->stream>>>(d, g);
     k_gather<<<pop->nsm * 4, 256, 0, pop->stream>>>(d, g);
@@ -1181,6 +1259,16 @@ int gen_incremental(gp_pop* pop) {
     if (d.funcset == GP_BOOL_MUX6) launch_walk<1, true>(pop, par);
     else if (d.K == 1) launch_walk<1>(pop, par); else if (d.K == 2) launch_walk<2>(pop, par); else launch_walk<4>(pop, par);
     phase_end(pop, PH_WALK);
+    if (g.lazy) {
+        // the next generation's plan from these children's fitness; only the
+        // children it selects as parents are built and get a cache
+        phase_begin(pop, PH_MAT);
+        CK(cudaMemsetAsync(g.sel, 0, sizeof(uint32_t) * d.P, pop->stream));
+        k_plan_next<<<(d.P + 7) / 8, 256, 0, pop->stream>>>(d, g, par);
+        k_materialise_assign<<<1, 1024, 0, pop->stream>>>(d, g);
+        k_copy_children<<<pop->nsm * 8, 256, 0, pop->stream>>>(d, g);
+        phase_end(pop, PH_MAT);
+    }
     // online training of the packing MLP on the levels the walks took
     k_mlp_targets<<<pb, 256, 0, pop->stream>>>(d, g, pop->mlp);
     k_mlp_train_pass<<<mb, 256, 0, pop->stream>>>(pop->mlp, d.P);
@@ -1226,5 +1314,10 @@ int gen_incremental(gp_pop* pop) {
     pop->have_children = false;
     g.evaluated = true;
     pop->last_kind = 1;
+    if (g.lazy) {
+        pop->have_next_plan = true;
+        pop->planned_gen = g.gen + 1;
+        pop->launches += 4;
+    }
     return GP_OK;
 }

@@ -37,13 +37,13 @@ def _expected_entries(tree, T):
 
 
 def run_generations(gp, w, *, T, gens, max_nodes, seed=1234, cache_check=16, stop_check=True,
-                    cases_per_lane=0, walk_team=0):
+                    cases_per_lane=0, walk_team=0, lazy=False):
     import oracle
     ops, off = w["ops"], w["off"]
     k, x, t = w["consts"], w["x"], w["t"]
     P = len(off) - 1
     pop = gp.Population(x, t, k, ops, off, max_nodes=max_nodes, cache_threshold=T, seed=seed,
-                        cases_per_lane=cases_per_lane, walk_team=walk_team)
+                        cases_per_lane=cases_per_lane, walk_team=walk_team, lazy=lazy)
     pop.eval_full()
     fit = pop.fitness()
     _, ofit = oracle.eval_pop_f32(ops, off, k, x, t)
@@ -84,9 +84,15 @@ def run_generations(gp, w, *, T, gens, max_nodes, seed=1234, cache_check=16, sto
                 ostop, depth = oracle.fdp_walk(mom, kid, int(pl["c"][i]), k, x)
                 assert stop[i] == ostop, f"gen {g}: child {i} stops at {stop[i]}, oracle {ostop}"
         # children's cache: positions and sampled values
-        for i in rng.choice(P, size=min(P, cache_check), replace=False):
+        checked = 0
+        for i in rng.permutation(P):
+            if checked >= min(P, cache_check):
+                break
             kid = kops[int(koff[i]):int(koff[i + 1])]
             pos, end, par = pop.cache_entries(int(i))
+            if lazy and len(pos) == 0:
+                continue                 # fitness-first: a child that is not a parent keeps no cache
+            checked += 1
             epos, eend, epar = _expected_entries(kid, T)
             assert np.array_equal(pos, epos) and np.array_equal(end, eend), (
                 f"gen {g}: child {i} cache structure: got pos {pos[:12]} end {end[:12]}, "
@@ -106,10 +112,40 @@ def run_generations(gp, w, *, T, gens, max_nodes, seed=1234, cache_check=16, sto
 
 
 @pytest.mark.parametrize("T", [1024, 64, 8])
-def test_generations_rhh(gp, T):
+@pytest.mark.parametrize("lazy", [False, True])
+def test_generations_rhh(gp, T, lazy):
     import synth
     w = synth.workload(0, n_trees=120)
-    run_generations(gp, w, T=T, gens=4, max_nodes=20000)
+    run_generations(gp, w, T=T, gens=4, max_nodes=20000, lazy=lazy)
+
+
+def test_fitness_first_matches_eager(gp):
+    """Fitness-first materialisation changes which children are built, not
+    any result: trees, fitness and stop levels equal the eager order's over
+    several generations, and fewer bytes are moved."""
+    import synth
+    w = synth.workload(0, n_trees=200)
+    runs = {}
+    for lazy in (False, True):
+        pop = gp.Population(w["x"], w["t"], w["consts"], w["ops"], w["off"], max_nodes=20000, cache_threshold=32,
+                            seed=77, lazy=lazy)
+        pop.eval_full()
+        hist = []
+        for g in range(6):
+            pop.crossover(g)
+            st = pop.eval_incremental()
+            hist.append((pop.fitness().copy(), [pop.tree(i).copy() for i in range(200)], pop.walk_info()[0].copy(),
+                         st.crossover_bytes))
+        pop.close()
+        runs[lazy] = hist
+    xo = {False: 0, True: 0}
+    for (fe, te, se, be), (fl, tl, sl, bl) in zip(runs[False], runs[True]):
+        assert fe.tobytes() == fl.tobytes()
+        assert all(np.array_equal(a, b) for a, b in zip(te, tl))
+        assert np.array_equal(se, sl)
+        xo[False] += be
+        xo[True] += bl
+    assert xo[True] < xo[False]
 
 
 def test_generations_small_cases_and_lanes(gp):
@@ -123,9 +159,9 @@ def test_generations_several_case_blocks(gp):
     """Value vectors longer than one warp's case block (32 x cases_per_lane):
     the walk goes block by block and stops only where every block agrees."""
     import synth
-    for C, K in ((1024, 4), (100, 1), (200, 2), (1024, 1)):
+    for C, K, lazy in ((1024, 4, False), (100, 1, True), (200, 2, False), (1024, 1, True)):
         w = synth.workload(0, n_trees=48, n_cases=C)
-        run_generations(gp, w, T=32, gens=2, max_nodes=20000, cases_per_lane=K, cache_check=8)
+        run_generations(gp, w, T=32, gens=2, max_nodes=20000, cases_per_lane=K, cache_check=8, lazy=lazy)
 
 
 def test_generations_uneven_population_1024_cases(gp):
@@ -161,12 +197,13 @@ def test_generations_tight_size_limit_makes_copies(gp):
     assert all(h[0]["children"] == 80 for h in hist)
 
 
-def test_generations_grafted_trees(gp):
+@pytest.mark.parametrize("lazy", [False, True])
+def test_generations_grafted_trees(gp, lazy):
     import synth
     ops, off = synth.population("big", synth.MASTER_SEED + 1, 24, target=60_000)
     x, t = synth.cases(synth.MASTER_SEED + 1, 48)
     w = {"ops": ops, "off": off, "x": x, "t": t, "consts": synth.consts(synth.MASTER_SEED + 1)}
-    hist = run_generations(gp, w, T=1024, gens=3, max_nodes=1 << 18, stop_check=True)
+    hist = run_generations(gp, w, T=1024, gens=3, max_nodes=1 << 18, stop_check=True, lazy=lazy)
     # failed disruption propagation stops most walks below the root
     stopped = sum(int((h[1] >= 0).sum()) for h in hist)
     assert stopped > 0

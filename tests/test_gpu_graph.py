@@ -151,3 +151,47 @@ def test_graph_capture_needs_graph_mode_and_even_count(gp):
     with pytest.raises(gp.GpError):
         pop.graph_launch()                            # nothing captured
     pop.close()
+
+
+@pytest.mark.parametrize("boolean", [False, True])
+def test_graph_replay_fitness_first(gp, boolean):
+    """Fitness-first order under graph replay: one eager generation draws the
+    next plan, then replays continue it; trees and fitness equal the eager
+    order's (children built at crossover) generation by generation."""
+    import oracle
+    w = _uneven(boolean, n_trees=256, target=20_000)
+    maxn, seed, T = 40_000, 21, 64
+
+    def make(lazy):
+        if w["boolean"]:
+            return gp.Population(None, None, np.zeros(251, np.float32), w["ops"], w["off"], max_nodes=maxn,
+                                 cache_threshold=T, boolean=True, seed=seed, lazy=lazy)
+        return gp.Population(w["x"], w["t"], w["consts"], w["ops"], w["off"], max_nodes=maxn,
+                             cache_threshold=T, seed=seed, lazy=lazy)
+
+    ref = make(False)
+    ref.eval_full()
+    want = {}
+    for g in range(5):
+        ref.crossover(g)
+        ref.eval_incremental()
+        want[g] = (ref.fitness().copy(), [ref.tree(i).copy() for i in range(ref.P)])
+    ref.close()
+    pop = make(True)
+    pop.set_graph_mode(True)
+    pop.eval_full()
+    pop.crossover(0)
+    pop.eval_incremental()
+    assert oracle.canon_nan(pop.fitness()).tobytes() == oracle.canon_nan(want[0][0]).tobytes()
+    with pytest.raises(gp.GpError):
+        pop.graph_capture(0, 2)                       # generation 1 is the planned one
+    pop.graph_capture(1, 2)
+    for r, g in enumerate((2, 4)):
+        pop.graph_launch()
+        assert oracle.canon_nan(pop.fitness()).tobytes() == oracle.canon_nan(want[g][0]).tobytes(), g
+        assert all(np.array_equal(pop.tree(i), want[g][1][i]) for i in range(pop.P)), g
+    with pytest.raises(gp.GpError):
+        pop.crossover(7)                              # generation 5 is the planned one
+    pop.crossover(5)
+    pop.eval_incremental()
+    pop.close()
