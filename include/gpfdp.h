@@ -194,6 +194,51 @@ int gp_cache_value(const gp_pop* pop, uint32_t i, uint32_t j, void* host_out, si
 int gp_walk_info(const gp_pop* pop, int32_t* stop_level, uint32_t* levels, uint32_t n);
 
 /*
+ * Disruption diagnostics (Fig. 4 and the walk of Sec. 6.2): how far a
+ * crossover's change of the test-case values travels up the chain of
+ * ancestors of the crossover point before it dies out.
+ *
+ * One record per child and walk level, level 0 being the crossover point
+ * and level j its j-th ancestor, for the levels the walk compares (up to and
+ * including the stop level, or up to the root):
+ *   disrupted  cases whose child value differs from the mother's value at
+ *              that node (bit patterns; Boolean: differing bits of the
+ *              64-case word);
+ *   finite     those of them where both values are finite (Boolean: all);
+ *   sum_sq     sum over the finite ones of (child - mother)^2, each
+ *              difference and square in binary64 (Boolean: 1 per case), so
+ *              the RMS difference of the disrupted cases is
+ *              sqrt(sum_sq / finite).  The summation order is not fixed:
+ *              two runs agree bit for bit, the CPU definition to within
+ *              2 (C - 1) binary64 roundings (every term is >= 0).
+ * The record at the stop level has disrupted == 0.  A clone of its mother
+ * has one record (level 0, zeros).
+ */
+typedef struct {
+    uint32_t disrupted;
+    uint32_t finite;
+    double sum_sq;
+} gp_disruption_level;
+
+/* Record up to max_levels levels per child in the following incremental
+ * evaluations (0 turns recording off and frees the records).  Allocates
+ * pop_size * max_levels records of 16 bytes.  While recording, children
+ * smaller than the cache threshold are walked level by level instead of
+ * being evaluated in one pass (same fitness, trees and cache).  Drops a
+ * captured graph (capture again afterwards).  Synchronising.  GP_EINVAL for
+ * max_levels > 65,536, GP_ENOMEM when the records do not fit. */
+int gp_set_disruption(gp_pop* pop, uint32_t max_levels);
+
+/* Records of the last gp_eval_incremental (or graph replay) that ran with
+ * recording on: records[i * max_levels + j] for child i and level j <
+ * n_levels[i] (min(levels walked + 1, max_levels); 0 when the child's walk
+ * failed).  `n` = pop_size * max_levels records must fit in records;
+ * n_levels holds pop_size entries; either pointer may be NULL.  GP_ESTATE
+ * when no such evaluation has run since recording was last set.
+ * Synchronising. */
+int gp_disruption(const gp_pop* pop, gp_disruption_level* records, size_t n, uint32_t* n_levels);
+
+/*
  * Work packing of the last gp_eval_incremental (Sec. 3 and Sec. 4.1 of
  * the paper: run the longest tasks first; one slow evaluation holds up the
  * population).  Per child: the packing MLP's prediction of

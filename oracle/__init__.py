@@ -68,6 +68,9 @@ def _load():
                 "or_splice": (u64, [u8p, u64, u64, u64, u8p, u64, u64, u8p]),
                 "or_fdp_walk": (i32, [u8p, u64, u8p, u64, u64, u8p, u8p, u32, u8p, u8p]),
                 "or_fdp_walk_bool": (i32, [u8p, u64, u8p, u64, u64, u8p, u8p]),
+                "or_fdp_disruption": (i32, [u8p, u64, u8p, u64, u64, u8p, u8p, u32, u32,
+                                            u8p, u8p, u8p, u8p]),
+                "or_fdp_disruption_bool": (i32, [u8p, u64, u8p, u64, u64, u32, u8p, u8p, u8p, u8p]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(lib, name)
@@ -276,6 +279,31 @@ def fdp_walk_bool(mom, kid, c: int) -> tuple[int, int]:
     if _load().or_fdp_walk_bool(_p(mom), len(mom), _p(kid), len(kid), c, _p(stop), _p(depth)):
         raise ValueError("malformed tree")
     return int(stop[0]), int(depth[0])
+
+
+def fdp_disruption(mom, kid, c: int, consts=None, x=None, max_levels: int = 4096, boolean: bool = False):
+    """Disruption along the FDP walk of one child (Fig. 4): per level (0 =
+    crossover point, up to the stop level or the root) the cases whose
+    child value differs from the mother's, those with both values finite,
+    and the binary64 sum of their squared differences.  Returns
+    (disrupted, finite, sum_sq, n_levels); the arrays hold
+    min(n_levels, max_levels) entries."""
+    mom, kid = _u8(mom), _u8(kid)
+    nd = np.zeros(max_levels, np.uint32)
+    nf = np.zeros(max_levels, np.uint32)
+    sq = np.zeros(max_levels, np.float64)
+    n = np.zeros(1, np.int64)
+    if boolean:
+        rc = _load().or_fdp_disruption_bool(_p(mom), len(mom), _p(kid), len(kid), c, max_levels,
+                                            _p(nd), _p(nf), _p(sq), _p(n))
+    else:
+        consts, x = _f32(consts), _f32(x)
+        rc = _load().or_fdp_disruption(_p(mom), len(mom), _p(kid), len(kid), c, _p(consts), _p(x), len(x),
+                                       max_levels, _p(nd), _p(nf), _p(sq), _p(n))
+    if rc:
+        raise ValueError("malformed tree")
+    k = min(int(n[0]), max_levels)
+    return nd[:k].copy(), nf[:k].copy(), sq[:k].copy(), int(n[0])
 
 
 def canon_nan(a: np.ndarray) -> np.ndarray:

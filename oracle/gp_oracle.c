@@ -387,3 +387,83 @@ int or_fdp_walk_bool(const uint8_t* mom, uint64_t n_m, const uint8_t* kid, uint6
     free(ends);
     return 0;
 }
+
+/* ---------------- disruption along the walk (Fig. 4) ---------------- */
+
+/* How a crossover's change of the test-case values fades along the chain of
+ * ancestors of the crossover point (Fig. 4: the number of disrupted cases
+ * and the RMS difference at each node of the chain).  For each level the
+ * FDP walk compares (level 0 = c, then each ancestor, up to and including
+ * the first level where the mother and the child agree on every case, or up
+ * to the root), with both nodes evaluated in full from the two trees:
+ *   disrupted[j] = cases whose child and mother values differ bit for bit;
+ *   finite[j]    = those of them where both values are finite;
+ *   sum_sq[j]    = sum over those finite cases, in case order, of
+ *                  ((double)child - (double)mother)^2 in binary64.
+ * Levels j < max_levels are written; *n = number of levels compared. */
+int or_fdp_disruption(const uint8_t* mom, uint64_t n_m, const uint8_t* kid, uint64_t n_k, uint64_t c,
+                      const float* k, const float* x, uint32_t C, uint32_t max_levels,
+                      uint32_t* disrupted, uint32_t* finite, double* sum_sq, int64_t* n) {
+    float* a = (float*)malloc(sizeof(float) * C);
+    float* b = (float*)malloc(sizeof(float) * C);
+    uint64_t* ends = (uint64_t*)malloc(sizeof(uint64_t) * n_m);
+    int64_t lvl = 0;
+    int64_t q = (int64_t)c;
+    if (or_tree_ends(mom, n_m, ends)) { free(a); free(b); free(ends); return -1; }
+    for (;;) {
+        if (or_eval_node_f32(mom, n_m, (uint64_t)q, k, x, C, a) ||
+            or_eval_node_f32(kid, n_k, (uint64_t)q, k, x, C, b)) { free(a); free(b); free(ends); return -1; }
+        uint32_t nd = 0, nf = 0;
+        double sq = 0.0;
+        for (uint32_t j = 0; j < C; ++j) {
+            uint32_t ua, ub;
+            memcpy(&ua, &a[j], 4);
+            memcpy(&ub, &b[j], 4);
+            if (ua == ub) continue;
+            ++nd;
+            if (isfinite(a[j]) && isfinite(b[j])) {
+                double df = (double)b[j] - (double)a[j];
+                ++nf;
+                sq += df * df;
+            }
+        }
+        if ((uint64_t)lvl < max_levels) { disrupted[lvl] = nd; finite[lvl] = nf; sum_sq[lvl] = sq; }
+        ++lvl;
+        if (nd == 0) break;                       /* the walk stops here */
+        int64_t p = parent_of(mom, ends, (uint64_t)q);
+        if (p < 0) break;                         /* the root differed */
+        q = p;
+    }
+    *n = lvl;
+    free(a); free(b); free(ends);
+    return 0;
+}
+
+/* The same for Boolean trees: each of the 64 cases is one bit of the node's
+ * word, a disrupted case is a differing bit and its difference is 1. */
+int or_fdp_disruption_bool(const uint8_t* mom, uint64_t n_m, const uint8_t* kid, uint64_t n_k, uint64_t c,
+                           uint32_t max_levels, uint32_t* disrupted, uint32_t* finite, double* sum_sq,
+                           int64_t* n) {
+    uint64_t* ends = (uint64_t*)malloc(sizeof(uint64_t) * n_m);
+    int64_t lvl = 0;
+    int64_t q = (int64_t)c;
+    if (or_tree_ends(mom, n_m, ends)) { free(ends); return -1; }
+    for (;;) {
+        uint64_t a, b;
+        if (or_eval_node_bool(mom, n_m, (uint64_t)q, &a) || or_eval_node_bool(kid, n_k, (uint64_t)q, &b)) {
+            free(ends);
+            return -1;
+        }
+        uint32_t nd = 0;
+        for (int t = 0; t < 64; ++t) nd += (uint32_t)(((a ^ b) >> t) & 1u);
+        if ((uint64_t)lvl < max_levels) { disrupted[lvl] = nd; finite[lvl] = nd; sum_sq[lvl] = (double)nd; }
+        ++lvl;
+        if (nd == 0) break;
+        int64_t p = parent_of(mom, ends, (uint64_t)q);
+        if (p < 0) break;
+        q = p;
+    }
+    *n = lvl;
+    free(ends);
+    return 0;
+}

@@ -97,6 +97,8 @@ def load() -> ctypes.CDLL:
         "gp_cache_value": (i32, [vp, u32, u32, vp, ctypes.c_size_t]),
         "gp_get_stats": (i32, [vp, ctypes.POINTER(GpStats)]),
         "gp_walk_info": (i32, [vp, vp, vp, u32]),
+        "gp_set_disruption": (i32, [vp, u32]),
+        "gp_disruption": (i32, [vp, vp, ctypes.c_size_t, vp]),
         "gp_pack_info": (i32, [vp, vp, vp, vp, vp, u32, vp]),
         "gp_mlp_eval_grad": (i32, [vp, vp, vp, u32, vp, vp]),
         "gp_eval_small_noalloc": (i32, [vp, ctypes.c_size_t, vp, u32, vp, vp, vp, u32, vp, vp, vp,
@@ -229,6 +231,25 @@ def gp_walk_info(h, n: int):
     lv = np.empty(n, np.uint32)
     _check(load().gp_walk_info(h, _ptr(stop), _ptr(lv), n), h)
     return stop, lv
+
+
+# one level of the disruption record (gp_disruption_level)
+DISRUPTION_DTYPE = np.dtype([("disrupted", np.uint32), ("finite", np.uint32), ("sum_sq", np.float64)])
+
+
+def gp_set_disruption(h, max_levels: int):
+    """Record up to max_levels walk levels per child in the following
+    incremental evaluations (0: off)."""
+    _check(load().gp_set_disruption(h, max_levels), h)
+
+
+def gp_disruption(h, n: int, max_levels: int):
+    """(records [n, max_levels] of DISRUPTION_DTYPE, levels recorded per child)
+    of the last incremental evaluation that recorded them (Fig. 4)."""
+    rec = np.zeros((n, max_levels), DISRUPTION_DTYPE)
+    nl = np.zeros(n, np.uint32)
+    _check(load().gp_disruption(h, _ptr(rec), rec.size, _ptr(nl)), h)
+    return rec, nl
 
 
 def gp_eval_small_noalloc(ops, off, x, t, consts, values, fitness, stream=None) -> int:
@@ -421,6 +442,13 @@ class Population:
 
     def pack_info(self):
         return gp_pack_info(self.h, self.P)
+
+    def set_disruption(self, max_levels: int):
+        gp_set_disruption(self.h, max_levels)
+        self.dis_levels = max_levels
+
+    def disruption(self):
+        return gp_disruption(self.h, self.P, getattr(self, "dis_levels", 0))
 
     def set_profiling(self, on: bool):
         gp_set_profiling(self.h, on)

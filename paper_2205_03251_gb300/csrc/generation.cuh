@@ -28,6 +28,13 @@ struct CacheView {
     const float* slots;
 };
 
+// one walk level of the disruption record: cases whose bits differ, those
+// with both values finite, and the sum of their squared differences (binary64)
+struct DisLevel {
+    uint32_t nd, nf;
+    double sq;
+};
+
 struct GenBufs {
     uint32_t *pbuf, *psize;          // parents (swapped with DevPop buf/size each generation)
     float* pfit;
@@ -76,6 +83,11 @@ struct GenBufs {
     uint32_t *nmother, *nfather, *ncpos, *nrsz, *ndpos, *nssz, *nflags;   // [P] next generation's plan
     uint32_t* sel;                   // [P] 1 for a child that is a parent of the next generation
     uint32_t* nfree;                 // [1] entries of the free-buffer stack (lazy mode: up to 2P)
+    // disruption diagnostics (Fig. 4): per child and walk level, the cases
+    // where the child's value differs from the mother's
+    DisLevel* dis;                   // [P][dis_L], null when not recording
+    uint32_t* dis_n;                 // [P] levels recorded
+    uint32_t dis_L;
     bool evaluated;
 };
 
@@ -983,6 +995,43 @@ __device__ bool walk_ancestors(const DevPop& d, const CacheView& par, uint32_t i
     return true;
 }
 
+// Disruption of one case between the child's value n and the mother's o:
+// bit patterns differ (Boolean: each differing bit is a case); for finite
+// pairs the squared difference, in binary64, joins the lane's sum.
+template <bool B>
+__device__ __forceinline__ void dis_case(float n, float o, uint32_t& nd, uint32_t& nf, double& sq) {
+    const uint32_t x = __float_as_uint(n) ^ __float_as_uint(o);
+    if (B) {
+        nd += __popc(x);
+    } else if (x) {
+        ++nd;
+        if (isfinite(n) && isfinite(o)) {
+            ++nf;
+            const double df = __dsub_rn((double)n, (double)o);
+            sq = __dadd_rn(sq, __dmul_rn(df, df));
+        }
+    }
+}
+
+// Warp-collective: sum the lanes' counts and squares, lane 0 stores level
+// `level` of child i (levels past the record's length are dropped).
+template <bool B>
+__device__ __forceinline__ void dis_store(const GenBufs& g, uint32_t i, uint32_t level, uint32_t nd, uint32_t nf,
+                                          double sq) {
+    nd = __reduce_add_sync(FULL, nd);
+    nf = __reduce_add_sync(FULL, nf);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sq = __dadd_rn(sq, __shfl_xor_sync(FULL, sq, o));
+    if (B) { nf = nd; sq = (double)nd; }
+    if (lane_id() == 0 && level < g.dis_L) {
+        DisLevel r;
+        r.nd = nd;
+        r.nf = nf;
+        r.sq = sq;
+        g.dis[(size_t)i * g.dis_L + level] = r;
+    }
+}
+
 // Bottom-up incremental evaluation of one child per team of nw warps
 // (Sec. 6.2, Fig. 3).  Level 0 compares the donated subtree's value with
 // the removed subtree's; each higher level combines the running values with
@@ -1045,9 +1094,20 @@ __global__ void __launch_bounds__(256, 2) k_walk(DevPop d, GenBufs g, CacheView 
         const uint32_t i = g.order[qi];
         const uint32_t fl = g.flags[i];
         const uint32_t m = g.mother[i];
-        if (tid == 0) { g.walkA[i] = -1; g.nins[i] = 0; g.pv_cnt[i] = 0; }
+        if (tid == 0) {
+            g.walkA[i] = -1; g.nins[i] = 0; g.pv_cnt[i] = 0;
+            if (g.dis) g.dis_n[i] = 0;
+        }
         if (fl & F_CLONE) {
-            if (tid == 0) { d.fit[i] = g.pfit[m]; g.stop[i] = 0; g.plen[i] = 0; ++st_stopped; }
+            if (tid == 0) {
+                d.fit[i] = g.pfit[m]; g.stop[i] = 0; g.plen[i] = 0; ++st_stopped;
+                if (g.dis) {
+                    DisLevel z;
+                    z.nd = 0; z.nf = 0; z.sq = 0.0;
+                    g.dis[(size_t)i * g.dis_L] = z;
+                    g.dis_n[i] = 1;
+                }
+            }
             continue;
         }
         const uint32_t f = g.father[i], c = g.cpos[i], r = g.rsz[i], dd = g.dpos[i], s = g.ssz[i];
@@ -1065,7 +1125,7 @@ __global__ void __launch_bounds__(256, 2) k_walk(DevPop d, GenBufs g, CacheView 
         // pass over the whole child costs less than a walk of its levels (same
         // values, bit for bit); its root value is recorded when it differs from
         // the mother's (or is a new root made of a small donated subtree)
-        if (nk < T) {
+        if (nk < T && !g.dis) {
             for (uint32_t cb = warp; cb < ncb; cb += nw) {
                 load_cases<K>(d, cb, ic.xv);
                 float v[K];
@@ -1217,6 +1277,12 @@ __global__ void __launch_bounds__(256, 2) k_walk(DevPop d, GenBufs g, CacheView 
         int32_t stop_level_w = stop_level;
         uint32_t levels_w = 0;
         if (warp == 0) {
+            if (g.dis) {                                   // level 0 of the disruption record
+                uint32_t nd = 0, nf = 0;
+                double sq = 0.0;
+                for (uint32_t j = lane; j < Cn; j += 32) dis_case<B>(nvs[j], ovs[j], nd, nf, sq);
+                dis_store<B>(g, i, 0, nd, nf, sq);
+            }
             uint32_t bq = c, bqend = c + s, bk = 0;        // builder state (lane 0)
             int32_t bpe = (nsmall > 0) ? -1 : A;
             bool btop = false;
@@ -1316,6 +1382,8 @@ __global__ void __launch_bounds__(256, 2) k_walk(DevPop d, GenBufs g, CacheView 
                 const float* svl = svs + slot * Cpad;
                 const float* pvv = mvs + slot * Cpad;
                 bool okl = true;
+                uint32_t dnd = 0, dnf = 0;
+                double dsq = 0.0;
                 for (uint32_t j = lane; j < Cpad; j += 32) {
                     float o[1] = {ovs[j]};
                     const float sv1[1] = {svl[j]};
@@ -1326,10 +1394,12 @@ __global__ void __launch_bounds__(256, 2) k_walk(DevPop d, GenBufs g, CacheView 
                         nvs[j] = n1[0];
                         if (D.pent >= 0) o[0] = pvv[j];
                         if (j < Cn && __float_as_uint(n1[0]) != __float_as_uint(o[0])) okl = false;
+                        if (g.dis && j < Cn) dis_case<B>(n1[0], o[0], dnd, dnf, dsq);
                     }
                     ovs[j] = o[0];
                 }
                 const bool lvl_eq = __all_sync(FULL, okl);
+                if (g.dis && !stopped_w) dis_store<B>(g, i, level, dnd, dnf, dsq);
                 __syncwarp();
                 if (!stopped_w) {
                     ++levels_w;
@@ -1426,6 +1496,7 @@ __global__ void __launch_bounds__(256, 2) k_walk(DevPop d, GenBufs g, CacheView 
         if (tid == 0) {
             g.stop[i] = stop_level;
             g.plen[i] = levels;
+            if (g.dis) g.dis_n[i] = min(levels + 1, g.dis_L);
             g.pv_cnt[i] = npv;
             g.nins[i] = nins_i;
             g.walkA[i] = A;

@@ -2,6 +2,7 @@
 #include "gpfdp.h"
 
 #include <cstdarg>
+#include <cstddef>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -15,6 +16,10 @@
 #include "interp.cuh"
 #include "eval_full.cuh"
 #include "generation.cuh"
+
+static_assert(sizeof(DisLevel) == sizeof(gp_disruption_level) &&
+                  offsetof(DisLevel, sq) == offsetof(gp_disruption_level, sum_sq),
+              "disruption record layout");
 
 namespace {
 
@@ -98,6 +103,8 @@ struct gp_pop {
     uint32_t planned_gen;             // ... for this generation number
     bool lazy_pending;                // some individuals exist only through their parents
     uint32_t host_nfree;              // pageable source of the free-stack count upload
+    // disruption diagnostics
+    bool dis_valid;                   // the last walk recorded into gb.dis
 };
 
 namespace {
@@ -609,6 +616,10 @@ int gp_pop_create(const gp_config* cfg_in, const float* x, const float* targets,
         g.seed = cfg.seed;
         g.gen = 0;
         g.evaluated = false;
+        g.dis = nullptr;
+        g.dis_n = nullptr;
+        g.dis_L = 0;
+        pop->dis_valid = false;
         DA2(pop->gwords, 4);
         cudaMemset(pop->gwords, 0, 4 * sizeof(uint32_t));
         g.gen_add = pop->gwords;
@@ -705,6 +716,7 @@ void gp_pop_destroy(gp_pop* pop) {
     if (pop->stream) cudaStreamSynchronize(pop->stream); else cudaDeviceSynchronize();
     if (pop->gexec) cudaGraphExecDestroy(pop->gexec);
     if (pop->cap_stream) cudaStreamDestroy(pop->cap_stream);
+    cudaFree(pop->gb.dis); cudaFree(pop->gb.dis_n);
     cudaFree(pop->pool); cudaFree(pop->live); cudaFree(pop->freeslot); cudaFree(pop->ftile);
     for (void* p : pop->allocs) cudaFree(p);
     for (int w = 0; w < 2; ++w) for (void* p : pop->sets[w].allocs) cudaFree(p);
@@ -830,6 +842,7 @@ int gp_graph_capture(gp_pop* pop, uint32_t first_generation, uint32_t n_generati
     const int cur0 = pop->cur;
     const uint32_t calls0 = pop->cum_calls;
     const int kind0 = pop->last_kind;
+    const bool dis0 = pop->dis_valid;
     const bool plan0 = pop->have_next_plan, pend0 = pop->lazy_pending;
     const uint32_t pgen0 = pop->planned_gen;
     pop->capturing = true;
@@ -857,6 +870,7 @@ int gp_graph_capture(gp_pop* pop, uint32_t first_generation, uint32_t n_generati
     pop->lazy_pending = pend0;
     pop->planned_gen = pgen0;
     pop->last_kind = kind0;
+    pop->dis_valid = dis0;
     pop->have_children = false;
     if (r != GP_OK) { if (graph) cudaGraphDestroy(graph); cudaGetLastError(); return r; }
     if (ce != cudaSuccess) { cudaGetLastError(); return fail(pop, GP_ECUDA, "stream capture failed: %s", cudaGetErrorString(ce)); }
@@ -885,6 +899,7 @@ int gp_graph_launch(gp_pop* pop) {
     pop->stats_graph = pop->graph_prof && pop->profiling;
     pop->launches = pop->graph_launches;
     pop->last_kind = 1;
+    pop->dis_valid = pop->gb.dis != nullptr;
     return GP_OK;
 }
 
@@ -1049,6 +1064,46 @@ int gp_walk_info(const gp_pop* cpop, int32_t* stop_level, uint32_t* levels, uint
     if (rc) return rc;
     if (stop_level) CK(cudaMemcpy(stop_level, pop->gb.stop, sizeof(int32_t) * n, cudaMemcpyDeviceToHost));
     if (levels) CK(cudaMemcpy(levels, pop->gb.plen, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost));
+    return GP_OK;
+}
+
+int gp_set_disruption(gp_pop* pop, uint32_t max_levels) {
+    if (!pop) return GP_EINVAL;
+    if (max_levels > 65536u) return fail(pop, GP_EINVAL, "max_levels %u > 65536", max_levels);
+    GenBufs& g = pop->gb;
+    if (pop->stream) CK(cudaStreamSynchronize(pop->stream)); else CK(cudaDeviceSynchronize());
+    if (pop->gexec) { cudaGraphExecDestroy(pop->gexec); pop->gexec = nullptr; pop->graph_n = 0; }
+    cudaFree(g.dis);
+    cudaFree(g.dis_n);
+    g.dis = nullptr;
+    g.dis_n = nullptr;
+    g.dis_L = 0;
+    pop->dis_valid = false;
+    if (max_levels == 0) return GP_OK;
+    const size_t n = (size_t)pop->d.P * max_levels;
+    if (cudaMalloc(&g.dis, n * sizeof(DisLevel)) != cudaSuccess ||
+        cudaMalloc(&g.dis_n, (size_t)pop->d.P * sizeof(uint32_t)) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(g.dis); cudaFree(g.dis_n);
+        g.dis = nullptr; g.dis_n = nullptr;
+        return fail(pop, GP_ENOMEM, "disruption records of %zu levels do not fit", n);
+    }
+    CK(cudaMemset(g.dis_n, 0, (size_t)pop->d.P * sizeof(uint32_t)));
+    g.dis_L = max_levels;
+    return GP_OK;
+}
+
+int gp_disruption(const gp_pop* cpop, gp_disruption_level* records, size_t n, uint32_t* n_levels) {
+    gp_pop* pop = const_cast<gp_pop*>(cpop);
+    if (!pop) return GP_EINVAL;
+    if (pop->last_kind != 1 || !pop->dis_valid || !pop->gb.dis)
+        return fail(pop, GP_ESTATE, "no incremental evaluation has recorded disruption since gp_set_disruption");
+    const size_t need = (size_t)pop->d.P * pop->gb.dis_L;
+    if (records && n < need) return fail(pop, GP_EINVAL, "records holds %zu < %zu entries", n, need);
+    int rc = check_status(pop);
+    if (rc) return rc;
+    if (records) CK(cudaMemcpy(records, pop->gb.dis, need * sizeof(DisLevel), cudaMemcpyDeviceToHost));
+    if (n_levels) CK(cudaMemcpy(n_levels, pop->gb.dis_n, sizeof(uint32_t) * pop->d.P, cudaMemcpyDeviceToHost));
     return GP_OK;
 }
 
@@ -1314,6 +1369,7 @@ int gen_incremental(gp_pop* pop) {
     pop->have_children = false;
     g.evaluated = true;
     pop->last_kind = 1;
+    pop->dis_valid = g.dis != nullptr;
     if (g.lazy) {
         pop->have_next_plan = true;
         pop->planned_gen = g.gen + 1;
