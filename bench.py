@@ -391,6 +391,32 @@ def run_packing(args):
     print(json.dumps(line), flush=True)
 
 
+def disruption_profile(pop, gen_step, n_cases, max_levels=1024, show=24):
+    """Fig. 4 over one whole generation, run after the measurements (not
+    timed): for each distance from the crossover point (level 0 = the
+    crossover point, level j = its j-th ancestor), how many children's walks
+    compared that level, the mean fraction of their test cases that differ
+    from the mother's value there, and the RMS difference over the disrupted
+    cases with finite values."""
+    pop.set_disruption(max_levels)
+    gen_step()
+    rec, nl = pop.disruption()
+    pop.set_disruption(0)
+    nl = nl.astype(np.int64)
+    out = {"levels": [], "children": [], "disrupted_fraction": [], "rms": [],
+           "mean_levels_compared": float(nl.mean()), "max_levels_compared": int(nl.max()),
+           "note": "one eager generation after the timed region, recording on"}
+    for j in range(min(show, int(nl.max()))):
+        mask = nl > j
+        r = rec[mask, j]
+        nf = int(r["finite"].sum())
+        out["levels"].append(j)
+        out["children"].append(int(mask.sum()))
+        out["disrupted_fraction"].append(float(r["disrupted"].mean()) / n_cases)
+        out["rms"].append(float(np.sqrt(r["sum_sq"].sum() / nf)) if nf else None)
+    return out
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -599,6 +625,8 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MIN)
         e2e["value"] = float(t.item()) * world
     line["e2e"] = e2e
+    if generational:
+        line["disruption"] = disruption_profile(pop, gen_step, 64 if args.boolean else args.cases)
     pop.close()
     if rank == 0:
         if not args.no_cpu and world == 1:
