@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--cases", type=int, default=48)
     ap.add_argument("--boolean", action="store_true", help="uneven workload on the 6-multiplexer")
     ap.add_argument("--threshold", type=int, default=1024)
+    ap.add_argument("--cases-per-lane", type=int, default=0, choices=[0, 1, 2, 4], help="0: automatic")
+    ap.add_argument("--walk-team", type=int, default=0, choices=[0, 1, 2, 4, 8], help="warps per child; 0: automatic")
     ap.add_argument("--packing", default="mlp", choices=list(PACKING))
     ap.add_argument("--lazy", dest="lazy", action="store_true", default=True,
                     help="fitness-first order (default): build only the children selected as parents")
@@ -397,23 +399,26 @@ def disruption_profile(pop, gen_step, n_cases, max_levels=1024, show=24):
     crossover point, level j = its j-th ancestor), how many children's walks
     compared that level, the mean fraction of their test cases that differ
     from the mother's value there, and the RMS difference over the disrupted
-    cases with finite values."""
+    cases with finite values (median over the children)."""
     pop.set_disruption(max_levels)
     gen_step()
     rec, nl = pop.disruption()
     pop.set_disruption(0)
     nl = nl.astype(np.int64)
-    out = {"levels": [], "children": [], "disrupted_fraction": [], "rms": [],
+    out = {"levels": [], "children": [], "disrupted_fraction": [], "rms_median": [],
            "mean_levels_compared": float(nl.mean()), "max_levels_compared": int(nl.max()),
            "note": "one eager generation after the timed region, recording on"}
     for j in range(min(show, int(nl.max()))):
         mask = nl > j
         r = rec[mask, j]
-        nf = int(r["finite"].sum())
+        fin = r["finite"] > 0
         out["levels"].append(j)
         out["children"].append(int(mask.sum()))
         out["disrupted_fraction"].append(float(r["disrupted"].mean()) / n_cases)
-        out["rms"].append(float(np.sqrt(r["sum_sq"].sum() / nf)) if nf else None)
+        # per-child RMS over its disrupted finite cases; the median, since the
+        # differences span dozens of orders of magnitude (Fig. 4 colours them on a log scale)
+        rms = np.sqrt(r["sum_sq"][fin] / r["finite"][fin])
+        out["rms_median"].append(float(np.median(rms)) if len(rms) else None)
     return out
 
 
@@ -443,7 +448,8 @@ def main():
     boolean = bool(w.get("boolean"))
     maxn = w.get("max_nodes", 1 << 21)
     pop_kw = {"cache_threshold": args.threshold, "packing": PACKING[args.packing],
-              "cache_budget_bytes": args.cache_budget_gb << 30, "lazy": args.lazy}
+              "cache_budget_bytes": args.cache_budget_gb << 30, "lazy": args.lazy,
+              "cases_per_lane": args.cases_per_lane, "walk_team": args.walk_team}
     tune = None
     if args.workload == "uneven" and args.autotune:
         ks = (1,) if boolean else ((1, 2) if args.cases <= 64 else (2, 4))
@@ -536,6 +542,10 @@ def main():
     line["config"]["packing"] = args.packing
     line["config"]["children"] = ("fitness-first: only the children selected as parents are built"
                                   if args.lazy else "every child built at crossover")
+    if args.cases_per_lane:
+        line["config"]["cases_per_lane"] = args.cases_per_lane
+    if args.walk_team:
+        line["config"]["walk_team"] = args.walk_team
     if tune:
         line["config"]["cases_per_lane"] = pop_kw["cases_per_lane"]
         line["config"]["cache_threshold"] = pop_kw["cache_threshold"]

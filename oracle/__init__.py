@@ -71,6 +71,17 @@ def _load():
                 "or_fdp_disruption": (i32, [u8p, u64, u8p, u64, u64, u8p, u8p, u32, u32,
                                             u8p, u8p, u8p, u8p]),
                 "or_fdp_disruption_bool": (i32, [u8p, u64, u8p, u64, u64, u32, u8p, u8p, u8p, u8p]),
+                "or_mux_inputs_count": (u32, [u32]),
+                "or_mux_words": (u64, [u32]),
+                "or_mux_input_word": (u64, [u32, u64]),
+                "or_mux_target_word": (u64, [u32, u64]),
+                "or_eval_node_mux": (i32, [u8p, u64, u64, u32, u8p]),
+                "or_fitness_mux": (u64, [u8p, u32]),
+                "or_eval_node_i32": (i32, [u8p, u64, u64, u8p, u8p, u32, u8p]),
+                "or_fitness_i32": (f32, [u8p, u8p, u32]),
+                "or_fdp_walk_mux": (i32, [u8p, u64, u8p, u64, u64, u32, u32, u8p, u8p, u8p, u8p, u8p, u8p]),
+                "or_fdp_walk_i32": (i32, [u8p, u64, u8p, u64, u64, u8p, u8p, u32, u32, u8p, u8p, u8p, u8p, u8p,
+                                          u8p]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(lib, name)
@@ -205,6 +216,115 @@ def eval_pop_bool(ops, off):
         words[i] = w
         errs[i] = fitness_bool(w)
     return words, errs
+
+
+# ---------------------------------------------------------------- wide Boolean (k-multiplexer)
+
+def mux_words(k: int) -> int:
+    """64-case words of the k-multiplexer (k = 2: 6-mux, 1 word; k = 3: 11-mux, 32 words)."""
+    return int(_load().or_mux_words(k))
+
+
+def mux_input_words(k: int) -> np.ndarray:
+    """[inputs, words] uint64: word w of input j (a0.. then d0..)."""
+    ni = int(_load().or_mux_inputs_count(k))
+    nw = mux_words(k)
+    return np.array([[_load().or_mux_input_word(j, w) for w in range(nw)] for j in range(ni)], np.uint64)
+
+
+def mux_target_words(k: int) -> np.ndarray:
+    return np.array([_load().or_mux_target_word(k, w) for w in range(mux_words(k))], np.uint64)
+
+
+def eval_node_mux(ops, i: int, k: int) -> np.ndarray:
+    ops = _u8(ops)
+    out = np.zeros(mux_words(k), np.uint64)
+    if _load().or_eval_node_mux(_p(ops), len(ops), i, k, _p(out)):
+        raise ValueError("malformed multiplexer tree")
+    return out
+
+
+def fitness_mux(words, k: int) -> int:
+    words = np.ascontiguousarray(words, np.uint64)
+    return int(_load().or_fitness_mux(_p(words), k))
+
+
+def eval_pop_mux(ops, off, k: int):
+    """Root words (P, words) and error counts (P,)."""
+    ops = _u8(ops)
+    off = np.asarray(off, np.uint64)
+    P = len(off) - 1
+    words = np.empty((P, mux_words(k)), np.uint64)
+    errs = np.empty(P, np.uint64)
+    for i in range(P):
+        words[i] = eval_node_mux(ops[int(off[i]):int(off[i + 1])], 0, k)
+        errs[i] = fitness_mux(words[i], k)
+    return words, errs
+
+
+def fdp_walk_mux(mom, kid, c: int, k: int, max_levels: int = 0):
+    """(stop, depth) of the FDP walk on k-multiplexer trees, and with
+    max_levels > 0 the disruption record (disrupted, finite, sum_sq, levels)."""
+    mom, kid = _u8(mom), _u8(kid)
+    L = max(1, max_levels)
+    nd, nf = np.zeros(L, np.uint32), np.zeros(L, np.uint32)
+    sq = np.zeros(L, np.float64)
+    stop, depth, nl = np.zeros(1, np.int64), np.zeros(1, np.int64), np.zeros(1, np.int64)
+    if _load().or_fdp_walk_mux(_p(mom), len(mom), _p(kid), len(kid), c, k, max_levels, _p(nd), _p(nf), _p(sq),
+                               _p(stop), _p(depth), _p(nl)):
+        raise ValueError("malformed tree")
+    if not max_levels:
+        return int(stop[0]), int(depth[0])
+    n = min(int(nl[0]), max_levels)
+    return int(stop[0]), int(depth[0]), (nd[:n].copy(), nf[:n].copy(), sq[:n].copy(), int(nl[0]))
+
+
+# ---------------------------------------------------------------- integer GP
+
+def _i32(a):
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+def eval_node_i32(ops, i: int, consts, x) -> np.ndarray:
+    ops, consts, x = _u8(ops), _i32(consts), _i32(x)
+    out = np.zeros(len(x), np.int32)
+    if _load().or_eval_node_i32(_p(ops), len(ops), i, _p(consts), _p(x), len(x), _p(out)):
+        raise ValueError("malformed tree")
+    return out
+
+
+def fitness_i32(v, t) -> np.float32:
+    v, t = _i32(v), _i32(t)
+    return np.float32(_load().or_fitness_i32(_p(v), _p(t), len(v)))
+
+
+def eval_pop_i32(ops, off, consts, x, t):
+    """Root values (P, C) int32 and fitness (P,) float32."""
+    ops = _u8(ops)
+    off = np.asarray(off, np.uint64)
+    P = len(off) - 1
+    vals = np.empty((P, len(x)), np.int32)
+    fit = np.empty(P, np.float32)
+    for i in range(P):
+        vals[i] = eval_node_i32(ops[int(off[i]):int(off[i + 1])], 0, consts, x)
+        fit[i] = fitness_i32(vals[i], t)
+    return vals, fit
+
+
+def fdp_walk_i32(mom, kid, c: int, consts, x, max_levels: int = 0):
+    """As fdp_walk_mux, for integer trees."""
+    mom, kid, consts, x = _u8(mom), _u8(kid), _i32(consts), _i32(x)
+    L = max(1, max_levels)
+    nd, nf = np.zeros(L, np.uint32), np.zeros(L, np.uint32)
+    sq = np.zeros(L, np.float64)
+    stop, depth, nl = np.zeros(1, np.int64), np.zeros(1, np.int64), np.zeros(1, np.int64)
+    if _load().or_fdp_walk_i32(_p(mom), len(mom), _p(kid), len(kid), c, _p(consts), _p(x), len(x), max_levels,
+                               _p(nd), _p(nf), _p(sq), _p(stop), _p(depth), _p(nl)):
+        raise ValueError("malformed tree")
+    if not max_levels:
+        return int(stop[0]), int(depth[0])
+    n = min(int(nl[0]), max_levels)
+    return int(stop[0]), int(depth[0]), (nd[:n].copy(), nf[:n].copy(), sq[:n].copy(), int(nl[0]))
 
 
 # ---------------------------------------------------------------- selection / crossover

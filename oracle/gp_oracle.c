@@ -237,6 +237,127 @@ uint32_t or_fitness_bool(uint64_t out) {
     return c;
 }
 
+/* ---------------- wide Boolean: the k-multiplexer (Sec. 4.2) ----------------
+ *
+ * k address lines a0..a(k-1) and 2^k data lines d0..d(2^k - 1) are the
+ * inputs 0 .. k + 2^k - 1 (opcodes 4 ..); case i (0 <= i < 2^(k + 2^k))
+ * gives input j the value of bit j of i, and the target is the data line
+ * the address selects: bit k + a of i, a = sum over j < k of a_j 2^j.  The
+ * 6-multiplexer is k = 2 (64 cases), the 11-multiplexer k = 3 (2,048
+ * cases).  Cases are packed 64 to a word: word w holds cases 64w .. 64w+63,
+ * case 64w + b in bit b.  The Boolean functions act on whole words at once,
+ * the bit-parallel evaluation of Sec. 4.2 widened to any number of words. */
+
+uint32_t or_mux_inputs_count(uint32_t k) { return k + (1u << k); }
+
+uint64_t or_mux_words(uint32_t k) { return ((uint64_t)1 << (k + (1u << k))) / 64; }
+
+/* word w of input j */
+uint64_t or_mux_input_word(uint32_t j, uint64_t w) {
+    uint64_t x = 0;
+    for (uint32_t b = 0; b < 64; ++b)
+        if (((64 * w + b) >> j) & 1) x |= (uint64_t)1 << b;
+    return x;
+}
+
+/* word w of the target */
+uint64_t or_mux_target_word(uint32_t k, uint64_t w) {
+    uint64_t x = 0;
+    for (uint32_t b = 0; b < 64; ++b) {
+        uint64_t i = 64 * w + b, a = 0;
+        for (uint32_t j = 0; j < k; ++j) a |= ((i >> j) & 1) << j;
+        if ((i >> (k + a)) & 1) x |= (uint64_t)1 << b;
+    }
+    return x;
+}
+
+static uint64_t evmux(const uint8_t* ops, uint64_t* pos, const uint64_t* in) {
+    uint8_t o = ops[(*pos)++];
+    if (o >= 4) return in[o - 4];
+    uint64_t a = evmux(ops, pos, in);
+    uint64_t b = evmux(ops, pos, in);
+    switch (o) {
+    case 0: return a & b;
+    case 1: return a | b;
+    case 2: return ~(a & b);
+    default: return ~(a | b);
+    }
+}
+
+/* Value words of the subtree at node i: one pass per word (64 cases). */
+int or_eval_node_mux(const uint8_t* ops, uint64_t n, uint64_t i, uint32_t k, uint64_t* out) {
+    uint64_t s = size_rec(ops, n, i);
+    uint32_t ni = or_mux_inputs_count(k);
+    uint64_t in[64];
+    if (!s || ni > 64) return -1;
+    for (uint64_t p = i; p < i + s; ++p) if (ops[p] >= 4 + ni) return -1;
+    for (uint64_t w = 0; w < or_mux_words(k); ++w) {
+        for (uint32_t j = 0; j < ni; ++j) in[j] = or_mux_input_word(j, w);
+        uint64_t pos = i;
+        out[w] = evmux(ops, &pos, in);
+    }
+    return 0;
+}
+
+/* Errors: number of cases the words get wrong. */
+uint64_t or_fitness_mux(const uint64_t* out, uint32_t k) {
+    uint64_t c = 0;
+    for (uint64_t w = 0; w < or_mux_words(k); ++w) {
+        uint64_t e = out[w] ^ or_mux_target_word(k, w);
+        for (int b = 0; b < 64; ++b) c += (e >> b) & 1;
+    }
+    return c;
+}
+
+/* ---------------- integer GP ----------------
+ *
+ * The same prefix trees over 32-bit signed integers: + - * wrap around
+ * modulo 2^32 (two's complement); protected division returns 1 for a zero
+ * divisor, the wrapped quotient INT32_MIN for INT32_MIN / -1, and otherwise
+ * the quotient truncated toward zero.  Opcodes 5..255 index a table of 251
+ * integer constants.  Fitness = sum over cases of |value - target|, exact in
+ * 64-bit integers, then rounded once to binary32 (the population's fitness
+ * type; equal sums give equal fitness). */
+
+static int32_t wrap32(uint32_t u) { return (int32_t)u; }   /* gcc: modulo 2^32 */
+
+static int32_t evi(const uint8_t* ops, uint64_t* pos, const int32_t* k, int32_t x) {
+    uint8_t o = ops[(*pos)++];
+    if (o == 4) return x;
+    if (o >= 5) return k[o - 5];
+    int32_t a = evi(ops, pos, k, x);
+    int32_t b = evi(ops, pos, k, x);
+    switch (o) {
+    case 0: return wrap32((uint32_t)a + (uint32_t)b);
+    case 1: return wrap32((uint32_t)a - (uint32_t)b);
+    case 2: return wrap32((uint32_t)a * (uint32_t)b);
+    default:
+        if (b == 0) return 1;
+        if (a == INT32_MIN && b == -1) return INT32_MIN;
+        return a / b;
+    }
+}
+
+int or_eval_node_i32(const uint8_t* ops, uint64_t n, uint64_t i, const int32_t* k,
+                     const int32_t* x, uint32_t C, int32_t* out) {
+    uint64_t s = size_rec(ops, n, i);
+    if (!s) return -1;
+    for (uint32_t c = 0; c < C; ++c) {
+        uint64_t pos = i;
+        out[c] = evi(ops, &pos, k, x[c]);
+    }
+    return 0;
+}
+
+float or_fitness_i32(const int32_t* v, const int32_t* t, uint32_t C) {
+    int64_t f = 0;
+    for (uint32_t c = 0; c < C; ++c) {
+        int64_t e = (int64_t)v[c] - (int64_t)t[c];
+        f += e < 0 ? -e : e;
+    }
+    return (float)f;
+}
+
 /* ---------------- random numbers ---------------- */
 
 /* SplitMix64 (Steele, Lea and Flood, OOPSLA 2014): the output for element
@@ -466,4 +587,98 @@ int or_fdp_disruption_bool(const uint8_t* mom, uint64_t n_m, const uint8_t* kid,
     *n = lvl;
     free(ends);
     return 0;
+}
+
+/* ---------------- the walk for the wide Boolean and integer sets ---------------- */
+
+/* Value vector of node i for one function set: `ctx` carries the set's
+ * parameters, `out` receives vbytes bytes. */
+typedef int (*node_fn)(const uint8_t* ops, uint64_t n, uint64_t i, const void* ctx, void* out);
+
+typedef struct { uint32_t k; } mux_ctx;
+typedef struct { const int32_t* k; const int32_t* x; uint32_t C; } i32_ctx;
+
+static int mux_node(const uint8_t* ops, uint64_t n, uint64_t i, const void* ctx, void* out) {
+    return or_eval_node_mux(ops, n, i, ((const mux_ctx*)ctx)->k, (uint64_t*)out);
+}
+
+static int i32_node(const uint8_t* ops, uint64_t n, uint64_t i, const void* ctx, void* out) {
+    const i32_ctx* c = (const i32_ctx*)ctx;
+    return or_eval_node_i32(ops, n, i, c->k, c->x, c->C, (int32_t*)out);
+}
+
+/* The FDP walk of Sec. 6.2 for any set (see or_fdp_walk), comparing whole
+ * value vectors bit for bit; with `profile` set, also the disruption record
+ * (see or_fdp_disruption): kind 1 = Boolean words (a differing bit is a
+ * disrupted case with difference 1), kind 2 = int32 cases (difference
+ * child - mother exact in 64-bit integers, squared in binary64). */
+static int fdp_walk_any(const uint8_t* mom, uint64_t n_m, const uint8_t* kid, uint64_t n_k, uint64_t c,
+                        node_fn fn, const void* ctx, size_t vbytes, int kind, uint32_t max_levels,
+                        uint32_t* disrupted, uint32_t* finite, double* sum_sq, int64_t* stop, int64_t* depth,
+                        int64_t* nlev) {
+    uint8_t* a = (uint8_t*)malloc(vbytes);
+    uint8_t* b = (uint8_t*)malloc(vbytes);
+    uint64_t* ends = (uint64_t*)malloc(sizeof(uint64_t) * n_m);
+    int64_t lvl = 0, found = -1, rec = 0;
+    int64_t q = (int64_t)c;
+    if (or_tree_ends(mom, n_m, ends)) { free(a); free(b); free(ends); return -1; }
+    while (q >= 0) {
+        if (found < 0) {
+            if (fn(mom, n_m, (uint64_t)q, ctx, a) || fn(kid, n_k, (uint64_t)q, ctx, b)) {
+                free(a); free(b); free(ends);
+                return -1;
+            }
+            uint32_t nd = 0, nf = 0;
+            double sq = 0.0;
+            if (kind == 1) {
+                for (size_t w = 0; w < vbytes / 8; ++w) {
+                    uint64_t x, y;
+                    memcpy(&x, a + 8 * w, 8);
+                    memcpy(&y, b + 8 * w, 8);
+                    for (int t = 0; t < 64; ++t) nd += (uint32_t)(((x ^ y) >> t) & 1u);
+                }
+                nf = nd;
+                sq = (double)nd;
+            } else {
+                for (size_t j = 0; j < vbytes / 4; ++j) {
+                    int32_t x, y;
+                    memcpy(&x, a + 4 * j, 4);
+                    memcpy(&y, b + 4 * j, 4);
+                    if (x == y) continue;
+                    double df = (double)((int64_t)y - (int64_t)x);
+                    ++nd;
+                    ++nf;
+                    sq += df * df;
+                }
+            }
+            if (disrupted && (uint64_t)lvl < max_levels) { disrupted[lvl] = nd; finite[lvl] = nf; sum_sq[lvl] = sq; }
+            rec = lvl + 1;
+            if (nd == 0) found = lvl;
+        }
+        int64_t p = parent_of(mom, ends, (uint64_t)q);
+        if (p < 0) break;
+        q = p;
+        ++lvl;
+    }
+    *stop = found;
+    *depth = lvl;
+    if (nlev) *nlev = rec;
+    free(a); free(b); free(ends);
+    return 0;
+}
+
+int or_fdp_walk_mux(const uint8_t* mom, uint64_t n_m, const uint8_t* kid, uint64_t n_k, uint64_t c,
+                    uint32_t k, uint32_t max_levels, uint32_t* disrupted, uint32_t* finite, double* sum_sq,
+                    int64_t* stop, int64_t* depth, int64_t* nlev) {
+    mux_ctx ctx = {k};
+    return fdp_walk_any(mom, n_m, kid, n_k, c, mux_node, &ctx, 8 * or_mux_words(k), 1, max_levels,
+                        disrupted, finite, sum_sq, stop, depth, nlev);
+}
+
+int or_fdp_walk_i32(const uint8_t* mom, uint64_t n_m, const uint8_t* kid, uint64_t n_k, uint64_t c,
+                    const int32_t* kt, const int32_t* x, uint32_t C, uint32_t max_levels, uint32_t* disrupted,
+                    uint32_t* finite, double* sum_sq, int64_t* stop, int64_t* depth, int64_t* nlev) {
+    i32_ctx ctx = {kt, x, C};
+    return fdp_walk_any(mom, n_m, kid, n_k, c, i32_node, &ctx, 4 * (size_t)C, 2, max_levels,
+                        disrupted, finite, sum_sq, stop, depth, nlev);
 }

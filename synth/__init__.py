@@ -85,14 +85,18 @@ def consts(seed: int) -> np.ndarray:
 
 
 def population(kind: str, seed: int, n_trees: int, *, boolean: bool = False,
-               target: int = 0, sizes=None, cap: int | None = None, threads: int | None = None):
+               target: int = 0, sizes=None, cap: int | None = None, threads: int | None = None,
+               n_inputs: int = 6):
     """Generate ``n_trees`` trees.  Returns ``(ops, off)``: all trees
     concatenated (uint8) and ``off`` (uint64, n_trees+1) with tree i at
     ``ops[off[i]:off[i+1]]``.
 
     kind='rhh' ignores target/sizes; kind='big' grows to ``target`` nodes;
-    kind='remy' builds trees with the given total ``sizes`` (odd)."""
+    kind='remy' builds trees with the given total ``sizes`` (odd).  Boolean
+    trees take their leaves uniformly from ``n_inputs`` inputs (opcodes 4..)."""
     lib = _load()
+    if boolean:
+        boolean = 1 if n_inputs == 6 else int(n_inputs)
     nint = None
     if kind == "rhh":
         cap = cap or 8192
@@ -137,6 +141,54 @@ def log_uniform_sizes(seed: int, n_trees: int, lo: float = 1e1, hi: float = 1e6)
     s = np.exp(np.log(lo) + u * (np.log(hi) - np.log(lo)))
     n = np.maximum(1, np.floor((s - 1) / 2)).astype(np.uint64)
     return 2 * n + 1
+
+
+def cases_int(seed: int, n_cases: int, lo: int = -8, hi: int = 8):
+    """Integer test cases x uniform in [lo, hi] and the sextic target
+    x^2 (x^2 - 1)^2, exact in integers (int32 for |x| <= 8)."""
+    lib = _load()
+    span = hi - lo + 1
+    x = np.array([lo + (lib.synth_draw(seed ^ 0x1A7E000000000001, i) >> 32) * span // (1 << 32)
+                  for i in range(n_cases)], np.int64)
+    t = x * x * (x * x - 1) ** 2
+    return x.astype(np.int32), t.astype(np.int32)
+
+
+def consts_int(seed: int, lo: int = -8, hi: int = 8) -> np.ndarray:
+    """251 integer constants uniform in [lo, hi]."""
+    lib = _load()
+    span = hi - lo + 1
+    return np.array([lo + (lib.synth_draw(seed ^ 0x1A7E000000000002, i) >> 32) * span // (1 << 32)
+                     for i in range(251)], np.int32)
+
+
+def workload_int(k: int, *, n_trees: int | None = None, n_cases: int | None = None, target: int | None = None):
+    """The integer variant of workload k: the same tree shapes over the
+    integer set (+, -, *, protected /, x, 251 integer constants in [-8, 8]),
+    integer cases x in [-8, 8] and the sextic target in exact integers."""
+    w = workload(k, n_trees=n_trees, n_cases=n_cases, target=target)
+    x, t = cases_int(w["seed"], n_cases or 48)
+    w.update({"x": x, "t": t, "consts": consts_int(w["seed"]), "integer": True})
+    return w
+
+
+def workload_mux(k: int, address_bits: int = 3, *, n_trees: int | None = None, target: int | None = None):
+    """Workload k's tree shapes over the k-multiplexer's Boolean set
+    (address_bits = 3: the 11-multiplexer, 2,048 cases)."""
+    n_in = address_bits + (1 << address_bits)
+    seed = MASTER_SEED + k
+    if k == 0:
+        ops, off = population("rhh", seed, n_trees or 500, boolean=True, n_inputs=n_in)
+    elif k == 3:
+        nt = n_trees or 4096
+        sizes = log_uniform_sizes(seed, nt, 1e1, float(target or 1e6))
+        ops, off = population("remy", seed, nt, boolean=True, sizes=sizes, n_inputs=n_in)
+    else:
+        ops, off = population("big", MASTER_SEED + 1, n_trees or 500, boolean=True,
+                              target=target or 1_000_000, n_inputs=n_in)
+        seed = MASTER_SEED + 1
+    return {"x": None, "t": None, "consts": np.zeros(251, np.float32), "ops": ops, "off": off, "seed": seed,
+            "n_cases": 1 << n_in, "boolean": True, "mux_k": address_bits}
 
 
 def workload(k: int, *, n_trees: int | None = None, n_cases: int | None = None,

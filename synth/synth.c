@@ -64,8 +64,10 @@ void synth_consts(uint64_t seed, float* k) {
 
 /* ---------------- ramped half-and-half ---------------- */
 
+/* boolean: 0 for the arithmetic sets, else the number of Boolean inputs
+ * (1 is read as the 6-multiplexer's 6) */
 static uint64_t leaf_op(rng_t* r, int boolean) {
-    if (boolean) return 4 + rng_below(r, 6);
+    if (boolean) return 4 + rng_below(r, boolean == 1 ? 6u : (uint64_t)boolean);
     if (rng_next(r) >> 63) return 4;                 /* x with p = 0.5 */
     return 5 + rng_below(r, 251);                   /* constant with p = 0.5 */
 }
