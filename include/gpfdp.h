@@ -36,9 +36,19 @@
  *   GP_BOOL_MUX6:  0 AND, 1 OR, 2 NAND, 3 NOR, 4..9 inputs a0 a1 d0 d1 d2 d3;
  *                  all 64 cases of the 6-multiplexer in one 64-bit word,
  *                  case i having a0 = bit 0 ... d3 = bit 5 of i (Sec. 4.2).
+ *   GP_BOOL_MUX11: the same functions, 4..14 inputs a0 a1 a2 d0 .. d7 of the
+ *                  11-multiplexer; 2,048 cases bit-packed in 32 words of 64
+ *                  bits (Sec. 4.2, widened), case i having input j = bit j
+ *                  of i; the target is d[a0 + 2 a1 + 4 a2].
+ *   GP_INT32_ARITH: the GP_FP32_ARITH opcodes over 32-bit signed integers:
+ *                  + - * wrap around modulo 2^32; protected '/' gives 1 for
+ *                  a zero divisor, INT32_MIN for INT32_MIN / -1, else the
+ *                  quotient truncated toward zero; consts, x and targets
+ *                  hold int32 values (passed through the float pointers).
  * Arithmetic is IEEE binary32 with no contraction into fused multiply-add
  * and no flushing of subnormals.  Fitness is sum_c |root(c) - target(c)|
- * accumulated in case order in binary32 (Boolean: number of wrong cases).
+ * accumulated in case order in binary32 (Boolean: number of wrong cases;
+ * integer: the sum exact in 64-bit integers, rounded once to binary32).
  */
 #ifndef GPFDP_H
 #define GPFDP_H
@@ -60,7 +70,7 @@ enum {
     GP_ESTATE = -6      /* call out of order (e.g. incremental without crossover) */
 };
 
-enum { GP_FP32_ARITH = 0, GP_BOOL_MUX6 = 1 };
+enum { GP_FP32_ARITH = 0, GP_BOOL_MUX6 = 1, GP_BOOL_MUX11 = 2, GP_INT32_ARITH = 3 };
 enum { GP_PACK_NONE = 0, GP_PACK_STATIC = 1, GP_PACK_MLP = 2 };
 
 typedef struct gp_pop gp_pop;
@@ -68,13 +78,14 @@ typedef struct gp_pop gp_pop;
 /* Population configuration (all fields by value). */
 typedef struct {
     uint32_t pop_size;          /* P individuals (one child per crossover, P children per generation) */
-    uint32_t n_cases;           /* C test cases (FP32 set); ignored (64) for GP_BOOL_MUX6 */
+    uint32_t n_cases;           /* C test cases (FP32 and integer sets); ignored for the Boolean sets */
     uint32_t max_nodes;         /* per-tree buffer capacity in nodes (Sec. 4.2: user-set maximum size) */
-    uint32_t funcset;           /* GP_FP32_ARITH or GP_BOOL_MUX6 */
+    uint32_t funcset;           /* GP_FP32_ARITH, GP_BOOL_MUX6, GP_BOOL_MUX11 or GP_INT32_ARITH */
     uint32_t cache_threshold;   /* subtree size from which node values are cached, 2..1024 (default 1024) */
     uint32_t tournament;        /* tournament size (default 7) */
     uint32_t packing;           /* GP_PACK_* order of incremental work */
-    uint32_t cases_per_lane;    /* 0 = auto; else 1, 2 or 4 test cases per GPU lane */
+    uint32_t cases_per_lane;    /* 0 = auto; else 1, 2 or 4 test cases per GPU lane (words for the
+                                   Boolean sets; 4 only for GP_FP32_ARITH; GP_BOOL_MUX6 uses 1) */
     uint64_t cache_budget_bytes;/* device bytes for cached value vectors (0 = 40 GiB) */
     uint64_t seed;              /* master seed of every stochastic choice */
     uint32_t walk_warps;        /* 0 = as many as fit; else at most this many warps run the walk */
@@ -111,7 +122,8 @@ typedef struct {
 
 /*
  * Create a population from host data.  x and targets hold n_cases floats
- * (ignored for GP_BOOL_MUX6); consts holds 251 floats; tree i is
+ * (int32 values for GP_INT32_ARITH; ignored for the Boolean sets); consts
+ * holds 251 floats (int32 values for GP_INT32_ARITH); tree i is
  * ops[offsets[i] .. offsets[i+1]) (offsets has pop_size+1 entries).  Each
  * tree must be a complete prefix expression with valid opcodes and at most
  * max_nodes nodes.  `stream` is a cudaStream_t (NULL = legacy default);
@@ -167,8 +179,11 @@ int gp_eval_incremental(gp_pop* pop, gp_stats* stats);
  * Synchronising. */
 int gp_fitness(const gp_pop* pop, float* host_out, uint32_t n);
 
-/* Copy the P x n_cases root values (FP32) or P root words (Boolean, as
- * uint64) to host.  `bytes` is the size of host_out.  Synchronising. */
+/* Copy the root value vectors to host: P x n_cases 32-bit values (binary32
+ * or int32), or for the Boolean sets P x (cases / 64) uint64 words.  A
+ * child that keeps no cache (fitness-first order, not selected as a
+ * parent) reads as NaN (binary32), 0x7FC00000 (int32) or 0 (Boolean).
+ * `bytes` is the size of host_out.  Synchronising. */
 int gp_root_values(const gp_pop* pop, void* host_out, size_t bytes);
 
 /* Copy tree i (its size into *size) to host_out of capacity cap bytes.
@@ -181,8 +196,8 @@ int gp_get_tree(const gp_pop* pop, uint32_t i, uint8_t* host_out, uint64_t cap, 
 int gp_cache_entries(const gp_pop* pop, uint32_t i, uint32_t* pos, uint32_t* end, int32_t* parent,
                      uint32_t nmax, uint32_t* n);
 
-/* Value vector of cache entry j of tree i (n_cases floats, or one uint64
- * for Boolean) to host.  Synchronising. */
+/* Value vector of cache entry j of tree i (n_cases 32-bit values, or
+ * cases / 64 uint64 words for the Boolean sets) to host.  Synchronising. */
 int gp_cache_value(const gp_pop* pop, uint32_t i, uint32_t j, void* host_out, size_t bytes);
 
 /* Per child of the last gp_eval_incremental: the level at which the walk

@@ -21,7 +21,7 @@ import numpy as np
 from ._build import LIB_PATH, build  # noqa: F401
 
 GP_OK, GP_EINVAL, GP_ENOMEM, GP_ECAPACITY, GP_ECUDA, GP_ETIMEOUT, GP_ESTATE = 0, -1, -2, -3, -4, -5, -6
-GP_FP32_ARITH, GP_BOOL_MUX6 = 0, 1
+GP_FP32_ARITH, GP_BOOL_MUX6, GP_BOOL_MUX11, GP_INT32_ARITH = 0, 1, 2, 3
 GP_PACK_NONE, GP_PACK_STATIC, GP_PACK_MLP = 0, 1, 2
 ERRNAMES = {GP_EINVAL: "GP_EINVAL", GP_ENOMEM: "GP_ENOMEM", GP_ECAPACITY: "GP_ECAPACITY",
             GP_ECUDA: "GP_ECUDA", GP_ETIMEOUT: "GP_ETIMEOUT", GP_ESTATE: "GP_ESTATE"}
@@ -188,10 +188,20 @@ def gp_fitness(h, n: int) -> np.ndarray:
     return out
 
 
-def gp_root_values(h, P: int, C: int, boolean: bool = False) -> np.ndarray:
-    out = np.empty(P, np.uint64) if boolean else np.empty((P, C), np.float32)
+def _value_array(shape_lead, C: int, kind: str):
+    """Host array for value vectors: binary32 or int32 cases, or the Boolean
+    sets' 64-case words (C cases)."""
+    if kind == "bool":
+        return np.empty(shape_lead + (C // 64,), np.uint64)
+    return np.empty(shape_lead + (C,), np.int32 if kind == "i32" else np.float32)
+
+
+def gp_root_values(h, P: int, C: int, kind: str = "f32") -> np.ndarray:
+    """Root value vectors (P, C); Boolean: (P, C / 64) words, or (P,) for the
+    6-multiplexer's single word."""
+    out = _value_array((P,), C, kind)
     _check(load().gp_root_values(h, _ptr(out), out.nbytes), h)
-    return out
+    return out[:, 0].copy() if (kind == "bool" and C == 64) else out
 
 
 def gp_get_tree(h, i: int) -> np.ndarray:
@@ -213,8 +223,8 @@ def gp_cache_entries(h, i: int):
     return pos[:m], end[:m], par[:m]
 
 
-def gp_cache_value(h, i: int, j: int, C: int, boolean: bool = False) -> np.ndarray:
-    out = np.empty(1, np.uint64) if boolean else np.empty(C, np.float32)   # Boolean: the 64-case word
+def gp_cache_value(h, i: int, j: int, C: int, kind: str = "f32") -> np.ndarray:
+    out = _value_array((), C, kind)        # Boolean: the 64-case words
     _check(load().gp_cache_value(h, i, j, _ptr(out), out.nbytes), h)
     return out
 
@@ -380,13 +390,25 @@ class Population:
     def __init__(self, x, t, consts, ops, off, *, max_nodes: int, cache_threshold: int = 1024,
                  boolean: bool = False, tournament: int = 7, packing: int = GP_PACK_STATIC,
                  cases_per_lane: int = 0, cache_budget_bytes: int = 0, seed: int = 0, stream=None,
-                 walk_warps: int = 0, mlp_lr_micro: int = 0, walk_team: int = 0, lazy: bool = False):
+                 walk_warps: int = 0, mlp_lr_micro: int = 0, walk_team: int = 0, lazy: bool = False,
+                 mux_k: int = 2, integer: bool = False):
+        """boolean: the k-multiplexer (mux_k = 2: 6-mux, 64 cases; 3: 11-mux,
+        2,048 cases); integer: the integer set (x, t, consts are int32)."""
         off = np.asarray(off, np.uint64)
         self.P = len(off) - 1
         self.boolean = boolean
-        self.C = 64 if boolean else len(x)
+        self.kind = "bool" if boolean else ("i32" if integer else "f32")
+        self.C = (1 << (mux_k + (1 << mux_k))) if boolean else len(x)
+        if boolean:
+            funcset = {2: GP_BOOL_MUX6, 3: GP_BOOL_MUX11}[mux_k]
+        else:
+            funcset = GP_INT32_ARITH if integer else GP_FP32_ARITH
+        if integer:
+            x = np.ascontiguousarray(x, np.int32).view(np.float32)
+            t = np.ascontiguousarray(t, np.int32).view(np.float32)
+            consts = np.ascontiguousarray(consts, np.int32).view(np.float32)
         cfg = GpConfig(pop_size=self.P, n_cases=self.C, max_nodes=max_nodes,
-                       funcset=GP_BOOL_MUX6 if boolean else GP_FP32_ARITH,
+                       funcset=funcset,
                        cache_threshold=cache_threshold, tournament=tournament, packing=packing,
                        cases_per_lane=cases_per_lane, cache_budget_bytes=cache_budget_bytes,
                        seed=seed & (2**64 - 1), walk_warps=walk_warps, mlp_lr_micro=mlp_lr_micro,
@@ -423,7 +445,7 @@ class Population:
         return gp_fitness(self.h, self.P)
 
     def root_values(self) -> np.ndarray:
-        return gp_root_values(self.h, self.P, self.C, self.boolean)
+        return gp_root_values(self.h, self.P, self.C, self.kind)
 
     def tree(self, i: int) -> np.ndarray:
         return gp_get_tree(self.h, i)
@@ -432,7 +454,7 @@ class Population:
         return gp_cache_entries(self.h, i)
 
     def cache_value(self, i: int, j: int) -> np.ndarray:
-        return gp_cache_value(self.h, i, j, self.C, self.boolean)
+        return gp_cache_value(self.h, i, j, self.C, self.kind)
 
     def stats(self) -> dict:
         return gp_get_stats(self.h).as_dict()

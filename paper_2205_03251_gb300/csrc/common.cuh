@@ -24,19 +24,26 @@ enum : uint32_t {
 // queue counters
 enum { Q_ITEMS = 0, Q_SKEL = 1, Q_WALK = 2, Q_MISC = 3, Q_ALLOC = 4, Q_PATHV = 5, NQ = 16 };
 
+// Value kinds of the function sets.  Every value travels as 32 bits in a
+// float register or slot: a binary32 number (VF), a word of 32 Boolean
+// cases (VB), or a two's-complement integer (VI).
+enum : int { VF = 0, VB = 1, VI = 2 };
+
 struct DevPop {
     // sizes
     uint32_t P, C, Cpad, K, ncb, T, cap, funcset;
     uint32_t Ecap, Scap, maxdepth, W;      // entries, slots, interpreter stack bound, smem stack depth
     uint32_t ovf_warps;                    // warps with an overflow stack region
     uint32_t strict_cap;                   // 1: a cache larger than Ecap is an error (no host regrow)
+    uint32_t vkind;                        // VF, VB or VI
+    uint32_t mux_k;                        // Boolean: address lines of the multiplexer (C = 2^(k + 2^k) / 32 words)
     // population
     uint8_t* arena;      // nbuf * cap bytes
     uint32_t* buf;       // [P] buffer holding individual i
     uint32_t* size;      // [P]
-    float* x;            // [Cpad] (padded cases are 0)
-    float* t;            // [C]
-    float* consts;       // [251]
+    float* x;            // [Cpad] (padded cases are 0; integer set: int32 bits; Boolean: unused)
+    float* t;            // [C] targets (integer set: int32 bits; Boolean: the target's case words)
+    float* consts;       // [251] (integer set: int32 bits)
     float* fit;          // [P]
     // structure / cache (current population)
     uint32_t* blk_off;   // [P+1]
@@ -98,4 +105,31 @@ __device__ __forceinline__ uint32_t find_segment(const uint32_t* off, uint32_t n
         if (off[mid] <= u) lo = mid; else hi = mid;
     }
     return lo;
+}
+
+// Fitness of one value vector, whose case (Boolean: word) j is at(j):
+//   binary32: sum over the cases, in case order, of |v - t|, each step
+//             rounded to binary32;
+//   Boolean:  the number of wrong cases, popcount(v ^ target) summed over
+//             the words;
+//   integer:  sum of |v - t| exact in 64-bit integers, rounded once to
+//             binary32.
+template <typename F>
+__device__ __forceinline__ float fitness_of(const DevPop& d, F at) {
+    if (d.vkind == VB) {
+        uint32_t e = 0;
+        for (uint32_t j = 0; j < d.C; ++j) e += __popc(__float_as_uint(at(j)) ^ __float_as_uint(d.t[j]));
+        return (float)e;
+    }
+    if (d.vkind == VI) {
+        long long s = 0;
+        for (uint32_t j = 0; j < d.C; ++j) {
+            const long long e = (long long)__float_as_int(at(j)) - (long long)__float_as_int(d.t[j]);
+            s += e < 0 ? -e : e;
+        }
+        return __ll2float_rn(s);
+    }
+    float f = 0.0f;
+    for (uint32_t j = 0; j < d.C; ++j) f = __fadd_rn(f, fabsf(__fsub_rn(at(j), d.t[j])));
+    return f;
 }

@@ -31,7 +31,7 @@ __global__ void k_build_items(DevPop d, const uint32_t* __restrict__ e_tree) {
 // Persistent warps over (item, case block) units.  The next unit's index
 // and descriptor are fetched, and its opcodes staged, while the current
 // one is interpreted (two staging buffers per warp).
-template <int K, bool B>
+template <int K, int V>
 __global__ void __launch_bounds__(GP_WARPS * 32) k_eval_items(DevPop d) {
     if (halted(d)) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -84,7 +84,7 @@ __global__ void __launch_bounds__(GP_WARPS * 32) k_eval_items(DevPop d) {
             for (int k = 0; k < K; ++k) st.acc[k] = 0.f;
             st.sp = 0;
             st.ok = true;
-            interp_staged<K, B>(stage0 + cur * STAGE_BYTES, desc.x, desc.x + desc.y, st, c);
+            interp_staged<K, V>(stage0 + cur * STAGE_BYTES, desc.x, desc.x + desc.y, st, c);
             if (!st.ok && lane == 0) set_status(d.status, ST_STACK);
             store_slot<K>(d, desc.z, cbk, st.acc);
             if (cbk == 0) ops_done += desc.y;
@@ -105,7 +105,7 @@ __global__ void __launch_bounds__(GP_WARPS * 32) k_eval_items(DevPop d) {
 // value -- then combined in order; a right child inside the same group is
 // taken from the group's own results.
 #define SKB 16
-template <int K, bool B>
+template <int K, int V>
 __global__ void __launch_bounds__(GP_WARPS * 32) k_eval_skeleton(DevPop d) {
     if (halted(d)) return;
     const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -161,11 +161,11 @@ __global__ void __launch_bounds__(GP_WARPS * 32) k_eval_skeleton(DevPop d) {
                             if (has0) {                       // left = entry e+1 = prev
 #pragma unroll
                                 for (int k = 0; k < K; ++k) val[k] = prev[k];
-                                apply_vec<K, B>(op, val, o);
+                                apply_vec<K, V>(op, val, o);
                             } else {                          // right = entry e+1 = prev
 #pragma unroll
                                 for (int k = 0; k < K; ++k) val[k] = o[k];
-                                apply_vec<K, B>(op, val, prev);
+                                apply_vec<K, V>(op, val, prev);
                             }
                             store_slot<K>(d, slots[j], cbk, val);
                             if (cbk == 0) ++cnt;
@@ -182,12 +182,7 @@ __global__ void __launch_bounds__(GP_WARPS * 32) k_eval_skeleton(DevPop d) {
     }
 }
 
-// Fitness of every tree from its root's cached vector: sum over cases in
-// case order of |value - target| in binary32; Boolean: wrong cases out of 64.
-__device__ __forceinline__ float bool_errors(const float* v) {
-    return (float)(__popc(__float_as_uint(v[0]) ^ mux_target_half(0)) + __popc(__float_as_uint(v[1]) ^ mux_target_half(1)));
-}
-
+// Fitness of every tree from its root's cached vector (fitness_of).
 __global__ void k_fitness(DevPop d) {
     if (halted(d)) return;
     const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -196,14 +191,7 @@ __global__ void k_fitness(DevPop d) {
     for (uint32_t tree = gw; tree < d.P; tree += nw) {
         if (lane_id() == 0) {
             const float* v = d.slots + (size_t)d.e_slot[d.e_off[tree]] * d.Cpad;
-            float f = 0.0f;
-            if (d.funcset == 1u) {
-                const float w[2] = {__ldcg(v), __ldcg(v + 1)};
-                f = bool_errors(w);
-            } else {
-                for (uint32_t c = 0; c < d.C; ++c) f = __fadd_rn(f, fabsf(__fsub_rn(__ldcg(v + c), d.t[c])));
-            }
-            d.fit[tree] = f;
+            d.fit[tree] = fitness_of(d, [&](uint32_t j) { return __ldcg(v + j); });
             atomicAdd(&d.acc_ops[1], (unsigned long long)d.size[tree]);
         }
     }

@@ -808,21 +808,21 @@ struct TeamLayout {
 };
 
 // left/right combination keeping the operand order of the node
-template <int K, bool B>
+template <int K, int V>
 __device__ __forceinline__ void combine(uint32_t op, bool path_left, float (&v)[K], const float (&sib)[K]) {
-    if (path_left) apply_vec<K, B>(op, v, sib);
+    if (path_left) apply_vec<K, V>(op, v, sib);
     else {
         float t[K];
 #pragma unroll
         for (int k = 0; k < K; ++k) t[k] = sib[k];
-        apply_vec<K, B>(op, t, v);
+        apply_vec<K, V>(op, t, v);
 #pragma unroll
         for (int k = 0; k < K; ++k) v[k] = t[k];
     }
 }
 
 // Evaluate bytes [s, e) of `src` (a small run: e - (s & ~15) <= STAGE_BYTES).
-template <int K, bool B>
+template <int K, int V>
 __device__ __forceinline__ void eval_run(const uint8_t* src, uint32_t s, uint32_t e, uint8_t* stage,
                                          const Ictx<K>& c, float (&out)[K], uint32_t* status) {
     __syncwarp();
@@ -835,7 +835,7 @@ __device__ __forceinline__ void eval_run(const uint8_t* src, uint32_t s, uint32_
     for (int k = 0; k < K; ++k) st.acc[k] = 0.f;
     st.sp = 0;
     st.ok = true;
-    interp_staged<K, B>(stage, s, e, st, c);
+    interp_staged<K, V>(stage, s, e, st, c);
     if (!st.ok && lane_id() == 0) set_status(status, ST_STACK);
 #pragma unroll
     for (int k = 0; k < K; ++k) out[k] = st.acc[k];
@@ -998,11 +998,18 @@ __device__ bool walk_ancestors(const DevPop& d, const CacheView& par, uint32_t i
 // Disruption of one case between the child's value n and the mother's o:
 // bit patterns differ (Boolean: each differing bit is a case); for finite
 // pairs the squared difference, in binary64, joins the lane's sum.
-template <bool B>
+template <int V>
 __device__ __forceinline__ void dis_case(float n, float o, uint32_t& nd, uint32_t& nf, double& sq) {
     const uint32_t x = __float_as_uint(n) ^ __float_as_uint(o);
-    if (B) {
+    if (V == VB) {
         nd += __popc(x);
+    } else if (V == VI) {
+        if (x) {
+            ++nd;
+            ++nf;
+            const double df = (double)((long long)__float_as_int(n) - (long long)__float_as_int(o));
+            sq = __dadd_rn(sq, __dmul_rn(df, df));
+        }
     } else if (x) {
         ++nd;
         if (isfinite(n) && isfinite(o)) {
@@ -1015,14 +1022,14 @@ __device__ __forceinline__ void dis_case(float n, float o, uint32_t& nd, uint32_
 
 // Warp-collective: sum the lanes' counts and squares, lane 0 stores level
 // `level` of child i (levels past the record's length are dropped).
-template <bool B>
+template <int V>
 __device__ __forceinline__ void dis_store(const GenBufs& g, uint32_t i, uint32_t level, uint32_t nd, uint32_t nf,
                                           double sq) {
     nd = __reduce_add_sync(FULL, nd);
     nf = __reduce_add_sync(FULL, nf);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) sq = __dadd_rn(sq, __shfl_xor_sync(FULL, sq, o));
-    if (B) { nf = nd; sq = (double)nd; }
+    if (V == VB) { nf = nd; sq = (double)nd; }
     if (lane_id() == 0 && level < g.dis_L) {
         DisLevel r;
         r.nd = nd;
@@ -1047,7 +1054,7 @@ __device__ __forceinline__ void dis_store(const GenBufs& g, uint32_t i, uint32_t
 // values of nodes that are cached in the child are recorded for the
 // child's cache; above the stop only child-cached nodes that the mother
 // does not cache need computing.
-template <int K, bool B>
+template <int K, int V>
 __global__ void __launch_bounds__(256, 2) k_walk(DevPop d, GenBufs g, CacheView par, uint32_t nw) {
     if (halted(d)) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1141,12 +1148,12 @@ __global__ void __launch_bounds__(256, 2) k_walk(DevPop d, GenBufs g, CacheView 
                     for (int kk = 0; kk < K; ++kk) ist.acc[kk] = 0.f;
                     ist.sp = 0;
                     ist.ok = true;
-                    interp_staged<K, B>(stA, 0, nk, ist, ic);
+                    interp_staged<K, V>(stA, 0, nk, ist, ic);
                     if (!ist.ok && lane == 0) set_status(d.status, ST_STACK);
 #pragma unroll
                     for (int kk = 0; kk < K; ++kk) v[kk] = ist.acc[kk];
                 } else {
-                    eval_run<K, B>(ok_, 0, nk, stA, ic, v, d.status);
+                    eval_run<K, V>(ok_, 0, nk, stA, ic, v, d.status);
                 }
                 st_interp += nk;
                 store_blk<K>(nvs, cb, v);
@@ -1182,14 +1189,7 @@ __global__ void __launch_bounds__(256, 2) k_walk(DevPop d, GenBufs g, CacheView 
                 g.nins[i] = (rec && c == 0) ? 1u : 0u;
                 g.stop[i] = -2;                 // evaluated in one pass, no walk
                 g.plen[i] = 0;
-                if (B) {
-                    d.fit[i] = (float)(__popc(__float_as_uint(nvs[0]) ^ mux_target_half(0)) +
-                                       __popc(__float_as_uint(nvs[1]) ^ mux_target_half(1)));
-                } else {
-                    float fsum = 0.0f;
-                    for (uint32_t cc = 0; cc < Cn; ++cc) fsum = __fadd_rn(fsum, fabsf(__fsub_rn(nvs[cc], d.t[cc])));
-                    d.fit[i] = fsum;
-                }
+                d.fit[i] = fitness_of(d, [&](uint32_t j) { return nvs[j]; });
             }
             __syncthreads();                 // nvs and the shared words are reused by the next child
             continue;
@@ -1223,13 +1223,13 @@ __global__ void __launch_bounds__(256, 2) k_walk(DevPop d, GenBufs g, CacheView 
             if (which == 0) {
                 if (ef >= 0) load_vec<K>(par.slots, Cpad, par.e_slot[ef], v, cb);
                 else {
-                    if (virt) eval_run<K, B>(d.arena + (size_t)g.pbuf[f] * d.cap, dd, dd + s, stA, ic, v, d.status);
-                    else eval_run<K, B>(ok_, c, c + s, stA, ic, v, d.status);
+                    if (virt) eval_run<K, V>(d.arena + (size_t)g.pbuf[f] * d.cap, dd, dd + s, stA, ic, v, d.status);
+                    else eval_run<K, V>(ok_, c, c + s, stA, ic, v, d.status);
                     st_interp += s;
                 }
             } else {
                 if (em >= 0) load_vec<K>(par.slots, Cpad, par.e_slot[em], v, cb);
-                else { eval_run<K, B>(g.stash + g.stash_off[i], 0, r, stA, ic, v, d.status); st_interp += r; }
+                else { eval_run<K, V>(g.stash + g.stash_off[i], 0, r, stA, ic, v, d.status); st_interp += r; }
             }
             store_blk<K>(which == 0 ? nvs : ovs, cb, v);
         }
@@ -1280,8 +1280,8 @@ __global__ void __launch_bounds__(256, 2) k_walk(DevPop d, GenBufs g, CacheView 
             if (g.dis) {                                   // level 0 of the disruption record
                 uint32_t nd = 0, nf = 0;
                 double sq = 0.0;
-                for (uint32_t j = lane; j < Cn; j += 32) dis_case<B>(nvs[j], ovs[j], nd, nf, sq);
-                dis_store<B>(g, i, 0, nd, nf, sq);
+                for (uint32_t j = lane; j < Cn; j += 32) dis_case<V>(nvs[j], ovs[j], nd, nf, sq);
+                dis_store<V>(g, i, 0, nd, nf, sq);
             }
             uint32_t bq = c, bqend = c + s, bk = 0;        // builder state (lane 0)
             int32_t bpe = (nsmall > 0) ? -1 : A;
@@ -1357,7 +1357,7 @@ __global__ void __launch_bounds__(256, 2) k_walk(DevPop d, GenBufs g, CacheView 
                             else {
                                 load_cases<K>(d, cb, ic.xv);
                                 const uint32_t sh = (D.flags & LD_LEFT) ? (uint32_t)tdl : 0u;
-                                eval_run<K, B>(ok_, D.ss - sh, D.se - sh, stA, ic, v, d.status);
+                                eval_run<K, V>(ok_, D.ss - sh, D.se - sh, stA, ic, v, d.status);
                                 st_interp += D.se - D.ss;
                             }
                             store_blk<K>(svs + slot * Cpad, cb, v);
@@ -1387,19 +1387,19 @@ __global__ void __launch_bounds__(256, 2) k_walk(DevPop d, GenBufs g, CacheView 
                 for (uint32_t j = lane; j < Cpad; j += 32) {
                     float o[1] = {ovs[j]};
                     const float sv1[1] = {svl[j]};
-                    combine<1, B>(op, left, o, sv1);         // mother's value at p (exact recomputation)
+                    combine<1, V>(op, left, o, sv1);         // mother's value at p (exact recomputation)
                     if (!stopped_w) {
                         float n1[1] = {nvs[j]};
-                        combine<1, B>(op, left, n1, sv1);
+                        combine<1, V>(op, left, n1, sv1);
                         nvs[j] = n1[0];
                         if (D.pent >= 0) o[0] = pvv[j];
                         if (j < Cn && __float_as_uint(n1[0]) != __float_as_uint(o[0])) okl = false;
-                        if (g.dis && j < Cn) dis_case<B>(n1[0], o[0], dnd, dnf, dsq);
+                        if (g.dis && j < Cn) dis_case<V>(n1[0], o[0], dnd, dnf, dsq);
                     }
                     ovs[j] = o[0];
                 }
                 const bool lvl_eq = __all_sync(FULL, okl);
-                if (g.dis && !stopped_w) dis_store<B>(g, i, level, dnd, dnf, dsq);
+                if (g.dis && !stopped_w) dis_store<V>(g, i, level, dnd, dnf, dsq);
                 __syncwarp();
                 if (!stopped_w) {
                     ++levels_w;
@@ -1473,7 +1473,7 @@ __global__ void __launch_bounds__(256, 2) k_walk(DevPop d, GenBufs g, CacheView 
                     else {
                         load_cases<K>(d, cb, ic.xv);
                         const uint32_t sh = (D.flags & LD_LEFT) ? (uint32_t)tdl : 0u;
-                        eval_run<K, B>(ok_, D.ss - sh, D.se - sh, stA, ic, v, d.status);
+                        eval_run<K, V>(ok_, D.ss - sh, D.se - sh, stA, ic, v, d.status);
                         st_interp += D.se - D.ss;
                     }
                     store_blk<K>(svs + slot * Cpad, cb, v);
@@ -1504,14 +1504,7 @@ __global__ void __launch_bounds__(256, 2) k_walk(DevPop d, GenBufs g, CacheView 
                 d.fit[i] = g.pfit[m];
                 ++st_stopped;
             } else {
-                float fsum = 0.0f;
-                if (B) {
-                    fsum = (float)(__popc(__float_as_uint(nvs[0]) ^ mux_target_half(0)) +
-                                   __popc(__float_as_uint(nvs[1]) ^ mux_target_half(1)));
-                } else {
-                    for (uint32_t cc = 0; cc < Cn; ++cc) fsum = __fadd_rn(fsum, fabsf(__fsub_rn(nvs[cc], d.t[cc])));
-                }
-                d.fit[i] = fsum;
+                d.fit[i] = fitness_of(d, [&](uint32_t j) { return nvs[j]; });
             }
             st_levels += levels;
         }
@@ -1954,7 +1947,7 @@ __global__ void k_mlp_features(DevPop d, GenBufs g, CacheView par, MlpBufs b) {
             const float* v = par.slots + (size_t)par.e_slot[par.e_off[t]] * d.Cpad;
             float lo = INFINITY, hi = -INFINITY;
             for (uint32_t cc = 0; cc < d.C; ++cc) {
-                const float a = v[cc];
+                const float a = (d.vkind == VI) ? (float)__float_as_int(v[cc]) : v[cc];
                 if (isfinite(a)) { lo = fminf(lo, a); hi = fmaxf(hi, a); }
             }
             spread[q] = (hi >= lo) ? fminf(log2f(1.f + (hi - lo)) / 8.f, 4.f) : 4.f;

@@ -192,11 +192,12 @@ int check_status(gp_pop* pop) {
 // nodes with opcodes of the function set.
 bool valid_tree(const uint8_t* ops, uint64_t n, uint32_t funcset) {
     if (n == 0) return false;
+    const uint32_t maxop = funcset == GP_BOOL_MUX6 ? 9u : funcset == GP_BOOL_MUX11 ? 14u : 255u;
     int64_t need = 1;
     for (uint64_t i = 0; i < n; ++i) {
         if (need <= 0) return false;
         uint8_t o = ops[i];
-        if (funcset == GP_BOOL_MUX6 && o > 9) return false;
+        if (o > maxop) return false;
         need += (o < 4) ? 1 : -1;
     }
     return need == 0;
@@ -233,12 +234,23 @@ __global__ void k_scatter_trees(const uint8_t* __restrict__ src, const uint64_t*
     }
 }
 
-template <int K, bool B = false>
+// Call f(K, V) with the population's cases per lane and value kind as
+// compile-time constants (the instantiated pairs: binary32 with K = 1, 2,
+// 4; Boolean and integer with K = 1, 2).
+template <int N> using IC = std::integral_constant<int, N>;
+template <typename F>
+auto with_kind(const DevPop& d, F&& f) {
+    if (d.vkind == VB) return d.K == 1 ? f(IC<1>{}, IC<VB>{}) : f(IC<2>{}, IC<VB>{});
+    if (d.vkind == VI) return d.K == 1 ? f(IC<1>{}, IC<VI>{}) : f(IC<2>{}, IC<VI>{});
+    return d.K == 1 ? f(IC<1>{}, IC<VF>{}) : d.K == 2 ? f(IC<2>{}, IC<VF>{}) : f(IC<4>{}, IC<VF>{});
+}
+
+template <int K, int V>
 int setup_items_kernel(gp_pop* pop) {
     size_t smem = SmemLayout<K>::total((int)pop->d.W, GP_WARPS);
-    CK(cudaFuncSetAttribute(k_eval_items<K, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    CK(cudaFuncSetAttribute(k_eval_items<K, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int nb = 0;
-    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_eval_items<K, B>, GP_WARPS * 32, smem));
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_eval_items<K, V>, GP_WARPS * 32, smem));
     if (nb < 1) nb = 1;
     pop->grid_items = nb * pop->nsm;
     pop->smem_items = smem;
@@ -250,15 +262,15 @@ int setup_items_kernel(gp_pop* pop) {
 // team at once, else 4 (one building and combining warp and three sibling
 // evaluators: enough resident warps per SM to hide the interpreter's
 // latency when children queue for teams).
-template <int K, bool B = false>
+template <int K, int V>
 int setup_walk_kernel(gp_pop* pop, uint32_t team) {
     const uint32_t ovf = pop->d.ovf_warps;      // the walk shares the interpreter's per-warp overflow stacks
-    CK(cudaFuncSetAttribute(k_walk<K, B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    CK(cudaFuncSetAttribute(k_walk<K, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                             (int)TeamLayout<K>((int)pop->d.W, pop->d.Cpad, 8).total));
     auto shape = [&](uint32_t nw, int& grid, size_t& smem) -> int {
         smem = TeamLayout<K>((int)pop->d.W, pop->d.Cpad, nw).total;
         int nb = 0;
-        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_walk<K, B>, (int)nw * 32, smem));
+        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_walk<K, V>, (int)nw * 32, smem));
         if (nb < 1) nb = 1;
         grid = nb * pop->nsm;
         if ((uint32_t)grid * nw > ovf) grid = (int)(ovf / nw);
@@ -280,19 +292,13 @@ int setup_walk_kernel(gp_pop* pop, uint32_t team) {
     return GP_OK;
 }
 
-template <int K, bool B = false>
+template <int K, int V>
 void launch_items(gp_pop* pop) {
-    k_eval_items<K, B><<<pop->grid_items, GP_WARPS * 32, pop->smem_items, pop->stream>>>(pop->d);
+    k_eval_items<K, V><<<pop->grid_items, GP_WARPS * 32, pop->smem_items, pop->stream>>>(pop->d);
 }
-template <int K, bool B = false>
+template <int K, int V>
 void launch_skeleton(gp_pop* pop) {
-    k_eval_skeleton<K, B><<<pop->grid_warps, GP_WARPS * 32, 0, pop->stream>>>(pop->d);
-}
-
-// dispatch on cases per lane; the Boolean set always runs with K = 1
-void launch_by_k(gp_pop* pop, void (*f1)(gp_pop*), void (*f2)(gp_pop*), void (*f4)(gp_pop*), void (*fb)(gp_pop*)) {
-    if (pop->d.funcset == GP_BOOL_MUX6) fb(pop);
-    else if (pop->d.K == 1) f1(pop); else if (pop->d.K == 2) f2(pop); else f4(pop);
+    k_eval_skeleton<K, V><<<pop->grid_warps, GP_WARPS * 32, 0, pop->stream>>>(pop->d);
 }
 
 // Advance the generation offset of a captured generation loop (last node of the graph).
@@ -453,10 +459,10 @@ int run_full(gp_pop* pop) {
     k_build_items<<<gthreads, 256, 0, pop->stream>>>(d, pop->sb.e_tree);
     phase_end(pop, PH_STRUCT);
     phase_begin(pop, PH_ITEMS);
-    launch_by_k(pop, launch_items<1>, launch_items<2>, launch_items<4>, launch_items<1, true>);
+    with_kind(pop->d, [&](auto k, auto v) { launch_items<decltype(k)::value, decltype(v)::value>(pop); return 0; });
     phase_end(pop, PH_ITEMS);
     phase_begin(pop, PH_SKEL);
-    launch_by_k(pop, launch_skeleton<1>, launch_skeleton<2>, launch_skeleton<4>, launch_skeleton<1, true>);
+    with_kind(pop->d, [&](auto k, auto v) { launch_skeleton<decltype(k)::value, decltype(v)::value>(pop); return 0; });
     phase_end(pop, PH_SKEL);
     phase_begin(pop, PH_FIT);
     k_fitness<<<pop->grid_warps, GP_WARPS * 32, 0, pop->stream>>>(d);
@@ -482,9 +488,12 @@ int gp_pop_create(const gp_config* cfg_in, const float* x, const float* targets,
     *out = nullptr;
     gp_config cfg = *cfg_in;
     if (cfg.pop_size == 0) return fail(nullptr, GP_EINVAL, "pop_size must be > 0");
-    if (cfg.funcset != GP_FP32_ARITH && cfg.funcset != GP_BOOL_MUX6) return fail(nullptr, GP_EINVAL, "bad funcset");
-    const bool boolean = cfg.funcset == GP_BOOL_MUX6;
-    if (boolean) { cfg.n_cases = 2; cfg.cases_per_lane = 1; }   // 64 cases: two 32-bit words
+    if (cfg.funcset > GP_INT32_ARITH) return fail(nullptr, GP_EINVAL, "bad funcset");
+    const bool boolean = cfg.funcset == GP_BOOL_MUX6 || cfg.funcset == GP_BOOL_MUX11;
+    const uint32_t mux_k = cfg.funcset == GP_BOOL_MUX6 ? 2u : cfg.funcset == GP_BOOL_MUX11 ? 3u : 0u;
+    // Boolean: n_cases counts 32-case words, 2^(k + 2^k) / 32 of them (6-mux 2, 11-mux 64)
+    if (boolean) cfg.n_cases = (1u << (mux_k + (1u << mux_k))) / 32u;
+    if (cfg.funcset == GP_BOOL_MUX6) cfg.cases_per_lane = 1;
     if (cfg.n_cases == 0 || cfg.n_cases > (1u << 20)) return fail(nullptr, GP_EINVAL, "n_cases out of range");
     if (!boolean && (!x || !targets)) return fail(nullptr, GP_EINVAL, "null x/targets");
     if (cfg.cache_threshold == 0) cfg.cache_threshold = 1024;
@@ -496,6 +505,8 @@ int gp_pop_create(const gp_config* cfg_in, const float* x, const float* targets,
     uint32_t K = cfg.cases_per_lane;
     if (K == 0) K = (cfg.n_cases <= 32) ? 1 : 2;
     if (K != 1 && K != 2 && K != 4) return fail(nullptr, GP_EINVAL, "cases_per_lane must be 0, 1, 2 or 4");
+    if (K == 4 && cfg.funcset != GP_FP32_ARITH)
+        return fail(nullptr, GP_EINVAL, "cases_per_lane 4 is for the binary32 set only");
     if (cfg.walk_team != 0 && cfg.walk_team != 1 && cfg.walk_team != 2 && cfg.walk_team != 4 && cfg.walk_team != 8)
         return fail(nullptr, GP_EINVAL, "walk_team must be 0, 1, 2, 4 or 8");
     if (cfg.lazy_children > 1) return fail(nullptr, GP_EINVAL, "lazy_children must be 0 or 1");
@@ -518,7 +529,7 @@ int gp_pop_create(const gp_config* cfg_in, const float* x, const float* targets,
     pop->launches = 0;
     pop->e_total_h = nullptr;
     pop->last_kind = 0;
-    pop->cases_stat = boolean ? 64u : cfg.n_cases;
+    pop->cases_stat = boolean ? 32u * cfg.n_cases : cfg.n_cases;
     memset(&pop->stats, 0, sizeof pop->stats);
     memset(pop->ev_count, 0, sizeof pop->ev_count);
     pop->gexec = nullptr;
@@ -543,6 +554,8 @@ int gp_pop_create(const gp_config* cfg_in, const float* x, const float* targets,
     d.T = T;
     d.cap = (uint32_t)(((uint64_t)cfg.max_nodes + GP_B - 1) / GP_B * GP_B);
     d.funcset = cfg.funcset;
+    d.vkind = boolean ? (uint32_t)VB : cfg.funcset == GP_INT32_ARITH ? (uint32_t)VI : (uint32_t)VF;
+    d.mux_k = mux_k;
     d.W = 16;                       // interpreter stack entries kept in shared memory
     d.maxdepth = d.W + T + 2;       // subtrees below the threshold need at most T + 1 entries
     const uint64_t total_cap = (uint64_t)P * d.cap;
@@ -602,8 +615,7 @@ int gp_pop_create(const gp_config* cfg_in, const float* x, const float* targets,
 
     // interpreter launch shape and its overflow stacks
     {
-        int r = (cfg.funcset == GP_BOOL_MUX6) ? setup_items_kernel<1, true>(pop)
-                : (K == 1) ? setup_items_kernel<1>(pop) : (K == 2) ? setup_items_kernel<2>(pop) : setup_items_kernel<4>(pop);
+        int r = with_kind(d, [&](auto k, auto v) { return setup_items_kernel<decltype(k)::value, decltype(v)::value>(pop); });
         if (r) return bail(r);
         d.ovf_warps = (uint32_t)pop->grid_items * GP_WARPS;
         DA2(d.ovf, (size_t)d.ovf_warps * (d.maxdepth - d.W) * 32 * K);
@@ -655,9 +667,9 @@ int gp_pop_create(const gp_config* cfg_in, const float* x, const float* targets,
     // incremental walk launch shape
     {
         const uint32_t team = cfg.walk_team;
-        int r = (cfg.funcset == GP_BOOL_MUX6) ? setup_walk_kernel<1, true>(pop, team)
-                : (K == 1) ? setup_walk_kernel<1>(pop, team) : (K == 2) ? setup_walk_kernel<2>(pop, team)
-                : setup_walk_kernel<4>(pop, team);
+        int r = with_kind(d, [&](auto k, auto v) {
+            return setup_walk_kernel<decltype(k)::value, decltype(v)::value>(pop, team);
+        });
         if (r) return bail(r);
         pop->grid_walk_max = pop->grid_walk;
         if (cfg.walk_warps) {
@@ -680,8 +692,21 @@ int gp_pop_create(const gp_config* cfg_in, const float* x, const float* targets,
     }
 
     // inputs
+    // (integer set: the caller's int32 bits, copied as they are; Boolean: the
+    // target's case words, bit l of word w for case 32w + l)
     std::vector<float> xp(d.Cpad, 0.0f), tp(d.C, 0.0f);
     if (!boolean) { memcpy(xp.data(), x, sizeof(float) * d.C); memcpy(tp.data(), targets, sizeof(float) * d.C); }
+    else {
+        for (uint32_t w = 0; w < d.C; ++w) {
+            uint32_t word = 0;
+            for (uint32_t l = 0; l < 32; ++l) {
+                const uint64_t i = 32ull * w + l;
+                const uint64_t a = i & ((1ull << mux_k) - 1);
+                word |= (uint32_t)((i >> (mux_k + a)) & 1ull) << l;
+            }
+            memcpy(&tp[w], &word, 4);
+        }
+    }
     std::vector<uint32_t> bufs(P);
     for (uint32_t i = 0; i < P; ++i) bufs[i] = i;
     uint8_t* stage = nullptr;
@@ -951,8 +976,7 @@ int gp_root_values(const gp_pop* cpop, void* host_out, size_t bytes) {
     gp_pop* pop = const_cast<gp_pop*>(cpop);
     if (!pop || !host_out) return GP_EINVAL;
     const DevPop& d = pop->d;
-    const bool boolean = d.funcset == GP_BOOL_MUX6;
-    const size_t need = boolean ? (size_t)d.P * sizeof(uint64_t) : (size_t)d.P * d.C * sizeof(float);
+    const size_t need = (size_t)d.P * d.C * sizeof(float);
     if (bytes < need) return fail(pop, GP_EINVAL, "host buffer too small");
     int rc = check_status(pop);
     if (rc) return rc;
@@ -961,19 +985,13 @@ int gp_root_values(const gp_pop* cpop, void* host_out, size_t bytes) {
     for (uint32_t i = 0; i < d.P; ++i) {
         if (eoff[i + 1] == eoff[i]) {
             // fitness-first mode: a child that is not a parent keeps no cache
-            if (boolean) static_cast<uint64_t*>(host_out)[i] = 0;
-            else for (uint32_t k = 0; k < d.C; ++k) static_cast<float*>(host_out)[(size_t)i * d.C + k] = NAN;
+            const uint32_t fill = (d.vkind == VB) ? 0u : 0x7FC00000u;
+            for (uint32_t k = 0; k < d.C; ++k) memcpy(static_cast<float*>(host_out) + (size_t)i * d.C + k, &fill, 4);
             continue;
         }
         CK(cudaMemcpy(slot.data(), d.e_slot + eoff[i], sizeof(uint32_t), cudaMemcpyDeviceToHost));
-        if (boolean) {
-            uint32_t w[2];
-            CK(cudaMemcpy(w, d.slots + (size_t)slot[0] * d.Cpad, sizeof w, cudaMemcpyDeviceToHost));
-            static_cast<uint64_t*>(host_out)[i] = (uint64_t)w[0] | ((uint64_t)w[1] << 32);
-        } else {
-            CK(cudaMemcpy(static_cast<float*>(host_out) + (size_t)i * d.C, d.slots + (size_t)slot[0] * d.Cpad,
-                          sizeof(float) * d.C, cudaMemcpyDeviceToHost));
-        }
+        CK(cudaMemcpy(static_cast<float*>(host_out) + (size_t)i * d.C, d.slots + (size_t)slot[0] * d.Cpad,
+                      sizeof(float) * d.C, cudaMemcpyDeviceToHost));
     }
     return GP_OK;
 }
@@ -1051,7 +1069,7 @@ int gp_cache_value(const gp_pop* cpop, uint32_t i, uint32_t j, void* host_out, s
     if (j >= eo[1] - eo[0]) return fail(pop, GP_EINVAL, "entry %u out of range", j);
     uint32_t slot = 0;
     CK(cudaMemcpy(&slot, pop->d.e_slot + eo[0] + j, sizeof slot, cudaMemcpyDeviceToHost));
-    // Boolean: the two 32-bit halves of the 64-case word (low half first)
+    // Boolean: the 32-case words in case order (as uint64: 64 cases, low half first)
     CK(cudaMemcpy(host_out, pop->d.slots + (size_t)slot * pop->d.Cpad, sizeof(float) * pop->d.C, cudaMemcpyDeviceToHost));
     return GP_OK;
 }
@@ -1229,9 +1247,9 @@ void swap_generation(gp_pop* pop) {
     std::swap(d.fit, g.pfit);
 }
 
-template <int K, bool B = false>
+template <int K, int V>
 void launch_walk(gp_pop* pop, const CacheView& par) {
-    k_walk<K, B><<<pop->grid_walk, pop->walk_nw * 32, pop->smem_walk, pop->stream>>>(pop->d, pop->gb, par, pop->walk_nw);
+    k_walk<K, V><<<pop->grid_walk, pop->walk_nw * 32, pop->smem_walk, pop->stream>>>(pop->d, pop->gb, par, pop->walk_nw);
 }
 
 }  // namespace
@@ -1311,8 +1329,7 @@ int gen_incremental(gp_pop* pop) {
     }
     phase_end(pop, PH_PACK);
     phase_begin(pop, PH_WALK);
-    if (d.funcset == GP_BOOL_MUX6) launch_walk<1, true>(pop, par);
-    else if (d.K == 1) launch_walk<1>(pop, par); else if (d.K == 2) launch_walk<2>(pop, par); else launch_walk<4>(pop, par);
+    with_kind(d, [&](auto k, auto v) { launch_walk<decltype(k)::value, decltype(v)::value>(pop, par); return 0; });
     phase_end(pop, PH_WALK);
     if (g.lazy) {
         // the next generation's plan from these children's fitness; only the

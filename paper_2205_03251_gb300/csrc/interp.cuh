@@ -16,7 +16,8 @@
 //
 // Arithmetic is binary32 with explicit round-to-nearest intrinsics (never
 // contracted into FMA); protected division returns 1 when the divisor
-// equals zero.
+// equals zero.  The same interpreter runs the Boolean multiplexer sets
+// (lanes hold 32-case words) and the integer set (lanes hold int32 bits).
 #pragma once
 #include "common.cuh"
 
@@ -53,18 +54,38 @@ __device__ __forceinline__ float apply_op(uint32_t op, float a, float b) {
     }
 }
 
-// Boolean 6-multiplexer set: 0 AND, 1 OR, 2 NAND, 3 NOR on 32-case halves
-// of the 64-case word (the value bits travel in float registers).
+// Boolean multiplexer sets: 0 AND, 1 OR, 2 NAND, 3 NOR on words of 32
+// cases (the value bits travel in float registers).
 __device__ __forceinline__ uint32_t bool_op(uint32_t op, uint32_t x, uint32_t y) {
     uint32_t r = (op & 1u) ? (x | y) : (x & y);
     return (op & 2u) ? ~r : r;
 }
 
-template <int K, bool B = false>
+// Integer set: + - * wrap around modulo 2^32; protected division returns 1
+// for a zero divisor and the wrapped quotient INT32_MIN for INT32_MIN / -1,
+// else the quotient truncated toward zero.
+__device__ __forceinline__ int32_t int_op(uint32_t op, int32_t x, int32_t y) {
+    switch (op) {
+    case 0: return (int32_t)((uint32_t)x + (uint32_t)y);
+    case 1: return (int32_t)((uint32_t)x - (uint32_t)y);
+    case 2: return (int32_t)((uint32_t)x * (uint32_t)y);
+    default:
+        if (y == 0) return 1;
+        if (x == INT32_MIN && y == -1) return INT32_MIN;
+        return x / y;
+    }
+}
+
+template <int K, int V = VF>
 __device__ __forceinline__ void apply_vec(uint32_t op, float (&a)[K], const float (&b)[K]) {
-    if constexpr (B) {
+    if constexpr (V == VB) {
 #pragma unroll
         for (int k = 0; k < K; ++k) a[k] = __uint_as_float(bool_op(op, __float_as_uint(a[k]), __float_as_uint(b[k])));
+        return;
+    }
+    if constexpr (V == VI) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) a[k] = __int_as_float(int_op(op, __float_as_int(a[k]), __float_as_int(b[k])));
         return;
     }
     if (op < 2) {
@@ -90,16 +111,31 @@ struct Ictx {
     float* s;            // shared stack: W entries x 32 lanes x K (this lane's K at s + lane*K)
     float* g;            // global overflow: (maxd - W) entries x 32 lanes x K
     const float* kc;     // shared constant table indexed by opcode (kc[5..255])
-    const float* kb;     // Boolean: shared input words, kb[(op-4)*32 + lane] for op 4..9
+    const float* kb;     // Boolean: shared words of inputs 0..4 (mux_pattern)
     int W, maxd;
-    float xv[K];         // this lane's test-case inputs
+    float xv[K];         // this lane's test-case inputs (Boolean: the index of each of its words)
 };
 
-template <int K, bool B>
+// Boolean input b (opcode 4 + b: a0.. then d0..) is bit b of the case index.
+// Word w holds cases 32w .. 32w + 31, so for b < 5 the word is the same
+// pattern in every word, and for b >= 5 it is all ones or all zeros by bit
+// b - 5 of w.
+__device__ __forceinline__ uint32_t mux_pattern(uint32_t b) {
+    uint32_t x = 0;
+    for (uint32_t l = 0; l < 32; ++l) x |= ((l >> b) & 1u) << l;
+    return x;
+}
+__device__ __forceinline__ uint32_t mux_word(uint32_t b, uint32_t pattern, uint32_t w) {
+    return b < 5u ? pattern : 0u - ((w >> ((b - 5u) & 31u)) & 1u);
+}
+
+template <int K, int V>
 __device__ __forceinline__ void leaf_value(uint32_t op, float (&acc)[K], const Ictx<K>& c, int lane) {
-    if constexpr (B) {
-        const uint32_t j = (op - 4u) < 6u ? op - 4u : 0u;
-        acc[0] = c.kb[j * 32 + lane];
+    if constexpr (V == VB) {
+        const uint32_t b = op - 4u;
+        const uint32_t pat = __float_as_uint(c.kb[b < 5u ? b : 0u]);
+#pragma unroll
+        for (int k = 0; k < K; ++k) acc[k] = __uint_as_float(mux_word(b, pat, __float_as_uint(c.xv[k])));
     } else {
         const float cv = c.kc[op];
 #pragma unroll
@@ -144,7 +180,7 @@ __device__ __forceinline__ uint32_t lds_u32(uint32_t a) {
 // One node, any stack depth (bounds checked).  The shared window is
 // accessed through the same volatile helpers as the fast path (so the two
 // keep their order), the overflow area through ordinary global accesses.
-template <int K, bool B = false>
+template <int K, int V = VF>
 __device__ __forceinline__ void step_checked(uint32_t op, Istate<K>& st, const Ictx<K>& c, int lane) {
     const uint32_t sw = (uint32_t)__cvta_generic_to_shared(c.s) + (uint32_t)lane * K * 4;
     if (op >= 4) {
@@ -152,7 +188,7 @@ __device__ __forceinline__ void step_checked(uint32_t op, Istate<K>& st, const I
         else if (st.sp < c.maxd) vstore<K>(c.g + ((size_t)(st.sp - c.W) * 32 + lane) * K, st.acc);
         else st.ok = false;
         if (st.sp < c.maxd) ++st.sp;
-        leaf_value<K, B>(op, st.acc, c, lane);
+        leaf_value<K, V>(op, st.acc, c, lane);
     } else {
         float r[K];
         if (st.sp <= 0) {
@@ -164,22 +200,24 @@ __device__ __forceinline__ void step_checked(uint32_t op, Istate<K>& st, const I
             if (st.sp < c.W) lds_vec<K>(sw + (uint32_t)st.sp * 32 * K * 4, r);
             else vload<K>(c.g + ((size_t)(st.sp - c.W) * 32 + lane) * K, r);
         }
-        apply_vec<K, B>(op, st.acc, r);
+        apply_vec<K, V>(op, st.acc, r);
     }
 }
 
 // One node when the whole stack access stays inside the shared window;
 // sa is this lane's next free stack entry, kca the constant table and kba
-// this lane's Boolean input words (shared-window addresses).
-template <int K, bool B = false>
+// the Boolean input patterns (shared-window addresses).
+template <int K, int V = VF>
 __device__ __forceinline__ void step_fast(uint32_t op, float (&acc)[K], uint32_t& sa, uint32_t kca, uint32_t kba,
                                           const Ictx<K>& c) {
     if (op >= 4) {
         sts_vec<K>(sa, acc);
         sa += 32 * K * 4;
-        if constexpr (B) {
-            const uint32_t j = (op - 4u) < 6u ? op - 4u : 0u;
-            acc[0] = lds_f32(kba + j * 32 * 4);
+        if constexpr (V == VB) {
+            const uint32_t b = op - 4u;
+            const uint32_t pat = lds_u32(kba + (b < 5u ? b : 0u) * 4);
+#pragma unroll
+            for (int k = 0; k < K; ++k) acc[k] = __uint_as_float(mux_word(b, pat, __float_as_uint(c.xv[k])));
         } else {
             const float cv = lds_f32(kca + op * 4);
 #pragma unroll
@@ -189,7 +227,7 @@ __device__ __forceinline__ void step_fast(uint32_t op, float (&acc)[K], uint32_t
         sa -= 32 * K * 4;
         float r[K];
         lds_vec<K>(sa, r);
-        apply_vec<K, B>(op, acc, r);
+        apply_vec<K, V>(op, acc, r);
     }
 }
 
@@ -203,7 +241,7 @@ __device__ __forceinline__ void step_fast(uint32_t op, float (&acc)[K], uint32_t
 // warp's stack are touched -- every shared-memory layout keeps that much
 // room below each stack -- and so does a run that does not end with exactly
 // one entry (the initial running value) on the stack.
-template <int K, bool B = false>
+template <int K, int V = VF>
 __device__ __forceinline__ void interp_staged(const uint8_t* stage, uint32_t s, uint32_t e,
                                               Istate<K>& st, const Ictx<K>& c) {
     const int lane = lane_id();
@@ -212,13 +250,13 @@ __device__ __forceinline__ void interp_staged(const uint8_t* stage, uint32_t s, 
     // head: single nodes down to a multiple of 4
     while (p > s && (p & 3u)) {
         --p;
-        step_checked<K, B>(stage[p - a], st, c, lane);
+        step_checked<K, V>(stage[p - a], st, c, lane);
     }
     const uint32_t* wp = reinterpret_cast<const uint32_t*>(stage);
     const uint32_t wa = (uint32_t)__cvta_generic_to_shared(stage) - a;      // shared address of byte 0
     const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(c.s) + lane * K * 4;
     const uint32_t kca = (uint32_t)__cvta_generic_to_shared(c.kc);
-    const uint32_t kba = B ? (uint32_t)__cvta_generic_to_shared(c.kb) + lane * 4 : 0u;
+    const uint32_t kba = (V == VB) ? (uint32_t)__cvta_generic_to_shared(c.kb) : 0u;
     const int wfast = c.W - 4;
     const uint32_t sfast = sbase + (uint32_t)wfast * 32 * K * 4;
     bool under = false;
@@ -227,26 +265,26 @@ __device__ __forceinline__ void interp_staged(const uint8_t* stage, uint32_t s, 
             uint32_t sa = sbase + (uint32_t)st.sp * 32 * K * 4;
             do {
                 const uint32_t w = lds_u32(wa + p - 4);
-                step_fast<K, B>(w >> 24, st.acc, sa, kca, kba, c);
-                step_fast<K, B>((w >> 16) & 0xFFu, st.acc, sa, kca, kba, c);
-                step_fast<K, B>((w >> 8) & 0xFFu, st.acc, sa, kca, kba, c);
-                step_fast<K, B>(w & 0xFFu, st.acc, sa, kca, kba, c);
+                step_fast<K, V>(w >> 24, st.acc, sa, kca, kba, c);
+                step_fast<K, V>((w >> 16) & 0xFFu, st.acc, sa, kca, kba, c);
+                step_fast<K, V>((w >> 8) & 0xFFu, st.acc, sa, kca, kba, c);
+                step_fast<K, V>(w & 0xFFu, st.acc, sa, kca, kba, c);
                 under |= ((int32_t)(sa - sbase) < 0);
                 p -= 4;
             } while (p >= s + 4 && (int32_t)(sa - sfast) <= 0 && (int32_t)(sa - sbase) >= 0);
             st.sp = (int32_t)(sa - sbase) / (32 * K * 4);
         } else {
             const uint32_t w = wp[(p - 4 - a) >> 2];
-            step_checked<K, B>(w >> 24, st, c, lane);
-            step_checked<K, B>((w >> 16) & 0xFFu, st, c, lane);
-            step_checked<K, B>((w >> 8) & 0xFFu, st, c, lane);
-            step_checked<K, B>(w & 0xFFu, st, c, lane);
+            step_checked<K, V>(w >> 24, st, c, lane);
+            step_checked<K, V>((w >> 16) & 0xFFu, st, c, lane);
+            step_checked<K, V>((w >> 8) & 0xFFu, st, c, lane);
+            step_checked<K, V>(w & 0xFFu, st, c, lane);
             p -= 4;
         }
     }
     while (p > s) {
         --p;
-        step_checked<K, B>(stage[p - a], st, c, lane);
+        step_checked<K, V>(stage[p - a], st, c, lane);
     }
     if (under || st.sp != 1) st.ok = false;
 }
@@ -274,7 +312,10 @@ template <int K>
 __device__ __forceinline__ void load_cases(const DevPop& d, uint32_t cbk, float (&xv)[K]) {
     const int lane = lane_id();
 #pragma unroll
-    for (int k = 0; k < K; ++k) xv[k] = d.x[cbk * 32 * K + k * 32 + lane];
+    for (int k = 0; k < K; ++k) {
+        const uint32_t j = cbk * 32 * K + k * 32 + lane;
+        xv[k] = (d.vkind == VB) ? __uint_as_float(j) : d.x[j];
+    }
 }
 
 // value vector of slot `slot`, case block cbk, as this lane's K cases
@@ -305,29 +346,9 @@ struct SmemLayout {
     __host__ __device__ static size_t total(int W, int warps) { return kc_bytes + warps * warp_bytes(W); }
 };
 
-// Boolean 6-multiplexer: 64 cases in one word, case i has a0 = bit 0, a1 =
-// bit 1, d0..d3 = bits 2..5 of i; input j's word has bit i set iff bit j of
-// i is set.  Lane 0 holds cases 0..31, lane 1 cases 32..63 (32-bit halves).
-__device__ __forceinline__ uint32_t mux_input_half(uint32_t j, uint32_t half) {
-    uint32_t w = 0;
-    for (uint32_t b = 0; b < 32; ++b) w |= (((b + 32u * half) >> j) & 1u) << b;
-    return w;
-}
-__device__ __forceinline__ uint32_t mux_target_half(uint32_t half) {
-    uint32_t w = 0;
-    for (uint32_t b = 0; b < 32; ++b) {
-        const uint32_t i = b + 32u * half;
-        const uint32_t addr = (i & 1u) + 2u * ((i >> 1) & 1u);
-        w |= ((i >> (2u + addr)) & 1u) << b;
-    }
-    return w;
-}
-// kb[j*32 + lane] = input word j's half for lanes 0 and 1, zero elsewhere
+// kb[b] = the word of Boolean input b < 5 (the same in every word)
 __device__ __forceinline__ void fill_kb(float* kb) {
-    for (int i = threadIdx.x; i < 6 * 32; i += blockDim.x) {
-        const uint32_t j = i / 32, l = i % 32;
-        kb[i] = __uint_as_float(l < 2 ? mux_input_half(j, l) : 0u);
-    }
+    for (int i = threadIdx.x; i < 5; i += blockDim.x) kb[i] = __uint_as_float(mux_pattern((uint32_t)i));
 }
 
 // Fill the opcode-indexed constant table (kc[5 + i] = consts[i]).
