@@ -55,7 +55,9 @@ def parse():
     ap.add_argument("--trees", type=int, default=None, help="default 500 (uneven: 4,096)")
     ap.add_argument("--target", type=int, default=1_000_000)
     ap.add_argument("--cases", type=int, default=48)
-    ap.add_argument("--boolean", action="store_true", help="uneven workload on the 6-multiplexer")
+    ap.add_argument("--boolean", action="store_true", help="uneven workload on the 6-multiplexer (= --funcset mux6)")
+    ap.add_argument("--funcset", default="fp32", choices=["fp32", "mux6", "mux11", "int32"],
+                    help="function set of the uneven workload: binary32, 6- or 11-multiplexer, integer")
     ap.add_argument("--threshold", type=int, default=1024)
     ap.add_argument("--cases-per-lane", type=int, default=0, choices=[0, 1, 2, 4], help="0: automatic")
     ap.add_argument("--walk-team", type=int, default=0, choices=[0, 1, 2, 4, 8], help="warps per child; 0: automatic")
@@ -77,6 +79,12 @@ def parse():
         a.steps = {"generation": 100, "uneven": 50, "full": 20, "packing": 1000}[a.workload]
     if a.trees is None:
         a.trees = 4096 if a.workload == "uneven" else 500
+    if a.funcset == "mux6":
+        a.boolean = True
+    if a.boolean:
+        a.funcset = "mux6"
+    if a.funcset != "fp32" and a.workload != "uneven":
+        ap.error("--funcset applies to the uneven workload")
     return a
 
 
@@ -154,11 +162,16 @@ def make_workload(args, rank: int):
     import synth
     if args.workload == "uneven":
         # each rank its own population of the same recipe (weak scaling)
-        w = synth.workload(3, n_trees=args.trees, n_cases=args.cases, target=args.target, boolean=args.boolean)
+        if args.funcset == "mux11":
+            w = synth.workload_mux(3, 3, n_trees=args.trees, target=args.target)
+        elif args.funcset == "int32":
+            w = synth.workload_int(3, n_trees=args.trees, n_cases=args.cases, target=args.target)
+        else:
+            w = synth.workload(3, n_trees=args.trees, n_cases=args.cases, target=args.target, boolean=args.boolean)
         if rank:
             sizes = synth.log_uniform_sizes(w["seed"] + rank, args.trees, 1e1, float(args.target))
             w["ops"], w["off"] = synth.population("remy", w["seed"] + rank, args.trees, boolean=args.boolean,
-                                                  sizes=sizes)
+                                                  sizes=sizes, n_inputs=11 if w.get("mux_k") == 3 else 6)
         w["max_nodes"] = 2 * args.target + 4096
         return w
     seed_shift = rank
@@ -172,14 +185,36 @@ def workload_config(args, w):
     what = ("one generation: selection, crossover, incremental evaluation with failed disruption "
             "propagation" if args.workload != "full" else "full evaluation")
     if args.workload == "uneven":
-        cases = "64 Boolean 6-multiplexer cases (one 64-bit word)" if args.boolean else f"{args.cases} cases"
+        cases = ("64 Boolean 6-multiplexer cases (one 64-bit word)" if args.boolean else
+                 "2048 Boolean 11-multiplexer cases (32 64-bit words)" if args.funcset == "mux11" else
+                 f"{args.cases} integer cases" if args.funcset == "int32" else f"{args.cases} cases")
         desc = (f"{args.trees} Remy trees with sizes log-uniform in [1e1, {args.target:.0e}] nodes, "
                 f"{cases}, {what}")
     else:
         desc = f"{args.trees} grafted ramped-half-and-half trees of ~{args.target:.0e} nodes, {args.cases} cases, {what}"
     return {"workload": desc, "trees": args.trees, "nodes": int(w["off"][-1]),
-            "cases": 64 if w.get("boolean") else args.cases, "cache_threshold": args.threshold,
+            "cases": _cases(w), "cache_threshold": args.threshold,
             "l2": "opcode arena %.2f GB > 129 MB L2; no flush" % (int(w["off"][-1]) / 1e9)}
+
+
+def _cases(w) -> int:
+    """Test cases of a workload (Boolean: all the multiplexer's cases)."""
+    if w.get("boolean"):
+        return 1 << (w.get("mux_k", 2) + (1 << w.get("mux_k", 2)))
+    return len(w["x"])
+
+
+def _oracle_tree(oracle, w, tree):
+    """The oracle's evaluation of one whole tree of workload w."""
+    sub = np.array([0, len(tree)], np.uint64)
+    if w.get("mux_k", 2) == 3 and w.get("boolean"):
+        oracle.eval_node_mux(tree, 0, 3)
+    elif w.get("boolean"):
+        oracle.eval_pop_bool(tree, sub)
+    elif w.get("integer"):
+        oracle.eval_pop_i32(tree, sub, w["consts"], w["x"], w["t"])
+    else:
+        oracle.eval_pop_f32(tree, sub, w["consts"], w["x"], w["t"])
 
 
 def cpu_baseline(w, seconds: float, gpu_fit=None):
@@ -193,16 +228,11 @@ def cpu_baseline(w, seconds: float, gpu_fit=None):
     oracle.build()
     ops, off = w["ops"], w["off"]
     boolean = bool(w.get("boolean"))
-    C = 64 if boolean else len(w["x"])
+    C = _cases(w)
     P = len(off) - 1
 
     def one(n):
-        sub = off[n:n + 2] - off[n]
-        tree = ops[int(off[n]):int(off[n + 1])]
-        if boolean:
-            oracle.eval_pop_bool(tree, sub)
-        else:
-            oracle.eval_pop_f32(tree, sub, w["consts"], w["x"], w["t"])
+        _oracle_tree(oracle, w, ops[int(off[n]):int(off[n + 1])])
         return int(off[n + 1] - off[n])
 
     def run(threads: int, budget: float):
@@ -233,13 +263,14 @@ def cpu_baseline(w, seconds: float, gpu_fit=None):
     one_v, one_n, one_nodes, one_dt = run(1, seconds / 3)
     cores = os.cpu_count() or 1
     all_v, all_n, all_nodes, all_dt = run(cores, 2 * seconds / 3)
-    kind = "recursive Boolean oracle" if boolean else "recursive FP32 oracle"
+    kind = ("recursive Boolean oracle" if boolean else "recursive integer oracle" if w.get("integer")
+            else "recursive FP32 oracle")
     out = {"value": all_v, "unit": "GPop/s", "cores": cores, "kind": "oracle",
            "sample": f"{all_n} trees ({all_nodes} nodes) x {C} cases in {all_dt:.1f} s, {kind}, one thread per "
                      f"core taking whole trees from a shared queue",
            "single_thread": {"value": one_v, "cores": 1,
                              "sample": f"{one_n} trees ({one_nodes} nodes) x {C} cases in {one_dt:.1f} s"}}
-    if gpu_fit is not None and one_n:
+    if gpu_fit is not None and one_n and not boolean and not w.get("integer"):
         n = min(one_n, len(gpu_fit))
         f64 = oracle.eval_pop_f64(ops[:int(off[n])], off[:n + 1], w["consts"], w["x"], w["t"])
         rel, nonfinite = oracle.max_rel_diff(gpu_fit[:n], f64)
@@ -283,18 +314,13 @@ def run_reference(args):
     w = make_workload(args, 0)
     import oracle
     oracle.build()
-    boolean = bool(w.get("boolean"))
-    C = 64 if boolean else len(w["x"])
+    C = _cases(w)
     units = reference_units(w)
     cores = os.cpu_count() or 1
     pos = [0]
 
     def one(tree):
-        sub = np.array([0, len(tree)], np.uint64)
-        if boolean:
-            oracle.eval_pop_bool(tree, sub)
-        else:
-            oracle.eval_pop_f32(tree, sub, w["consts"], w["x"], w["t"])
+        _oracle_tree(oracle, w, tree)
 
     def step():
         batch = [units[(pos[0] + j) % len(units)] for j in range(cores)]
@@ -313,10 +339,13 @@ def run_reference(args):
         nodes += step()
     dt = time.perf_counter() - t0
     val = nodes * C / dt / 1e9
-    kind = "recursive Boolean oracle" if boolean else "recursive FP32 oracle"
+    boolean, integer = bool(w.get("boolean")), bool(w.get("integer"))
+    kind = ("recursive Boolean oracle" if boolean else "recursive integer oracle" if integer
+            else "recursive FP32 oracle")
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "GPop/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64" if boolean else "f32",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u64" if boolean else "i32" if integer else "f32",
             "data": "synthetic", "config": workload_config(args, w),
             "cpu_baseline": {"value": val, "unit": "GPop/s", "cores": cores, "kind": "oracle",
                              "sample": f"per step {cores} subtrees of 1,024-65,536 nodes cut from the workload's "
@@ -446,23 +475,26 @@ def main():
     w = make_workload(args, rank)
     stream = torch.cuda.current_stream()
     boolean = bool(w.get("boolean"))
+    integer = bool(w.get("integer"))
+    kind_kw = {"mux_k": w.get("mux_k", 2), "integer": integer}
     maxn = w.get("max_nodes", 1 << 21)
     pop_kw = {"cache_threshold": args.threshold, "packing": PACKING[args.packing],
               "cache_budget_bytes": args.cache_budget_gb << 30, "lazy": args.lazy,
               "cases_per_lane": args.cases_per_lane, "walk_team": args.walk_team}
     tune = None
     if args.workload == "uneven" and args.autotune:
-        ks = (1,) if boolean else ((1, 2) if args.cases <= 64 else (2, 4))
+        ks = ((1,) if (boolean and kind_kw["mux_k"] == 2) else (1, 2) if (boolean or integer or args.cases <= 64)
+              else (2, 4))
         best, table = gp.autotune(w["x"], w["t"], w["consts"], w["ops"], w["off"], max_nodes=maxn, ks=ks,
                                   ts=(256, 1024), teams=(1, 2, 4), generations=2, boolean=boolean,
                                   seed=0x5EED + rank, packing=pop_kw["packing"], stream=stream,
-                                  cache_budget_bytes=args.cache_budget_gb << 30)
+                                  cache_budget_bytes=args.cache_budget_gb << 30, **kind_kw)
         pop_kw.update(best)
         tune = {"chosen": best, "candidates": [{k: r[k] for k in ("cases_per_lane", "cache_threshold", "walk_team",
                                                                    "ms_full", "ms_generation", "identical")}
                                                for r in table]}
     pop = gp.Population(None if boolean else w["x"], None if boolean else w["t"], w["consts"], w["ops"], w["off"],
-                        max_nodes=maxn, boolean=boolean, seed=0x5EED + rank, stream=stream, **pop_kw)
+                        max_nodes=maxn, boolean=boolean, seed=0x5EED + rank, stream=stream, **kind_kw, **pop_kw)
     generational = args.workload != "full"
     chunk = graph_chunk(args.steps) if (generational and args.graph) else 0
 
@@ -482,7 +514,7 @@ def main():
     # full evaluation (also the starting point of the generation loop)
     for _ in range(2):
         pop.eval_full()
-    fit0 = None if boolean else pop.fitness().copy()     # the initial trees' fitness, for the FP64 comparison
+    fit0 = None if (boolean or integer) else pop.fitness().copy()     # the initial trees' fitness, for the FP64 comparison
     full_ms, full_st = timed(pop.eval_full, 3) if generational else (None, None)
     if chunk:
         pop.set_graph_mode(True)         # pre-sized caches, no host syncs in the loop
@@ -535,7 +567,8 @@ def main():
 
     line = {"metric": METRIC, "value": value, "unit": "GPop/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "u64" if boolean else "f32", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64" if boolean else "i32" if integer else "f32",
+            "data": "synthetic",
             "config": workload_config(args, w), "actual_gpops": actual, "phase_ms": phases}
     line["config"]["execution"] = (f"CUDA graph of {chunk} generations, {n_calls} replay(s) timed "
                                    f"after {args.warmup} eager warm-up generations" if chunk else "eager calls")
@@ -636,7 +669,7 @@ def main():
         e2e["value"] = float(t.item()) * world
     line["e2e"] = e2e
     if generational:
-        line["disruption"] = disruption_profile(pop, gen_step, 64 if args.boolean else args.cases)
+        line["disruption"] = disruption_profile(pop, gen_step, _cases(w))
     pop.close()
     if rank == 0:
         if not args.no_cpu and world == 1:

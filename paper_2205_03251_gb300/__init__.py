@@ -359,17 +359,24 @@ def gp_autotune_pick(results: list[dict], generations: int) -> int:
 
 def autotune(x, t, consts, ops, off, *, max_nodes: int, ks=(1, 2, 4), ts=(64, 256, 1024), teams=(0,),
              generations: int = 2, boolean: bool = False, tournament: int = 7, packing: int = GP_PACK_STATIC,
-             cache_budget_bytes: int = 0, seed: int = 0, stream=None):
+             cache_budget_bytes: int = 0, seed: int = 0, stream=None, mux_k: int = 2, integer: bool = False):
     """Autotune the case, subtree and walk-team splits for a population;
     returns (keyword arguments for Population with the chosen split, result
     table).  A team of 0 means the automatic choice."""
     off = np.asarray(off, np.uint64)
-    C = 64 if boolean else len(x)
+    C = (1 << (mux_k + (1 << mux_k))) if boolean else len(x)
     if boolean:
         x = np.zeros(1, np.float32)
         t = np.zeros(1, np.float32)
+        funcset = {2: GP_BOOL_MUX6, 3: GP_BOOL_MUX11}[mux_k]
+    else:
+        funcset = GP_INT32_ARITH if integer else GP_FP32_ARITH
+    if integer:
+        x = np.ascontiguousarray(x, np.int32).view(np.float32)
+        t = np.ascontiguousarray(t, np.int32).view(np.float32)
+        consts = np.ascontiguousarray(consts, np.int32).view(np.float32)
     cfg = GpConfig(pop_size=len(off) - 1, n_cases=C, max_nodes=max_nodes,
-                   funcset=GP_BOOL_MUX6 if boolean else GP_FP32_ARITH, cache_threshold=1024,
+                   funcset=funcset, cache_threshold=1024,
                    tournament=tournament, packing=packing, cases_per_lane=0,
                    cache_budget_bytes=cache_budget_bytes, seed=seed & (2**64 - 1))
     best, table = gp_autotune(cfg, x, t, consts, ops, off, ks, ts, teams, generations, stream)

@@ -13,8 +13,11 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string.h>
+#include <string>
 #include <vector>
 #include "../../include/gpfdp.h"
+
+extern "C" void gpfdp_set_create_error(const char* msg);
 
 namespace {
 
@@ -40,10 +43,10 @@ int timed_ms(cudaStream_t stream, float* ms, F&& fn) {
 
 int run_candidate(const gp_config* cfg, const float* x, const float* targets, const float* consts,
                   const uint8_t* ops, const uint64_t* offsets, uint32_t generations, cudaStream_t stream,
-                  gp_tune_result* res, std::vector<float>& fit) {
+                  gp_tune_result* res, std::vector<float>& fit, std::string& err) {
     gp_pop* pop = nullptr;
     int rc = gp_pop_create(cfg, x, targets, consts, ops, offsets, stream, &pop);
-    if (rc) return rc;
+    if (rc) { err = gp_last_error(nullptr); return rc; }
     // first evaluation: loads the kernels and sizes the cache (may regrow)
     rc = gp_eval_full(pop);
     if (!rc) rc = gp_fitness(pop, fit.data(), cfg->pop_size);
@@ -62,6 +65,7 @@ int run_candidate(const gp_config* cfg, const float* x, const float* targets, co
         if (!rc) rc = gp_fitness(pop, fit.data(), cfg->pop_size);
         res->ms_generation = rc ? 0.f : ms / (float)generations;
     }
+    if (rc) err = gp_last_error(pop);
     gp_pop_destroy(pop);
     return rc;
 }
@@ -94,6 +98,7 @@ int gp_autotune(const gp_config* base, const float* x, const float* targets, con
     const uint32_t n = n_k * n_t * n_team;
     std::vector<float> ref(base->pop_size), fit(base->pop_size);
     bool have_ref = false;
+    std::string first_err;
     for (uint32_t a = 0; a < n_k; ++a) {
         for (uint32_t b = 0; b < n_t; ++b) {
             for (uint32_t w = 0; w < n_team; ++w) {
@@ -106,16 +111,25 @@ int gp_autotune(const gp_config* base, const float* x, const float* targets, con
                 cfg.cases_per_lane = ks[a];
                 cfg.cache_threshold = ts[b];
                 cfg.walk_team = teams[w];
+                std::string err;
                 r.status = run_candidate(&cfg, x, targets, consts, ops, offsets, generations,
-                                         static_cast<cudaStream_t>(stream), &r, fit);
-                if (r.status != GP_OK) continue;
+                                         static_cast<cudaStream_t>(stream), &r, fit, err);
+                if (r.status != GP_OK) {
+                    if (first_err.empty())
+                        first_err = "K=" + std::to_string(ks[a]) + " T=" + std::to_string(ts[b]) + " team=" +
+                                    std::to_string(teams[w]) + ": " + err;
+                    continue;
+                }
                 if (!have_ref) { ref = fit; have_ref = true; }
                 r.identical = memcmp(ref.data(), fit.data(), sizeof(float) * base->pop_size) == 0 ? 1u : 0u;
             }
         }
     }
     const int j = gp_autotune_pick(results, n, generations);
-    if (j < 0) return GP_ENOMEM;
+    if (j < 0) {
+        gpfdp_set_create_error(("no candidate ran; first failure " + first_err).c_str());
+        return GP_ENOMEM;
+    }
     *best = *base;
     best->cases_per_lane = results[j].cases_per_lane;
     best->cache_threshold = results[j].cache_threshold;

@@ -477,6 +477,9 @@ int run_full(gp_pop* pop) {
 
 extern "C" {
 
+// the autotuner's report when no candidate ran (read back by gp_last_error(NULL))
+void gpfdp_set_create_error(const char* msg) { g_create_error = msg ? msg : ""; }
+
 const char* gp_last_error(const gp_pop* pop) {
     return pop ? pop->err.c_str() : g_create_error.c_str();
 }
