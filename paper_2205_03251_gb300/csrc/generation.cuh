@@ -786,7 +786,7 @@ __host__ __device__ inline uint32_t walk_ring(uint32_t Cpad) { return Cpad <= 12
 
 template <int K>
 struct TeamLayout {
-    uint32_t kc, anc, ancg, lvl, desc, nv, ov, sv, mv, sc, warp0, warp_bytes, total;
+    uint32_t kc, anc, ancg, lvl, desc, nv, ov, sv, mv, cur, sc, warp0, warp_bytes, total;
     __host__ __device__ TeamLayout(int W, uint32_t Cpad, uint32_t nw) {
         const uint32_t ring = walk_ring(Cpad);
         uint32_t o = 0;
@@ -799,6 +799,8 @@ struct TeamLayout {
         ov = o;   o += Cpad * 4;
         sv = o;   o += ring * Cpad * 4;
         mv = o;   o += ring * Cpad * 4;
+        o = (o + 15u) & ~15u;
+        cur = o;  o += 16;                                                  // evaluators' next item
         sc = o;   o += (16 + 2 * WALK_RING) * 4;
         o = (o + 15u) & ~15u;
         warp0 = o;
@@ -1087,6 +1089,7 @@ __global__ void __launch_bounds__(256, 2) k_walk(DevPop d, GenBufs g, CacheView 
     uint8_t* stB = stA + STAGE_BYTES;
     volatile uint32_t* dtag = sc + 16;                 // [WALK_RING] level + 1 whose descriptor is in the slot
     volatile uint32_t* vcnt = sc + 16 + WALK_RING;     // [WALK_RING] case blocks of the slot's sibling done
+    unsigned long long* cur = reinterpret_cast<unsigned long long*>(smem_raw + L.cur);   // level << 32 | case block
     const uint32_t nev = nw - 1;                       // sibling evaluators (warps 1..nw-1)
     const uint32_t ring = walk_ring(Cpad);
     const uint32_t ahead = ring;                       // levels built ahead of the combination
@@ -1271,6 +1274,7 @@ __global__ void __launch_bounds__(256, 2) k_walk(DevPop d, GenBufs g, CacheView 
         // level, each without waiting for the others.  The combination stops
         // where the method stops; siblings computed past it are discarded.
         if (tid < WALK_RING) { dtag[tid] = 0u; vcnt[tid] = 0u; }
+        if (tid == 0) *cur = 0ull;
         if (tid == 0) sc[8] = 0u;                          // done flag
         __syncthreads();
         bool stopped_w = stopped;
@@ -1446,21 +1450,33 @@ __global__ void __launch_bounds__(256, 2) k_walk(DevPop d, GenBufs g, CacheView 
             __threadfence_block();
             if (lane == 0) sc[8] = 1u;                      // evaluators stop
         } else {
-            // evaluators: (level, case block) items it = warp - 1, warp - 1 + nev, ...
-            for (uint32_t it = warp - 1;; it += nev) {
-                const uint32_t k = it / ncb, cb = it - k * ncb;
+            // evaluators: each takes the next (level, case block) item in level order from a
+            // shared cursor once the level's descriptor is built, so a long sibling holds up
+            // only the warp evaluating it
+            for (;;) {
+                uint32_t k = 0, r = 0, fin = 0;
+                if (lane == 0) {
+                    uint32_t spins = 0;
+                    for (;;) {
+                        if (sc[8]) { fin = 1; break; }                  // the combination is over
+                        const unsigned long long c = *reinterpret_cast<volatile unsigned long long*>(cur);
+                        const uint32_t ck = (uint32_t)(c >> 32), cr = (uint32_t)c;
+                        const uint32_t cs = ck % ring;
+                        if (dtag[cs] == ck + 1) {
+                            __threadfence_block();
+                            const unsigned long long nx = (cr + 1 < ncb) ? c + 1 : ((unsigned long long)(ck + 1) << 32);
+                            if (atomicCAS(cur, c, nx) == c) { k = ck; r = cr; break; }
+                            continue;
+                        }
+                        if (++spins >= WALK_SPIN) { set_status(d.status, ST_TIMEOUT); fin = 1; break; }
+                        __nanosleep(64);
+                    }
+                }
+                if (__shfl_sync(FULL, fin, 0)) break;
+                k = __shfl_sync(FULL, k, 0);
+                r = __shfl_sync(FULL, r, 0);
+                const uint32_t cb = r;
                 const uint32_t slot = k % ring;
-                uint32_t spins = 0, st = 0;
-                for (;;) {
-                    st = __shfl_sync(FULL, lane == 0 ? (sc[8] ? 0xFFFFFFFFu : dtag[slot]) : 0u, 0);
-                    if (st == 0xFFFFFFFFu || st == k + 1) break;
-                    if (++spins >= WALK_SPIN) break;
-                    __nanosleep(64);
-                }
-                if (st != k + 1) {
-                    if (st != 0xFFFFFFFFu && lane == 0) set_status(d.status, ST_TIMEOUT);
-                    break;
-                }
                 __threadfence_block();
                 const LevelDesc D = desc[slot];
                 if (!(D.flags & (LD_BAD | LD_NOSIB))) {
