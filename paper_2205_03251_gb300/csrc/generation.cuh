@@ -1600,31 +1600,68 @@ __device__ __forceinline__ bool drops(const CacheView& par, int32_t e, int32_t d
     return pos > 0 && (int64_t)par.e_end[e] + delta - (int64_t)pos < (int64_t)T;
 }
 
+// Warp-collective: first index in [lo, hi) of the sorted array a with
+// a[i] >= x (hi if none), by 32-way splitting (two rounds for 1,000 entries).
+__device__ __forceinline__ uint32_t warp_lower_bound(const uint32_t* a, uint32_t lo, uint32_t hi, uint32_t x) {
+    const uint32_t lane = (uint32_t)lane_id();
+    while (hi - lo > 32) {
+        const uint32_t step = (hi - lo + 31) / 32;
+        const uint32_t last = min(lo + (lane + 1) * step, hi) - 1;     // last index of this lane's segment
+        const uint32_t m = __ballot_sync(FULL, a[last] >= x);
+        if (!m) return hi;
+        const uint32_t f = (uint32_t)__ffs(m) - 1;                      // first segment ending at >= x
+        const uint32_t nlo = lo + f * step;
+        hi = min(nlo + step, hi);
+        lo = nlo;
+    }
+    const uint32_t i = lo + lane;
+    const uint32_t m = __ballot_sync(FULL, i < hi && a[i] >= x);
+    return m ? lo + (uint32_t)__ffs(m) - 1 : hi;
+}
+
+// deepest cached ancestor of c in the mother (entry index) or -1; warp-collective
+__device__ __forceinline__ int32_t warp_mother_anchor(const CacheView& par, uint32_t me0, uint32_t me1, uint32_t c,
+                                                      uint32_t r, uint32_t T) {
+    if (c == 0) return -1;
+    const uint32_t jc = warp_lower_bound(par.e_pos, me0, me1, c);
+    if (r >= T) return (jc < me1 && par.e_pos[jc] == c) ? par.e_par[jc] : -1;
+    int32_t e = (jc > me0) ? (int32_t)(jc - 1) : -1;
+    uint32_t guard = 0;
+    while (e >= 0 && par.e_end[e] <= c && guard++ < (1u << 24)) e = par.e_par[e];
+    return e;
+}
+
+// Entry count of each child (a warp per child: its four bound searches are
+// warp-parallel, the walk over the dropped ancestors is short).
 __global__ void k_merge_count(DevPop d, GenBufs g, CacheView par) {
     if (halted(d)) return;
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < d.P; i += gridDim.x * blockDim.x) {
+    const uint32_t lane = (uint32_t)lane_id();
+    const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nwarp = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t i = gw; i < d.P; i += nwarp) {
         const uint32_t m = g.mother[i];
         const uint32_t me0 = par.e_off[m], me1 = par.e_off[m + 1];
-        if (g.lazy && !g.sel[i]) { g.mcnt[i] = 0; continue; }     // never a parent: no cache
-        if (g.flags[i] & F_CLONE) { g.mcnt[i] = me1 - me0; continue; }
+        if (g.lazy && !g.sel[i]) { if (lane == 0) g.mcnt[i] = 0; continue; }     // never a parent: no cache
+        if (g.flags[i] & F_CLONE) { if (lane == 0) g.mcnt[i] = me1 - me0; continue; }
         const uint32_t f = g.father[i], c = g.cpos[i], r = g.rsz[i], dd = g.dpos[i], s = g.ssz[i];
         const int32_t delta = (int32_t)s - (int32_t)r;
         const uint32_t fe0 = par.e_off[f], fe1 = par.e_off[f + 1];
-        const uint32_t jc = lower_bound_pos(par.e_pos, me0, me1, c);
-        const uint32_t jcr = lower_bound_pos(par.e_pos, me0, me1, c + r);
-        uint32_t jd = lower_bound_pos(par.e_pos, fe0, fe1, dd);
-        const uint32_t jds = lower_bound_pos(par.e_pos, fe0, fe1, dd + s);
+        const uint32_t jc = warp_lower_bound(par.e_pos, me0, me1, c);
+        const uint32_t jcr = warp_lower_bound(par.e_pos, me0, me1, c + r);
+        uint32_t jd = warp_lower_bound(par.e_pos, fe0, fe1, dd);
+        const uint32_t jds = warp_lower_bound(par.e_pos, fe0, fe1, dd + s);
         // a father's root is cached whatever its size; inside the child it is
         // cached only when it becomes the child's root or is itself large
         if (dd == 0 && c != 0 && s < d.T && jd < jds) ++jd;
         uint32_t ndrop = 0;
         if (delta < 0) {
-            int32_t e = mother_anchor(par, me0, me1, c, r, d.T);
+            int32_t e = warp_mother_anchor(par, me0, me1, c, r, d.T);
             uint32_t guard = 0;
             while (e >= 0 && drops(par, e, delta, d.T) && guard++ < (1u << 24)) { ++ndrop; e = par.e_par[e]; }
         }
-        g.mb[i] = make_uint4(jc, jcr, jd, jds);
-        g.mcnt[i] = (jc - me0) - ndrop + g.nins[i] + (jds - jd) + (me1 - jcr);
+        if (lane == 0) {
+            g.mb[i] = make_uint4(jc, jcr, jd, jds);
+            g.mcnt[i] = (jc - me0) - ndrop + g.nins[i] + (jds - jd) + (me1 - jcr);
+        }
     }
 }
 

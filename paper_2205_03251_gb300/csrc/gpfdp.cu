@@ -1355,7 +1355,7 @@ int gen_incremental(gp_pop* pop) {
     phase_begin(pop, PH_CACHE);
     k_pv_offsets<<<1, 1024, 0, pop->stream>>>(d, g);
     k_pv_scatter<<<gt, 256, 0, pop->stream>>>(d, g);
-    k_merge_count<<<(d.P + 255) / 256, 256, 0, pop->stream>>>(d, g, par);
+    k_merge_count<<<(d.P + 7) / 8, 256, 0, pop->stream>>>(d, g, par);
     k_merge_offsets<<<1, 1024, 0, pop->stream>>>(d, g);
     if (!d.strict_cap) {
         CK(cudaMemcpyAsync(pop->e_total_h, d.e_total, sizeof(uint32_t), cudaMemcpyDeviceToHost, pop->stream));

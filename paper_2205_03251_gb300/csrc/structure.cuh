@@ -426,28 +426,50 @@ __global__ void k_entry_chunkmax(DevPop d, StructBufs sb) {
 __global__ void k_entry_parents(DevPop d, StructBufs sb) {
     const uint32_t ne = d.e_off[d.P];
     if (ne > d.Ecap) return;
-    for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < ne; e += gridDim.x * blockDim.x) {
-        const uint32_t tree = sb.e_tree[e];
-        const uint32_t e0 = d.e_off[tree];
+    const uint32_t lane = (uint32_t)lane_id();
+    const uint32_t nch = (ne + 31) / 32;
+    const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nwarp = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t ch = gw; ch < nch; ch += nwarp) {
+        // a warp per 32 consecutive entries: the parent is the nearest earlier
+        // entry of the same tree whose subtree ends at or after this one's end
+        const uint32_t e = ch * 32 + lane;
+        const bool valid = e < ne;
+        const uint32_t tree = valid ? sb.e_tree[e] : 0u;
+        const uint32_t e0 = valid ? d.e_off[tree] : 0u;
+        const uint32_t ee = valid ? d.e_end[e] : 0u;
+        const bool need = valid && e > e0;            // a tree's root has no parent
         int32_t par = -1;
-        if (e > e0) {
-            const uint32_t ee = d.e_end[e];
-            int64_t p = (int64_t)e - 1;
-            // within e's 32-entry chunk
-            int64_t cstart = (int64_t)(e & ~31u);
-            for (; p >= (int64_t)e0 && p >= cstart; --p)
-                if (d.e_end[p] >= ee) { par = (int32_t)p; break; }
-            // earlier chunks, skipping those whose maximum end is too small
-            if (par < 0) {
-                for (int64_t ch = cstart / 32 - 1; ch >= (int64_t)(e0 / 32) && par < 0; --ch) {
-                    if (sb.e_cmax[ch] < ee) continue;
-                    for (int64_t q = ch * 32 + 31; q >= ch * 32 && q >= (int64_t)e0; --q)
-                        if (d.e_end[q] >= ee) { par = (int32_t)q; break; }
+        // inside the chunk, nearest first (values by shuffle)
+        for (uint32_t dl = 1; dl < 32; ++dl) {
+            const uint32_t ve = __shfl_up_sync(FULL, ee, dl);
+            if (need && par < 0 && lane >= dl && e - dl >= e0 && ve >= ee) par = (int32_t)(e - dl);
+        }
+        // earlier chunks, for one unresolved lane at a time: 32 chunk maxima per
+        // step, then the nearest qualifying entry of the nearest qualifying chunk
+        uint32_t pend = __ballot_sync(FULL, need && par < 0);
+        while (pend) {
+            const uint32_t l = (uint32_t)__ffs(pend) - 1;
+            pend &= pend - 1;
+            const uint32_t le = __shfl_sync(FULL, ee, l), l0 = __shfl_sync(FULL, e0, l);
+            const int64_t first = (int64_t)(l0 / 32);
+            int32_t found = -1;
+            for (int64_t top = (int64_t)ch - 1; top >= first && found < 0; top -= 32) {
+                const int64_t c2 = top - (int64_t)lane;
+                uint32_t m = __ballot_sync(FULL, c2 >= first && sb.e_cmax[c2] >= le);
+                while (m && found < 0) {
+                    const int64_t cf = top - (int64_t)(__ffs(m) - 1);      // nearest chunk left
+                    m &= m - 1;
+                    const uint32_t q = (uint32_t)cf * 32 + lane;
+                    const uint32_t mq = __ballot_sync(FULL, q >= l0 && q < ne && d.e_end[q] >= le);
+                    if (mq) found = (int32_t)((uint32_t)cf * 32 + (31 - __clz(mq)));
                 }
             }
-            if (par < 0) set_error(d, ST_STRUCT, 2, tree, d.e_pos[e], e - e0);
+            if (lane == l) par = found;
         }
-        d.e_par[e] = par;
+        if (valid) {
+            if (need && par < 0) set_error(d, ST_STRUCT, 2, tree, d.e_pos[e], e - e0);
+            d.e_par[e] = par;
+        }
     }
 }
 
