@@ -114,10 +114,12 @@ typedef struct {
     uint64_t cum_equivalent_ops;/* sums of the three counters above over those calls */
     uint64_t cum_actual_ops;
     uint64_t cum_crossover_bytes;
-    float    ms[9];             /* per-phase device milliseconds when profiling is on, mean over
+    float    ms[10];            /* per-phase device milliseconds when profiling is on, mean over
                                    the calls since profiling was (re)enabled (last 128 kept):
                                    structure, items, skeleton, fitness, crossover, walk, cache, pack,
-                                   materialise (fitness-first order: next plan and the parents' copies) */
+                                   materialise (fitness-first order: copies of the children selected
+                                   as parents), plan (fitness-first order: the next generation's
+                                   selection and crossover points, buffers for the selected) */
 } gp_stats;
 
 /*

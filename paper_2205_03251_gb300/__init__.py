@@ -44,7 +44,7 @@ class GpStats(ctypes.Structure):
                 ("stopped", ctypes.c_uint32), ("children", ctypes.c_uint32),
                 ("launches", ctypes.c_uint32), ("cum_calls", ctypes.c_uint32),
                 ("cum_equivalent_ops", ctypes.c_uint64), ("cum_actual_ops", ctypes.c_uint64),
-                ("cum_crossover_bytes", ctypes.c_uint64), ("ms", ctypes.c_float * 9)]
+                ("cum_crossover_bytes", ctypes.c_uint64), ("ms", ctypes.c_float * 10)]
 
     def as_dict(self) -> dict:
         d = {k: getattr(self, k) for k, _ in self._fields_ if k != "ms"}
@@ -61,7 +61,7 @@ class GpTuneResult(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
-PHASES = ("structure", "items", "skeleton", "fitness", "crossover", "walk", "cache", "pack", "materialise")
+PHASES = ("structure", "items", "skeleton", "fitness", "crossover", "walk", "cache", "pack", "materialise", "plan")
 
 _lib = None
 

@@ -25,7 +25,7 @@ namespace {
 
 thread_local std::string g_create_error;
 
-enum Phase { PH_STRUCT = 0, PH_ITEMS, PH_SKEL, PH_FIT, PH_XO, PH_WALK, PH_CACHE, PH_PACK, PH_MAT, NPH };
+enum Phase { PH_STRUCT = 0, PH_ITEMS, PH_SKEL, PH_FIT, PH_XO, PH_WALK, PH_CACHE, PH_PACK, PH_MAT, PH_PLAN, NPH };
 constexpr int NREC = 128;   // event pairs kept per phase: stats average the last NREC calls
 
 }  // namespace
@@ -1188,7 +1188,7 @@ int gp_get_stats(const gp_pop* cpop, gp_stats* out) {
     int rc = check_status(pop);
     if (rc) return rc;
     gp_stats s = pop->stats;
-    for (int i = 0; i < NPH && i < 9; ++i) {
+    for (int i = 0; i < NPH && i < 10; ++i) {
         s.ms[i] = 0.f;
         const bool gr = pop->stats_graph;
         uint32_t n = gr ? pop->gev_n[i] : (pop->ev_count[i] < (uint32_t)NREC ? pop->ev_count[i] : (uint32_t)NREC);
@@ -1337,10 +1337,12 @@ int gen_incremental(gp_pop* pop) {
     if (g.lazy) {
         // the next generation's plan from these children's fitness; only the
         // children it selects as parents are built and get a cache
-        phase_begin(pop, PH_MAT);
+        phase_begin(pop, PH_PLAN);
         CK(cudaMemsetAsync(g.sel, 0, sizeof(uint32_t) * d.P, pop->stream));
         k_plan_next<<<(d.P + 7) / 8, 256, 0, pop->stream>>>(d, g, par);
         k_materialise_assign<<<1, 1024, 0, pop->stream>>>(d, g);
+        phase_end(pop, PH_PLAN);
+        phase_begin(pop, PH_MAT);
         k_copy_children<<<pop->nsm * 8, 256, 0, pop->stream>>>(d, g);
         phase_end(pop, PH_MAT);
     }
