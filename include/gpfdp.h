@@ -90,8 +90,7 @@ typedef struct {
     uint64_t seed;              /* master seed of every stochastic choice */
     uint32_t walk_warps;        /* 0 = as many as fit; else at most this many warps run the walk */
     uint32_t mlp_lr_micro;      /* Adam learning rate of the packing MLP in 1e-6 units (0 = 1000) */
-    uint32_t walk_team;         /* warps per child in the incremental walk: 1, 2, 4, 8, or 0 = auto
-                                   (8 when every child gets a team at once, else 4) */
+    uint32_t walk_team;         /* warps per child in the incremental walk: 1, 2, 4, 8, or 0 = auto (4) */
     uint32_t lazy_children;     /* 1 = fitness-first order (Sec. 6.3): the walk reads each child
                                    through its parents, the next generation's plan is drawn
                                    right after it, and only the children selected as parents

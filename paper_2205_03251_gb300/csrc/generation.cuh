@@ -778,11 +778,11 @@ struct LevelDesc {
 #define LD_BAD (1u << 10)
 #define LD_NOSIB (1u << 11)
 
-#define WALK_RING 16           // most levels a walk team keeps in flight (descriptors and sibling values)
+#define WALK_RING 32           // most levels a walk team keeps in flight (descriptors and sibling values)
 #define WALK_SPIN (1u << 22)   // bound on the polls of one wait inside a walk team
 
 // levels in flight: fewer when value vectors are long
-__host__ __device__ inline uint32_t walk_ring(uint32_t Cpad) { return Cpad <= 128 ? 16u : Cpad <= 256 ? 8u : 4u; }
+__host__ __device__ inline uint32_t walk_ring(uint32_t Cpad) { return Cpad <= 128 ? 32u : Cpad <= 256 ? 8u : 4u; }
 
 template <int K>
 struct TeamLayout {

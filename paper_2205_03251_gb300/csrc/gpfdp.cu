@@ -258,10 +258,10 @@ int setup_items_kernel(gp_pop* pop) {
 }
 
 // Team size of the incremental walk (warps per child) and its launch
-// shape.  Auto: a team of 8 when every child of the population gets its own
-// team at once, else 4 (one building and combining warp and three sibling
-// evaluators: enough resident warps per SM to hide the interpreter's
-// latency when children queue for teams).
+// shape.  Auto: a team of 4 -- one building and combining warp and three
+// sibling evaluators; larger teams measured slower (their evaluators take
+// the issue slots the combining warp needs), smaller ones leave long
+// children short of evaluators.
 template <int K, int V>
 int setup_walk_kernel(gp_pop* pop, uint32_t team) {
     const uint32_t ovf = pop->d.ovf_warps;      // the walk shares the interpreter's per-warp overflow stacks
@@ -279,11 +279,7 @@ int setup_walk_kernel(gp_pop* pop, uint32_t team) {
     uint32_t nw = team;
     int grid = 0;
     size_t smem = 0;
-    if (!nw) {
-        int r = shape(8, grid, smem);
-        if (r) return r;
-        nw = ((uint32_t)grid >= pop->d.P) ? 8u : 4u;
-    }
+    if (!nw) nw = 4;
     int r = shape(nw, grid, smem);
     if (r) return r;
     pop->walk_nw = nw;
