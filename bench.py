@@ -607,7 +607,8 @@ def main():
                             "peak_note": f"{nsm} SMs x 128 FP32 lanes x {sm_max:.0f} MHz; one node x case = one lane op",
                             "timing": timing}
         # the HBM-bound part: the crossover kernels (their bytes are exact)
-        ratio = profile_figure("crossover_dram_traffic_100x1e6.md", "traffic_per_algorithmic_byte")
+        ratio = profile_figure("k_copy_children_fitness_first_200x1e6.md" if args.lazy else
+                               "crossover_dram_traffic_100x1e6.md", "traffic_per_algorithmic_byte")
         line["roofline_crossover"] = {"bound": "hbm", "achieved": xo_gbs, "peak": hbm, "unit": "GB/s",
                                       "frac": (xo_gbs / hbm) if (xo_gbs and hbm) else None,
                                       "traffic": ratio * xo_bytes if ratio else None,
