@@ -61,6 +61,8 @@ def parse():
     ap.add_argument("--threshold", type=int, default=1024)
     ap.add_argument("--cases-per-lane", type=int, default=0, choices=[0, 1, 2, 4], help="0: automatic")
     ap.add_argument("--walk-team", type=int, default=0, choices=[0, 1, 2, 4, 8], help="warps per child; 0: automatic")
+    ap.add_argument("--arena-buffers", type=int, default=0,
+                    help="tree buffers in the arena (fitness-first order; 0: 2 x trees)")
     ap.add_argument("--packing", default="mlp", choices=list(PACKING))
     ap.add_argument("--lazy", dest="lazy", action="store_true", default=True,
                     help="fitness-first order (default): build only the children selected as parents")
@@ -480,7 +482,8 @@ def main():
     maxn = w.get("max_nodes", 1 << 21)
     pop_kw = {"cache_threshold": args.threshold, "packing": PACKING[args.packing],
               "cache_budget_bytes": args.cache_budget_gb << 30, "lazy": args.lazy,
-              "cases_per_lane": args.cases_per_lane, "walk_team": args.walk_team}
+              "cases_per_lane": args.cases_per_lane, "walk_team": args.walk_team,
+              "arena_buffers": args.arena_buffers}
     tune = None
     if args.workload == "uneven" and args.autotune:
         ks = ((1,) if (boolean and kind_kw["mux_k"] == 2) else (1, 2) if (boolean or integer or args.cases <= 64)
@@ -579,6 +582,8 @@ def main():
         line["config"]["cases_per_lane"] = args.cases_per_lane
     if args.walk_team:
         line["config"]["walk_team"] = args.walk_team
+    if args.arena_buffers:
+        line["config"]["arena_buffers"] = args.arena_buffers
     if tune:
         line["config"]["cases_per_lane"] = pop_kw["cases_per_lane"]
         line["config"]["cache_threshold"] = pop_kw["cache_threshold"]

@@ -96,6 +96,12 @@ typedef struct {
                                    right after it, and only the children selected as parents
                                    get a tree buffer and a cache (no in-place construction);
                                    results are identical.  0 = build every child at crossover */
+    uint32_t arena_buffers;     /* tree buffers of max_nodes bytes: 0 = 2 x pop_size.  Fitness-first
+                                   order only, from pop_size + 1 up: a generation holds the buffers
+                                   of its parents plus those of the children it selects as the next
+                                   parents; one that finds too few free stops (later kernels return
+                                   at once) and the next synchronising call reports GP_ECAPACITY,
+                                   after which the population must be reloaded (gp_load_trees) */
 } gp_config;
 
 /* Per-call statistics of the last evaluation (host copy). */

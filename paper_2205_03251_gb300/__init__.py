@@ -34,7 +34,7 @@ class GpConfig(ctypes.Structure):
                 ("packing", ctypes.c_uint32), ("cases_per_lane", ctypes.c_uint32),
                 ("cache_budget_bytes", ctypes.c_uint64), ("seed", ctypes.c_uint64),
                 ("walk_warps", ctypes.c_uint32), ("mlp_lr_micro", ctypes.c_uint32),
-                ("walk_team", ctypes.c_uint32), ("lazy_children", ctypes.c_uint32)]
+                ("walk_team", ctypes.c_uint32), ("lazy_children", ctypes.c_uint32), ("arena_buffers", ctypes.c_uint32)]
 
 
 class GpStats(ctypes.Structure):
@@ -398,7 +398,7 @@ class Population:
                  boolean: bool = False, tournament: int = 7, packing: int = GP_PACK_STATIC,
                  cases_per_lane: int = 0, cache_budget_bytes: int = 0, seed: int = 0, stream=None,
                  walk_warps: int = 0, mlp_lr_micro: int = 0, walk_team: int = 0, lazy: bool = False,
-                 mux_k: int = 2, integer: bool = False):
+                 mux_k: int = 2, integer: bool = False, arena_buffers: int = 0):
         """boolean: the k-multiplexer (mux_k = 2: 6-mux, 64 cases; 3: 11-mux,
         2,048 cases); integer: the integer set (x, t, consts are int32)."""
         off = np.asarray(off, np.uint64)
@@ -419,7 +419,7 @@ class Population:
                        cache_threshold=cache_threshold, tournament=tournament, packing=packing,
                        cases_per_lane=cases_per_lane, cache_budget_bytes=cache_budget_bytes,
                        seed=seed & (2**64 - 1), walk_warps=walk_warps, mlp_lr_micro=mlp_lr_micro,
-                       walk_team=walk_team, lazy_children=1 if lazy else 0)
+                       walk_team=walk_team, lazy_children=1 if lazy else 0, arena_buffers=arena_buffers)
         if boolean:
             x = np.zeros(1, np.float32)
             t = np.zeros(1, np.float32)

@@ -78,9 +78,12 @@ __device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
 
 // In graph mode the cache arrays are never regrown: a kernel that finds the
 // entry count above Ecap raises ST_ENTRIES, and every later kernel of the
-// (captured) sequence that indexes a cache or a plan returns at once.
+// (captured) sequence that indexes a cache or a plan returns at once.  The
+// same holds in every mode once a generation found no free tree buffer
+// (ST_CAPACITY): its selected children have no buffer to be read from.
 __device__ __forceinline__ bool halted(const DevPop& d) {
-    return d.strict_cap && (*reinterpret_cast<const volatile uint32_t*>(d.status) & ST_ENTRIES);
+    const uint32_t st = *reinterpret_cast<const volatile uint32_t*>(d.status);
+    return (st & ST_CAPACITY) || (d.strict_cap && (st & ST_ENTRIES));
 }
 
 __device__ __forceinline__ void set_status(uint32_t* st, uint32_t bit) { atomicOr(st, bit); }

@@ -105,6 +105,7 @@ struct gp_pop {
     uint32_t host_nfree;              // pageable source of the free-stack count upload
     // disruption diagnostics
     bool dis_valid;                   // the last walk recorded into gb.dis
+    uint32_t nbuf;                    // tree buffers in the arena
 };
 
 namespace {
@@ -181,7 +182,8 @@ int check_status(gp_pop* pop) {
     if (ei[0]) snprintf(where, sizeof where, " [site %u, individual %u, position %u, detail %u]", ei[0], ei[1], ei[2], ei[3]);
     if (st & ST_ENTRIES) return fail(pop, GP_ENOMEM, "cache entry capacity (%u) exceeded", pop->d.Ecap);
     if (st & ST_SLOTS) return fail(pop, GP_ENOMEM, "cache value budget (%u slots) exceeded", pop->d.Scap);
-    if (st & ST_CAPACITY) return fail(pop, GP_ECAPACITY, "a child exceeded max_nodes");
+    if (st & ST_CAPACITY)
+        return fail(pop, GP_ECAPACITY, "out of tree buffers (arena_buffers %u; reload the population)", pop->nbuf);
     if (st & ST_TIMEOUT) return fail(pop, GP_ETIMEOUT, "a bounded device wait gave up");
     if (st & ST_STACK) return fail(pop, GP_EINVAL, "interpreter stack bound exceeded (malformed tree?)");
     if (st & ST_PATH) return fail(pop, GP_ENOMEM, "incremental path scratch exceeded");
@@ -509,6 +511,9 @@ int gp_pop_create(const gp_config* cfg_in, const float* x, const float* targets,
     if (cfg.walk_team != 0 && cfg.walk_team != 1 && cfg.walk_team != 2 && cfg.walk_team != 4 && cfg.walk_team != 8)
         return fail(nullptr, GP_EINVAL, "walk_team must be 0, 1, 2, 4 or 8");
     if (cfg.lazy_children > 1) return fail(nullptr, GP_EINVAL, "lazy_children must be 0 or 1");
+    if (cfg.arena_buffers && (!cfg.lazy_children || cfg.arena_buffers <= cfg.pop_size ||
+                              cfg.arena_buffers > 2 * cfg.pop_size))
+        return fail(nullptr, GP_EINVAL, "arena_buffers must be 0, or in (pop_size, 2 x pop_size] with lazy_children");
     const uint32_t P = cfg.pop_size;
     for (uint32_t i = 0; i < P; ++i) {
         if (offsets[i + 1] < offsets[i]) return fail(nullptr, GP_EINVAL, "offsets not increasing at %u", i);
@@ -567,7 +572,8 @@ int gp_pop_create(const gp_config* cfg_in, const float* x, const float* targets,
     const uint64_t pv_slots = (uint64_t)P * PV_PER_CHILD;
     if (pop->slot_limit < 2ull * P + pv_slots) { g_create_error = "cache budget too small for one vector per tree"; delete pop; return GP_ENOMEM; }
     if (ecap + pv_slots > pop->slot_limit) ecap = pop->slot_limit - pv_slots;
-    const uint32_t nbuf = 2 * P;     // parents + children (copy targets)
+    const uint32_t nbuf = cfg.arena_buffers ? cfg.arena_buffers : 2 * P;   // parents + children (copy targets)
+    pop->nbuf = nbuf;
     d.ovf_warps = 0;
 
     // grids
@@ -655,9 +661,9 @@ int gp_pop_create(const gp_config* cfg_in, const float* x, const float* targets,
         DA2(g.nflags, P); DA2(g.sel, P); DA2(g.nfree, 1);
         DA2(g.walkA, P); DA2(g.nins, P); DA2(g.mb, P); DA2(g.mcnt, P + 1);
         DA2(g.order, P); DA2(g.gstat, NGSTAT);
-        std::vector<uint32_t> fb(P);
-        for (uint32_t i = 0; i < P; ++i) fb[i] = P + i;          // buffers P..2P-1 start free
-        const uint32_t nfree_init = P;
+        std::vector<uint32_t> fb(P, 0u);
+        for (uint32_t i = 0; i < nbuf - P; ++i) fb[i] = P + i;   // buffers P..nbuf-1 start free
+        const uint32_t nfree_init = nbuf - P;
         if (cudaMemcpy(g.nfree, &nfree_init, sizeof nfree_init, cudaMemcpyHostToDevice) != cudaSuccess ||
             cudaMemcpy(g.free_buf, fb.data(), sizeof(uint32_t) * P, cudaMemcpyHostToDevice) != cudaSuccess)
             return bail(GP_ECUDA);
@@ -780,11 +786,14 @@ int gp_load_trees(gp_pop* pop, const uint8_t* ops, const uint64_t* offsets) {
     k_scatter_trees<<<(P < 4096 ? P : 4096), 256, 0, pop->stream>>>(pop->stage, pop->stage_off, pop->d);
     CK(cudaGetLastError());
     if (pop->host_free.size() != P) {
-        pop->host_free.resize(P);
-        for (uint32_t i = 0; i < P; ++i) pop->host_free[i] = P + i;
+        pop->host_free.assign(P, 0u);
+        for (uint32_t i = 0; i < pop->nbuf - P; ++i) pop->host_free[i] = P + i;
     }
     CK(cudaMemcpyAsync(pop->gb.free_buf, pop->host_free.data(), sizeof(uint32_t) * P, cudaMemcpyHostToDevice, pop->stream));
-    pop->host_nfree = P;
+    pop->host_nfree = pop->nbuf - P;
+    // a reload starts over: no device failure of the previous population remains
+    CK(cudaMemsetAsync(pop->d.status, 0, sizeof(uint32_t), pop->stream));
+    CK(cudaMemsetAsync(pop->d.errinfo, 0, 4 * sizeof(uint32_t), pop->stream));
     CK(cudaMemcpyAsync(pop->gb.nfree, &pop->host_nfree, sizeof(uint32_t), cudaMemcpyHostToDevice, pop->stream));
     pop->have_next_plan = false;
     pop->lazy_pending = false;

@@ -285,6 +285,7 @@ __global__ void __launch_bounds__(SCAN_TILE) k_scan_apply(DevPop d, StructBufs s
 
 // e_off / e_cnt per tree from the unit prefix.
 __global__ void k_tree_entry_offsets(DevPop d, StructBufs sb) {
+    if (halted(d)) return;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i <= d.P; i += gridDim.x * blockDim.x) {
         uint32_t v = sb.u_epre[d.blk_off[i]];
         d.e_off[i] = v;
@@ -343,6 +344,7 @@ __device__ __forceinline__ uint32_t first_chunk_at_least(const int32_t* cm, uint
 
 // end(entry) = first position q >= pos with after-balance >= bal + 1, plus one.
 __global__ void k_entry_ends(DevPop d, StructBufs sb) {
+    if (halted(d)) return;
     const uint32_t ne = sb.u_epre[d.blk_off[d.P]];
     if (ne > d.Ecap) return;
     for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < ne; e += gridDim.x * blockDim.x) {
@@ -406,6 +408,7 @@ __global__ void k_entry_ends(DevPop d, StructBufs sb) {
 }
 
 __global__ void k_entry_chunkmax(DevPop d, StructBufs sb) {
+    if (halted(d)) return;
     const uint32_t ne = d.e_off[d.P];
     if (ne > d.Ecap) return;
     const uint32_t nch = (ne + 31) / 32;
@@ -424,6 +427,7 @@ __global__ void k_entry_chunkmax(DevPop d, StructBufs sb) {
 // or after end(e): earlier entries either contain e (ancestors, end >=
 // end(e)) or end before pos(e) < end(e).
 __global__ void k_entry_parents(DevPop d, StructBufs sb) {
+    if (halted(d)) return;
     const uint32_t ne = d.e_off[d.P];
     if (ne > d.Ecap) return;
     const uint32_t lane = (uint32_t)lane_id();
@@ -474,6 +478,7 @@ __global__ void k_entry_parents(DevPop d, StructBufs sb) {
 }
 
 __global__ void k_entry_links(DevPop d, StructBufs sb) {
+    if (halted(d)) return;
     const uint32_t ne = d.e_off[d.P];
     if (ne > d.Ecap) return;
     for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < ne; e += gridDim.x * blockDim.x) {

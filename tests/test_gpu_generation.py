@@ -296,3 +296,43 @@ def test_full_size_uneven_population_sampled(gp):
         cur_off[1:] = np.cumsum(sz)
         fit = gfit
     pop.close()
+
+
+def test_memory_lean_arena(gp):
+    """Fitness-first order with fewer than 2P tree buffers: the same
+    children and fitness as with 2P while the generations fit; an arena too
+    small for a generation's selected children stops it cleanly
+    (GP_ECAPACITY at the next synchronising call), and a reload recovers."""
+    import oracle
+    import synth
+    w = synth.workload(3, n_trees=256, target=20_000)
+    P = 256
+
+    def make(nb):
+        return gp.Population(w["x"], w["t"], w["consts"], w["ops"], w["off"], max_nodes=40_000, cache_threshold=64,
+                             seed=13, lazy=True, arena_buffers=nb)
+    ref, lean = make(0), make(P + P // 2 + 8)
+    for p in (ref, lean):
+        p.eval_full()
+    for g in range(5):
+        for p in (ref, lean):
+            p.crossover(g)
+            p.eval_incremental()
+        assert oracle.canon_nan(ref.fitness()).tobytes() == oracle.canon_nan(lean.fitness()).tobytes(), g
+        assert all(np.array_equal(ref.tree(i), lean.tree(i)) for i in range(P)), g
+    ref.close()
+    lean.close()
+    tiny = make(P + 1)
+    tiny.eval_full()
+    tiny.crossover(0)
+    with pytest.raises(gp.GpError) as ei:
+        tiny.eval_incremental()                   # its statistics synchronise
+        tiny.fitness()
+    assert ei.value.code == gp.GP_ECAPACITY
+    tiny.load_trees(w["ops"], w["off"])
+    tiny.eval_full()
+    _, fit = oracle.eval_pop_f32(w["ops"], w["off"], w["consts"], w["x"], w["t"])
+    assert oracle.canon_nan(tiny.fitness()).tobytes() == oracle.canon_nan(fit).tobytes()
+    tiny.close()
+    with pytest.raises(gp.GpError):
+        gp.Population(w["x"], w["t"], w["consts"], w["ops"], w["off"], max_nodes=40_000, arena_buffers=P + 10)
