@@ -83,6 +83,7 @@ struct GenBufs {
     uint32_t *nmother, *nfather, *ncpos, *nrsz, *ndpos, *nssz, *nflags;   // [P] next generation's plan
     uint32_t* sel;                   // [P] 1 for a child that is a parent of the next generation
     uint32_t* nfree;                 // [1] entries of the free-buffer stack (lazy mode: up to 2P)
+    uint32_t* pref;                  // [P] parent read by a child of this generation (mother or father)
     // disruption diagnostics (Fig. 4): per child and walk level, the cases
     // where the child's value differs from the mother's
     DisLevel* dis;                   // [P][dis_L], null when not recording
@@ -481,24 +482,39 @@ __global__ void __launch_bounds__(1024) k_assign_lazy(DevPop d, GenBufs g) {
 __global__ void __launch_bounds__(1024) k_materialise_assign(DevPop d, GenBufs g) {
     if (halted(d)) return;
     __shared__ uint64_t ws[32];
-    __shared__ uint64_t carry[3];
+    __shared__ uint64_t carry[4];
     __shared__ uint32_t nfree0;
-    if (threadIdx.x < 3) carry[threadIdx.x] = 0;
+    if (threadIdx.x < 4) carry[threadIdx.x] = 0;
     if (threadIdx.x == 0) nfree0 = *g.nfree;
-    __syncthreads();
     const uint32_t P = d.P;
-    // count the selected children first: they take the top of the stack
+    // parents that a child of this generation reads (its mother's tree, or
+    // its father's, for the trees of the children that are not built)
+    for (uint32_t j = threadIdx.x; j < P; j += blockDim.x) g.pref[j] = 0u;
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) { g.pref[g.mother[i]] = 1u; g.pref[g.father[i]] = 1u; }
+    __syncthreads();
+    // parents no child reads give their buffers back first (the initial
+    // population's unselected trees); the selected children then take the
+    // top of the stack
+    for (uint32_t base = 0; base < P; base += blockDim.x) {
+        const uint32_t j = base + threadIdx.x;
+        const uint32_t b = (j < P) ? g.pbuf[j] : BUF_NONE;
+        const uint32_t dead = (b != BUF_NONE && !g.pref[j]) ? 1u : 0u;
+        const uint64_t pos = block_excl_scan(dead, ws, &carry[3]);
+        if (dead) g.free_buf[nfree0 + pos] = b;
+    }
     for (uint32_t base = 0; base < P; base += blockDim.x) {
         const uint32_t i = base + threadIdx.x;
         const uint32_t selc = (i < P && g.sel[i]) ? 1u : 0u;
         block_excl_scan(selc, ws, &carry[2]);
     }
     const uint32_t nsel = (uint32_t)carry[2];
-    if (nsel > nfree0) {
+    const uint32_t nfree1 = nfree0 + (uint32_t)carry[3];
+    if (nsel > nfree1) {
         if (threadIdx.x == 0) set_status(d.status, ST_CAPACITY);
         return;
     }
-    const uint32_t take0 = nfree0 - nsel;
+    const uint32_t take0 = nfree1 - nsel;
     for (uint32_t base = 0; base < P; base += blockDim.x) {
         const uint32_t i = base + threadIdx.x;
         uint32_t selc = 0, nch = 0;
@@ -518,14 +534,15 @@ __global__ void __launch_bounds__(1024) k_materialise_assign(DevPop d, GenBufs g
         }
     }
     __syncthreads();
-    // previous parents' buffers back on the stack
+    // the parents that children read go back on the stack after the targets:
+    // they are overwritten no earlier than the next generation's copies
     __shared__ uint64_t cfree;
     if (threadIdx.x == 0) cfree = 0;
     __syncthreads();
     for (uint32_t base = 0; base < P; base += blockDim.x) {
         const uint32_t j = base + threadIdx.x;
         const uint32_t b = (j < P) ? g.pbuf[j] : BUF_NONE;
-        const uint32_t has = (b != BUF_NONE) ? 1u : 0u;
+        const uint32_t has = (b != BUF_NONE && g.pref[j]) ? 1u : 0u;
         const uint64_t pos = block_excl_scan(has, ws, &cfree);
         if (has) g.free_buf[take0 + pos] = b;
     }

@@ -658,7 +658,7 @@ int gp_pop_create(const gp_config* cfg_in, const float* x, const float* targets,
         DA2(g.rec_entry, g.pvcap);
         g.lazy = cfg.lazy_children;
         DA2(g.nmother, P); DA2(g.nfather, P); DA2(g.ncpos, P); DA2(g.nrsz, P); DA2(g.ndpos, P); DA2(g.nssz, P);
-        DA2(g.nflags, P); DA2(g.sel, P); DA2(g.nfree, 1);
+        DA2(g.nflags, P); DA2(g.sel, P); DA2(g.nfree, 1); DA2(g.pref, P);
         DA2(g.walkA, P); DA2(g.nins, P); DA2(g.mb, P); DA2(g.mcnt, P + 1);
         DA2(g.order, P); DA2(g.gstat, NGSTAT);
         std::vector<uint32_t> fb(P, 0u);

@@ -300,7 +300,8 @@ def test_full_size_uneven_population_sampled(gp):
 
 def test_memory_lean_arena(gp):
     """Fitness-first order with fewer than 2P tree buffers: the same
-    children and fitness as with 2P while the generations fit; an arena too
+    children and fitness as with 2P while the generations fit (parents that
+    no child reads give their buffers back before the copies); an arena too
     small for a generation's selected children stops it cleanly
     (GP_ECAPACITY at the next synchronising call), and a reload recovers."""
     import oracle
@@ -308,10 +309,10 @@ def test_memory_lean_arena(gp):
     w = synth.workload(3, n_trees=256, target=20_000)
     P = 256
 
-    def make(nb):
+    def make(nb, tournament=7):
         return gp.Population(w["x"], w["t"], w["consts"], w["ops"], w["off"], max_nodes=40_000, cache_threshold=64,
-                             seed=13, lazy=True, arena_buffers=nb)
-    ref, lean = make(0), make(P + P // 2 + 8)
+                             seed=13, lazy=True, arena_buffers=nb, tournament=tournament)
+    ref, lean = make(0), make(P + P // 4)
     for p in (ref, lean):
         p.eval_full()
     for g in range(5):
@@ -322,7 +323,8 @@ def test_memory_lean_arena(gp):
         assert all(np.array_equal(ref.tree(i), lean.tree(i)) for i in range(P)), g
     ref.close()
     lean.close()
-    tiny = make(P + 1)
+    # random selection (tournaments of one) builds ~86 % of the children: P + 1 buffers cannot hold them
+    tiny = make(P + 1, tournament=1)
     tiny.eval_full()
     tiny.crossover(0)
     with pytest.raises(gp.GpError) as ei:
