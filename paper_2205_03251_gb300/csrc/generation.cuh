@@ -854,7 +854,7 @@ __device__ __forceinline__ void eval_run(const uint8_t* src, uint32_t s, uint32_
     for (int k = 0; k < K; ++k) st.acc[k] = 0.f;
     st.sp = 0;
     st.ok = true;
-    interp_staged<K, V>(stage, s, e, st, c);
+    interp_staged_lone<K, V>(stage, s, e, st, c);
     if (!st.ok && lane_id() == 0) set_status(status, ST_STACK);
 #pragma unroll
     for (int k = 0; k < K; ++k) out[k] = st.acc[k];
@@ -1168,7 +1168,7 @@ __global__ void __launch_bounds__(256, 2) k_walk(DevPop d, GenBufs g, CacheView 
                     for (int kk = 0; kk < K; ++kk) ist.acc[kk] = 0.f;
                     ist.sp = 0;
                     ist.ok = true;
-                    interp_staged<K, V>(stA, 0, nk, ist, ic);
+                    interp_staged_lone<K, V>(stA, 0, nk, ist, ic);
                     if (!ist.ok && lane == 0) set_status(d.status, ST_STACK);
 #pragma unroll
                     for (int kk = 0; kk < K; ++kk) v[kk] = ist.acc[kk];
