@@ -98,6 +98,8 @@ struct gp_pop {
     uint32_t graph_n;                 // generations per replay
     uint32_t graph_launches;          // kernel launches per replay
     cudaStream_t cap_stream;          // private capture stream when the population runs on the legacy stream
+    cudaStream_t side;                // second stream: the packing MLP's training beside the cache update
+    cudaEvent_t fork_ev, join_ev;
     // fitness-first materialisation
     bool have_next_plan;              // the last walk drew the next generation's plan
     uint32_t planned_gen;             // ... for this generation number
@@ -539,6 +541,8 @@ int gp_pop_create(const gp_config* cfg_in, const float* x, const float* targets,
     pop->gexec = nullptr;
     pop->graph_n = 0;
     pop->cap_stream = nullptr;
+    pop->side = nullptr;
+    pop->fork_ev = pop->join_ev = nullptr;
     pop->gev_made = pop->capturing = pop->graph_prof = pop->stats_graph = false;
     memset(pop->gev_n, 0, sizeof pop->gev_n);
     auto bail = [&](int code) { gp_pop_destroy(pop); return code; };
@@ -547,6 +551,13 @@ int gp_pop_create(const gp_config* cfg_in, const float* x, const float* targets,
     cudaDeviceGetAttribute(&pop->nsm, cudaDevAttrMultiProcessorCount, pop->dev);
     for (int i = 0; i < NPH; ++i)
         for (int j = 0; j < NREC; ++j) { cudaEventCreate(&pop->ev[i][j][0]); cudaEventCreate(&pop->ev[i][j][1]); }
+    if (cudaStreamCreateWithFlags(&pop->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&pop->fork_ev, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&pop->join_ev, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        g_create_error = "stream or event creation failed";
+        return bail(GP_ECUDA);
+    }
 
     DevPop& d = pop->d;
     memset(&d, 0, sizeof d);
@@ -746,6 +757,9 @@ void gp_pop_destroy(gp_pop* pop) {
     if (pop->stream) cudaStreamSynchronize(pop->stream); else cudaDeviceSynchronize();
     if (pop->gexec) cudaGraphExecDestroy(pop->gexec);
     if (pop->cap_stream) cudaStreamDestroy(pop->cap_stream);
+    if (pop->side) cudaStreamDestroy(pop->side);
+    if (pop->fork_ev) cudaEventDestroy(pop->fork_ev);
+    if (pop->join_ev) cudaEventDestroy(pop->join_ev);
     cudaFree(pop->gb.dis); cudaFree(pop->gb.dis_n);
     cudaFree(pop->pool); cudaFree(pop->live); cudaFree(pop->freeslot); cudaFree(pop->ftile);
     for (void* p : pop->allocs) cudaFree(p);
@@ -1351,14 +1365,6 @@ int gen_incremental(gp_pop* pop) {
         k_copy_children<<<pop->nsm * 8, 256, 0, pop->stream>>>(d, g);
         phase_end(pop, PH_MAT);
     }
-    // online training of the packing MLP on the levels the walks took
-    k_mlp_targets<<<pb, 256, 0, pop->stream>>>(d, g, pop->mlp);
-    k_mlp_train_pass<<<mb, 256, 0, pop->stream>>>(pop->mlp, d.P);
-    k_mlp_loss<<<1, 256, 0, pop->stream>>>(pop->mlp, d.P);
-    k_mlp_grad_chunks<<<(d.P + MLP_CH - 1) / MLP_CH, 256, 0, pop->stream>>>(pop->mlp, d.P);
-    k_mlp_grad_reduce<<<(MLP_NP + 255) / 256, 256, 0, pop->stream>>>(pop->mlp, d.P);
-    k_mlp_adam<<<(MLP_NP + 255) / 256, 256, 0, pop->stream>>>(pop->mlp, pop->mlp_lr);
-    k_mlp_bump<<<1, 32, 0, pop->stream>>>(pop->mlp);
     phase_begin(pop, PH_CACHE);
     k_pv_offsets<<<1, 1024, 0, pop->stream>>>(d, g);
     k_pv_scatter<<<gt, 256, 0, pop->stream>>>(d, g);
@@ -1378,6 +1384,22 @@ int gen_incremental(gp_pop* pop) {
             k_merge_offsets<<<1, 1024, 0, pop->stream>>>(d, g);
         }
     }
+    // online training of the packing MLP on the levels the walks took, on a
+    // second stream beside the rest of the cache update (independent data;
+    // joined before the generation ends)
+    {
+        cudaStream_t ms = pop->side;
+        CK(cudaEventRecord(pop->fork_ev, pop->stream));
+        CK(cudaStreamWaitEvent(ms, pop->fork_ev, 0));
+        k_mlp_targets<<<pb, 256, 0, ms>>>(d, g, pop->mlp);
+        k_mlp_train_pass<<<mb, 256, 0, ms>>>(pop->mlp, d.P);
+        k_mlp_loss<<<1, 256, 0, ms>>>(pop->mlp, d.P);
+        k_mlp_grad_chunks<<<(d.P + MLP_CH - 1) / MLP_CH, 256, 0, ms>>>(pop->mlp, d.P);
+        k_mlp_grad_reduce<<<(MLP_NP + 255) / 256, 256, 0, ms>>>(pop->mlp, d.P);
+        k_mlp_adam<<<(MLP_NP + 255) / 256, 256, 0, ms>>>(pop->mlp, pop->mlp_lr);
+        k_mlp_bump<<<1, 32, 0, ms>>>(pop->mlp);
+        CK(cudaEventRecord(pop->join_ev, ms));
+    }
     k_merge_write<<<d.P < (uint32_t)pop->nsm * 8 ? d.P : pop->nsm * 8, 256, 0, pop->stream>>>(d, g, par);
     k_mark_live<<<gt, 256, 0, pop->stream>>>(d, g);
     k_free_count<<<pop->nsm * 2, 1024, 0, pop->stream>>>(d, g);
@@ -1388,6 +1410,7 @@ int gen_incremental(gp_pop* pop) {
     k_entry_parents<<<gt, 256, 0, pop->stream>>>(d, pop->sb);
     k_entry_links<<<gt, 256, 0, pop->stream>>>(d, pop->sb);
     k_child_sizes<<<(d.P + 255) / 256, 256, 0, pop->stream>>>(d, g);
+    CK(cudaStreamWaitEvent(pop->stream, pop->join_ev, 0));
     phase_end(pop, PH_CACHE);
     k_accumulate<<<1, 32, 0, pop->stream>>>(pop->cum, d.acc_ops, g.gstat, pop->cases_stat, 1);
     ++pop->cum_calls;
