@@ -99,7 +99,8 @@ struct gp_pop {
     uint32_t graph_launches;          // kernel launches per replay
     cudaStream_t cap_stream;          // private capture stream when the population runs on the legacy stream
     cudaStream_t side;                // second stream: the packing MLP's training beside the cache update
-    cudaEvent_t fork_ev, join_ev;
+    cudaEvent_t fork_ev, join_ev;     // training fork / join
+    cudaEvent_t pfork_ev, pjoin_ev;   // work-order fork (at crossover) / join (before the walk)
     // fitness-first materialisation
     bool have_next_plan;              // the last walk drew the next generation's plan
     uint32_t planned_gen;             // ... for this generation number
@@ -150,25 +151,27 @@ int dalloc(gp_pop* pop, T** ptr, size_t count) {
         if (r_) return r_;                           \
     } while (0)
 
-void phase_begin(gp_pop* pop, int ph) {
+void phase_begin(gp_pop* pop, int ph, cudaStream_t st) {
     if (!pop->profiling) return;
     if (pop->capturing) {
         if (pop->gev_n[ph] < (uint32_t)NREC)
-            cudaEventRecordWithFlags(pop->gev[ph][pop->gev_n[ph]][0], pop->stream, cudaEventRecordExternal);
+            cudaEventRecordWithFlags(pop->gev[ph][pop->gev_n[ph]][0], st, cudaEventRecordExternal);
         return;
     }
-    cudaEventRecord(pop->ev[ph][pop->ev_count[ph] % NREC][0], pop->stream);
+    cudaEventRecord(pop->ev[ph][pop->ev_count[ph] % NREC][0], st);
 }
-void phase_end(gp_pop* pop, int ph) {
+void phase_end(gp_pop* pop, int ph, cudaStream_t st) {
     if (!pop->profiling) return;
     if (pop->capturing) {
         if (pop->gev_n[ph] < (uint32_t)NREC)
-            cudaEventRecordWithFlags(pop->gev[ph][pop->gev_n[ph]++][1], pop->stream, cudaEventRecordExternal);
+            cudaEventRecordWithFlags(pop->gev[ph][pop->gev_n[ph]++][1], st, cudaEventRecordExternal);
         return;
     }
     pop->stats_graph = false;
-    cudaEventRecord(pop->ev[ph][pop->ev_count[ph]++ % NREC][1], pop->stream);
+    cudaEventRecord(pop->ev[ph][pop->ev_count[ph]++ % NREC][1], st);
 }
+void phase_begin(gp_pop* pop, int ph) { phase_begin(pop, ph, pop->stream); }
+void phase_end(gp_pop* pop, int ph) { phase_end(pop, ph, pop->stream); }
 
 int check_status(gp_pop* pop) {
     uint32_t st = 0;
@@ -542,7 +545,7 @@ int gp_pop_create(const gp_config* cfg_in, const float* x, const float* targets,
     pop->graph_n = 0;
     pop->cap_stream = nullptr;
     pop->side = nullptr;
-    pop->fork_ev = pop->join_ev = nullptr;
+    pop->fork_ev = pop->join_ev = pop->pfork_ev = pop->pjoin_ev = nullptr;
     pop->gev_made = pop->capturing = pop->graph_prof = pop->stats_graph = false;
     memset(pop->gev_n, 0, sizeof pop->gev_n);
     auto bail = [&](int code) { gp_pop_destroy(pop); return code; };
@@ -553,7 +556,9 @@ int gp_pop_create(const gp_config* cfg_in, const float* x, const float* targets,
         for (int j = 0; j < NREC; ++j) { cudaEventCreate(&pop->ev[i][j][0]); cudaEventCreate(&pop->ev[i][j][1]); }
     if (cudaStreamCreateWithFlags(&pop->side, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&pop->fork_ev, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&pop->join_ev, cudaEventDisableTiming) != cudaSuccess) {
+        cudaEventCreateWithFlags(&pop->join_ev, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&pop->pfork_ev, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&pop->pjoin_ev, cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();
         g_create_error = "stream or event creation failed";
         return bail(GP_ECUDA);
@@ -760,6 +765,8 @@ void gp_pop_destroy(gp_pop* pop) {
     if (pop->side) cudaStreamDestroy(pop->side);
     if (pop->fork_ev) cudaEventDestroy(pop->fork_ev);
     if (pop->join_ev) cudaEventDestroy(pop->join_ev);
+    if (pop->pfork_ev) cudaEventDestroy(pop->pfork_ev);
+    if (pop->pjoin_ev) cudaEventDestroy(pop->pjoin_ev);
     cudaFree(pop->gb.dis); cudaFree(pop->gb.dis_n);
     cudaFree(pop->pool); cudaFree(pop->live); cudaFree(pop->freeslot); cudaFree(pop->ftile);
     for (void* p : pop->allocs) cudaFree(p);
@@ -1280,6 +1287,33 @@ void launch_walk(gp_pop* pop, const CacheView& par) {
 // children (copy, or in place for the last child of a mother).  The
 // parents' trees stay addressable through the retained buffer indices until
 // their buffers are overwritten; their cache set is kept for the walk.
+// Work order of the coming walk (A10): MLP features and prediction, or the
+// mother-size key, and the sort -- on the second stream, as soon as the
+// plan exists, beside the crossover kernels; the walk waits for it.
+int launch_pack(gp_pop* pop, const CacheView& par) {
+    DevPop& d = pop->d;
+    GenBufs& g = pop->gb;
+    cudaStream_t ms = pop->side;
+    CK(cudaEventRecord(pop->pfork_ev, pop->stream));
+    CK(cudaStreamWaitEvent(ms, pop->pfork_ev, 0));
+    phase_begin(pop, PH_PACK, ms);
+    const int pb = (d.P + 255) / 256;
+    k_mlp_features<<<pb, 256, 0, ms>>>(d, g, par, pop->mlp);
+    const int mb = (d.P + 7) / 8 < pop->nsm * 2 ? (d.P + 7) / 8 : pop->nsm * 2;   // 8 samples per CTA pass
+    k_mlp_infer<<<mb, 256, 0, ms>>>(pop->mlp, d.P, pop->mlp.pred_pack);
+    if (pop->cfg.packing == GP_PACK_MLP && d.P <= SORT_MAX) {
+        k_sort_desc<<<1, 1024, 0, ms>>>(pop->mlp.pred_pack, d.P, g.order);
+    } else if (pop->cfg.packing == GP_PACK_STATIC && d.P <= SORT_MAX) {
+        k_static_key<<<pb, 256, 0, ms>>>(d, g, pop->mlp);
+        k_sort_desc<<<1, 1024, 0, ms>>>(pop->mlp.target, d.P, g.order);
+    } else {
+        k_order_identity<<<pb, 256, 0, ms>>>(d, g);
+    }
+    phase_end(pop, PH_PACK, ms);
+    CK(cudaEventRecord(pop->pjoin_ev, ms));
+    return GP_OK;
+}
+
 int gen_crossover(gp_pop* pop, uint32_t generation) {
     DevPop& d = pop->d;
     GenBufs& g = pop->gb;
@@ -1302,6 +1336,10 @@ int gen_crossover(gp_pop* pop, uint32_t generation) {
         // evaluated parents), fragments and stash; the children are built later
         if (pop->have_next_plan) k_plan_take<<<(d.P + 255) / 256, 256, 0, pop->stream>>>(d, g);
         else k_plan<<<(d.P + 7) / 8, 256, 0, pop->stream>>>(d, g, par);
+        {
+            int r = launch_pack(pop, par);
+            if (r) return r;
+        }
         k_assign_lazy<<<1, 1024, 0, pop->stream>>>(d, g);
         k_gather<<<pop->nsm * 4, 256, 0, pop->stream>>>(d, g);
         phase_end(pop, PH_XO);
@@ -1313,6 +1351,10 @@ int gen_crossover(gp_pop* pop, uint32_t generation) {
         return GP_OK;
     }
     k_plan<<<(d.P + 7) / 8, 256, 0, pop->stream>>>(d, g, par);
+    {
+        int r = launch_pack(pop, par);
+        if (r) return r;
+    }
     k_assign<<<1, 1024, 0, pop->stream>>>(d, g);
     k_gather<<<pop->nsm * 4, 256, 0, pop->stream>>>(d, g);
     k_copy_children<<<pop->nsm * 8, 256, 0, pop->stream>>>(d, g);
@@ -1336,20 +1378,10 @@ int gen_incremental(gp_pop* pop) {
     const CacheView par = view_of(pop, pop->sets[pop->cur ^ 1]);
     const int gt = pop->grid_threads;
     CK(cudaMemsetAsync(d.q, 0, sizeof(uint32_t) * NQ, pop->stream));
-    phase_begin(pop, PH_PACK);
     const int pb = (d.P + 255) / 256;
-    k_mlp_features<<<pb, 256, 0, pop->stream>>>(d, g, par, pop->mlp);
     const int mb = (d.P + 7) / 8 < pop->nsm * 2 ? (d.P + 7) / 8 : pop->nsm * 2;   // 8 samples per CTA pass
-    k_mlp_infer<<<mb, 256, 0, pop->stream>>>(pop->mlp, d.P, pop->mlp.pred_pack);
-    if (pop->cfg.packing == GP_PACK_MLP && d.P <= SORT_MAX) {
-        k_sort_desc<<<1, 1024, 0, pop->stream>>>(pop->mlp.pred_pack, d.P, g.order);
-    } else if (pop->cfg.packing == GP_PACK_STATIC && d.P <= SORT_MAX) {
-        k_static_key<<<pb, 256, 0, pop->stream>>>(d, g, pop->mlp);
-        k_sort_desc<<<1, 1024, 0, pop->stream>>>(pop->mlp.target, d.P, g.order);
-    } else {
-        k_order_identity<<<pb, 256, 0, pop->stream>>>(d, g);
-    }
-    phase_end(pop, PH_PACK);
+    // the work order was computed on the second stream since the crossover
+    CK(cudaStreamWaitEvent(pop->stream, pop->pjoin_ev, 0));
     phase_begin(pop, PH_WALK);
     with_kind(d, [&](auto k, auto v) { launch_walk<decltype(k)::value, decltype(v)::value>(pop, par); return 0; });
     phase_end(pop, PH_WALK);
