@@ -98,7 +98,9 @@ struct gp_pop {
     uint32_t graph_n;                 // generations per replay
     uint32_t graph_launches;          // kernel launches per replay
     cudaStream_t cap_stream;          // private capture stream when the population runs on the legacy stream
-    cudaStream_t side;                // second stream: the packing MLP's training beside the cache update
+    cudaStream_t side;                // second stream: work order (at crossover), copies (beside the cache update)
+    cudaStream_t side2;               // third stream: the packing MLP's training beside the cache update
+    cudaEvent_t cfork_ev, cjoin_ev;   // copies fork / join
     cudaEvent_t fork_ev, join_ev;     // training fork / join
     cudaEvent_t pfork_ev, pjoin_ev;   // work-order fork (at crossover) / join (before the walk)
     // fitness-first materialisation
@@ -545,6 +547,8 @@ int gp_pop_create(const gp_config* cfg_in, const float* x, const float* targets,
     pop->graph_n = 0;
     pop->cap_stream = nullptr;
     pop->side = nullptr;
+    pop->side2 = nullptr;
+    pop->cfork_ev = pop->cjoin_ev = nullptr;
     pop->fork_ev = pop->join_ev = pop->pfork_ev = pop->pjoin_ev = nullptr;
     pop->gev_made = pop->capturing = pop->graph_prof = pop->stats_graph = false;
     memset(pop->gev_n, 0, sizeof pop->gev_n);
@@ -555,6 +559,9 @@ int gp_pop_create(const gp_config* cfg_in, const float* x, const float* targets,
     for (int i = 0; i < NPH; ++i)
         for (int j = 0; j < NREC; ++j) { cudaEventCreate(&pop->ev[i][j][0]); cudaEventCreate(&pop->ev[i][j][1]); }
     if (cudaStreamCreateWithFlags(&pop->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&pop->side2, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&pop->cfork_ev, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&pop->cjoin_ev, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&pop->fork_ev, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&pop->join_ev, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&pop->pfork_ev, cudaEventDisableTiming) != cudaSuccess ||
@@ -760,9 +767,14 @@ int gp_pop_create(const gp_config* cfg_in, const float* x, const float* targets,
 void gp_pop_destroy(gp_pop* pop) {
     if (!pop) return;
     if (pop->stream) cudaStreamSynchronize(pop->stream); else cudaDeviceSynchronize();
+    if (pop->side) cudaStreamSynchronize(pop->side);
+    if (pop->side2) cudaStreamSynchronize(pop->side2);
     if (pop->gexec) cudaGraphExecDestroy(pop->gexec);
     if (pop->cap_stream) cudaStreamDestroy(pop->cap_stream);
     if (pop->side) cudaStreamDestroy(pop->side);
+    if (pop->side2) cudaStreamDestroy(pop->side2);
+    if (pop->cfork_ev) cudaEventDestroy(pop->cfork_ev);
+    if (pop->cjoin_ev) cudaEventDestroy(pop->cjoin_ev);
     if (pop->fork_ev) cudaEventDestroy(pop->fork_ev);
     if (pop->join_ev) cudaEventDestroy(pop->join_ev);
     if (pop->pfork_ev) cudaEventDestroy(pop->pfork_ev);
@@ -1393,9 +1405,14 @@ int gen_incremental(gp_pop* pop) {
         k_plan_next<<<(d.P + 7) / 8, 256, 0, pop->stream>>>(d, g, par);
         k_materialise_assign<<<1, 1024, 0, pop->stream>>>(d, g);
         phase_end(pop, PH_PLAN);
-        phase_begin(pop, PH_MAT);
-        k_copy_children<<<pop->nsm * 8, 256, 0, pop->stream>>>(d, g);
-        phase_end(pop, PH_MAT);
+        // the copies on the second stream, beside the cache update (which
+        // reads and writes caches only); joined before the generation ends
+        CK(cudaEventRecord(pop->cfork_ev, pop->stream));
+        CK(cudaStreamWaitEvent(pop->side, pop->cfork_ev, 0));
+        phase_begin(pop, PH_MAT, pop->side);
+        k_copy_children<<<pop->nsm * 8, 256, 0, pop->side>>>(d, g);
+        phase_end(pop, PH_MAT, pop->side);
+        CK(cudaEventRecord(pop->cjoin_ev, pop->side));
     }
     phase_begin(pop, PH_CACHE);
     k_pv_offsets<<<1, 1024, 0, pop->stream>>>(d, g);
@@ -1409,8 +1426,10 @@ int gen_incremental(gp_pop* pop) {
             uint64_t want = (uint64_t)*pop->e_total_h + *pop->e_total_h / 4 + 64;
             const uint64_t room = pop->slot_limit > pop->gb.pvcap ? pop->slot_limit - pop->gb.pvcap : 0;
             if (want > room) want = room;
-            if (want < *pop->e_total_h)
+            if (want < *pop->e_total_h) {
+                if (g.lazy) cudaStreamWaitEvent(pop->stream, pop->cjoin_ev, 0);
                 return fail(pop, GP_ENOMEM, "cache of %u entries exceeds the cache budget", *pop->e_total_h);
+            }
             int r = grow_cache(pop, (uint32_t)want);
             if (r) return r;
             k_merge_offsets<<<1, 1024, 0, pop->stream>>>(d, g);
@@ -1420,7 +1439,7 @@ int gen_incremental(gp_pop* pop) {
     // second stream beside the rest of the cache update (independent data;
     // joined before the generation ends)
     {
-        cudaStream_t ms = pop->side;
+        cudaStream_t ms = pop->side2;
         CK(cudaEventRecord(pop->fork_ev, pop->stream));
         CK(cudaStreamWaitEvent(ms, pop->fork_ev, 0));
         k_mlp_targets<<<pb, 256, 0, ms>>>(d, g, pop->mlp);
@@ -1443,6 +1462,7 @@ int gen_incremental(gp_pop* pop) {
     k_entry_links<<<gt, 256, 0, pop->stream>>>(d, pop->sb);
     k_child_sizes<<<(d.P + 255) / 256, 256, 0, pop->stream>>>(d, g);
     CK(cudaStreamWaitEvent(pop->stream, pop->join_ev, 0));
+    if (g.lazy) CK(cudaStreamWaitEvent(pop->stream, pop->cjoin_ev, 0));
     phase_end(pop, PH_CACHE);
     k_accumulate<<<1, 32, 0, pop->stream>>>(pop->cum, d.acc_ops, g.gstat, pop->cases_stat, 1);
     ++pop->cum_calls;
