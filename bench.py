@@ -42,6 +42,32 @@ N_SM_DEFAULT = 152
 FP32_LANES_PER_SM = 128
 
 
+def reduce_timing(dist, device, ms: float, eq: float, act: float):
+    """Across ranks (weak scaling): the slowest rank's time and the sums of
+    all ranks' equivalent and actual operations, so that value = all the
+    work done / the time of the slowest rank.  dist None: one process."""
+    if dist is None:
+        return ms, eq, act
+    import torch
+    t = torch.tensor([ms], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    tot = torch.tensor([float(eq), float(act)], device=device, dtype=torch.float64)
+    dist.all_reduce(tot)
+    e, a = tot.tolist()
+    return float(t.item()), e, a
+
+
+def reduce_e2e(dist, device, value: float, world: int) -> float:
+    """End-to-end rate across ranks: the slowest rank's rate times the
+    number of ranks."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MIN)
+    return float(t.item()) * world
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -549,16 +575,7 @@ def main():
     clk = clocks.stop()
     if chunk:
         gen[0] += args.steps
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-        tot = torch.tensor([float(st["cum_equivalent_ops"]), float(st["cum_actual_ops"])], device="cuda",
-                           dtype=torch.float64)
-        dist.all_reduce(tot)
-        eq_total, act_total = tot.tolist()
-    else:
-        eq_total, act_total = st["cum_equivalent_ops"], st["cum_actual_ops"]
+    ms, eq_total, act_total = reduce_timing(dist, "cuda", ms, st["cum_equivalent_ops"], st["cum_actual_ops"])
     value = eq_total / (ms * 1e-3) / 1e9
     actual = act_total / (ms * 1e-3) / 1e9
     phases = dict(zip(gp.PHASES, st["ms"]))
@@ -669,10 +686,7 @@ def main():
         eq = pop.stats()["equivalent_ops"]
         e2e = {"value": eq * args.e2e_steps / e2e_s / 1e9, "unit": "GPop/s",
                "h2d_bytes_per_step": int(w["off"][-1]) + 8 * (P + 1), "d2h_bytes_per_step": 4 * P}
-    if dist:
-        t = torch.tensor([e2e["value"]], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MIN)
-        e2e["value"] = float(t.item()) * world
+    e2e["value"] = reduce_e2e(dist, "cuda", e2e["value"], world)
     line["e2e"] = e2e
     if generational:
         line["disruption"] = disruption_profile(pop, gen_step, _cases(w))
