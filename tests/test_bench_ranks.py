@@ -6,7 +6,6 @@ import os
 import socket
 
 
-
 def _port() -> int:
     with socket.socket() as s:
         s.bind(("127.0.0.1", 0))
