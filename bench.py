@@ -654,11 +654,23 @@ def main():
     P = len(w["off"]) - 1
     if generational:
         # a generation has no host inputs (the population stays resident); the host reads back the
-        # fitness of every child and the best child's tree each step
+        # fitness of every child and the best child's tree after each step.  With graphs a step is
+        # one replay of a captured pair of generations (gp_graph_launch), else one eager generation
+        # (gp_crossover + gp_eval_incremental)
+        per = 2 if chunk else 1
+        if chunk:
+            pop.graph_capture(gen[0], per)
+            pop.set_profiling(False)                   # counts the e2e replays only
+
+            def e2e_step():
+                pop.graph_launch()
+                gen[0] += per
+        else:
+            e2e_step = gen_step
         t0 = time.perf_counter()
         d2h = 0
         for _ in range(args.e2e_steps):
-            gen_step()
+            e2e_step()
             f = pop.fitness()
             best = int(np.nanargmin(f)) if np.isfinite(f).any() else 0
             tr = pop.tree(best)
@@ -667,8 +679,9 @@ def main():
         eq = pop.stats()["cum_equivalent_ops"]          # summed on the device over the e2e steps
         e2e = {"value": eq / e2e_s / 1e9, "unit": "GPop/s", "h2d_bytes_per_step": 0,
                "d2h_bytes_per_step": d2h // args.e2e_steps,
-               "note": "eager generation steps through gp_crossover + gp_eval_incremental + gp_fitness + "
-                       "gp_get_tree"}
+               "note": ("per step one gp_graph_launch of 2 captured generations" if chunk else
+                        "per step one eager generation (gp_crossover + gp_eval_incremental)")
+               + ", then gp_fitness and gp_get_tree of the best child; wall clock"}
     else:
         pinned = torch.empty(len(w["ops"]), dtype=torch.uint8, pin_memory=True)
         pinned.numpy()[:] = w["ops"]
