@@ -338,3 +338,32 @@ def test_memory_lean_arena(gp):
     tiny.close()
     with pytest.raises(gp.GpError):
         gp.Population(w["x"], w["t"], w["consts"], w["ops"], w["off"], max_nodes=40_000, arena_buffers=P + 10)
+
+
+def test_full_size_bench_configuration_sampled(gp):
+    """500 trees of ~1e6 nodes in the benchmark's configuration: fitness-first
+    order, MLP packing, graph mode, generations replayed from a captured
+    graph.  Sampled children of the last generation (their trees assembled
+    through their parents where they are not built) have exactly the fitness
+    that a full evaluation of their trees gives."""
+    import oracle
+    import synth
+    w = synth.workload(1)
+    k, x, t = w["consts"], w["x"], w["t"]
+    pop = gp.Population(x, t, k, w["ops"], w["off"], max_nodes=1 << 21, cache_threshold=1024, seed=0x5EED,
+                        packing=gp.GP_PACK_MLP, lazy=True)
+    pop.set_graph_mode(True)
+    pop.eval_full()
+    pop.crossover(0)
+    pop.eval_incremental()
+    pop.graph_capture(1, 2)
+    for _ in range(2):
+        pop.graph_launch()
+    fit = pop.fitness()
+    stop, _ = pop.walk_info()
+    assert (stop >= 0).mean() > 0.5            # most walks stop below the root, as in the benchmark
+    for i in (0, 7, 250, 499):
+        kid = pop.tree(i)
+        want = oracle.fitness_f32(oracle.eval_node_f32(kid, 0, k, x), t)
+        assert oracle.canon_nan(np.array([fit[i]]))[0] == oracle.canon_nan(np.array([want]))[0], i
+    pop.close()
