@@ -52,3 +52,48 @@ def test_create_rejects_bad_input_without_gpu(lib):
     with pytest.raises(gp.GpError) as ei:
         gp.gp_pop_create(cfg, x, x, k, np.array([0, 4, 4], np.uint8), np.array([0, 3], np.uint64), stream=0)
     assert ei.value.code == gp.GP_ECAPACITY
+
+
+def test_create_validates_every_configuration_field_without_gpu(lib):
+    # each field's range and each function set's opcode range is checked on
+    # the host, before any device allocation
+    import numpy as np
+    import paper_2205_03251_gb300 as gp
+    x = np.zeros(4, np.float32)
+    k = np.zeros(251, np.float32)
+    good = (np.array([0, 4, 5], np.uint8), np.array([0, 3], np.uint64))
+
+    def create(ops=None, off=None, **kw):
+        base = dict(pop_size=1, n_cases=4, max_nodes=64, funcset=gp.GP_FP32_ARITH, cache_threshold=1024)
+        base.update(kw)
+        o, f = good if ops is None else (np.array(ops, np.uint8), np.array(off, np.uint64))
+        with pytest.raises(gp.GpError) as ei:
+            gp.gp_pop_create(gp.GpConfig(**base), x, x, k, o, f, stream=0)
+        return ei.value.code, str(ei.value)
+
+    code = lambda *a, **kw: create(*a, **kw)[0]
+    assert code(funcset=4) == gp.GP_EINVAL
+    assert code(pop_size=0) == gp.GP_EINVAL
+    assert code(n_cases=0) == gp.GP_EINVAL
+    assert code(n_cases=(1 << 20) + 1) == gp.GP_EINVAL
+    assert code(cache_threshold=1) == gp.GP_EINVAL
+    assert code(cache_threshold=2048) == gp.GP_EINVAL
+    assert code(max_nodes=(1 << 30) + 1) == gp.GP_EINVAL
+    assert code(cases_per_lane=3) == gp.GP_EINVAL
+    assert code(cases_per_lane=8) == gp.GP_EINVAL
+    assert code(funcset=gp.GP_INT32_ARITH, cases_per_lane=4) == gp.GP_EINVAL
+    assert code(funcset=gp.GP_BOOL_MUX11, cases_per_lane=4) == gp.GP_EINVAL
+    assert code(walk_team=3) == gp.GP_EINVAL
+    assert code(walk_team=16) == gp.GP_EINVAL
+    assert code(lazy_children=2) == gp.GP_EINVAL
+    assert code(arena_buffers=2) == gp.GP_EINVAL                     # needs the fitness-first order
+    assert code(arena_buffers=1, lazy_children=1) == gp.GP_EINVAL    # at least pop_size + 1
+    assert code(arena_buffers=3, lazy_children=1) == gp.GP_EINVAL    # at most 2 x pop_size
+    # offsets must not decrease; each tree a complete prefix expression
+    assert code([4, 4], [1, 0]) == gp.GP_EINVAL
+    assert code([0, 4, 4, 4], [0, 4]) == gp.GP_EINVAL                # a leaf left over
+    assert code([], [0, 0]) == gp.GP_EINVAL                          # empty tree
+    # input opcodes: 6-multiplexer 4..9, 11-multiplexer 4..14; Boolean has no constants
+    for ops, fs in (([0, 4, 10], gp.GP_BOOL_MUX6), ([0, 4, 15], gp.GP_BOOL_MUX11)):
+        c, msg = create(ops, [0, 3], funcset=fs)
+        assert c == gp.GP_EINVAL and "valid opcodes" in msg, msg
