@@ -444,7 +444,6 @@ int run_structure(gp_pop* pop) {
     k_entry_ends<<<gthreads, 256, 0, pop->stream>>>(d, pop->sb);
     k_entry_chunkmax<<<pop->grid_warps, GP_WARPS * 32, 0, pop->stream>>>(d, pop->sb);
     k_entry_parents<<<gthreads, 256, 0, pop->stream>>>(d, pop->sb);
-    k_entry_links<<<gthreads, 256, 0, pop->stream>>>(d, pop->sb);
     return GP_OK;
 }
 
@@ -454,7 +453,7 @@ int run_full(gp_pop* pop) {
     const int gthreads = pop->grid_threads;
     CK(cudaMemsetAsync(d.q, 0, sizeof(uint32_t) * NQ, pop->stream));
     CK(cudaMemsetAsync(d.acc_ops, 0, 4 * sizeof(unsigned long long), pop->stream));
-    pop->launches = 16;
+    pop->launches = 15;
     pop->last_kind = 0;
     phase_begin(pop, PH_STRUCT);
     {
@@ -1459,7 +1458,6 @@ int gen_incremental(gp_pop* pop) {
     k_copy_values<<<pop->nsm * 16, 256, 0, pop->stream>>>(d, g, par);
     k_entry_chunkmax<<<pop->grid_warps, GP_WARPS * 32, 0, pop->stream>>>(d, pop->sb);
     k_entry_parents<<<gt, 256, 0, pop->stream>>>(d, pop->sb);
-    k_entry_links<<<gt, 256, 0, pop->stream>>>(d, pop->sb);
     k_child_sizes<<<(d.P + 255) / 256, 256, 0, pop->stream>>>(d, g);
     CK(cudaStreamWaitEvent(pop->stream, pop->join_ev, 0));
     if (g.lazy) CK(cudaStreamWaitEvent(pop->stream, pop->cjoin_ev, 0));
@@ -1467,7 +1465,7 @@ int gen_incremental(gp_pop* pop) {
     k_accumulate<<<1, 32, 0, pop->stream>>>(pop->cum, d.acc_ops, g.gstat, pop->cases_stat, 1);
     ++pop->cum_calls;
     CK(cudaGetLastError());
-    pop->launches += 12 + 14;
+    pop->launches += 12 + 13;
     pop->have_children = false;
     g.evaluated = true;
     pop->last_kind = 1;
