@@ -1,8 +1,9 @@
 """CPU oracle for the GP population hot path -- TEST INFRASTRUCTURE ONLY.
 
-A plain, slow restatement of what the method computes (recursive FP32 and
-FP64 interpreters, fitness, SplitMix64 draws, tournament selection, the
-crossover plan, splicing, and the failed-disruption-propagation walk).
+A plain, slow restatement of what the method computes (recursive FP32,
+FP64, Boolean multiplexer and int32 interpreters, fitness, SplitMix64
+draws, tournament selection, the crossover plan, splicing, the
+failed-disruption-propagation walk and its per-level disruption record).
 Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU
 baseline may use it.  It shares no code with the CUDA library; the only
 thing both consume is the ``synth`` input generator.

@@ -13,16 +13,23 @@
  *
  * Encoding (Sec. 3.1, Sec. 5: flattened linear prefix trees, one byte per
  * node): 0 '+', 1 '-', 2 '*', 3 protected '/', 4 x, 5..255 constant
- * k[op-5]; Boolean: 0 AND, 1 OR, 2 NAND, 3 NOR, 4..9 a0 a1 d0 d1 d2 d3.
- * Binary functions take the first child in prefix order as the left
- * operand.  Protected division returns 1.0 when the divisor compares equal
- * to zero (+0 or -0); otherwise it is the IEEE quotient.
+ * k[op-5]; Boolean: 0 AND, 1 OR, 2 NAND, 3 NOR, 4..9 a0 a1 d0 d1 d2 d3
+ * (6-multiplexer), or 4..14 a0 a1 a2 d0..d7 (11-multiplexer, input j =
+ * bit j of the case index); integer: the arithmetic opcodes over int32
+ * with wrap-around.  Binary functions take the first child in prefix
+ * order as the left operand.  Protected division returns 1.0 when the
+ * divisor compares equal to zero (+0 or -0); otherwise it is the IEEE
+ * quotient (integer: 1 for a zero divisor, INT32_MIN for INT32_MIN / -1,
+ * else the quotient truncated toward zero).
  *
- * Pins (see tests/test_oracle_pins.py): closed-form trees, brute force on
- * every tree of up to 7 nodes against exact rational arithmetic rounded
- * once per operation, the Boolean 6-multiplexer solved by a known tree,
- * published SplitMix64 vectors, and selection frequencies against their
- * closed forms.
+ * Pins: tests/test_oracle_pins.py (closed-form trees, brute force on every
+ * tree of up to 7 nodes against exact rational arithmetic rounded once per
+ * operation, the 6-multiplexer solved by a known tree, published
+ * SplitMix64 vectors, selection frequencies against their closed forms),
+ * tests/test_oracle_wide.py (the 11-multiplexer's known solution and
+ * closed-form error counts, the integer set against Python integers by
+ * brute force) and tests/test_oracle_disruption.py (hand-worked
+ * disruption records).
  */
 #include <stdint.h>
 #include <string.h>
