@@ -97,3 +97,16 @@ def test_create_validates_every_configuration_field_without_gpu(lib):
     for ops, fs in (([0, 4, 10], gp.GP_BOOL_MUX6), ([0, 4, 15], gp.GP_BOOL_MUX11)):
         c, msg = create(ops, [0, 3], funcset=fs)
         assert c == gp.GP_EINVAL and "valid opcodes" in msg, msg
+
+
+def test_no_fallback_when_the_library_or_the_gpu_is_missing(monkeypatch):
+    # the binding raises instead of computing anything on the CPU
+    import paper_2205_03251_gb300 as gp
+    monkeypatch.setattr(gp, "_lib", None)
+    monkeypatch.setattr(gp, "LIB_PATH", os.path.join(ROOT, "no-such-dir", "libgpfdp.so"))
+    with pytest.raises(RuntimeError, match="not built"):
+        gp.load()
+    import torch
+    if not torch.cuda.is_available():
+        with pytest.raises(RuntimeError, match="no CUDA device"):
+            gp._default_stream()

@@ -60,3 +60,15 @@ def test_single_process_passes_through():
     import bench
     assert bench.reduce_timing(None, "cpu", 3.0, 4.0, 5.0) == (3.0, 4.0, 5.0)
     assert bench.reduce_e2e(None, "cpu", 7.0, 1) == 7.0
+
+
+def test_graph_chunk_divides_the_timed_steps():
+    import bench
+    assert bench.graph_chunk(100) == 100
+    assert bench.graph_chunk(30) == 30
+    assert bench.graph_chunk(200) == 100
+    assert bench.graph_chunk(150) == 50
+    assert bench.graph_chunk(7) == 0            # odd: eager loop
+    for k in range(2, 300, 2):
+        g = bench.graph_chunk(k)
+        assert g % 2 == 0 and k % g == 0 and 2 <= g <= 100
