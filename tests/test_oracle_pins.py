@@ -454,3 +454,22 @@ def test_fdp_walk_bool(oracle_mod):
     stop, _ = oracle_mod.fdp_walk_bool(mom, oracle_mod.splice(mom, c, 1, np.array([A0], np.uint8), 0, 1), c)
     assert stop == 0
     assert oracle_mod.eval_node_bool(same, 0) == oracle_mod.mux6_target()
+
+
+def test_crossover_points_uniform_over_all_nodes(oracle_mod):
+    # Sec. 3: a crossover point is any node of the parent, leaves included,
+    # with equal chance (no bias toward functions); both parents alike
+    tree = np.array([ADD, MUL, SUB, X, 5, DIV, X, 6, ADD, MUL, X, 7, SUB, 5, X], np.uint8)
+    n, P = len(tree), 6000
+    assert oracle_mod.subtree_size(tree, 0) == n
+    ops = np.tile(tree, P)
+    off = (np.arange(P + 1) * n).astype(np.uint64)
+    pl = oracle_mod.plan(ops, off, np.zeros(P, np.float32), seed=77, gen=0, max_nodes=4 * n)
+    for key in ("c", "d"):
+        h = np.bincount(pl[key].astype(np.int64), minlength=n)
+        assert len(h) == n
+        chi2 = float((((h - P / n) ** 2) / (P / n)).sum())
+        assert chi2 < 36.1, (key, h)           # 14 degrees of freedom, p = 0.001
+    # leaves (8 of 15 nodes) are chosen about 8/15 of the time
+    leaf = np.array([o >= 4 for o in tree])
+    assert abs(leaf[pl["c"].astype(np.int64)].mean() - 8 / 15) < 0.03
