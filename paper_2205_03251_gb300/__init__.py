@@ -139,6 +139,25 @@ def _default_stream() -> int:
 
 # ------------------------------------------------------------------ C names
 
+def _check_sizes(cfg: GpConfig, x, targets, consts, ops, offsets):
+    """The C entry points take plain host pointers and read as many
+    elements as the configuration says; refuse arrays that are shorter."""
+    boolean = cfg.funcset in (GP_BOOL_MUX6, GP_BOOL_MUX11)
+    if not boolean and (x.size < cfg.n_cases or targets.size < cfg.n_cases):
+        raise ValueError(f"x and targets need n_cases = {cfg.n_cases} values (got {x.size}, {targets.size})")
+    if consts.size < 251:
+        raise ValueError(f"consts needs 251 values (got {consts.size})")
+    if cfg.pop_size:                  # pop_size 0 is refused by the library itself
+        _check_trees(cfg.pop_size, ops, offsets)
+
+
+def _check_trees(pop_size: int, ops, offsets):
+    if offsets.size != pop_size + 1:
+        raise ValueError(f"offsets needs pop_size + 1 = {pop_size + 1} entries (got {offsets.size})")
+    if offsets.size and int(offsets.max()) > ops.size:
+        raise ValueError(f"offsets reach {int(offsets.max())} but ops holds {ops.size} bytes")
+
+
 def gp_pop_create(cfg: GpConfig, x, targets, consts, ops, offsets, stream=None):
     """Create a population; returns the opaque handle (int)."""
     lib = load()
@@ -147,6 +166,7 @@ def gp_pop_create(cfg: GpConfig, x, targets, consts, ops, offsets, stream=None):
     consts = np.ascontiguousarray(consts, np.float32)
     ops = np.ascontiguousarray(ops, np.uint8)
     offsets = np.ascontiguousarray(offsets, np.uint64)
+    _check_sizes(cfg, x, targets, consts, ops, offsets)
     if stream is None:
         stream = _default_stream()
     elif hasattr(stream, "cuda_stream"):
@@ -161,10 +181,12 @@ def gp_pop_destroy(h):
     load().gp_pop_destroy(h)
 
 
-def gp_load_trees(h, ops, offsets):
-    """Upload new trees (host arrays; pin them for an asynchronous copy)."""
+def gp_load_trees(h, ops, offsets, pop_size: int | None = None):
+    """Upload new trees (host arrays; pin them for an asynchronous copy).
+    pop_size, when given, is checked against the offsets."""
     ops = np.ascontiguousarray(ops, np.uint8)
     offsets = np.ascontiguousarray(offsets, np.uint64)
+    _check_trees(offsets.size - 1 if pop_size is None else pop_size, ops, offsets)
     _check(load().gp_load_trees(h, _ptr(ops), _ptr(offsets)), h)
 
 
@@ -333,6 +355,7 @@ def gp_autotune(cfg: GpConfig, x, targets, consts, ops, offsets, ks, ts, teams, 
     consts = np.ascontiguousarray(consts, np.float32)
     ops = np.ascontiguousarray(ops, np.uint8)
     offsets = np.ascontiguousarray(offsets, np.uint64)
+    _check_sizes(cfg, x, targets, consts, ops, offsets)
     ks = np.ascontiguousarray(ks, np.uint32)
     ts = np.ascontiguousarray(ts, np.uint32)
     teams = np.ascontiguousarray(teams, np.uint32)
@@ -437,7 +460,7 @@ class Population:
             pass
 
     def load_trees(self, ops, off):
-        gp_load_trees(self.h, ops, off)
+        gp_load_trees(self.h, ops, off, self.P)
 
     def eval_full(self):
         gp_eval_full(self.h)

@@ -67,8 +67,9 @@ def test_create_validates_every_configuration_field_without_gpu(lib):
         base = dict(pop_size=1, n_cases=4, max_nodes=64, funcset=gp.GP_FP32_ARITH, cache_threshold=1024)
         base.update(kw)
         o, f = good if ops is None else (np.array(ops, np.uint8), np.array(off, np.uint64))
+        xs = np.zeros(max(4, base["n_cases"]), np.float32)     # long enough for the binding's size check
         with pytest.raises(gp.GpError) as ei:
-            gp.gp_pop_create(gp.GpConfig(**base), x, x, k, o, f, stream=0)
+            gp.gp_pop_create(gp.GpConfig(**base), xs, xs, k, o, f, stream=0)
         return ei.value.code, str(ei.value)
 
     code = lambda *a, **kw: create(*a, **kw)[0]
@@ -110,3 +111,32 @@ def test_no_fallback_when_the_library_or_the_gpu_is_missing(monkeypatch):
     if not torch.cuda.is_available():
         with pytest.raises(RuntimeError, match="no CUDA device"):
             gp._default_stream()
+
+
+def test_binding_refuses_short_host_arrays(lib):
+    # the C entry points read as many elements as the configuration says:
+    # the binding checks the host arrays first
+    import numpy as np
+    import paper_2205_03251_gb300 as gp
+    k = np.zeros(251, np.float32)
+    ops = np.array([0, 4, 5, 4], np.uint8)
+    off = np.array([0, 3, 4], np.uint64)
+    cfg = gp.GpConfig(pop_size=2, n_cases=8, max_nodes=64, funcset=gp.GP_FP32_ARITH)
+    x8 = np.zeros(8, np.float32)
+    with pytest.raises(ValueError, match="n_cases"):
+        gp.gp_pop_create(cfg, np.zeros(7, np.float32), x8, k, ops, off, stream=0)
+    with pytest.raises(ValueError, match="n_cases"):
+        gp.gp_pop_create(cfg, x8, np.zeros(4, np.float32), k, ops, off, stream=0)
+    with pytest.raises(ValueError, match="251"):
+        gp.gp_pop_create(cfg, x8, x8, k[:250], ops, off, stream=0)
+    with pytest.raises(ValueError, match="pop_size"):
+        gp.gp_pop_create(cfg, x8, x8, k, ops, off[:2], stream=0)
+    with pytest.raises(ValueError, match="ops holds"):
+        gp.gp_pop_create(cfg, x8, x8, k, ops[:3], off, stream=0)
+    with pytest.raises(ValueError, match="pop_size"):
+        gp.gp_load_trees(None, ops, off, pop_size=3)
+    # Boolean sets take no x or targets
+    cfg.funcset = gp.GP_BOOL_MUX6
+    with pytest.raises(gp.GpError):        # reaches the C validation: opcode 5 is an input of the 6-mux,
+        gp.gp_pop_create(cfg, np.zeros(1, np.float32), np.zeros(1, np.float32), k,   # but '+' 4 5 leaves
+                         np.array([0, 4, 5, 0], np.uint8), off, stream=0)            # tree 1 incomplete
