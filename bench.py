@@ -198,8 +198,9 @@ def make_workload(args, rank: int):
             w = synth.workload(3, n_trees=args.trees, n_cases=args.cases, target=args.target, boolean=args.boolean)
         if rank:
             sizes = synth.log_uniform_sizes(w["seed"] + rank, args.trees, 1e1, float(args.target))
-            w["ops"], w["off"] = synth.population("remy", w["seed"] + rank, args.trees, boolean=args.boolean,
-                                                  sizes=sizes, n_inputs=11 if w.get("mux_k") == 3 else 6)
+            w["ops"], w["off"] = synth.population("remy", w["seed"] + rank, args.trees,
+                                                  boolean=bool(w.get("boolean")), sizes=sizes,
+                                                  n_inputs=11 if w.get("mux_k") == 3 else 6)
         w["max_nodes"] = 2 * args.target + 4096
         return w
     seed_shift = rank

@@ -72,3 +72,21 @@ def test_graph_chunk_divides_the_timed_steps():
     for k in range(2, 300, 2):
         g = bench.graph_chunk(k)
         assert g % 2 == 0 and k % g == 0 and 2 <= g <= 100
+
+
+def test_other_ranks_build_valid_trees_of_every_function_set(oracle_mod):
+    # a rank other than 0 draws its own trees of the same recipe and function set
+    import argparse
+    import bench
+    for funcset, boolean, max_op in (("fp32", False, 255), ("mux6", True, 9), ("mux11", False, 14),
+                                     ("int32", False, 255)):
+        args = argparse.Namespace(workload="uneven", trees=24, cases=48, target=3000, boolean=boolean,
+                                  funcset=funcset, threshold=1024)
+        w0, w1 = bench.make_workload(args, 0), bench.make_workload(args, 1)
+        assert w0["ops"].tobytes() != w1["ops"].tobytes()
+        off = w1["off"]
+        for i in range(len(off) - 1):
+            t = w1["ops"][int(off[i]):int(off[i + 1])]
+            assert int(t.max()) <= max_op and oracle_mod.subtree_size(t, 0) == len(t), funcset
+        if funcset in ("mux6", "mux11"):
+            assert w1["ops"].max() == max_op          # inputs only, up to the set's last input
