@@ -607,6 +607,10 @@ def main():
         line["config"]["cache_threshold"] = pop_kw["cache_threshold"]
         line["config"]["walk_team"] = pop_kw["walk_team"]
         line["autotune"] = tune
+    # DRAM traffic figures come from ncu captures of the grafted 1e6-node trees at 48 cases and
+    # threshold 1,024; other workloads report none
+    profiled = (args.workload in ("generation", "full") and args.cases == 48 and args.threshold == 1024
+                and args.target == 1_000_000 and args.funcset == "fp32")
     if generational:
         xo_ms = phases["crossover"] + phases.get("materialise", 0.0)
         xo_bytes = st["cum_crossover_bytes"] / max(1, st["cum_calls"])
@@ -622,7 +626,7 @@ def main():
         walk_ms = phases["walk"]
         walk_ops = st["cum_actual_ops"] / max(1, st["cum_calls"])
         walk_t = walk_ops / (walk_ms * 1e-3) / 1e12 if walk_ms > 0 else None
-        per_child = profile_figure("k_walk_generation_200x1e6.md", "traffic_bytes_per_child")
+        per_child = profile_figure("k_walk_generation_200x1e6.md", "traffic_bytes_per_child") if profiled else None
         line["roofline"] = {"bound": "alu", "achieved": walk_t, "peak": alu_peak, "unit": "TFLOP/s",
                             "frac": (walk_t / alu_peak) if walk_t else None,
                             "traffic": per_child * (len(w["off"]) - 1) if per_child else None,
@@ -631,7 +635,7 @@ def main():
                             "timing": timing}
         # the HBM-bound part: the crossover kernels (their bytes are exact)
         ratio = profile_figure("k_copy_children_fitness_first_200x1e6.md" if args.lazy else
-                               "crossover_dram_traffic_100x1e6.md", "traffic_per_algorithmic_byte")
+                               "crossover_dram_traffic_100x1e6.md", "traffic_per_algorithmic_byte") if profiled else None
         line["roofline_crossover"] = {"bound": "hbm", "achieved": xo_gbs, "peak": hbm, "unit": "GB/s",
                                       "frac": (xo_gbs / hbm) if (xo_gbs and hbm) else None,
                                       "traffic": ratio * xo_bytes if ratio else None,
@@ -641,7 +645,7 @@ def main():
     else:
         t_items = phases["items"]
         achieved = st["interp_ops"] / (t_items * 1e-3) / 1e12 if t_items > 0 else None
-        per_node = profile_figure("k_eval_items_full_eval_100x1e6.md", "traffic_bytes_per_node")
+        per_node = profile_figure("k_eval_items_full_eval_100x1e6.md", "traffic_bytes_per_node") if profiled else None
         line["roofline"] = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
                             "frac": (achieved / alu_peak) if achieved else None,
                             "traffic": per_node * int(w["off"][-1]) if per_node else None,
