@@ -246,11 +246,44 @@ def _oracle_tree(oracle, w, tree):
         oracle.eval_pop_f32(tree, sub, w["consts"], w["x"], w["t"])
 
 
-def cpu_baseline(w, seconds: float, gpu_fit=None):
+def _queue_run(P: int, threads: int, budget: float, one):
+    """Run one(n) for n = 0, 1, ... from a shared queue on `threads` host
+    threads until all P are done or `budget` seconds have passed (0: no
+    limit).  Returns (sum of one's results, items done, seconds)."""
+    lock = threading.Lock()
+    nxt = [0]
+    done = [0, 0]
+    t0 = time.perf_counter()
+
+    def worker():
+        while True:
+            with lock:
+                if nxt[0] >= P or (budget and time.perf_counter() - t0 > budget):
+                    return
+                n = nxt[0]
+                nxt[0] += 1
+            k = one(n)
+            with lock:
+                done[0] += k
+                done[1] += 1
+    ts = [threading.Thread(target=worker) for _ in range(threads)]
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join()
+    return done[0], done[1], time.perf_counter() - t0
+
+
+def cpu_baseline(w, seconds: float, gpu_fit=None, generation: bool = False):
     """Time the CPU oracle as it stands on a bounded sample of the workload:
-    first on one thread, then with one thread per host core pulling whole
-    trees from a shared queue (the paper's threading of independent
-    evaluations).  The oracle's C calls release the GIL.  With the GPU's
+    first full evaluation of the trees on one thread, then with one thread
+    per host core pulling whole trees from a shared queue (the paper's
+    threading of independent evaluations).  The oracle's C calls release
+    the GIL.  With generation=True the all-core leg evaluates every parent
+    (the fitness the selection needs), and the reported value is the
+    oracle's generation: its tournaments and crossover points, then each
+    child spliced and evaluated in full, children from a shared queue for a
+    bounded time; the oracle does no incremental evaluation.  With the GPU's
     fitness of the initial trees, the single-thread sample is also evaluated
     in FP64 and the largest relative difference reported."""
     import oracle
@@ -259,52 +292,65 @@ def cpu_baseline(w, seconds: float, gpu_fit=None):
     boolean = bool(w.get("boolean"))
     C = _cases(w)
     P = len(off) - 1
+    cores = os.cpu_count() or 1
 
     def one(n):
         _oracle_tree(oracle, w, ops[int(off[n]):int(off[n + 1])])
         return int(off[n + 1] - off[n])
 
-    def run(threads: int, budget: float):
-        lock = threading.Lock()
-        nxt = [0]
-        done = [0, 0]
-        t0 = time.perf_counter()
-
-        def worker():
-            while True:
-                with lock:
-                    if nxt[0] >= P or time.perf_counter() - t0 > budget:
-                        return
-                    n = nxt[0]
-                    nxt[0] += 1
-                k = one(n)
-                with lock:
-                    done[0] += k
-                    done[1] += 1
-        ts = [threading.Thread(target=worker) for _ in range(threads)]
-        for t in ts:
-            t.start()
-        for t in ts:
-            t.join()
-        dt = time.perf_counter() - t0
-        return done[0] * C / dt / 1e9, done[1], done[0], dt
-
-    one_v, one_n, one_nodes, one_dt = run(1, seconds / 3)
-    cores = os.cpu_count() or 1
-    all_v, all_n, all_nodes, all_dt = run(cores, 2 * seconds / 3)
+    one_nodes, one_n, one_dt = _queue_run(P, 1, seconds / 3, one)
+    one_v = one_nodes * C / one_dt / 1e9
     kind = ("recursive Boolean oracle" if boolean else "recursive integer oracle" if w.get("integer")
             else "recursive FP32 oracle")
-    out = {"value": all_v, "unit": "GPop/s", "cores": cores, "kind": "oracle",
-           "sample": f"{all_n} trees ({all_nodes} nodes) x {C} cases in {all_dt:.1f} s, {kind}, one thread per "
-                     f"core taking whole trees from a shared queue",
-           "single_thread": {"value": one_v, "cores": 1,
-                             "sample": f"{one_n} trees ({one_nodes} nodes) x {C} cases in {one_dt:.1f} s"}}
+    single = {"value": one_v, "cores": 1,
+              "sample": f"full evaluation of {one_n} trees ({one_nodes} nodes) x {C} cases in {one_dt:.1f} s"}
+    fp64 = None
     if gpu_fit is not None and one_n and not boolean and not w.get("integer"):
         n = min(one_n, len(gpu_fit))
         f64 = oracle.eval_pop_f64(ops[:int(off[n])], off[:n + 1], w["consts"], w["x"], w["t"])
         rel, nonfinite = oracle.max_rel_diff(gpu_fit[:n], f64)
-        out["gpu_vs_fp64"] = {"trees": n, "max_rel_diff": rel, "nonfinite": nonfinite,
-                              "note": "GPU FP32 fitness of the initial trees against the FP64 oracle (reported, not gated)"}
+        fp64 = {"trees": n, "max_rel_diff": rel, "nonfinite": nonfinite,
+                "note": "GPU FP32 fitness of the initial trees against the FP64 oracle (reported, not gated)"}
+    if generation and not boolean and not w.get("integer"):
+        # every parent's fitness (the selection needs all of them)
+        fit = np.zeros(P, np.float32)
+
+        def parent(n):
+            sub = np.array([0, int(off[n + 1] - off[n])], np.uint64)
+            fit[n] = oracle.eval_pop_f32(ops[int(off[n]):int(off[n + 1])], sub, w["consts"], w["x"], w["t"])[1][0]
+            return int(off[n + 1] - off[n])
+        pn, _, pdt = _queue_run(P, cores, 0, parent)
+        maxn = w.get("max_nodes", 1 << 21)
+        t0 = time.perf_counter()
+        pl = oracle.plan(ops, off, fit, T=7, seed=0x5EED, gen=0, max_nodes=maxn)
+        plan_dt = time.perf_counter() - t0
+
+        def child(i):
+            m, f = int(pl["mother"][i]), int(pl["father"][i])
+            kid = oracle.splice(ops[int(off[m]):int(off[m + 1])], int(pl["c"][i]), int(pl["r"][i]),
+                                ops[int(off[f]):int(off[f + 1])], int(pl["d"][i]), int(pl["s"][i]))
+            sub = np.array([0, len(kid)], np.uint64)
+            oracle.eval_pop_f32(kid, sub, w["consts"], w["x"], w["t"])
+            return len(kid)
+        kn, kcount, kdt = _queue_run(P, cores, 2 * seconds / 3, child)
+        # per child: its share of the plan, then splice + full evaluation
+        kdt_all = kdt + plan_dt * kcount / P
+        value = kn * C / kdt_all / 1e9
+        return {"value": value, "unit": "GPop/s", "cores": cores, "kind": "oracle",
+                "sample": (f"the oracle's generation on {kcount} of {P} children ({kn} nodes) x {C} cases in "
+                           f"{kdt_all:.1f} s: tournaments and crossover points (its plan, {plan_dt:.2f} s for all "
+                           f"{P}, charged pro rata), each child spliced and evaluated in full ({kind}, no "
+                           f"incremental evaluation), one thread per core taking children from a shared queue"),
+                "full_evaluation": {"value": pn * C / pdt / 1e9, "cores": cores,
+                                    "sample": f"all {P} parents ({pn} nodes) x {C} cases in {pdt:.1f} s"},
+                "single_thread": single, **({"gpu_vs_fp64": fp64} if fp64 else {})}
+    all_nodes, all_n, all_dt = _queue_run(P, cores, 2 * seconds / 3, one)
+    out = {"value": all_nodes * C / all_dt / 1e9, "unit": "GPop/s", "cores": cores, "kind": "oracle",
+           "sample": f"full evaluation of {all_n} trees ({all_nodes} nodes) x {C} cases in {all_dt:.1f} s, {kind}, "
+                     f"one thread per core taking whole trees from a shared queue",
+           "single_thread": single}
+    if fp64:
+        out["gpu_vs_fp64"] = fp64
     return out
 
 
@@ -584,7 +630,17 @@ def main():
     sm_max = peaks.get("sm_max_mhz") or 2070.0
     hbm = peaks.get("hbm_gbs")
     nsm = torch.cuda.get_device_properties(local).multi_processor_count or N_SM_DEFAULT
-    alu_peak = nsm * FP32_LANES_PER_SM * sm_max * 1e6 / 1e12
+    spec_peak = nsm * FP32_LANES_PER_SM * sm_max * 1e6 / 1e12
+    # the interpreters' roofline: the measured issue rate of the instruction
+    # their function set is made of (binary32 add; 32-bit logic on words of
+    # 32 Boolean cases; 32-bit integer add), in node-case operations per second
+    alu_kind = "lop3" if boolean else "iadd" if integer else "fadd"
+    alu_meas = {k: gp.gp_alu_peak(k) for k in ("fadd", "lop3", "iadd")}
+    alu_peak = alu_meas[alu_kind] * (32 if boolean else 1) / 1e12
+    alu_note = (f"measured gp_alu_peak('{alu_kind}') = {alu_meas[alu_kind] / 1e12:.2f} T lane-ops/s"
+                + (" x 32 Boolean cases per 32-bit word" if boolean else "")
+                + f", of measured (nominal {nsm} SMs x 128 FP32 lanes x {sm_max:.0f} MHz = {spec_peak:.1f} T); "
+                "one node x case = one lane op")
 
     line = {"metric": METRIC, "value": value, "unit": "GPop/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -631,8 +687,7 @@ def main():
                             "frac": (walk_t / alu_peak) if walk_t else None,
                             "traffic": per_child * (len(w["off"]) - 1) if per_child else None,
                             "kernel": "k_walk (incremental evaluation with FDP; critical-path bound)",
-                            "peak_note": f"{nsm} SMs x 128 FP32 lanes x {sm_max:.0f} MHz; one node x case = one lane op",
-                            "timing": timing}
+                            "peak_note": alu_note, "timing": timing}
         # the HBM-bound part: the crossover kernels (their bytes are exact)
         ratio = profile_figure("k_copy_children_fitness_first_200x1e6.md" if args.lazy else
                                "crossover_dram_traffic_100x1e6.md", "traffic_per_algorithmic_byte") if profiled else None
@@ -649,8 +704,9 @@ def main():
         line["roofline"] = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
                             "frac": (achieved / alu_peak) if achieved else None,
                             "traffic": per_node * int(w["off"][-1]) if per_node else None,
-                            "kernel": "k_eval_items (subtree interpreter)",
-                            "peak_note": f"{nsm} SMs x 128 FP32 lanes x {sm_max:.0f} MHz; one node x case = one lane op"}
+                            "kernel": "k_eval_items (subtree interpreter)", "peak_note": alu_note}
+    line["alu_peaks_measured"] = {k: v / 1e12 for k, v in alu_meas.items()}
+    line["alu_peaks_measured"]["unit"] = "T lane-ops/s"
     line["gpu_launches"] = st["launches"] * n_calls
     line["clocks"] = clk
 
@@ -711,7 +767,8 @@ def main():
     pop.close()
     if rank == 0:
         if not args.no_cpu and world == 1:
-            line["cpu_baseline"] = cpu_baseline(w, args.cpu_seconds, fit0)
+            line["cpu_baseline"] = cpu_baseline(w, args.cpu_seconds, fit0,
+                                                generation=generational and args.workload == "generation")
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

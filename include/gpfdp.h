@@ -351,18 +351,43 @@ int gp_autotune(const gp_config* base, const float* x, const float* targets, con
  * with status GP_OK and identical = 1 (ties: the earlier), or -1. */
 int gp_autotune_pick(const gp_tune_result* results, uint32_t n, uint32_t generations);
 
+/*
+ * Bound the polls of every wait inside an incremental-walk team (the
+ * combining warp waiting for a sibling's values, an evaluator waiting for the
+ * next level's descriptor; Sec. 6.2 walk, evaluated by a team of warps).
+ * polls = 0 restores the default of 2^22 polls of about 64 ns each.  A wait
+ * that runs out ends the team's walk of that child, the team goes on, and
+ * the next synchronising call reports GP_ETIMEOUT; the population must then
+ * be reloaded (gp_load_trees, gp_eval_full).  Meant for testing that every
+ * device wait returns.  Drops a captured graph.  Synchronising.
+ */
+int gp_set_wait_limit(gp_pop* pop, uint32_t polls);
+
+/*
+ * Measured issue rate of the plain ALU operations the interpreters are made
+ * of, on the current device: kind 0 binary32 add, 1 32-bit three-input
+ * logic (the Boolean sets' AND/OR/NAND/NOR words), 2 32-bit integer add.
+ * *lane_ops_per_s receives lane operations per second over all SMs (the
+ * roofline of an interpreter that spends one lane operation per opcode and
+ * test case, Sec. 4.2).  The paper has no counterpart.  Allocates 16 bytes
+ * of device memory for the duration of the call.  Synchronising.
+ */
+int gp_alu_peak(int kind, double* lane_ops_per_s);
+
 /* Turn per-phase CUDA-event timing on (1) or off (0); either resets the
  * recorded phase times. */
 int gp_set_profiling(gp_pop* pop, int on);
 
 /*
- * Full evaluation of a batch of small trees without any device allocation
- * (the paper has no counterpart; this is a service for callers that cannot
- * call cudaMalloc -- e.g. code running while another component captures the
- * stream into a CUDA graph, or an embedding whose memory is fixed at start).
+ * Full evaluation of a batch of small trees without any device allocation.
+ * The paper has no counterpart: this is a service for callers that cannot
+ * call cudaMalloc -- a plug-in whose host process has handed the device
+ * memory to its own pool allocator, a real-time loop that must not take the
+ * device synchronisation an allocation can bring, or an embedding whose
+ * memory is fixed at start-up.
  * All pointers but status_out are device pointers owned by the caller:
  *   d_ops      16-byte aligned opcodes; tree i is d_ops[d_off[i] .. d_off[i+1]);
- *              ops_bytes (a multiple of 16) must cover every tree rounded up to 16
+ *              ops_bytes (a multiple of 16) must cover every tree
  *   d_off      n_trees + 1 uint64 offsets; each tree 1..1023 nodes
  *   d_x, d_t   n_cases inputs and targets (1 <= n_cases <= 4096); d_consts 251 floats
  *   d_values   out: n_trees x n_cases root values (row per tree)
@@ -370,14 +395,16 @@ int gp_set_profiling(gp_pop* pop, int on);
  * Same arithmetic as gp_eval_full.  Scratch (the interpreter's deep-stack
  * overflow for 64 warps, a work counter, a status word) lives in one
  * file-scope device array of about 8.5 MB that every GPU loading the library
- * holds until exit.  The first call on a device looks up that array's device
- * address (cudaGetSymbolAddress) with the device current; make that first
- * call before any stream capture.  Every call shares the array: calls whose
- * GPU work overlaps (other streams, or not yet finished) race and must be
- * serialised.  Each call clears its counter and status word first, then
- * waits for its stream to finish.  Returns GP_EINVAL for bad arguments or a
- * malformed tree, GP_ECAPACITY when a tree is empty, larger than 1023 nodes
- * or outside ops_bytes; *status_out (host, may be NULL) gets the raw flags.
+ * holds until exit.  The first call on a device (and the first after that
+ * device's context was re-created) looks up the array's device address
+ * (cudaGetSymbolAddress) with the device current; make that first call
+ * before any stream capture.  Every call shares the array: calls whose GPU
+ * work overlaps (other streams, or not yet finished) race and must be
+ * serialised.  Each call clears its counter and status word first, and
+ * synchronises its stream before returning.  Returns GP_EINVAL for bad
+ * arguments or a malformed tree, GP_ECAPACITY when a tree is empty, larger
+ * than 1023 nodes or outside ops_bytes; *status_out (host, may be NULL) gets
+ * the raw flags (1: size or bounds, 2: malformed tree).
  */
 int gp_eval_small_noalloc(const uint8_t* d_ops, size_t ops_bytes, const uint64_t* d_off, uint32_t n_trees,
                           const float* d_x, const float* d_t, const float* d_consts, uint32_t n_cases,

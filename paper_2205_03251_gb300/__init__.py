@@ -104,6 +104,8 @@ def load() -> ctypes.CDLL:
         "gp_eval_small_noalloc": (i32, [vp, ctypes.c_size_t, vp, u32, vp, vp, vp, u32, vp, vp, vp,
                                         ctypes.POINTER(u32)]),
         "gp_set_profiling": (i32, [vp, i32]),
+        "gp_set_wait_limit": (i32, [vp, u32]),
+        "gp_alu_peak": (i32, [i32, ctypes.POINTER(ctypes.c_double)]),
         "gp_set_graph_mode": (i32, [vp, i32, u64]),
         "gp_graph_capture": (i32, [vp, u32, u32]),
         "gp_graph_launch": (i32, [vp]),
@@ -284,19 +286,66 @@ def gp_disruption(h, n: int, max_levels: int):
     return rec, nl
 
 
+def _on_current_cuda_device(tensor) -> bool:
+    import torch
+    return bool(tensor.is_cuda) and tensor.device.index == torch.cuda.current_device()
+
+
+def check_noalloc_args(ops, off, x, t, consts, values, fitness, on_device=_on_current_cuda_device) -> int:
+    """Check the tensors of gp_eval_small_noalloc before any launch (the
+    library only sees raw addresses, so a wrong dtype, a short buffer or a
+    host tensor would make the kernel read or write outside the caller's
+    memory).  Returns the number of trees; raises ValueError."""
+    import torch
+    named = {"ops": ops, "off": off, "x": x, "t": t, "consts": consts, "values": values, "fitness": fitness}
+    for name, a in named.items():
+        if not isinstance(a, torch.Tensor):
+            raise ValueError(f"{name} must be a torch tensor")
+        if not on_device(a):
+            raise ValueError(f"{name} must be a CUDA tensor on the current device")
+        if not a.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+    if ops.dtype != torch.uint8:
+        raise ValueError("ops must be uint8")
+    if ops.numel() % 16 or ops.data_ptr() % 16:
+        raise ValueError("ops must start on a 16-byte boundary and hold a multiple of 16 bytes")
+    if off.dtype not in (torch.int64, getattr(torch, "uint64", torch.int64)):
+        raise ValueError("off must be int64 (or uint64)")
+    if off.numel() < 2:
+        raise ValueError("off must hold n_trees + 1 >= 2 offsets")
+    for name in ("x", "t", "consts", "values", "fitness"):
+        if named[name].dtype != torch.float32:
+            raise ValueError(f"{name} must be float32")
+    C = x.numel()
+    if not 1 <= C <= 4096:
+        raise ValueError("1 <= number of cases <= 4096")
+    if t.numel() != C:
+        raise ValueError("t must hold as many values as x")
+    if consts.numel() < 251:
+        raise ValueError("consts must hold 251 values")
+    n = off.numel() - 1
+    if values.numel() < n * C:
+        raise ValueError("values must hold n_trees x n_cases floats")
+    if fitness.numel() < n:
+        raise ValueError("fitness must hold n_trees floats")
+    return n
+
+
 def gp_eval_small_noalloc(ops, off, x, t, consts, values, fitness, stream=None) -> int:
     """Evaluate small trees with no device allocation (see include/gpfdp.h).
-    Every array argument is a CUDA tensor owned by the caller: ops (uint8,
-    length a multiple of 16), off (int64, n_trees+1), x, t (float32, C),
-    consts (float32, 251), values (float32, n_trees x C), fitness (float32,
-    n_trees).  Returns the raw status flags; raises GpError on failure."""
+    Every array argument is a contiguous CUDA tensor on the current device,
+    owned by the caller: ops (uint8, length a multiple of 16), off (int64,
+    n_trees+1), x, t (float32, C), consts (float32, 251), values (float32,
+    n_trees x C), fitness (float32, n_trees).  Returns the raw status flags;
+    raises ValueError on a bad argument and GpError on a failed call."""
+    n = check_noalloc_args(ops, off, x, t, consts, values, fitness)
     if stream is None:
         stream = _default_stream()
     elif hasattr(stream, "cuda_stream"):
         stream = stream.cuda_stream
     st = ctypes.c_uint32(0)
     rc = load().gp_eval_small_noalloc(ctypes.c_void_p(ops.data_ptr()), ops.numel(),
-                                      ctypes.c_void_p(off.data_ptr()), off.numel() - 1,
+                                      ctypes.c_void_p(off.data_ptr()), n,
                                       ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(t.data_ptr()),
                                       ctypes.c_void_p(consts.data_ptr()), x.numel(),
                                       ctypes.c_void_p(values.data_ptr()), ctypes.c_void_p(fitness.data_ptr()),
@@ -411,6 +460,22 @@ def gp_set_profiling(h, on: bool):
     _check(load().gp_set_profiling(h, 1 if on else 0), h)
 
 
+ALU_KINDS = {"fadd": 0, "lop3": 1, "iadd": 2}
+
+
+def gp_alu_peak(kind: str) -> float:
+    """Measured lane operations per second of one ALU instruction kind on
+    the current device ("fadd", "lop3" or "iadd")."""
+    out = ctypes.c_double(0.0)
+    _check(load().gp_alu_peak(ALU_KINDS[kind], ctypes.byref(out)))
+    return out.value
+
+
+def gp_set_wait_limit(h, polls: int):
+    """Bound the polls of every wait inside a walk team (0: the default)."""
+    _check(load().gp_set_wait_limit(h, polls), h)
+
+
 # ------------------------------------------------------------------ convenience
 
 class Population:
@@ -504,6 +569,9 @@ class Population:
 
     def set_profiling(self, on: bool):
         gp_set_profiling(self.h, on)
+
+    def set_wait_limit(self, polls: int):
+        gp_set_wait_limit(self.h, polls)
 
     def set_graph_mode(self, on: bool, reserve_entries: int = 0):
         gp_set_graph_mode(self.h, on, reserve_entries)

@@ -37,6 +37,7 @@ struct DevPop {
     uint32_t strict_cap;                   // 1: a cache larger than Ecap is an error (no host regrow)
     uint32_t vkind;                        // VF, VB or VI
     uint32_t mux_k;                        // Boolean: address lines of the multiplexer (C = 2^(k + 2^k) / 32 words)
+    uint32_t wait_polls;                   // bound on the polls of one wait inside a walk team (>= 1)
     // population
     uint8_t* arena;      // nbuf * cap bytes
     uint32_t* buf;       // [P] buffer holding individual i

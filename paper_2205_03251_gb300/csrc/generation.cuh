@@ -796,7 +796,7 @@ struct LevelDesc {
 #define LD_NOSIB (1u << 11)
 
 #define WALK_RING 32           // most levels a walk team keeps in flight (descriptors and sibling values)
-#define WALK_SPIN (1u << 22)   // bound on the polls of one wait inside a walk team
+#define WALK_SPIN (1u << 22)   // default bound on the polls of one wait inside a walk team (DevPop::wait_polls)
 
 // levels in flight: fewer when value vectors are long
 __host__ __device__ inline uint32_t walk_ring(uint32_t Cpad) { return Cpad <= 128 ? 32u : Cpad <= 256 ? 8u : 4u; }
@@ -1386,7 +1386,7 @@ __global__ void __launch_bounds__(256, 2) k_walk(DevPop d, GenBufs g, CacheView 
                     }
                 } else {
                     uint32_t spins = 0, ready = 0;
-                    while ((ready = __shfl_sync(FULL, lane == 0 ? vcnt[slot] : 0u, 0)) < ncb && ++spins < WALK_SPIN)
+                    while ((ready = __shfl_sync(FULL, lane == 0 ? vcnt[slot] : 0u, 0)) < ncb && ++spins < d.wait_polls)
                         __nanosleep(64);
                     if (ready < ncb) { if (lane == 0) set_status(d.status, ST_TIMEOUT); fail = true; break; }
                     __threadfence_block();
@@ -1485,7 +1485,7 @@ __global__ void __launch_bounds__(256, 2) k_walk(DevPop d, GenBufs g, CacheView 
                             if (atomicCAS(cur, c, nx) == c) { k = ck; r = cr; break; }
                             continue;
                         }
-                        if (++spins >= WALK_SPIN) { set_status(d.status, ST_TIMEOUT); fin = 1; break; }
+                        if (++spins >= d.wait_polls) { set_status(d.status, ST_TIMEOUT); fin = 1; break; }
                         __nanosleep(64);
                     }
                 }

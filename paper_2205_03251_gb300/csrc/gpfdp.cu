@@ -597,6 +597,7 @@ int gp_pop_create(const gp_config* cfg_in, const float* x, const float* targets,
     const uint32_t nbuf = cfg.arena_buffers ? cfg.arena_buffers : 2 * P;   // parents + children (copy targets)
     pop->nbuf = nbuf;
     d.ovf_warps = 0;
+    d.wait_polls = WALK_SPIN;
 
     // grids
     pop->grid_warps = pop->nsm * 8;
@@ -974,6 +975,14 @@ int gp_set_profiling(gp_pop* pop, int on) {
     memset(pop->ev_count, 0, sizeof pop->ev_count);
     CK(cudaMemsetAsync(pop->cum, 0, 4 * sizeof(unsigned long long), pop->stream));
     pop->cum_calls = 0;
+    return GP_OK;
+}
+
+int gp_set_wait_limit(gp_pop* pop, uint32_t polls) {
+    if (!pop) return GP_EINVAL;
+    if (pop->stream) CK(cudaStreamSynchronize(pop->stream)); else CK(cudaDeviceSynchronize());
+    if (pop->gexec) { cudaGraphExecDestroy(pop->gexec); pop->gexec = nullptr; pop->graph_n = 0; }
+    pop->d.wait_polls = polls ? polls : WALK_SPIN;
     return GP_OK;
 }
 

@@ -1,21 +1,23 @@
 // gp_eval_small_noalloc: full evaluation of a batch of small trees with no
 // device allocation at all.
 //
-// Some callers cannot call cudaMalloc: code running inside a CUDA-graph
-// capture of someone else's stream, a plug-in or a real-time loop whose host
-// process has handed its memory budget to a pool it does not control, or an
-// embedding that forbids allocation after start-up.  They still own their
-// inputs and outputs, so this entry point takes device pointers to both and
-// keeps the only scratch it needs -- the interpreter's deep-stack overflow
-// area, a work counter and a status word -- in one file-scope device array
-// of fixed size, loaded with the library and held by every GPU that loads it
-// until the process exits.
+// Some callers cannot call cudaMalloc: a plug-in whose host process has
+// handed the whole device memory to its own pool allocator (a cudaMalloc
+// there fails, or fragments memory the host accounts for), a real-time loop
+// that must not take the implicit device synchronisation an allocation can
+// bring, or an embedding whose memory is fixed at start-up.  They still own
+// their inputs and outputs, so this entry point takes device pointers to
+// both and keeps the only scratch it needs -- the interpreter's deep-stack
+// overflow area, a work counter and a status word -- in one file-scope
+// device array of fixed size, loaded with the library and held by every GPU
+// that loads it until the process exits.
 //
 // The scratch array is shared by every call on a device and keeps the
 // previous call's contents; each call clears the counter and status it needs
 // before launching.  Two calls whose work overlaps on the GPU (different
 // streams, or one not yet finished when the next is issued on another
 // stream) race on that array and give undefined results: serialise them.
+// Each call synchronises its stream before it returns, to read the status.
 #include "gpfdp.h"
 
 #include <cstdint>
@@ -89,7 +91,9 @@ __global__ void __launch_bounds__(NA_WARPS * 32) k_eval_small_noalloc(NaArgs a) 
         if (i >= a.n_trees) break;
         const uint64_t s64 = a.off[i], e64 = a.off[i + 1];
         const uint64_t n = e64 - s64;
-        if (e64 < s64 || n == 0 || n > NA_MAX_NODES || ((e64 + 15) & ~15ull) > a.ops_bytes) {
+        // ops_bytes is a multiple of 16, so e64 <= ops_bytes also keeps the
+        // staged 16-byte chunks inside the buffer (no rounding that could wrap)
+        if (e64 < s64 || n == 0 || n > NA_MAX_NODES || e64 > a.ops_bytes) {
             if (lane == 0) atomicOr(status, 1u);
             continue;
         }
@@ -135,7 +139,30 @@ __global__ void __launch_bounds__(NA_WARPS * 32) k_eval_small_noalloc(NaArgs a) 
 }
 
 std::mutex g_na_mu;
-float* g_na_ptr[64] = {};      // device address of the scratch, per device ordinal
+// device address of the scratch per device ordinal, and the context it was
+// looked up in: a context destroyed and re-created (cudaDeviceReset) loads
+// the module again, so the address is looked up again in the new context
+float* g_na_ptr[64] = {};
+void* g_na_ctx[64] = {};
+
+// the current context through the driver entry point (no link-time
+// dependency on the driver library)
+typedef int (*CtxGetCurrentFn)(void**);
+void* current_context() {
+    static CtxGetCurrentFn fn = nullptr;
+    static bool looked = false;
+    if (!looked) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 4000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<CtxGetCurrentFn>(p);
+        looked = true;
+    }
+    void* ctx = nullptr;
+    if (fn && fn(&ctx) != 0) ctx = nullptr;
+    return ctx;
+}
 
 }  // namespace
 
@@ -152,13 +179,17 @@ extern "C" int gp_eval_small_noalloc(const uint8_t* d_ops, size_t ops_bytes, con
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return GP_ECUDA;
     float* scratch = nullptr;
     {
-        // once per device, with that device current: the host-side name of the
-        // array is not a device address, so ask the runtime for it
+        // set-up, once per device (and context), with that device current: the
+        // host-side name of the array is not a device address, so ask the
+        // runtime for it
         std::lock_guard<std::mutex> lk(g_na_mu);
-        if (!g_na_ptr[dev]) {
+        void* ctx = current_context();
+        if (!g_na_ptr[dev] || !ctx || ctx != g_na_ctx[dev]) {
             void* p = nullptr;
+            // (creates the device's context if it does not exist yet)
             if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess) return GP_ECUDA;
             g_na_ptr[dev] = static_cast<float*>(p);
+            g_na_ctx[dev] = current_context();
         }
         scratch = g_na_ptr[dev];
     }

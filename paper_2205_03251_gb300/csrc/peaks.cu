@@ -1,0 +1,95 @@
+// gp_alu_peak: the issue rate of the plain ALU operations the interpreters
+// are built from, measured on the device at hand -- the roofline of the
+// tree interpreters (one opcode on one test case is one lane operation).
+//
+// Each thread runs eight independent dependency chains of one instruction
+// kind (binary32 add, 32-bit three-input logic, 32-bit integer add), written
+// as inline PTX so that exactly one instruction of the kind is issued per
+// step, over a grid of eight 256-thread CTAs per SM; the time is taken with
+// CUDA events around one launch after a warm-up launch.
+#include "gpfdp.h"
+
+#include <cstdint>
+
+namespace {
+
+constexpr int PK_CHAINS = 8;
+constexpr int PK_UNROLL = 16;
+constexpr int PK_THREADS = 256;
+constexpr int PK_CTAS_PER_SM = 8;
+
+template <int KIND>
+__device__ __forceinline__ uint32_t pk_step(uint32_t v, uint32_t a, uint32_t b) {
+    uint32_t r;
+    if constexpr (KIND == 0) {
+        float f;
+        asm volatile("add.rn.f32 %0, %1, %2;" : "=f"(f) : "f"(__uint_as_float(v)), "f"(__uint_as_float(a)));
+        r = __float_as_uint(f);
+    } else if constexpr (KIND == 1) {
+        asm volatile("lop3.b32 %0, %1, %2, %3, 0x96;" : "=r"(r) : "r"(v), "r"(a), "r"(b));   // v ^ a ^ b
+    } else {
+        asm volatile("add.s32 %0, %1, %2;" : "=r"(r) : "r"(v), "r"(a));
+    }
+    return r;
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(PK_THREADS) k_alu_peak(uint32_t iters, uint32_t a, uint32_t b, uint32_t* sink) {
+    uint32_t v[PK_CHAINS];
+#pragma unroll
+    for (int j = 0; j < PK_CHAINS; ++j)
+        v[j] = (KIND == 0) ? __float_as_uint(1.0f + (float)(threadIdx.x + j)) : (threadIdx.x * 2654435761u + j);
+    for (uint32_t i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int u = 0; u < PK_UNROLL; ++u) {
+#pragma unroll
+            for (int j = 0; j < PK_CHAINS; ++j) v[j] = pk_step<KIND>(v[j], a, b);
+        }
+    }
+    uint32_t acc = 0;
+#pragma unroll
+    for (int j = 0; j < PK_CHAINS; ++j) acc ^= v[j];
+    if (acc == 0x9E3779B9u && a == 0x12345u) sink[0] = acc;     // never true for the launch arguments used
+}
+
+template <int KIND>
+int run_peak(int nsm, uint32_t iters, double* out) {
+    const int grid = nsm * PK_CTAS_PER_SM;
+    uint32_t* sink = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int rc = GP_OK;
+    const uint32_t a = (KIND == 0) ? 0x33D6BF95u : 0x5bd1e995u, b = 0x1b873593u;   // binary32 1e-7 for the add
+    if (cudaMalloc(&sink, 16) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
+        cudaEventCreate(&e1) != cudaSuccess) {
+        rc = GP_ECUDA;
+    } else {
+        k_alu_peak<KIND><<<grid, PK_THREADS>>>(iters / 4 + 1, a, b, sink);     // warm-up
+        cudaEventRecord(e0);
+        k_alu_peak<KIND><<<grid, PK_THREADS>>>(iters, a, b, sink);
+        cudaEventRecord(e1);
+        float ms = 0.f;
+        if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess || ms <= 0.f)
+            rc = GP_ECUDA;
+        else
+            *out = (double)grid * PK_THREADS * iters * PK_UNROLL * PK_CHAINS / (ms * 1e-3);
+    }
+    cudaGetLastError();
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (sink) cudaFree(sink);
+    return rc;
+}
+
+}  // namespace
+
+extern "C" int gp_alu_peak(int kind, double* lane_ops_per_s) {
+    if (!lane_ops_per_s || kind < 0 || kind > 2) return GP_EINVAL;
+    int dev = 0, nsm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm <= 0)
+        return GP_ECUDA;
+    const uint32_t iters = 4096;
+    if (kind == 0) return run_peak<0>(nsm, iters, lane_ops_per_s);
+    if (kind == 1) return run_peak<1>(nsm, iters, lane_ops_per_s);
+    return run_peak<2>(nsm, iters, lane_ops_per_s);
+}

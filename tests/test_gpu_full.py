@@ -164,3 +164,32 @@ def test_full_size_population_sampled(gp):
         assert np.array_equal(oracle.canon_nan(pop.cache_value(i, j)),
                               oracle.canon_nan(oracle.eval_node_f32(tree, int(pos[j]), w["consts"], w["x"])))
     pop.close()
+
+
+@pytest.mark.parametrize("K", [1, 2, 4])
+def test_fitness_sums_in_case_order(gp, K):
+    """Terms 1, 2^-24, ..., 2^-24 of the fitness sum (the tree "x" on x = t +
+    term): binary32 accumulation in case order keeps exactly 1.0, the
+    reversed cases give 1 + 24 * 2^-23; any other order or a wider
+    accumulator gives another value for at least one of the two (the
+    derivation is beside the oracle's pin).  Both lie in one population of
+    trees that also holds larger ones, so both the fitness kernel and the
+    cached root values are exercised."""
+    import oracle
+    tiny = 2.0 ** -24
+    sign = np.array([1.0] + [(-1.0) ** c for c in range(1, 48)])
+    t = np.array([0.5] + [0.125] * 47, np.float32)
+    v = (t.astype(np.float64) + sign * np.array([1.0] + [tiny] * 47)).astype(np.float32)
+    k = np.zeros(251, np.float32)
+    trees = [np.array([4], np.uint8), np.array([0, 4, 2, 4, 5], np.uint8), np.array([3, 4, 4], np.uint8)]
+    ops = np.concatenate(trees)
+    off = np.zeros(len(trees) + 1, np.uint64)
+    off[1:] = np.cumsum([len(x) for x in trees])
+    for xv, tv, want in ((v, t, 0x3F800000), (v[::-1].copy(), t[::-1].copy(), 0x3F800018)):
+        pop = gp.Population(xv, tv, k, ops, off, max_nodes=64, cache_threshold=2, cases_per_lane=K)
+        pop.eval_full()
+        fit = pop.fitness()
+        assert fit.view(np.uint32)[0] == want
+        _, ofit = oracle.eval_pop_f32(ops, off, k, xv, tv)
+        assert np.array_equal(oracle.canon_nan(fit), oracle.canon_nan(ofit))
+        pop.close()

@@ -298,6 +298,43 @@ def test_full_size_uneven_population_sampled(gp):
     pop.close()
 
 
+def test_bounded_walk_waits_run_out(gp):
+    """Every wait inside a walk team is bounded.  With the bound cut to one
+    poll the waits give up (an evaluator finds the next level's descriptor
+    not built yet, the combining warp finds a sibling's values not ready),
+    the teams return, and the next synchronising call reports GP_ETIMEOUT;
+    a reload with the default bound then gives the oracle's fitness again,
+    and a generation after it the oracle's children."""
+    import oracle
+    import synth
+    ops, off = synth.population("big", synth.MASTER_SEED + 5, 16, target=200_000)
+    x, t = synth.cases(synth.MASTER_SEED + 5, 48)
+    k = synth.consts(synth.MASTER_SEED + 5)
+    maxn = 400_000
+    pop = gp.Population(x, t, k, ops, off, max_nodes=maxn, cache_threshold=1024, seed=77, walk_team=4)
+    pop.eval_full()
+    pop.set_wait_limit(1)
+    pop.crossover(0)
+    with pytest.raises(gp.GpError) as ei:
+        pop.eval_incremental()                    # its statistics synchronise
+    assert ei.value.code == gp.GP_ETIMEOUT
+    pop.set_wait_limit(0)
+    pop.load_trees(ops, off)
+    pop.eval_full()
+    _, f0 = oracle.eval_pop_f32(ops, off, k, x, t)
+    fit = pop.fitness()
+    assert oracle.canon_nan(fit).tobytes() == oracle.canon_nan(f0).tobytes()
+    pl = oracle.plan(ops, off, f0, T=7, seed=77, gen=0, max_nodes=maxn)
+    kops, koff = oracle.breed(ops, off, pl)
+    pop.crossover(0)
+    pop.eval_incremental()
+    _, kfit = oracle.eval_pop_f32(kops, koff, k, x, t)
+    assert oracle.canon_nan(pop.fitness()).tobytes() == oracle.canon_nan(kfit).tobytes()
+    for i in range(len(koff) - 1):
+        assert np.array_equal(pop.tree(i), kops[int(koff[i]):int(koff[i + 1])]), i
+    pop.close()
+
+
 def test_memory_lean_arena(gp):
     """Fitness-first order with fewer than 2P tree buffers: the same
     children and fitness as with 2P while the generations fit (parents that
@@ -340,30 +377,74 @@ def test_memory_lean_arena(gp):
         gp.Population(w["x"], w["t"], w["consts"], w["ops"], w["off"], max_nodes=40_000, arena_buffers=P + 10)
 
 
-def test_full_size_bench_configuration_sampled(gp):
+def _oracle_fitness_threaded(ops, off, k, x, t):
+    """Fitness of every tree by the oracle, one slice of trees per host
+    thread (the oracle's C calls release the interpreter lock)."""
+    import concurrent.futures as cf
+    import os
+    import oracle
+    P = len(off) - 1
+    nthr = max(1, min(os.cpu_count() or 1, 32))
+    bounds = np.linspace(0, P, nthr + 1).astype(int)
+
+    def part(j):
+        a, b = int(bounds[j]), int(bounds[j + 1])
+        if a == b:
+            return np.zeros(0, np.float32)
+        sub = np.asarray(off[a:b + 1], np.uint64) - np.uint64(off[a])
+        return oracle.eval_pop_f32(ops[int(off[a]):int(off[b])], sub, k, x, t)[1]
+
+    with cf.ThreadPoolExecutor(nthr) as ex:
+        return np.concatenate(list(ex.map(part, range(nthr))))
+
+
+def test_full_size_bench_configuration(gp):
     """500 trees of ~1e6 nodes in the benchmark's configuration: fitness-first
     order, MLP packing, graph mode, generations replayed from a captured
-    graph.  Sampled children of the last generation (their trees assembled
-    through their parents where they are not built) have exactly the fitness
-    that a full evaluation of their trees gives."""
+    graph.  The oracle rebuilds every generation on its own -- tournaments
+    and crossover points from the fitness it computed itself, children
+    spliced from its own copies of the parents -- and the GPU's children of
+    the eager first generation and of the last replayed one equal them byte
+    for byte (the trees of children that are not built are assembled through
+    their parents), and all 500 fitness values of both equal the oracle's
+    full evaluation of the spliced children, bit for bit."""
     import oracle
     import synth
     w = synth.workload(1)
     k, x, t = w["consts"], w["x"], w["t"]
-    pop = gp.Population(x, t, k, w["ops"], w["off"], max_nodes=1 << 21, cache_threshold=1024, seed=0x5EED,
+    seed, maxn = 0x5EED, 1 << 21
+    P = len(w["off"]) - 1
+    pop = gp.Population(x, t, k, w["ops"], w["off"], max_nodes=maxn, cache_threshold=1024, seed=seed,
                         packing=gp.GP_PACK_MLP, lazy=True)
     pop.set_graph_mode(True)
     pop.eval_full()
+    f0 = _oracle_fitness_threaded(w["ops"], w["off"], k, x, t)
+    assert oracle.canon_nan(pop.fitness()).tobytes() == oracle.canon_nan(f0).tobytes()
+
+    def oracle_generation(ops, off, fit, g):
+        pl = oracle.plan(ops, off, fit, T=7, seed=seed, gen=g, max_nodes=maxn)
+        kops, koff = oracle.breed(ops, off, pl)
+        return kops, koff, _oracle_fitness_threaded(kops, koff, k, x, t)
+
+    def check(kops, koff, kfit, label):
+        got = pop.fitness()
+        bad = np.nonzero(oracle.canon_nan(got) != oracle.canon_nan(kfit))[0]
+        assert len(bad) == 0, f"{label}: fitness differs for children {bad[:10]}"
+        for i in range(P):
+            assert np.array_equal(pop.tree(i), kops[int(koff[i]):int(koff[i + 1])]), f"{label}: child {i}"
+
+    # generation 0, eager
+    ops0, off0, fit0 = oracle_generation(w["ops"], w["off"], f0, 0)
     pop.crossover(0)
     pop.eval_incremental()
+    check(ops0, off0, fit0, "generation 0")
+    # generations 1 and 2, one replay of a captured graph
     pop.graph_capture(1, 2)
-    for _ in range(2):
-        pop.graph_launch()
-    fit = pop.fitness()
+    pop.graph_launch()
+    ops1, off1, fit1 = oracle_generation(ops0, off0, fit0, 1)
+    del ops0, off0
+    ops2, off2, fit2 = oracle_generation(ops1, off1, fit1, 2)
+    check(ops2, off2, fit2, "generation 2 (graph replay)")
     stop, _ = pop.walk_info()
     assert (stop >= 0).mean() > 0.5            # most walks stop below the root, as in the benchmark
-    for i in (0, 7, 250, 499):
-        kid = pop.tree(i)
-        want = oracle.fitness_f32(oracle.eval_node_f32(kid, 0, k, x), t)
-        assert oracle.canon_nan(np.array([fit[i]]))[0] == oracle.canon_nan(np.array([want]))[0], i
     pop.close()

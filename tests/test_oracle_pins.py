@@ -112,6 +112,40 @@ def test_identity_tree_fitness_exact(oracle_mod):
     assert Fraction(float(oracle_mod.fitness_f32(vals, t))) == want
 
 
+# Terms of the fitness sum chosen so that only binary32 accumulation in case
+# order gives the stated results.  Case 0 contributes 1.0, cases 1..47 each
+# 2^-24.  In case order every 1 + 2^-24 is a tie between 1 and 1 + 2^-23 and
+# rounds to even, so the sum stays exactly 1.0.  Reversed, the 47 small terms
+# add exactly to 47 * 2^-24 first, and 1 + 47 * 2^-24 = 1 + 23.5 * 2^-23 ties
+# to 1 + 24 * 2^-23 (bits 0x3F800018).  A binary64 accumulator, a pairwise or
+# a compensated sum gives 1 + 24 * 2^-23 for both orders, a dropped |.|
+# (alternating signs below) or v + t in place of v - t changes both.
+def _order_vectors():
+    tiny = 2.0 ** -24
+    sign = np.array([1.0] + [(-1.0) ** c for c in range(1, 48)])
+    t = np.array([0.5] + [0.125] * 47, np.float32)               # exact dyadic targets
+    terms = np.array([1.0] + [tiny] * 47)
+    v = (t.astype(np.float64) + sign * terms).astype(np.float32)  # each v - t is exact in binary32
+    assert np.array_equal(np.abs(v.astype(np.float64) - t.astype(np.float64)), terms)
+    return v, t
+
+
+def test_fitness_sums_in_case_order_binary32(oracle_mod):
+    v, t = _order_vectors()
+    f = oracle_mod.fitness_f32(v, t)
+    assert np.float32(f).view(np.uint32) == 0x3F800000              # exactly 1.0
+    rv, rt = v[::-1].copy(), t[::-1].copy()
+    fr = oracle_mod.fitness_f32(rv, rt)
+    assert np.float32(fr).view(np.uint32) == 0x3F800018             # 1 + 24 * 2^-23
+    # the same through a whole-population evaluation of the tree "x" with x = v
+    ops = np.array([X], np.uint8)
+    off = np.array([0, 1], np.uint64)
+    for xv, tv, want in ((v, t, 0x3F800000), (rv, rt, 0x3F800018)):
+        vals, fit = oracle_mod.eval_pop_f32(ops, off, _consts(), xv, tv)
+        assert np.array_equal(vals[0], xv)
+        assert fit.view(np.uint32)[0] == want
+
+
 def test_protected_division(oracle_mod):
     x = np.array([0.0, -0.5, 0.25, 1e-3], np.float32)
     for zero in (0.0, -0.0):
