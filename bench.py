@@ -87,6 +87,10 @@ def parse():
     ap.add_argument("--threshold", type=int, default=1024)
     ap.add_argument("--cases-per-lane", type=int, default=0, choices=[0, 1, 2, 4], help="0: automatic")
     ap.add_argument("--walk-team", type=int, default=0, choices=[0, 1, 2, 4, 8], help="warps per child; 0: automatic")
+    ap.add_argument("--stack-window", type=int, default=0, choices=[0, 16, 32, 64],
+                    help="interpreter stack entries per warp in shared memory; 0: 16 (uneven: autotuned)")
+    ap.add_argument("--long-walks", type=int, default=0,
+                    help="first children of the work order walked by 16-warp teams; 0: none")
     ap.add_argument("--arena-buffers", type=int, default=0,
                     help="tree buffers in the arena (fitness-first order; 0: 2 x trees)")
     ap.add_argument("--packing", default="mlp", choices=list(PACKING))
@@ -556,18 +560,22 @@ def main():
     pop_kw = {"cache_threshold": args.threshold, "packing": PACKING[args.packing],
               "cache_budget_bytes": args.cache_budget_gb << 30, "lazy": args.lazy,
               "cases_per_lane": args.cases_per_lane, "walk_team": args.walk_team,
-              "arena_buffers": args.arena_buffers}
+              "arena_buffers": args.arena_buffers, "long_walks": args.long_walks,
+              "stack_window": args.stack_window}
     tune = None
     if args.workload == "uneven" and args.autotune:
         ks = ((1,) if (boolean and kind_kw["mux_k"] == 2) else (1, 2) if (boolean or integer or args.cases <= 64)
               else (2, 4))
         best, table = gp.autotune(w["x"], w["t"], w["consts"], w["ops"], w["off"], max_nodes=maxn, ks=ks,
-                                  ts=(256, 1024), teams=(1, 2, 4), generations=2, boolean=boolean,
+                                  ts=(256, 1024), teams=(1, 2, 4),
+                                  ws=((args.stack_window,) if args.stack_window else (16, 64)),
+                                  generations=2, boolean=boolean,
                                   seed=0x5EED + rank, packing=pop_kw["packing"], stream=stream,
                                   cache_budget_bytes=args.cache_budget_gb << 30, **kind_kw)
         pop_kw.update(best)
         tune = {"chosen": best, "candidates": [{k: r[k] for k in ("cases_per_lane", "cache_threshold", "walk_team",
-                                                                   "ms_full", "ms_generation", "identical")}
+                                                                   "stack_window", "ms_full", "ms_generation",
+                                                                   "identical")}
                                                for r in table]}
     pop = gp.Population(None if boolean else w["x"], None if boolean else w["t"], w["consts"], w["ops"], w["off"],
                         max_nodes=maxn, boolean=boolean, seed=0x5EED + rank, stream=stream, **kind_kw, **pop_kw)
@@ -633,9 +641,13 @@ def main():
     spec_peak = nsm * FP32_LANES_PER_SM * sm_max * 1e6 / 1e12
     # the interpreters' roofline: the measured issue rate of the instruction
     # their function set is made of (binary32 add; 32-bit logic on words of
-    # 32 Boolean cases; 32-bit integer add), in node-case operations per second
-    alu_kind = "lop3" if boolean else "iadd" if integer else "fadd"
-    alu_meas = {k: gp.gp_alu_peak(k) for k in ("fadd", "lop3", "iadd")}
+    # 32 Boolean cases), in node-case operations per second.  The integer set
+    # takes the binary32 add's rate: 32-bit integer and binary32 adds issue on
+    # the same lanes, and a chain of integer adds of a loop-invariant operand
+    # measured twice that rate (the adds are combined), so it does not measure
+    # one add per instruction
+    alu_kind = "lop3" if boolean else "fadd"
+    alu_meas = {k: gp.gp_alu_peak(k) for k in ("fadd", "lop3")}
     alu_peak = alu_meas[alu_kind] * (32 if boolean else 1) / 1e12
     alu_note = (f"measured gp_alu_peak('{alu_kind}') = {alu_meas[alu_kind] / 1e12:.2f} T lane-ops/s"
                 + (" x 32 Boolean cases per 32-bit word" if boolean else "")
@@ -656,12 +668,17 @@ def main():
         line["config"]["cases_per_lane"] = args.cases_per_lane
     if args.walk_team:
         line["config"]["walk_team"] = args.walk_team
+    if args.long_walks:
+        line["config"]["long_walks"] = args.long_walks
+    if args.stack_window:
+        line["config"]["stack_window"] = args.stack_window
     if args.arena_buffers:
         line["config"]["arena_buffers"] = args.arena_buffers
     if tune:
         line["config"]["cases_per_lane"] = pop_kw["cases_per_lane"]
         line["config"]["cache_threshold"] = pop_kw["cache_threshold"]
         line["config"]["walk_team"] = pop_kw["walk_team"]
+        line["config"]["stack_window"] = pop_kw["stack_window"]
         line["autotune"] = tune
     # DRAM traffic figures come from ncu captures of the grafted 1e6-node trees at 48 cases and
     # threshold 1,024; other workloads report none

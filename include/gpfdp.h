@@ -102,6 +102,20 @@ typedef struct {
                                    parents; one that finds too few free stops (later kernels return
                                    at once) and the next synchronising call reports GP_ECAPACITY,
                                    after which the population must be reloaded (gp_load_trees) */
+    uint32_t long_walks;        /* the first long_walks children of the work order (the longest predicted
+                                   walks, Sec. 3 and Sec. 4.1: the longest tasks first) are walked by teams
+                                   of 16 warps (8 when 16 do not fit shared memory), beside the teams of
+                                   walk_team warps that walk the others: 0 (or 0xFFFFFFFF) = none */
+    uint32_t onepass_nodes;     /* children of at most this many nodes are interpreted in one pass
+                                   instead of walked level by level (same values, bit for bit; the
+                                   walk pays per level, a small child with a deep crossover point has
+                                   many levels): 0 = 4,096 (the most allowed), 0xFFFFFFFF = none */
+    uint32_t stack_window;      /* interpreter stack entries per warp kept in shared memory (deeper ones
+                                   go to a slower per-warp global area): 0 = 16, or 16, 32, 64.  Deep
+                                   trees (uniform random binary trees of n nodes need about 2 sqrt(n)
+                                   entries) want more; each entry costs 128 x cases_per_lane bytes per
+                                   warp of shared memory.  GP_EINVAL when the kernels' shared memory
+                                   does not fit */
 } gp_config;
 
 /* Per-call statistics of the last evaluation (host copy). */
@@ -322,6 +336,7 @@ typedef struct {
     uint32_t cases_per_lane;    /* K: test cases per lane, i.e. 32 x K cases per warp task */
     uint32_t cache_threshold;   /* T: subtree size from which values are cached (the subtree split) */
     uint32_t walk_team;         /* warps per child in the incremental walk */
+    uint32_t stack_window;      /* interpreter stack entries kept in shared memory */
     int32_t  status;            /* GP_OK, or the error that ruled the candidate out */
     uint32_t identical;         /* 1 when its fitness equals the first valid candidate's, bit for bit */
     float    ms_full;           /* one gp_eval_full, device milliseconds */
@@ -329,23 +344,26 @@ typedef struct {
 } gp_tune_result;
 
 /*
- * Autotune the work splits for a population: for every triple of
- * ks[0..n_k) x ts[0..n_t) x teams[0..n_team) (cases_per_lane x
- * cache_threshold x walk_team) build the population described by base and
+ * Autotune the work splits for a population: for every combination of
+ * ks[0..n_k) x ts[0..n_t) x teams[0..n_team) x ws[0..n_w) (cases_per_lane
+ * x cache_threshold x walk_team x stack_window; ws may be NULL with n_w = 0:
+ * base's stack window only) build the population described by base and
  * the host data (same rules as gp_pop_create), time one gp_eval_full and,
  * when generations > 0 (even), one replay of a captured graph of that many
  * generations (after four warm-up replays), and check that its fitness
- * matches the first candidate's bit for bit.  results[(a * n_t + b) * n_team + w]
- * receives candidate (ks[a], ts[b], teams[w]); *best = base with the fastest
- * valid candidate's three fields (fastest per generation when generations >
- * 0, else fastest full evaluation).  One candidate's population exists at a
+ * matches the first candidate's bit for bit.
+ * results[((a * n_t + b) * n_team + w) * max(n_w, 1) + v] receives candidate
+ * (ks[a], ts[b], teams[w], ws[v]); *best = base with the fastest valid
+ * candidate's four fields (fastest per generation when generations > 0,
+ * else fastest full evaluation).  One candidate's population exists at a
  * time.  Synchronising.  Returns GP_ENOMEM when no candidate could run.
  * The paper has no counterpart: its CPU interpreter has one fixed layout.
  */
 int gp_autotune(const gp_config* base, const float* x, const float* targets, const float* consts,
                 const uint8_t* ops, const uint64_t* offsets, const uint32_t* ks, uint32_t n_k,
                 const uint32_t* ts, uint32_t n_t, const uint32_t* teams, uint32_t n_team,
-                uint32_t generations, void* stream, gp_tune_result* results, gp_config* best);
+                const uint32_t* ws, uint32_t n_w, uint32_t generations, void* stream,
+                gp_tune_result* results, gp_config* best);
 
 /* The autotuner's choice rule on its own: index of the fastest candidate
  * with status GP_OK and identical = 1 (ties: the earlier), or -1. */
@@ -366,7 +384,7 @@ int gp_set_wait_limit(gp_pop* pop, uint32_t polls);
 /*
  * Measured issue rate of the plain ALU operations the interpreters are made
  * of, on the current device: kind 0 binary32 add, 1 32-bit three-input
- * logic (the Boolean sets' AND/OR/NAND/NOR words), 2 32-bit integer add.
+ * logic (the Boolean sets' AND/OR/NAND/NOR words); GP_EINVAL for others.
  * *lane_ops_per_s receives lane operations per second over all SMs (the
  * roofline of an interpreter that spends one lane operation per opcode and
  * test case, Sec. 4.2).  The paper has no counterpart.  Allocates 16 bytes

@@ -34,7 +34,9 @@ class GpConfig(ctypes.Structure):
                 ("packing", ctypes.c_uint32), ("cases_per_lane", ctypes.c_uint32),
                 ("cache_budget_bytes", ctypes.c_uint64), ("seed", ctypes.c_uint64),
                 ("walk_warps", ctypes.c_uint32), ("mlp_lr_micro", ctypes.c_uint32),
-                ("walk_team", ctypes.c_uint32), ("lazy_children", ctypes.c_uint32), ("arena_buffers", ctypes.c_uint32)]
+                ("walk_team", ctypes.c_uint32), ("lazy_children", ctypes.c_uint32), ("arena_buffers", ctypes.c_uint32),
+                ("long_walks", ctypes.c_uint32), ("onepass_nodes", ctypes.c_uint32),
+                ("stack_window", ctypes.c_uint32)]
 
 
 class GpStats(ctypes.Structure):
@@ -54,7 +56,8 @@ class GpStats(ctypes.Structure):
 
 class GpTuneResult(ctypes.Structure):
     _fields_ = [("cases_per_lane", ctypes.c_uint32), ("cache_threshold", ctypes.c_uint32),
-                ("walk_team", ctypes.c_uint32), ("status", ctypes.c_int32), ("identical", ctypes.c_uint32),
+                ("walk_team", ctypes.c_uint32), ("stack_window", ctypes.c_uint32), ("status", ctypes.c_int32),
+                ("identical", ctypes.c_uint32),
                 ("ms_full", ctypes.c_float), ("ms_generation", ctypes.c_float)]
 
     def as_dict(self) -> dict:
@@ -109,8 +112,8 @@ def load() -> ctypes.CDLL:
         "gp_set_graph_mode": (i32, [vp, i32, u64]),
         "gp_graph_capture": (i32, [vp, u32, u32]),
         "gp_graph_launch": (i32, [vp]),
-        "gp_autotune": (i32, [ctypes.POINTER(GpConfig), vp, vp, vp, vp, vp, vp, u32, vp, u32, vp, u32, u32, vp,
-                              ctypes.POINTER(GpTuneResult), ctypes.POINTER(GpConfig)]),
+        "gp_autotune": (i32, [ctypes.POINTER(GpConfig), vp, vp, vp, vp, vp, vp, u32, vp, u32, vp, u32, vp, u32, u32,
+                              vp, ctypes.POINTER(GpTuneResult), ctypes.POINTER(GpConfig)]),
         "gp_autotune_pick": (i32, [ctypes.POINTER(GpTuneResult), u32, u32]),
     }
     for name, (res, args) in sig.items():
@@ -394,10 +397,11 @@ def gp_graph_launch(h):
     _check(load().gp_graph_launch(h), h)
 
 
-def gp_autotune(cfg: GpConfig, x, targets, consts, ops, offsets, ks, ts, teams, generations: int, stream=None):
-    """Time every (cases_per_lane, cache_threshold, walk_team) triple of
-    ks x ts x teams on this population; returns (best GpConfig, list of
-    GpTuneResult dicts)."""
+def gp_autotune(cfg: GpConfig, x, targets, consts, ops, offsets, ks, ts, teams, generations: int, stream=None,
+                ws=()):
+    """Time every (cases_per_lane, cache_threshold, walk_team, stack_window)
+    combination of ks x ts x teams x ws (ws empty: cfg's stack window) on
+    this population; returns (best GpConfig, list of GpTuneResult dicts)."""
     lib = load()
     x = np.ascontiguousarray(x, np.float32)
     targets = np.ascontiguousarray(targets, np.float32)
@@ -408,14 +412,17 @@ def gp_autotune(cfg: GpConfig, x, targets, consts, ops, offsets, ks, ts, teams, 
     ks = np.ascontiguousarray(ks, np.uint32)
     ts = np.ascontiguousarray(ts, np.uint32)
     teams = np.ascontiguousarray(teams, np.uint32)
+    ws = np.ascontiguousarray(ws if len(ws) else [0], np.uint32)
+    n_w = len(ws) if ws[0] or len(ws) > 1 else 0
     if stream is None:
         stream = _default_stream()
     elif hasattr(stream, "cuda_stream"):
         stream = stream.cuda_stream
-    res = (GpTuneResult * (len(ks) * len(ts) * len(teams)))()
+    res = (GpTuneResult * (len(ks) * len(ts) * len(teams) * max(1, n_w)))()
     best = GpConfig()
     _check(lib.gp_autotune(ctypes.byref(cfg), _ptr(x), _ptr(targets), _ptr(consts), _ptr(ops), _ptr(offsets),
-                           _ptr(ks), len(ks), _ptr(ts), len(ts), _ptr(teams), len(teams), generations,
+                           _ptr(ks), len(ks), _ptr(ts), len(ts), _ptr(teams), len(teams),
+                           _ptr(ws) if n_w else None, n_w, generations,
                            ctypes.c_void_p(stream), res, ctypes.byref(best)))
     return best, [r.as_dict() for r in res]
 
@@ -429,12 +436,13 @@ def gp_autotune_pick(results: list[dict], generations: int) -> int:
     return load().gp_autotune_pick(arr, len(results), generations)
 
 
-def autotune(x, t, consts, ops, off, *, max_nodes: int, ks=(1, 2, 4), ts=(64, 256, 1024), teams=(0,),
+def autotune(x, t, consts, ops, off, *, max_nodes: int, ks=(1, 2, 4), ts=(64, 256, 1024), teams=(0,), ws=(),
              generations: int = 2, boolean: bool = False, tournament: int = 7, packing: int = GP_PACK_STATIC,
              cache_budget_bytes: int = 0, seed: int = 0, stream=None, mux_k: int = 2, integer: bool = False):
-    """Autotune the case, subtree and walk-team splits for a population;
-    returns (keyword arguments for Population with the chosen split, result
-    table).  A team of 0 means the automatic choice."""
+    """Autotune the case, subtree, walk-team and stack-window splits for a
+    population; returns (keyword arguments for Population with the chosen
+    split, result table).  A team of 0 means the automatic choice; ws empty
+    keeps the default stack window."""
     off = np.asarray(off, np.uint64)
     C = (1 << (mux_k + (1 << mux_k))) if boolean else len(x)
     if boolean:
@@ -451,21 +459,21 @@ def autotune(x, t, consts, ops, off, *, max_nodes: int, ks=(1, 2, 4), ts=(64, 25
                    funcset=funcset, cache_threshold=1024,
                    tournament=tournament, packing=packing, cases_per_lane=0,
                    cache_budget_bytes=cache_budget_bytes, seed=seed & (2**64 - 1))
-    best, table = gp_autotune(cfg, x, t, consts, ops, off, ks, ts, teams, generations, stream)
+    best, table = gp_autotune(cfg, x, t, consts, ops, off, ks, ts, teams, generations, stream, ws=ws)
     return ({"cases_per_lane": best.cases_per_lane, "cache_threshold": best.cache_threshold,
-             "walk_team": best.walk_team}, table)
+             "walk_team": best.walk_team, "stack_window": best.stack_window}, table)
 
 
 def gp_set_profiling(h, on: bool):
     _check(load().gp_set_profiling(h, 1 if on else 0), h)
 
 
-ALU_KINDS = {"fadd": 0, "lop3": 1, "iadd": 2}
+ALU_KINDS = {"fadd": 0, "lop3": 1}
 
 
 def gp_alu_peak(kind: str) -> float:
     """Measured lane operations per second of one ALU instruction kind on
-    the current device ("fadd", "lop3" or "iadd")."""
+    the current device ("fadd" or "lop3")."""
     out = ctypes.c_double(0.0)
     _check(load().gp_alu_peak(ALU_KINDS[kind], ctypes.byref(out)))
     return out.value
@@ -486,7 +494,8 @@ class Population:
                  boolean: bool = False, tournament: int = 7, packing: int = GP_PACK_STATIC,
                  cases_per_lane: int = 0, cache_budget_bytes: int = 0, seed: int = 0, stream=None,
                  walk_warps: int = 0, mlp_lr_micro: int = 0, walk_team: int = 0, lazy: bool = False,
-                 mux_k: int = 2, integer: bool = False, arena_buffers: int = 0):
+                 mux_k: int = 2, integer: bool = False, arena_buffers: int = 0, long_walks: int = 0,
+                 onepass_nodes: int = 0, stack_window: int = 0):
         """boolean: the k-multiplexer (mux_k = 2: 6-mux, 64 cases; 3: 11-mux,
         2,048 cases); integer: the integer set (x, t, consts are int32)."""
         off = np.asarray(off, np.uint64)
@@ -507,7 +516,9 @@ class Population:
                        cache_threshold=cache_threshold, tournament=tournament, packing=packing,
                        cases_per_lane=cases_per_lane, cache_budget_bytes=cache_budget_bytes,
                        seed=seed & (2**64 - 1), walk_warps=walk_warps, mlp_lr_micro=mlp_lr_micro,
-                       walk_team=walk_team, lazy_children=1 if lazy else 0, arena_buffers=arena_buffers)
+                       walk_team=walk_team, lazy_children=1 if lazy else 0, arena_buffers=arena_buffers,
+                       long_walks=long_walks & 0xFFFFFFFF, onepass_nodes=onepass_nodes & 0xFFFFFFFF,
+                       stack_window=stack_window)
         if boolean:
             x = np.zeros(1, np.float32)
             t = np.zeros(1, np.float32)

@@ -1,9 +1,11 @@
-// Project-written autotuner for the three splits of the evaluation work:
+// Project-written autotuner for the splits of the evaluation work:
 // cases_per_lane (how many test cases each lane carries, i.e. the case
 // tile of one warp: 32 x K cases), cache_threshold (the subtree size from
 // which node values are cached, i.e. where trees are cut into the
 // warp-sized subtree tasks of the interpreter and the levels of the
-// incremental walk) and walk_team (warps per child in the walk).  Each
+// incremental walk), walk_team (warps per child in the walk) and
+// stack_window (interpreter stack entries per warp in shared memory: deep
+// trees want more, at the price of fewer resident warps).  Each
 // candidate is measured on the caller's own population: a full evaluation,
 // then a captured graph of generations, both timed with CUDA events on the
 // population's stream.  Results never depend
@@ -90,38 +92,45 @@ int gp_autotune_pick(const gp_tune_result* results, uint32_t n, uint32_t generat
 int gp_autotune(const gp_config* base, const float* x, const float* targets, const float* consts,
                 const uint8_t* ops, const uint64_t* offsets, const uint32_t* ks, uint32_t n_k,
                 const uint32_t* ts, uint32_t n_t, const uint32_t* teams, uint32_t n_team,
-                uint32_t generations, void* stream, gp_tune_result* results, gp_config* best) {
+                const uint32_t* ws, uint32_t n_w, uint32_t generations, void* stream,
+                gp_tune_result* results, gp_config* best) {
     if (!base || !consts || !ops || !offsets || !ks || !ts || !teams || !results || !best || n_k == 0 ||
-        n_t == 0 || n_team == 0)
+        n_t == 0 || n_team == 0 || (n_w && !ws))
         return GP_EINVAL;
     if (generations & 1u) return GP_EINVAL;
-    const uint32_t n = n_k * n_t * n_team;
+    const uint32_t nw = n_w ? n_w : 1u;
+    const uint32_t n = n_k * n_t * n_team * nw;
     std::vector<float> ref(base->pop_size), fit(base->pop_size);
     bool have_ref = false;
     std::string first_err;
     for (uint32_t a = 0; a < n_k; ++a) {
         for (uint32_t b = 0; b < n_t; ++b) {
             for (uint32_t w = 0; w < n_team; ++w) {
-                gp_tune_result& r = results[(a * n_t + b) * n_team + w];
-                memset(&r, 0, sizeof r);
-                r.cases_per_lane = ks[a];
-                r.cache_threshold = ts[b];
-                r.walk_team = teams[w];
-                gp_config cfg = *base;
-                cfg.cases_per_lane = ks[a];
-                cfg.cache_threshold = ts[b];
-                cfg.walk_team = teams[w];
-                std::string err;
-                r.status = run_candidate(&cfg, x, targets, consts, ops, offsets, generations,
-                                         static_cast<cudaStream_t>(stream), &r, fit, err);
-                if (r.status != GP_OK) {
-                    if (first_err.empty())
-                        first_err = "K=" + std::to_string(ks[a]) + " T=" + std::to_string(ts[b]) + " team=" +
-                                    std::to_string(teams[w]) + ": " + err;
-                    continue;
+                for (uint32_t v = 0; v < nw; ++v) {
+                    gp_tune_result& r = results[((a * n_t + b) * n_team + w) * nw + v];
+                    memset(&r, 0, sizeof r);
+                    gp_config cfg = *base;
+                    cfg.cases_per_lane = ks[a];
+                    cfg.cache_threshold = ts[b];
+                    cfg.walk_team = teams[w];
+                    if (n_w) cfg.stack_window = ws[v];
+                    r.cases_per_lane = ks[a];
+                    r.cache_threshold = ts[b];
+                    r.walk_team = teams[w];
+                    r.stack_window = cfg.stack_window;
+                    std::string err;
+                    r.status = run_candidate(&cfg, x, targets, consts, ops, offsets, generations,
+                                             static_cast<cudaStream_t>(stream), &r, fit, err);
+                    if (r.status != GP_OK) {
+                        if (first_err.empty())
+                            first_err = "K=" + std::to_string(ks[a]) + " T=" + std::to_string(ts[b]) + " team=" +
+                                        std::to_string(teams[w]) + " W=" + std::to_string(cfg.stack_window) + ": " +
+                                        err;
+                        continue;
+                    }
+                    if (!have_ref) { ref = fit; have_ref = true; }
+                    r.identical = memcmp(ref.data(), fit.data(), sizeof(float) * base->pop_size) == 0 ? 1u : 0u;
                 }
-                if (!have_ref) { ref = fit; have_ref = true; }
-                r.identical = memcmp(ref.data(), fit.data(), sizeof(float) * base->pop_size) == 0 ? 1u : 0u;
             }
         }
     }
@@ -134,6 +143,7 @@ int gp_autotune(const gp_config* base, const float* x, const float* targets, con
     best->cases_per_lane = results[j].cases_per_lane;
     best->cache_threshold = results[j].cache_threshold;
     best->walk_team = results[j].walk_team;
+    best->stack_window = results[j].stack_window;
     return GP_OK;
 }
 

@@ -22,7 +22,7 @@ enum : uint32_t {
 };
 
 // queue counters
-enum { Q_ITEMS = 0, Q_SKEL = 1, Q_WALK = 2, Q_MISC = 3, Q_ALLOC = 4, Q_PATHV = 5, NQ = 16 };
+enum { Q_ITEMS = 0, Q_SKEL = 1, Q_WALK = 2, Q_MISC = 3, Q_ALLOC = 4, Q_PATHV = 5, Q_WALK_LONG = 6, NQ = 16 };
 
 // Value kinds of the function sets.  Every value travels as 32 bits in a
 // float register or slot: a binary32 number (VF), a word of 32 Boolean

@@ -69,6 +69,12 @@ struct GenBufs {
     uint32_t* pv_end;                // [pvcap] child end of the recorded node
     uint32_t pvcap;
     uint32_t* order;                 // [P] walk order
+    uint32_t* small_cnt;             // [P] case blocks of a one-pass child evaluated so far
+    float* small_val;                // [P][Cpad] root values of the one-pass children
+    uint32_t* onepass;               // [P] 1: the child is evaluated in one pass (k_onepass_*), not walked
+    uint32_t* op_base;               // [P] first walk record of a one-pass child
+    uint32_t* op_cnt;                // [OP_BUCKETS] one-pass children per size bucket, then [OP_BUCKETS] units taken
+    uint32_t* op_bucket;             // [OP_BUCKETS][P] one-pass children by size bucket (log2 of the size)
     unsigned long long* gstat;       // [NGSTAT]
     uint32_t max_nodes, tsize;
     uint64_t seed;
@@ -1073,8 +1079,16 @@ __device__ __forceinline__ void dis_store(const GenBufs& g, uint32_t i, uint32_t
 // values of nodes that are cached in the child are recorded for the
 // child's cache; above the stop only child-cached nodes that the mother
 // does not cache need computing.
-template <int K, int V>
-__global__ void __launch_bounds__(256, 2) k_walk(DevPop d, GenBufs g, CacheView par, uint32_t nw) {
+// The children one launch walks: entries [q_lo, q_hi) of the work order,
+// taken through queue counter qctr; its warps use the interpreter overflow
+// stacks from warp ovf_base on.
+struct WalkRange {
+    uint32_t q_lo, q_hi, qctr, ovf_base;
+};
+
+template <int K, int V, int MAXT>
+__global__ void __launch_bounds__(MAXT, 512 / MAXT) k_walk(DevPop d, GenBufs g, CacheView par, uint32_t nw,
+                                                           WalkRange wr) {
     if (halted(d)) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const uint32_t Cpad = d.Cpad, Cn = d.C, ncb = d.ncb, T = d.T;
@@ -1101,7 +1115,7 @@ __global__ void __launch_bounds__(256, 2) k_walk(DevPop d, GenBufs g, CacheView 
     ic.maxd = (int)d.maxdepth;
     ic.kc = kc;
     ic.kb = kc + 256;
-    ic.g = d.ovf + (size_t)(blockIdx.x * nw + warp) * (d.maxdepth - d.W) * 32 * K;
+    ic.g = d.ovf + (size_t)(wr.ovf_base + blockIdx.x * nw + warp) * (d.maxdepth - d.W) * 32 * K;
     uint8_t* stA = wb + (size_t)d.W * 32 * K * 4;
     uint8_t* stB = stA + STAGE_BYTES;
     volatile uint32_t* dtag = sc + 16;                 // [WALK_RING] level + 1 whose descriptor is in the slot
@@ -1113,14 +1127,16 @@ __global__ void __launch_bounds__(256, 2) k_walk(DevPop d, GenBufs g, CacheView 
     unsigned long long st_interp = 0, st_levels = 0, st_stopped = 0, st_pathops = 0;
 
     for (;;) {
-        if (tid == 0) sc[0] = atomicAdd(&d.q[Q_WALK], 1u);
+        if (tid == 0) sc[0] = atomicAdd(&d.q[wr.qctr], 1u);
         __syncthreads();
-        const uint32_t qi = sc[0];
+        const uint32_t qi = wr.q_lo + sc[0];
         __syncthreads();
-        if (qi >= d.P) break;
+        if (qi >= wr.q_hi) break;
         const uint32_t i = g.order[qi];
         const uint32_t fl = g.flags[i];
         const uint32_t m = g.mother[i];
+        // children evaluated in one pass (k_onepass_eval) are not walked
+        if (g.onepass[i]) continue;
         if (tid == 0) {
             g.walkA[i] = -1; g.nins[i] = 0; g.pv_cnt[i] = 0;
             if (g.dis) g.dis_n[i] = 0;
@@ -1147,73 +1163,6 @@ __global__ void __launch_bounds__(256, 2) k_walk(DevPop d, GenBufs g, CacheView 
         const uint32_t me0 = par.e_off[m], me1 = par.e_off[m + 1];
         const uint32_t fe0 = par.e_off[f], fe1 = par.e_off[f + 1];
         uint32_t npv = 0, nins_i = 0;
-
-        // ---- a child smaller than the threshold caches only its root: one
-        // pass over the whole child costs less than a walk of its levels (same
-        // values, bit for bit); its root value is recorded when it differs from
-        // the mother's (or is a new root made of a small donated subtree)
-        if (nk < T && !g.dis) {
-            for (uint32_t cb = warp; cb < ncb; cb += nw) {
-                load_cases<K>(d, cb, ic.xv);
-                float v[K];
-                if (virt) {
-                    // the whole child from its three pieces: mother head, donated subtree, mother tail
-                    const uint8_t* fb = d.arena + (size_t)g.pbuf[f] * d.cap;
-                    __syncwarp();
-                    for (uint32_t x = lane; x < nk; x += 32)
-                        stA[x] = x < c ? ok_[x] : (x < c + s ? fb[dd + (x - c)] : ok_[x - tdl]);
-                    __syncwarp();
-                    Istate<K> ist;
-#pragma unroll
-                    for (int kk = 0; kk < K; ++kk) ist.acc[kk] = 0.f;
-                    ist.sp = 0;
-                    ist.ok = true;
-                    interp_staged_lone<K, V>(stA, 0, nk, ist, ic);
-                    if (!ist.ok && lane == 0) set_status(d.status, ST_STACK);
-#pragma unroll
-                    for (int kk = 0; kk < K; ++kk) v[kk] = ist.acc[kk];
-                } else {
-                    eval_run<K, V>(ok_, 0, nk, stA, ic, v, d.status);
-                }
-                st_interp += nk;
-                store_blk<K>(nvs, cb, v);
-                if (c != 0) {
-                    load_vec<K>(par.slots, Cpad, par.e_slot[me0], v, cb);
-                    store_blk<K>(ovs, cb, v);
-                }
-            }
-            __syncthreads();
-            bool same = (c != 0);
-            if (same)
-                for (uint32_t j = tid; j < Cn; j += nthr)
-                    if (__float_as_uint(nvs[j]) != __float_as_uint(ovs[j])) same = false;
-            same = __syncthreads_and(same) != 0;
-            const bool rec = (c != 0) ? !same : (dd != 0);
-            uint32_t slot = 0;
-            if (rec) {
-                if (tid == 0) sc[1] = atomicAdd(&g.misc[M_PV], 1u);
-                __syncthreads();
-                slot = sc[1];
-                __syncthreads();
-                if (slot >= g.pvcap) { if (tid == 0) set_status(d.status, ST_PATH); continue; }
-                float* dst = g.pv_val + (size_t)slot * Cpad;
-                for (uint32_t j = tid; j < Cpad; j += nthr) dst[j] = nvs[j];
-            }
-            if (tid == 0) {
-                if (rec) {
-                    g.pv_rec[slot] = make_uint4(i, 0u, 0u, slot | (c == 0 ? 0x80000000u : 0u));
-                    g.rec_entry[slot] = 0xFFFFFFFFu;
-                    g.pv_end[slot] = nk;
-                }
-                g.pv_cnt[i] = rec ? 1u : 0u;
-                g.nins[i] = (rec && c == 0) ? 1u : 0u;
-                g.stop[i] = -2;                 // evaluated in one pass, no walk
-                g.plen[i] = 0;
-                d.fit[i] = fitness_of(d, [&](uint32_t j) { return nvs[j]; });
-            }
-            __syncthreads();                 // nvs and the shared words are reused by the next child
-            continue;
-        }
 
         // ---- level 0: donated subtree vs removed subtree
         int32_t ef = -1, em = -1;
@@ -1245,11 +1194,14 @@ __global__ void __launch_bounds__(256, 2) k_walk(DevPop d, GenBufs g, CacheView 
                 else {
                     if (virt) eval_run<K, V>(d.arena + (size_t)g.pbuf[f] * d.cap, dd, dd + s, stA, ic, v, d.status);
                     else eval_run<K, V>(ok_, c, c + s, stA, ic, v, d.status);
-                    st_interp += s;
+                    if (cb == 0) st_interp += s;
                 }
             } else {
                 if (em >= 0) load_vec<K>(par.slots, Cpad, par.e_slot[em], v, cb);
-                else { eval_run<K, V>(g.stash + g.stash_off[i], 0, r, stA, ic, v, d.status); st_interp += r; }
+                else {
+                    eval_run<K, V>(g.stash + g.stash_off[i], 0, r, stA, ic, v, d.status);
+                    if (cb == 0) st_interp += r;
+                }
             }
             store_blk<K>(which == 0 ? nvs : ovs, cb, v);
         }
@@ -1379,7 +1331,7 @@ __global__ void __launch_bounds__(256, 2) k_walk(DevPop d, GenBufs g, CacheView 
                                 load_cases<K>(d, cb, ic.xv);
                                 const uint32_t sh = (D.flags & LD_LEFT) ? (uint32_t)tdl : 0u;
                                 eval_run<K, V>(ok_, D.ss - sh, D.se - sh, stA, ic, v, d.status);
-                                st_interp += D.se - D.ss;
+                                if (cb == 0) st_interp += D.se - D.ss;
                             }
                             store_blk<K>(svs + slot * Cpad, cb, v);
                         }
@@ -1507,7 +1459,7 @@ __global__ void __launch_bounds__(256, 2) k_walk(DevPop d, GenBufs g, CacheView 
                         load_cases<K>(d, cb, ic.xv);
                         const uint32_t sh = (D.flags & LD_LEFT) ? (uint32_t)tdl : 0u;
                         eval_run<K, V>(ok_, D.ss - sh, D.se - sh, stA, ic, v, d.status);
-                        st_interp += D.se - D.ss;
+                        if (cb == 0) st_interp += D.se - D.ss;
                     }
                     store_blk<K>(svs + slot * Cpad, cb, v);
                 }
@@ -1549,6 +1501,292 @@ __global__ void __launch_bounds__(256, 2) k_walk(DevPop d, GenBufs g, CacheView 
         atomicAdd(&g.gstat[G_STOPPED], st_stopped);
         atomicAdd(&g.gstat[G_PATHOPS], st_pathops);
     }
+}
+
+// ---- one-pass evaluation of children of at most ONEPASS_MAX nodes.
+//
+// The walk's cost per level (finding the ancestor, its sibling, waiting for
+// the sibling's value) pays off when the tree is large and the walk stops
+// early; on a child of a few thousand nodes whose crossover point lies deep
+// (a uniform random binary tree of n nodes has paths of order sqrt(n)
+// levels) interpreting the whole child once costs less and gives the same
+// values bit for bit, since every node is evaluated from the same operands
+// in the same order (Sec. 6.2: incremental evaluation only skips work, it
+// never changes a value).  The child's cache then needs new values only at
+// the ancestors of the crossover point that the child caches (subtree of at
+// least T nodes, or the root): every other cached node keeps the value of
+// its mother's or father's entry.
+//
+// k_onepass_plan (a warp per child) finds those ancestors from the balance
+// S(q) = sum over k < q of (arity_k - 1) of the child's bytes: p < c is an
+// ancestor of c iff S never falls below S(p) on (p, c]; its subtree ends at
+// the first q > c where S reaches S(p) - 1.  It reserves one walk record per
+// cached ancestor (and one for a new root made of a small donated subtree),
+// and checks that the interpreter's stack bound holds (the deepest stack of
+// the right-to-left scan is max S + 1).  k_onepass_eval (a warp per child
+// and case block, the full-evaluation launch shape) interprets the child
+// and writes each recorded ancestor's values as the scan passes it; the
+// warp that completes a child's last case block writes its fitness.  The
+// walk skips these children.  Disruption recording walks every child.
+#define ONEPASS_MAX 4096                 // most nodes of a child evaluated in one pass (2 staging buffers)
+#define OP_BUCKETS 13                    // size buckets floor(log2(n)), n <= 4096
+#define ONEPASS_WARPS 4                  // warps per CTA of the plan kernel
+#define OP_STAGE (2 * STAGE_BYTES)       // staged bytes per warp
+
+struct OnePassSmem {
+    uint8_t stage[ONEPASS_WARPS][OP_STAGE];
+    int16_t S[ONEPASS_WARPS][ONEPASS_MAX + 8];     // balance before position q, then prefix minima after c
+    uint16_t anc[ONEPASS_WARPS][ONEPASS_MAX / 2 + 8];   // ancestors of c (function nodes), nearest first
+};
+
+// Assemble child i's bytes [0, nk) in `stage` (warp-collective): from its
+// three pieces in fitness-first order, else from its own buffer.
+__device__ __forceinline__ void stage_child(const DevPop& d, const GenBufs& g, uint32_t i, uint32_t nk, uint8_t* stage) {
+    const int lane = lane_id();
+    __syncwarp();
+    if (g.lazy) {
+        const uint32_t m = g.mother[i], c = g.cpos[i], s = g.ssz[i], dd = g.dpos[i];
+        const uint8_t* mb = d.arena + (size_t)g.pbuf[m] * d.cap;
+        const uint8_t* fb = d.arena + (size_t)g.pbuf[g.father[i]] * d.cap;
+        const int32_t tdl = (int32_t)s - (int32_t)g.rsz[i];
+        // four loads in flight per lane before the stores
+        for (uint32_t x0 = lane; x0 < nk; x0 += 128) {
+            uint8_t b[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const uint32_t x = x0 + 32 * j;
+                b[j] = x < nk ? (x < c ? mb[x] : (x < c + s ? fb[dd + (x - c)] : mb[x - tdl])) : (uint8_t)0;
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (x0 + 32 * j < nk) stage[x0 + 32 * j] = b[j];
+        }
+    } else {
+        stage_issue(stage, d.arena + (size_t)d.buf[i] * d.cap, 0, nk);
+        cp_async_commit();
+        cp_async_wait<0>();
+    }
+    __syncwarp();
+}
+
+__global__ void __launch_bounds__(ONEPASS_WARPS * 32) k_onepass_plan(DevPop d, GenBufs g, CacheView par,
+                                                                      uint32_t max_nodes) {
+    if (halted(d)) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    OnePassSmem& sm = *reinterpret_cast<OnePassSmem*>(smem_raw);
+    const int lane = lane_id(), warp = threadIdx.x >> 5;
+    uint8_t* stage = sm.stage[warp];
+    int16_t* S = sm.S[warp];
+    uint16_t* anc = sm.anc[warp];
+    const uint32_t T = d.T;
+    const uint32_t gw = blockIdx.x * ONEPASS_WARPS + warp, nwp = gridDim.x * ONEPASS_WARPS;
+    for (uint32_t i = gw; i < d.P; i += nwp) {
+        const uint32_t nk = d.size[i];
+        const bool take = !(g.flags[i] & F_CLONE) && nk <= max_nodes && nk <= ONEPASS_MAX && !g.dis && nk > 0;
+        if (!take) { if (lane == 0) g.onepass[i] = 0u; continue; }
+        stage_child(d, g, i, nk, stage);
+        const uint32_t c = g.cpos[i], s = g.ssz[i], dd = g.dpos[i], m = g.mother[i];
+        // S(q) for q in [0, nk]: lane l sums its chunk [l L, l L + L)
+        const uint32_t L = (nk + 31) / 32;
+        const uint32_t q0 = min(nk, lane * L), q1 = min(nk, q0 + L);
+        int tot = 0;
+        for (uint32_t q = q0; q < q1; ++q) tot += (stage[q] < 4) ? 1 : -1;
+        int incl = tot;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) { const int v = __shfl_up_sync(FULL, incl, o); if (lane >= o) incl += v; }
+        int run = incl - tot, mx = run;
+        for (uint32_t q = q0; q < q1; ++q) { S[q] = (int16_t)run; run += (stage[q] < 4) ? 1 : -1; mx = max(mx, run); }
+        if (lane == 31) S[nk] = (int16_t)run;            // -1 for a complete tree
+        mx = __reduce_max_sync(FULL, mx);
+        __syncwarp();
+        // the scan's deepest stack is max S + 1 entries: beyond the bound the walk takes the child
+        if ((uint32_t)mx + 2u > d.maxdepth) { if (lane == 0) g.onepass[i] = 0u; continue; }
+        // ancestors of c: p < c with min over (p, c] of S >= S(p); lane l's chunk, nearest first
+        uint32_t na = 0;
+        if (c > 0) {
+            const uint32_t e1 = min(q1, c);                 // the lane's positions p < e1
+            // minimum of S over (q0, e1] (the lane's part of every later p's range), then over the later lanes
+            int cm = 0x7FFF;
+            for (uint32_t q = q0 + 1; q <= e1 && q0 < e1; ++q) cm = min(cm, (int)S[q]);
+            int later = cm;                                   // suffix minimum over lanes > l
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) { const int v = __shfl_down_sync(FULL, later, o); if (lane + o < 32) later = min(later, v); }
+            later = __shfl_down_sync(FULL, later, 1);
+            if (lane == 31) later = 0x7FFF;
+            // count, then list nearest first (the nearest ancestors are in the highest lanes)
+            uint32_t cnt = 0;
+            int R = 0x7FFF;
+            for (int32_t p = (int32_t)e1 - 1; p >= (int32_t)q0; --p) {
+                R = min(R, (int)S[p + 1]);
+                if (min(R, later) >= (int)S[p]) ++cnt;
+            }
+            uint32_t after = cnt;                             // ancestors in lanes > l
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) { const uint32_t v = __shfl_down_sync(FULL, after, o); if (lane + o < 32) after += v; }
+            na = __shfl_sync(FULL, after, 0);
+            after -= cnt;
+            uint32_t k = after;
+            R = 0x7FFF;
+            for (int32_t p = (int32_t)e1 - 1; p >= (int32_t)q0; --p) {
+                R = min(R, (int)S[p + 1]);
+                if (min(R, later) >= (int)S[p]) anc[k++] = (uint16_t)p;
+            }
+        }
+        __syncwarp();
+        // prefix minima of S after c, in place: PM(q) = min over (c, q] of S
+        if (c + 1 <= nk) {
+            const uint32_t span = nk - c, L2 = (span + 31) / 32;
+            const uint32_t r0 = c + 1 + min(span, lane * L2), r1 = c + 1 + min(span, lane * L2 + L2);
+            int lm = 0x7FFF;
+            for (uint32_t q = r0; q < r1; ++q) lm = min(lm, (int)S[q]);
+            int pre = lm;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) { const int v = __shfl_up_sync(FULL, pre, o); if (lane >= o) pre = min(pre, v); }
+            int cur = __shfl_up_sync(FULL, pre, 1);
+            if (lane == 0) cur = 0x7FFF;
+            __syncwarp();
+            for (uint32_t q = r0; q < r1; ++q) { cur = min(cur, (int)S[q]); S[q] = (int16_t)cur; }
+        }
+        __syncwarp();
+        // per ancestor (nearest first): its end, whether the child caches it, whether the mother does
+        const uint32_t me0 = par.e_off[m], me1 = par.e_off[m + 1];
+        uint32_t ncached = 0;
+        for (uint32_t base = 0; base < na; base += 32) {
+            const uint32_t k = base + lane;
+            bool cached = false;
+            if (k < na) {
+                const uint32_t p = anc[k];
+                const int target = (int)S[p] - 1;            // S(p) is untouched (p < c)
+                // first q in (c, nk] with PM(q) <= target (PM is non-increasing; PM(nk) = -1)
+                uint32_t lo = c + 1, hi = nk;
+                while (lo < hi) { const uint32_t mid = (lo + hi) >> 1; if ((int)S[mid] <= target) hi = mid; else lo = mid + 1; }
+                cached = (p == 0) || (lo - p >= T);
+            }
+            const uint32_t bal = __ballot_sync(FULL, cached);
+            ncached += __popc(bal);
+        }
+        const bool rootrec = (c == 0) && (s < T) && (dd != 0);   // a new root made of a small donated subtree
+        const uint32_t R = ncached + (rootrec ? 1u : 0u);
+        uint32_t base = 0;
+        if (lane == 0 && R) base = atomicAdd(&g.misc[M_PV], R);
+        base = __shfl_sync(FULL, base, 0);
+        if (R && base + R > g.pvcap) {
+            if (lane == 0) { set_status(d.status, ST_PATH); g.onepass[i] = 0u; }
+            continue;
+        }
+        // the records, nearest ancestor first (positions decreasing: the walk's order)
+        uint32_t nins = 0, done = 0;
+        for (uint32_t b0 = 0; b0 < na; b0 += 32) {
+            const uint32_t k = b0 + lane;
+            bool cached = false;
+            uint32_t p = 0, e = 0;
+            if (k < na) {
+                p = anc[k];
+                const int target = (int)S[p] - 1;
+                uint32_t lo = c + 1, hi = nk;
+                while (lo < hi) { const uint32_t mid = (lo + hi) >> 1; if ((int)S[mid] <= target) hi = mid; else lo = mid + 1; }
+                e = lo;
+                cached = (p == 0) || (e - p >= T);
+            }
+            const uint32_t bal = __ballot_sync(FULL, cached);
+            if (cached) {
+                const uint32_t slot = base + done + __popc(bal & ((1u << lane) - 1u));
+                const bool ins = find_exact(par.e_pos, me0, me1, p) < 0;
+                g.pv_rec[slot] = make_uint4(i, slot - base, p, slot | (ins ? 0x80000000u : 0u));
+                g.pv_end[slot] = e;
+                g.rec_entry[slot] = 0xFFFFFFFFu;
+                nins += ins ? 1u : 0u;
+            }
+            done += __popc(bal);
+        }
+        nins = __reduce_add_sync(FULL, nins);
+        if (lane == 0) {
+            if (rootrec) {
+                const uint32_t slot = base + ncached;
+                g.pv_rec[slot] = make_uint4(i, ncached, 0u, slot | 0x80000000u);
+                g.pv_end[slot] = nk;
+                g.rec_entry[slot] = 0xFFFFFFFFu;
+                ++nins;
+            }
+            g.onepass[i] = 1u;
+            g.op_base[i] = base;
+            const uint32_t bk = 31u - __clz(nk);                  // floor(log2 nk) <= 12
+            g.op_bucket[(size_t)bk * d.P + atomicAdd(&g.op_cnt[bk], 1u)] = i;
+            g.pv_cnt[i] = R;
+            g.nins[i] = nins;
+            g.walkA[i] = -1;
+            g.stop[i] = -2;                 // evaluated in one pass, no walk
+            g.plen[i] = 0;
+        }
+    }
+}
+
+template <int K, int V>
+__global__ void __launch_bounds__(GP_WARPS * 32) k_onepass_eval(DevPop d, GenBufs g) {
+    if (halted(d)) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float* kc = reinterpret_cast<float*>(smem_raw);
+    const int lane = lane_id(), warp = threadIdx.x >> 5;
+    fill_kc(kc, d.consts);
+    fill_kb(kc + 256);
+    __syncthreads();
+    unsigned char* wbase = smem_raw + SmemLayout<K>::kc_bytes + (size_t)warp * SmemLayout<K>::warp_bytes((int)d.W);
+    Ictx<K> ic;
+    ic.s = reinterpret_cast<float*>(wbase);
+    ic.W = (int)d.W;
+    ic.maxd = (int)d.maxdepth;
+    ic.kc = kc;
+    ic.kb = kc + 256;
+    uint8_t* const stage = wbase + SmemLayout<K>::stack_bytes((int)d.W);     // both staging buffers: 4,224 bytes
+    const uint32_t gwarp = blockIdx.x * GP_WARPS + warp, nwarps = gridDim.x * GP_WARPS;
+    ic.g = d.ovf + (size_t)gwarp * (d.maxdepth - d.W) * 32 * K;
+    const uint32_t ncb = d.ncb, Cpad = d.Cpad;
+    (void)nwarps;
+    unsigned long long st_interp = 0;
+    // units (child, case block) from the largest size bucket down: the longest
+    // interpretations start first and the short ones fill in behind them
+    int bk = OP_BUCKETS - 1;
+    for (;;) {
+        uint32_t i = 0, cb = 0, got = 0;
+        if (lane == 0) {
+            while (bk >= 0) {
+                const uint32_t nu = __ldcg(&g.op_cnt[bk]) * ncb;
+                if (nu) {
+                    const uint32_t u = atomicAdd(&g.op_cnt[OP_BUCKETS + bk], 1u);
+                    if (u < nu) { i = g.op_bucket[(size_t)bk * d.P + u / ncb]; cb = u % ncb; got = 1; break; }
+                }
+                --bk;
+            }
+        }
+        if (!__shfl_sync(FULL, got, 0)) break;
+        i = __shfl_sync(FULL, i, 0);
+        cb = __shfl_sync(FULL, cb, 0);
+        const uint32_t nk = d.size[i];
+        stage_child(d, g, i, nk, stage);
+        load_cases<K>(d, cb, ic.xv);
+        Istate<K> st;
+#pragma unroll
+        for (int k = 0; k < K; ++k) st.acc[k] = 0.f;
+        st.sp = 0;
+        st.ok = true;
+        const uint32_t base = g.op_base[i], R = g.pv_cnt[i];
+        interp_staged_capture<K, V>(stage, nk, st, ic, R,
+            [&](uint32_t k) { return g.pv_rec[base + k].z; },
+            [&](uint32_t k) { store_blk<K>(g.pv_val + (size_t)(base + k) * Cpad, cb, st.acc); });
+        if (!st.ok && lane == 0) set_status(d.status, ST_STACK);
+        float* row = g.small_val + (size_t)i * Cpad;
+        store_blk<K>(row, cb, st.acc);
+        if (cb == 0) st_interp += nk;
+        // the warp that completes the child's last case block writes its fitness
+        __threadfence();
+        __syncwarp();
+        uint32_t last = 0;
+        if (lane == 0) last = (atomicAdd(&g.small_cnt[i], 1u) == ncb - 1) ? 1u : 0u;
+        if (!__shfl_sync(FULL, last, 0)) continue;
+        __threadfence();
+        if (lane == 0) d.fit[i] = fitness_of(d, [&](uint32_t j) { return __ldcg(row + j); });
+    }
+    if (lane == 0 && st_interp) atomicAdd(&g.gstat[G_INTERP], st_interp);
 }
 
 // ------------------------------------------------------------------ A9 child cache

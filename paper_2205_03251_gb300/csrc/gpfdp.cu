@@ -89,6 +89,13 @@ struct gp_pop {
     int grid_walk_max;
     uint32_t walk_nw;                 // warps per child in the incremental walk
     size_t smem_walk;
+    uint32_t onepass_nodes;           // children of at most this many nodes are evaluated in one pass
+    uint32_t walk_long_n;             // children walked by the large teams (first in the work order)
+    uint32_t walk_long_nw;            // warps per large team (16 or 8; 0 = no large teams)
+    int grid_walk_long;
+    size_t smem_walk_long;
+    cudaEvent_t wfork_ev, wjoin_ev;   // large-team walk fork / join
+    int prio_high;                    // greatest stream priority of the device (the large teams' launch)
     MlpBufs mlp;
     float mlp_lr;
     uint32_t cases_stat;              // test cases per value vector (64 for the Boolean word)
@@ -257,7 +264,13 @@ auto with_kind(const DevPop& d, F&& f) {
 template <int K, int V>
 int setup_items_kernel(gp_pop* pop) {
     size_t smem = SmemLayout<K>::total((int)pop->d.W, GP_WARPS);
+    int max_optin = 0;
+    CK(cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, pop->dev));
+    if (smem > (size_t)max_optin)
+        return fail(pop, GP_EINVAL, "stack_window %u x cases_per_lane %u needs %zu bytes of shared memory per CTA (%d)",
+                    pop->d.W, pop->d.K, smem, max_optin);
     CK(cudaFuncSetAttribute(k_eval_items<K, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    CK(cudaFuncSetAttribute(k_onepass_eval<K, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int nb = 0;
     CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_eval_items<K, V>, GP_WARPS * 32, smem));
     if (nb < 1) nb = 1;
@@ -268,32 +281,72 @@ int setup_items_kernel(gp_pop* pop) {
 
 // Team size of the incremental walk (warps per child) and its launch
 // shape.  Auto: a team of 4 -- one building and combining warp and three
-// sibling evaluators; larger teams measured slower (their evaluators take
-// the issue slots the combining warp needs), smaller ones leave long
-// children short of evaluators.
+// sibling evaluators; larger teams for every child measured slower (their
+// evaluators take the issue slots the combining warp needs), smaller ones
+// leave long children short of evaluators.  On request (long_walks) the
+// children the work order puts first (the longest predicted walks) get
+// teams of 16 warps in a second launch beside the first, so that the
+// longest walk's sibling interpretations spread over 15 evaluators; the two
+// launches use disjoint interpreter overflow stacks.  Off by default: on
+// the 500 x 1e6 population it measured slower (the ordinary teams hold the
+// shared memory the large ones need, so the longest walks start late).
 template <int K, int V>
 int setup_walk_kernel(gp_pop* pop, uint32_t team) {
     const uint32_t ovf = pop->d.ovf_warps;      // the walk shares the interpreter's per-warp overflow stacks
-    CK(cudaFuncSetAttribute(k_walk<K, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                            (int)TeamLayout<K>((int)pop->d.W, pop->d.Cpad, 8).total));
+    int max_optin = 0;
+    CK(cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, pop->dev));
+    {
+        size_t s8 = TeamLayout<K>((int)pop->d.W, pop->d.Cpad, 8).total;
+        if (s8 > (size_t)max_optin) s8 = (size_t)max_optin;
+        CK(cudaFuncSetAttribute(k_walk<K, V, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s8));
+    }
+    const size_t smem16 = TeamLayout<K>((int)pop->d.W, pop->d.Cpad, 16).total;
+    const bool can16 = smem16 <= (size_t)max_optin;
+    if (can16)
+        CK(cudaFuncSetAttribute(k_walk<K, V, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem16));
     auto shape = [&](uint32_t nw, int& grid, size_t& smem) -> int {
         smem = TeamLayout<K>((int)pop->d.W, pop->d.Cpad, nw).total;
         int nb = 0;
-        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_walk<K, V>, (int)nw * 32, smem));
+        if (nw > 8) CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_walk<K, V, 512>, (int)nw * 32, smem));
+        else CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_walk<K, V, 256>, (int)nw * 32, smem));
         if (nb < 1) nb = 1;
         grid = nb * pop->nsm;
-        if ((uint32_t)grid * nw > ovf) grid = (int)(ovf / nw);
         return GP_OK;
     };
     uint32_t nw = team;
+    if (!nw) nw = 4;
+    if (TeamLayout<K>((int)pop->d.W, pop->d.Cpad, nw).total > (size_t)max_optin)
+        return fail(pop, GP_EINVAL, "a walk team of %u warps with stack_window %u does not fit shared memory", nw, pop->d.W);
     int grid = 0;
     size_t smem = 0;
-    if (!nw) nw = 4;
     int r = shape(nw, grid, smem);
     if (r) return r;
+    // large teams for the first children of the work order
+    const uint32_t P = pop->d.P;
+    uint32_t nlong = pop->cfg.long_walks;
+    if (nlong == 0xFFFFFFFFu) nlong = 0;
+    if (nlong > P) nlong = P;
+    uint32_t nwl = can16 ? 16u : 8u;
+    if (nwl <= nw) nlong = 0;
+    int gridl = 0;
+    size_t smeml = 0;
+    if (nlong) {
+        r = shape(nwl, gridl, smeml);
+        if (r) return r;
+        if ((uint32_t)gridl > nlong) gridl = (int)nlong;
+        if ((uint64_t)gridl * nwl > ovf / 2) gridl = (int)(ovf / 2 / nwl);
+        if (gridl < 1) nlong = 0;
+    }
+    if (!nlong) { nwl = 0; gridl = 0; smeml = 0; }
+    const uint32_t ovf_left = ovf - (uint32_t)gridl * nwl;
+    if ((uint32_t)grid * nw > ovf_left) grid = (int)(ovf_left / nw);
     pop->walk_nw = nw;
     pop->grid_walk = grid;
     pop->smem_walk = smem;
+    pop->walk_long_n = nlong;
+    pop->walk_long_nw = nwl;
+    pop->grid_walk_long = gridl;
+    pop->smem_walk_long = smeml;
     return GP_OK;
 }
 
@@ -517,6 +570,8 @@ int gp_pop_create(const gp_config* cfg_in, const float* x, const float* targets,
     if (cfg.walk_team != 0 && cfg.walk_team != 1 && cfg.walk_team != 2 && cfg.walk_team != 4 && cfg.walk_team != 8)
         return fail(nullptr, GP_EINVAL, "walk_team must be 0, 1, 2, 4 or 8");
     if (cfg.lazy_children > 1) return fail(nullptr, GP_EINVAL, "lazy_children must be 0 or 1");
+    if (cfg.stack_window != 0 && cfg.stack_window != 16 && cfg.stack_window != 32 && cfg.stack_window != 64)
+        return fail(nullptr, GP_EINVAL, "stack_window must be 0, 16, 32 or 64");
     if (cfg.arena_buffers && (!cfg.lazy_children || cfg.arena_buffers <= cfg.pop_size ||
                               cfg.arena_buffers > 2 * cfg.pop_size))
         return fail(nullptr, GP_EINVAL, "arena_buffers must be 0, or in (pop_size, 2 x pop_size] with lazy_children");
@@ -549,12 +604,18 @@ int gp_pop_create(const gp_config* cfg_in, const float* x, const float* targets,
     pop->side2 = nullptr;
     pop->cfork_ev = pop->cjoin_ev = nullptr;
     pop->fork_ev = pop->join_ev = pop->pfork_ev = pop->pjoin_ev = nullptr;
+    pop->wfork_ev = pop->wjoin_ev = nullptr;
     pop->gev_made = pop->capturing = pop->graph_prof = pop->stats_graph = false;
     memset(pop->gev_n, 0, sizeof pop->gev_n);
     auto bail = [&](int code) { gp_pop_destroy(pop); return code; };
     cudaError_t ce = cudaGetDevice(&pop->dev);
     if (ce != cudaSuccess) { g_create_error = cudaGetErrorString(ce); delete pop; return GP_ECUDA; }
     cudaDeviceGetAttribute(&pop->nsm, cudaDevAttrMultiProcessorCount, pop->dev);
+    {
+        int least = 0, greatest = 0;
+        if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess) { cudaGetLastError(); greatest = 0; }
+        pop->prio_high = greatest;
+    }
     for (int i = 0; i < NPH; ++i)
         for (int j = 0; j < NREC; ++j) { cudaEventCreate(&pop->ev[i][j][0]); cudaEventCreate(&pop->ev[i][j][1]); }
     if (cudaStreamCreateWithFlags(&pop->side, cudaStreamNonBlocking) != cudaSuccess ||
@@ -564,7 +625,9 @@ int gp_pop_create(const gp_config* cfg_in, const float* x, const float* targets,
         cudaEventCreateWithFlags(&pop->fork_ev, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&pop->join_ev, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&pop->pfork_ev, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&pop->pjoin_ev, cudaEventDisableTiming) != cudaSuccess) {
+        cudaEventCreateWithFlags(&pop->pjoin_ev, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&pop->wfork_ev, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&pop->wjoin_ev, cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();
         g_create_error = "stream or event creation failed";
         return bail(GP_ECUDA);
@@ -582,7 +645,7 @@ int gp_pop_create(const gp_config* cfg_in, const float* x, const float* targets,
     d.funcset = cfg.funcset;
     d.vkind = boolean ? (uint32_t)VB : cfg.funcset == GP_INT32_ARITH ? (uint32_t)VI : (uint32_t)VF;
     d.mux_k = mux_k;
-    d.W = 16;                       // interpreter stack entries kept in shared memory
+    d.W = cfg.stack_window ? cfg.stack_window : 16u;   // interpreter stack entries kept in shared memory
     d.maxdepth = d.W + T + 2;       // subtrees below the threshold need at most T + 1 entries
     const uint64_t total_cap = (uint64_t)P * d.cap;
     // initial cache-entry capacity; grown on demand by gp_eval_full
@@ -642,9 +705,11 @@ int gp_pop_create(const gp_config* cfg_in, const float* x, const float* targets,
     DA2(sb.tile_b, sb.Ucap / SCAN_TILE + 2);
 
     // interpreter launch shape and its overflow stacks
+    if (cudaFuncSetAttribute(k_onepass_plan, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(OnePassSmem)) !=
+        cudaSuccess) { cudaGetLastError(); g_create_error = "shared memory of the one-pass plan kernel"; return bail(GP_ECUDA); }
     {
         int r = with_kind(d, [&](auto k, auto v) { return setup_items_kernel<decltype(k)::value, decltype(v)::value>(pop); });
-        if (r) return bail(r);
+        if (r) { g_create_error = pop->err; return bail(r); }
         d.ovf_warps = (uint32_t)pop->grid_items * GP_WARPS;
         DA2(d.ovf, (size_t)d.ovf_warps * (d.maxdepth - d.W) * 32 * K);
     }
@@ -684,6 +749,11 @@ int gp_pop_create(const gp_config* cfg_in, const float* x, const float* targets,
         DA2(g.nflags, P); DA2(g.sel, P); DA2(g.nfree, 1); DA2(g.pref, P);
         DA2(g.walkA, P); DA2(g.nins, P); DA2(g.mb, P); DA2(g.mcnt, P + 1);
         DA2(g.order, P); DA2(g.gstat, NGSTAT);
+        DA2(g.small_cnt, P); DA2(g.small_val, (size_t)P * d.Cpad); DA2(g.onepass, P); DA2(g.op_base, P);
+        DA2(g.op_cnt, 2 * OP_BUCKETS); DA2(g.op_bucket, (size_t)OP_BUCKETS * P);
+        pop->onepass_nodes = cfg.onepass_nodes == 0 ? (uint32_t)ONEPASS_MAX
+                             : cfg.onepass_nodes == 0xFFFFFFFFu ? 0u
+                             : (cfg.onepass_nodes < (uint32_t)ONEPASS_MAX ? cfg.onepass_nodes : (uint32_t)ONEPASS_MAX);
         std::vector<uint32_t> fb(P, 0u);
         for (uint32_t i = 0; i < nbuf - P; ++i) fb[i] = P + i;   // buffers P..nbuf-1 start free
         const uint32_t nfree_init = nbuf - P;
@@ -698,7 +768,7 @@ int gp_pop_create(const gp_config* cfg_in, const float* x, const float* targets,
         int r = with_kind(d, [&](auto k, auto v) {
             return setup_walk_kernel<decltype(k)::value, decltype(v)::value>(pop, team);
         });
-        if (r) return bail(r);
+        if (r) { g_create_error = pop->err; return bail(r); }
         pop->grid_walk_max = pop->grid_walk;
         if (cfg.walk_warps) {
             int g = (int)((cfg.walk_warps + pop->walk_nw - 1) / pop->walk_nw);
@@ -779,6 +849,8 @@ void gp_pop_destroy(gp_pop* pop) {
     if (pop->join_ev) cudaEventDestroy(pop->join_ev);
     if (pop->pfork_ev) cudaEventDestroy(pop->pfork_ev);
     if (pop->pjoin_ev) cudaEventDestroy(pop->pjoin_ev);
+    if (pop->wfork_ev) cudaEventDestroy(pop->wfork_ev);
+    if (pop->wjoin_ev) cudaEventDestroy(pop->wjoin_ev);
     cudaFree(pop->gb.dis); cudaFree(pop->gb.dis_n);
     cudaFree(pop->pool); cudaFree(pop->live); cudaFree(pop->freeslot); cudaFree(pop->ftile);
     for (void* p : pop->allocs) cudaFree(p);
@@ -1296,9 +1368,47 @@ void swap_generation(gp_pop* pop) {
     std::swap(d.fit, g.pfit);
 }
 
+// The children of at most onepass_nodes nodes (one pass each), then the walk:
+// the first walk_long_n children of the work order by the large teams on
+// the second stream, the rest by the ordinary teams beside them.
 template <int K, int V>
-void launch_walk(gp_pop* pop, const CacheView& par) {
-    k_walk<K, V><<<pop->grid_walk, pop->walk_nw * 32, pop->smem_walk, pop->stream>>>(pop->d, pop->gb, par, pop->walk_nw);
+int launch_walk(gp_pop* pop, const CacheView& par) {
+    const DevPop& d = pop->d;
+    CK(cudaMemsetAsync(pop->gb.op_cnt, 0, sizeof(uint32_t) * 2 * OP_BUCKETS, pop->stream));
+    k_onepass_plan<<<pop->nsm * 3, ONEPASS_WARPS * 32, sizeof(OnePassSmem), pop->stream>>>(d, pop->gb, par,
+                                                                                          pop->onepass_nodes);
+    if (!pop->gb.dis && pop->onepass_nodes) {
+        CK(cudaMemsetAsync(pop->gb.small_cnt, 0, sizeof(uint32_t) * d.P, pop->stream));
+        k_onepass_eval<K, V><<<pop->grid_items, GP_WARPS * 32, pop->smem_items, pop->stream>>>(d, pop->gb);
+    }
+    const uint32_t nl = pop->walk_long_n;
+    if (nl) {
+        CK(cudaEventRecord(pop->wfork_ev, pop->stream));
+        CK(cudaStreamWaitEvent(pop->side2, pop->wfork_ev, 0));
+        const WalkRange wl{0u, nl, (uint32_t)Q_WALK_LONG, 0u};
+        // the large teams are dispatched before the ordinary ones (the highest
+        // scheduling priority): they carry the longest walks
+        cudaLaunchConfig_t lc = {};
+        lc.gridDim = dim3((unsigned)pop->grid_walk_long);
+        lc.blockDim = dim3(pop->walk_long_nw * 32);
+        lc.dynamicSmemBytes = pop->smem_walk_long;
+        lc.stream = pop->side2;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributePriority;
+        at[0].val.priority = pop->prio_high;
+        lc.attrs = at;
+        lc.numAttrs = 1;
+        const GenBufs& gb = pop->gb;
+        const uint32_t nwl = pop->walk_long_nw;
+        if (nwl > 8) CK(cudaLaunchKernelEx(&lc, k_walk<K, V, 512>, d, gb, par, nwl, wl));
+        else CK(cudaLaunchKernelEx(&lc, k_walk<K, V, 256>, d, gb, par, nwl, wl));
+        CK(cudaEventRecord(pop->wjoin_ev, pop->side2));
+    }
+    const WalkRange wn{nl, d.P, (uint32_t)Q_WALK, (uint32_t)pop->grid_walk_long * pop->walk_long_nw};
+    k_walk<K, V, 256><<<pop->grid_walk, pop->walk_nw * 32, pop->smem_walk, pop->stream>>>(d, pop->gb, par,
+                                                                                         pop->walk_nw, wn);
+    if (nl) CK(cudaStreamWaitEvent(pop->stream, pop->wjoin_ev, 0));
+    return GP_OK;
 }
 
 }  // namespace
@@ -1403,7 +1513,10 @@ int gen_incremental(gp_pop* pop) {
     // the work order was computed on the second stream since the crossover
     CK(cudaStreamWaitEvent(pop->stream, pop->pjoin_ev, 0));
     phase_begin(pop, PH_WALK);
-    with_kind(d, [&](auto k, auto v) { launch_walk<decltype(k)::value, decltype(v)::value>(pop, par); return 0; });
+    {
+        int r = with_kind(d, [&](auto k, auto v) { return launch_walk<decltype(k)::value, decltype(v)::value>(pop, par); });
+        if (r) return r;
+    }
     phase_end(pop, PH_WALK);
     if (g.lazy) {
         // the next generation's plan from these children's fitness; only the
@@ -1474,7 +1587,7 @@ int gen_incremental(gp_pop* pop) {
     k_accumulate<<<1, 32, 0, pop->stream>>>(pop->cum, d.acc_ops, g.gstat, pop->cases_stat, 1);
     ++pop->cum_calls;
     CK(cudaGetLastError());
-    pop->launches += 12 + 13;
+    pop->launches += 12 + 13 + 1 + ((g.dis || !pop->onepass_nodes) ? 0u : 1u) + (pop->walk_long_n ? 1u : 0u);
     pop->have_children = false;
     g.evaluated = true;
     pop->last_kind = 1;

@@ -401,6 +401,77 @@ __device__ __forceinline__ void interp_staged_lone(const uint8_t* stage, uint32_
     if (under || st.sp != 1) st.ok = false;
 }
 
+// interp_staged over a whole staged tree [0, n) that also hands out the
+// value of chosen nodes: cap(k) is called (warp-uniformly) right after node
+// pos(k) is evaluated, when st.acc holds the value of the subtree starting
+// there; the positions pos(0) > pos(1) > ... (ncap of them) are visited in
+// that order, since the scan runs right to left.  Words of four nodes that
+// hold no chosen node take the unchecked fast path.
+template <int K, int V, typename PosF, typename CapF>
+__device__ __forceinline__ void interp_staged_capture(const uint8_t* stage, uint32_t n, Istate<K>& st,
+                                                      const Ictx<K>& c, uint32_t ncap, PosF pos, CapF cap) {
+    const int lane = lane_id();
+    uint32_t k = 0;
+    int32_t nextp = ncap ? (int32_t)pos(0) : -1;
+    auto after = [&](uint32_t p) {
+        if ((int32_t)p == nextp) {
+            cap(k);
+            ++k;
+            nextp = (k < ncap) ? (int32_t)pos(k) : -1;
+        }
+    };
+    uint32_t p = n;
+    while (p > 0 && (p & 3u)) {
+        --p;
+        step_checked<K, V>(stage[p], st, c, lane);
+        after(p);
+    }
+    const uint32_t wa = (uint32_t)__cvta_generic_to_shared(stage);
+    const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(c.s) + lane * K * 4;
+    const uint32_t kca = (uint32_t)__cvta_generic_to_shared(c.kc);
+    const uint32_t kba = (V == VB) ? (uint32_t)__cvta_generic_to_shared(c.kb) : 0u;
+    const int wfast = c.W - 4;
+    const uint32_t sfast = sbase + (uint32_t)wfast * 32 * K * 4;
+    bool under = false;
+    while (p >= 4) {
+        if (nextp >= (int32_t)p - 4) {
+            // a chosen node in this word: node by node
+            const uint32_t w = lds_u32(wa + p - 4);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                --p;
+                step_checked<K, V>((w >> (24 - 8 * i)) & 0xFFu, st, c, lane);
+                after(p);
+            }
+        } else if (st.sp >= 0 && st.sp <= wfast) {
+            uint32_t sa = sbase + (uint32_t)st.sp * 32 * K * 4;
+            do {
+                const uint32_t w = lds_u32(wa + p - 4);
+                step_fast<K, V>(w >> 24, st.acc, sa, kca, kba, c);
+                step_fast<K, V>((w >> 16) & 0xFFu, st.acc, sa, kca, kba, c);
+                step_fast<K, V>((w >> 8) & 0xFFu, st.acc, sa, kca, kba, c);
+                step_fast<K, V>(w & 0xFFu, st.acc, sa, kca, kba, c);
+                under |= ((int32_t)(sa - sbase) < 0);
+                p -= 4;
+            } while (p >= 4 && nextp < (int32_t)p - 4 && (int32_t)(sa - sfast) <= 0 && (int32_t)(sa - sbase) >= 0);
+            st.sp = (int32_t)(sa - sbase) / (32 * K * 4);
+        } else {
+            const uint32_t w = lds_u32(wa + p - 4);
+            step_checked<K, V>(w >> 24, st, c, lane);
+            step_checked<K, V>((w >> 16) & 0xFFu, st, c, lane);
+            step_checked<K, V>((w >> 8) & 0xFFu, st, c, lane);
+            step_checked<K, V>(w & 0xFFu, st, c, lane);
+            p -= 4;
+        }
+    }
+    while (p > 0) {
+        --p;
+        step_checked<K, V>(stage[p], st, c, lane);
+        after(p);
+    }
+    if (under || st.sp != 1) st.ok = false;
+}
+
 // ---- staging with cp.async (16 bytes per lane per instruction) ----
 
 __device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {

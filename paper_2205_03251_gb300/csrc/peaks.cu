@@ -3,7 +3,7 @@
 // tree interpreters (one opcode on one test case is one lane operation).
 //
 // Each thread runs eight independent dependency chains of one instruction
-// kind (binary32 add, 32-bit three-input logic, 32-bit integer add), written
+// kind (binary32 add, 32-bit three-input logic), written
 // as inline PTX so that exactly one instruction of the kind is issued per
 // step, over a grid of eight 256-thread CTAs per SM; the time is taken with
 // CUDA events around one launch after a warm-up launch.
@@ -25,10 +25,8 @@ __device__ __forceinline__ uint32_t pk_step(uint32_t v, uint32_t a, uint32_t b) 
         float f;
         asm volatile("add.rn.f32 %0, %1, %2;" : "=f"(f) : "f"(__uint_as_float(v)), "f"(__uint_as_float(a)));
         r = __float_as_uint(f);
-    } else if constexpr (KIND == 1) {
-        asm volatile("lop3.b32 %0, %1, %2, %3, 0x96;" : "=r"(r) : "r"(v), "r"(a), "r"(b));   // v ^ a ^ b
     } else {
-        asm volatile("add.s32 %0, %1, %2;" : "=r"(r) : "r"(v), "r"(a));
+        asm volatile("lop3.b32 %0, %1, %2, %3, 0x96;" : "=r"(r) : "r"(v), "r"(a), "r"(b));   // v ^ a ^ b
     }
     return r;
 }
@@ -83,13 +81,12 @@ int run_peak(int nsm, uint32_t iters, double* out) {
 }  // namespace
 
 extern "C" int gp_alu_peak(int kind, double* lane_ops_per_s) {
-    if (!lane_ops_per_s || kind < 0 || kind > 2) return GP_EINVAL;
+    if (!lane_ops_per_s || kind < 0 || kind > 1) return GP_EINVAL;
     int dev = 0, nsm = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm <= 0)
         return GP_ECUDA;
     const uint32_t iters = 4096;
     if (kind == 0) return run_peak<0>(nsm, iters, lane_ops_per_s);
-    if (kind == 1) return run_peak<1>(nsm, iters, lane_ops_per_s);
-    return run_peak<2>(nsm, iters, lane_ops_per_s);
+    return run_peak<1>(nsm, iters, lane_ops_per_s);
 }

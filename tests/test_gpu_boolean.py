@@ -94,8 +94,8 @@ def test_boolean_generations(gp, T):
         for i in range(100):
             m = int(pl["mother"][i])
             kid = kops[int(koff[i]):int(koff[i + 1])]
-            if stop[i] == -2:                 # one-pass evaluation below the threshold
-                assert len(kid) < T
+            if stop[i] == -2:                 # one-pass evaluation (children of at most 4,096 nodes)
+                assert len(kid) <= 4096
                 continue
             ostop, _ = oracle.fdp_walk_bool(cur_ops[int(cur_off[m]):int(cur_off[m + 1])], kid, int(pl["c"][i]))
             assert stop[i] == ostop

@@ -37,13 +37,13 @@ def _expected_entries(tree, T):
     return pos, end, par
 
 
-def _check_population(gp, w, T, K=0, check_cache=True, max_nodes=None):
+def _check_population(gp, w, T, K=0, check_cache=True, max_nodes=None, W=0):
     import oracle
     ops, off = w["ops"], w["off"]
     sizes = np.diff(off)
     pop = gp.Population(w["x"], w["t"], w["consts"], ops, off,
                         max_nodes=int(max_nodes or sizes.max()), cache_threshold=T,
-                        cases_per_lane=K)
+                        cases_per_lane=K, stack_window=W)
     pop.eval_full()
     fit = pop.fitness()
     vals = pop.root_values()
@@ -193,3 +193,12 @@ def test_fitness_sums_in_case_order(gp, K):
         _, ofit = oracle.eval_pop_f32(ops, off, k, xv, tv)
         assert np.array_equal(oracle.canon_nan(fit), oracle.canon_nan(ofit))
         pop.close()
+
+
+@pytest.mark.parametrize("W,K", [(32, 2), (64, 1), (64, 2)])
+def test_stack_windows_on_deep_trees(gp, W, K):
+    """Uniform random binary trees (deep stacks) with 32 or 64 interpreter
+    stack entries in shared memory: the oracle's values, bit for bit."""
+    import synth
+    w = synth.workload(3, n_trees=64, target=50_000)
+    _check_population(gp, w, 1024, K=K, W=W, check_cache=False)

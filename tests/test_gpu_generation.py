@@ -37,13 +37,14 @@ def _expected_entries(tree, T):
 
 
 def run_generations(gp, w, *, T, gens, max_nodes, seed=1234, cache_check=16, stop_check=True,
-                    cases_per_lane=0, walk_team=0, lazy=False):
+                    cases_per_lane=0, walk_team=0, lazy=False, long_walks=0, onepass_nodes=0, stack_window=0):
     import oracle
     ops, off = w["ops"], w["off"]
     k, x, t = w["consts"], w["x"], w["t"]
     P = len(off) - 1
     pop = gp.Population(x, t, k, ops, off, max_nodes=max_nodes, cache_threshold=T, seed=seed,
-                        cases_per_lane=cases_per_lane, walk_team=walk_team, lazy=lazy)
+                        cases_per_lane=cases_per_lane, walk_team=walk_team, lazy=lazy, long_walks=long_walks,
+                        onepass_nodes=onepass_nodes, stack_window=stack_window)
     pop.eval_full()
     fit = pop.fitness()
     _, ofit = oracle.eval_pop_f32(ops, off, k, x, t)
@@ -78,8 +79,8 @@ def run_generations(gp, w, *, T, gens, max_nodes, seed=1234, cache_check=16, sto
                 mom = cur_ops[int(cur_off[m]):int(cur_off[m + 1])]
                 kid = kops[int(koff[i]):int(koff[i + 1])]
                 if stop[i] == -2:
-                    # below the threshold the child is evaluated in one pass, not walked
-                    assert len(kid) < T
+                    # a child of at most onepass_nodes nodes is evaluated in one pass, not walked
+                    assert len(kid) <= (4096 if onepass_nodes == 0 else onepass_nodes)
                     continue
                 ostop, depth = oracle.fdp_walk(mom, kid, int(pl["c"][i]), k, x)
                 assert stop[i] == ostop, f"gen {g}: child {i} stops at {stop[i]}, oracle {ostop}"
@@ -113,10 +114,13 @@ def run_generations(gp, w, *, T, gens, max_nodes, seed=1234, cache_check=16, sto
 
 @pytest.mark.parametrize("T", [1024, 64, 8])
 @pytest.mark.parametrize("lazy", [False, True])
-def test_generations_rhh(gp, T, lazy):
+@pytest.mark.parametrize("onepass", [0, 0xFFFFFFFF])
+def test_generations_rhh(gp, T, lazy, onepass):
+    """Ramped half-and-half trees (~700 nodes): children of at most 4,096
+    nodes interpreted in one pass (the default), or every child walked."""
     import synth
     w = synth.workload(0, n_trees=120)
-    run_generations(gp, w, T=T, gens=4, max_nodes=20000, lazy=lazy)
+    run_generations(gp, w, T=T, gens=4, max_nodes=20000, lazy=lazy, onepass_nodes=onepass)
 
 
 def test_fitness_first_matches_eager(gp):
@@ -152,7 +156,8 @@ def test_generations_small_cases_and_lanes(gp):
     import synth
     for C, K in ((1, 0), (32, 1), (33, 2), (100, 4)):
         w = synth.workload(0, n_trees=60, n_cases=C)
-        run_generations(gp, w, T=32, gens=2, max_nodes=20000, cases_per_lane=K)
+        for onepass in (0, 0xFFFFFFFF):
+            run_generations(gp, w, T=32, gens=2, max_nodes=20000, cases_per_lane=K, onepass_nodes=onepass)
 
 
 def test_generations_several_case_blocks(gp):
@@ -161,7 +166,9 @@ def test_generations_several_case_blocks(gp):
     import synth
     for C, K, lazy in ((1024, 4, False), (100, 1, True), (200, 2, False), (1024, 1, True)):
         w = synth.workload(0, n_trees=48, n_cases=C)
-        run_generations(gp, w, T=32, gens=2, max_nodes=20000, cases_per_lane=K, cache_check=8, lazy=lazy)
+        for onepass in (0, 0xFFFFFFFF):
+            run_generations(gp, w, T=32, gens=2, max_nodes=20000, cases_per_lane=K, cache_check=8, lazy=lazy,
+                            onepass_nodes=onepass)
 
 
 def test_generations_uneven_population_1024_cases(gp):
@@ -169,6 +176,19 @@ def test_generations_uneven_population_1024_cases(gp):
     import synth
     w = synth.workload(3, n_trees=64, target=20_000, n_cases=1024)
     run_generations(gp, w, T=256, gens=2, max_nodes=40_000, cache_check=6)
+
+
+@pytest.mark.parametrize("W", [16, 32, 64])
+@pytest.mark.parametrize("onepass", [0, 0xFFFFFFFF])
+def test_generations_stack_windows_on_deep_trees(gp, W, onepass):
+    """Uniform random binary trees need deep interpreter stacks (about
+    2 sqrt(n) entries): 16, 32 or 64 entries in shared memory, the rest in
+    the per-warp global area, give the oracle's children, fitness, stop
+    levels and caches, interpreted in one pass or walked."""
+    import synth
+    w = synth.workload(3, n_trees=96, target=20_000)
+    run_generations(gp, w, T=256, gens=2, max_nodes=40_000, cache_check=6, stack_window=W, onepass_nodes=onepass,
+                    lazy=True)
 
 
 @pytest.mark.parametrize("team", [1, 2, 4, 8])
@@ -179,7 +199,22 @@ def test_generations_walk_team_sizes(gp, team):
     import synth
     for C, K in ((48, 2), (200, 1)):
         w = synth.workload(0, n_trees=40, n_cases=C)
-        run_generations(gp, w, T=16, gens=2, max_nodes=20000, cases_per_lane=K, walk_team=team, cache_check=6)
+        run_generations(gp, w, T=16, gens=2, max_nodes=20000, cases_per_lane=K, walk_team=team, cache_check=6,
+                        onepass_nodes=0xFFFFFFFF)
+
+
+@pytest.mark.parametrize("long_walks", [1, 7, 40, 0xFFFFFFFF])
+@pytest.mark.parametrize("team", [1, 4])
+def test_generations_large_teams_for_the_first_children(gp, long_walks, team):
+    """The first children of the work order walked by 16-warp teams in a
+    second launch beside the ordinary teams (some, all or none of them):
+    the oracle's children, fitness and stop levels, with one and several
+    case blocks per vector, eager and fitness-first order."""
+    import synth
+    for C, K, lazy in ((48, 2, False), (200, 1, True)):
+        w = synth.workload(0, n_trees=40, n_cases=C)
+        run_generations(gp, w, T=16, gens=2, max_nodes=20000, cases_per_lane=K, walk_team=team, cache_check=6,
+                        lazy=lazy, long_walks=long_walks, onepass_nodes=0xFFFFFFFF)
 
 
 def test_walk_team_is_validated(gp):
