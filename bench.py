@@ -87,6 +87,8 @@ def parse():
     ap.add_argument("--threshold", type=int, default=1024)
     ap.add_argument("--cases-per-lane", type=int, default=0, choices=[0, 1, 2, 4], help="0: automatic")
     ap.add_argument("--walk-team", type=int, default=0, choices=[0, 1, 2, 4, 8], help="warps per child; 0: automatic")
+    ap.add_argument("--lazy-inplace", action="store_true",
+                    help="fitness-first order, memory-lean: a mother's last selected child is built in place")
     ap.add_argument("--stack-window", type=int, default=0, choices=[0, 16, 32, 64],
                     help="interpreter stack entries per warp in shared memory; 0: 16 (uneven: autotuned)")
     ap.add_argument("--long-walks", type=int, default=0,
@@ -561,7 +563,7 @@ def main():
               "cache_budget_bytes": args.cache_budget_gb << 30, "lazy": args.lazy,
               "cases_per_lane": args.cases_per_lane, "walk_team": args.walk_team,
               "arena_buffers": args.arena_buffers, "long_walks": args.long_walks,
-              "stack_window": args.stack_window}
+              "stack_window": args.stack_window, "lazy_inplace": args.lazy_inplace}
     tune = None
     if args.workload == "uneven" and args.autotune:
         ks = ((1,) if (boolean and kind_kw["mux_k"] == 2) else (1, 2) if (boolean or integer or args.cases <= 64)
@@ -672,6 +674,8 @@ def main():
         line["config"]["long_walks"] = args.long_walks
     if args.stack_window:
         line["config"]["stack_window"] = args.stack_window
+    if args.lazy_inplace:
+        line["config"]["lazy_inplace"] = True
     if args.arena_buffers:
         line["config"]["arena_buffers"] = args.arena_buffers
     if tune:

@@ -94,7 +94,7 @@ typedef struct {
     uint32_t lazy_children;     /* 1 = fitness-first order (Sec. 6.3): the walk reads each child
                                    through its parents, the next generation's plan is drawn
                                    right after it, and only the children selected as parents
-                                   get a tree buffer and a cache (no in-place construction);
+                                   get a tree buffer and a cache (in place with lazy_inplace);
                                    results are identical.  0 = build every child at crossover */
     uint32_t arena_buffers;     /* tree buffers of max_nodes bytes: 0 = 2 x pop_size.  Fitness-first
                                    order only, from pop_size + 1 up: a generation holds the buffers
@@ -116,6 +116,14 @@ typedef struct {
                                    entries) want more; each entry costs 128 x cases_per_lane bytes per
                                    warp of shared memory.  GP_EINVAL when the kernels' shared memory
                                    does not fit */
+    uint32_t lazy_inplace;      /* fitness-first order only: 1 = memory-lean (Sec. 5, Fig. 2): the last
+                                   child that the next tournaments select of each mother takes her
+                                   buffer and is built there in place, whatever its size change, at the
+                                   start of the next gp_crossover (until then it is read through its
+                                   parents, as the children that are not built are); the other selected
+                                   children are copied.  A generation then needs about P + (selected
+                                   children - their distinct mothers) buffers.  0 = copy every selected
+                                   child (beside the cache update, off the critical path) */
 } gp_config;
 
 /* Per-call statistics of the last evaluation (host copy). */

@@ -36,7 +36,7 @@ class GpConfig(ctypes.Structure):
                 ("walk_warps", ctypes.c_uint32), ("mlp_lr_micro", ctypes.c_uint32),
                 ("walk_team", ctypes.c_uint32), ("lazy_children", ctypes.c_uint32), ("arena_buffers", ctypes.c_uint32),
                 ("long_walks", ctypes.c_uint32), ("onepass_nodes", ctypes.c_uint32),
-                ("stack_window", ctypes.c_uint32)]
+                ("stack_window", ctypes.c_uint32), ("lazy_inplace", ctypes.c_uint32)]
 
 
 class GpStats(ctypes.Structure):
@@ -495,7 +495,7 @@ class Population:
                  cases_per_lane: int = 0, cache_budget_bytes: int = 0, seed: int = 0, stream=None,
                  walk_warps: int = 0, mlp_lr_micro: int = 0, walk_team: int = 0, lazy: bool = False,
                  mux_k: int = 2, integer: bool = False, arena_buffers: int = 0, long_walks: int = 0,
-                 onepass_nodes: int = 0, stack_window: int = 0):
+                 onepass_nodes: int = 0, stack_window: int = 0, lazy_inplace: bool = False):
         """boolean: the k-multiplexer (mux_k = 2: 6-mux, 64 cases; 3: 11-mux,
         2,048 cases); integer: the integer set (x, t, consts are int32)."""
         off = np.asarray(off, np.uint64)
@@ -518,7 +518,7 @@ class Population:
                        seed=seed & (2**64 - 1), walk_warps=walk_warps, mlp_lr_micro=mlp_lr_micro,
                        walk_team=walk_team, lazy_children=1 if lazy else 0, arena_buffers=arena_buffers,
                        long_walks=long_walks & 0xFFFFFFFF, onepass_nodes=onepass_nodes & 0xFFFFFFFF,
-                       stack_window=stack_window)
+                       stack_window=stack_window, lazy_inplace=1 if lazy_inplace else 0)
         if boolean:
             x = np.zeros(1, np.float32)
             t = np.zeros(1, np.float32)

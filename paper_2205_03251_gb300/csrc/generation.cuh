@@ -6,8 +6,8 @@
 #include "structure.cuh"
 #include "mlp.cuh"
 
-#define HALO_MAX 64            // largest |size change| moved in place (halo bytes per block)
 #define SHIFT_BS 16384         // bytes of tail per block of the in-place move
+#define EAGER_HALO_MAX 1024    // eager order: largest |size change| built in place (else copied)
 #define COPY_CH 32768          // bytes of a copied child per work unit
 #define PV_PER_CHILD 256       // walk records (new path values) reserved per child on average
 #define WALK_MAXLVL 520        // small-ancestor levels held in shared memory (T <= 1024)
@@ -51,8 +51,12 @@ struct GenBufs {
     uint8_t* stash;
     uint64_t stash_cap;
     uint32_t* shift_off;             // [P+1] in-place move blocks per child (prefix)
+    uint64_t* halo_off;              // [P+1] halo bytes per in-place child (prefix; min(|delta|, SHIFT_BS) per block)
+    uint64_t halo_cap;               // bytes of the halo pool
+    int32_t* lastsel;                // [P] highest index of a child selected as a parent, per mother (-1: none)
+    uint32_t* npend;                 // [1] children built in place at the next crossover (fitness-first order)
     uint32_t* copy_off;              // [P+1] COPY_CH-byte chunks of the copied children (prefix)
-    uint8_t* halo;                   // [blocks * HALO_MAX]
+    uint8_t* halo;                   // [halo_cap] bytes of in-place move blocks that other blocks overwrite
     uint32_t shift_cap;
     int32_t* stop;                   // [P] FDP stop level, -1 if the root differs
     uint32_t* plen;                  // [P] levels evaluated above the crossover point
@@ -72,6 +76,8 @@ struct GenBufs {
     uint32_t* small_cnt;             // [P] case blocks of a one-pass child evaluated so far
     float* small_val;                // [P][Cpad] root values of the one-pass children
     uint32_t* onepass;               // [P] 1: the child is evaluated in one pass (k_onepass_*), not walked
+    uint32_t onepass_max;            // children of at most this many nodes are evaluated in one pass (0: none)
+    float* ovf_op;                   // interpreter overflow stacks of the one-pass warps (ONEPASS_DEPTH deep)
     uint32_t* op_base;               // [P] first walk record of a one-pass child
     uint32_t* op_cnt;                // [OP_BUCKETS] one-pass children per size bucket, then [OP_BUCKETS] units taken
     uint32_t* op_bucket;             // [OP_BUCKETS][P] one-pass children by size bucket (log2 of the size)
@@ -86,6 +92,7 @@ struct GenBufs {
     // after the walk, and only the children it selects as parents get a tree
     // buffer and a cache
     uint32_t lazy;                   // 1: the walk reads children through their mother and father
+    uint32_t lazy_inplace;           // 1 (with lazy): a mother's last selected child takes her buffer
     uint32_t *nmother, *nfather, *ncpos, *nrsz, *ndpos, *nssz, *nflags;   // [P] next generation's plan
     uint32_t* sel;                   // [P] 1 for a child that is a parent of the next generation
     uint32_t* nfree;                 // [1] entries of the free-buffer stack (lazy mode: up to 2P)
@@ -349,31 +356,56 @@ __device__ __forceinline__ uint64_t block_excl_scan(uint64_t v, uint64_t* ws, ui
     return res;
 }
 
+// Halo bytes reserved per block of an in-place move with size change delta:
+// at most min(|delta|, SHIFT_BS) bytes of a block's source are overwritten
+// by the other blocks' destinations.
+__host__ __device__ __forceinline__ uint32_t halo_stride(int32_t delta) {
+    const uint32_t a = (uint32_t)(delta < 0 ? -delta : delta);
+    return a < (uint32_t)SHIFT_BS ? a : (uint32_t)SHIFT_BS;
+}
+
 // Buffer assignment and offsets (one CTA of 1024 threads).  The last child
-// of a mother is built in place in her buffer when its size change is at
-// most HALO_MAX (Fig. 2), every other child is copied into a free buffer
-// (Fig. 1).  Buffers of parents without an in-place child are freed.
+// of a mother is built in place in her buffer (Fig. 2) when its size change
+// is at most EAGER_HALO_MAX bytes (and the halo pool has room); every other
+// child is copied into a free buffer (Fig. 1), which the eager order always
+// has.  A larger size change would route most of the tail through the halo
+// (about min(|delta|, SHIFT_BS) of every SHIFT_BS bytes), costing more than
+// the copy.  Buffers of parents without an in-place child are freed.
 __global__ void __launch_bounds__(1024) k_assign(DevPop d, GenBufs g) {
     if (halted(d)) return;
     __shared__ uint64_t ws[32];
-    __shared__ uint64_t carry[6];
-    if (threadIdx.x < 6) carry[threadIdx.x] = 0;
+    __shared__ uint64_t carry[7];
+    if (threadIdx.x < 7) carry[threadIdx.x] = 0;
     for (uint32_t j = threadIdx.x; j < d.P; j += blockDim.x) g.hasip[j] = 0;
     __syncthreads();
     const uint32_t P = d.P;
     for (uint32_t base = 0; base < P; base += blockDim.x) {
         const uint32_t i = base + threadIdx.x;
         uint32_t copy = 0, nblk = 0, nch = 0;
-        uint64_t fragb = 0, stashb = 0, xob = 0;
+        uint64_t fragb = 0, stashb = 0, xob = 0, hb = 0;
+        bool last = false, clone = false;
+        uint32_t m = 0, fl = 0, r = 0, s = 0, c = 0, sm = 0;
+        int64_t delta = 0;
+        uint64_t tail = 0;
         if (i < P) {
-            const uint32_t m = g.mother[i];
-            uint32_t fl = g.flags[i];
-            const bool last = g.lastidx[m] == (int32_t)i;
-            const bool clone = fl & F_CLONE;
-            const uint32_t r = g.rsz[i], s = g.ssz[i], c = g.cpos[i];
-            const uint32_t sm = g.psize[m];
-            const int64_t delta = (int64_t)s - (int64_t)r;
-            const bool inplace = last && (clone || (delta >= -HALO_MAX && delta <= HALO_MAX));
+            m = g.mother[i];
+            fl = g.flags[i];
+            last = g.lastidx[m] == (int32_t)i;
+            clone = (fl & F_CLONE) != 0;
+            r = g.rsz[i]; s = g.ssz[i]; c = g.cpos[i];
+            sm = g.psize[m];
+            delta = (int64_t)s - (int64_t)r;
+            tail = (uint64_t)sm - c - r;
+            if (last && !clone && delta != 0 && tail > 0 && delta >= -EAGER_HALO_MAX && delta <= EAGER_HALO_MAX) {
+                nblk = (uint32_t)((tail + SHIFT_BS - 1) / SHIFT_BS);
+                hb = (uint64_t)nblk * halo_stride((int32_t)delta);
+            }
+        }
+        const uint64_t ho = block_excl_scan(hb, ws, &carry[6]);
+        if (i < P) {
+            const bool inplace = last && (clone || (delta >= -EAGER_HALO_MAX && delta <= EAGER_HALO_MAX &&
+                                                    ho + hb <= g.halo_cap));
+            if (!inplace) nblk = 0;
             if (last) fl |= F_LAST;
             if (inplace) { fl |= F_INPLACE; g.hasip[m] = 1; }
             g.flags[i] = fl;
@@ -383,13 +415,14 @@ __global__ void __launch_bounds__(1024) k_assign(DevPop d, GenBufs g) {
             if (!clone) {
                 fragb = (s + 15u) & ~15u;
                 if (r < d.T) stashb = (r + 15u) & ~15u;
-                const uint64_t tail = (uint64_t)sm - c - r;
-                if (inplace && delta != 0 && tail > 0) nblk = (uint32_t)((tail + SHIFT_BS - 1) / SHIFT_BS);
                 xob = 2ull * s + (r < d.T ? 2ull * r : 0) +
                       (inplace ? (delta != 0 ? 2ull * tail : 0) + s : 2ull * ((uint64_t)sm - r + s));
             } else if (!inplace) {
                 xob = 2ull * sm;
             }
+            g.halo_off[i] = ho;
+            const uint32_t nk = (uint32_t)((int64_t)sm + delta);
+            g.onepass[i] = (!clone && nk <= g.onepass_max && !g.dis) ? 1u : 0u;
         }
         const uint64_t rank = block_excl_scan(copy, ws, &carry[0]);
         const uint64_t fo = block_excl_scan(fragb, ws, &carry[1]);
@@ -399,7 +432,6 @@ __global__ void __launch_bounds__(1024) k_assign(DevPop d, GenBufs g) {
         const uint64_t co = block_excl_scan(nch, ws, &carry[5]);
         (void)xo;
         if (i < P) {
-            const uint32_t m = g.mother[i];
             d.buf[i] = copy ? g.free_buf[rank] : g.pbuf[m];
             g.frag_off[i] = fo;
             g.stash_off[i] = so;
@@ -413,6 +445,7 @@ __global__ void __launch_bounds__(1024) k_assign(DevPop d, GenBufs g) {
         g.stash_off[P] = carry[2];
         g.shift_off[P] = (uint32_t)carry[3];
         g.copy_off[P] = (uint32_t)carry[5];
+        g.halo_off[P] = carry[6];
         g.misc[M_NCOPY] = (uint32_t)carry[0];
         g.misc[M_NSHIFT] = (uint32_t)carry[3];
         g.gstat[G_XOBYTES] = carry[4];
@@ -453,6 +486,7 @@ __global__ void __launch_bounds__(1024) k_assign_lazy(DevPop d, GenBufs g) {
             const uint32_t r = g.rsz[i], s = g.ssz[i];
             d.size[i] = (uint32_t)((int64_t)g.psize[m] + (int64_t)s - (int64_t)r);
             d.buf[i] = BUF_NONE;
+            g.onepass[i] = (!clone && d.size[i] <= g.onepass_max && !g.dis) ? 1u : 0u;
             if (!clone) {
                 fragb = (s + 15u) & ~15u;
                 if (r < d.T) stashb = (r + 15u) & ~15u;
@@ -482,22 +516,34 @@ __global__ void __launch_bounds__(1024) k_assign_lazy(DevPop d, GenBufs g) {
 }
 
 // Fitness-first order, after the walk: the children selected as parents
-// take buffers from the free stack and get copy chunks; the previous
-// parents' buffers return to the stack (they are read by the copies, and
-// by gp_get_tree of unselected children, until the next materialisation).
+// get their buffers.  In the memory-lean form (lazy_inplace) the last
+// selected child of each mother takes her buffer and is built there in
+// place at the start of the next crossover
+// (Fig. 2: no sibling reads the mother after this generation's copies, and
+// the children that are not built are readable through their parents only
+// until then), while the halo pool of the move has room; a cloned child
+// needs no move at all.  The other selected children take buffers from the
+// free stack and get copy chunks; the previous parents' buffers not taken
+// in place return to the stack (they are read by the copies, and by
+// gp_get_tree of unselected children, until the next materialisation).
 __global__ void __launch_bounds__(1024) k_materialise_assign(DevPop d, GenBufs g) {
     if (halted(d)) return;
     __shared__ uint64_t ws[32];
-    __shared__ uint64_t carry[4];
+    __shared__ uint64_t carry[7];
     __shared__ uint32_t nfree0;
-    if (threadIdx.x < 4) carry[threadIdx.x] = 0;
+    if (threadIdx.x < 7) carry[threadIdx.x] = 0;
     if (threadIdx.x == 0) nfree0 = *g.nfree;
     const uint32_t P = d.P;
     // parents that a child of this generation reads (its mother's tree, or
-    // its father's, for the trees of the children that are not built)
-    for (uint32_t j = threadIdx.x; j < P; j += blockDim.x) g.pref[j] = 0u;
+    // its father's, for the trees of the children that are not built), and
+    // each mother's last selected child
+    for (uint32_t j = threadIdx.x; j < P; j += blockDim.x) { g.pref[j] = 0u; g.lastsel[j] = -1; g.hasip[j] = 0u; }
     __syncthreads();
-    for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) { g.pref[g.mother[i]] = 1u; g.pref[g.father[i]] = 1u; }
+    for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) {
+        g.pref[g.mother[i]] = 1u;
+        g.pref[g.father[i]] = 1u;
+        if (g.sel[i]) atomicMax(&g.lastsel[g.mother[i]], (int32_t)i);
+    }
     __syncthreads();
     // parents no child reads give their buffers back first (the initial
     // population's unselected trees); the selected children then take the
@@ -509,9 +555,41 @@ __global__ void __launch_bounds__(1024) k_materialise_assign(DevPop d, GenBufs g
         const uint64_t pos = block_excl_scan(dead, ws, &carry[3]);
         if (dead) g.free_buf[nfree0 + pos] = b;
     }
+    // which selected children are built in place (halo pool permitting)
     for (uint32_t base = 0; base < P; base += blockDim.x) {
         const uint32_t i = base + threadIdx.x;
-        const uint32_t selc = (i < P && g.sel[i]) ? 1u : 0u;
+        bool ip = false, clone = false;
+        uint64_t hb = 0;
+        uint32_t nblk = 0;
+        if (i < P && g.sel[i]) {
+            const uint32_t m = g.mother[i];
+            ip = g.lazy_inplace && g.lastsel[m] == (int32_t)i && g.pbuf[m] != BUF_NONE;
+            clone = (g.flags[i] & F_CLONE) != 0;
+            if (ip && !clone) {
+                const int32_t delta = (int32_t)g.ssz[i] - (int32_t)g.rsz[i];
+                const uint32_t tail = (uint32_t)((int64_t)d.size[i] - delta) - g.cpos[i] - g.rsz[i];
+                if (delta != 0 && tail > 0) {
+                    nblk = (tail + SHIFT_BS - 1) / SHIFT_BS;
+                    hb = (uint64_t)nblk * halo_stride(delta);
+                }
+            }
+        }
+        const uint64_t ho = block_excl_scan(hb, ws, &carry[5]);
+        if (i < P) {
+            if (ip && !clone && ho + hb > g.halo_cap) { ip = false; nblk = 0; }
+            uint32_t fl = g.flags[i] & ~F_INPLACE;
+            if (ip) { fl |= F_INPLACE; g.hasip[g.mother[i]] = 1u; }
+            g.flags[i] = fl;
+            g.halo_off[i] = ho;
+        }
+        const uint64_t bo = block_excl_scan(nblk, ws, &carry[6]);
+        if (i < P) g.shift_off[i] = (uint32_t)bo;
+    }
+    __syncthreads();
+    // the children selected and not built in place need buffers
+    for (uint32_t base = 0; base < P; base += blockDim.x) {
+        const uint32_t i = base + threadIdx.x;
+        const uint32_t selc = (i < P && g.sel[i] && !(g.flags[i] & F_INPLACE)) ? 1u : 0u;
         block_excl_scan(selc, ws, &carry[2]);
     }
     const uint32_t nsel = (uint32_t)carry[2];
@@ -521,42 +599,55 @@ __global__ void __launch_bounds__(1024) k_materialise_assign(DevPop d, GenBufs g
         return;
     }
     const uint32_t take0 = nfree1 - nsel;
+    __shared__ uint32_t npend;
+    if (threadIdx.x == 0) npend = 0;
+    __syncthreads();
     for (uint32_t base = 0; base < P; base += blockDim.x) {
         const uint32_t i = base + threadIdx.x;
         uint32_t selc = 0, nch = 0;
         uint64_t xob = 0;
-        if (i < P && g.sel[i]) {
+        const bool ip = i < P && (g.flags[i] & F_INPLACE);
+        if (i < P && g.sel[i] && !ip) {
             selc = 1;
             const uint32_t nk = d.size[i];
             nch = (nk + COPY_CH - 1) / COPY_CH;
             xob = 2ull * nk;
+        } else if (ip && !(g.flags[i] & F_CLONE)) {
+            const int32_t delta = (int32_t)g.ssz[i] - (int32_t)g.rsz[i];
+            const uint64_t tail = (uint64_t)((int64_t)d.size[i] - delta) - g.cpos[i] - g.rsz[i];
+            xob = (delta != 0 ? 2ull * tail : 0ull) + g.ssz[i];
+            atomicAdd(&npend, 1u);
         }
         const uint64_t rank = block_excl_scan(selc, ws, &carry[0]);
         const uint64_t co = block_excl_scan(nch, ws, &carry[1]);
         if (i < P) {
-            d.buf[i] = selc ? g.free_buf[take0 + rank] : BUF_NONE;
+            d.buf[i] = selc ? g.free_buf[take0 + rank] : ip ? g.pbuf[g.mother[i]] : BUF_NONE;
             g.copy_off[i] = (uint32_t)co;
-            if (selc) atomicAdd(&g.gstat[G_XOBYTES], xob);
+            if (xob) atomicAdd(&g.gstat[G_XOBYTES], xob);
         }
     }
     __syncthreads();
-    // the parents that children read go back on the stack after the targets:
-    // they are overwritten no earlier than the next generation's copies
+    // the parents that children read go back on the stack after the targets
+    // (unless a child took the buffer in place): they are overwritten no
+    // earlier than the next generation's copies
     __shared__ uint64_t cfree;
     if (threadIdx.x == 0) cfree = 0;
     __syncthreads();
     for (uint32_t base = 0; base < P; base += blockDim.x) {
         const uint32_t j = base + threadIdx.x;
         const uint32_t b = (j < P) ? g.pbuf[j] : BUF_NONE;
-        const uint32_t has = (b != BUF_NONE && g.pref[j]) ? 1u : 0u;
+        const uint32_t has = (b != BUF_NONE && g.pref[j] && !g.hasip[j]) ? 1u : 0u;
         const uint64_t pos = block_excl_scan(has, ws, &cfree);
         if (has) g.free_buf[take0 + pos] = b;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
         g.copy_off[P] = (uint32_t)carry[1];
+        g.halo_off[P] = carry[5];
+        g.shift_off[P] = (uint32_t)carry[6];
         g.misc[M_NCOPY] = nsel;
         *g.nfree = take0 + (uint32_t)cfree;
+        *g.npend = npend;
     }
 }
 
@@ -637,64 +728,99 @@ __global__ void __launch_bounds__(256) k_copy_children(DevPop d, GenBufs g) {
 }
 
 // In-place children (Fig. 2): the tail [c+r, n) of the mother moves by
-// delta = s - r within her buffer.  Blocks of SHIFT_BS source bytes move
-// concurrently; the |delta| bytes of a block that its neighbour overwrites
-// are saved first (k_save_halo) and read from there.
-__device__ __forceinline__ void shift_block_geom(const DevPop& d, const GenBufs& g, uint32_t b, uint32_t& i,
-                                                 uint32_t& j, uint32_t& nblk, uint32_t& src0, uint32_t& len,
-                                                 int32_t& delta) {
-    i = find_segment(g.shift_off, d.P, b);
-    j = b - g.shift_off[i];
-    nblk = g.shift_off[i + 1] - g.shift_off[i];
-    const uint32_t m = g.mother[i];
-    const uint32_t tail = g.psize[m] - g.cpos[i] - g.rsz[i];
-    src0 = g.cpos[i] + g.rsz[i] + j * SHIFT_BS;
-    len = min((uint32_t)SHIFT_BS, tail - j * SHIFT_BS);
-    delta = (int32_t)g.ssz[i] - (int32_t)g.rsz[i];
+// delta = s - r within her buffer, then the donated subtree is written at
+// c.  Blocks of SHIFT_BS source bytes move concurrently.  The bytes of a
+// block's source that another block's destination covers are saved first
+// (k_save_halo) and read from there: for delta > 0 they are the block's
+// bytes at or after c + s that the earlier blocks' destinations [c + s,
+// a_j + delta) reach, for delta < 0 the bytes from a_j + L_j + delta on that
+// the later blocks' destinations reach -- at most min(|delta|, SHIFT_BS)
+// bytes per block, whatever the size change.  A block's own source and
+// destination may overlap: it stages its source in shared memory first.
+//
+// Eager order builds a mother's last child at crossover (its buffer is
+// d.buf[i], the mother's size psize[mother]).  Fitness-first order defers
+// it to the start of the next crossover, after every sibling has been
+// copied from the mother and before the buffers are read again: the
+// generations have then been swapped, so the child's buffer is pbuf[i] and
+// its size psize[i] (deferred = true).
+struct InPlace {
+    uint8_t* buf;
+    uint32_t c, r, s, tail;
+    int32_t delta;
+};
+
+__device__ __forceinline__ InPlace inplace_of(const DevPop& d, const GenBufs& g, uint32_t i, bool deferred) {
+    InPlace q;
+    q.c = g.cpos[i];
+    q.r = g.rsz[i];
+    q.s = g.ssz[i];
+    q.delta = (int32_t)q.s - (int32_t)q.r;
+    uint32_t b, nm;
+    if (deferred) { b = g.pbuf[i]; nm = (uint32_t)((int64_t)g.psize[i] - q.delta); }
+    else { b = d.buf[i]; nm = g.psize[g.mother[i]]; }
+    q.buf = d.arena + (size_t)b * d.cap;
+    q.tail = nm - q.c - q.r;
+    return q;
 }
 
-// One thread per possible halo byte (HALO_MAX per block).
-__global__ void k_save_halo(DevPop d, GenBufs g) {
+// Block b of the moves: child i, its block j, source [src0, src0 + len),
+// the halo range [h0, h1) of that source and where its bytes are kept.
+struct ShiftBlock {
+    uint32_t i, j, src0, len, h0, h1;
+    InPlace q;
+    uint8_t* halo;
+};
+
+__device__ __forceinline__ ShiftBlock shift_block(const DevPop& d, const GenBufs& g, uint32_t b, bool deferred) {
+    ShiftBlock k;
+    k.i = find_segment(g.shift_off, d.P, b);
+    k.j = b - g.shift_off[k.i];
+    k.q = inplace_of(d, g, k.i, deferred);
+    k.src0 = k.q.c + k.q.r + k.j * SHIFT_BS;
+    k.len = min((uint32_t)SHIFT_BS, k.q.tail - k.j * SHIFT_BS);
+    const int64_t a = k.src0, e = (int64_t)k.src0 + k.len, dl = k.q.delta;
+    int64_t h0, h1;
+    if (dl > 0) { h0 = max(a, (int64_t)k.q.c + k.q.s); h1 = min(e, a + dl); }
+    else { h0 = max(a, e + dl); h1 = min(e, (int64_t)k.q.c + k.q.r + k.q.tail + dl); }
+    if (h1 < h0) h1 = h0;
+    k.h0 = (uint32_t)h0;
+    k.h1 = (uint32_t)h1;
+    k.halo = g.halo + g.halo_off[k.i] + (uint64_t)k.j * halo_stride(k.q.delta);
+    return k;
+}
+
+// the halo bytes of every block, before any block moves (a CTA per block)
+__global__ void k_save_halo(DevPop d, GenBufs g, int deferred) {
     if (halted(d)) return;
+    if (deferred && *g.npend == 0) return;          // nothing deferred (or a stale plan)
     const uint32_t nb = g.shift_off[d.P];
-    if (nb > g.shift_cap) return;
-    for (uint32_t u = blockIdx.x * blockDim.x + threadIdx.x; u < nb * HALO_MAX; u += gridDim.x * blockDim.x) {
-        const uint32_t b = u / HALO_MAX, t = u % HALO_MAX;
-        uint32_t i, j, nblk, src0, len;
-        int32_t delta;
-        shift_block_geom(d, g, b, i, j, nblk, src0, len, delta);
-        const uint32_t ad = (uint32_t)(delta > 0 ? delta : -delta);
-        const uint32_t k = min(ad, len);
-        if (t >= k) continue;
-        const uint8_t* buf = d.arena + (size_t)d.buf[i] * d.cap;
-        uint8_t* h = g.halo + (size_t)b * HALO_MAX;
-        if (delta > 0 && j > 0) h[t] = buf[src0 + t];
-        if (delta < 0 && j + 1 < nblk) h[t] = buf[src0 + len - k + t];
+    if (nb > g.shift_cap || g.halo_off[d.P] > g.halo_cap) return;
+    for (uint32_t b = blockIdx.x; b < nb; b += gridDim.x) {
+        const ShiftBlock k = shift_block(d, g, b, deferred != 0);
+        for (uint32_t x = k.h0 + threadIdx.x; x < k.h1; x += blockDim.x) k.halo[x - k.h0] = k.q.buf[x];
     }
 }
 
-__global__ void __launch_bounds__(512) k_shift(DevPop d, GenBufs g) {
+__global__ void __launch_bounds__(512) k_shift(DevPop d, GenBufs g, int deferred) {
     if (halted(d)) return;
+    if (deferred && *g.npend == 0) return;          // nothing deferred (or a stale plan)
     // the block's source bytes from its 16-byte-aligned start, plus slack for the shifted reads
     __shared__ __align__(16) uint8_t sb[SHIFT_BS + 48];
     const uint32_t nb = g.shift_off[d.P];
-    if (nb > g.shift_cap) return;
+    if (nb > g.shift_cap || g.halo_off[d.P] > g.halo_cap) return;
     for (uint32_t b = blockIdx.x; b < nb; b += gridDim.x) {
-        uint32_t i, j, nblk, src0, len;
-        int32_t delta;
-        shift_block_geom(d, g, b, i, j, nblk, src0, len, delta);
-        uint8_t* buf = d.arena + (size_t)d.buf[i] * d.cap;
-        const uint8_t* h = g.halo + (size_t)b * HALO_MAX;
-        const uint32_t ad = (uint32_t)(delta > 0 ? delta : -delta);
-        const uint32_t k = min(ad, len);
+        const ShiftBlock k = shift_block(d, g, b, deferred != 0);
+        uint8_t* buf = k.q.buf;
+        const uint32_t src0 = k.src0, len = k.len;
+        const int32_t delta = k.q.delta;
         const uint32_t a0 = src0 & ~15u, m0 = src0 & 15u;
-        // stage the source quads (bytes a neighbour may be writing are replaced from the halo below)
+        // stage the source quads (the halo range, which other blocks may be writing, from the halo)
         const uint32_t nq = (m0 + len + 15u) / 16u;
         for (uint32_t q = threadIdx.x; q < nq; q += blockDim.x)
             reinterpret_cast<uint4*>(sb)[q] = reinterpret_cast<const uint4*>(buf + a0)[q];
         __syncthreads();
-        if (delta > 0 && j > 0) { for (uint32_t t = threadIdx.x; t < k; t += blockDim.x) sb[m0 + t] = h[t]; }
-        if (delta < 0 && j + 1 < nblk) { for (uint32_t t = threadIdx.x; t < k; t += blockDim.x) sb[m0 + len - k + t] = h[t]; }
+        for (uint32_t x = k.h0 + threadIdx.x; x < k.h1; x += blockDim.x) sb[m0 + (x - src0)] = k.halo[x - k.h0];
         __syncthreads();
         // destination [dst0, dst0 + len): whole aligned quads in the middle, single bytes at the ends
         const uint32_t dst0 = (uint32_t)((int64_t)src0 + delta);
@@ -736,25 +862,34 @@ __global__ void __launch_bounds__(512) k_shift(DevPop d, GenBufs g) {
 // Donated subtree written into the in-place children (after the move):
 // whole aligned quads of the destination from the (shifted) fragment, single
 // bytes at the two ends.
-__global__ void k_write_frags(DevPop d, GenBufs g) {
+__global__ void k_write_frags(DevPop d, GenBufs g, int deferred) {
     if (halted(d)) return;
+    if (deferred && *g.npend == 0) return;          // nothing deferred (or a stale plan)
     if (g.frag_off[d.P] > g.frag_cap) return;
     for (uint32_t i = blockIdx.x; i < d.P; i += gridDim.x) {
         const uint32_t fl = g.flags[i];
         if (!(fl & F_INPLACE) || (fl & F_CLONE)) continue;
-        uint8_t* buf = d.arena + (size_t)d.buf[i] * d.cap;
+        const InPlace q = inplace_of(d, g, i, deferred != 0);
+        uint8_t* buf = q.buf;
         const uint8_t* fr = g.frag + g.frag_off[i];
-        const uint32_t c = g.cpos[i], s = g.ssz[i];
+        const uint32_t c = q.c, s = q.s;
         const uint32_t dq0 = (c + 15u) / 16u, dq1 = (c + s) / 16u;
         const uint32_t head_end = min(16u * dq0, c + s);
         const uint32_t tail_begin = max(16u * dq1, head_end);
         for (uint32_t x = c + threadIdx.x; x < head_end; x += blockDim.x) buf[x] = fr[x - c];
         for (uint32_t x = tail_begin + threadIdx.x; x < c + s; x += blockDim.x) buf[x] = fr[x - c];
         if (dq1 > dq0) {
-            for (uint32_t q = dq0 + threadIdx.x; q < dq1; q += blockDim.x)
-                reinterpret_cast<uint4*>(buf)[q] = load16u(fr + (16u * q - c));
+            for (uint32_t q4 = dq0 + threadIdx.x; q4 < dq1; q4 += blockDim.x)
+                reinterpret_cast<uint4*>(buf)[q4] = load16u(fr + (16u * q4 - c));
         }
     }
+}
+
+// Fitness-first order: the deferred in-place children are built; the flags
+// of this generation's plan are then cleared of F_INPLACE by the plan the
+// crossover takes next.
+__global__ void k_inplace_done(GenBufs g) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) *g.npend = 0;
 }
 
 // ------------------------------------------------------------------ A7 incremental walk
@@ -1522,14 +1657,18 @@ __global__ void __launch_bounds__(MAXT, 512 / MAXT) k_walk(DevPop d, GenBufs g, 
 // ancestor of c iff S never falls below S(p) on (p, c]; its subtree ends at
 // the first q > c where S reaches S(p) - 1.  It reserves one walk record per
 // cached ancestor (and one for a new root made of a small donated subtree),
-// and checks that the interpreter's stack bound holds (the deepest stack of
-// the right-to-left scan is max S + 1).  k_onepass_eval (a warp per child
+// (the deepest stack of the right-to-left scan is max S + 1 <= n / 2 + 1
+// entries: the one-pass warps have overflow stacks that deep of their own,
+// so they run beside the walk).  k_onepass_eval (a warp per child
 // and case block, the full-evaluation launch shape) interprets the child
 // and writes each recorded ancestor's values as the scan passes it; the
-// warp that completes a child's last case block writes its fitness.  The
-// walk skips these children.  Disruption recording walks every child.
+// warp that completes a child's last case block writes its fitness.  Which
+// children take this path is decided at crossover (size at most
+// onepass_max, not a clone); the walk skips them.  Disruption recording
+// walks every child.
 #define ONEPASS_MAX 4096                 // most nodes of a child evaluated in one pass (2 staging buffers)
 #define OP_BUCKETS 13                    // size buckets floor(log2(n)), n <= 4096
+#define ONEPASS_DEPTH (ONEPASS_MAX / 2 + 4)   // overflow stack entries per one-pass warp
 #define ONEPASS_WARPS 4                  // warps per CTA of the plan kernel
 #define OP_STAGE (2 * STAGE_BYTES)       // staged bytes per warp
 
@@ -1569,8 +1708,7 @@ __device__ __forceinline__ void stage_child(const DevPop& d, const GenBufs& g, u
     __syncwarp();
 }
 
-__global__ void __launch_bounds__(ONEPASS_WARPS * 32) k_onepass_plan(DevPop d, GenBufs g, CacheView par,
-                                                                      uint32_t max_nodes) {
+__global__ void __launch_bounds__(ONEPASS_WARPS * 32) k_onepass_plan(DevPop d, GenBufs g, CacheView par) {
     if (halted(d)) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     OnePassSmem& sm = *reinterpret_cast<OnePassSmem*>(smem_raw);
@@ -1581,9 +1719,8 @@ __global__ void __launch_bounds__(ONEPASS_WARPS * 32) k_onepass_plan(DevPop d, G
     const uint32_t T = d.T;
     const uint32_t gw = blockIdx.x * ONEPASS_WARPS + warp, nwp = gridDim.x * ONEPASS_WARPS;
     for (uint32_t i = gw; i < d.P; i += nwp) {
+        if (!g.onepass[i]) continue;                      // decided at crossover (uniform per warp)
         const uint32_t nk = d.size[i];
-        const bool take = !(g.flags[i] & F_CLONE) && nk <= max_nodes && nk <= ONEPASS_MAX && !g.dis && nk > 0;
-        if (!take) { if (lane == 0) g.onepass[i] = 0u; continue; }
         stage_child(d, g, i, nk, stage);
         const uint32_t c = g.cpos[i], s = g.ssz[i], dd = g.dpos[i], m = g.mother[i];
         // S(q) for q in [0, nk]: lane l sums its chunk [l L, l L + L)
@@ -1597,10 +1734,7 @@ __global__ void __launch_bounds__(ONEPASS_WARPS * 32) k_onepass_plan(DevPop d, G
         int run = incl - tot, mx = run;
         for (uint32_t q = q0; q < q1; ++q) { S[q] = (int16_t)run; run += (stage[q] < 4) ? 1 : -1; mx = max(mx, run); }
         if (lane == 31) S[nk] = (int16_t)run;            // -1 for a complete tree
-        mx = __reduce_max_sync(FULL, mx);
         __syncwarp();
-        // the scan's deepest stack is max S + 1 entries: beyond the bound the walk takes the child
-        if ((uint32_t)mx + 2u > d.maxdepth) { if (lane == 0) g.onepass[i] = 0u; continue; }
         // ancestors of c: p < c with min over (p, c] of S >= S(p); lane l's chunk, nearest first
         uint32_t na = 0;
         if (c > 0) {
@@ -1671,7 +1805,7 @@ __global__ void __launch_bounds__(ONEPASS_WARPS * 32) k_onepass_plan(DevPop d, G
         if (lane == 0 && R) base = atomicAdd(&g.misc[M_PV], R);
         base = __shfl_sync(FULL, base, 0);
         if (R && base + R > g.pvcap) {
-            if (lane == 0) { set_status(d.status, ST_PATH); g.onepass[i] = 0u; }
+            if (lane == 0) { set_status(d.status, ST_PATH); g.pv_cnt[i] = 0u; g.nins[i] = 0u; g.op_base[i] = 0u; }
             continue;
         }
         // the records, nearest ancestor first (positions decreasing: the walk's order)
@@ -1708,7 +1842,6 @@ __global__ void __launch_bounds__(ONEPASS_WARPS * 32) k_onepass_plan(DevPop d, G
                 g.rec_entry[slot] = 0xFFFFFFFFu;
                 ++nins;
             }
-            g.onepass[i] = 1u;
             g.op_base[i] = base;
             const uint32_t bk = 31u - __clz(nk);                  // floor(log2 nk) <= 12
             g.op_bucket[(size_t)bk * d.P + atomicAdd(&g.op_cnt[bk], 1u)] = i;
@@ -1738,10 +1871,11 @@ __global__ void __launch_bounds__(GP_WARPS * 32) k_onepass_eval(DevPop d, GenBuf
     ic.kc = kc;
     ic.kb = kc + 256;
     uint8_t* const stage = wbase + SmemLayout<K>::stack_bytes((int)d.W);     // both staging buffers: 4,224 bytes
-    const uint32_t gwarp = blockIdx.x * GP_WARPS + warp, nwarps = gridDim.x * GP_WARPS;
-    ic.g = d.ovf + (size_t)gwarp * (d.maxdepth - d.W) * 32 * K;
+    const uint32_t gwarp = blockIdx.x * GP_WARPS + warp;
+    // a child of at most ONEPASS_MAX nodes needs at most ONEPASS_MAX / 2 + 1 stack entries
+    ic.maxd = (int)d.W + ONEPASS_DEPTH;
+    ic.g = g.ovf_op + (size_t)gwarp * ONEPASS_DEPTH * 32 * K;
     const uint32_t ncb = d.ncb, Cpad = d.Cpad;
-    (void)nwarps;
     unsigned long long st_interp = 0;
     // units (child, case block) from the largest size bucket down: the longest
     // interpretations start first and the short ones fill in behind them

@@ -95,6 +95,9 @@ struct gp_pop {
     int grid_walk_long;
     size_t smem_walk_long;
     cudaEvent_t wfork_ev, wjoin_ev;   // large-team walk fork / join
+    cudaStream_t side3;               // fourth stream: the one-pass children beside the walk
+    cudaEvent_t ofork_ev, ojoin_ev;   // one-pass fork / join
+    int grid_onepass;                 // CTAs of the one-pass interpreter (each with its own overflow stacks)
     int prio_high;                    // greatest stream priority of the device (the large teams' launch)
     MlpBufs mlp;
     float mlp_lr;
@@ -114,6 +117,7 @@ struct gp_pop {
     bool have_next_plan;              // the last walk drew the next generation's plan
     uint32_t planned_gen;             // ... for this generation number
     bool lazy_pending;                // some individuals exist only through their parents
+    bool have_next_plan_at_xo;        // the last crossover took a drawn plan (and built deferred children)
     uint32_t host_nfree;              // pageable source of the free-stack count upload
     // disruption diagnostics
     bool dis_valid;                   // the last walk recorded into gb.dis
@@ -570,6 +574,8 @@ int gp_pop_create(const gp_config* cfg_in, const float* x, const float* targets,
     if (cfg.walk_team != 0 && cfg.walk_team != 1 && cfg.walk_team != 2 && cfg.walk_team != 4 && cfg.walk_team != 8)
         return fail(nullptr, GP_EINVAL, "walk_team must be 0, 1, 2, 4 or 8");
     if (cfg.lazy_children > 1) return fail(nullptr, GP_EINVAL, "lazy_children must be 0 or 1");
+    if (cfg.lazy_inplace > 1 || (cfg.lazy_inplace && !cfg.lazy_children))
+        return fail(nullptr, GP_EINVAL, "lazy_inplace must be 0, or 1 with lazy_children");
     if (cfg.stack_window != 0 && cfg.stack_window != 16 && cfg.stack_window != 32 && cfg.stack_window != 64)
         return fail(nullptr, GP_EINVAL, "stack_window must be 0, 16, 32 or 64");
     if (cfg.arena_buffers && (!cfg.lazy_children || cfg.arena_buffers <= cfg.pop_size ||
@@ -605,6 +611,8 @@ int gp_pop_create(const gp_config* cfg_in, const float* x, const float* targets,
     pop->cfork_ev = pop->cjoin_ev = nullptr;
     pop->fork_ev = pop->join_ev = pop->pfork_ev = pop->pjoin_ev = nullptr;
     pop->wfork_ev = pop->wjoin_ev = nullptr;
+    pop->side3 = nullptr;
+    pop->ofork_ev = pop->ojoin_ev = nullptr;
     pop->gev_made = pop->capturing = pop->graph_prof = pop->stats_graph = false;
     memset(pop->gev_n, 0, sizeof pop->gev_n);
     auto bail = [&](int code) { gp_pop_destroy(pop); return code; };
@@ -627,7 +635,10 @@ int gp_pop_create(const gp_config* cfg_in, const float* x, const float* targets,
         cudaEventCreateWithFlags(&pop->pfork_ev, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&pop->pjoin_ev, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&pop->wfork_ev, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&pop->wjoin_ev, cudaEventDisableTiming) != cudaSuccess) {
+        cudaEventCreateWithFlags(&pop->wjoin_ev, cudaEventDisableTiming) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&pop->side3, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&pop->ofork_ev, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&pop->ojoin_ev, cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();
         g_create_error = "stream or event creation failed";
         return bail(GP_ECUDA);
@@ -732,28 +743,40 @@ int gp_pop_create(const gp_config* cfg_in, const float* x, const float* targets,
         g.frag_cap = (uint64_t)P * d.cap;
         g.stash_cap = (uint64_t)P * (T + 16);
         g.shift_cap = (uint32_t)((uint64_t)P * d.cap / SHIFT_BS + P);
+        // halo pool of the in-place moves: an eighth of a buffer per individual
+        // (a generation whose moves need more copies the rest of its children)
+        g.halo_cap = (uint64_t)P * d.cap / 8 + 65536;
         DA2(g.pbuf, P); DA2(g.psize, P); DA2(g.pfit, P);
         DA2(g.mother, P); DA2(g.father, P); DA2(g.cpos, P); DA2(g.rsz, P); DA2(g.dpos, P); DA2(g.ssz, P);
         DA2(g.flags, P); DA2(g.lastidx, P); DA2(g.free_buf, 2 * P); DA2(g.free_next, P); DA2(g.hasip, P);
         DA2(g.misc, NMISC);
         DA2(g.frag_off, P + 1); DA2(g.frag, g.frag_cap + 64);
         DA2(g.stash_off, P + 1); DA2(g.stash, g.stash_cap + 64);
-        DA2(g.shift_off, P + 1); DA2(g.halo, (size_t)g.shift_cap * HALO_MAX);
+        DA2(g.shift_off, P + 1); DA2(g.halo, g.halo_cap + 64); DA2(g.halo_off, P + 1);
+        DA2(g.lastsel, P); DA2(g.npend, 1);
+        cudaMemset(g.npend, 0, sizeof(uint32_t));
         DA2(g.copy_off, P + 1);
         DA2(g.stop, P); DA2(g.plen, P);
         DA2(g.pv_rec, g.pvcap); DA2(g.pv_cnt, P); DA2(g.pv_off, P + 1); DA2(g.pv_sorted, g.pvcap);
         DA2(g.pv_end, g.pvcap); DA2(g.pv_val, (size_t)g.pvcap * d.Cpad);
         DA2(g.rec_entry, g.pvcap);
         g.lazy = cfg.lazy_children;
+        g.lazy_inplace = cfg.lazy_inplace;
         DA2(g.nmother, P); DA2(g.nfather, P); DA2(g.ncpos, P); DA2(g.nrsz, P); DA2(g.ndpos, P); DA2(g.nssz, P);
         DA2(g.nflags, P); DA2(g.sel, P); DA2(g.nfree, 1); DA2(g.pref, P);
         DA2(g.walkA, P); DA2(g.nins, P); DA2(g.mb, P); DA2(g.mcnt, P + 1);
         DA2(g.order, P); DA2(g.gstat, NGSTAT);
         DA2(g.small_cnt, P); DA2(g.small_val, (size_t)P * d.Cpad); DA2(g.onepass, P); DA2(g.op_base, P);
         DA2(g.op_cnt, 2 * OP_BUCKETS); DA2(g.op_bucket, (size_t)OP_BUCKETS * P);
+        cudaMemset(g.onepass, 0, sizeof(uint32_t) * P);
         pop->onepass_nodes = cfg.onepass_nodes == 0 ? (uint32_t)ONEPASS_MAX
                              : cfg.onepass_nodes == 0xFFFFFFFFu ? 0u
                              : (cfg.onepass_nodes < (uint32_t)ONEPASS_MAX ? cfg.onepass_nodes : (uint32_t)ONEPASS_MAX);
+        g.onepass_max = pop->onepass_nodes;
+        pop->grid_onepass = pop->grid_items < 2 * pop->nsm ? pop->grid_items : 2 * pop->nsm;
+        g.ovf_op = nullptr;
+        if (pop->onepass_nodes)
+            DA2(g.ovf_op, (size_t)pop->grid_onepass * GP_WARPS * ONEPASS_DEPTH * 32 * K);
         std::vector<uint32_t> fb(P, 0u);
         for (uint32_t i = 0; i < nbuf - P; ++i) fb[i] = P + i;   // buffers P..nbuf-1 start free
         const uint32_t nfree_init = nbuf - P;
@@ -843,6 +866,7 @@ void gp_pop_destroy(gp_pop* pop) {
     if (pop->cap_stream) cudaStreamDestroy(pop->cap_stream);
     if (pop->side) cudaStreamDestroy(pop->side);
     if (pop->side2) cudaStreamDestroy(pop->side2);
+    if (pop->side3) cudaStreamDestroy(pop->side3);
     if (pop->cfork_ev) cudaEventDestroy(pop->cfork_ev);
     if (pop->cjoin_ev) cudaEventDestroy(pop->cjoin_ev);
     if (pop->fork_ev) cudaEventDestroy(pop->fork_ev);
@@ -851,6 +875,8 @@ void gp_pop_destroy(gp_pop* pop) {
     if (pop->pjoin_ev) cudaEventDestroy(pop->pjoin_ev);
     if (pop->wfork_ev) cudaEventDestroy(pop->wfork_ev);
     if (pop->wjoin_ev) cudaEventDestroy(pop->wjoin_ev);
+    if (pop->ofork_ev) cudaEventDestroy(pop->ofork_ev);
+    if (pop->ojoin_ev) cudaEventDestroy(pop->ojoin_ev);
     cudaFree(pop->gb.dis); cudaFree(pop->gb.dis_n);
     cudaFree(pop->pool); cudaFree(pop->live); cudaFree(pop->freeslot); cudaFree(pop->ftile);
     for (void* p : pop->allocs) cudaFree(p);
@@ -900,6 +926,7 @@ int gp_load_trees(gp_pop* pop, const uint8_t* ops, const uint64_t* offsets) {
     CK(cudaMemsetAsync(pop->d.status, 0, sizeof(uint32_t), pop->stream));
     CK(cudaMemsetAsync(pop->d.errinfo, 0, 4 * sizeof(uint32_t), pop->stream));
     CK(cudaMemcpyAsync(pop->gb.nfree, &pop->host_nfree, sizeof(uint32_t), cudaMemcpyHostToDevice, pop->stream));
+    CK(cudaMemsetAsync(pop->gb.npend, 0, sizeof(uint32_t), pop->stream));
     pop->have_next_plan = false;
     pop->lazy_pending = false;
     pop->have_children = false;
@@ -1128,7 +1155,16 @@ int gp_get_tree(const gp_pop* cpop, uint32_t i, uint8_t* host_out, uint64_t cap,
     *size = n;
     if (!host_out) return GP_OK;
     if (cap < n) return fail(pop, GP_EINVAL, "host buffer too small for tree %u (%u nodes)", i, n);
-    if (b != BUF_NONE) {
+    // fitness-first order: a child that takes its mother's buffer is built
+    // there only at the next crossover; until then it is read like the
+    // children that are not built
+    uint32_t fl0 = 0, npend = 0;
+    if (pop->gb.lazy && pop->have_next_plan) {
+        CK(cudaMemcpy(&fl0, pop->gb.flags + i, 4, cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(&npend, pop->gb.npend, 4, cudaMemcpyDeviceToHost));
+    }
+    const bool pending = npend && (fl0 & F_INPLACE) && !(fl0 & F_CLONE);
+    if (b != BUF_NONE && !pending) {
         CK(cudaMemcpy(host_out, pop->d.arena + (size_t)b * pop->d.cap, n, cudaMemcpyDeviceToHost));
         return GP_OK;
     }
@@ -1374,12 +1410,18 @@ void swap_generation(gp_pop* pop) {
 template <int K, int V>
 int launch_walk(gp_pop* pop, const CacheView& par) {
     const DevPop& d = pop->d;
-    CK(cudaMemsetAsync(pop->gb.op_cnt, 0, sizeof(uint32_t) * 2 * OP_BUCKETS, pop->stream));
-    k_onepass_plan<<<pop->nsm * 3, ONEPASS_WARPS * 32, sizeof(OnePassSmem), pop->stream>>>(d, pop->gb, par,
-                                                                                          pop->onepass_nodes);
-    if (!pop->gb.dis && pop->onepass_nodes) {
-        CK(cudaMemsetAsync(pop->gb.small_cnt, 0, sizeof(uint32_t) * d.P, pop->stream));
-        k_onepass_eval<K, V><<<pop->grid_items, GP_WARPS * 32, pop->smem_items, pop->stream>>>(d, pop->gb);
+    // the one-pass children on a stream of their own, beside the walk (own
+    // overflow stacks; their walk records and fitness are disjoint from the walk's)
+    const bool op = !pop->gb.dis && pop->onepass_nodes;
+    if (op) {
+        cudaStream_t os = pop->side3;
+        CK(cudaEventRecord(pop->ofork_ev, pop->stream));
+        CK(cudaStreamWaitEvent(os, pop->ofork_ev, 0));
+        CK(cudaMemsetAsync(pop->gb.op_cnt, 0, sizeof(uint32_t) * 2 * OP_BUCKETS, os));
+        CK(cudaMemsetAsync(pop->gb.small_cnt, 0, sizeof(uint32_t) * d.P, os));
+        k_onepass_plan<<<pop->nsm * 3, ONEPASS_WARPS * 32, sizeof(OnePassSmem), os>>>(d, pop->gb, par);
+        k_onepass_eval<K, V><<<pop->grid_onepass, GP_WARPS * 32, pop->smem_items, os>>>(d, pop->gb);
+        CK(cudaEventRecord(pop->ojoin_ev, os));
     }
     const uint32_t nl = pop->walk_long_n;
     if (nl) {
@@ -1408,6 +1450,7 @@ int launch_walk(gp_pop* pop, const CacheView& par) {
     k_walk<K, V, 256><<<pop->grid_walk, pop->walk_nw * 32, pop->smem_walk, pop->stream>>>(d, pop->gb, par,
                                                                                          pop->walk_nw, wn);
     if (nl) CK(cudaStreamWaitEvent(pop->stream, pop->wjoin_ev, 0));
+    if (op) CK(cudaStreamWaitEvent(pop->stream, pop->ojoin_ev, 0));
     return GP_OK;
 }
 
@@ -1453,6 +1496,7 @@ int gen_crossover(gp_pop* pop, uint32_t generation) {
         return fail(pop, GP_ESTATE, "fitness-first mode drew generation %u's plan; gp_crossover(%u) must follow",
                     pop->planned_gen, generation);
     g.gen = generation;
+    pop->have_next_plan_at_xo = g.lazy && g.lazy_inplace && pop->have_next_plan;
     swap_generation(pop);
     const CacheView par = view_of(pop, pop->sets[pop->cur]);
     pop->cur ^= 1;
@@ -1462,8 +1506,16 @@ int gen_crossover(gp_pop* pop, uint32_t generation) {
     CK(cudaMemsetAsync(g.misc, 0, sizeof(uint32_t) * NMISC, pop->stream));
     CK(cudaMemsetAsync(g.gstat, 0, sizeof(unsigned long long) * NGSTAT, pop->stream));
     if (g.lazy) {
-        // fitness-first: the plan (drawn after the last walk, or now for freshly
-        // evaluated parents), fragments and stash; the children are built later
+        // fitness-first: the last generation's children built in place in their
+        // mothers' buffers (deferred until no sibling reads the mother); then the
+        // plan (drawn after the last walk, or now for freshly evaluated parents),
+        // fragments and stash; this generation's children are built later
+        if (pop->have_next_plan && g.lazy_inplace) {
+            k_save_halo<<<pop->nsm * 8, 256, 0, pop->stream>>>(d, g, 1);
+            k_shift<<<pop->nsm * 4, 512, 0, pop->stream>>>(d, g, 1);
+            k_write_frags<<<pop->nsm * 4, 256, 0, pop->stream>>>(d, g, 1);
+            k_inplace_done<<<1, 32, 0, pop->stream>>>(g);
+        }
         if (pop->have_next_plan) k_plan_take<<<(d.P + 255) / 256, 256, 0, pop->stream>>>(d, g);
         else k_plan<<<(d.P + 7) / 8, 256, 0, pop->stream>>>(d, g, par);
         {
@@ -1477,7 +1529,7 @@ int gen_crossover(gp_pop* pop, uint32_t generation) {
         pop->have_children = true;
         pop->lazy_pending = true;
         g.evaluated = false;
-        pop->launches = 3;
+        pop->launches = pop->have_next_plan_at_xo ? 7 : 3;
         return GP_OK;
     }
     k_plan<<<(d.P + 7) / 8, 256, 0, pop->stream>>>(d, g, par);
@@ -1488,9 +1540,9 @@ int gen_crossover(gp_pop* pop, uint32_t generation) {
     k_assign<<<1, 1024, 0, pop->stream>>>(d, g);
     k_gather<<<pop->nsm * 4, 256, 0, pop->stream>>>(d, g);
     k_copy_children<<<pop->nsm * 8, 256, 0, pop->stream>>>(d, g);
-    k_save_halo<<<pop->nsm * 8, 256, 0, pop->stream>>>(d, g);
-    k_shift<<<pop->nsm * 4, 512, 0, pop->stream>>>(d, g);
-    k_write_frags<<<pop->nsm * 4, 256, 0, pop->stream>>>(d, g);
+    k_save_halo<<<pop->nsm * 8, 256, 0, pop->stream>>>(d, g, 0);
+    k_shift<<<pop->nsm * 4, 512, 0, pop->stream>>>(d, g, 0);
+    k_write_frags<<<pop->nsm * 4, 256, 0, pop->stream>>>(d, g, 0);
     phase_end(pop, PH_XO);
     CK(cudaGetLastError());
     pop->have_children = true;

@@ -37,14 +37,16 @@ def _expected_entries(tree, T):
 
 
 def run_generations(gp, w, *, T, gens, max_nodes, seed=1234, cache_check=16, stop_check=True,
-                    cases_per_lane=0, walk_team=0, lazy=False, long_walks=0, onepass_nodes=0, stack_window=0):
+                    cases_per_lane=0, walk_team=0, lazy=False, long_walks=0, onepass_nodes=0, stack_window=0,
+                    lazy_inplace=False, arena_buffers=0):
     import oracle
     ops, off = w["ops"], w["off"]
     k, x, t = w["consts"], w["x"], w["t"]
     P = len(off) - 1
     pop = gp.Population(x, t, k, ops, off, max_nodes=max_nodes, cache_threshold=T, seed=seed,
                         cases_per_lane=cases_per_lane, walk_team=walk_team, lazy=lazy, long_walks=long_walks,
-                        onepass_nodes=onepass_nodes, stack_window=stack_window)
+                        onepass_nodes=onepass_nodes, stack_window=stack_window, lazy_inplace=lazy_inplace,
+                        arena_buffers=arena_buffers)
     pop.eval_full()
     fit = pop.fitness()
     _, ofit = oracle.eval_pop_f32(ops, off, k, x, t)
@@ -367,6 +369,55 @@ def test_bounded_walk_waits_run_out(gp):
     assert oracle.canon_nan(pop.fitness()).tobytes() == oracle.canon_nan(kfit).tobytes()
     for i in range(len(koff) - 1):
         assert np.array_equal(pop.tree(i), kops[int(koff[i]):int(koff[i + 1])]), i
+    pop.close()
+
+
+@pytest.mark.parametrize("T,onepass", [(1024, 0), (64, 0xFFFFFFFF)])
+def test_generations_memory_lean_in_place(gp, T, onepass):
+    """Fitness-first order, memory-lean: each mother's last selected child
+    takes her buffer and is built there in place at the next crossover,
+    whatever its size change (grafted trees of ~20,000 nodes: tails of
+    several move blocks, size changes from a few bytes to whole subtrees).
+    Children (read through their parents until they are built), fitness,
+    stop levels and caches equal the oracle's for several generations, in
+    an arena of 1.5 P buffers."""
+    import synth
+    ops, off = synth.population("big", synth.MASTER_SEED + 3, 64, target=20_000)
+    x, t = synth.cases(synth.MASTER_SEED + 3, 48)
+    w = {"ops": ops, "off": off, "x": x, "t": t, "consts": synth.consts(synth.MASTER_SEED + 3)}
+    run_generations(gp, w, T=T, gens=5, max_nodes=60_000, lazy=True, lazy_inplace=True, arena_buffers=96,
+                    onepass_nodes=onepass, cache_check=6)
+
+
+def test_memory_lean_huge_trees(gp):
+    """Trees of 10^7 nodes (the paper grows trees far beyond 10^6 nodes,
+    Sec. 5) in the memory-lean fitness-first order with 1.5 P buffers of
+    2^24 bytes: three generations whose children and fitness equal the
+    oracle's (the oracle evaluates every child in full, one tree per host
+    thread)."""
+    import oracle
+    import synth
+    ops, off = synth.population("big", synth.MASTER_SEED + 7, 12, target=10_000_000)
+    x, t = synth.cases(synth.MASTER_SEED + 7, 48)
+    k = synth.consts(synth.MASTER_SEED + 7)
+    maxn, seed = 1 << 24, 71
+    pop = gp.Population(x, t, k, ops, off, max_nodes=maxn, cache_threshold=1024, seed=seed, lazy=True,
+                        lazy_inplace=True, arena_buffers=18, packing=gp.GP_PACK_MLP)
+    pop.eval_full()
+    fit = _oracle_fitness_threaded(ops, off, k, x, t)
+    assert oracle.canon_nan(pop.fitness()).tobytes() == oracle.canon_nan(fit).tobytes()
+    cur_ops, cur_off = ops, off
+    for g in range(3):
+        pl = oracle.plan(cur_ops, cur_off, fit, T=7, seed=seed, gen=g, max_nodes=maxn)
+        kops, koff = oracle.breed(cur_ops, cur_off, pl)
+        pop.crossover(g)
+        pop.eval_incremental()
+        kfit = _oracle_fitness_threaded(kops, koff, k, x, t)
+        assert oracle.canon_nan(pop.fitness()).tobytes() == oracle.canon_nan(kfit).tobytes(), g
+        for i in range(len(koff) - 1):
+            assert np.array_equal(pop.tree(i), kops[int(koff[i]):int(koff[i + 1])]), (g, i)
+        assert int(np.diff(koff).max()) >= 10_000_000
+        cur_ops, cur_off, fit = kops, koff, kfit
     pop.close()
 
 
