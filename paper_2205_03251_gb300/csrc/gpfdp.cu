@@ -97,7 +97,9 @@ struct gp_pop {
     cudaEvent_t wfork_ev, wjoin_ev;   // large-team walk fork / join
     cudaStream_t side3;               // fourth stream: the one-pass children beside the walk
     cudaEvent_t ofork_ev, ojoin_ev;   // one-pass fork / join
+    cudaEvent_t xfork_ev[2], xjoin_ev[2];   // cache update: records beside counts, links beside the slot pool
     int grid_onepass;                 // CTAs of the one-pass interpreter (each with its own overflow stacks)
+    uint32_t* rank;                   // [P] work-order ranks
     int prio_high;                    // greatest stream priority of the device (the large teams' launch)
     MlpBufs mlp;
     float mlp_lr;
@@ -613,6 +615,7 @@ int gp_pop_create(const gp_config* cfg_in, const float* x, const float* targets,
     pop->wfork_ev = pop->wjoin_ev = nullptr;
     pop->side3 = nullptr;
     pop->ofork_ev = pop->ojoin_ev = nullptr;
+    pop->xfork_ev[0] = pop->xfork_ev[1] = pop->xjoin_ev[0] = pop->xjoin_ev[1] = nullptr;
     pop->gev_made = pop->capturing = pop->graph_prof = pop->stats_graph = false;
     memset(pop->gev_n, 0, sizeof pop->gev_n);
     auto bail = [&](int code) { gp_pop_destroy(pop); return code; };
@@ -638,7 +641,11 @@ int gp_pop_create(const gp_config* cfg_in, const float* x, const float* targets,
         cudaEventCreateWithFlags(&pop->wjoin_ev, cudaEventDisableTiming) != cudaSuccess ||
         cudaStreamCreateWithFlags(&pop->side3, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&pop->ofork_ev, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&pop->ojoin_ev, cudaEventDisableTiming) != cudaSuccess) {
+        cudaEventCreateWithFlags(&pop->ojoin_ev, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&pop->xfork_ev[0], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&pop->xfork_ev[1], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&pop->xjoin_ev[0], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&pop->xjoin_ev[1], cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();
         g_create_error = "stream or event creation failed";
         return bail(GP_ECUDA);
@@ -765,7 +772,7 @@ int gp_pop_create(const gp_config* cfg_in, const float* x, const float* targets,
         DA2(g.nmother, P); DA2(g.nfather, P); DA2(g.ncpos, P); DA2(g.nrsz, P); DA2(g.ndpos, P); DA2(g.nssz, P);
         DA2(g.nflags, P); DA2(g.sel, P); DA2(g.nfree, 1); DA2(g.pref, P);
         DA2(g.walkA, P); DA2(g.nins, P); DA2(g.mb, P); DA2(g.mcnt, P + 1);
-        DA2(g.order, P); DA2(g.gstat, NGSTAT);
+        DA2(g.order, P); DA2(g.gstat, NGSTAT); DA2(pop->rank, P);
         DA2(g.small_cnt, P); DA2(g.small_val, (size_t)P * d.Cpad); DA2(g.onepass, P); DA2(g.op_base, P);
         DA2(g.op_cnt, 2 * OP_BUCKETS); DA2(g.op_bucket, (size_t)OP_BUCKETS * P);
         cudaMemset(g.onepass, 0, sizeof(uint32_t) * P);
@@ -875,6 +882,10 @@ void gp_pop_destroy(gp_pop* pop) {
     if (pop->pjoin_ev) cudaEventDestroy(pop->pjoin_ev);
     if (pop->wfork_ev) cudaEventDestroy(pop->wfork_ev);
     if (pop->wjoin_ev) cudaEventDestroy(pop->wjoin_ev);
+    for (int k = 0; k < 2; ++k) {
+        if (pop->xfork_ev[k]) cudaEventDestroy(pop->xfork_ev[k]);
+        if (pop->xjoin_ev[k]) cudaEventDestroy(pop->xjoin_ev[k]);
+    }
     if (pop->ofork_ev) cudaEventDestroy(pop->ofork_ev);
     if (pop->ojoin_ev) cudaEventDestroy(pop->ojoin_ev);
     cudaFree(pop->gb.dis); cudaFree(pop->gb.dis_n);
@@ -1474,11 +1485,16 @@ int launch_pack(gp_pop* pop, const CacheView& par) {
     k_mlp_features<<<pb, 256, 0, ms>>>(d, g, par, pop->mlp);
     const int mb = (d.P + 7) / 8 < pop->nsm * 2 ? (d.P + 7) / 8 : pop->nsm * 2;   // 8 samples per CTA pass
     k_mlp_infer<<<mb, 256, 0, ms>>>(pop->mlp, d.P, pop->mlp.pred_pack);
+    const dim3 rg((d.P + 255) / 256, (d.P + RANK_TILE - 1) / RANK_TILE);
     if (pop->cfg.packing == GP_PACK_MLP && d.P <= SORT_MAX) {
-        k_sort_desc<<<1, 1024, 0, ms>>>(pop->mlp.pred_pack, d.P, g.order);
+        CK(cudaMemsetAsync(pop->rank, 0, sizeof(uint32_t) * d.P, ms));
+        k_rank_desc<<<rg, 256, 0, ms>>>(pop->mlp.pred_pack, d.P, pop->rank);
+        k_rank_scatter<<<pb, 256, 0, ms>>>(pop->rank, d.P, g.order);
     } else if (pop->cfg.packing == GP_PACK_STATIC && d.P <= SORT_MAX) {
         k_static_key<<<pb, 256, 0, ms>>>(d, g, pop->mlp);
-        k_sort_desc<<<1, 1024, 0, ms>>>(pop->mlp.target, d.P, g.order);
+        CK(cudaMemsetAsync(pop->rank, 0, sizeof(uint32_t) * d.P, ms));
+        k_rank_desc<<<rg, 256, 0, ms>>>(pop->mlp.target, d.P, pop->rank);
+        k_rank_scatter<<<pb, 256, 0, ms>>>(pop->rank, d.P, g.order);
     } else {
         k_order_identity<<<pb, 256, 0, ms>>>(d, g);
     }
@@ -1588,8 +1604,12 @@ int gen_incremental(gp_pop* pop) {
         CK(cudaEventRecord(pop->cjoin_ev, pop->side));
     }
     phase_begin(pop, PH_CACHE);
-    k_pv_offsets<<<1, 1024, 0, pop->stream>>>(d, g);
-    k_pv_scatter<<<gt, 256, 0, pop->stream>>>(d, g);
+    // the walk records grouped per child (fourth stream) beside the children's entry counts
+    CK(cudaEventRecord(pop->xfork_ev[0], pop->stream));
+    CK(cudaStreamWaitEvent(pop->side3, pop->xfork_ev[0], 0));
+    k_pv_offsets<<<1, 1024, 0, pop->side3>>>(d, g);
+    k_pv_scatter<<<gt, 256, 0, pop->side3>>>(d, g);
+    CK(cudaEventRecord(pop->xjoin_ev[0], pop->side3));
     k_merge_count<<<(d.P + 7) / 8, 256, 0, pop->stream>>>(d, g, par);
     k_merge_offsets<<<1, 1024, 0, pop->stream>>>(d, g);
     if (!d.strict_cap) {
@@ -1601,6 +1621,7 @@ int gen_incremental(gp_pop* pop) {
             if (want > room) want = room;
             if (want < *pop->e_total_h) {
                 if (g.lazy) cudaStreamWaitEvent(pop->stream, pop->cjoin_ev, 0);
+                cudaStreamWaitEvent(pop->stream, pop->xjoin_ev[0], 0);
                 return fail(pop, GP_ENOMEM, "cache of %u entries exceeds the cache budget", *pop->e_total_h);
             }
             int r = grow_cache(pop, (uint32_t)want);
@@ -1624,22 +1645,29 @@ int gen_incremental(gp_pop* pop) {
         k_mlp_bump<<<1, 32, 0, ms>>>(pop->mlp);
         CK(cudaEventRecord(pop->join_ev, ms));
     }
+    CK(cudaStreamWaitEvent(pop->stream, pop->xjoin_ev[0], 0));
     k_merge_write<<<d.P < (uint32_t)pop->nsm * 8 ? d.P : pop->nsm * 8, 256, 0, pop->stream>>>(d, g, par);
+    // the entries' parent and child links (fourth stream) beside the value-slot pool
+    CK(cudaEventRecord(pop->xfork_ev[1], pop->stream));
+    CK(cudaStreamWaitEvent(pop->side3, pop->xfork_ev[1], 0));
+    k_entry_chunkmax<<<pop->grid_warps, GP_WARPS * 32, 0, pop->side3>>>(d, pop->sb);
+    k_entry_parents<<<gt, 256, 0, pop->side3>>>(d, pop->sb);
+    k_child_sizes<<<(d.P + 255) / 256, 256, 0, pop->side3>>>(d, g);
+    CK(cudaEventRecord(pop->xjoin_ev[1], pop->side3));
     k_mark_live<<<gt, 256, 0, pop->stream>>>(d, g);
     k_free_count<<<pop->nsm * 2, 1024, 0, pop->stream>>>(d, g);
     k_free_top<<<1, 1024, 0, pop->stream>>>(d, g);
     k_free_emit<<<pop->nsm * 2, 1024, 0, pop->stream>>>(d, g);
     k_copy_values<<<pop->nsm * 16, 256, 0, pop->stream>>>(d, g, par);
-    k_entry_chunkmax<<<pop->grid_warps, GP_WARPS * 32, 0, pop->stream>>>(d, pop->sb);
-    k_entry_parents<<<gt, 256, 0, pop->stream>>>(d, pop->sb);
-    k_child_sizes<<<(d.P + 255) / 256, 256, 0, pop->stream>>>(d, g);
+    k_check_slots<<<gt, 256, 0, pop->stream>>>(d);
+    CK(cudaStreamWaitEvent(pop->stream, pop->xjoin_ev[1], 0));
     CK(cudaStreamWaitEvent(pop->stream, pop->join_ev, 0));
     if (g.lazy) CK(cudaStreamWaitEvent(pop->stream, pop->cjoin_ev, 0));
     phase_end(pop, PH_CACHE);
     k_accumulate<<<1, 32, 0, pop->stream>>>(pop->cum, d.acc_ops, g.gstat, pop->cases_stat, 1);
     ++pop->cum_calls;
     CK(cudaGetLastError());
-    pop->launches += 12 + 13 + 1 + ((g.dis || !pop->onepass_nodes) ? 0u : 1u) + (pop->walk_long_n ? 1u : 0u);
+    pop->launches += 12 + 14 + 1 + ((g.dis || !pop->onepass_nodes) ? 0u : 1u) + (pop->walk_long_n ? 1u : 0u);
     pop->have_children = false;
     g.evaluated = true;
     pop->last_kind = 1;

@@ -273,34 +273,37 @@ __global__ void k_mlp_init(MlpBufs b, uint64_t seed) {
 
 // Sort n (<= 4096) keys descending with their indices: one CTA, bitonic in
 // shared memory.  Ties keep the lower index first (stable order).
-#define SORT_MAX 4096
-__global__ void __launch_bounds__(1024) k_sort_desc(const float* __restrict__ key, uint32_t n, uint32_t* __restrict__ order) {
-    __shared__ float ks[SORT_MAX];
-    __shared__ uint32_t is[SORT_MAX];
-    uint32_t m = 1;
-    while (m < n) m <<= 1;
-    for (uint32_t i = threadIdx.x; i < m; i += blockDim.x) {
-        float kv = (i < n) ? key[i] : -INFINITY;
-        if (isnan(kv)) kv = -INFINITY;
-        ks[i] = kv;
-        is[i] = i;
-    }
+#define SORT_MAX 16384     // work orders of larger populations are the identity
+#define RANK_TILE 1024     // keys compared by one CTA
+
+// Descending order of n keys (NaN as -infinity; equal keys by index) by
+// ranks: the rank of key i is the number of keys that come before it, so
+// order[rank(i)] = i.  A CTA takes 256 keys and a tile of RANK_TILE keys to
+// compare them with (staged in shared memory) and adds its partial counts;
+// the grid spreads the n^2 comparisons over the GPU instead of running the
+// log^2 n barrier stages of a one-block sort.  rank[] starts at zero.
+__device__ __forceinline__ float sort_key(const float* key, uint32_t i) {
+    const float k = key[i];
+    return isnan(k) ? -INFINITY : k;
+}
+
+__global__ void __launch_bounds__(256) k_rank_desc(const float* __restrict__ key, uint32_t n, uint32_t* __restrict__ rank) {
+    __shared__ float kt[RANK_TILE];
+    const uint32_t t0 = blockIdx.y * RANK_TILE;
+    const uint32_t tn = min((uint32_t)RANK_TILE, n - t0);
+    for (uint32_t j = threadIdx.x; j < tn; j += blockDim.x) kt[j] = sort_key(key, t0 + j);
     __syncthreads();
-    for (uint32_t size = 2; size <= m; size <<= 1) {
-        for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
-            for (uint32_t i = threadIdx.x; i < m; i += blockDim.x) {
-                const uint32_t j = i ^ stride;
-                if (j > i) {
-                    const bool desc = (i & size) == 0;
-                    const float a = ks[i], c = ks[j];
-                    const uint32_t ia = is[i], ic = is[j];
-                    // "a before c" in descending order with index tie-break
-                    const bool a_first = (a > c) || (a == c && ia < ic);
-                    if (desc ? !a_first : a_first) { ks[i] = c; ks[j] = a; is[i] = ic; is[j] = ia; }
-                }
-            }
-            __syncthreads();
-        }
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float ki = sort_key(key, i);
+    uint32_t r = 0;
+    for (uint32_t j = 0; j < tn; ++j) {
+        const float kj = kt[j];
+        r += (kj > ki || (kj == ki && t0 + j < i)) ? 1u : 0u;
     }
-    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) order[i] = is[i];
+    if (r) atomicAdd(&rank[i], r);
+}
+
+__global__ void k_rank_scatter(const uint32_t* __restrict__ rank, uint32_t n, uint32_t* __restrict__ order) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) order[rank[i]] = i;
 }

@@ -502,14 +502,23 @@ __global__ void k_entry_parents(DevPop d, StructBufs sb) {
         if (valid) {
             if (need && par < 0) set_error(d, ST_STRUCT, 2, tree, pos, e - d.e_off[tree]);
             d.e_par[e] = par;
-            // every entry must hold a value slot by now; never leave one unassigned
-            if (d.e_slot[e] == SLOT_NEW) { d.e_slot[e] = 0; set_error(d, ST_STRUCT, 8, tree, pos, 0); }
             if (par >= 0) {
                 if (pos == d.e_pos[par] + 1) d.e_c0[par] = (int32_t)e;
                 else d.e_c1[par] = (int32_t)e;
             }
         }
     }
+}
+
+// Every cache entry must hold a value slot once a generation's values are
+// assigned; one that does not would index the pool out of bounds later, so
+// it gets slot 0 and the status records the inconsistency.
+__global__ void k_check_slots(DevPop d) {
+    if (halted(d)) return;
+    const uint32_t ne = d.e_off[d.P];
+    if (ne > d.Ecap) return;
+    for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < ne; e += gridDim.x * blockDim.x)
+        if (d.e_slot[e] == SLOT_NEW) { d.e_slot[e] = 0; set_error(d, ST_STRUCT, 8, d.e_tree[e], d.e_pos[e], 0); }
 }
 
 // blk_off[i] = sum_{j<i} ceil(size_j / GP_B); one CTA of 1024 threads.

@@ -78,6 +78,10 @@ def test_packing_never_changes_results():
             assert a.tobytes() == b.tobytes()
         order = pk[-1][3]
         assert sorted(order.tolist()) == list(range(40))
+        if p == gp.GP_PACK_MLP:
+            # longest predicted walk first; equal predictions by child index
+            kk = np.where(np.isnan(pk[-1][0]), -np.inf, pk[-1][0])[order]
+            assert np.all((kk[:-1] > kk[1:]) | ((kk[:-1] == kk[1:]) & (order[:-1] < order[1:])))
 
 
 def _spearman(a, b):
