@@ -1085,7 +1085,12 @@ __device__ bool walk_ancestors(const DevPop& d, const CacheView& par, uint32_t i
                 const int64_t j = (int64_t)c - 1 - 32 * lane - t;
                 if (j >= (int64_t)lo) {
                     gsum += (stB[j - a16] < 4) ? 1 : -1;
-                    if (fmask & (1u << t)) { anc[k] = (uint32_t)j; ancg[k] = gsum; ++k; }
+                    if (fmask & (1u << t)) {
+                        anc[k] = (uint32_t)j;
+                        // balance offset (>= 0 at an ancestor), operator byte in bits 24..
+                        ancg[k] = (int32_t)((uint32_t)gsum | ((uint32_t)stB[j - a16] << 24));
+                        ++k;
+                    }
                 }
             }
             nsmall = tot;
@@ -1095,7 +1100,7 @@ __device__ bool walk_ancestors(const DevPop& d, const CacheView& par, uint32_t i
     // ---- child ends of the small ancestors: forward scan after the donated subtree
     // balance relative to b[c] is 1 at c+s; lvl[v] = first position where it reaches v
     uint32_t maxv = 1;
-    if (nsmall) maxv = (uint32_t)ancg[nsmall - 1] + 1;
+    if (nsmall) maxv = (uint32_t)(ancg[nsmall - 1] & 0xFFFFFF) + 1;
     if (maxv >= WALK_MAXLVL) { if (lane == 0) set_status(d.status, ST_PATH); return false; }
     int32_t hneed = -1;
     if (nsmall) {
@@ -1143,7 +1148,7 @@ __device__ bool walk_ancestors(const DevPop& d, const CacheView& par, uint32_t i
         // highest small ancestor that the child caches (needs a value even above the stop)
         for (uint32_t k = lane; k < nsmall; k += 32) {
             const uint32_t p = anc[k];
-            const uint32_t pe = lvl[ancg[k] + 1];
+            const uint32_t pe = lvl[(ancg[k] & 0xFFFFFF) + 1];
             if (pe - p >= T) hneed = max(hneed, (int32_t)k);
         }
 #pragma unroll
@@ -1214,6 +1219,87 @@ __device__ __forceinline__ void dis_store(const GenBufs& g, uint32_t i, uint32_t
 // values of nodes that are cached in the child are recorded for the
 // child's cache; above the stop only child-cached nodes that the mother
 // does not cache need computing.
+// Builder of the walk's level descriptors (one lane): the ancestors of the
+// crossover point from the nearest up -- the small ones from the backward
+// balance scan (anc, ancg, lvl), then the mother's cached ancestors through
+// their parent links -- each with its sibling's range in the child and, for
+// a large sibling, its cache entry.  `stopped` ends the building above the
+// stop except for small ancestors that the child caches (they need values).
+
+struct WalkBuilder {
+    uint32_t bq, bqend, bk;
+    int32_t bpe;
+    bool btop;
+};
+
+struct WalkCtx {
+    const uint8_t* ok_;        // child bytes before the crossover point (the mother's in fitness-first order)
+    uint32_t nsmall, nk, s, r, T;
+    int32_t A, hneed;
+    const uint32_t* anc;
+    const int32_t* ancg;
+    const uint32_t* lvl;
+};
+
+// Build the next level into D; false (and btop set) when there is none.
+// The walk's critical path on long paths runs through this builder, one
+// dependent chain of cache-link loads per level: every field of a cached
+// ancestor's entry is loaded at once (one round trip), then its operator
+// byte and its large sibling's slot (a second one); a small ancestor's
+// operator byte was kept by the backward scan (bits 24.. of ancg).
+__device__ __forceinline__ bool build_level(const CacheView& par, const WalkCtx& w, WalkBuilder& b, bool stopped,
+                                            LevelDesc& D) {
+    if (b.btop) return false;
+    uint32_t p, pend, op;
+    int32_t pent, c0 = -1, c1 = -1, nextp = -1;
+    uint32_t pslot = 0;
+    if (b.bk < w.nsmall) {
+        const int32_t gk = w.ancg[b.bk];
+        p = w.anc[b.bk];
+        pend = w.lvl[(gk & 0xFFFFFF) + 1];
+        op = (uint32_t)gk >> 24;
+        pent = -1;
+    } else {
+        pent = (b.bk == w.nsmall) ? w.A : b.bpe;
+        if (pent < 0) { b.btop = true; return false; }                  // above the root
+        p = __ldg(par.e_pos + pent);
+        const uint32_t e = __ldg(par.e_end + pent);
+        c0 = __ldg(par.e_c0 + pent);
+        c1 = __ldg(par.e_c1 + pent);
+        pslot = __ldg(par.e_slot + pent);
+        nextp = __ldg(par.e_par + pent);
+        pend = (uint32_t)((int64_t)e + ((int64_t)w.s - (int64_t)w.r));
+        op = 0xFFFFFFFFu;
+    }
+    // above the stop only small ancestors that the child caches need values
+    if (stopped && (pent >= 0 || (int32_t)b.bk > w.hneed)) { b.btop = true; return false; }
+    const bool left = (b.bq == p + 1);
+    const uint32_t ss = left ? b.bqend : p + 1;
+    const uint32_t se = left ? pend : b.bq;
+    int32_t sib = -1;
+    uint32_t bad = 0;
+    if (se <= ss || se > w.nk) bad = LD_BAD;
+    else if (se - ss >= w.T) {
+        sib = (pent < 0) ? -1 : (left ? c1 : c0);
+        if (sib < 0) bad = LD_NOSIB;
+    }
+    if (op == 0xFFFFFFFFu) op = w.ok_[p];
+    const uint32_t sslot = (sib >= 0) ? __ldg(par.e_slot + sib) : 0u;
+    const uint32_t flg = op | (left ? LD_LEFT : 0u) | ((p == 0 || pend - p >= w.T) ? LD_CACHED : 0u) | bad;
+    D.p = p; D.pend = pend; D.ss = ss; D.se = se; D.pent = pent; D.sib = sib; D.flags = flg;
+    D.k = (int32_t)b.bk;
+    D.pslot = pslot;
+    D.sslot = sslot;
+    D.pad0 = 0u; D.pad1 = 0u;
+    if (bad) { b.btop = true; return true; }
+    b.bq = p;
+    b.bqend = pend;
+    if (b.bk >= w.nsmall) b.bpe = nextp;
+    ++b.bk;
+    if (p == 0) b.btop = true;
+    return true;
+}
+
 // The children one launch walks: entries [q_lo, q_hi) of the work order,
 // taken through queue counter qctr; its warps use the interpreter overflow
 // stacks from warp ovf_base on.
@@ -1391,63 +1477,41 @@ __global__ void __launch_bounds__(MAXT, 512 / MAXT) k_walk(DevPop d, GenBufs g, 
                 for (uint32_t j = lane; j < Cn; j += 32) dis_case<V>(nvs[j], ovs[j], nd, nf, sq);
                 dis_store<V>(g, i, 0, nd, nf, sq);
             }
-            uint32_t bq = c, bqend = c + s, bk = 0;        // builder state (lane 0)
-            int32_t bpe = (nsmall > 0) ? -1 : A;
+            WalkBuilder b;                                 // builder state (lane 0)
+            b.bq = c; b.bqend = c + s; b.bk = 0; b.bpe = (nsmall > 0) ? -1 : A; b.btop = false;
+            const WalkCtx wc{ok_, nsmall, nk, s, r, T, A, hneed, anc, ancg, lvl};
             bool btop = false;
             uint32_t nb = 0, ncm = 0, level = 0;           // levels built, levels combined
             uint32_t rbase = 0, rleft = 0;                 // this child's reserved record slots
             bool fail = false;
             uint32_t guard = 0;
             while (guard++ < (1u << 24)) {
-                // build ahead while the ring has room
-                if (lane == 0) {
-                    while (!btop && nb < ncm + ahead) {
-                        uint32_t p, pend;
-                        int32_t pent;
-                        if (bk < nsmall) {
-                            p = anc[bk];
-                            pend = lvl[ancg[bk] + 1];
-                            pent = -1;
-                        } else {
-                            pent = (bk == nsmall) ? A : bpe;
-                            if (pent < 0) { btop = true; break; }                  // above the root
-                            p = par.e_pos[pent];
-                            pend = (uint32_t)((int64_t)par.e_end[pent] + ((int64_t)s - (int64_t)r));
-                        }
-                        // above the stop only small ancestors that the child caches need values
-                        if (stopped_w && (pent >= 0 || (int32_t)bk > hneed)) { btop = true; break; }
-                        const bool left = (bq == p + 1);
-                        const uint32_t ss = left ? bqend : p + 1;
-                        const uint32_t se = left ? pend : bq;
-                        uint32_t flg = ok_[p] | (left ? LD_LEFT : 0u) | ((p == 0 || pend - p >= T) ? LD_CACHED : 0u);
-                        int32_t sib = -1;
-                        if (se <= ss || se > nk) flg |= LD_BAD;
-                        else if (se - ss >= T) {
-                            sib = (pent < 0) ? -1 : (left ? par.e_c1[pent] : par.e_c0[pent]);
-                            if (sib < 0) flg |= LD_NOSIB;
-                        }
+                // combine the next level as soon as its sibling values are in;
+                // until then build one more level (the builder's chain of loads
+                // overlaps the evaluators' work instead of delaying the combining)
+                bool ready = false;
+                if (ncm < nb) ready = nev == 0 || __shfl_sync(FULL, lane == 0 ? vcnt[ncm % ring] : 0u, 0) >= ncb;
+                if (!ready) {
+                    uint32_t built = 0;
+                    if (lane == 0 && !b.btop && nb < ncm + ahead) {
                         LevelDesc& D = desc[nb % ring];
-                        D.p = p; D.pend = pend; D.ss = ss; D.se = se; D.pent = pent; D.sib = sib; D.flags = flg;
-                        D.k = (int32_t)bk;
-                        D.pslot = (pent >= 0) ? par.e_slot[pent] : 0u;
-                        D.sslot = (sib >= 0) ? par.e_slot[sib] : 0u;
-                        __threadfence_block();
-                        dtag[nb % ring] = nb + 1;
-                        ++nb;
-                        if (flg & (LD_BAD | LD_NOSIB)) { btop = true; break; }
-                        bq = p;
-                        bqend = pend;
-                        if (bk >= nsmall) bpe = par.e_par[pent];
-                        ++bk;
-                        if (p == 0) { btop = true; break; }
+                        if (build_level(par, wc, b, stopped_w, D)) {
+                            __threadfence_block();
+                            dtag[nb % ring] = nb + 1;
+                            ++nb;
+                            built = 1;
+                            if (D.flags & (LD_BAD | LD_NOSIB)) b.btop = true;
+                        }
                     }
-                }
-                __syncwarp();
-                nb = __shfl_sync(FULL, nb, 0);
-                btop = __shfl_sync(FULL, btop ? 1u : 0u, 0) != 0;
-                if (ncm == nb) {
-                    if (btop) break;                                           // nothing left to combine
-                    continue;
+                    if (lane == 0) btop = b.btop;
+                    __syncwarp();
+                    nb = __shfl_sync(FULL, nb, 0);
+                    btop = __shfl_sync(FULL, btop ? 1u : 0u, 0) != 0;
+                    if (__shfl_sync(FULL, built, 0)) continue;
+                    if (ncm == nb) {
+                        if (btop) break;                                       // nothing left to combine
+                        continue;
+                    }
                 }
                 const uint32_t slot = ncm % ring;
                 LevelDesc D = desc[slot];

@@ -38,7 +38,7 @@ def _expected_entries(tree, T):
 
 def run_generations(gp, w, *, T, gens, max_nodes, seed=1234, cache_check=16, stop_check=True,
                     cases_per_lane=0, walk_team=0, lazy=False, long_walks=0, onepass_nodes=0, stack_window=0,
-                    lazy_inplace=False, arena_buffers=0):
+                    lazy_inplace=False, arena_buffers=0, packing=None):
     import oracle
     ops, off = w["ops"], w["off"]
     k, x, t = w["consts"], w["x"], w["t"]
@@ -46,7 +46,7 @@ def run_generations(gp, w, *, T, gens, max_nodes, seed=1234, cache_check=16, sto
     pop = gp.Population(x, t, k, ops, off, max_nodes=max_nodes, cache_threshold=T, seed=seed,
                         cases_per_lane=cases_per_lane, walk_team=walk_team, lazy=lazy, long_walks=long_walks,
                         onepass_nodes=onepass_nodes, stack_window=stack_window, lazy_inplace=lazy_inplace,
-                        arena_buffers=arena_buffers)
+                        arena_buffers=arena_buffers, packing=gp.GP_PACK_STATIC if packing is None else packing)
     pop.eval_full()
     fit = pop.fitness()
     _, ofit = oracle.eval_pop_f32(ops, off, k, x, t)
@@ -123,6 +123,24 @@ def test_generations_rhh(gp, T, lazy, onepass):
     import synth
     w = synth.workload(0, n_trees=120)
     run_generations(gp, w, T=T, gens=4, max_nodes=20000, lazy=lazy, onepass_nodes=onepass)
+
+
+@pytest.mark.parametrize("lazy", [False, True])
+@pytest.mark.parametrize("T", [1024, 64])
+def test_generations_learned_packing(gp, lazy, T):
+    """Learned packing (the MLP's predicted path lengths order the walk and
+    are trained online on the measured ones): children, fitness, stop
+    levels and caches equal the oracle's, every child walked (no one-pass
+    children) and with the one-pass path on deep uniform random trees."""
+    import synth
+    ops, off = synth.population("big", synth.MASTER_SEED + 4, 48, target=30_000)
+    x, t = synth.cases(synth.MASTER_SEED + 4, 48)
+    w = {"ops": ops, "off": off, "x": x, "t": t, "consts": synth.consts(synth.MASTER_SEED + 4)}
+    run_generations(gp, w, T=T, gens=5, max_nodes=80_000, lazy=lazy, packing=gp.GP_PACK_MLP,
+                    onepass_nodes=0xFFFFFFFF, cache_check=6)
+    w3 = synth.workload(3, n_trees=96, target=20_000)
+    run_generations(gp, w3, T=T, gens=3, max_nodes=40_000, lazy=lazy, packing=gp.GP_PACK_MLP, cache_check=4,
+                    stack_window=64)
 
 
 def test_fitness_first_matches_eager(gp):
