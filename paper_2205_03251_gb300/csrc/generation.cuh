@@ -984,7 +984,8 @@ __device__ __forceinline__ void combine(uint32_t op, bool path_left, float (&v)[
 // Evaluate bytes [s, e) of `src` (a small run: e - (s & ~15) <= STAGE_BYTES).
 template <int K, int V>
 __device__ __forceinline__ void eval_run(const uint8_t* src, uint32_t s, uint32_t e, uint8_t* stage,
-                                         const Ictx<K>& c, float (&out)[K], uint32_t* status) {
+                                         const Ictx<K>& c, float (&out)[K], uint32_t* status,
+                                         const volatile uint32_t* stop = nullptr, bool* aborted = nullptr) {
     __syncwarp();
     stage_issue(stage, src, s, e);
     cp_async_commit();
@@ -995,7 +996,9 @@ __device__ __forceinline__ void eval_run(const uint8_t* src, uint32_t s, uint32_
     for (int k = 0; k < K; ++k) st.acc[k] = 0.f;
     st.sp = 0;
     st.ok = true;
-    interp_staged_lone<K, V>(stage, s, e, st, c);
+    bool ab = false;
+    interp_staged_lone<K, V>(stage, s, e, st, c, stop, &ab);
+    if (ab) { if (aborted) *aborted = true; return; }
     if (!st.ok && lane_id() == 0) set_status(status, ST_STACK);
 #pragma unroll
     for (int k = 0; k < K; ++k) out[k] = st.acc[k];
@@ -1325,7 +1328,7 @@ __global__ void __launch_bounds__(MAXT, 512 / MAXT) k_walk(DevPop d, GenBufs g, 
     float* mvs = reinterpret_cast<float*>(smem_raw + L.mv);
     volatile uint32_t* sc = reinterpret_cast<volatile uint32_t*>(smem_raw + L.sc);
     const int lane = lane_id();
-    const uint32_t warp = threadIdx.x >> 5, tid = threadIdx.x, nthr = nw * 32;
+    const uint32_t warp = threadIdx.x >> 5, tid = threadIdx.x;
     fill_kc(kc, d.consts);
     fill_kb(kc + 256);
     __syncthreads();
@@ -1406,86 +1409,102 @@ __global__ void __launch_bounds__(MAXT, 512 / MAXT) k_walk(DevPop d, GenBufs g, 
             __syncthreads();
             if (rslot >= g.pvcap) { if (tid == 0) set_status(d.status, ST_PATH); continue; }
         }
-        for (uint32_t it = warp; it < 2 * ncb; it += nw) {
-            const uint32_t which = it & 1u, cb = it >> 1;
-            load_cases<K>(d, cb, ic.xv);
-            float v[K];
-            if (which == 0) {
-                if (ef >= 0) load_vec<K>(par.slots, Cpad, par.e_slot[ef], v, cb);
-                else {
-                    if (virt) eval_run<K, V>(d.arena + (size_t)g.pbuf[f] * d.cap, dd, dd + s, stA, ic, v, d.status);
-                    else eval_run<K, V>(ok_, c, c + s, stA, ic, v, d.status);
-                    if (cb == 0) st_interp += s;
-                }
-            } else {
-                if (em >= 0) load_vec<K>(par.slots, Cpad, par.e_slot[em], v, cb);
-                else {
-                    eval_run<K, V>(g.stash + g.stash_off[i], 0, r, stA, ic, v, d.status);
-                    if (cb == 0) st_interp += r;
-                }
-            }
-            store_blk<K>(which == 0 ? nvs : ovs, cb, v);
-        }
-        __syncthreads();
-        bool okc = true;
-        for (uint32_t j = tid; j < Cn; j += nthr)
-            if (__float_as_uint(nvs[j]) != __float_as_uint(ovs[j])) okc = false;
-        bool stopped = __syncthreads_and(okc) != 0;
-        int32_t stop_level = stopped ? 0 : -1;
-        if (root_rec) {
-            float* dst = g.pv_val + (size_t)rslot * Cpad;
-            for (uint32_t j = tid; j < Cpad; j += nthr) dst[j] = nvs[j];
-            if (tid == 0) {
-                g.pv_rec[rslot] = make_uint4(i, npv, 0u, rslot | 0x80000000u);
-                g.pv_end[rslot] = s;
-                g.rec_entry[rslot] = 0xFFFFFFFFu;
-            }
-            ++npv;
-            ++nins_i;
-        }
-
-        // ---- ancestors (warp 0), broadcast through shared memory
-        if (warp == 0) {
-            int32_t A = -1, hneed = -1;
-            uint32_t nsmall = 0;
-            const bool ok = walk_ancestors<K>(d, par, i, ok_, tdl, c, s, nk, em, me0, me1, stB, anc, ancg, lvl, A,
-                                              nsmall, hneed);
-            if (lane == 0) { sc[2] = nsmall; sc[3] = (uint32_t)A; sc[4] = ok ? 0u : 1u; sc[5] = (uint32_t)hneed; }
-        }
-        __syncthreads();
-        const uint32_t nsmall = sc[2];
-        const int32_t A = (int32_t)sc[3];
-        const int32_t hneed = (int32_t)sc[5];
-        if (sc[4]) continue;
-
-        // ---- walk up.  Warp 0 builds level descriptors ahead (a ring of
-        // WALK_RING levels) and combines the levels in order as their sibling
-        // values arrive; warps 1.. evaluate siblings ahead of it, level after
-        // level, each without waiting for the others.  The combination stops
-        // where the method stops; siblings computed past it are discarded.
+        // ---- level 0 (donated subtree vs removed subtree), ancestors, walk.
+        // Neither the ancestors nor the siblings depend on the level-0 values,
+        // so in a team of several warps the evaluators interpret the donated
+        // and removed subtrees (up to T - 1 nodes each) while warp 0 finds the
+        // ancestors and builds the first levels; warp 0 compares level 0 just
+        // before it combines level 1.  A team of one does them in turn.
         if (tid < WALK_RING) { dtag[tid] = 0u; vcnt[tid] = 0u; }
-        if (tid == 0) *cur = 0ull;
-        if (tid == 0) sc[8] = 0u;                          // done flag
+        if (tid == 0) { *cur = 0ull; sc[8] = 0u; sc[6] = 0u; sc[4] = 0u; }
         __syncthreads();
-        bool stopped_w = stopped;
-        int32_t stop_level_w = stop_level;
+        auto level0 = [&](uint32_t first, uint32_t step) {
+            for (uint32_t it = first; it < 2 * ncb; it += step) {
+                const uint32_t which = it & 1u, cb = it >> 1;
+                load_cases<K>(d, cb, ic.xv);
+                float v[K];
+                if (which == 0) {
+                    if (ef >= 0) load_vec<K>(par.slots, Cpad, par.e_slot[ef], v, cb);
+                    else {
+                        if (virt) eval_run<K, V>(d.arena + (size_t)g.pbuf[f] * d.cap, dd, dd + s, stA, ic, v, d.status);
+                        else eval_run<K, V>(ok_, c, c + s, stA, ic, v, d.status);
+                        if (cb == 0) st_interp += s;
+                    }
+                } else {
+                    if (em >= 0) load_vec<K>(par.slots, Cpad, par.e_slot[em], v, cb);
+                    else {
+                        eval_run<K, V>(g.stash + g.stash_off[i], 0, r, stA, ic, v, d.status);
+                        if (cb == 0) st_interp += r;
+                    }
+                }
+                store_blk<K>(which == 0 ? nvs : ovs, cb, v);
+            }
+        };
+        if (nev == 0) level0(0, 1);
+        else if (warp >= 1) {
+            level0(warp - 1, nev);
+            __threadfence_block();
+            __syncwarp();
+            if (lane == 0) atomicAdd(const_cast<uint32_t*>(&sc[6]), 1u);
+        }
+        bool stopped = false;
+        int32_t stop_level = -1;
+        bool stopped_w = false;
+        int32_t stop_level_w = -1;
         uint32_t levels_w = 0;
         if (warp == 0) {
-            if (g.dis) {                                   // level 0 of the disruption record
-                uint32_t nd = 0, nf = 0;
-                double sq = 0.0;
-                for (uint32_t j = lane; j < Cn; j += 32) dis_case<V>(nvs[j], ovs[j], nd, nf, sq);
-                dis_store<V>(g, i, 0, nd, nf, sq);
-            }
+            // ---- ancestors
+            int32_t A = -1, hneed = -1;
+            uint32_t nsmall = 0;
+            const bool anc_ok = walk_ancestors<K>(d, par, i, ok_, tdl, c, s, nk, em, me0, me1, stB, anc, ancg, lvl, A,
+                                                  nsmall, hneed);
+            // level 0 compared once every level-0 item is in (bounded wait)
+            bool l0done = false, fail = false;
+            auto finish_level0 = [&]() {
+                if (l0done) return;
+                l0done = true;
+                if (nev) {
+                    uint32_t spins = 0, got = 0;
+                    while ((got = __shfl_sync(FULL, lane == 0 ? sc[6] : 0u, 0)) < nev && ++spins < d.wait_polls)
+                        __nanosleep(64);
+                    if (got < nev) { if (lane == 0) set_status(d.status, ST_TIMEOUT); fail = true; return; }
+                    __threadfence_block();
+                }
+                bool okc = true;
+                for (uint32_t j = lane; j < Cn; j += 32)
+                    if (__float_as_uint(nvs[j]) != __float_as_uint(ovs[j])) okc = false;
+                stopped = __all_sync(FULL, okc);
+                stop_level = stopped ? 0 : -1;
+                stopped_w = stopped;
+                stop_level_w = stop_level;
+                if (root_rec) {
+                    float* dst = g.pv_val + (size_t)rslot * Cpad;
+                    for (uint32_t j = lane; j < Cpad; j += 32) dst[j] = nvs[j];
+                    if (lane == 0) {
+                        g.pv_rec[rslot] = make_uint4(i, npv, 0u, rslot | 0x80000000u);
+                        g.pv_end[rslot] = s;
+                        g.rec_entry[rslot] = 0xFFFFFFFFu;
+                    }
+                    ++npv;
+                    ++nins_i;
+                }
+                if (g.dis) {                               // level 0 of the disruption record
+                    uint32_t nd = 0, nf = 0;
+                    double sq = 0.0;
+                    for (uint32_t j = lane; j < Cn; j += 32) dis_case<V>(nvs[j], ovs[j], nd, nf, sq);
+                    dis_store<V>(g, i, 0, nd, nf, sq);
+                }
+            };
+            if (!anc_ok) { fail = true; if (lane == 0) sc[4] = 1u; }
             WalkBuilder b;                                 // builder state (lane 0)
             b.bq = c; b.bqend = c + s; b.bk = 0; b.bpe = (nsmall > 0) ? -1 : A; b.btop = false;
             const WalkCtx wc{ok_, nsmall, nk, s, r, T, A, hneed, anc, ancg, lvl};
             bool btop = false;
             uint32_t nb = 0, ncm = 0, level = 0;           // levels built, levels combined
             uint32_t rbase = 0, rleft = 0;                 // this child's reserved record slots
-            bool fail = false;
             uint32_t guard = 0;
-            while (guard++ < (1u << 24)) {
+            if (lane == 0) sc[3] = (uint32_t)A;
+            while (!fail && guard++ < (1u << 24)) {
                 // combine the next level as soon as its sibling values are in;
                 // until then build one more level (the builder's chain of loads
                 // overlaps the evaluators' work instead of delaying the combining)
@@ -1513,6 +1532,8 @@ __global__ void __launch_bounds__(MAXT, 512 / MAXT) k_walk(DevPop d, GenBufs g, 
                         continue;
                     }
                 }
+                finish_level0();
+                if (fail) break;
                 const uint32_t slot = ncm % ring;
                 LevelDesc D = desc[slot];
                 if (stopped_w && (D.pent >= 0 || D.k > hneed)) break;
@@ -1614,7 +1635,10 @@ __global__ void __launch_bounds__(MAXT, 512 / MAXT) k_walk(DevPop d, GenBufs g, 
                     g.pv_rec[rbase + k] = make_uint4(0xFFFFFFFFu, 0u, 0u, 0u);
                     g.rec_entry[rbase + k] = 0xFFFFFFFFu;
                 }
-            (void)fail;
+            // a walk without levels (the child's root is the donated subtree, or
+            // the ancestors failed) still compares level 0
+            if (anc_ok && !fail) finish_level0();
+            if (fail && lane == 0) sc[4] = 1u;
             __threadfence_block();
             if (lane == 0) sc[8] = 1u;                      // evaluators stop
         } else {
@@ -1653,13 +1677,16 @@ __global__ void __launch_bounds__(MAXT, 512 / MAXT) k_walk(DevPop d, GenBufs g, 
                         load_vec<K>(par.slots, Cpad, D.pslot, v, cb);
                         store_blk<K>(mvs + slot * Cpad, cb, v);
                     }
+                    bool ab = false;
                     if (D.sib >= 0) load_vec<K>(par.slots, Cpad, D.sslot, v, cb);
                     else {
                         load_cases<K>(d, cb, ic.xv);
                         const uint32_t sh = (D.flags & LD_LEFT) ? (uint32_t)tdl : 0u;
-                        eval_run<K, V>(ok_, D.ss - sh, D.se - sh, stA, ic, v, d.status);
-                        if (cb == 0) st_interp += D.se - D.ss;
+                        // abandoned once the combination is over (the walk stopped below this level)
+                        eval_run<K, V>(ok_, D.ss - sh, D.se - sh, stA, ic, v, d.status, sc + 8, &ab);
+                        if (cb == 0 && !ab) st_interp += D.se - D.ss;
                     }
+                    if (ab) break;
                     store_blk<K>(svs + slot * Cpad, cb, v);
                 }
                 __threadfence_block();
@@ -1671,11 +1698,17 @@ __global__ void __launch_bounds__(MAXT, 512 / MAXT) k_walk(DevPop d, GenBufs g, 
         // the combiner's results, from warp 0 to the team
         if (tid == 0) { sc[9] = stopped_w ? 1u : 0u; sc[10] = (uint32_t)stop_level_w; sc[11] = levels_w; sc[12] = npv; sc[13] = nins_i; }
         __syncthreads();
+        const bool walk_failed = sc[4] != 0;
         stopped = sc[9] != 0;
         stop_level = (int32_t)sc[10];
         const uint32_t levels = sc[11];
+        const int32_t A = (int32_t)sc[3];
         npv = sc[12];
         nins_i = sc[13];
+        if (walk_failed) {                   // an inconsistency was recorded; the next synchronising call reports it
+            __syncthreads();
+            continue;
+        }
         // ---- fitness
         if (tid == 0) {
             g.stop[i] = stop_level;
@@ -2012,6 +2045,7 @@ __global__ void k_pv_scatter(DevPop d, GenBufs g) {
     for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
         const uint4 rec = g.pv_rec[r];
         if (rec.x >= d.P) continue;                     // a reserved slot left unused
+        if (rec.y >= g.pv_cnt[rec.x]) continue;         // a record of a walk that failed (not counted)
         g.pv_sorted[g.pv_off[rec.x] + rec.y] = make_uint4(rec.z, rec.w, g.pv_end[r], 0u);
     }
 }

@@ -328,9 +328,13 @@ __device__ __forceinline__ void apply_sel(uint32_t op, const float (&a)[K], cons
     }
 }
 
+// `stop` (optional): a shared word that, once nonzero, means the value is
+// no longer wanted (a walk that has stopped below this sibling's level); it
+// is read every 16 words and the run then ends early with *aborted set.
 template <int K, int V>
 __device__ __forceinline__ void interp_staged_lone(const uint8_t* stage, uint32_t s, uint32_t e, Istate<K>& st,
-                                                   const Ictx<K>& c) {
+                                                   const Ictx<K>& c, const volatile uint32_t* stop = nullptr,
+                                                   bool* aborted = nullptr) {
     const int lane = lane_id();
     const uint32_t a = s & ~15u;
     uint32_t p = e;
@@ -346,12 +350,15 @@ __device__ __forceinline__ void interp_staged_lone(const uint8_t* stage, uint32_
     const uint32_t stride = 32 * K * 4;
     const uint32_t sfast = sbase + (uint32_t)wfast * stride;
     bool under = false;
+    uint32_t words = 0;
     while (p >= s + 4) {
+        if (stop && (++words & 15u) == 0 && *stop) { *aborted = true; return; }
         if (st.sp >= 0 && st.sp <= wfast) {
             uint32_t sa = sbase + (uint32_t)st.sp * stride;
             float t1[K];
             lds_vec<K>(sa - stride, t1);        // the top entry (below the base when the stack is empty: unused)
             do {
+                if (stop && (++words & 15u) == 0 && *stop) { *aborted = true; return; }
                 const uint32_t w = lds_u32(wa + p - 4);
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
