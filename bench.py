@@ -105,6 +105,8 @@ def parse():
     ap.add_argument("--autotune", dest="autotune", action="store_true", default=True)
     ap.add_argument("--no-autotune", dest="autotune", action="store_false")
     ap.add_argument("--cache-budget-gb", type=int, default=40, help="device memory for cached value vectors")
+    ap.add_argument("--graph-reserve", type=int, default=0,
+                    help="cache entries reserved for the captured generations (0: twice the current count + 64 per tree)")
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu", action="store_true")
@@ -603,7 +605,7 @@ def main():
     fit0 = None if (boolean or integer) else pop.fitness().copy()     # the initial trees' fitness, for the FP64 comparison
     full_ms, full_st = timed(pop.eval_full, 3) if generational else (None, None)
     if chunk:
-        pop.set_graph_mode(True)         # pre-sized caches, no host syncs in the loop
+        pop.set_graph_mode(True, args.graph_reserve)   # pre-sized caches, no host syncs in the loop
         pop.eval_full()
 
     gen = [0]
@@ -674,6 +676,8 @@ def main():
         line["config"]["long_walks"] = args.long_walks
     if args.stack_window:
         line["config"]["stack_window"] = args.stack_window
+    if args.graph_reserve:
+        line["config"]["graph_reserve_entries"] = args.graph_reserve
     if args.lazy_inplace:
         line["config"]["lazy_inplace"] = True
     if args.arena_buffers:
