@@ -1776,27 +1776,21 @@ struct OnePassSmem {
 };
 
 // Assemble child i's bytes [0, nk) in `stage` (warp-collective): from its
-// three pieces in fitness-first order, else from its own buffer.
+// three pieces in fitness-first order -- the mother's head, the donated
+// subtree (gathered into the fragment pool at crossover), the mother's tail
+// -- 16 destination bytes per lane at a time (the copy kernel's quads),
+// else from its own buffer.
 __device__ __forceinline__ void stage_child(const DevPop& d, const GenBufs& g, uint32_t i, uint32_t nk, uint8_t* stage) {
     const int lane = lane_id();
     __syncwarp();
     if (g.lazy) {
-        const uint32_t m = g.mother[i], c = g.cpos[i], s = g.ssz[i], dd = g.dpos[i];
+        const uint32_t m = g.mother[i];
         const uint8_t* mb = d.arena + (size_t)g.pbuf[m] * d.cap;
-        const uint8_t* fb = d.arena + (size_t)g.pbuf[g.father[i]] * d.cap;
-        const int32_t tdl = (int32_t)s - (int32_t)g.rsz[i];
-        // four loads in flight per lane before the stores
-        for (uint32_t x0 = lane; x0 < nk; x0 += 128) {
-            uint8_t b[4];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const uint32_t x = x0 + 32 * j;
-                b[j] = x < nk ? (x < c ? mb[x] : (x < c + s ? fb[dd + (x - c)] : mb[x - tdl])) : (uint8_t)0;
-            }
-#pragma unroll
-            for (int j = 0; j < 4; ++j)
-                if (x0 + 32 * j < nk) stage[x0 + 32 * j] = b[j];
-        }
+        const bool clone = (g.flags[i] & F_CLONE) != 0;
+        const uint32_t c = clone ? nk : g.cpos[i], r = clone ? 0 : g.rsz[i], s = clone ? 0 : g.ssz[i];
+        const uint8_t* fr = g.frag + (clone ? 0 : g.frag_off[i]);
+        for (uint32_t q = lane; q < (nk + 15) / 16; q += 32)
+            reinterpret_cast<uint4*>(stage)[q] = child_quad(mb, fr, 16 * q, c, r, s, nk);
     } else {
         stage_issue(stage, d.arena + (size_t)d.buf[i] * d.cap, 0, nk);
         cp_async_commit();
@@ -2463,8 +2457,29 @@ __global__ void k_child_sizes(DevPop d, GenBufs g) {
 // flag and a constant.
 __global__ void k_mlp_features(DevPop d, GenBufs g, CacheView par, MlpBufs b) {
     if (halted(d)) return;
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < d.P; i += gridDim.x * blockDim.x) {
-        const uint32_t m = g.mother[i], f = g.father[i], c = g.cpos[i], r = g.rsz[i], dd = g.dpos[i], s = g.ssz[i];
+    // a warp per child: the lanes share the spread of the two root vectors
+    const int lane = lane_id();
+    const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nwp = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t i = gw; i < d.P; i += nwp) {
+        const uint32_t m = g.mother[i], f = g.father[i];
+        float spread[2];
+        for (int q = 0; q < 2; ++q) {
+            const uint32_t t = q ? f : m;
+            const float* v = par.slots + (size_t)par.e_slot[par.e_off[t]] * d.Cpad;
+            float lo = INFINITY, hi = -INFINITY;
+            for (uint32_t cc = lane; cc < d.C; cc += 32) {
+                const float a = (d.vkind == VI) ? (float)__float_as_int(v[cc]) : v[cc];
+                if (isfinite(a)) { lo = fminf(lo, a); hi = fmaxf(hi, a); }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                lo = fminf(lo, __shfl_xor_sync(FULL, lo, o));
+                hi = fmaxf(hi, __shfl_xor_sync(FULL, hi, o));
+            }
+            spread[q] = (hi >= lo) ? fminf(log2f(1.f + (hi - lo)) / 8.f, 4.f) : 4.f;
+        }
+        if (lane != 0) continue;
+        const uint32_t c = g.cpos[i], r = g.rsz[i], dd = g.dpos[i], s = g.ssz[i];
         const float sm = (float)g.psize[m], sf = (float)g.psize[f];
         float* x = b.feat + (size_t)i * MLP_IN;
         const float dl = (float)s - (float)r;
@@ -2481,17 +2496,6 @@ __global__ void k_mlp_features(DevPop d, GenBufs g, CacheView par, MlpBufs b) {
         x[9] = isfinite(fm) ? fminf(log2f(1.f + fabsf(fm)) / 8.f, 4.f) : 4.f;
         x[10] = isfinite(ff) ? fminf(log2f(1.f + fabsf(ff)) / 8.f, 4.f) : 4.f;
         x[11] = log2f(1.f + (float)(par.e_off[m + 1] - par.e_off[m])) / 16.f;
-        float spread[2];
-        for (int q = 0; q < 2; ++q) {
-            const uint32_t t = q ? f : m;
-            const float* v = par.slots + (size_t)par.e_slot[par.e_off[t]] * d.Cpad;
-            float lo = INFINITY, hi = -INFINITY;
-            for (uint32_t cc = 0; cc < d.C; ++cc) {
-                const float a = (d.vkind == VI) ? (float)__float_as_int(v[cc]) : v[cc];
-                if (isfinite(a)) { lo = fminf(lo, a); hi = fmaxf(hi, a); }
-            }
-            spread[q] = (hi >= lo) ? fminf(log2f(1.f + (hi - lo)) / 8.f, 4.f) : 4.f;
-        }
         x[12] = spread[0];
         x[13] = spread[1];
         x[14] = (g.flags[i] & F_CLONE) ? 1.f : 0.f;

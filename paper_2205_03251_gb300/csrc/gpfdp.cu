@@ -1482,7 +1482,7 @@ int launch_pack(gp_pop* pop, const CacheView& par) {
     CK(cudaStreamWaitEvent(ms, pop->pfork_ev, 0));
     phase_begin(pop, PH_PACK, ms);
     const int pb = (d.P + 255) / 256;
-    k_mlp_features<<<pb, 256, 0, ms>>>(d, g, par, pop->mlp);
+    k_mlp_features<<<(d.P + 7) / 8, 256, 0, ms>>>(d, g, par, pop->mlp);
     const int mb = (d.P + 7) / 8 < pop->nsm * 2 ? (d.P + 7) / 8 : pop->nsm * 2;   // 8 samples per CTA pass
     k_mlp_infer<<<mb, 256, 0, ms>>>(pop->mlp, d.P, pop->mlp.pred_pack);
     const dim3 rg((d.P + 255) / 256, (d.P + RANK_TILE - 1) / RANK_TILE);
