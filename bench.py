@@ -449,10 +449,10 @@ def graph_chunk(k: int) -> int:
 
 
 def run_packing(args):
-    """Learned against static packing: the same generations (same seed) with
-    the MLP order and with the mother-size order, the walk limited to
-    --walk-warps warps so that children queue for teams; fitness must come
-    out bit-identical."""
+    """Learned against static packing and against no packing: the same
+    generations (same seed) with the MLP order, the mother-size order and
+    the children's own order, the walk limited to --walk-warps warps so that
+    children queue for teams; fitness must come out bit-identical."""
     import torch
     import paper_2205_03251_gb300 as gp
     gp.build()
@@ -463,7 +463,7 @@ def run_packing(args):
     chunk = graph_chunk(args.steps) or 2
     steps = (args.steps // chunk) * chunk
     arms = {}
-    for name in ("mlp", "static"):
+    for name in ("mlp", "static", "none"):
         pop = gp.Population(w["x"], w["t"], w["consts"], w["ops"], w["off"], max_nodes=1 << 21,
                             cache_threshold=args.threshold, seed=0x5EED, stream=stream, packing=PACKING[name],
                             walk_warps=args.walk_warps)
@@ -489,18 +489,21 @@ def run_packing(args):
         arms[name] = {"ms": ms, "equivalent": st["cum_equivalent_ops"], "fitness": pop.fitness().copy(),
                       "walk_ms": dict(zip(gp.PHASES, st["ms"]))["walk"], "pack": pop.pack_info()}
         pop.close()
-    m, s_ = arms["mlp"], arms["static"]
+    m, s_, n_ = arms["mlp"], arms["static"], arms["none"]
     value = m["equivalent"] / (m["ms"] * 1e-3) / 1e9
     pred, meas, key, order, loss = m["pack"]
     line = {"metric": METRIC, "value": value, "unit": "GPop/s", "n_gpus": 1, "steps": steps,
             "warmup": args.warmup, "ms_per_step": m["ms"] / steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": dict(workload_config(args, w), packing="mlp vs static", walk_warps=args.walk_warps,
+            "config": dict(workload_config(args, w), packing="mlp vs static vs none", walk_warps=args.walk_warps,
                            execution=f"CUDA graphs of {chunk} generations, {steps // chunk} replays per arm"),
             "static_value": s_["equivalent"] / (s_["ms"] * 1e-3) / 1e9,
+            "none_value": n_["equivalent"] / (n_["ms"] * 1e-3) / 1e9,
             "mlp_over_static": s_["ms"] / m["ms"],
-            "walk_ms_last_replay": {"mlp": m["walk_ms"], "static": s_["walk_ms"]},
-            "fitness_identical": bool(m["fitness"].tobytes() == s_["fitness"].tobytes()),
+            "mlp_over_none": n_["ms"] / m["ms"],
+            "static_over_none": n_["ms"] / s_["ms"],
+            "walk_ms_last_replay": {"mlp": m["walk_ms"], "static": s_["walk_ms"], "none": n_["walk_ms"]},
+            "fitness_identical": bool(m["fitness"].tobytes() == s_["fitness"].tobytes() == n_["fitness"].tobytes()),
             "mlp_loss_last": float(loss)}
     print(json.dumps(line), flush=True)
 

@@ -137,3 +137,36 @@ __device__ __forceinline__ float fitness_of(const DevPop& d, F at) {
     for (uint32_t j = 0; j < d.C; ++j) f = __fadd_rn(f, fabsf(__fsub_rn(at(j), d.t[j])));
     return f;
 }
+
+// fitness_of with the whole warp (all 32 lanes call it; every lane returns
+// the fitness): the lanes fetch and form the terms of 32 cases at a time in
+// parallel, and every lane adds them in case order from shuffles, so the
+// binary32 sum is rounded in the same order and has the same bits; the
+// Boolean and integer sums are exact, so their order does not matter.
+template <typename F>
+__device__ __forceinline__ float fitness_warp(const DevPop& d, F at) {
+    const uint32_t lane = threadIdx.x & 31u;
+    if (d.vkind == VB) {
+        uint32_t e = 0;
+        for (uint32_t j = lane; j < d.C; j += 32) e += __popc(__float_as_uint(at(j)) ^ __float_as_uint(d.t[j]));
+        return (float)__reduce_add_sync(FULL, e);
+    }
+    if (d.vkind == VI) {
+        long long s = 0;
+        for (uint32_t j = lane; j < d.C; j += 32) {
+            const long long e = (long long)__float_as_int(at(j)) - (long long)__float_as_int(d.t[j]);
+            s += e < 0 ? -e : e;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(FULL, s, o);
+        return __ll2float_rn(s);
+    }
+    float f = 0.0f;
+    for (uint32_t b = 0; b < d.C; b += 32) {
+        const uint32_t j = b + lane;
+        const float term = (j < d.C) ? fabsf(__fsub_rn(at(j), d.t[j])) : 0.0f;
+        const uint32_t n = min(32u, d.C - b);
+        for (uint32_t q = 0; q < n; ++q) f = __fadd_rn(f, __shfl_sync(FULL, term, q));
+    }
+    return f;
+}

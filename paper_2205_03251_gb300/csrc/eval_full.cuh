@@ -182,16 +182,17 @@ __global__ void __launch_bounds__(GP_WARPS * 32) k_eval_skeleton(DevPop d) {
     }
 }
 
-// Fitness of every tree from its root's cached vector (fitness_of).
+// Fitness of every tree from its root's cached vector (a warp per tree).
 __global__ void k_fitness(DevPop d) {
     if (halted(d)) return;
     const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
     if (d.e_off[d.P] > d.Ecap) return;
     for (uint32_t tree = gw; tree < d.P; tree += nw) {
+        const float* v = d.slots + (size_t)d.e_slot[d.e_off[tree]] * d.Cpad;
+        const float f = fitness_warp(d, [&](uint32_t j) { return __ldcg(v + j); });
         if (lane_id() == 0) {
-            const float* v = d.slots + (size_t)d.e_slot[d.e_off[tree]] * d.Cpad;
-            d.fit[tree] = fitness_of(d, [&](uint32_t j) { return __ldcg(v + j); });
+            d.fit[tree] = f;
             atomicAdd(&d.acc_ops[1], (unsigned long long)d.size[tree]);
         }
     }

@@ -2009,7 +2009,8 @@ __global__ void __launch_bounds__(GP_WARPS * 32) k_onepass_eval(DevPop d, GenBuf
         if (lane == 0) last = (atomicAdd(&g.small_cnt[i], 1u) == ncb - 1) ? 1u : 0u;
         if (!__shfl_sync(FULL, last, 0)) continue;
         __threadfence();
-        if (lane == 0) d.fit[i] = fitness_of(d, [&](uint32_t j) { return __ldcg(row + j); });
+        const float fv = fitness_warp(d, [&](uint32_t j) { return __ldcg(row + j); });
+        if (lane == 0) d.fit[i] = fv;
     }
     if (lane == 0 && st_interp) atomicAdd(&g.gstat[G_INTERP], st_interp);
 }

@@ -204,12 +204,129 @@ __device__ __forceinline__ void step_checked(uint32_t op, Istate<K>& st, const I
     }
 }
 
+// The binary32 node of the fast path written with branches declared
+// uniform (bra.uni): the opcode is the same in every lane of the warp (all
+// lanes read it from the same shared word), so no branch needs the
+// reconvergence bookkeeping of a possibly divergent one.  Same operations
+// on the same operands as the C++ form below: a leaf pushes the running
+// value and loads x or its constant; a function pops its right operand and
+// applies + (subtraction as addition of the negated operand, which IEEE 754
+// defines it to be), x, or protected division (1 for a zero divisor of
+// either sign, else the round-to-nearest quotient), never contracted.
+#define GP_SF_LEAF_SEL(k, xk) "selp.f32 %" #k ", %" #xk ", cv, pq;\n\t"
+template <int K>
+__device__ __forceinline__ void step_fast_f32(uint32_t op, float (&acc)[K], uint32_t& sa, uint32_t kca,
+                                              const float (&xv)[K]) {
+    if constexpr (K == 1) {
+        asm volatile(
+            "{\n\t.reg .pred pf, pq, pz;\n\t.reg .f32 r0, cv;\n\t.reg .u32 ca;\n\t"
+            "setp.lt.u32 pf, %2, 4;\n\t"
+            "@pf bra.uni SF_FN;\n\t"
+            "st.shared.f32 [%1], %0;\n\t"
+            "add.u32 %1, %1, 128;\n\t"
+            "shl.b32 ca, %2, 2;\n\tadd.u32 ca, ca, %3;\n\t"
+            "ld.shared.f32 cv, [ca];\n\t"
+            "setp.eq.u32 pq, %2, 4;\n\t" GP_SF_LEAF_SEL(0, 4)
+            "bra.uni SF_END;\n"
+            "SF_FN:\n\t"
+            "sub.u32 %1, %1, 128;\n\t"
+            "ld.shared.f32 r0, [%1];\n\t"
+            "setp.lt.u32 pq, %2, 2;\n\t"
+            "@pq bra.uni SF_AS;\n\t"
+            "setp.eq.u32 pq, %2, 2;\n\t"
+            "@!pq bra.uni SF_DV;\n\t"
+            "mul.rn.f32 %0, %0, r0;\n\t"
+            "bra.uni SF_END;\n"
+            "SF_DV:\n\t"
+            "setp.eq.f32 pz, r0, 0f00000000;\n\tdiv.rn.f32 %0, %0, r0;\n\t@pz mov.f32 %0, 0f3F800000;\n\t"
+            "bra.uni SF_END;\n"
+            "SF_AS:\n\t"
+            "setp.eq.u32 pq, %2, 1;\n\t"
+            "@pq neg.f32 r0, r0;\n\t"
+            "add.rn.f32 %0, %0, r0;\n"
+            "SF_END:\n\t}"
+            : "+f"(acc[0]), "+r"(sa)
+            : "r"(op), "r"(kca), "f"(xv[0]));
+    } else if constexpr (K == 2) {
+        asm volatile(
+            "{\n\t.reg .pred pf, pq, pz;\n\t.reg .f32 r0, r1, cv;\n\t.reg .u32 ca;\n\t"
+            "setp.lt.u32 pf, %3, 4;\n\t"
+            "@pf bra.uni SF_FN;\n\t"
+            "st.shared.v2.f32 [%2], {%0, %1};\n\t"
+            "add.u32 %2, %2, 256;\n\t"
+            "shl.b32 ca, %3, 2;\n\tadd.u32 ca, ca, %4;\n\t"
+            "ld.shared.f32 cv, [ca];\n\t"
+            "setp.eq.u32 pq, %3, 4;\n\t" GP_SF_LEAF_SEL(0, 5) GP_SF_LEAF_SEL(1, 6)
+            "bra.uni SF_END;\n"
+            "SF_FN:\n\t"
+            "sub.u32 %2, %2, 256;\n\t"
+            "ld.shared.v2.f32 {r0, r1}, [%2];\n\t"
+            "setp.lt.u32 pq, %3, 2;\n\t"
+            "@pq bra.uni SF_AS;\n\t"
+            "setp.eq.u32 pq, %3, 2;\n\t"
+            "@!pq bra.uni SF_DV;\n\t"
+            "mul.rn.f32 %0, %0, r0;\n\tmul.rn.f32 %1, %1, r1;\n\t"
+            "bra.uni SF_END;\n"
+            "SF_DV:\n\t"
+            "setp.eq.f32 pz, r0, 0f00000000;\n\tdiv.rn.f32 %0, %0, r0;\n\t@pz mov.f32 %0, 0f3F800000;\n\t"
+            "setp.eq.f32 pz, r1, 0f00000000;\n\tdiv.rn.f32 %1, %1, r1;\n\t@pz mov.f32 %1, 0f3F800000;\n\t"
+            "bra.uni SF_END;\n"
+            "SF_AS:\n\t"
+            "setp.eq.u32 pq, %3, 1;\n\t"
+            "@pq neg.f32 r0, r0;\n\t@pq neg.f32 r1, r1;\n\t"
+            "add.rn.f32 %0, %0, r0;\n\tadd.rn.f32 %1, %1, r1;\n"
+            "SF_END:\n\t}"
+            : "+f"(acc[0]), "+f"(acc[1]), "+r"(sa)
+            : "r"(op), "r"(kca), "f"(xv[0]), "f"(xv[1]));
+    } else {
+        static_assert(K == 4, "cases per lane: 1, 2 or 4");
+        asm volatile(
+            "{\n\t.reg .pred pf, pq, pz;\n\t.reg .f32 r0, r1, r2, r3, cv;\n\t.reg .u32 ca;\n\t"
+            "setp.lt.u32 pf, %5, 4;\n\t"
+            "@pf bra.uni SF_FN;\n\t"
+            "st.shared.v4.f32 [%4], {%0, %1, %2, %3};\n\t"
+            "add.u32 %4, %4, 512;\n\t"
+            "shl.b32 ca, %5, 2;\n\tadd.u32 ca, ca, %6;\n\t"
+            "ld.shared.f32 cv, [ca];\n\t"
+            "setp.eq.u32 pq, %5, 4;\n\t" GP_SF_LEAF_SEL(0, 7) GP_SF_LEAF_SEL(1, 8) GP_SF_LEAF_SEL(2, 9)
+            GP_SF_LEAF_SEL(3, 10)
+            "bra.uni SF_END;\n"
+            "SF_FN:\n\t"
+            "sub.u32 %4, %4, 512;\n\t"
+            "ld.shared.v4.f32 {r0, r1, r2, r3}, [%4];\n\t"
+            "setp.lt.u32 pq, %5, 2;\n\t"
+            "@pq bra.uni SF_AS;\n\t"
+            "setp.eq.u32 pq, %5, 2;\n\t"
+            "@!pq bra.uni SF_DV;\n\t"
+            "mul.rn.f32 %0, %0, r0;\n\tmul.rn.f32 %1, %1, r1;\n\tmul.rn.f32 %2, %2, r2;\n\tmul.rn.f32 %3, %3, r3;\n\t"
+            "bra.uni SF_END;\n"
+            "SF_DV:\n\t"
+            "setp.eq.f32 pz, r0, 0f00000000;\n\tdiv.rn.f32 %0, %0, r0;\n\t@pz mov.f32 %0, 0f3F800000;\n\t"
+            "setp.eq.f32 pz, r1, 0f00000000;\n\tdiv.rn.f32 %1, %1, r1;\n\t@pz mov.f32 %1, 0f3F800000;\n\t"
+            "setp.eq.f32 pz, r2, 0f00000000;\n\tdiv.rn.f32 %2, %2, r2;\n\t@pz mov.f32 %2, 0f3F800000;\n\t"
+            "setp.eq.f32 pz, r3, 0f00000000;\n\tdiv.rn.f32 %3, %3, r3;\n\t@pz mov.f32 %3, 0f3F800000;\n\t"
+            "bra.uni SF_END;\n"
+            "SF_AS:\n\t"
+            "setp.eq.u32 pq, %5, 1;\n\t"
+            "@pq neg.f32 r0, r0;\n\t@pq neg.f32 r1, r1;\n\t@pq neg.f32 r2, r2;\n\t@pq neg.f32 r3, r3;\n\t"
+            "add.rn.f32 %0, %0, r0;\n\tadd.rn.f32 %1, %1, r1;\n\tadd.rn.f32 %2, %2, r2;\n\tadd.rn.f32 %3, %3, r3;\n"
+            "SF_END:\n\t}"
+            : "+f"(acc[0]), "+f"(acc[1]), "+f"(acc[2]), "+f"(acc[3]), "+r"(sa)
+            : "r"(op), "r"(kca), "f"(xv[0]), "f"(xv[1]), "f"(xv[2]), "f"(xv[3]));
+    }
+}
+#undef GP_SF_LEAF_SEL
+
 // One node when the whole stack access stays inside the shared window;
 // sa is this lane's next free stack entry, kca the constant table and kba
 // the Boolean input patterns (shared-window addresses).
 template <int K, int V = VF>
 __device__ __forceinline__ void step_fast(uint32_t op, float (&acc)[K], uint32_t& sa, uint32_t kca, uint32_t kba,
                                           const Ictx<K>& c) {
+    if constexpr (V == VF) {
+        step_fast_f32<K>(op, acc, sa, kca, c.xv);
+        return;
+    }
     if (op >= 4) {
         sts_vec<K>(sa, acc);
         sa += 32 * K * 4;
@@ -258,7 +375,9 @@ __device__ __forceinline__ void interp_staged(const uint8_t* stage, uint32_t s, 
     const uint32_t kca = (uint32_t)__cvta_generic_to_shared(c.kc);
     const uint32_t kba = (V == VB) ? (uint32_t)__cvta_generic_to_shared(c.kb) : 0u;
     const int wfast = c.W - 4;
-    const uint32_t sfast = sbase + (uint32_t)wfast * 32 * K * 4;
+    // one unsigned test per word: the depth is within [0, wfast] (below the
+    // bottom the difference wraps to a large value)
+    const uint32_t span = (uint32_t)wfast * 32 * K * 4;
     bool under = false;
     while (p >= s + 4) {
         if (st.sp >= 0 && st.sp <= wfast) {
@@ -269,9 +388,9 @@ __device__ __forceinline__ void interp_staged(const uint8_t* stage, uint32_t s, 
                 step_fast<K, V>((w >> 16) & 0xFFu, st.acc, sa, kca, kba, c);
                 step_fast<K, V>((w >> 8) & 0xFFu, st.acc, sa, kca, kba, c);
                 step_fast<K, V>(w & 0xFFu, st.acc, sa, kca, kba, c);
-                under |= ((int32_t)(sa - sbase) < 0);
                 p -= 4;
-            } while (p >= s + 4 && (int32_t)(sa - sfast) <= 0 && (int32_t)(sa - sbase) >= 0);
+            } while (p >= s + 4 && sa - sbase <= span);
+            under |= ((int32_t)(sa - sbase) < 0);
             st.sp = (int32_t)(sa - sbase) / (32 * K * 4);
         } else {
             const uint32_t w = wp[(p - 4 - a) >> 2];
@@ -438,7 +557,7 @@ __device__ __forceinline__ void interp_staged_capture(const uint8_t* stage, uint
     const uint32_t kca = (uint32_t)__cvta_generic_to_shared(c.kc);
     const uint32_t kba = (V == VB) ? (uint32_t)__cvta_generic_to_shared(c.kb) : 0u;
     const int wfast = c.W - 4;
-    const uint32_t sfast = sbase + (uint32_t)wfast * 32 * K * 4;
+    const uint32_t span = (uint32_t)wfast * 32 * K * 4;
     bool under = false;
     while (p >= 4) {
         if (nextp >= (int32_t)p - 4) {
@@ -458,9 +577,9 @@ __device__ __forceinline__ void interp_staged_capture(const uint8_t* stage, uint
                 step_fast<K, V>((w >> 16) & 0xFFu, st.acc, sa, kca, kba, c);
                 step_fast<K, V>((w >> 8) & 0xFFu, st.acc, sa, kca, kba, c);
                 step_fast<K, V>(w & 0xFFu, st.acc, sa, kca, kba, c);
-                under |= ((int32_t)(sa - sbase) < 0);
                 p -= 4;
-            } while (p >= 4 && nextp < (int32_t)p - 4 && (int32_t)(sa - sfast) <= 0 && (int32_t)(sa - sbase) >= 0);
+            } while (p >= 4 && nextp < (int32_t)p - 4 && sa - sbase <= span);
+            under |= ((int32_t)(sa - sbase) < 0);
             st.sp = (int32_t)(sa - sbase) / (32 * K * 4);
         } else {
             const uint32_t w = lds_u32(wa + p - 4);
