@@ -1757,23 +1757,63 @@ __global__ void __launch_bounds__(MAXT, 512 / MAXT) k_walk(DevPop d, GenBufs g, 
 // (the deepest stack of the right-to-left scan is max S + 1 <= n / 2 + 1
 // entries: the one-pass warps have overflow stacks that deep of their own,
 // so they run beside the walk).  k_onepass_eval (a warp per child
-// and case block, the full-evaluation launch shape) interprets the child
-// and writes each recorded ancestor's values as the scan passes it; the
+// and case block, CTAs of 4 warps) interprets the child a piece of
+// OP_CHUNK bytes at a time and writes each recorded ancestor's values as
+// the scan passes it; the
 // warp that completes a child's last case block writes its fitness.  Which
 // children take this path is decided at crossover (size at most
 // onepass_max, not a clone); the walk skips them.  Disruption recording
 // walks every child.
-#define ONEPASS_MAX 4096                 // most nodes of a child evaluated in one pass (2 staging buffers)
+#define ONEPASS_MAX 4096                 // most nodes of a child evaluated in one pass
 #define OP_BUCKETS 13                    // size buckets floor(log2(n)), n <= 4096
 #define ONEPASS_DEPTH (ONEPASS_MAX / 2 + 4)   // overflow stack entries per one-pass warp
 #define ONEPASS_WARPS 4                  // warps per CTA of the plan kernel
-#define OP_STAGE (2 * STAGE_BYTES)       // staged bytes per warp
+#define OP_STAGE (2 * STAGE_BYTES)       // staged bytes per warp of the plan kernel (a whole child)
+#define OP_EVAL_WARPS 4                  // warps per CTA of k_onepass_eval
+#define OP_CHUNK 1024                    // bytes of a child staged at a time by k_onepass_eval
+#define OP_CTAS_PER_SM 6                 // at most this many k_onepass_eval CTAs per SM (24 warps)
+
+// Shared memory of a k_onepass_eval CTA: the constant and Boolean-input
+// tables, then per warp a staged piece of the child (OP_CHUNK bytes, at
+// least four stack entries so that a malformed run's underflow stays in the
+// warp's own region) followed by its stack window.  Staging the child a
+// piece at a time (instead of whole) leaves room for more warps per SM.
+template <int K>
+struct OnePassEvalLayout {
+    static constexpr size_t stage_bytes = (OP_CHUNK > 4 * 32 * K * 4) ? OP_CHUNK : 4 * 32 * K * 4;
+    __host__ __device__ static size_t warp_bytes(int W) { return stage_bytes + SmemLayout<K>::stack_bytes(W); }
+    __host__ __device__ static size_t total(int W) { return SmemLayout<K>::kc_bytes + OP_EVAL_WARPS * warp_bytes(W); }
+};
 
 struct OnePassSmem {
     uint8_t stage[ONEPASS_WARPS][OP_STAGE];
     int16_t S[ONEPASS_WARPS][ONEPASS_MAX + 8];     // balance before position q, then prefix minima after c
     uint16_t anc[ONEPASS_WARPS][ONEPASS_MAX / 2 + 8];   // ancestors of c (function nodes), nearest first
 };
+
+// Assemble bytes [lo, hi) of child i (lo a multiple of 16, hi - lo <=
+// OP_CHUNK) in `stage` (warp-collective), as stage_child below does for
+// the whole child.
+__device__ __forceinline__ void stage_child_piece(const DevPop& d, const GenBufs& g, uint32_t i, uint32_t nk,
+                                                  uint32_t lo, uint32_t hi, uint8_t* stage) {
+    const int lane = lane_id();
+    __syncwarp();
+    if (g.lazy) {
+        const uint32_t m = g.mother[i];
+        const uint8_t* mb = d.arena + (size_t)g.pbuf[m] * d.cap;
+        const bool clone = (g.flags[i] & F_CLONE) != 0;
+        const uint32_t c = clone ? nk : g.cpos[i], r = clone ? 0 : g.rsz[i], s = clone ? 0 : g.ssz[i];
+        const uint8_t* fr = g.frag + (clone ? 0 : g.frag_off[i]);
+        const uint32_t q0 = lo / 16, q1 = (hi + 15) / 16;
+        for (uint32_t q = q0 + lane; q < q1; q += 32)
+            reinterpret_cast<uint4*>(stage)[q - q0] = child_quad(mb, fr, 16 * q, c, r, s, nk);
+    } else {
+        stage_issue(stage, d.arena + (size_t)d.buf[i] * d.cap, lo, hi);
+        cp_async_commit();
+        cp_async_wait<0>();
+    }
+    __syncwarp();
+}
 
 // Assemble child i's bytes [0, nk) in `stage` (warp-collective): from its
 // three pieces in fitness-first order -- the mother's head, the donated
@@ -1946,7 +1986,7 @@ __global__ void __launch_bounds__(ONEPASS_WARPS * 32) k_onepass_plan(DevPop d, G
 }
 
 template <int K, int V>
-__global__ void __launch_bounds__(GP_WARPS * 32) k_onepass_eval(DevPop d, GenBufs g) {
+__global__ void __launch_bounds__(OP_EVAL_WARPS * 32, 1) k_onepass_eval(DevPop d, GenBufs g) {
     if (halted(d)) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float* kc = reinterpret_cast<float*>(smem_raw);
@@ -1954,15 +1994,13 @@ __global__ void __launch_bounds__(GP_WARPS * 32) k_onepass_eval(DevPop d, GenBuf
     fill_kc(kc, d.consts);
     fill_kb(kc + 256);
     __syncthreads();
-    unsigned char* wbase = smem_raw + SmemLayout<K>::kc_bytes + (size_t)warp * SmemLayout<K>::warp_bytes((int)d.W);
+    uint8_t* const stage = smem_raw + SmemLayout<K>::kc_bytes + (size_t)warp * OnePassEvalLayout<K>::warp_bytes((int)d.W);
     Ictx<K> ic;
-    ic.s = reinterpret_cast<float*>(wbase);
+    ic.s = reinterpret_cast<float*>(stage + OnePassEvalLayout<K>::stage_bytes);
     ic.W = (int)d.W;
-    ic.maxd = (int)d.maxdepth;
     ic.kc = kc;
     ic.kb = kc + 256;
-    uint8_t* const stage = wbase + SmemLayout<K>::stack_bytes((int)d.W);     // both staging buffers: 4,224 bytes
-    const uint32_t gwarp = blockIdx.x * GP_WARPS + warp;
+    const uint32_t gwarp = blockIdx.x * OP_EVAL_WARPS + warp;
     // a child of at most ONEPASS_MAX nodes needs at most ONEPASS_MAX / 2 + 1 stack entries
     ic.maxd = (int)d.W + ONEPASS_DEPTH;
     ic.g = g.ovf_op + (size_t)gwarp * ONEPASS_DEPTH * 32 * K;
@@ -1987,7 +2025,6 @@ __global__ void __launch_bounds__(GP_WARPS * 32) k_onepass_eval(DevPop d, GenBuf
         i = __shfl_sync(FULL, i, 0);
         cb = __shfl_sync(FULL, cb, 0);
         const uint32_t nk = d.size[i];
-        stage_child(d, g, i, nk, stage);
         load_cases<K>(d, cb, ic.xv);
         Istate<K> st;
 #pragma unroll
@@ -1995,9 +2032,18 @@ __global__ void __launch_bounds__(GP_WARPS * 32) k_onepass_eval(DevPop d, GenBuf
         st.sp = 0;
         st.ok = true;
         const uint32_t base = g.op_base[i], R = g.pv_cnt[i];
-        interp_staged_capture<K, V>(stage, nk, st, ic, R,
-            [&](uint32_t k) { return g.pv_rec[base + k].z; },
-            [&](uint32_t k) { store_blk<K>(g.pv_val + (size_t)(base + k) * Cpad, cb, st.acc); });
+        auto pos = [&](uint32_t k) { return g.pv_rec[base + k].z; };
+        auto cap = [&](uint32_t k) { store_blk<K>(g.pv_val + (size_t)(base + k) * Cpad, cb, st.acc); };
+        CaptureCursor cur{0u, R ? (int32_t)pos(0) : -1};
+        bool under = false;
+        // the child a piece at a time, right to left (pieces end on multiples of OP_CHUNK)
+        for (uint32_t hi = nk; hi > 0;) {
+            const uint32_t lo = (hi - 1) & ~(uint32_t)(OP_CHUNK - 1);
+            stage_child_piece(d, g, i, nk, lo, hi, stage);
+            interp_capture_range<K, V>(stage, lo, hi, st, ic, R, cur, under, pos, cap);
+            hi = lo;
+        }
+        if (under || st.sp != 1) st.ok = false;
         if (!st.ok && lane == 0) set_status(d.status, ST_STACK);
         float* row = g.small_val + (size_t)i * Cpad;
         store_blk<K>(row, cb, st.acc);

@@ -99,6 +99,7 @@ struct gp_pop {
     cudaEvent_t ofork_ev, ojoin_ev;   // one-pass fork / join
     cudaEvent_t xfork_ev[2], xjoin_ev[2];   // cache update: records beside counts, links beside the slot pool
     int grid_onepass;                 // CTAs of the one-pass interpreter (each with its own overflow stacks)
+    size_t smem_onepass;              // its dynamic shared memory per CTA
     uint32_t* rank;                   // [P] work-order ranks
     int prio_high;                    // greatest stream priority of the device (the large teams' launch)
     MlpBufs mlp;
@@ -276,12 +277,24 @@ int setup_items_kernel(gp_pop* pop) {
         return fail(pop, GP_EINVAL, "stack_window %u x cases_per_lane %u needs %zu bytes of shared memory per CTA (%d)",
                     pop->d.W, pop->d.K, smem, max_optin);
     CK(cudaFuncSetAttribute(k_eval_items<K, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    CK(cudaFuncSetAttribute(k_onepass_eval<K, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int nb = 0;
     CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_eval_items<K, V>, GP_WARPS * 32, smem));
     if (nb < 1) nb = 1;
     pop->grid_items = nb * pop->nsm;
     pop->smem_items = smem;
+    // the one-pass interpreter: CTAs of OP_EVAL_WARPS warps, as many as fit
+    // (at most OP_CTAS_PER_SM per SM), each warp with its own overflow stack
+    const size_t smem_op = OnePassEvalLayout<K>::total((int)pop->d.W);
+    if (smem_op > (size_t)max_optin)
+        return fail(pop, GP_EINVAL, "stack_window %u x cases_per_lane %u needs %zu bytes of shared memory per CTA (%d)",
+                    pop->d.W, pop->d.K, smem_op, max_optin);
+    CK(cudaFuncSetAttribute(k_onepass_eval<K, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_op));
+    int nbo = 0;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nbo, k_onepass_eval<K, V>, OP_EVAL_WARPS * 32, smem_op));
+    if (nbo < 1) nbo = 1;
+    if (nbo > OP_CTAS_PER_SM) nbo = OP_CTAS_PER_SM;
+    pop->grid_onepass = nbo * pop->nsm;
+    pop->smem_onepass = smem_op;
     return GP_OK;
 }
 
@@ -780,10 +793,9 @@ int gp_pop_create(const gp_config* cfg_in, const float* x, const float* targets,
                              : cfg.onepass_nodes == 0xFFFFFFFFu ? 0u
                              : (cfg.onepass_nodes < (uint32_t)ONEPASS_MAX ? cfg.onepass_nodes : (uint32_t)ONEPASS_MAX);
         g.onepass_max = pop->onepass_nodes;
-        pop->grid_onepass = pop->grid_items < 2 * pop->nsm ? pop->grid_items : 2 * pop->nsm;
         g.ovf_op = nullptr;
         if (pop->onepass_nodes)
-            DA2(g.ovf_op, (size_t)pop->grid_onepass * GP_WARPS * ONEPASS_DEPTH * 32 * K);
+            DA2(g.ovf_op, (size_t)pop->grid_onepass * OP_EVAL_WARPS * ONEPASS_DEPTH * 32 * K);
         std::vector<uint32_t> fb(P, 0u);
         for (uint32_t i = 0; i < nbuf - P; ++i) fb[i] = P + i;   // buffers P..nbuf-1 start free
         const uint32_t nfree_init = nbuf - P;
@@ -1431,7 +1443,7 @@ int launch_walk(gp_pop* pop, const CacheView& par) {
         CK(cudaMemsetAsync(pop->gb.op_cnt, 0, sizeof(uint32_t) * 2 * OP_BUCKETS, os));
         CK(cudaMemsetAsync(pop->gb.small_cnt, 0, sizeof(uint32_t) * d.P, os));
         k_onepass_plan<<<pop->nsm * 3, ONEPASS_WARPS * 32, sizeof(OnePassSmem), os>>>(d, pop->gb, par);
-        k_onepass_eval<K, V><<<pop->grid_onepass, GP_WARPS * 32, pop->smem_items, os>>>(d, pop->gb);
+        k_onepass_eval<K, V><<<pop->grid_onepass, OP_EVAL_WARPS * 32, pop->smem_onepass, os>>>(d, pop->gb);
         CK(cudaEventRecord(pop->ojoin_ev, os));
     }
     const uint32_t nl = pop->walk_long_n;

@@ -358,9 +358,13 @@ __device__ __forceinline__ void step_fast(uint32_t op, float (&acc)[K], uint32_t
 // warp's stack are touched -- every shared-memory layout keeps that much
 // room below each stack -- and so does a run that does not end with exactly
 // one entry (the initial running value) on the stack.
+//
+// `stop` (optional, as in interp_staged_lone below): a shared word that,
+// once nonzero, ends the run early with *aborted set; read every 16 words.
 template <int K, int V = VF>
 __device__ __forceinline__ void interp_staged(const uint8_t* stage, uint32_t s, uint32_t e,
-                                              Istate<K>& st, const Ictx<K>& c) {
+                                              Istate<K>& st, const Ictx<K>& c,
+                                              const volatile uint32_t* stop = nullptr, bool* aborted = nullptr) {
     const int lane = lane_id();
     const uint32_t a = s & ~15u;
     uint32_t p = e;
@@ -379,10 +383,13 @@ __device__ __forceinline__ void interp_staged(const uint8_t* stage, uint32_t s, 
     // bottom the difference wraps to a large value)
     const uint32_t span = (uint32_t)wfast * 32 * K * 4;
     bool under = false;
+    uint32_t words = 0;
     while (p >= s + 4) {
+        if (stop && (++words & 15u) == 0 && *stop) { *aborted = true; return; }
         if (st.sp >= 0 && st.sp <= wfast) {
             uint32_t sa = sbase + (uint32_t)st.sp * 32 * K * 4;
             do {
+                if (stop && (++words & 15u) == 0 && *stop) { *aborted = true; return; }
                 const uint32_t w = lds_u32(wa + p - 4);
                 step_fast<K, V>(w >> 24, st.acc, sa, kca, kba, c);
                 step_fast<K, V>((w >> 16) & 0xFFu, st.acc, sa, kca, kba, c);
@@ -527,40 +534,47 @@ __device__ __forceinline__ void interp_staged_lone(const uint8_t* stage, uint32_
     if (under || st.sp != 1) st.ok = false;
 }
 
-// interp_staged over a whole staged tree [0, n) that also hands out the
-// value of chosen nodes: cap(k) is called (warp-uniformly) right after node
-// pos(k) is evaluated, when st.acc holds the value of the subtree starting
-// there; the positions pos(0) > pos(1) > ... (ncap of them) are visited in
-// that order, since the scan runs right to left.  Words of four nodes that
-// hold no chosen node take the unchecked fast path.
+// interp_staged over one piece [lo, hi) of a tree (lo a multiple of 16,
+// `stage` holding bytes lo .. hi - 1) that also hands out the value of
+// chosen nodes: cap(k) is called (warp-uniformly) right after node pos(k)
+// is evaluated, when st.acc holds the value of the subtree starting there;
+// the positions pos(0) > pos(1) > ... (ncap of them) are visited in that
+// order, since the scan runs right to left.  The pieces of a tree are
+// taken right to left, the state (st, the cursor, `under`) carried from one
+// to the next; after the last one (lo = 0) the caller checks
+// `under || st.sp != 1`.  Words of four nodes that hold no chosen node take
+// the unchecked fast path.
+struct CaptureCursor {
+    uint32_t k;          // captures done
+    int32_t nextp;       // position of the next one, or -1
+};
+
 template <int K, int V, typename PosF, typename CapF>
-__device__ __forceinline__ void interp_staged_capture(const uint8_t* stage, uint32_t n, Istate<K>& st,
-                                                      const Ictx<K>& c, uint32_t ncap, PosF pos, CapF cap) {
+__device__ __forceinline__ void interp_capture_range(const uint8_t* stage, uint32_t lo, uint32_t hi, Istate<K>& st,
+                                                     const Ictx<K>& c, uint32_t ncap, CaptureCursor& cur,
+                                                     bool& under, PosF pos, CapF cap) {
     const int lane = lane_id();
-    uint32_t k = 0;
-    int32_t nextp = ncap ? (int32_t)pos(0) : -1;
     auto after = [&](uint32_t p) {
-        if ((int32_t)p == nextp) {
-            cap(k);
-            ++k;
-            nextp = (k < ncap) ? (int32_t)pos(k) : -1;
+        if ((int32_t)p == cur.nextp) {
+            cap(cur.k);
+            ++cur.k;
+            cur.nextp = (cur.k < ncap) ? (int32_t)pos(cur.k) : -1;
         }
     };
-    uint32_t p = n;
-    while (p > 0 && (p & 3u)) {
+    uint32_t p = hi;
+    while (p > lo && (p & 3u)) {
         --p;
-        step_checked<K, V>(stage[p], st, c, lane);
+        step_checked<K, V>(stage[p - lo], st, c, lane);
         after(p);
     }
-    const uint32_t wa = (uint32_t)__cvta_generic_to_shared(stage);
+    const uint32_t wa = (uint32_t)__cvta_generic_to_shared(stage) - lo;      // shared address of byte 0
     const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(c.s) + lane * K * 4;
     const uint32_t kca = (uint32_t)__cvta_generic_to_shared(c.kc);
     const uint32_t kba = (V == VB) ? (uint32_t)__cvta_generic_to_shared(c.kb) : 0u;
     const int wfast = c.W - 4;
     const uint32_t span = (uint32_t)wfast * 32 * K * 4;
-    bool under = false;
-    while (p >= 4) {
-        if (nextp >= (int32_t)p - 4) {
+    while (p >= lo + 4) {
+        if (cur.nextp >= (int32_t)p - 4) {
             // a chosen node in this word: node by node
             const uint32_t w = lds_u32(wa + p - 4);
 #pragma unroll
@@ -578,7 +592,7 @@ __device__ __forceinline__ void interp_staged_capture(const uint8_t* stage, uint
                 step_fast<K, V>((w >> 8) & 0xFFu, st.acc, sa, kca, kba, c);
                 step_fast<K, V>(w & 0xFFu, st.acc, sa, kca, kba, c);
                 p -= 4;
-            } while (p >= 4 && nextp < (int32_t)p - 4 && sa - sbase <= span);
+            } while (p >= lo + 4 && cur.nextp < (int32_t)p - 4 && sa - sbase <= span);
             under |= ((int32_t)(sa - sbase) < 0);
             st.sp = (int32_t)(sa - sbase) / (32 * K * 4);
         } else {
@@ -590,12 +604,11 @@ __device__ __forceinline__ void interp_staged_capture(const uint8_t* stage, uint
             p -= 4;
         }
     }
-    while (p > 0) {
+    while (p > lo) {
         --p;
-        step_checked<K, V>(stage[p], st, c, lane);
+        step_checked<K, V>(stage[p - lo], st, c, lane);
         after(p);
     }
-    if (under || st.sp != 1) st.ok = false;
 }
 
 // ---- staging with cp.async (16 bytes per lane per instruction) ----
