@@ -1987,8 +1987,17 @@ __global__ void __launch_bounds__(ONEPASS_WARPS * 32) k_onepass_plan(DevPop d, G
 
 template <int K, int V>
 __global__ void __launch_bounds__(OP_EVAL_WARPS * 32, 1) k_onepass_eval(DevPop d, GenBufs g) {
-    if (halted(d)) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    // CTAs beyond one warp per unit leave at once (most generations of large
+    // trees have few children this small); one thread decides for the CTA
+    __shared__ uint32_t s_units;
+    if (threadIdx.x == 0) {
+        uint32_t n = 0;
+        for (int b = 0; b < OP_BUCKETS; ++b) n += __ldcg(&g.op_cnt[b]);
+        s_units = halted(d) ? 0u : n * d.ncb;
+    }
+    __syncthreads();
+    if ((unsigned long long)blockIdx.x * OP_EVAL_WARPS >= s_units) return;
     float* kc = reinterpret_cast<float*>(smem_raw);
     const int lane = lane_id(), warp = threadIdx.x >> 5;
     fill_kc(kc, d.consts);

@@ -1427,25 +1427,34 @@ void swap_generation(gp_pop* pop) {
     std::swap(d.fit, g.pfit);
 }
 
-// The children of at most onepass_nodes nodes (one pass each), then the walk:
-// the first walk_long_n children of the work order by the large teams on
-// the second stream, the rest by the ordinary teams beside them.
+// The children of at most onepass_nodes nodes, one pass each, on a stream of
+// their own (own overflow stacks; their walk records and fitness are
+// disjoint from the walk's).  They need only the crossover, so they start
+// as soon as it is done, beside the work order; launch_walk joins them.
+bool onepass_on(const gp_pop* pop) { return !pop->gb.dis && pop->onepass_nodes; }
+
+template <int K, int V>
+int launch_onepass(gp_pop* pop, const CacheView& par) {
+    const DevPop& d = pop->d;
+    if (!onepass_on(pop)) return GP_OK;
+    cudaStream_t os = pop->side3;
+    CK(cudaEventRecord(pop->ofork_ev, pop->stream));
+    CK(cudaStreamWaitEvent(os, pop->ofork_ev, 0));
+    CK(cudaMemsetAsync(pop->gb.op_cnt, 0, sizeof(uint32_t) * 2 * OP_BUCKETS, os));
+    CK(cudaMemsetAsync(pop->gb.small_cnt, 0, sizeof(uint32_t) * d.P, os));
+    k_onepass_plan<<<pop->nsm * 3, ONEPASS_WARPS * 32, sizeof(OnePassSmem), os>>>(d, pop->gb, par);
+    k_onepass_eval<K, V><<<pop->grid_onepass, OP_EVAL_WARPS * 32, pop->smem_onepass, os>>>(d, pop->gb);
+    CK(cudaEventRecord(pop->ojoin_ev, os));
+    return GP_OK;
+}
+
+// The walk: the first walk_long_n children of the work order by the large
+// teams on the second stream, the rest by the ordinary teams beside them;
+// then the one-pass children are joined.
 template <int K, int V>
 int launch_walk(gp_pop* pop, const CacheView& par) {
     const DevPop& d = pop->d;
-    // the one-pass children on a stream of their own, beside the walk (own
-    // overflow stacks; their walk records and fitness are disjoint from the walk's)
-    const bool op = !pop->gb.dis && pop->onepass_nodes;
-    if (op) {
-        cudaStream_t os = pop->side3;
-        CK(cudaEventRecord(pop->ofork_ev, pop->stream));
-        CK(cudaStreamWaitEvent(os, pop->ofork_ev, 0));
-        CK(cudaMemsetAsync(pop->gb.op_cnt, 0, sizeof(uint32_t) * 2 * OP_BUCKETS, os));
-        CK(cudaMemsetAsync(pop->gb.small_cnt, 0, sizeof(uint32_t) * d.P, os));
-        k_onepass_plan<<<pop->nsm * 3, ONEPASS_WARPS * 32, sizeof(OnePassSmem), os>>>(d, pop->gb, par);
-        k_onepass_eval<K, V><<<pop->grid_onepass, OP_EVAL_WARPS * 32, pop->smem_onepass, os>>>(d, pop->gb);
-        CK(cudaEventRecord(pop->ojoin_ev, os));
-    }
+    const bool op = onepass_on(pop);
     const uint32_t nl = pop->walk_long_n;
     if (nl) {
         CK(cudaEventRecord(pop->wfork_ev, pop->stream));
@@ -1590,6 +1599,10 @@ int gen_incremental(gp_pop* pop) {
     CK(cudaMemsetAsync(d.q, 0, sizeof(uint32_t) * NQ, pop->stream));
     const int pb = (d.P + 255) / 256;
     const int mb = (d.P + 7) / 8 < pop->nsm * 2 ? (d.P + 7) / 8 : pop->nsm * 2;   // 8 samples per CTA pass
+    {
+        int r = with_kind(d, [&](auto k, auto v) { return launch_onepass<decltype(k)::value, decltype(v)::value>(pop, par); });
+        if (r) return r;
+    }
     // the work order was computed on the second stream since the crossover
     CK(cudaStreamWaitEvent(pop->stream, pop->pjoin_ev, 0));
     phase_begin(pop, PH_WALK);
