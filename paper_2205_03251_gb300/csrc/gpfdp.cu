@@ -100,6 +100,7 @@ struct gp_pop {
     cudaEvent_t xfork_ev[2], xjoin_ev[2];   // cache update: records beside counts, links beside the slot pool
     int grid_onepass;                 // CTAs of the one-pass interpreter (each with its own overflow stacks)
     size_t smem_onepass;              // its dynamic shared memory per CTA
+    uint32_t pack_launches;           // kernels of the last work-order computation
     uint32_t* rank;                   // [P] work-order ranks
     int prio_high;                    // greatest stream priority of the device (the large teams' launch)
     MlpBufs mlp;
@@ -1506,18 +1507,22 @@ int launch_pack(gp_pop* pop, const CacheView& par) {
     k_mlp_features<<<(d.P + 7) / 8, 256, 0, ms>>>(d, g, par, pop->mlp);
     const int mb = (d.P + 7) / 8 < pop->nsm * 2 ? (d.P + 7) / 8 : pop->nsm * 2;   // 8 samples per CTA pass
     k_mlp_infer<<<mb, 256, 0, ms>>>(pop->mlp, d.P, pop->mlp.pred_pack);
+    pop->pack_launches = 2;
     const dim3 rg((d.P + 255) / 256, (d.P + RANK_TILE - 1) / RANK_TILE);
     if (pop->cfg.packing == GP_PACK_MLP && d.P <= SORT_MAX) {
         CK(cudaMemsetAsync(pop->rank, 0, sizeof(uint32_t) * d.P, ms));
         k_rank_desc<<<rg, 256, 0, ms>>>(pop->mlp.pred_pack, d.P, pop->rank);
         k_rank_scatter<<<pb, 256, 0, ms>>>(pop->rank, d.P, g.order);
+        pop->pack_launches += 2;
     } else if (pop->cfg.packing == GP_PACK_STATIC && d.P <= SORT_MAX) {
         k_static_key<<<pb, 256, 0, ms>>>(d, g, pop->mlp);
         CK(cudaMemsetAsync(pop->rank, 0, sizeof(uint32_t) * d.P, ms));
         k_rank_desc<<<rg, 256, 0, ms>>>(pop->mlp.target, d.P, pop->rank);
         k_rank_scatter<<<pb, 256, 0, ms>>>(pop->rank, d.P, g.order);
+        pop->pack_launches += 3;
     } else {
         k_order_identity<<<pb, 256, 0, ms>>>(d, g);
+        pop->pack_launches += 1;
     }
     phase_end(pop, PH_PACK, ms);
     CK(cudaEventRecord(pop->pjoin_ev, ms));
@@ -1566,7 +1571,7 @@ int gen_crossover(gp_pop* pop, uint32_t generation) {
         pop->have_children = true;
         pop->lazy_pending = true;
         g.evaluated = false;
-        pop->launches = pop->have_next_plan_at_xo ? 7 : 3;
+        pop->launches = (pop->have_next_plan_at_xo ? 4u : 0u) + 3u + pop->pack_launches;
         return GP_OK;
     }
     k_plan<<<(d.P + 7) / 8, 256, 0, pop->stream>>>(d, g, par);
@@ -1584,7 +1589,7 @@ int gen_crossover(gp_pop* pop, uint32_t generation) {
     CK(cudaGetLastError());
     pop->have_children = true;
     g.evaluated = false;
-    pop->launches = 7;
+    pop->launches = 7 + pop->pack_launches;
     return GP_OK;
 }
 
@@ -1692,7 +1697,11 @@ int gen_incremental(gp_pop* pop) {
     k_accumulate<<<1, 32, 0, pop->stream>>>(pop->cum, d.acc_ops, g.gstat, pop->cases_stat, 1);
     ++pop->cum_calls;
     CK(cudaGetLastError());
-    pop->launches += 12 + 14 + 1 + ((g.dis || !pop->onepass_nodes) ? 0u : 1u) + (pop->walk_long_n ? 1u : 0u);
+    // walk (and the large teams), one-pass plan and evaluation, next plan and
+    // copies (fitness-first order, 3), walk records (2), merge counts (2),
+    // MLP training (7), merge, links (3), slot pool (6), statistics
+    pop->launches += 1 + (pop->walk_long_n ? 1u : 0u) + (onepass_on(pop) ? 2u : 0u) + (g.lazy ? 3u : 0u) + 2 + 2 + 7 +
+                     1 + 3 + 6 + 1;
     pop->have_children = false;
     g.evaluated = true;
     pop->last_kind = 1;
@@ -1700,7 +1709,6 @@ int gen_incremental(gp_pop* pop) {
     if (g.lazy) {
         pop->have_next_plan = true;
         pop->planned_gen = g.gen + 1;
-        pop->launches += 4;
     }
     return GP_OK;
 }

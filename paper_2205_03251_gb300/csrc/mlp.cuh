@@ -73,12 +73,12 @@ __device__ void mlp_stage(MlpSmem& m, const MlpBufs& b) {
     }
 }
 
-// One sample by one warp: lane l holds hidden units l and l + 32 of both
-// layers; returns the output (all lanes).
-__device__ __forceinline__ float mlp_forward_warp(const MlpSmem& m, const float* __restrict__ x, float& h1a,
-                                                  float& h1b, float& h2a, float& h2b) {
+// One sample by one warp: lane l < 16 holds feature l (xv), and lane l
+// holds hidden units l and l + 32 of both layers; returns the output (all
+// lanes).
+__device__ __forceinline__ float mlp_forward_lanes(const MlpSmem& m, float xv, float& h1a, float& h1b, float& h2a,
+                                                   float& h2b) {
     const int lane = lane_id();
-    const float xv = lane < MLP_IN ? x[lane] : 0.f;
     float a0 = m.b1[lane], a1 = m.b1[lane + 32];
 #pragma unroll
     for (int f = 0; f < MLP_IN; ++f) {
@@ -101,6 +101,13 @@ __device__ __forceinline__ float mlp_forward_warp(const MlpSmem& m, const float*
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) y += __shfl_xor_sync(FULL, y, o);
     return y + m.b3;
+}
+
+// The same with the sample's 16 features at x (global memory).
+__device__ __forceinline__ float mlp_forward_warp(const MlpSmem& m, const float* __restrict__ x, float& h1a,
+                                                  float& h1b, float& h2a, float& h2b) {
+    const int lane = lane_id();
+    return mlp_forward_lanes(m, lane < MLP_IN ? x[lane] : 0.f, h1a, h1b, h2a, h2b);
 }
 
 // Training pass over the batch (FP32 master weights): forward, keeping the
@@ -271,8 +278,6 @@ __global__ void k_mlp_init(MlpBufs b, uint64_t seed) {
     if (blockIdx.x == 0 && threadIdx.x == 0) *b.step = 0;
 }
 
-// Sort n (<= 4096) keys descending with their indices: one CTA, bitonic in
-// shared memory.  Ties keep the lower index first (stable order).
 #define SORT_MAX 16384     // work orders of larger populations are the identity
 #define RANK_TILE 1024     // keys compared by one CTA
 
