@@ -711,10 +711,16 @@ def main():
         walk_ops = st["cum_actual_ops"] / max(1, st["cum_calls"])
         walk_t = walk_ops / (walk_ms * 1e-3) / 1e12 if walk_ms > 0 else None
         per_child = profile_figure("k_walk_generation_200x1e6.md", "traffic_bytes_per_child") if profiled else None
+        # children of at most 4,096 nodes are interpreted in one pass (k_onepass_eval)
+        # beside the walk; on populations of small trees they are most of the phase
+        kernel = "k_walk (incremental evaluation with FDP; critical-path bound)"
+        if line["path_levels_per_child"] < 1.0:
+            kernel = ("k_walk and k_onepass_eval side by side (most children are evaluated in one pass; "
+                      "latency-bound)")
         line["roofline"] = {"bound": "alu", "achieved": walk_t, "peak": alu_peak, "unit": "TFLOP/s",
                             "frac": (walk_t / alu_peak) if walk_t else None,
                             "traffic": per_child * (len(w["off"]) - 1) if per_child else None,
-                            "kernel": "k_walk (incremental evaluation with FDP; critical-path bound)",
+                            "kernel": kernel,
                             "peak_note": alu_note, "timing": timing}
         # the HBM-bound part: the crossover kernels (their bytes are exact)
         ratio = profile_figure("k_copy_children_fitness_first_200x1e6.md" if args.lazy else
