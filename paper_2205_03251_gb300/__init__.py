@@ -231,12 +231,17 @@ def gp_root_values(h, P: int, C: int, kind: str = "f32") -> np.ndarray:
     return out[:, 0].copy() if (kind == "bool" and C == 64) else out
 
 
-def gp_get_tree(h, i: int) -> np.ndarray:
+def gp_get_tree(h, i: int, max_nodes: int = 0) -> np.ndarray:
+    """Tree i's opcodes.  With max_nodes (the population's bound) one call
+    reads them into a buffer of that size; else a first call asks for the
+    size."""
     n = ctypes.c_uint64()
-    _check(load().gp_get_tree(h, i, None, 0, ctypes.byref(n)), h)
-    out = np.empty(max(1, n.value), np.uint8)
+    if max_nodes <= 0:
+        _check(load().gp_get_tree(h, i, None, 0, ctypes.byref(n)), h)
+        max_nodes = n.value
+    out = np.empty(max(1, max_nodes), np.uint8)
     _check(load().gp_get_tree(h, i, _ptr(out), out.nbytes, ctypes.byref(n)), h)
-    return out[:n.value]
+    return out[:n.value] if 2 * n.value >= out.nbytes else out[:n.value].copy()
 
 
 def gp_cache_entries(h, i: int):
@@ -511,6 +516,7 @@ class Population:
             x = np.ascontiguousarray(x, np.int32).view(np.float32)
             t = np.ascontiguousarray(t, np.int32).view(np.float32)
             consts = np.ascontiguousarray(consts, np.int32).view(np.float32)
+        self.max_nodes = max_nodes
         cfg = GpConfig(pop_size=self.P, n_cases=self.C, max_nodes=max_nodes,
                        funcset=funcset,
                        cache_threshold=cache_threshold, tournament=tournament, packing=packing,
@@ -554,7 +560,7 @@ class Population:
         return gp_root_values(self.h, self.P, self.C, self.kind)
 
     def tree(self, i: int) -> np.ndarray:
-        return gp_get_tree(self.h, i)
+        return gp_get_tree(self.h, i, self.max_nodes)
 
     def cache_entries(self, i: int):
         return gp_cache_entries(self.h, i)

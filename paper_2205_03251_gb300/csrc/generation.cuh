@@ -892,6 +892,45 @@ __global__ void k_inplace_done(GenBufs g) {
     if (threadIdx.x == 0 && blockIdx.x == 0) *g.npend = 0;
 }
 
+// Individual i's bytes into `out` (a device buffer of at least cap bytes)
+// for gp_get_tree: from its own buffer, or -- a child of the fitness-first
+// order that is not built, or built in place only at the next crossover --
+// from its mother's head, the donated subtree in its father's buffer and
+// the mother's tail (Fig. 1).  meta = {size, 1 if the bytes are available}.
+// Every CTA derives the same pieces and copies its share of the bytes.
+__global__ void k_get_tree(DevPop d, GenBufs g, uint32_t i, uint32_t lazy_plan, uint8_t* __restrict__ out,
+                           uint32_t* __restrict__ meta) {
+    const uint32_t n = d.size[i], b = d.buf[i];
+    uint32_t fl0 = 0, npend = 0;
+    if (lazy_plan) { fl0 = g.flags[i]; npend = *g.npend; }
+    const bool pending = npend && (fl0 & F_INPLACE) && !(fl0 & F_CLONE);
+    const uint8_t* s0 = nullptr;
+    const uint8_t* s1 = nullptr;
+    const uint8_t* s2 = nullptr;
+    uint32_t l0 = n, l1 = 0, ok = 1;
+    if (b != BUF_NONE && !pending) {
+        s0 = d.arena + (size_t)b * d.cap;
+    } else {
+        const uint32_t m = g.mother[i], f = g.father[i], bm = g.pbuf[m], bf = g.pbuf[f];
+        if (bm == BUF_NONE || bf == BUF_NONE) {
+            ok = 0;
+        } else {
+            s0 = d.arena + (size_t)bm * d.cap;
+            if (!(g.flags[i] & F_CLONE)) {
+                const uint32_t c = g.cpos[i], r = g.rsz[i];
+                l0 = c;
+                l1 = g.ssz[i];
+                s1 = d.arena + (size_t)bf * d.cap + g.dpos[i];
+                s2 = s0 + c + r;                 // the tail: child byte x >= c + l1 is mother byte x - l1 + r
+            }
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) { meta[0] = n; meta[1] = ok; }
+    if (!ok || !out) return;
+    for (uint32_t x = blockIdx.x * blockDim.x + threadIdx.x; x < n; x += gridDim.x * blockDim.x)
+        out[x] = x < l0 ? s0[x] : x < l0 + l1 ? s1[x - l0] : s2[x - l0 - l1];
+}
+
 // ------------------------------------------------------------------ A7 incremental walk
 
 template <int K>

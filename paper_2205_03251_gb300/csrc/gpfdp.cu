@@ -101,6 +101,9 @@ struct gp_pop {
     int grid_onepass;                 // CTAs of the one-pass interpreter (each with its own overflow stacks)
     size_t smem_onepass;              // its dynamic shared memory per CTA
     uint32_t pack_launches;           // kernels of the last work-order computation
+    uint8_t* tree_out;                // [cap] device copy of one tree for gp_get_tree
+    uint32_t* tree_meta;              // [4] its size and availability
+    uint32_t* io_h;                   // [4] pinned host words: status, tree size and availability
     uint32_t* rank;                   // [P] work-order ranks
     int prio_high;                    // greatest stream priority of the device (the large teams' launch)
     MlpBufs mlp;
@@ -615,6 +618,7 @@ int gp_pop_create(const gp_config* cfg_in, const float* x, const float* targets,
     pop->stage_cap = 0;
     pop->launches = 0;
     pop->e_total_h = nullptr;
+    pop->io_h = nullptr;
     pop->last_kind = 0;
     pop->cases_stat = boolean ? 32u * cfg.n_cases : cfg.n_cases;
     memset(&pop->stats, 0, sizeof pop->stats);
@@ -721,6 +725,9 @@ int gp_pop_create(const gp_config* cfg_in, const float* x, const float* targets,
     cudaMemset(d.errinfo, 0, 4 * sizeof(uint32_t));
     DA2(d.e_total, 4);
     if (cudaMallocHost(&pop->e_total_h, sizeof(uint32_t)) != cudaSuccess) { g_create_error = "cudaMallocHost failed"; return bail(GP_ENOMEM); }
+    if (cudaMallocHost(&pop->io_h, 4 * sizeof(uint32_t)) != cudaSuccess) { g_create_error = "cudaMallocHost failed"; return bail(GP_ENOMEM); }
+    DA2(pop->tree_out, (size_t)d.cap + 16);
+    DA2(pop->tree_meta, 4);
     DA2(d.q, NQ);
     DA2(d.acc_ops, 4);
     StructBufs& sb = pop->sb;
@@ -906,6 +913,7 @@ void gp_pop_destroy(gp_pop* pop) {
     for (void* p : pop->allocs) cudaFree(p);
     for (int w = 0; w < 2; ++w) for (void* p : pop->sets[w].allocs) cudaFree(p);
     if (pop->e_total_h) cudaFreeHost(pop->e_total_h);
+    if (pop->io_h) cudaFreeHost(pop->io_h);
     if (pop->stage) cudaFree(pop->stage);
     if (pop->stage_off) cudaFree(pop->stage_off);
     for (int i = 0; i < NPH; ++i)
@@ -1137,10 +1145,12 @@ int gp_eval_incremental(gp_pop* pop, gp_stats* stats) {
 int gp_fitness(const gp_pop* cpop, float* host_out, uint32_t n) {
     gp_pop* pop = const_cast<gp_pop*>(cpop);
     if (!pop || !host_out || n > pop->d.P) return GP_EINVAL;
-    int rc = check_status(pop);
-    if (rc) return rc;
+    // the status word and the fitness values in one round trip (the values
+    // are not used when the status reports an error)
+    CK(cudaMemcpyAsync(pop->io_h, pop->d.status, sizeof(uint32_t), cudaMemcpyDeviceToHost, pop->stream));
     CK(cudaMemcpyAsync(host_out, pop->d.fit, sizeof(float) * n, cudaMemcpyDeviceToHost, pop->stream));
     CK(cudaStreamSynchronize(pop->stream));
+    if (pop->io_h[0]) return check_status(pop);
     return GP_OK;
 }
 
@@ -1171,50 +1181,24 @@ int gp_root_values(const gp_pop* cpop, void* host_out, size_t bytes) {
 int gp_get_tree(const gp_pop* cpop, uint32_t i, uint8_t* host_out, uint64_t cap, uint64_t* size) {
     gp_pop* pop = const_cast<gp_pop*>(cpop);
     if (!pop || i >= pop->d.P || !size) return GP_EINVAL;
-    int rc = check_status(pop);
-    if (rc) return rc;
-    uint32_t n = 0, b = 0;
-    CK(cudaMemcpy(&n, pop->d.size + i, sizeof n, cudaMemcpyDeviceToHost));
-    CK(cudaMemcpy(&b, pop->d.buf + i, sizeof b, cudaMemcpyDeviceToHost));
+    // the status word, the tree's size and availability in one round trip;
+    // the bytes (assembled on the device when the child is not built) in a second
+    const uint32_t lazy_plan = (pop->gb.lazy && pop->have_next_plan) ? 1u : 0u;
+    const int nb = (int)((pop->d.cap + 255) / 256) < 2 * pop->nsm ? (int)((pop->d.cap + 255) / 256) : 2 * pop->nsm;
+    k_get_tree<<<nb, 256, 0, pop->stream>>>(pop->d, pop->gb, i, lazy_plan, host_out ? pop->tree_out : nullptr,
+                                           pop->tree_meta);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(pop->io_h, pop->d.status, sizeof(uint32_t), cudaMemcpyDeviceToHost, pop->stream));
+    CK(cudaMemcpyAsync(pop->io_h + 1, pop->tree_meta, 2 * sizeof(uint32_t), cudaMemcpyDeviceToHost, pop->stream));
+    CK(cudaStreamSynchronize(pop->stream));
+    if (pop->io_h[0]) return check_status(pop);
+    const uint32_t n = pop->io_h[1];
     *size = n;
     if (!host_out) return GP_OK;
     if (cap < n) return fail(pop, GP_EINVAL, "host buffer too small for tree %u (%u nodes)", i, n);
-    // fitness-first order: a child that takes its mother's buffer is built
-    // there only at the next crossover; until then it is read like the
-    // children that are not built
-    uint32_t fl0 = 0, npend = 0;
-    if (pop->gb.lazy && pop->have_next_plan) {
-        CK(cudaMemcpy(&fl0, pop->gb.flags + i, 4, cudaMemcpyDeviceToHost));
-        CK(cudaMemcpy(&npend, pop->gb.npend, 4, cudaMemcpyDeviceToHost));
-    }
-    const bool pending = npend && (fl0 & F_INPLACE) && !(fl0 & F_CLONE);
-    if (b != BUF_NONE && !pending) {
-        CK(cudaMemcpy(host_out, pop->d.arena + (size_t)b * pop->d.cap, n, cudaMemcpyDeviceToHost));
-        return GP_OK;
-    }
-    // a child of the fitness-first order that is not built: mother's head,
-    // the donated subtree (from the father), mother's tail
-    const GenBufs& g = pop->gb;
-    uint32_t m = 0, f = 0, c = 0, r = 0, dd = 0, sv = 0, fl = 0, bm = 0, bf = 0;
-    CK(cudaMemcpy(&m, g.mother + i, 4, cudaMemcpyDeviceToHost));
-    CK(cudaMemcpy(&f, g.father + i, 4, cudaMemcpyDeviceToHost));
-    CK(cudaMemcpy(&c, g.cpos + i, 4, cudaMemcpyDeviceToHost));
-    CK(cudaMemcpy(&r, g.rsz + i, 4, cudaMemcpyDeviceToHost));
-    CK(cudaMemcpy(&dd, g.dpos + i, 4, cudaMemcpyDeviceToHost));
-    CK(cudaMemcpy(&sv, g.ssz + i, 4, cudaMemcpyDeviceToHost));
-    CK(cudaMemcpy(&fl, g.flags + i, 4, cudaMemcpyDeviceToHost));
-    CK(cudaMemcpy(&bm, g.pbuf + m, 4, cudaMemcpyDeviceToHost));
-    CK(cudaMemcpy(&bf, g.pbuf + f, 4, cudaMemcpyDeviceToHost));
-    if (bm == BUF_NONE || bf == BUF_NONE) return fail(pop, GP_ESTATE, "tree %u is no longer available", i);
-    const uint8_t* mb = pop->d.arena + (size_t)bm * pop->d.cap;
-    if (fl & F_CLONE) {
-        CK(cudaMemcpy(host_out, mb, n, cudaMemcpyDeviceToHost));
-        return GP_OK;
-    }
-    const uint8_t* fbp = pop->d.arena + (size_t)bf * pop->d.cap;
-    if (c) CK(cudaMemcpy(host_out, mb, c, cudaMemcpyDeviceToHost));
-    CK(cudaMemcpy(host_out + c, fbp + dd, sv, cudaMemcpyDeviceToHost));
-    if (n > c + sv) CK(cudaMemcpy(host_out + c + sv, mb + c + r, n - c - sv, cudaMemcpyDeviceToHost));
+    if (!pop->io_h[2]) return fail(pop, GP_ESTATE, "tree %u is no longer available", i);
+    CK(cudaMemcpyAsync(host_out, pop->tree_out, n, cudaMemcpyDeviceToHost, pop->stream));
+    CK(cudaStreamSynchronize(pop->stream));
     return GP_OK;
 }
 
@@ -1509,17 +1493,27 @@ int launch_pack(gp_pop* pop, const CacheView& par) {
     k_mlp_infer<<<mb, 256, 0, ms>>>(pop->mlp, d.P, pop->mlp.pred_pack);
     pop->pack_launches = 2;
     const dim3 rg((d.P + 255) / 256, (d.P + RANK_TILE - 1) / RANK_TILE);
+    // the order of the keys, largest first: one CTA for small populations
+    auto rank_order = [&](const float* key) -> int {
+        if (d.P <= RANK_SMALL) {
+            k_rank_small<<<1, 1024, 0, ms>>>(key, d.P, g.order);
+            pop->pack_launches += 1;
+        } else {
+            CK(cudaMemsetAsync(pop->rank, 0, sizeof(uint32_t) * d.P, ms));
+            k_rank_desc<<<rg, 256, 0, ms>>>(key, d.P, pop->rank);
+            k_rank_scatter<<<pb, 256, 0, ms>>>(pop->rank, d.P, g.order);
+            pop->pack_launches += 2;
+        }
+        return GP_OK;
+    };
     if (pop->cfg.packing == GP_PACK_MLP && d.P <= SORT_MAX) {
-        CK(cudaMemsetAsync(pop->rank, 0, sizeof(uint32_t) * d.P, ms));
-        k_rank_desc<<<rg, 256, 0, ms>>>(pop->mlp.pred_pack, d.P, pop->rank);
-        k_rank_scatter<<<pb, 256, 0, ms>>>(pop->rank, d.P, g.order);
-        pop->pack_launches += 2;
+        int r = rank_order(pop->mlp.pred_pack);
+        if (r) return r;
     } else if (pop->cfg.packing == GP_PACK_STATIC && d.P <= SORT_MAX) {
         k_static_key<<<pb, 256, 0, ms>>>(d, g, pop->mlp);
-        CK(cudaMemsetAsync(pop->rank, 0, sizeof(uint32_t) * d.P, ms));
-        k_rank_desc<<<rg, 256, 0, ms>>>(pop->mlp.target, d.P, pop->rank);
-        k_rank_scatter<<<pb, 256, 0, ms>>>(pop->rank, d.P, g.order);
-        pop->pack_launches += 3;
+        pop->pack_launches += 1;
+        int r = rank_order(pop->mlp.target);
+        if (r) return r;
     } else {
         k_order_identity<<<pb, 256, 0, ms>>>(d, g);
         pop->pack_launches += 1;

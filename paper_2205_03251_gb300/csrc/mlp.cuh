@@ -312,3 +312,23 @@ __global__ void __launch_bounds__(256) k_rank_desc(const float* __restrict__ key
 __global__ void k_rank_scatter(const uint32_t* __restrict__ rank, uint32_t n, uint32_t* __restrict__ order) {
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) order[rank[i]] = i;
 }
+
+// The same order for n <= RANK_SMALL keys in one CTA: every thread ranks its
+// keys against all n (staged in shared memory) and writes them to their
+// places, one launch instead of a clear, the ranks and the scatter.
+#define RANK_SMALL 1024
+__global__ void __launch_bounds__(1024) k_rank_small(const float* __restrict__ key, uint32_t n,
+                                                     uint32_t* __restrict__ order) {
+    __shared__ float kt[RANK_SMALL];
+    for (uint32_t j = threadIdx.x; j < n; j += blockDim.x) kt[j] = sort_key(key, j);
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
+        const float ki = kt[i];
+        uint32_t r = 0;
+        for (uint32_t j = 0; j < n; ++j) {
+            const float kj = kt[j];
+            r += (kj > ki || (kj == ki && j < i)) ? 1u : 0u;
+        }
+        order[r] = i;
+    }
+}
