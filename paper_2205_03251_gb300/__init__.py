@@ -560,7 +560,16 @@ class Population:
         return gp_root_values(self.h, self.P, self.C, self.kind)
 
     def tree(self, i: int) -> np.ndarray:
-        return gp_get_tree(self.h, i, self.max_nodes)
+        """Tree i's opcodes, read through a pinned host buffer kept by the
+        population (a device-to-host copy into pinned memory is several
+        times faster than into pageable memory)."""
+        if getattr(self, "_tree_buf", None) is None:
+            import torch
+            self._tree_buf = torch.empty(max(1, self.max_nodes), dtype=torch.uint8, pin_memory=True)
+        buf = self._tree_buf
+        n = ctypes.c_uint64()
+        _check(load().gp_get_tree(self.h, i, ctypes.c_void_p(buf.data_ptr()), buf.numel(), ctypes.byref(n)), self.h)
+        return buf.numpy()[:n.value].copy()
 
     def cache_entries(self, i: int):
         return gp_cache_entries(self.h, i)
