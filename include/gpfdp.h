@@ -215,7 +215,12 @@ int gp_fitness(const gp_pop* pop, float* host_out, uint32_t n);
  * `bytes` is the size of host_out.  Synchronising. */
 int gp_root_values(const gp_pop* pop, void* host_out, size_t bytes);
 
-/* Copy tree i (its size into *size) to host_out of capacity cap bytes.
+/* Copy tree i (its size into *size) to host_out of capacity cap bytes;
+ * host_out may be NULL to ask for the size only.  A child of the
+ * fitness-first order that is not built (or built in its mother's buffer
+ * only at the next crossover) is assembled from its parents (Fig. 1) by a
+ * kernel on the population's stream.  GP_EINVAL if cap is smaller than the
+ * tree, GP_ESTATE if its parents' buffers were given to other trees.
  * Synchronising. */
 int gp_get_tree(const gp_pop* pop, uint32_t i, uint8_t* host_out, uint64_t cap, uint64_t* size);
 
@@ -231,8 +236,8 @@ int gp_cache_value(const gp_pop* pop, uint32_t i, uint32_t j, void* host_out, si
 
 /* Per child of the last gp_eval_incremental: the level at which the walk
  * stopped (0 = at the crossover point; -1 = the root differed, fitness
- * recomputed; -2 = a child smaller than the cache threshold, evaluated in
- * one pass instead of walked -- same fitness bits) and the number of levels
+ * recomputed; -2 = a child of at most onepass_nodes nodes, evaluated in one
+ * pass instead of walked -- same fitness bits) and the number of levels
  * evaluated above the crossover point.  Either pointer may be NULL; n <=
  * pop_size.  Synchronising. */
 int gp_walk_info(const gp_pop* pop, int32_t* stop_level, uint32_t* levels, uint32_t n);
